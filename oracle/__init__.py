@@ -1,0 +1,242 @@
+"""CPU oracle for QIHT (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may
+import this package. It wraps the plain C implementation in qiht_oracle.c
+(FP64, single thread) with ctypes and numpy. It shares no code with the CUDA
+library of the package and never imports it.
+
+Functions mirror the paper's steps:
+  philox4x32_10, uniform         random numbers of the stochastic quantizer
+  absmax                         c_v = max |v| (Appendix, quantization lemma)
+  quantize / dequantize          Q(v, b) of Section III-A, and its value c * q_code
+  gemv_t, gemv_cols              plain FP64 products
+  top_s                          hard threshold H_s (Eq. NIHT)
+  niht                           Algorithm 2 (Algorithm 1 when both matrices are Phi)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qiht_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libqiht_oracle.so")
+
+# status codes of the oracle (same numbering as the CUDA library's, compared in tests)
+OK, ERR_ARG, ERR_BITS, ERR_NONFINITE, ERR_BACKTRACK_CAP = 0, 1, 2, 3, 5
+
+
+def build(force: bool = False, mutant: int = 0, out: str | None = None) -> str:
+    """Compile qiht_oracle.c into a shared library (gcc, no FMA contraction).
+
+    mutant != 0 builds a variant with one deliberate mistake (mutation tests only)."""
+    lib_path = out or (_LIB if mutant == 0 else os.path.join(_HERE, "_build", f"libqiht_oracle_m{mutant}.so"))
+    os.makedirs(os.path.dirname(lib_path), exist_ok=True)
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC):
+        return lib_path
+    tmp = lib_path + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           f"-DQO_MUTANT={int(mutant)}", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, lib_path)
+    return lib_path
+
+
+_lib = None
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("c", ctypes.c_double), ("max_backtrack", ctypes.c_int32)]
+
+
+class _Trace(ctypes.Structure):
+    _fields_ = [("support", ctypes.c_void_p), ("kth", ctypes.c_void_p), ("min_gap", ctypes.c_void_p),
+                ("mu", ctypes.c_void_p), ("bt", ctypes.c_void_p), ("min_margin", ctypes.c_void_p),
+                ("resid2", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("iters_run", ctypes.c_int32), ("backtracks", ctypes.c_int32),
+                ("support_changes", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("resid_norm2", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        # QIHT_ORACLE_LIB points the wrapper at another build (mutation tests only)
+        path = os.environ.get("QIHT_ORACLE_LIB") or build()
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        L.qo_philox4x32_10.argtypes = [P, P, P]
+        L.qo_philox4x32_10.restype = None
+        L.qo_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64]
+        L.qo_uniform.restype = ctypes.c_float
+        L.qo_absmax.argtypes = [P, ctypes.c_int64, P]
+        L.qo_absmax.restype = ctypes.c_float
+        L.qo_quantize.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                                  ctypes.c_uint32, ctypes.c_float, P]
+        L.qo_quantize.restype = ctypes.c_int
+        L.qo_dequantize.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_float, P]
+        L.qo_dequantize.restype = None
+        L.qo_gemv_t.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, P]
+        L.qo_gemv_t.restype = None
+        L.qo_gemv_cols.argtypes = [P, ctypes.c_int64, ctypes.c_int64, P, P, ctypes.c_int64, P]
+        L.qo_gemv_cols.restype = None
+        L.qo_top_s.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P]
+        L.qo_top_s.restype = None
+        L.qo_niht.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.POINTER(_Params), P, P, ctypes.POINTER(_Trace),
+                              ctypes.POINTER(_Report)]
+        L.qo_niht.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def philox4x32_10(counter, key) -> np.ndarray:
+    c = np.ascontiguousarray(counter, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().qo_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def uniform(seed: int, stream: int, e: int) -> float:
+    return float(lib().qo_uniform(seed, stream, e))
+
+
+def absmax(v: np.ndarray) -> tuple[float, int]:
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    bad = ctypes.c_int64(0)
+    c = lib().qo_absmax(_ptr(v), v.size, ctypes.addressof(bad))
+    return float(np.float32(c)), int(bad.value)
+
+
+def quantize(v: np.ndarray, bits: int, seed: int, stream: int, scale: float | None = None, *,
+             row0: int = 0, col0: int = 0, rows_total: int | None = None) -> tuple[np.ndarray, float]:
+    """Q(v, b) elementwise on a matrix (m x n) or vector (m,). Returns (codes, scale).
+
+    codes have the shape of v (uint16). scale is c = max |v| unless given (for
+    a block of a larger matrix, pass the whole matrix's scale, the block's
+    position and the whole matrix's row count).
+    """
+    v = np.asarray(v, dtype=np.float32)
+    vec = v.ndim == 1
+    v2 = np.ascontiguousarray(v.reshape(-1, 1) if vec else v)
+    rows, cols = v2.shape
+    if scale is None:
+        scale, bad = absmax(v2)
+        if bad:
+            raise ValueError("non-finite input")
+    codes = np.zeros((rows, cols), dtype=np.uint16)
+    st = lib().qo_quantize(_ptr(v2), rows, cols, cols, row0, col0,
+                           rows if rows_total is None else rows_total,
+                           bits, seed, stream, np.float32(scale), _ptr(codes))
+    if st != OK:
+        raise ValueError(f"qo_quantize status {st}")
+    return (codes.reshape(-1) if vec else codes), float(np.float32(scale))
+
+
+def dequantize(codes: np.ndarray, bits: int, scale: float) -> np.ndarray:
+    c = np.ascontiguousarray(codes, dtype=np.uint16)
+    out = np.zeros(c.shape, dtype=np.float64)
+    lib().qo_dequantize(_ptr(c), c.size, bits, np.float32(scale), _ptr(out))
+    return out
+
+
+def gemv_t(A: np.ndarray, r: np.ndarray) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    m, n = A.shape
+    g = np.zeros(n, dtype=np.float64)
+    lib().qo_gemv_t(_ptr(A), _ptr(r), m, n, _ptr(g))
+    return g
+
+
+def gemv_cols(A: np.ndarray, idx: np.ndarray, v: np.ndarray) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    m, n = A.shape
+    z = np.zeros(m, dtype=np.float64)
+    lib().qo_gemv_cols(_ptr(A), m, n, _ptr(idx), _ptr(v), idx.size, _ptr(z))
+    return z
+
+
+def top_s(a: np.ndarray, s: int) -> tuple[np.ndarray, np.ndarray]:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    sel = np.zeros(s, dtype=np.int32)
+    kth = np.zeros(2, dtype=np.float64)
+    lib().qo_top_s(_ptr(a), a.size, s, _ptr(sel), _ptr(kth))
+    return sel, kth
+
+
+@dataclass
+class NihtResult:
+    x: np.ndarray
+    support: np.ndarray
+    status: int
+    iters_run: int
+    backtracks: int
+    support_changes: int
+    resid_norm2: float
+    mu: float
+    trace: dict | None
+
+
+def niht(A1: np.ndarray, A2: np.ndarray, y: np.ndarray, s: int, iters: int, *, k: float = 2.0,
+         c: float = 0.01, max_backtrack: int = 32, trace: bool | str = False) -> NihtResult:
+    """Algorithm 2 with matrices A1 (for g = A1^T r) and A2 (for A2 x, mu, omega), FP64.
+
+    trace=True records supports, gaps, step sizes and residuals per iteration;
+    trace="x" also records every iterate."""
+    A1 = np.ascontiguousarray(A1, dtype=np.float64)
+    A2 = A1 if A2 is A1 else np.ascontiguousarray(A2, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    m, n = A1.shape
+    x = np.zeros(n, dtype=np.float64)
+    sup = np.zeros(s, dtype=np.int32)
+    p = _Params(k, c, max_backtrack)
+    rep = _Report()
+    tr = None
+    arrays = None
+    if trace:
+        T = iters + 1
+        arrays = {"support": np.zeros((T, s), np.int32), "kth": np.zeros((T, 2)),
+                  "min_gap": np.zeros(T), "mu": np.zeros(T), "bt": np.zeros(T, np.int32),
+                  "min_margin": np.zeros(T), "resid2": np.zeros(T),
+                  "x": np.zeros((T, n)) if trace == "x" else None}
+        tr = _Trace(*[_ptr(arrays[f]) if arrays[f] is not None else None for f, _ in _Trace._fields_])
+    lib().qo_niht(_ptr(A1), _ptr(A2), _ptr(y), m, n, s, iters, ctypes.byref(p), _ptr(x), _ptr(sup),
+                  ctypes.byref(tr) if tr is not None else None, ctypes.byref(rep))
+    if arrays is not None:
+        T = rep.iters_run + 1
+        arrays = {kk: vv[:T] for kk, vv in arrays.items() if vv is not None}
+    return NihtResult(x=x, support=sup, status=rep.status, iters_run=rep.iters_run,
+                      backtracks=rep.backtracks, support_changes=rep.support_changes,
+                      resid_norm2=rep.resid_norm2, mu=rep.mu, trace=arrays)
+
+
+def qiht(phi: np.ndarray, y: np.ndarray, s: int, iters: int, *, bits_phi: int, bits_y: int,
+         seed: int, **kw):
+    """Quantize Phi twice (streams 0 and 1) and y once (stream 2), then run Algorithm 2.
+
+    Returns (NihtResult, dict with codes and scales)."""
+    c1, sphi = quantize(phi, bits_phi, seed, 0)
+    c2, _ = quantize(phi, bits_phi, seed, 1, sphi)
+    cy, sy = quantize(y, bits_y, seed, 2)
+    A1 = dequantize(c1, bits_phi, sphi)
+    A2 = dequantize(c2, bits_phi, sphi)
+    yq = dequantize(cy, bits_y, sy)
+    res = niht(A1, A2, yq, s, iters, **kw)
+    return res, {"codes1": c1, "codes2": c2, "codes_y": cy, "scale_phi": sphi, "scale_y": sy,
+                 "A1": A1, "A2": A2, "yq": yq}

@@ -1,0 +1,402 @@
+/*
+ * qiht_oracle.c -- slow, plain reference implementation of QIHT.
+ *
+ * TEST INFRASTRUCTURE. Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load this library. The CUDA library of the
+ * package shares no code, header, table or constant generator with it, and
+ * neither side calls the other.
+ *
+ * Method: Gurel et al., "Compressive Sensing Using Iterative Hard Thresholding
+ * with Low Precision Data Representation" (IEEE TSP 2020):
+ *   - stochastic quantizer Q(v, b)                       Section III-A
+ *   - max-abs normalisation c_v before quantizing        Appendix, Lemma (quantization error)
+ *   - normalized IHT with adaptive step and backtracking Section II-A, Algorithm 1, Eq. (step_size)
+ *   - QIHT: NIHT on two independent quantizations        Section III-A, Algorithm 2
+ *
+ * Arithmetic: FP64 everywhere except the quantisation decision, which is
+ * taken in binary32 because the paper defines Q on single-precision inputs
+ * (Section III-A) and the decision must be identical on both sides.
+ * Build with -O2 -ffp-contract=off: no fused multiply-add anywhere.
+ *
+ * Readings of the paper (where it is silent or garbled):
+ *   - 2^b equally spaced levels on [-1, 1], spacing 2/(2^b - 1)   (Section III-A)
+ *   - scale c = max |v| over the whole matrix / vector; c = 0 -> the
+ *     normalised value is taken as 0 (the dequantised value is 0 anyway)
+ *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), one stream per
+ *     quantisation (the paper used XORShift on CPU; the generator is free)
+ *   - Algorithm 2's "x^{[n]}" inside g is x^{[n-1]}; the branches that set
+ *     x^{[n]} = x^{[n-1]} are read as "accept the proposal" (Section II-A text)
+ *   - the mu denominator uses the second quantisation only:
+ *     ||Q2[:, G] g_G||^2 (a positive number), and omega uses Q2 as well
+ *   - H_s keeps exactly s indices: order by |a| descending, then index ascending
+ *   - if ||g_G||^2 == 0 or ||Q2 g_G||^2 == 0 the solve stops (converged)
+ *
+ * QO_MUTANT (default 0) plants one deliberate mistake; it is set only by the
+ * mutation tests, which build such variants to show that the pins catch them.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define QO_OK 0
+#define QO_ERR_ARG 1
+#define QO_ERR_BITS 2
+#define QO_ERR_NONFINITE 3
+#define QO_ERR_BACKTRACK_CAP 5
+
+#ifndef QO_MUTANT
+#define QO_MUTANT 0
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As   */
+/* Easy as 1, 2, 3", SC'11. Multipliers and Weyl key increments as published. */
+/* ------------------------------------------------------------------ */
+void qo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0 && QO_MUTANT != 7) {  /* key schedule: add the Weyl constants */
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Uniform in [0, 1) for logical element e of one quantisation.
+ * Counter (e>>2 low word, e>>2 high word, stream, 0), key (seed low, seed high);
+ * element e uses output word e & 3; u = (word >> 8) * 2^-24. */
+float qo_uniform(uint64_t seed, uint32_t stream, uint64_t e)
+{
+    uint64_t q = e >> 2;
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), stream, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    qo_philox4x32_10(ctr, key, w);
+    return (float)(w[e & 3u] >> 8) * 0x1p-24f;
+}
+
+/* c_v = max_i |v_i| (Appendix, quantization-error lemma). Counts non-finite entries. */
+float qo_absmax(const float* v, int64_t count, int64_t* nonfinite)
+{
+    float c = 0.0f;
+    int64_t bad = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        float a = fabsf(v[i]);
+        if (!isfinite(a)) { ++bad; continue; }
+        if (a > c) c = a;
+    }
+    if (nonfinite) *nonfinite = bad;
+    return c;
+}
+
+/* One quantisation decision, Section III-A.
+ * Levels q_k = -1 + 2k/(L-1), k = 0..L-1, L = 2^b. With t = (v/c + 1)(L-1)/2,
+ * v lies between q_i and q_{i+1} for i = floor(t); it is rounded up to q_{i+1}
+ * with probability f = t - i (so E[Q(v)] = v) and down to q_i otherwise. */
+static int qo_code(float v, float c, int bits, float u)
+{
+    const int L = 1 << bits;
+    const float half = (QO_MUTANT == 2) ? (float)L * 0.5f : (float)(L - 1) * 0.5f;  /* exact */
+    float vt = (c > 0.0f) ? v / c : 0.0f;               /* binary32, round to nearest */
+    float t = (vt + 1.0f) * half;
+    if (t < 0.0f) t = 0.0f;
+    if (t > (float)(L - 1)) t = (float)(L - 1);
+    float fi = floorf(t);
+    float f = t - fi;                                    /* exact */
+    int code = (int)fi + ((QO_MUTANT == 1) ? (u > f ? 1 : 0) : (u < f ? 1 : 0));
+    if (code > L - 1) code = L - 1;
+    return code;
+}
+
+/* Quantise a block of a matrix. The block is rows x cols, row-major with row
+ * stride ld, and sits at (row0, col0) of a matrix with rows_total rows. The
+ * random number of element (i, j) is the one of logical index e = j*rows_total + i
+ * (column-major numbering), so the codes depend only on (i, j, seed, stream).
+ * codes: rows x cols, row-major. A vector is a matrix with one column. */
+int qo_quantize(const float* v, int64_t rows, int64_t cols, int64_t ld,
+                int64_t row0, int64_t col0, int64_t rows_total,
+                int bits, uint64_t seed, uint32_t stream, float scale, uint16_t* codes)
+{
+    if (bits < 1 || bits > 16) return QO_ERR_BITS;
+    if (!(scale >= 0.0f) || !isfinite(scale)) return QO_ERR_NONFINITE;
+    for (int64_t i = 0; i < rows; ++i) {
+        for (int64_t j = 0; j < cols; ++j) {
+            uint64_t e = (uint64_t)(col0 + j) * (uint64_t)rows_total + (uint64_t)(row0 + i);
+            float u = qo_uniform(seed, stream, e);
+            codes[i * cols + j] = (uint16_t)qo_code(v[i * ld + j], scale, bits, u);
+        }
+    }
+    return QO_OK;
+}
+
+/* Dequantised value c * q_code = (c / (L-1)) * (2 code - (L-1)), in FP64. */
+void qo_dequantize(const uint16_t* codes, int64_t count, int bits, float scale, double* out)
+{
+    const double lm1 = (double)((1 << bits) - 1);
+    const double alpha = (double)scale / lm1;
+    for (int64_t i = 0; i < count; ++i)
+        out[i] = alpha * (2.0 * (double)codes[i] - ((QO_MUTANT == 9) ? lm1 + 1.0 : lm1));
+}
+
+/* ------------------------------------------------------------------ */
+/* Dense products (A row-major m x n, FP64). Each output is one sum in     */
+/* ascending index order; loops are arranged so A is read row by row.     */
+/* ------------------------------------------------------------------ */
+
+/* g = A^T r */
+void qo_gemv_t(const double* A, const double* r, int64_t m, int64_t n, double* g)
+{
+    for (int64_t j = 0; j < n; ++j) g[j] = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        const double* row = A + i * n;
+        const double ri = r[i];
+        for (int64_t j = 0; j < n; ++j) g[j] += row[j] * ri;
+    }
+}
+
+/* z = A[:, idx] v over a list of columns (in list order) */
+void qo_gemv_cols(const double* A, int64_t m, int64_t n, const int32_t* idx, const double* v,
+                  int64_t k, double* z)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        const double* row = A + i * n;
+        double acc = 0.0;
+        for (int64_t t = 0; t < k; ++t) acc += row[idx[t]] * v[t];
+        z[i] = acc;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Hard threshold H_s (Eq. NIHT): keep the s entries of largest magnitude.  */
+/* Order: |a| descending, ties by index ascending; exactly s are kept.      */
+/* ------------------------------------------------------------------ */
+typedef struct { double key; int32_t idx; } qo_kv;
+
+static int qo_kv_cmp(const void* pa, const void* pb)
+{
+    const qo_kv* a = (const qo_kv*)pa;
+    const qo_kv* b = (const qo_kv*)pb;
+    if (QO_MUTANT == 5) { if (a->key < b->key) return -1; if (a->key > b->key) return 1; }
+    else { if (a->key > b->key) return -1; if (a->key < b->key) return 1; }
+    return (a->idx < b->idx) ? -1 : (a->idx > b->idx);
+}
+
+static int qo_int_cmp(const void* pa, const void* pb)
+{
+    int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    return (a > b) - (a < b);
+}
+
+/* sel: s indices sorted ascending; kth[0] = s-th largest |a|, kth[1] = (s+1)-th (0 if s == n).
+ * work: n entries of scratch. */
+void qo_hard_threshold(const double* a, int32_t n, int32_t s, int32_t* sel, double kth[2], qo_kv* work)
+{
+    for (int32_t j = 0; j < n; ++j) { work[j].key = fabs(a[j]); work[j].idx = j; }
+    qsort(work, (size_t)n, sizeof(qo_kv), qo_kv_cmp);
+    for (int32_t t = 0; t < s; ++t) sel[t] = work[t].idx;
+    qsort(sel, (size_t)s, sizeof(int32_t), qo_int_cmp);
+    kth[0] = (s > 0) ? work[s - 1].key : 0.0;
+    kth[1] = (s < n) ? work[s].key : 0.0;
+}
+
+/* exported for tests: H_s on a vector */
+void qo_top_s(const double* a, int32_t n, int32_t s, int32_t* sel, double* kth)
+{
+    qo_kv* work = (qo_kv*)malloc(sizeof(qo_kv) * (size_t)(n > 0 ? n : 1));
+    qo_hard_threshold(a, n, s, sel, kth, work);
+    free(work);
+}
+
+/* ------------------------------------------------------------------ */
+/* QIHT / NIHT (Algorithm 2; Algorithm 1 when A1 = A2 = Phi).               */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double k;              /* shrinkage, k > 1/(1-c) (Section II-A) */
+    double c;              /* small constant in (0, 1) */
+    int32_t max_backtrack; /* cap on mu shrinks per iteration */
+} qo_params;
+
+typedef struct {           /* all optional (NULL); arrays have iters + 1 rows */
+    int32_t* support;      /* (iters+1) x s: row 0 = initial support, row t = after iteration t */
+    double* kth;           /* (iters+1) x 2: s-th and (s+1)-th |a| of the accepted selection */
+    double* min_gap;       /* (iters+1): min relative gap (kth0-kth1)/kth0 over this iteration's selections */
+    double* mu;            /* (iters+1): accepted step size (row 0: 0) */
+    int32_t* bt;           /* (iters+1): number of shrinks */
+    double* min_margin;    /* (iters+1): min |mu - (1-c) omega| / mu over omega tests (INFINITY if none) */
+    double* resid2;        /* (iters+1): ||y - A2 x||^2 after the iteration */
+    double* x;             /* (iters+1) x n: iterate after each iteration (row 0 = 0) */
+} qo_trace;
+
+typedef struct {
+    int32_t iters_run;
+    int32_t backtracks;
+    int32_t support_changes;
+    int32_t status;
+    double resid_norm2;
+    double mu;
+} qo_report;
+
+static double qo_rel_gap(const double kth[2])
+{
+    return kth[0] > 0.0 ? (kth[0] - kth[1]) / kth[0] : 0.0;
+}
+
+static int qo_same_set(const int32_t* a, const int32_t* b, int32_t s)
+{
+    for (int32_t t = 0; t < s; ++t) if (a[t] != b[t]) return 0;
+    return 1;
+}
+
+static double qo_resid2(const double* A2, const double* y, int32_t m, int32_t n,
+                        const int32_t* sup, const double* x, int32_t s, double* xs, double* z)
+{
+    for (int32_t t = 0; t < s; ++t) xs[t] = x[sup[t]];
+    qo_gemv_cols(A2, m, n, sup, xs, s, z);
+    double acc = 0.0;
+    for (int32_t i = 0; i < m; ++i) { double r = y[i] - z[i]; acc += r * r; }
+    return acc;
+}
+
+/* A1, A2: m x n row-major (the two dequantised matrices, or Phi twice).
+ * y: m. x: n (output, s-sparse). support: s (output, ascending).
+ * Returns a status code; rep is filled in any case. */
+int qo_niht(const double* A1, const double* A2, const double* y, int32_t m, int32_t n, int32_t s,
+            int32_t iters, const qo_params* p, double* x, int32_t* support, qo_trace* tr,
+            qo_report* rep)
+{
+    memset(rep, 0, sizeof(*rep));
+    if (m <= 0 || n <= 0 || s <= 0 || s > n || s > m || iters < 0) {
+        rep->status = QO_ERR_ARG;
+        return QO_ERR_ARG;
+    }
+    const double shrink = p->k * (1.0 - p->c);
+    double* g = (double*)malloc(sizeof(double) * (size_t)n);
+    double* a = (double*)malloc(sizeof(double) * (size_t)n);
+    double* r = (double*)malloc(sizeof(double) * (size_t)m);
+    double* z = (double*)malloc(sizeof(double) * (size_t)m);
+    double* xn = (double*)malloc(sizeof(double) * (size_t)n);
+    double* coef = (double*)malloc(sizeof(double) * (size_t)(2 * s));
+    int32_t* uni = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * s));
+    int32_t* sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)s);
+    qo_kv* work = (qo_kv*)malloc(sizeof(qo_kv) * (size_t)n);
+    int status = QO_OK;
+
+    /* Initialisation (Algorithm 2): x = 0, support of H_s(A1^T y). */
+    for (int32_t j = 0; j < n; ++j) x[j] = 0.0;
+    qo_gemv_t(A1, y, m, n, g);
+    double kth[2];
+    qo_hard_threshold(g, n, s, support, kth, work);
+    if (tr) {
+        if (tr->support) memcpy(tr->support, support, sizeof(int32_t) * (size_t)s);
+        if (tr->kth) { tr->kth[0] = kth[0]; tr->kth[1] = kth[1]; }
+        if (tr->min_gap) tr->min_gap[0] = qo_rel_gap(kth);
+        if (tr->mu) tr->mu[0] = 0.0;
+        if (tr->bt) tr->bt[0] = 0;
+        if (tr->min_margin) tr->min_margin[0] = INFINITY;
+        if (tr->resid2) { double acc = 0.0; for (int32_t i = 0; i < m; ++i) acc += y[i] * y[i]; tr->resid2[0] = acc; }
+        if (tr->x) memcpy(tr->x, x, sizeof(double) * (size_t)n);
+    }
+
+    int32_t t;
+    for (t = 1; t <= iters; ++t) {
+        /* g = A1^T (y - A2 x) */
+        for (int32_t q = 0; q < s; ++q) coef[q] = x[support[q]];
+        qo_gemv_cols(A2, m, n, support, coef, s, z);
+        for (int32_t i = 0; i < m; ++i) r[i] = (QO_MUTANT == 8) ? z[i] - y[i] : y[i] - z[i];
+        qo_gemv_t((QO_MUTANT == 3) ? A2 : A1, r, m, n, g);
+
+        /* step size (Eq. step_size on the current support) */
+        double num = 0.0;
+        for (int32_t q = 0; q < s; ++q) {
+            double gq = g[support[q]];
+            num += (QO_MUTANT == 4) ? fabs(gq) : gq * gq;
+            coef[q] = gq;
+        }
+        qo_gemv_cols(A2, m, n, support, coef, s, z);
+        double den = 0.0;
+        for (int32_t i = 0; i < m; ++i) den += z[i] * z[i];
+        if (num == 0.0 || den == 0.0) break;               /* converged: x unchanged */
+        double mu = num / den;
+
+        /* proposal x' = H_s(x + mu g) */
+        for (int32_t j = 0; j < n; ++j) a[j] = x[j] + mu * g[j];
+        qo_hard_threshold(a, n, s, sel, kth, work);
+        double min_gap = qo_rel_gap(kth);
+        double min_margin = INFINITY;
+        int32_t nbt = 0;
+        int changed = !qo_same_set(sel, support, s);
+
+        if (changed) {
+            for (;;) {
+                /* x' on its support; Delta = x' - x over the union of supports */
+                for (int32_t j = 0; j < n; ++j) xn[j] = 0.0;
+                for (int32_t q = 0; q < s; ++q) xn[sel[q]] = a[sel[q]];
+                int32_t nu = 0;
+                for (int32_t q = 0; q < s; ++q) uni[nu++] = sel[q];
+                for (int32_t q = 0; q < s; ++q) {
+                    int32_t j = support[q];
+                    int in_new = 0;
+                    for (int32_t w = 0; w < s; ++w) if (sel[w] == j) { in_new = 1; break; }
+                    if (!in_new) uni[nu++] = j;
+                }
+                double dn = 0.0;
+                for (int32_t q = 0; q < nu; ++q) { coef[q] = xn[uni[q]] - x[uni[q]]; dn += coef[q] * coef[q]; }
+                if (dn == 0.0) break;                        /* nothing moves: accept */
+                qo_gemv_cols(A2, m, n, uni, coef, nu, z);
+                double dd = 0.0;
+                for (int32_t i = 0; i < m; ++i) dd += z[i] * z[i];
+                double omega = (dd > 0.0) ? dn / dd : INFINITY;
+                double bound = (1.0 - p->c) * omega;
+                double margin = fabs(mu - bound) / mu;
+                if (margin < min_margin) min_margin = margin;
+                if ((QO_MUTANT == 6) ? (mu > bound) : (mu <= bound)) break;  /* sufficient decrease holds */
+                if (nbt >= p->max_backtrack) { status = QO_ERR_BACKTRACK_CAP; break; }
+                mu = mu / shrink;
+                ++nbt;
+                for (int32_t j = 0; j < n; ++j) a[j] = x[j] + mu * g[j];
+                qo_hard_threshold(a, n, s, sel, kth, work);
+                double gp = qo_rel_gap(kth);
+                if (gp < min_gap) min_gap = gp;
+                if (qo_same_set(sel, support, s)) break;
+            }
+        }
+        if (status != QO_OK) break;
+
+        /* accept x' */
+        if (!qo_same_set(sel, support, s)) rep->support_changes++;
+        for (int32_t q = 0; q < s; ++q) x[support[q]] = 0.0;
+        for (int32_t q = 0; q < s; ++q) x[sel[q]] = a[sel[q]];
+        memcpy(support, sel, sizeof(int32_t) * (size_t)s);
+        rep->backtracks += nbt;
+        rep->mu = mu;
+        if (tr) {
+            if (tr->support) memcpy(tr->support + (size_t)t * s, support, sizeof(int32_t) * (size_t)s);
+            if (tr->kth) { tr->kth[2 * t] = kth[0]; tr->kth[2 * t + 1] = kth[1]; }
+            if (tr->min_gap) tr->min_gap[t] = min_gap;
+            if (tr->mu) tr->mu[t] = mu;
+            if (tr->bt) tr->bt[t] = nbt;
+            if (tr->min_margin) tr->min_margin[t] = min_margin;
+            if (tr->resid2) tr->resid2[t] = qo_resid2(A2, y, m, n, support, x, s, coef, z);
+            if (tr->x) memcpy(tr->x + (size_t)t * n, x, sizeof(double) * (size_t)n);
+        }
+    }
+    rep->iters_run = (t > iters) ? iters : t - 1;
+    rep->status = status;
+    rep->resid_norm2 = qo_resid2(A2, y, m, n, support, x, s, coef, z);
+
+    free(g); free(a); free(r); free(z); free(xn); free(coef); free(uni); free(sel); free(work);
+    return status;
+}
