@@ -1,0 +1,375 @@
+"""Benchmark of the QIHT hot path on one GB300 (or N replicas under torchrun).
+
+Workload (the large single solve): Gaussian Phi 8192 x 32768 with entries
+N(0, 1/m), x with s = 256 nonzeros +-U(0.5, 1.5), y = Phi x + noise at 30 dB,
+Phi and y quantized to b bits (default 8), 300 QIHT iterations.
+
+One step = the whole hot path on one input: max |Phi|, max |y|, three stochastic
+quantizations (Q1, Q2 of Phi, Q(y)) and the 300-iteration solve (one CUDA graph).
+value   = iterations per second over the timed steps (inputs resident in HBM).
+e2e     = the same metric with Phi and y copied from pinned host memory and x,
+          the support and the report copied back, inside the timed region.
+roofline: the gradient kernel g = Q1^T r (one pass over the codes of Q1), timed
+          alone with CUDA events on its stream with the solver's launch plan;
+          algorithmic bytes = m n b / 8 + 4 m + 4 n per launch.
+cpu_baseline / --impl reference: the CPU oracle (plain FP64 C, one thread) on a
+          bounded sample (the first rows of the same matrix), scaled per iteration.
+
+Under torchrun with N > 1 ranks, every rank solves its own independent instance
+(replicas; no collective in the data path) and the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+M, N, S, ITERS = 8192, 32768, 256, 300
+METRIC = "NIHT iterations/s"
+UNIT = "iterations/s"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemv_t_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--bits", type=int, default=8)
+    ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--m", type=int, default=M)
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--s", type=int, default=S)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gemv-launches", type=int, default=200)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config(args, world):
+    return {"workload": f"large single solve: Gaussian Phi {args.m}x{args.n} N(0,1/m), s={args.s}, "
+                        f"x=+-U(0.5,1.5), 30 dB, Phi and y quantized to {args.bits} bits, {args.iters} iterations",
+            "m": args.m, "n": args.n, "s": args.s, "bits_phi": args.bits, "bits_y": args.bits,
+            "iters_per_step": args.iters, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2: Q1 codes %.0f MiB streamed every iteration" %
+                  (args.m * args.n * args.bits / 8 / 2**20),
+            "step": "max|Phi|, max|y|, quantize Q1, Q2, Q(y), 300-iteration solve (one graph launch)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(p, bits, iters_total, rows=1024, iters=8):
+    """Oracle timing on the first `rows` rows of the workload (same n, s): the
+    quantization and the per-iteration work scale linearly with m, so the step
+    time of the full problem is estimated as (m/rows) x (quantize time +
+    iters_total x per-iteration time)."""
+    import oracle
+    sub_phi = np.ascontiguousarray(p.phi[:rows])
+    sub_y = np.ascontiguousarray(p.y[:rows])
+    t0 = time.perf_counter()
+    c1, sphi = oracle.quantize(sub_phi, bits, 0, 0)
+    c2, _ = oracle.quantize(sub_phi, bits, 0, 1, sphi)
+    cy, sy = oracle.quantize(sub_y, bits, 0, 2)
+    A1 = oracle.dequantize(c1, bits, sphi)
+    A2 = oracle.dequantize(c2, bits, sphi)
+    yq = oracle.dequantize(cy, bits, sy)
+    t1 = time.perf_counter()
+    oracle.niht(A1, A2, yq, p.s, iters)
+    t2 = time.perf_counter()
+    scale = p.m / rows
+    t_quant = (t1 - t0) * scale
+    t_iter = (t2 - t1) / iters * scale
+    step = t_quant + iters_total * t_iter
+    return {"value": iters_total / step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} of {p.m} rows (n={p.n}, s={p.s}): quantize Q1,Q2,Q(y) + {iters} "
+                      f"iterations, single-threaded FP64 C; step time scaled by m/{rows} = {scale:g}",
+            "sample_seconds": round(t2 - t0, 3), "est_step_seconds": round(step, 3)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    p = synth.large_noisy(seed=0, m=args.m, n=args.n, s=args.s)
+    for _ in range(args.warmup):
+        oracle_sample(p, args.bits, args.iters, rows=256, iters=2)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(p, args.bits, args.iters)
+        vals.append(last["est_step_seconds"])
+    wall = time.perf_counter() - t0
+    step = statistics.mean(vals)
+    value = args.iters / step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_seconds": round(wall, 2)}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/qiht_clocks_{os.getpid()}.csv"
+        self.uuid = uuid
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for_kernel(bits):
+    """DRAM bytes per launch of the gradient kernel from a committed ncu summary,
+    only while the kernel source is unchanged since the capture."""
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+        src = open(os.path.join(ROOT, "paper_1802_04907_gb300", "csrc", "gemv.cu"), "rb").read()
+        if d.get("gemv_cu_sha1") != hashlib.sha1(src).hexdigest():
+            return None
+        return d.get("bytes_per_launch", {}).get(str(bits))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1802_04907_gb300 as q
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    p = synth.large_noisy(seed=rank, m=args.m, n=args.n, s=args.s)
+    phi_h = torch.from_numpy(p.phi).pin_memory()
+    y_h = torch.from_numpy(p.y).pin_memory()
+    phi = phi_h.to(dev)
+    y = y_h.to(dev)
+    bits = args.bits
+    codes = q.quantize_problem(phi, y, bits, bits, seed=rank)
+    solver = q.Solver(args.m, args.n, args.s, args.iters, device=dev)
+
+    def step():
+        q.quantize_problem(phi, y, bits, bits, seed=rank, out=codes)
+        solver(*codes)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    rep0 = solver.read_report()
+    assert rep0.status == q.OK, rep0
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clk = Clocks(uuid)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.stop()
+    rep = solver.read_report()
+    iters_done = rep.iters_run
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps * iters_done / (ms_max / 1e3)
+
+    # solve only (quantization excluded), same buffers
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solver(*codes)
+    ev1.record(stream)
+    barrier()
+    solve_ms = ev0.elapsed_time(ev1) / args.steps
+
+    # gradient kernel alone: average launch duration with CUDA events on its stream
+    q1 = codes[0]
+    r = (torch.randn(args.m, device=dev) * 0.01).float()
+    rmax = r.abs().max().reshape(1).contiguous()
+    g = torch.empty(args.n, dtype=torch.float32, device=dev)
+    for _ in range(5):
+        q.gemv_t_prescaled(q1, r, rmax, g, stream=stream)
+    barrier()
+    nl = args.gemv_launches
+    ev0.record(stream)
+    for _ in range(nl):
+        q.gemv_t_prescaled(q1, r, rmax, g, stream=stream)
+    ev1.record(stream)
+    barrier()
+    gemv_ms = ev0.elapsed_time(ev1) / nl
+    alg_bytes = args.m * args.n * bits / 8 + 4 * args.m + 4 * args.n
+    peak, peak_kind = load_peaks()
+    achieved = alg_bytes / (gemv_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_for_kernel(bits), "kernel": "k_gemv_t (g = Q1^T r)",
+                "avg_launch_us": gemv_ms * 1e3, "algorithmic_bytes_per_launch": alg_bytes,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+
+    # end to end: host buffers in, host results out, through the public API
+    e2e = None
+    if not args.no_e2e:
+        x_h = torch.empty(args.n, dtype=torch.float32).pin_memory()
+        sup_h = torch.empty(args.s, dtype=torch.int32).pin_memory()
+        rep_h = torch.empty(q.REPORT_BYTES, dtype=torch.uint8).pin_memory()
+
+        def e2e_step():
+            phi.copy_(phi_h, non_blocking=True)
+            y.copy_(y_h, non_blocking=True)
+            step()
+            x_h.copy_(solver.x, non_blocking=True)
+            sup_h.copy_(solver.support, non_blocking=True)
+            rep_h.copy_(solver.report, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        ev1.record(stream)
+        barrier()
+        e_ms = ev0.elapsed_time(ev1)
+        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps * iters_done / (float(te.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(p.phi.nbytes + p.y.nbytes),
+               "d2h_bytes_per_step": int(4 * args.n + 4 * args.s + q.REPORT_BYTES)}
+
+    # kernels launched per step: 2 max-abs + 3 quantize, 3 in the solver's set-up,
+    # 5 per iteration (step size, threshold, backtracking test, residual, gradient)
+    # plus 2 per step-size shrink
+    launches_per_step = 5 + 3 + 5 * iters_done + 2 * rep.backtracks
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(p, bits, args.iters)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": f"u{bits}", "data": "synthetic",
+                "config": config(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": args.steps * launches_per_step,
+                "solve_only": {"ms_per_solve": solve_ms, "iters_per_s": iters_done / (solve_ms / 1e3),
+                               "us_per_iter": solve_ms * 1e3 / max(iters_done, 1)},
+                "arith": "codes x 24-bit fixed-point residual via dp4a, exact int accumulation; FP32 vectors; "
+                         "FP64 step size and norms",
+                "report": {"iters_run": rep.iters_run, "backtracks": rep.backtracks,
+                           "support_changes": rep.support_changes, "resid_norm2": rep.resid_norm2}}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

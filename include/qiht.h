@@ -1,0 +1,196 @@
+/*
+ * qiht.h -- C ABI of the QIHT library (GB300, sm_103a).
+ *
+ * QIHT is normalized iterative hard thresholding run on stochastically
+ * quantized data: Gurel et al., "Compressive Sensing Using Iterative Hard
+ * Thresholding with Low Precision Data Representation", IEEE TSP 2020.
+ *   problem      y = Phi x + e, minimise ||y - Phi x||^2 s.t. ||x||_0 <= s     (Section I-A)
+ *   quantizer    Q(v, b): 2^b levels on [-1, 1], stochastic rounding            (Section III-A)
+ *   iteration    x <- H_s(x + mu Q1^T (Q(y) - Q2 x)), adaptive mu, backtracking (Algorithm 2)
+ *
+ * Conventions (every entry point):
+ *   - Pointers marked [device] are CUDA device addresses; [host] are host
+ *     addresses. The caller owns every buffer, including workspaces. The
+ *     library never allocates device memory on these paths.
+ *   - Calls are asynchronous on `stream` unless stated otherwise; results are
+ *     valid after the stream is synchronised. NULL stream = legacy default stream.
+ *   - Argument errors are detected on the host before any launch and returned
+ *     as a status; nothing is launched then. Errors found on the device (non-
+ *     finite scales, a backtracking cap) are written to the device report.
+ *   - No exception crosses this boundary.
+ *
+ * Code matrix layout ("column-packed"): a quantized rows x cols matrix is
+ * stored as cols columns of ld_words 32-bit words each, column j starting at
+ * word j * ld_words (16-byte aligned). With G = 32 / bits codes per word, word
+ * q of a column holds rows q*G .. q*G+G-1; the code of row q*G + 4k + p
+ * (k = 0 .. G/4-1, p = 0..3) sits at bit 8p + bits*k. Rows past `rows` hold
+ * code 0 and never contribute. A vector is a matrix with one column.
+ * The value of code c is scale * (2c - (2^bits - 1)) / (2^bits - 1).
+ *
+ * Random numbers of the quantizer: Philox4x32-10 (Salmon et al., SC'11) with
+ * key (seed low 32 bits, seed high 32 bits) and counter (e>>2 low, e>>2 high,
+ * stream_id, 0), where e = j * rows + i is the column-major index of element
+ * (i, j); element e uses output word e & 3 and u = (word >> 8) * 2^-24.
+ * The rounding decision is taken in binary32: t = (v / c + 1) * (2^b - 1) / 2,
+ * code = floor(t) + (u < t - floor(t)), each operation correctly rounded.
+ */
+#ifndef QIHT_H
+#define QIHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QIHT_ABI_VERSION 1
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* qiht_stream_t;
+
+typedef enum {
+    QIHT_OK = 0,
+    QIHT_ERR_ARG = 1,            /* null pointer, size out of range, s > m or s > n, ... */
+    QIHT_ERR_BITS = 2,           /* bits not in {2, 4, 8} */
+    QIHT_ERR_NONFINITE = 3,      /* NaN or Inf in the input (its scale is not finite) */
+    QIHT_ERR_TIMEOUT = 4,        /* a device-side wait ran out of its budget */
+    QIHT_ERR_BACKTRACK_CAP = 5,  /* the step size was shrunk max_backtrack times in one iteration */
+    QIHT_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+    QIHT_ERR_WORKSPACE = 7       /* workspace missing, too small or not 256-byte aligned */
+} qiht_status;
+
+/* Human-readable name of a status (static string). */
+const char* qiht_status_string(int32_t status);
+
+/* Version of this ABI (QIHT_ABI_VERSION of the built library). */
+int32_t qiht_abi_version(void);
+
+/* A quantized matrix or vector in the column-packed layout (see above). */
+typedef struct {
+    const uint32_t* words;   /* [device] cols * ld_words words */
+    const float* scale;      /* [device] one float: c = max |v| used by the quantizer */
+    int32_t rows;            /* rows of the logical matrix (length of a vector) */
+    int32_t cols;            /* columns (1 for a vector) */
+    int32_t bits;            /* 2, 4 or 8 */
+    int32_t ld_words;        /* words per column; must equal qiht_ld_words(rows, bits) */
+} qiht_codes;
+
+/* Words per column of the column-packed layout: ceil(rows / (32/bits)) rounded
+ * up to a multiple of 4. Returns -1 for bits not in {2, 4, 8} or rows < 1. */
+int32_t qiht_ld_words(int32_t rows, int32_t bits);
+
+/* ---------------------------------------------------------------------- */
+/* Quantization (Section III-A; scale c_v = max |v| from the Appendix's    */
+/* quantization-error lemma)                                                */
+/* ---------------------------------------------------------------------- */
+
+#define QIHT_SCALE_GIVEN   1  /* use *scale as it is (do not compute max |v|) */
+#define QIHT_CHECK_FINITE  2  /* synchronise `stream` and return QIHT_ERR_NONFINITE if the scale is not finite */
+
+/* Quantize a rows x cols float32 matrix `in` [device], row-major with row
+ * stride ld_in >= cols (floats), to `bits`-bit codes in the column-packed
+ * layout at `words` [device, cols * ld_words words, 16-byte aligned]. *scale
+ * [device] receives c = max |in| (or is read, with QIHT_SCALE_GIVEN). A
+ * non-finite input makes *scale non-finite. seed and stream_id select the
+ * random numbers (the solver uses 0 for Q1, 1 for Q2, 2 for y by convention).
+ * Launches two kernels (max |v|, then quantize + pack) unless the scale is given. */
+qiht_status qiht_quantize(const float* in, int32_t rows, int32_t cols, int64_t ld_in, int32_t bits,
+                          uint64_t seed, uint32_t stream_id, int32_t flags,
+                          uint32_t* words, int32_t ld_words, float* scale, qiht_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Building blocks of one iteration (exposed for tests and measurement)     */
+/* ---------------------------------------------------------------------- */
+
+/* g = Q^T r: the gradient product of Algorithm 2 (g = Q1^T r), one pass over
+ * all codes of Q. r [device, Q->rows floats], g [device, Q->cols floats].
+ * Inner sums are exact: r is converted to 24-bit block fixed point (scale =
+ * a power of two set by max |r|) and codes times fixed-point r are summed in
+ * integers; the result is scaled once per column. Requires Q->rows <= 16384.
+ * Workspace: qiht_gemv_t_workspace_size() bytes, 256-byte aligned. */
+size_t qiht_gemv_t_workspace_size(void);
+qiht_status qiht_gemv_t(const qiht_codes* Q, const float* r, float* g,
+                        void* workspace, size_t workspace_bytes, qiht_stream_t stream);
+
+/* The same product when max |r| is already known: rmax [device, one float]
+ * must hold max |r| exactly (as the solver keeps it). Launches one kernel,
+ * the one the solver runs every iteration, with the same launch plan. */
+qiht_status qiht_gemv_t_prescaled(const qiht_codes* Q, const float* r, const float* rmax, float* g,
+                                  qiht_stream_t stream);
+
+/* z = Q[:, cols] coef: product with a column subset (Q2 x on the support,
+ * Q2_G g_G of the step size, Q2 (x' - x) of the backtracking test).
+ * cols [device, count int32 in [0, Q->cols)], coef [device, count floats],
+ * z [device, Q->rows floats]. FP32 sums in a fixed order (deterministic).
+ * Workspace: qiht_gemv_cols_workspace_size(Q->rows, count) bytes. */
+size_t qiht_gemv_cols_workspace_size(int32_t rows, int32_t count);
+qiht_status qiht_gemv_cols(const qiht_codes* Q, const int32_t* cols, const float* coef, int32_t count,
+                           float* z, void* workspace, size_t workspace_bytes, qiht_stream_t stream);
+
+/* Hard threshold H_s (Eq. NIHT): the s entries of a [device, n floats] of
+ * largest magnitude, ties broken by the lower index; exactly s are kept.
+ * idx [device, s int32] receives their indices in ascending order, val
+ * [device, s floats, may be NULL] their values, kth [device, 2 floats, may be
+ * NULL] the s-th and (s+1)-th largest magnitudes (0 if s == n).
+ * Requires 1 <= s <= n <= 49152. Workspace: qiht_top_s_workspace_size(n). */
+size_t qiht_top_s_workspace_size(int32_t n);
+qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float* val, float* kth,
+                       void* workspace, size_t workspace_bytes, qiht_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* The solver (Algorithm 2)                                                 */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    double k;               /* shrinkage of the step size, k > 1/(1-c) (Section II-A); default 2 */
+    double c;               /* small constant of the descent test, 0 < c < 1; default 0.01 */
+    int32_t max_backtrack;  /* shrinks allowed per iteration before QIHT_ERR_BACKTRACK_CAP; default 32 */
+    int32_t reserved;       /* must be 0 */
+} qiht_params;
+
+typedef struct {            /* written on the device after every iteration */
+    int32_t iters_run;      /* iterations completed (an iteration that stopped early is not counted) */
+    int32_t backtracks;     /* total step-size shrinks */
+    int32_t support_changes;/* iterations whose accepted support differs from the previous one */
+    int32_t status;         /* qiht_status of the run: OK, NONFINITE or BACKTRACK_CAP */
+    double resid_norm2;     /* ||Q(y) - Q2 x||^2 of the returned x (FP64 sum of FP32 residuals) */
+    double mu;              /* last accepted step size */
+} qiht_report;
+
+typedef struct {            /* optional per-iteration record [device]; any field may be NULL */
+    int32_t* support;       /* (iters+1) x s: row 0 = initial support, row t = support after iteration t */
+    float* kth;             /* (iters+1) x 2: s-th and (s+1)-th |x + mu g| of the accepted selection */
+    double* mu;             /* (iters+1): accepted step size (row 0 = 0) */
+    int32_t* bt;            /* (iters+1): shrinks in that iteration */
+    double* resid2;         /* (iters+1): ||Q(y) - Q2 x||^2 after that iteration */
+} qiht_trace;
+
+/* Workspace bytes for qiht_niht_solve with these sizes (256-byte aligned buffer). */
+size_t qiht_solve_workspace_size(int32_t m, int32_t n, int32_t s);
+
+/* Run `iters` iterations of QIHT (Algorithm 2) with fixed quantizations:
+ * g = Q1^T (Q(y) - Q2 x) with Q1, Q2 two independent quantizations of Phi
+ * (m x n) and y (m, one column); mu = ||g_G||^2 / ||Q2_G g_G||^2 on the
+ * current support G; x' = H_s(x + mu g); when the support changes, the step is
+ * shrunk by k(1-c) while mu > (1-c) ||x'-x||^2 / ||Q2 (x'-x)||^2.
+ * Initial state: x = 0, G = supp H_s(Q1^T Q(y)). The run stops early when
+ * ||g_G||^2 or ||Q2_G g_G||^2 is zero (converged) or on a device error.
+ * Outputs: x [device, n floats, dense, s-sparse], support [device, s int32,
+ * ascending], report [device, one qiht_report]. trace may be NULL.
+ * The whole run is one CUDA-graph launch (built on the first call with a given
+ * set of arguments and cached); control never returns to the host between
+ * iterations. Requires 1 <= s <= min(m, n), m <= 16384, n <= 49152. */
+qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* y,
+                            int32_t s, int32_t iters, const qiht_params* params,
+                            float* x, int32_t* support, qiht_report* report, const qiht_trace* trace,
+                            void* workspace, size_t workspace_bytes, qiht_stream_t stream);
+
+/* Drop every cached solver graph (e.g. before freeing buffers they reference). */
+void qiht_clear_graph_cache(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QIHT_H */

@@ -1,0 +1,309 @@
+"""QIHT on GB300: thin Python binding of the C ABI in include/qiht.h.
+
+Every step of the method runs in the CUDA library libqiht.so; this module only
+marshals arguments (torch tensors for device memory, torch streams) and keeps
+the names of the C entry points. There is no CPU fallback: if the library is
+missing, every call raises.
+
+Paper: Gurel et al., "Compressive Sensing Using Iterative Hard Thresholding with
+Low Precision Data Representation" (IEEE TSP 2020), Algorithm 2 (QIHT) with the
+stochastic quantizer of Section III-A.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqiht.so")
+
+OK, ERR_ARG, ERR_BITS, ERR_NONFINITE, ERR_TIMEOUT, ERR_BACKTRACK_CAP, ERR_CUDA, ERR_WORKSPACE = range(8)
+SCALE_GIVEN = 1
+CHECK_FINITE = 2
+
+# stream ids of the random numbers, by convention of the solver
+STREAM_Q1, STREAM_Q2, STREAM_Y = 0, 1, 2
+
+
+class QihtError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class _Codes(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("rows", ctypes.c_int32),
+                ("cols", ctypes.c_int32), ("bits", ctypes.c_int32), ("ld_words", ctypes.c_int32)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("c", ctypes.c_double), ("max_backtrack", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("iters_run", ctypes.c_int32), ("backtracks", ctypes.c_int32),
+                ("support_changes", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("resid_norm2", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+class _Trace(ctypes.Structure):
+    _fields_ = [("support", ctypes.c_void_p), ("kth", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("bt", ctypes.c_void_p), ("resid2", ctypes.c_void_p)]
+
+
+REPORT_BYTES = ctypes.sizeof(_Report)
+
+EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_ld_words", "qiht_quantize",
+           "qiht_gemv_t_workspace_size", "qiht_gemv_t", "qiht_gemv_t_prescaled",
+           "qiht_gemv_cols_workspace_size", "qiht_gemv_cols",
+           "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
+           "qiht_clear_graph_cache"]
+
+_lib = None
+
+
+def lib():
+    """The loaded libqiht.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1802_04907_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, U32, U64, SZ = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                     ctypes.c_uint64, ctypes.c_size_t)
+        sig = {
+            "qiht_status_string": ([I32], ctypes.c_char_p),
+            "qiht_abi_version": ([], I32),
+            "qiht_ld_words": ([I32, I32], I32),
+            "qiht_quantize": ([P, I32, I32, I64, I32, U64, U32, I32, P, I32, P, P], I32),
+            "qiht_gemv_t_workspace_size": ([], SZ),
+            "qiht_gemv_t": ([ctypes.POINTER(_Codes), P, P, P, SZ, P], I32),
+            "qiht_gemv_t_prescaled": ([ctypes.POINTER(_Codes), P, P, P, P], I32),
+            "qiht_gemv_cols_workspace_size": ([I32, I32], SZ),
+            "qiht_gemv_cols": ([ctypes.POINTER(_Codes), P, P, I32, P, P, SZ, P], I32),
+            "qiht_top_s_workspace_size": ([I32], SZ),
+            "qiht_top_s": ([P, I32, I32, P, P, P, P, SZ, P], I32),
+            "qiht_solve_workspace_size": ([I32, I32, I32], SZ),
+            "qiht_niht_solve": ([ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), I32, I32,
+                                 ctypes.POINTER(_Params), P, P, P, ctypes.POINTER(_Trace), P, SZ, P], I32),
+            "qiht_clear_graph_cache": ([], None),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().qiht_status_string(status).decode()
+    except Exception:
+        return f"status {status}"
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise QihtError(status, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def ld_words(rows: int, bits: int) -> int:
+    return int(lib().qiht_ld_words(rows, bits))
+
+
+@dataclass
+class Codes:
+    """A quantized matrix (rows x cols) or vector (cols = 1) in the column-packed layout."""
+    words: torch.Tensor      # int32 view of the u32 words, cols * ld_words
+    scale: torch.Tensor      # float32 [1]: c = max |v|
+    rows: int
+    cols: int
+    bits: int
+
+    @property
+    def ld_words(self) -> int:
+        return ld_words(self.rows, self.bits)
+
+    def c_struct(self) -> _Codes:
+        return _Codes(self.words.data_ptr(), self.scale.data_ptr(), self.rows, self.cols, self.bits, self.ld_words)
+
+    @property
+    def nbytes(self) -> int:
+        return self.words.numel() * 4
+
+
+def quantize(v: torch.Tensor, bits: int, seed: int, stream_id: int, *, scale: torch.Tensor | None = None,
+             scale_given: bool = False, check_finite: bool = False, out: Codes | None = None,
+             stream=None) -> Codes:
+    """qiht_quantize: Q(v, b) of a float32 matrix (rows x cols, row-major) or vector."""
+    assert v.is_cuda and v.dtype == torch.float32
+    if v.dim() == 1:
+        rows, cols, ld = v.shape[0], 1, 1
+    else:
+        rows, cols = v.shape
+        ld = v.stride(0)
+        assert v.stride(1) == 1
+    ldw = ld_words(rows, bits) if bits in (2, 4, 8) else 4
+    if out is None:
+        words = torch.empty(cols * ldw, dtype=torch.int32, device=v.device)
+        sc = scale if scale is not None else torch.zeros(1, dtype=torch.float32, device=v.device)
+        out = Codes(words, sc, rows, cols, bits)
+    elif scale is not None:
+        out.scale = scale
+    flags = (SCALE_GIVEN if scale_given else 0) | (CHECK_FINITE if check_finite else 0)
+    st = lib().qiht_quantize(v.data_ptr(), rows, cols, ld, bits, seed & (2**64 - 1), stream_id, flags,
+                             out.words.data_ptr(), ldw, out.scale.data_ptr(), _stream(stream))
+    _check(st, "qiht_quantize")
+    return out
+
+
+def gemv_t(Q: Codes, r: torch.Tensor, g: torch.Tensor | None = None, *, workspace: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """qiht_gemv_t: g = Q^T r."""
+    if g is None:
+        g = torch.empty(Q.cols, dtype=torch.float32, device=r.device)
+    ws = workspace if workspace is not None else _ws(lib().qiht_gemv_t_workspace_size(), r.device)
+    c = Q.c_struct()
+    _check(lib().qiht_gemv_t(ctypes.byref(c), r.data_ptr(), g.data_ptr(), ws.data_ptr(), ws.numel(),
+                             _stream(stream)), "qiht_gemv_t")
+    return g
+
+
+def gemv_t_prescaled(Q: Codes, r: torch.Tensor, rmax: torch.Tensor, g: torch.Tensor, *, stream=None):
+    """qiht_gemv_t_prescaled: g = Q^T r with max |r| given in rmax (one kernel launch)."""
+    c = Q.c_struct()
+    _check(lib().qiht_gemv_t_prescaled(ctypes.byref(c), r.data_ptr(), rmax.data_ptr(), g.data_ptr(),
+                                       _stream(stream)), "qiht_gemv_t_prescaled")
+    return g
+
+
+def gemv_cols(Q: Codes, cols: torch.Tensor, coef: torch.Tensor, z: torch.Tensor | None = None, *,
+              workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """qiht_gemv_cols: z = Q[:, cols] coef."""
+    count = cols.numel()
+    if z is None:
+        z = torch.empty(Q.rows, dtype=torch.float32, device=coef.device)
+    ws = workspace if workspace is not None else _ws(lib().qiht_gemv_cols_workspace_size(Q.rows, count), coef.device)
+    c = Q.c_struct()
+    _check(lib().qiht_gemv_cols(ctypes.byref(c), cols.data_ptr(), coef.data_ptr(), count, z.data_ptr(),
+                                ws.data_ptr(), ws.numel(), _stream(stream)), "qiht_gemv_cols")
+    return z
+
+
+def top_s(a: torch.Tensor, s: int, *, with_values: bool = True, stream=None):
+    """qiht_top_s: H_s of a vector; returns (indices ascending, values, kth[2])."""
+    n = a.numel()
+    idx = torch.empty(s, dtype=torch.int32, device=a.device)
+    val = torch.empty(s, dtype=torch.float32, device=a.device) if with_values else None
+    kth = torch.empty(2, dtype=torch.float32, device=a.device)
+    _check(lib().qiht_top_s(a.data_ptr(), n, s, idx.data_ptr(), _ptr(val), kth.data_ptr(), None, 0,
+                            _stream(stream)), "qiht_top_s")
+    return idx, val, kth
+
+
+def solve_workspace_size(m: int, n: int, s: int) -> int:
+    return int(lib().qiht_solve_workspace_size(m, n, s))
+
+
+@dataclass
+class Report:
+    iters_run: int
+    backtracks: int
+    support_changes: int
+    status: int
+    resid_norm2: float
+    mu: float
+
+
+def report_from_bytes(buf: bytes) -> Report:
+    r = _Report.from_buffer_copy(buf)
+    return Report(r.iters_run, r.backtracks, r.support_changes, r.status, r.resid_norm2, r.mu)
+
+
+class Solver:
+    """Buffers of one qiht_niht_solve configuration (outputs, workspace, trace).
+
+    Keeping the same Solver object keeps the same pointers, so the library's
+    cached CUDA graph is reused on every call."""
+
+    def __init__(self, m: int, n: int, s: int, iters: int, *, device="cuda", trace: bool = False,
+                 k: float = 2.0, c: float = 0.01, max_backtrack: int = 32):
+        self.m, self.n, self.s, self.iters = m, n, s, iters
+        self.params = _Params(k, c, max_backtrack, 0)
+        self.x = torch.empty(n, dtype=torch.float32, device=device)
+        self.support = torch.empty(s, dtype=torch.int32, device=device)
+        self.report = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=device)
+        self.workspace = _ws(solve_workspace_size(m, n, s), device)
+        self.trace = None
+        if trace:
+            T = iters + 1
+            self.trace = {"support": torch.zeros((T, s), dtype=torch.int32, device=device),
+                          "kth": torch.zeros((T, 2), dtype=torch.float32, device=device),
+                          "mu": torch.zeros(T, dtype=torch.float64, device=device),
+                          "bt": torch.zeros(T, dtype=torch.int32, device=device),
+                          "resid2": torch.zeros(T, dtype=torch.float64, device=device)}
+
+    def __call__(self, Q1: Codes, Q2: Codes, y: Codes, stream=None):
+        """qiht_niht_solve (asynchronous); results in self.x, self.support, self.report."""
+        c1, c2, cy = Q1.c_struct(), Q2.c_struct(), y.c_struct()
+        tr = None
+        if self.trace is not None:
+            t = self.trace
+            tr = _Trace(t["support"].data_ptr(), t["kth"].data_ptr(), t["mu"].data_ptr(), t["bt"].data_ptr(),
+                        t["resid2"].data_ptr())
+        st = lib().qiht_niht_solve(ctypes.byref(c1), ctypes.byref(c2), ctypes.byref(cy), self.s, self.iters,
+                                   ctypes.byref(self.params), self.x.data_ptr(), self.support.data_ptr(),
+                                   self.report.data_ptr(), ctypes.byref(tr) if tr is not None else None,
+                                   self.workspace.data_ptr(), self.workspace.numel(), _stream(stream))
+        _check(st, "qiht_niht_solve")
+        return self
+
+    def read_report(self) -> Report:
+        return report_from_bytes(bytes(self.report.cpu().numpy().tobytes()))
+
+
+def niht_solve(Q1: Codes, Q2: Codes, y: Codes, s: int, iters: int, *, trace: bool = False, stream=None, **kw):
+    """One QIHT solve (Algorithm 2). Returns the Solver holding x, support, report (and trace)."""
+    sv = Solver(Q1.rows, Q1.cols, s, iters, device=Q1.words.device, trace=trace, **kw)
+    return sv(Q1, Q2, y, stream=stream)
+
+
+def quantize_problem(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: int, seed: int, *,
+                     out: tuple | None = None, stream=None):
+    """Q1, Q2 (two independent quantizations of Phi, sharing its scale) and Q(y)."""
+    if out is None:
+        q1 = quantize(phi, bits_phi, seed, STREAM_Q1, stream=stream)
+        q2 = quantize(phi, bits_phi, seed, STREAM_Q2, scale=q1.scale, scale_given=True, stream=stream)
+        qy = quantize(y, bits_y, seed, STREAM_Y, stream=stream)
+        return q1, q2, qy
+    q1, q2, qy = out
+    quantize(phi, bits_phi, seed, STREAM_Q1, out=q1, stream=stream)
+    quantize(phi, bits_phi, seed, STREAM_Q2, scale=q1.scale, scale_given=True, out=q2, stream=stream)
+    quantize(y, bits_y, seed, STREAM_Y, out=qy, stream=stream)
+    return q1, q2, qy
+
+
+def clear_graph_cache():
+    lib().qiht_clear_graph_cache()

@@ -1,0 +1,340 @@
+// z = Q[:, list] coef: products of the quantized matrix with a column subset.
+// In one QIHT iteration (Algorithm 2) this kernel serves three uses, each with
+// its own epilogue:
+//   Mu     z = Q2_G g_G on the current support; mu = ||g_G||^2 / ||z||^2   (Eq. step_size)
+//   Omega  z = Q2 (x' - x) on G' u G; omega = ||x'-x||^2 / ||z||^2, and the
+//          backtracking test mu <= (1-c) omega (Section II-A); shrink mu by k(1-c) if it fails
+//   Resid  z = Q2_G' x'; r = Q(y) - z, ||r||^2, max |r|; commit x <- x', G <- G'
+// Grid: (row blocks of 256 words) x (chunks of 8 list entries). Each CTA sums its
+// chunk for its rows into a partial buffer; the last CTA of a row block (arrival
+// counter) adds the chunks in chunk order, and the last row block finishes the
+// scalars. Sums are in a fixed order, so results are deterministic. No CTA ever
+// waits on another one.
+#include <cfloat>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace qiht {
+
+__device__ __forceinline__ void set_cond(unsigned long long h, unsigned v)
+{
+    if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
+}
+
+// Deterministic block sum of one double per thread (fixed shuffle tree, then warps in order).
+__device__ double block_sum_d(double v, double* sh)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+        sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+__device__ unsigned block_max_u(unsigned v, unsigned* sh)
+{
+    v = __reduce_max_sync(0xffffffffu, v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = max(t, sh[i]);
+        sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// Sum of squares of a list (g[idx[q]] when idx != nullptr, else v[q]) in a fixed order.
+__device__ double list_norm2(const float* v, const int32_t* idx, int count, double* sh)
+{
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < count; q += blockDim.x) {
+        const float e = idx ? __ldcg(v + __ldcg(idx + q)) : __ldcg(v + q);
+        acc += (double)e * (double)e;
+    }
+    return block_sum_d(acc, sh);
+}
+
+__device__ void write_report(const GatherArgs& a, const State* st)
+{
+    if (!a.report) return;
+    a.report->iters_run = st->iter;
+    a.report->backtracks = st->backtracks_total;
+    a.report->support_changes = st->support_changes_total;
+    a.report->status = st->status;
+    a.report->resid_norm2 = st->resid2;
+    a.report->mu = st->mu_accepted;
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
+{
+    constexpr int G = 32 / BITS;
+    constexpr int L = 1 << BITS;
+    __shared__ double shd[33];
+    __shared__ unsigned shu[33];
+    __shared__ int flag;
+    State* st = a.st;
+    const bool first = blockIdx.x == 0 && blockIdx.y == 0;
+
+    if (st) {
+        if (st->stop) {
+            if (first && threadIdx.x == 0) {
+                if (a.mode == kGatherOmega) set_cond(a.h_bt, 0);
+                if (a.mode == kGatherResid) write_report(a, st);
+            }
+            return;
+        }
+        if (a.mode == kGatherOmega && !st->changed) {
+            if (first && threadIdx.x == 0) set_cond(a.h_bt, 0);
+            return;
+        }
+    }
+
+    const int count = (a.mode == kGatherOmega) ? st->union_count : (a.mode == kGatherPlain ? a.count : a.s);
+    const int nchunks = (count + kGatherCols - 1) / kGatherCols;
+    const int ld = a.Q.ld;
+    const int rows_pad = ld * G;
+    const int m = a.Q.rows;
+    const int rb = blockIdx.x, jc = blockIdx.y;
+    const int q = rb * kGatherThreads + threadIdx.x;       // word index in every column
+    const int32_t* list = (a.mode == kGatherMu) ? a.support : (a.mode == kGatherResid ? a.new_sel : a.cols);
+    const float* coefs = (a.mode == kGatherResid) ? a.new_val : a.coef;
+
+    if (jc < nchunks) {
+        float z[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) z[k] = 0.0f;
+        if (q < ld) {
+#pragma unroll 2
+            for (int c = 0; c < kGatherCols; ++c) {
+                const int jj = jc * kGatherCols + c;
+                if (jj < count) {
+                    const int col = __ldcg(list + jj);
+                    const float cf = (a.mode == kGatherMu) ? __ldcg(a.g + col) : __ldcg(coefs + jj);
+                    const uint32_t w = __ldg(a.Q.words + (size_t)col * ld + q);
+#pragma unroll
+                    for (int k = 0; k < G; ++k) {
+                        const int code = (int)((w >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
+                        z[k] = fmaf((float)(2 * code - (L - 1)), cf, z[k]);
+                    }
+                }
+            }
+            float* dst = a.partial + (size_t)jc * rows_pad + (size_t)q * G;
+#pragma unroll
+            for (int k = 0; k < G; k += 4) __stcg(reinterpret_cast<float4*>(dst + k), make_float4(z[k], z[k + 1], z[k + 2], z[k + 3]));
+        }
+    }
+
+    // arrival of this CTA in its row block
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) flag = (atomicAdd(&a.counters[rb], 1u) == gridDim.y - 1);
+    __syncthreads();
+    if (!flag) return;
+    __threadfence();
+
+    const float alpha = (float)((double)(*a.Q.scale) / (double)(L - 1));
+    double acc = 0.0;
+    unsigned mx = 0;
+    if (q < ld) {
+        float zz[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) zz[k] = 0.0f;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const float* src = a.partial + (size_t)ch * rows_pad + (size_t)q * G;
+#pragma unroll
+            for (int k = 0; k < G; k += 4) {
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(src + k));
+                zz[k] += v.x; zz[k + 1] += v.y; zz[k + 2] += v.z; zz[k + 3] += v.w;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int i = q * G + k;
+            if (i < m) {
+                if (a.mode == kGatherPlain) {
+                    a.z[i] = alpha * zz[k];
+                } else if (a.mode == kGatherResid) {
+                    const float ri = fmaf(-alpha, zz[k], __ldcg(a.yhat + i));
+                    a.r[i] = ri;
+                    acc += (double)ri * (double)ri;
+                    mx = max(mx, __float_as_uint(ri) & 0x7fffffffu);
+                } else {
+                    acc += (double)zz[k] * (double)zz[k];
+                }
+            }
+        }
+    }
+    if (a.mode == kGatherPlain) {
+        __syncthreads();
+        if (threadIdx.x == 0) a.counters[rb] = 0;
+        return;
+    }
+    acc = block_sum_d(acc, shd);
+    mx = block_max_u(mx, shu);
+    if (threadIdx.x == 0) {
+        a.rb_partial[2 * rb] = acc;
+        a.rb_partial[2 * rb + 1] = (double)mx;   // exact: mx < 2^32
+        a.counters[rb] = 0;
+    }
+    // arrival of this row block
+    __threadfence();
+    __syncthreads();
+    const int nrb = gridDim.x;
+    if (threadIdx.x == 0) flag = (atomicAdd(&a.counters[nrb], 1u) == (unsigned)nrb - 1);
+    __syncthreads();
+    if (!flag) return;
+    __threadfence();
+
+    // final scalars (one CTA)
+    double total = 0.0;
+    double mxd = 0.0;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < nrb; ++b) {
+            total += __ldcg(a.rb_partial + 2 * b);
+            mxd = fmax(mxd, __ldcg(a.rb_partial + 2 * b + 1));
+        }
+        a.counters[nrb] = 0;
+        shd[32] = total;
+        shd[31] = mxd;
+    }
+    __syncthreads();
+    total = shd[32];
+    mxd = shd[31];
+    const double alpha_d = (double)(*a.Q.scale) / (double)(L - 1);
+
+    if (a.mode == kGatherMu) {
+        const double num = list_norm2(a.g, a.support, a.s, shd);
+        if (threadIdx.x == 0) {
+            const double den = alpha_d * alpha_d * total;
+            st->num = num;
+            st->bt = 0;
+            if (!isfinite(num) || !isfinite(den)) {
+                st->status = QIHT_ERR_NONFINITE;
+                st->stop = 1;
+            } else if (num == 0.0 || den == 0.0) {
+                st->stop = 1;                      // converged: x stays
+            } else {
+                st->mu = num / den;
+            }
+        }
+    } else if (a.mode == kGatherOmega) {
+        const double dn = list_norm2(a.coef, nullptr, count, shd);
+        if (threadIdx.x == 0) {
+            const double dd = alpha_d * alpha_d * total;
+            unsigned again = 0;
+            if (dn > 0.0) {
+                const double omega = dd > 0.0 ? dn / dd : INFINITY;
+                const double bound = (1.0 - a.c) * omega;
+                const double mu = st->mu;
+                if (!(mu <= bound)) {
+                    if (st->bt >= a.max_bt) {
+                        st->status = QIHT_ERR_BACKTRACK_CAP;
+                        st->stop = 1;
+                    } else {
+                        st->mu = mu / (a.k * (1.0 - a.c));
+                        st->bt += 1;
+                        again = 1;
+                    }
+                }
+            }
+            set_cond(a.h_bt, again);
+        }
+    } else {  // Resid: commit the accepted proposal
+        const int s = a.s;
+        // zero the old support, then write the new one
+        for (int q2 = threadIdx.x; q2 < s; q2 += blockDim.x) a.x[__ldcg(a.support_out + q2)] = 0.0f;
+        __syncthreads();
+        for (int q2 = threadIdx.x; q2 < s; q2 += blockDim.x) {
+            const int j = __ldcg(a.new_sel + q2);
+            a.x[j] = __ldcg(a.new_val + q2);
+            a.support_out[q2] = j;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int it = st->iter + 1;
+            st->iter = it;
+            st->resid2 = total;
+            st->rmax_bits = (unsigned)mxd;
+            st->mu_accepted = st->mu;
+            st->backtracks_total += st->bt;
+            st->support_changes_total += st->changed;
+            if (!isfinite(total)) {
+                st->status = QIHT_ERR_NONFINITE;
+                st->stop = 1;
+            }
+            if (a.trace.kth) { a.trace.kth[2 * it] = st->kth0; a.trace.kth[2 * it + 1] = st->kth1; }
+            if (a.trace.mu) a.trace.mu[it] = st->mu;
+            if (a.trace.bt) a.trace.bt[it] = st->bt;
+            if (a.trace.resid2) a.trace.resid2[it] = total;
+            if (it >= st->iters) st->stop = 1;
+            write_report(a, st);
+        }
+        __syncthreads();
+        if (a.trace.support) {
+            const int it = st->iter;
+            for (int q2 = threadIdx.x; q2 < s; q2 += blockDim.x)
+                a.trace.support[(size_t)it * s + q2] = __ldcg(a.new_sel + q2);
+        }
+    }
+}
+
+int gather_row_blocks(int rows, int bits)
+{
+    const int G = 32 / bits;
+    const int words = (rows + G - 1) / G;
+    return (words + kGatherThreads - 1) / kGatherThreads;
+}
+
+int gather_chunks(int count) { return (count + kGatherCols - 1) / kGatherCols; }
+
+size_t gather_partial_floats(int rows, int bits, int count)
+{
+    const int G = 32 / bits;
+    const int ld = qiht_ld_words(rows, bits);
+    return (size_t)gather_chunks(count) * (size_t)ld * (size_t)G;
+}
+
+static void* gather_fn(int bits)
+{
+    switch (bits) {
+    case 2: return (void*)k_gather<2>;
+    case 4: return (void*)k_gather<4>;
+    default: return (void*)k_gather<8>;
+    }
+}
+
+void gather_node(const GatherArgs& a, cudaKernelNodeParams* p, void** argbuf)
+{
+    const int maxcount = (a.mode == kGatherOmega) ? 2 * a.s : (a.mode == kGatherPlain ? a.count : a.s);
+    p->func = gather_fn(a.Q.bits);
+    p->gridDim = dim3(gather_row_blocks(a.Q.rows, a.Q.bits), gather_chunks(maxcount));
+    p->blockDim = dim3(kGatherThreads);
+    p->sharedMemBytes = 0;
+    p->kernelParams = argbuf;
+    p->extra = nullptr;
+}
+
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
+{
+    cudaKernelNodeParams p{};
+    GatherArgs copy = a;
+    void* args[1] = {&copy};
+    gather_node(a, &p, args);
+    return cudaLaunchKernel(p.func, p.gridDim, p.blockDim, args, 0, s);
+}
+
+}  // namespace qiht

@@ -1,0 +1,142 @@
+// Internal declarations shared by the translation units of the QIHT CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/qiht.h"
+
+namespace qiht {
+
+constexpr int kMaxRows = 16384;   // m limit of the integer GEMV^T (32-bit lane sums cannot overflow)
+constexpr int kMaxTopN = 49152;   // n limit of the one-CTA radix select (keys held in shared memory)
+constexpr int kGatherCols = 8;    // columns per CTA in the column-subset product
+constexpr int kGatherThreads = 256;
+
+// Device view of a quantized matrix (see the column-packed layout in qiht.h).
+struct Codes {
+    const uint32_t* words;
+    const float* scale;
+    int rows, cols, bits, ld;
+};
+
+__host__ __device__ inline int codes_per_word(int bits) { return 32 / bits; }
+
+// Per-solve device state, placed at the start of the solver workspace.
+struct State {
+    double mu;             // step size of the current proposal
+    double num;            // ||g_G||^2 of this iteration
+    double resid2;         // ||Q(y) - Q2 x||^2 after the last accepted iterate
+    double mu_accepted;    // step size of the last accepted iterate
+    int iter;              // completed iterations
+    int changed;           // 1 if the current proposal's support differs from G
+    int bt;                // shrinks in the current iteration
+    int stop;              // 1: nothing left to do (done, converged, error)
+    int status;            // qiht_status
+    int union_count;       // entries of the (G' u G) list of x' - x
+    unsigned rmax_bits;    // float bits of max |r|
+    int backtracks_total;
+    int support_changes_total;
+    float kth0, kth1;      // s-th and (s+1)-th |x + mu g| of the current proposal
+    int iters;             // requested iterations
+    int outer_guard;       // executions of the outer loop body (bounds the loop)
+    unsigned counters[3][32];  // arrival counters of the three column-subset products
+};
+
+// Column-subset product modes (one epilogue each).
+enum GatherMode { kGatherPlain = 0, kGatherMu = 1, kGatherOmega = 2, kGatherResid = 3 };
+
+struct GatherArgs {
+    Codes Q;
+    const int32_t* cols;      // list of column indices
+    const float* coef;        // list of coefficients
+    int count;                // list length (host-known upper bound when count_dev != nullptr)
+    const int* count_dev;     // device list length (nullptr: use count)
+    float* z;                 // plain mode: output z (rows)
+    float* partial;           // [chunks][rows_pad] partial sums
+    double* rb_partial;       // [row_blocks][2] per-row-block sums
+    unsigned* counters;       // [row_blocks + 1]
+    int mode;
+    // solver fields (modes Mu, Omega, Resid)
+    State* st;
+    const float* g;           // Mu: gradient
+    const int32_t* support;   // Mu: current support G (s entries)
+    const float* yhat;        // Resid: dequantized observation
+    float* r;                 // Resid: residual output
+    float* x;                 // Resid: dense iterate (committed)
+    int32_t* support_out;     // Resid: support to commit into (the caller's support array)
+    const int32_t* new_sel;   // Resid: G' (s entries)
+    const float* new_val;     // Resid: x' values on G'
+    int s;
+    double k, c;              // backtracking parameters
+    int max_bt;
+    unsigned long long h_outer, h_bt;   // conditional graph handles (0 when not in a graph)
+    qiht_report* report;
+    qiht_trace trace;
+};
+
+struct GemvTArgs {
+    Codes Q;
+    const float* r;
+    const unsigned* rmax_bits;  // float bits of max |r| (device)
+    float* g;
+    State* st;                  // non-null in the solver: skip when st->stop
+    unsigned long long h_outer; // outer-loop handle (solver loop body only): set by thread 0 of CTA 0
+};
+
+struct TopArgs {
+    const float* g;
+    const float* x;             // dense iterate (nullptr: zero)
+    const double* mu;           // step (nullptr: 1)
+    int n, s;
+    int32_t* sel;               // G' (ascending)
+    float* val;                 // x' values on G'
+    float* kth;                 // optional [2]
+    // solver fields
+    State* st;
+    const int32_t* support;     // current support G (compare / union)
+    int32_t* uni;               // union list (2s)
+    float* delta;               // x' - x on the union list
+    int init;                   // 1: initial selection written straight into `support_init`
+    int32_t* support_init;
+    qiht_trace trace;
+    unsigned long long h_bt;    // backtracking-loop handle: cleared on entry, set later by the Omega product
+};
+
+struct InitArgs {
+    Codes Y;
+    const Codes* Q1;            // unused on device; scales are checked through these pointers
+    const float* scale_q1;
+    const float* scale_q2;
+    float* yhat;
+    float* r;
+    float* x;
+    int n, m, s, iters;
+    State* st;
+    qiht_report* report;
+    qiht_trace trace;
+};
+
+// Kernel node builders (each translation unit owns its kernels).
+void gemv_t_node(const GemvTArgs& a, int num_sms, cudaKernelNodeParams* p, void** argbuf);
+void gather_node(const GatherArgs& a, cudaKernelNodeParams* p, void** argbuf);
+void top_node(const TopArgs& a, cudaKernelNodeParams* p, void** argbuf);
+void init_node(const InitArgs& a, cudaKernelNodeParams* p, void** argbuf);
+
+// Direct launches (building blocks).
+cudaError_t launch_absmax(const float* in, int rows, int cols, int64_t ld, float* scale, cudaStream_t s);
+cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int bits, uint64_t seed,
+                            uint32_t stream_id, uint32_t* words, int ld_words, const float* scale,
+                            cudaStream_t s);
+cudaError_t launch_gemv_t(const GemvTArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+cudaError_t launch_top(const TopArgs& a, cudaStream_t s);
+
+int gather_row_blocks(int rows, int bits);
+int gather_chunks(int count);
+size_t gather_partial_floats(int rows, int bits, int count);
+size_t top_smem_bytes(int n);
+int num_sms();
+
+}  // namespace qiht

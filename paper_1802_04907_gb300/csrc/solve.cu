@@ -1,0 +1,653 @@
+// C ABI of the QIHT library and the iteration driver of Algorithm 2.
+//
+// One call of qiht_niht_solve launches one CUDA graph:
+//   init:  Q(y) dequantized, r = Q(y), x = 0        (k_init)
+//          g = Q1^T r                              (gemv_t)
+//          G = supp H_s(g)                         (top, init mode)
+//   WHILE (not done):                              conditional node, set by Resid
+//          mu = ||g_G||^2 / ||Q2_G g_G||^2          (gather, Mu)
+//          x' = H_s(x + mu g), G'                   (top)
+//          backtracking test on G' u G              (gather, Omega)
+//          WHILE (test failed): shrink mu; top; Omega   conditional node, set by Omega
+//          r = Q(y) - Q2_G' x', commit x, G          (gather, Resid)
+//          g = Q1^T r                              (gemv_t)
+// Control stays on the device for the whole solve. Graphs are cached per
+// argument set (pointers, sizes, parameters, device).
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace qiht {
+
+int num_sms()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+__device__ __forceinline__ void set_cond_init(unsigned long long h, unsigned v)
+{
+    if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
+}
+
+struct InitKernelArgs {
+    InitArgs a;
+    unsigned long long h_outer;
+};
+
+// Initial state: dequantized observation Q(y), r = Q(y), x = 0, scalars reset.
+__global__ void __launch_bounds__(1024) k_init(InitKernelArgs ka)
+{
+    const InitArgs& a = ka.a;
+    State* st = a.st;
+    __shared__ double shd[33];
+    __shared__ unsigned shu[33];
+    const int Ly = 1 << a.Y.bits;
+    const int Gy = 32 / a.Y.bits;
+    const float sy = *a.Y.scale, s1 = *a.scale_q1, s2 = *a.scale_q2;
+    const bool finite = isfinite(sy) && isfinite(s1) && isfinite(s2);
+    const double alpha_y = (double)sy / (double)(Ly - 1);
+    double acc = 0.0;
+    unsigned mx = 0;
+    for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
+        const uint32_t w = a.Y.words[i / Gy];
+        const int k = i % Gy;
+        const int code = (int)((w >> (8 * (k & 3) + a.Y.bits * (k >> 2))) & (uint32_t)(Ly - 1));
+        const float v = (float)(alpha_y * (double)(2 * code - (Ly - 1)));
+        a.yhat[i] = v;
+        a.r[i] = v;
+        acc += (double)v * (double)v;
+        mx = max(mx, __float_as_uint(v) & 0x7fffffffu);
+    }
+    for (int j = threadIdx.x; j < a.n; j += blockDim.x) a.x[j] = 0.0f;
+    // deterministic block reductions
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) { shd[threadIdx.x >> 5] = acc; shu[threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += shd[w]; b = max(b, shu[w]); }
+        memset(st, 0, sizeof(State));
+        st->iters = a.iters;
+        st->resid2 = t;
+        st->rmax_bits = b;
+        st->status = finite ? QIHT_OK : QIHT_ERR_NONFINITE;
+        st->stop = finite ? 0 : 1;     // iters == 0 still selects the initial support
+        if (a.trace.mu) a.trace.mu[0] = 0.0;
+        if (a.trace.bt) a.trace.bt[0] = 0;
+        if (a.trace.resid2) a.trace.resid2[0] = t;
+        if (a.report) {
+            a.report->iters_run = 0;
+            a.report->backtracks = 0;
+            a.report->support_changes = 0;
+            a.report->status = st->status;
+            a.report->resid_norm2 = t;
+            a.report->mu = 0.0;
+        }
+        set_cond_init(ka.h_outer, (finite && a.iters > 0) ? 1u : 0u);
+    }
+}
+
+void init_node(const InitArgs&, cudaKernelNodeParams*, void**) {}
+
+}  // namespace qiht
+
+using namespace qiht;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static bool bits_ok(int b) { return b == 2 || b == 4 || b == 8; }
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static qiht_status check_codes(const qiht_codes* Q)
+{
+    if (!Q || !Q->words || !Q->scale) return QIHT_ERR_ARG;
+    if (!bits_ok(Q->bits)) return QIHT_ERR_BITS;
+    if (Q->rows < 1 || Q->cols < 1) return QIHT_ERR_ARG;
+    if (Q->ld_words != qiht_ld_words(Q->rows, Q->bits)) return QIHT_ERR_ARG;
+    if (!aligned(Q->words, 16)) return QIHT_ERR_ARG;
+    return QIHT_OK;
+}
+
+static Codes view(const qiht_codes* Q)
+{
+    Codes c;
+    c.words = Q->words;
+    c.scale = Q->scale;
+    c.rows = Q->rows;
+    c.cols = Q->cols;
+    c.bits = Q->bits;
+    c.ld = Q->ld_words;
+    return c;
+}
+
+extern "C" {
+
+const char* qiht_status_string(int32_t status)
+{
+    switch (status) {
+    case QIHT_OK: return "QIHT_OK";
+    case QIHT_ERR_ARG: return "QIHT_ERR_ARG";
+    case QIHT_ERR_BITS: return "QIHT_ERR_BITS";
+    case QIHT_ERR_NONFINITE: return "QIHT_ERR_NONFINITE";
+    case QIHT_ERR_TIMEOUT: return "QIHT_ERR_TIMEOUT";
+    case QIHT_ERR_BACKTRACK_CAP: return "QIHT_ERR_BACKTRACK_CAP";
+    case QIHT_ERR_CUDA: return "QIHT_ERR_CUDA";
+    case QIHT_ERR_WORKSPACE: return "QIHT_ERR_WORKSPACE";
+    default: return "QIHT_UNKNOWN_STATUS";
+    }
+}
+
+int32_t qiht_abi_version(void) { return QIHT_ABI_VERSION; }
+
+int32_t qiht_ld_words(int32_t rows, int32_t bits)
+{
+    if (!bits_ok(bits) || rows < 1) return -1;
+    const int G = 32 / bits;
+    const int w = (rows + G - 1) / G;
+    return (w + 3) & ~3;
+}
+
+qiht_status qiht_quantize(const float* in, int32_t rows, int32_t cols, int64_t ld_in, int32_t bits,
+                          uint64_t seed, uint32_t stream_id, int32_t flags,
+                          uint32_t* words, int32_t ld_words, float* scale, qiht_stream_t stream)
+{
+    if (!bits_ok(bits)) return QIHT_ERR_BITS;
+    if (!in || !words || !scale || rows < 1 || cols < 1 || ld_in < cols) return QIHT_ERR_ARG;
+    if (ld_words != qiht_ld_words(rows, bits) || !aligned(words, 16)) return QIHT_ERR_ARG;
+    if (flags & ~(QIHT_SCALE_GIVEN | QIHT_CHECK_FINITE)) return QIHT_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!(flags & QIHT_SCALE_GIVEN)) {
+        if (launch_absmax(in, rows, cols, ld_in, scale, s) != cudaSuccess) return QIHT_ERR_CUDA;
+    }
+    if (launch_quantize(in, rows, cols, ld_in, bits, seed, stream_id, words, ld_words, scale, s) != cudaSuccess)
+        return QIHT_ERR_CUDA;
+    if (flags & QIHT_CHECK_FINITE) {
+        float h = 0.0f;
+        if (cudaMemcpyAsync(&h, scale, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess) return QIHT_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return QIHT_ERR_CUDA;
+        if (!std::isfinite(h)) return QIHT_ERR_NONFINITE;
+    }
+    return QIHT_OK;
+}
+
+size_t qiht_gemv_t_workspace_size(void) { return 256; }
+
+qiht_status qiht_gemv_t(const qiht_codes* Q, const float* r, float* g, void* workspace, size_t workspace_bytes,
+                        qiht_stream_t stream)
+{
+    qiht_status e = check_codes(Q);
+    if (e != QIHT_OK) return e;
+    if (!r || !g) return QIHT_ERR_ARG;
+    if (Q->rows > kMaxRows) return QIHT_ERR_ARG;
+    if (!workspace || workspace_bytes < qiht_gemv_t_workspace_size() || !aligned(workspace, 256))
+        return QIHT_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float* rmax = reinterpret_cast<float*>(workspace);
+    if (launch_absmax(r, Q->rows, 1, 1, rmax, s) != cudaSuccess) return QIHT_ERR_CUDA;
+    GemvTArgs a{};
+    a.Q = view(Q);
+    a.r = r;
+    a.rmax_bits = reinterpret_cast<const unsigned*>(rmax);
+    a.g = g;
+    a.st = nullptr;
+    if (launch_gemv_t(a, num_sms(), s) != cudaSuccess) return QIHT_ERR_CUDA;
+    return QIHT_OK;
+}
+
+qiht_status qiht_gemv_t_prescaled(const qiht_codes* Q, const float* r, const float* rmax, float* g,
+                                  qiht_stream_t stream)
+{
+    qiht_status e = check_codes(Q);
+    if (e != QIHT_OK) return e;
+    if (!r || !g || !rmax) return QIHT_ERR_ARG;
+    if (Q->rows > kMaxRows) return QIHT_ERR_ARG;
+    GemvTArgs a{};
+    a.Q = view(Q);
+    a.r = r;
+    a.rmax_bits = reinterpret_cast<const unsigned*>(rmax);
+    a.g = g;
+    a.st = nullptr;
+    if (launch_gemv_t(a, num_sms(), reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return QIHT_ERR_CUDA;
+    return QIHT_OK;
+}
+
+size_t qiht_gemv_cols_workspace_size(int32_t rows, int32_t count)
+{
+    if (rows < 1 || count < 1) return 0;
+    const int rb = gather_row_blocks(rows, 2) > gather_row_blocks(rows, 8) ? gather_row_blocks(rows, 2)
+                                                                            : gather_row_blocks(rows, 8);
+    size_t fl = 0;
+    for (int b : {2, 4, 8}) {
+        const size_t f = gather_partial_floats(rows, b, count);
+        if (f > fl) fl = f;
+    }
+    return align256(fl * 4) + align256((size_t)rb * 2 * 8) + align256((size_t)(rb + 1) * 4);
+}
+
+qiht_status qiht_gemv_cols(const qiht_codes* Q, const int32_t* cols, const float* coef, int32_t count, float* z,
+                           void* workspace, size_t workspace_bytes, qiht_stream_t stream)
+{
+    qiht_status e = check_codes(Q);
+    if (e != QIHT_OK) return e;
+    if (!cols || !coef || !z || count < 1) return QIHT_ERR_ARG;
+    const size_t need = qiht_gemv_cols_workspace_size(Q->rows, count);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return QIHT_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* w = reinterpret_cast<char*>(workspace);
+    const int rb = gather_row_blocks(Q->rows, Q->bits);
+    size_t fl = 0;
+    for (int b : {2, 4, 8}) {
+        const size_t f = gather_partial_floats(Q->rows, b, count);
+        if (f > fl) fl = f;
+    }
+    const int rbmax = gather_row_blocks(Q->rows, 2) > gather_row_blocks(Q->rows, 8) ? gather_row_blocks(Q->rows, 2)
+                                                                                  : gather_row_blocks(Q->rows, 8);
+    GatherArgs a{};
+    a.Q = view(Q);
+    a.cols = cols;
+    a.coef = coef;
+    a.count = count;
+    a.z = z;
+    a.partial = reinterpret_cast<float*>(w);
+    a.rb_partial = reinterpret_cast<double*>(w + align256(fl * 4));
+    a.counters = reinterpret_cast<unsigned*>(w + align256(fl * 4) + align256((size_t)rbmax * 2 * 8));
+    a.mode = kGatherPlain;
+    if (cudaMemsetAsync(a.counters, 0, (size_t)(rb + 1) * 4, s) != cudaSuccess) return QIHT_ERR_CUDA;
+    if (launch_gather(a, s) != cudaSuccess) return QIHT_ERR_CUDA;
+    return QIHT_OK;
+}
+
+size_t qiht_top_s_workspace_size(int32_t) { return 0; }
+
+qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float* val, float* kth, void*, size_t,
+                       qiht_stream_t stream)
+{
+    if (!a || !idx || n < 1 || s < 1 || s > n || n > kMaxTopN) return QIHT_ERR_ARG;
+    TopArgs t{};
+    t.g = a;
+    t.x = nullptr;
+    t.mu = nullptr;
+    t.n = n;
+    t.s = s;
+    t.sel = idx;
+    t.val = val;
+    t.kth = kth;
+    t.st = nullptr;
+    if (launch_top(t, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return QIHT_ERR_CUDA;
+    return QIHT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// solver workspace plan
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Plan {
+    size_t off_state, off_yhat, off_r, off_g, off_sel, off_val, off_uni, off_delta, off_partial, off_rbp, total;
+};
+
+Plan plan_solve(int m, int n, int s)
+{
+    Plan p{};
+    size_t o = 0;
+    const size_t rows_pad = (size_t)qiht_ld_words(m, 2) * 16;   // the largest padding over b in {2, 4, 8}
+    p.off_state = o; o += align256(sizeof(State));
+    p.off_yhat = o; o += align256(rows_pad * 4);
+    p.off_r = o; o += align256(rows_pad * 4);
+    p.off_g = o; o += align256((size_t)n * 4);
+    p.off_sel = o; o += align256((size_t)s * 4);
+    p.off_val = o; o += align256((size_t)s * 4);
+    p.off_uni = o; o += align256((size_t)2 * s * 4);
+    p.off_delta = o; o += align256((size_t)2 * s * 4);
+    size_t fl = 0;
+    for (int b : {2, 4, 8}) {
+        const size_t f = gather_partial_floats(m, b, 2 * s);
+        if (f > fl) fl = f;
+    }
+    p.off_partial = o; o += align256(fl * 4);
+    const int rb = gather_row_blocks(m, 2) > gather_row_blocks(m, 8) ? gather_row_blocks(m, 2) : gather_row_blocks(m, 8);
+    p.off_rbp = o; o += align256((size_t)rb * 2 * 8);
+    p.total = o;
+    return p;
+}
+
+struct Key {
+    std::vector<uint64_t> v;
+    bool operator<(const Key& o) const { return v < o.v; }
+};
+
+struct Cached {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+std::mutex g_mu;
+std::map<Key, Cached> g_cache;
+
+uint64_t dbits(double d)
+{
+    uint64_t u;
+    std::memcpy(&u, &d, 8);
+    return u;
+}
+
+void push_codes(std::vector<uint64_t>& v, const qiht_codes* Q)
+{
+    v.push_back(reinterpret_cast<uint64_t>(Q->words));
+    v.push_back(reinterpret_cast<uint64_t>(Q->scale));
+    v.push_back((uint64_t)Q->rows);
+    v.push_back((uint64_t)Q->cols);
+    v.push_back((uint64_t)Q->bits);
+    v.push_back((uint64_t)Q->ld_words);
+}
+
+#define CK(x)                                       \
+    do {                                            \
+        if ((x) != cudaSuccess) return QIHT_ERR_CUDA; \
+    } while (0)
+
+qiht_status add_kernel(cudaGraph_t g, cudaGraphNode_t* out, const cudaGraphNode_t* dep, int ndep,
+                       const cudaKernelNodeParams& p)
+{
+    CK(cudaGraphAddKernelNode(out, g, dep, ndep, &p));
+    return QIHT_OK;
+}
+
+qiht_status add_while(cudaGraph_t g, cudaGraphNode_t* out, const cudaGraphNode_t* dep, int ndep,
+                      cudaGraphConditionalHandle h, cudaGraph_t* body)
+{
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CK(cudaGraphAddNode(out, g, dep, nullptr, ndep, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    return QIHT_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        qiht_status _e = (x);           \
+        if (_e != QIHT_OK) return _e;   \
+    } while (0)
+
+qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s, int iters,
+                        const qiht_params* prm, float* x, int32_t* support, qiht_report* report,
+                        const qiht_trace* trace, char* ws, cudaGraph_t* out)
+{
+    const int m = Q1->rows, n = Q1->cols;
+    const Plan pl = plan_solve(m, n, s);
+    State* st = reinterpret_cast<State*>(ws + pl.off_state);
+    float* yhat = reinterpret_cast<float*>(ws + pl.off_yhat);
+    float* r = reinterpret_cast<float*>(ws + pl.off_r);
+    float* g = reinterpret_cast<float*>(ws + pl.off_g);
+    int32_t* sel = reinterpret_cast<int32_t*>(ws + pl.off_sel);
+    float* val = reinterpret_cast<float*>(ws + pl.off_val);
+    int32_t* uni = reinterpret_cast<int32_t*>(ws + pl.off_uni);
+    float* delta = reinterpret_cast<float*>(ws + pl.off_delta);
+    float* partial = reinterpret_cast<float*>(ws + pl.off_partial);
+    double* rbp = reinterpret_cast<double*>(ws + pl.off_rbp);
+    qiht_trace tr{};
+    if (trace) tr = *trace;
+    const int nsm = num_sms();
+
+    cudaGraph_t top;
+    CK(cudaGraphCreate(&top, 0));
+    cudaGraphConditionalHandle h_outer;
+    CK(cudaGraphConditionalHandleCreate(&h_outer, top, 1, cudaGraphCondAssignDefault));
+
+    // --- init ---
+    InitKernelArgs ia{};
+    ia.a.Y = view(Y);
+    ia.a.scale_q1 = Q1->scale;
+    ia.a.scale_q2 = Q2->scale;
+    ia.a.yhat = yhat;
+    ia.a.r = r;
+    ia.a.x = x;
+    ia.a.n = n;
+    ia.a.m = m;
+    ia.a.s = s;
+    ia.a.iters = iters;
+    ia.a.st = st;
+    ia.a.report = report;
+    ia.a.trace = tr;
+    ia.h_outer = (unsigned long long)h_outer;
+    cudaKernelNodeParams kp{};
+    void* init_args[1] = {&ia};
+    kp.func = (void*)k_init;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1024);
+    kp.kernelParams = init_args;
+    cudaGraphNode_t n_init;
+    TRY(add_kernel(top, &n_init, nullptr, 0, kp));
+
+    GemvTArgs ga{};
+    ga.Q = view(Q1);
+    ga.r = r;
+    ga.rmax_bits = &st->rmax_bits;
+    ga.g = g;
+    ga.st = st;
+    ga.h_outer = 0;                 // the set-up product does not steer the loop
+    int tpc = 0;
+    void* gemv_args[2] = {&ga, &tpc};
+    cudaKernelNodeParams gp{};
+    gemv_t_node(ga, nsm, &gp, gemv_args);
+    cudaGraphNode_t n_g0;
+    TRY(add_kernel(top, &n_g0, &n_init, 1, gp));
+
+    TopArgs t0{};
+    t0.g = g;
+    t0.x = nullptr;
+    t0.mu = nullptr;
+    t0.n = n;
+    t0.s = s;
+    t0.sel = sel;
+    t0.val = val;
+    t0.kth = nullptr;
+    t0.st = st;
+    t0.init = 1;
+    t0.support_init = support;
+    t0.trace = tr;
+    void* t0_args[1] = {&t0};
+    cudaKernelNodeParams tp0{};
+    top_node(t0, &tp0, t0_args);
+    cudaGraphNode_t n_t0;
+    TRY(add_kernel(top, &n_t0, &n_g0, 1, tp0));
+
+    // --- outer loop ---
+    cudaGraphNode_t n_w;
+    cudaGraph_t body;
+    TRY(add_while(top, &n_w, &n_t0, 1, h_outer, &body));
+    cudaGraphConditionalHandle h_bt;
+    CK(cudaGraphConditionalHandleCreate(&h_bt, body, 0, 0));
+
+    GatherArgs base{};
+    base.Q = view(Q2);
+    base.partial = partial;
+    base.rb_partial = rbp;
+    base.st = st;
+    base.g = g;
+    base.support = support;
+    base.yhat = yhat;
+    base.r = r;
+    base.x = x;
+    base.support_out = support;
+    base.new_sel = sel;
+    base.new_val = val;
+    base.s = s;
+    base.k = prm->k;
+    base.c = prm->c;
+    base.max_bt = prm->max_backtrack;
+    base.h_outer = (unsigned long long)h_outer;
+    base.h_bt = (unsigned long long)h_bt;
+    base.report = report;
+    base.trace = tr;
+
+    GatherArgs gmu = base;
+    gmu.mode = kGatherMu;
+    gmu.counters = st->counters[0];
+    void* mu_args[1] = {&gmu};
+    cudaKernelNodeParams pmu{};
+    gather_node(gmu, &pmu, mu_args);
+
+    TopArgs tt{};
+    tt.g = g;
+    tt.x = x;
+    tt.mu = &st->mu;
+    tt.n = n;
+    tt.s = s;
+    tt.sel = sel;
+    tt.val = val;
+    tt.kth = nullptr;
+    tt.st = st;
+    tt.support = support;
+    tt.uni = uni;
+    tt.delta = delta;
+    tt.init = 0;
+    tt.trace = tr;
+    tt.h_bt = (unsigned long long)h_bt;
+    void* tt_args[1] = {&tt};
+    cudaKernelNodeParams ptt{};
+    top_node(tt, &ptt, tt_args);
+
+    GatherArgs gom = base;
+    gom.mode = kGatherOmega;
+    gom.cols = uni;
+    gom.coef = delta;
+    gom.counters = st->counters[1];
+    void* om_args[1] = {&gom};
+    cudaKernelNodeParams pom{};
+    gather_node(gom, &pom, om_args);
+
+    GatherArgs gre = base;
+    gre.mode = kGatherResid;
+    gre.counters = st->counters[2];
+    void* re_args[1] = {&gre};
+    cudaKernelNodeParams pre{};
+    gather_node(gre, &pre, re_args);
+
+    cudaGraphNode_t b_mu, b_top, b_om, b_w, b_re, b_g;
+    TRY(add_kernel(body, &b_mu, nullptr, 0, pmu));
+    TRY(add_kernel(body, &b_top, &b_mu, 1, ptt));
+    TRY(add_kernel(body, &b_om, &b_top, 1, pom));
+    cudaGraph_t inner;
+    TRY(add_while(body, &b_w, &b_om, 1, h_bt, &inner));
+    cudaGraphNode_t i_top, i_om;
+    TRY(add_kernel(inner, &i_top, nullptr, 0, ptt));
+    TRY(add_kernel(inner, &i_om, &i_top, 1, pom));
+    TRY(add_kernel(body, &b_re, &b_w, 1, pre));
+    GemvTArgs gb = ga;
+    gb.h_outer = (unsigned long long)h_outer;   // the loop body's product decides whether to go on
+    int tpcb = 0;
+    void* gemvb_args[2] = {&gb, &tpcb};
+    cudaKernelNodeParams gpb{};
+    gemv_t_node(gb, nsm, &gpb, gemvb_args);
+    TRY(add_kernel(body, &b_g, &b_re, 1, gpb));
+    *out = top;
+    return QIHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qiht_solve_workspace_size(int32_t m, int32_t n, int32_t s)
+{
+    if (m < 1 || n < 1 || s < 1) return 0;
+    return plan_solve(m, n, s).total;
+}
+
+qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* y, int32_t s, int32_t iters,
+                            const qiht_params* params, float* x, int32_t* support, qiht_report* report,
+                            const qiht_trace* trace, void* workspace, size_t workspace_bytes, qiht_stream_t stream)
+{
+    TRY(check_codes(Q1));
+    TRY(check_codes(Q2));
+    TRY(check_codes(y));
+    const int m = Q1->rows, n = Q1->cols;
+    if (Q2->rows != m || Q2->cols != n || Q2->bits != Q1->bits) return QIHT_ERR_ARG;
+    if (y->rows != m || y->cols != 1) return QIHT_ERR_ARG;
+    if (s < 1 || s > m || s > n || iters < 0) return QIHT_ERR_ARG;
+    if (m > kMaxRows || n > kMaxTopN) return QIHT_ERR_ARG;
+    if (!x || !support || !report) return QIHT_ERR_ARG;
+    qiht_params prm{2.0, 0.01, 32, 0};
+    if (params) prm = *params;
+    if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.reserved != 0)
+        return QIHT_ERR_ARG;
+    if (!workspace || workspace_bytes < qiht_solve_workspace_size(m, n, s) || !aligned(workspace, 256))
+        return QIHT_ERR_WORKSPACE;
+
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    Key key;
+    key.v.push_back((uint64_t)dev);
+    push_codes(key.v, Q1);
+    push_codes(key.v, Q2);
+    push_codes(key.v, y);
+    key.v.push_back((uint64_t)s);
+    key.v.push_back((uint64_t)iters);
+    key.v.push_back(dbits(prm.k));
+    key.v.push_back(dbits(prm.c));
+    key.v.push_back((uint64_t)prm.max_backtrack);
+    key.v.push_back(reinterpret_cast<uint64_t>(x));
+    key.v.push_back(reinterpret_cast<uint64_t>(support));
+    key.v.push_back(reinterpret_cast<uint64_t>(report));
+    key.v.push_back(reinterpret_cast<uint64_t>(workspace));
+    qiht_trace tr{};
+    if (trace) tr = *trace;
+    key.v.push_back(reinterpret_cast<uint64_t>(tr.support));
+    key.v.push_back(reinterpret_cast<uint64_t>(tr.kth));
+    key.v.push_back(reinterpret_cast<uint64_t>(tr.mu));
+    key.v.push_back(reinterpret_cast<uint64_t>(tr.bt));
+    key.v.push_back(reinterpret_cast<uint64_t>(tr.resid2));
+
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            exec = it->second.exec;
+        } else {
+            cudaGraph_t graph = nullptr;
+            TRY(build_graph(Q1, Q2, y, s, iters, &prm, x, support, report, trace ? &tr : nullptr,
+                            reinterpret_cast<char*>(workspace), &graph));
+            if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return QIHT_ERR_CUDA;
+            }
+            g_cache[key] = Cached{graph, exec};
+        }
+    }
+    CK(cudaGraphLaunch(exec, reinterpret_cast<cudaStream_t>(stream)));
+    return QIHT_OK;
+}
+
+void qiht_clear_graph_cache(void)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (auto& kv : g_cache) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+    }
+    g_cache.clear();
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+// Hard threshold H_s (Eq. NIHT): keep the s entries of a = x + mu g of largest
+// magnitude, ties broken by the lower index, exactly s entries.
+//
+// One CTA of 1024 threads. Keys are the float bits of |a| (monotone for
+// non-negative floats) held in shared memory. A 4-pass MSB-first radix select
+// (8-bit digits, shared-memory histograms) finds the s-th largest key T; an
+// ordered compaction (two block scans) then emits every key > T plus the
+// lowest-index keys == T, in ascending index order. In the solver the same CTA
+// compares the new support G' with the current one and builds the list of
+// x' - x over G' u G for the backtracking test (Section II-A).
+#include "internal.cuh"
+
+namespace qiht {
+
+constexpr int kTopThreads = 1024;
+
+__device__ __forceinline__ bool tid0() { return threadIdx.x == 0; }
+
+// Exclusive block scan of one int per thread (thread order); returns the total in *total.
+__device__ int block_excl_scan(int v, int* sh, int* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+        int t = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sh[lane] = t - s;            // exclusive prefix of warp totals
+        if (lane == 31) sh[32] = t;  // grand total
+    }
+    __syncthreads();
+    const int r = sh[w] + x - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_top(TopArgs a)
+{
+    extern __shared__ uint32_t keys[];            // n keys, then n/32 bitmap words
+    __shared__ unsigned hist[256];
+    __shared__ int scan_sh[33];
+    __shared__ int sel_digit, sel_above;
+    __shared__ unsigned red_u[32];
+    State* st = a.st;
+    if (a.h_bt && tid0()) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_bt, 0u);
+    if (st && st->stop) return;
+
+    const int n = a.n, s = a.s;
+    const int tid = threadIdx.x;
+    const float mu = a.mu ? (float)(*a.mu) : 1.0f;
+    const int per = (n + kTopThreads - 1) / kTopThreads;
+    const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
+
+    // keys of |x + mu g|
+    int bad = 0;
+    for (int j = tid; j < n; j += kTopThreads) {
+        const float x = a.x ? __ldcg(a.x + j) : 0.0f;
+        const float v = fmaf(mu, __ldcg(a.g + j), x);
+        const uint32_t k = __float_as_uint(v) & 0x7fffffffu;
+        bad |= (k > 0x7f800000u);
+        keys[j] = k;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && st) {
+        if (tid == 0) { st->status = QIHT_ERR_NONFINITE; st->stop = 1; }
+        return;
+    }
+
+    // radix select of the s-th largest key
+    uint32_t prefix = 0;
+    int need = s;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        if (tid < 256) hist[tid] = 0;
+        __syncthreads();
+        for (int j = j0; j < j1; ++j) {
+            const uint32_t k = keys[j];
+            if (pass == 0 || (k >> (shift + 8)) == (prefix >> (shift + 8))) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // lane l holds digits 255-8l .. 248-8l (descending)
+            int c[8], tot = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { c[i] = (int)hist[255 - 8 * tid - i]; tot += c[i]; }
+            int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (tid >= o) incl += y;
+            }
+            const int excl = incl - tot;
+            if (excl < need && need <= incl) {
+                int run = excl;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (run + c[i] >= need) { sel_digit = 255 - 8 * tid - i; sel_above = run; break; }
+                    run += c[i];
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)sel_digit << shift;
+        need -= sel_above;
+        __syncthreads();
+    }
+    const uint32_t T = prefix;    // s-th largest key; take `need` of the keys equal to T
+
+    // ordered compaction
+    int gt = 0, eq = 0;
+    for (int j = j0; j < j1; ++j) { const uint32_t k = keys[j]; gt += (k > T); eq += (k == T); }
+    int eq_total;
+    const int eq_before = block_excl_scan(eq, scan_sh, &eq_total);
+    const int take_eq = max(0, min(eq, need - eq_before));
+    int sel_total;
+    int pos = block_excl_scan(gt + take_eq, scan_sh, &sel_total);
+    int taken = 0;
+    for (int j = j0; j < j1; ++j) {
+        const uint32_t k = keys[j];
+        const bool take = (k > T) || (k == T && taken < take_eq);
+        if (k == T && take) ++taken;
+        if (take) {
+            a.sel[pos] = j;
+            if (a.val) {
+                const float x = a.x ? __ldcg(a.x + j) : 0.0f;
+                a.val[pos] = fmaf(mu, __ldcg(a.g + j), x);
+            }
+            ++pos;
+        }
+    }
+    // (s+1)-th largest key: T again if more keys equal T than were taken, else the largest key below T
+    unsigned below = 0;
+    for (int j = j0; j < j1; ++j) { const uint32_t k = keys[j]; if (k < T) below = max(below, k); }
+    below = __reduce_max_sync(0xffffffffu, below);
+    if ((tid & 31) == 0) red_u[tid >> 5] = below;
+    __syncthreads();
+    float kth0 = __uint_as_float(T), kth1 = 0.0f;
+    if (tid == 0) {
+        unsigned b = 0;
+        for (int w = 0; w < kTopThreads / 32; ++w) b = max(b, red_u[w]);
+        kth1 = (eq_total > need) ? __uint_as_float(T) : (s < n ? __uint_as_float(b) : 0.0f);
+        if (a.kth) { a.kth[0] = kth0; a.kth[1] = kth1; }
+        if (st) { st->kth0 = kth0; st->kth1 = kth1; }
+    }
+    __syncthreads();   // a.sel / a.val visible to the whole CTA
+
+    if (a.init) {
+        // initial support (Algorithm 2 initialisation): G = supp H_s(Q1^T Q(y))
+        for (int q = tid; q < s; q += kTopThreads) {
+            const int j = a.sel[q];
+            a.support_init[q] = j;
+            if (a.trace.support) a.trace.support[q] = j;
+        }
+        if (tid == 0 && a.trace.kth) { a.trace.kth[0] = kth0; a.trace.kth[1] = kth1; }
+        return;
+    }
+    if (!st) return;
+
+    // compare G' with G (both ascending) and build the x' - x list over G' u G
+    uint32_t* bitmap = keys + n;                  // n/32 words (keys no longer needed)
+    const int nbw = (n + 31) / 32;
+    for (int w = tid; w < nbw; w += kTopThreads) bitmap[w] = 0u;
+    __syncthreads();
+    int diff = 0;
+    for (int q = tid; q < s; q += kTopThreads) {
+        const int j = a.sel[q];
+        diff |= (j != __ldcg(a.support + q));
+        atomicOr(&bitmap[j >> 5], 1u << (j & 31));
+        a.uni[q] = j;
+        a.delta[q] = a.val[q] - __ldcg(a.x + j);
+    }
+    diff = __syncthreads_or(diff);
+    // old support entries not in G', in support order
+    const int sper = (s + kTopThreads - 1) / kTopThreads;
+    const int q0 = min(s, tid * sper), q1 = min(s, q0 + sper);
+    int cnt = 0;
+    for (int q = q0; q < q1; ++q) {
+        const int j = __ldcg(a.support + q);
+        cnt += !((bitmap[j >> 5] >> (j & 31)) & 1u);
+    }
+    int extra;
+    int p = block_excl_scan(cnt, scan_sh, &extra);
+    for (int q = q0; q < q1; ++q) {
+        const int j = __ldcg(a.support + q);
+        if (!((bitmap[j >> 5] >> (j & 31)) & 1u)) {
+            a.uni[s + p] = j;
+            a.delta[s + p] = -__ldcg(a.x + j);
+            ++p;
+        }
+    }
+    if (tid == 0) {
+        st->changed = diff ? 1 : 0;
+        st->union_count = s + extra;
+    }
+}
+
+size_t top_smem_bytes(int n) { return (size_t)n * 4 + (size_t)((n + 31) / 32) * 4; }
+
+static bool g_top_attr_set = false;
+
+static void ensure_top_attr()
+{
+    if (!g_top_attr_set) {
+        cudaFuncSetAttribute((const void*)k_top, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)top_smem_bytes(kMaxTopN));
+        g_top_attr_set = true;
+    }
+}
+
+void top_node(const TopArgs& a, cudaKernelNodeParams* p, void** argbuf)
+{
+    ensure_top_attr();
+    p->func = (void*)k_top;
+    p->gridDim = dim3(1);
+    p->blockDim = dim3(kTopThreads);
+    p->sharedMemBytes = (unsigned)top_smem_bytes(a.n);
+    p->kernelParams = argbuf;
+    p->extra = nullptr;
+}
+
+cudaError_t launch_top(const TopArgs& a, cudaStream_t s)
+{
+    cudaKernelNodeParams p{};
+    TopArgs copy = a;
+    void* args[1] = {&copy};
+    top_node(a, &p, args);
+    return cudaLaunchKernel(p.func, p.gridDim, p.blockDim, args, p.sharedMemBytes, s);
+}
+
+}  // namespace qiht

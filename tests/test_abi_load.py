@@ -1,0 +1,93 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/qiht.h. Only host-side paths are called here (argument
+checks that return before any CUDA call), so this runs without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1802_04907_gb300 as q
+from paper_1802_04907_gb300 import build as qbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "qiht.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qiht_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    qbuild.build()
+    return q.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "qiht_niht_solve" in names and "qiht_quantize" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(q.EXPORTS) == set(names)
+
+
+def test_host_only_entry_points(lib):
+    assert lib.qiht_abi_version() == 1
+    assert q.status_string(q.OK) == "QIHT_OK"
+    assert q.status_string(q.ERR_BACKTRACK_CAP) == "QIHT_ERR_BACKTRACK_CAP"
+    # words per column: ceil(rows / (32/bits)) rounded up to a multiple of 4
+    assert q.ld_words(8192, 8) == 2048 and q.ld_words(8192, 4) == 1024 and q.ld_words(8192, 2) == 512
+    assert q.ld_words(4512, 2) == 284 and q.ld_words(1, 8) == 4 and q.ld_words(17, 2) == 4
+    assert q.ld_words(10, 3) == -1 and q.ld_words(0, 8) == -1
+    assert q.solve_workspace_size(8192, 32768, 256) > 0
+    assert q.solve_workspace_size(0, 1, 1) == 0
+    assert lib.qiht_gemv_t_workspace_size() >= 4
+
+
+def test_argument_errors_return_before_launch(lib):
+    P = ctypes.c_void_p
+    # bits not in {2,4,8}
+    assert lib.qiht_quantize(P(16), 4, 4, 4, 3, 0, 0, 0, P(16), 4, P(16), None) == q.ERR_BITS
+    # null input
+    assert lib.qiht_quantize(None, 4, 4, 4, 8, 0, 0, 0, P(16), 4, P(16), None) == q.ERR_ARG
+    # wrong ld_words
+    assert lib.qiht_quantize(P(16), 4, 4, 4, 8, 0, 0, 0, P(16), 5, P(16), None) == q.ERR_ARG
+    # unknown flag
+    assert lib.qiht_quantize(P(16), 4, 4, 4, 8, 0, 0, 64, P(16), 4, P(16), None) == q.ERR_ARG
+    c = q._Codes(16, 16, 64, 128, 8, q.ld_words(64, 8))
+    cy = q._Codes(16, 16, 64, 1, 8, q.ld_words(64, 8))
+    prm = q._Params(2.0, 0.01, 32, 0)
+    solve = lib.qiht_niht_solve
+    # s > m, s < 1, null outputs, bad params, mismatched shapes, missing workspace
+    assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 65, 10, ctypes.byref(prm), P(16), P(16),
+                 P(16), None, P(256), 1 << 30, None) == q.ERR_ARG
+    assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 0, 10, ctypes.byref(prm), P(16), P(16),
+                 P(16), None, P(256), 1 << 30, None) == q.ERR_ARG
+    assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 4, 10, ctypes.byref(prm), None, P(16),
+                 P(16), None, P(256), 1 << 30, None) == q.ERR_ARG
+    bad = q._Params(1.0, 0.01, 32, 0)     # k (1 - c) must exceed 1
+    assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 4, 10, ctypes.byref(bad), P(16), P(16),
+                 P(16), None, P(256), 1 << 30, None) == q.ERR_ARG
+    c2 = q._Codes(16, 16, 64, 127, 8, q.ld_words(64, 8))
+    assert solve(ctypes.byref(c), ctypes.byref(c2), ctypes.byref(cy), 4, 10, ctypes.byref(prm), P(16), P(16),
+                 P(16), None, P(256), 1 << 30, None) == q.ERR_ARG
+    assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 4, 10, ctypes.byref(prm), P(16), P(16),
+                 P(16), None, None, 0, None) == q.ERR_WORKSPACE
+    assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 4, 10, ctypes.byref(prm), P(16), P(16),
+                 P(16), None, P(272), 1 << 30, None) == q.ERR_WORKSPACE      # not 256-byte aligned
+    # m above the GEMV^T limit
+    big = q._Codes(16, 16, 20000, 128, 8, q.ld_words(20000, 8))
+    bigy = q._Codes(16, 16, 20000, 1, 8, q.ld_words(20000, 8))
+    assert solve(ctypes.byref(big), ctypes.byref(big), ctypes.byref(bigy), 4, 10, ctypes.byref(prm), P(16),
+                 P(16), P(16), None, P(256), 1 << 40, None) == q.ERR_ARG
+    # top_s: s > n
+    assert lib.qiht_top_s(P(16), 10, 11, P(16), None, None, None, 0, None) == q.ERR_ARG
+
+
+def test_package_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(q, "_lib", None)
+    monkeypatch.setattr(q, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        q.lib()

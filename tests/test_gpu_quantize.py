@@ -1,0 +1,98 @@
+"""GPU quantizer (qiht_quantize) vs the CPU oracle: codes bit-exact, scales exact.
+
+Shapes span several 128 x 32 tiles with ragged tails (rows not a multiple of
+the codes per word, columns not a multiple of 32), vectors, strided inputs,
+a zero matrix, non-finite inputs, and the full-size 8192 x 32768 matrix on
+sampled columns."""
+import numpy as np
+import pytest
+import torch
+
+import layout
+import oracle
+import paper_1802_04907_gb300 as q
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(1, 1), (3, 5), (37, 53), (128, 33), (257, 100), (1000, 7), (4512, 64), (129, 1)]
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_codes_bit_exact(bits, shape):
+    m, n = shape
+    v = synth.random_floats((m, n), seed=m * 7 + n + bits)
+    seed = 0xDEADBEEF12345 + bits
+    Q = q.quantize(torch.from_numpy(v).cuda(), bits, seed, 1)
+    torch.cuda.synchronize()
+    want, c = oracle.quantize(v, bits, seed, 1)
+    assert Q.scale.item() == c
+    words = Q.words.cpu().numpy()
+    assert np.array_equal(layout.unpack(words, m, n, bits), want)
+    assert layout.padding_is_zero(words, m, n, bits)
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_vector_and_given_scale(bits):
+    m, n = 1001, 17
+    v = synth.random_floats((m, n), seed=5)
+    y = synth.random_floats(m, seed=6)
+    phi = torch.from_numpy(v).cuda()
+    q1, q2, qy = q.quantize_problem(phi, torch.from_numpy(y).cuda(), bits, bits, seed=99)
+    torch.cuda.synchronize()
+    c1, c = oracle.quantize(v, bits, 99, 0)
+    c2, _ = oracle.quantize(v, bits, 99, 1, c)
+    cy, sy = oracle.quantize(y, bits, 99, 2)
+    assert np.array_equal(layout.unpack(q1.words.cpu().numpy(), m, n, bits), c1)
+    assert np.array_equal(layout.unpack(q2.words.cpu().numpy(), m, n, bits), c2)
+    assert np.array_equal(layout.unpack(qy.words.cpu().numpy(), m, 1, bits)[:, 0], cy)
+    assert qy.scale.item() == sy and q2.scale.item() == c
+
+
+def test_strided_input():
+    big = synth.random_floats((300, 90), seed=2)
+    t = torch.from_numpy(big).cuda()[:, 10:73]
+    assert t.stride(0) == 90
+    Q = q.quantize(t, 4, 7, 0)
+    torch.cuda.synchronize()
+    want, c = oracle.quantize(np.ascontiguousarray(big[:, 10:73]), 4, 7, 0)
+    assert Q.scale.item() == c
+    assert np.array_equal(layout.unpack(Q.words.cpu().numpy(), 300, 63, 4), want)
+
+
+def test_zero_matrix():
+    v = np.zeros((64, 40), dtype=np.float32)
+    Q = q.quantize(torch.from_numpy(v).cuda(), 8, 1, 0)
+    torch.cuda.synchronize()
+    want, c = oracle.quantize(v, 8, 1, 0)
+    assert Q.scale.item() == 0.0 and c == 0.0
+    assert np.array_equal(layout.unpack(Q.words.cpu().numpy(), 64, 40, 8), want)
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_nonfinite_is_reported(bad):
+    v = synth.random_floats((50, 20), seed=1)
+    v[13, 7] = bad
+    with pytest.raises(q.QihtError) as e:
+        q.quantize(torch.from_numpy(v).cuda(), 8, 1, 0, check_finite=True)
+    assert e.value.status == q.ERR_NONFINITE
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_full_size_sampled_columns(bits):
+    # 8192 x 32768 (the large single-solve workload), sampled columns checked exactly
+    p = synth.large_noisy(seed=0)
+    phi = torch.from_numpy(p.phi).cuda()
+    Q = q.quantize(phi, bits, 12345, 0)
+    torch.cuda.synchronize()
+    c, bad = oracle.absmax(p.phi)
+    assert bad == 0 and Q.scale.item() == c
+    rng = np.random.Generator(np.random.PCG64(bits))
+    cols = np.concatenate([[0, 31, 32, p.n - 1], rng.choice(p.n, 12, replace=False)])
+    ldw = q.ld_words(p.m, bits)
+    words = Q.words.view(p.n, ldw)
+    for j in cols:
+        want, _ = oracle.quantize(np.ascontiguousarray(p.phi[:, j]), bits, 12345, 0, c, col0=int(j), rows_total=p.m)
+        got = layout.unpack(words[j].cpu().numpy(), p.m, 1, bits)[:, 0]
+        assert np.array_equal(got, want), j

@@ -1,0 +1,180 @@
+"""End-to-end parity of qiht_niht_solve (Algorithm 2 on the GPU) with the CPU oracle.
+
+Both sides quantize the same seeded inputs (codes are bit-exact, see
+test_gpu_quantize.py) and run the same number of iterations. The GPU computes
+g in exact integer sums of 24-bit fixed-point residuals and everything else in
+FP32 with FP64 scalars; the oracle is FP64. The rule:
+  - the support after every iteration is identical up to the first iteration
+    whose selection was ambiguous in the oracle (relative gap between the s-th
+    and (s+1)-th magnitudes below 1e-5, or a backtracking test within 1e-5 of
+    its threshold); the step size agrees to 1e-4 relative there
+  - when no iteration was ambiguous, the final x agrees to 1e-4 relative L2
+  - otherwise both recoveries are compared against the ground truth and the
+    first ambiguous iteration is reported.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1802_04907_gb300 as q
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GAP = 1e-5
+
+
+def _run_pair(p, bits_phi, bits_y, iters, seed, **kw):
+    phi = torch.from_numpy(p.phi).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    q1, q2, qy = q.quantize_problem(phi, y, bits_phi, bits_y, seed)
+    sv = q.niht_solve(q1, q2, qy, p.s, iters, trace=True, **kw)
+    torch.cuda.synchronize()
+    ref, _ = oracle.qiht(p.phi, p.y, p.s, iters, bits_phi=bits_phi, bits_y=bits_y, seed=seed, trace=True, **kw)
+    return sv, ref
+
+
+def _first_ambiguous(ref):
+    tr = ref.trace
+    for t in range(ref.iters_run + 1):
+        if tr["min_gap"][t] < GAP or tr["min_margin"][t] < GAP:
+            return t
+    return None
+
+
+def _check(sv, ref, p, label=""):
+    rep = sv.read_report()
+    assert rep.status == ref.status, (rep, ref.status)
+    amb = _first_ambiguous(ref)
+    T = ref.iters_run if amb is None else amb - 1
+    sup = sv.trace["support"].cpu().numpy()
+    mu = sv.trace["mu"].cpu().numpy()
+    for t in range(0, T + 1):
+        assert np.array_equal(sup[t], ref.trace["support"][t]), f"{label}: support differs at iteration {t}"
+        if t > 0:
+            assert abs(mu[t] - ref.trace["mu"][t]) <= 1e-4 * ref.trace["mu"][t], f"{label}: mu at {t}"
+    x = sv.x.cpu().numpy().astype(np.float64)
+    assert np.count_nonzero(x) <= p.s
+    truth = np.linalg.norm(p.x_true)
+    if amb is None:
+        assert rep.iters_run == ref.iters_run
+        assert np.array_equal(np.sort(sv.support.cpu().numpy()), ref.support)
+        rel = np.linalg.norm(x - ref.x) / max(np.linalg.norm(ref.x), 1e-300)
+        assert rel <= 1e-4, f"{label}: x differs from the oracle by {rel:.3e}"
+        return rel, None
+    e_gpu = np.linalg.norm(x - p.x_true) / truth
+    e_ref = np.linalg.norm(ref.x - p.x_true) / truth
+    assert e_gpu <= max(1.5 * e_ref, e_ref + 0.02), f"{label}: gpu error {e_gpu:.3e} vs oracle {e_ref:.3e}"
+    return None, amb
+
+
+def test_small_noiseless_8bit():
+    # 256 x 1024, s = 16, N(0,1) nonzeros, noiseless, 8-bit Phi and y, 200 iterations, seed 0
+    p = synth.small_noiseless(0)
+    sv, ref = _run_pair(p, 8, 8, 200, seed=0)
+    _check(sv, ref, p, "small")
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_noisy_ragged(bits):
+    # sizes not multiples of the tiles: rows 1000 (not a multiple of 16), cols 3001
+    p = synth.gaussian(1000, 3001, 25, seed=bits, snr_db=30.0, values="pm_u")
+    sv, ref = _run_pair(p, bits, bits, 80, seed=11)
+    _check(sv, ref, p, f"ragged-{bits}")
+
+
+@pytest.mark.parametrize("bits_phi,bits_y", [(2, 8), (4, 8), (8, 4)])
+def test_mixed_precision(bits_phi, bits_y):
+    p = synth.gaussian(512, 2048, 20, seed=3, snr_db=25.0)
+    sv, ref = _run_pair(p, bits_phi, bits_y, 60, seed=5)
+    _check(sv, ref, p, f"{bits_phi}/{bits_y}")
+
+
+def test_interferometry_small():
+    p = synth.interferometry(n_ant=12, grid=32, n_src=6, s=8, snr_db=20.0, seed=2)
+    sv, ref = _run_pair(p, 8, 8, 60, seed=1)
+    _check(sv, ref, p, "interferometry")
+
+
+def test_backtracking_instance():
+    # equal magnitudes, low SNR: shrinks happen; their count must match where unambiguous
+    for seed in range(40):
+        p = synth.gaussian(48, 128, 12, seed=300 + seed, values="ones", snr_db=10.0)
+        ref, _ = oracle.qiht(p.phi, p.y, 12, 40, bits_phi=8, bits_y=8, seed=seed, trace=True)
+        if ref.backtracks > 0:
+            break
+    sv, ref = _run_pair(p, 8, 8, 40, seed=seed)
+    _check(sv, ref, p, "backtracking")
+    amb = _first_ambiguous(ref)
+    T = ref.iters_run if amb is None else amb - 1
+    bt = sv.trace["bt"].cpu().numpy()
+    assert np.array_equal(bt[1:T + 1], ref.trace["bt"][1:T + 1])
+
+
+def test_zero_iterations_gives_initial_support():
+    p = synth.gaussian(200, 700, 9, seed=4)
+    sv, ref = _run_pair(p, 8, 8, 0, seed=2)
+    rep = sv.read_report()
+    assert rep.iters_run == 0 and rep.status == q.OK
+    assert torch.all(sv.x == 0)
+    assert np.array_equal(sv.support.cpu().numpy(), ref.support)
+
+
+def test_zero_observation_converges_immediately():
+    p = synth.gaussian(64, 256, 4, seed=1)
+    p.y[:] = 0.0
+    sv, ref = _run_pair(p, 8, 8, 10, seed=1)
+    rep = sv.read_report()
+    assert rep.iters_run == 0 == ref.iters_run and rep.status == q.OK
+    assert torch.all(sv.x == 0)
+
+
+def test_nonfinite_input_reports_status():
+    p = synth.gaussian(64, 256, 4, seed=1)
+    p.phi[3, 3] = np.nan
+    phi = torch.from_numpy(p.phi).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    q1, q2, qy = q.quantize_problem(phi, y, 8, 8, 1)
+    sv = q.niht_solve(q1, q2, qy, 4, 10)
+    torch.cuda.synchronize()
+    assert sv.read_report().status == q.ERR_NONFINITE
+
+
+def test_deterministic_and_graph_reuse():
+    p = synth.gaussian(700, 2500, 30, seed=8, snr_db=20.0)
+    phi = torch.from_numpy(p.phi).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    q1, q2, qy = q.quantize_problem(phi, y, 4, 4, 3)
+    sv = q.Solver(700, 2500, 30, 50)
+    sv(q1, q2, qy)
+    torch.cuda.synchronize()
+    x1 = sv.x.clone()
+    r1 = sv.read_report()
+    sv(q1, q2, qy)          # same pointers: cached graph
+    torch.cuda.synchronize()
+    assert torch.equal(sv.x, x1)
+    assert sv.read_report() == r1
+
+
+def test_full_size_large_solve():
+    # 8192 x 32768, s = 256, +-U(0.5,1.5) nonzeros, 30 dB, 8-bit, 300 iterations (the benchmarked
+    # configuration): properties that hold at any size, plus recovery of the true support
+    p = synth.large_noisy(seed=0)
+    phi = torch.from_numpy(p.phi).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    q1, q2, qy = q.quantize_problem(phi, y, 8, 8, 0)
+    sv = q.niht_solve(q1, q2, qy, p.s, 300, trace=True)
+    torch.cuda.synchronize()
+    rep = sv.read_report()
+    assert rep.status == q.OK
+    x = sv.x.cpu().numpy().astype(np.float64)
+    sup = np.sort(sv.support.cpu().numpy())
+    assert np.count_nonzero(x) <= p.s
+    assert set(np.flatnonzero(x)) <= set(sup)
+    assert len(np.intersect1d(sup, p.support)) >= 0.99 * p.s
+    rel = np.linalg.norm(x - p.x_true) / np.linalg.norm(p.x_true)
+    assert rel < 0.05, rel
+    # the residual reported is the one of the returned x
+    r2 = sv.trace["resid2"].cpu().numpy()[: rep.iters_run + 1]
+    assert abs(r2[-1] - rep.resid_norm2) <= 1e-12 * rep.resid_norm2
