@@ -57,16 +57,6 @@ __device__ unsigned block_max_u(unsigned v, unsigned* sh)
 }
 
 // Sum of squares of a list (g[idx[q]] when idx != nullptr, else v[q]) in a fixed order.
-__device__ double list_norm2(const float* v, const int32_t* idx, int count, double* sh)
-{
-    double acc = 0.0;
-    for (int q = threadIdx.x; q < count; q += blockDim.x) {
-        const float e = idx ? __ldcg(v + __ldcg(idx + q)) : __ldcg(v + q);
-        acc += (double)e * (double)e;
-    }
-    return block_sum_d(acc, sh);
-}
-
 __device__ void write_report(const GatherArgs& a, const State* st)
 {
     if (!a.report) return;
@@ -112,22 +102,45 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     const int q = rb * kGatherThreads + threadIdx.x;       // word index in every column
     const int32_t* list = (a.mode == kGatherMu) ? a.support : (a.mode == kGatherResid ? a.new_sel : a.cols);
     const float* coefs = (a.mode == kGatherResid) ? a.new_val : a.coef;
+    __shared__ int s_col[kGatherCols];
+    __shared__ float s_cf[kGatherCols];
 
     if (jc < nchunks) {
-        float z[G];
-#pragma unroll
-        for (int k = 0; k < G; ++k) z[k] = 0.0f;
+        // this chunk's columns and coefficients, loaded once for the CTA
+        if (threadIdx.x < kGatherCols) {
+            const int jj = jc * kGatherCols + threadIdx.x;
+            int col = -1;
+            float cf = 0.0f;
+            if (jj < count) {
+                col = __ldcg(list + jj);
+                cf = (a.mode == kGatherMu) ? __ldcg(a.g + col) : __ldcg(coefs + jj);
+            }
+            s_col[threadIdx.x] = col;
+            s_cf[threadIdx.x] = cf;
+        }
+        __syncthreads();
+        if (rb == 0 && threadIdx.x == 0 && a.chunk_partial) {
+            double acc2 = 0.0;
+            for (int c = 0; c < kGatherCols; ++c) acc2 += (double)s_cf[c] * (double)s_cf[c];
+            a.chunk_partial[jc] = acc2;
+        }
         if (q < ld) {
-#pragma unroll 2
+            uint32_t w[kGatherCols];
+#pragma unroll
             for (int c = 0; c < kGatherCols; ++c) {
-                const int jj = jc * kGatherCols + c;
-                if (jj < count) {
-                    const int col = __ldcg(list + jj);
-                    const float cf = (a.mode == kGatherMu) ? __ldcg(a.g + col) : __ldcg(coefs + jj);
-                    const uint32_t w = __ldg(a.Q.words + (size_t)col * ld + q);
+                const int col = s_col[c];
+                w[c] = col >= 0 ? __ldg(a.Q.words + (size_t)col * ld + q) : 0u;
+            }
+            float z[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) z[k] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kGatherCols; ++c) {
+                if (s_col[c] >= 0) {
+                    const float cf = s_cf[c];
 #pragma unroll
                     for (int k = 0; k < G; ++k) {
-                        const int code = (int)((w >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
+                        const int code = (int)((w[c] >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
                         z[k] = fmaf((float)(2 * code - (L - 1)), cf, z[k]);
                     }
                 }
@@ -153,11 +166,27 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
         float zz[G];
 #pragma unroll
         for (int k = 0; k < G; ++k) zz[k] = 0.0f;
-        for (int ch = 0; ch < nchunks; ++ch) {
-            const float* src = a.partial + (size_t)ch * rows_pad + (size_t)q * G;
+        const float* src0 = a.partial + (size_t)q * G;
+        int ch = 0;
+        for (; ch + 4 <= nchunks; ch += 4) {
+            float4 v[4][G / 4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < G; k += 4)
+                    v[u][k / 4] = __ldcg(reinterpret_cast<const float4*>(src0 + (size_t)(ch + u) * rows_pad + k));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < G; k += 4) {
+                    zz[k] += v[u][k / 4].x; zz[k + 1] += v[u][k / 4].y;
+                    zz[k + 2] += v[u][k / 4].z; zz[k + 3] += v[u][k / 4].w;
+                }
+        }
+        for (; ch < nchunks; ++ch) {
 #pragma unroll
             for (int k = 0; k < G; k += 4) {
-                const float4 v = __ldcg(reinterpret_cast<const float4*>(src + k));
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(src0 + (size_t)ch * rows_pad + k));
                 zz[k] += v.x; zz[k + 1] += v.y; zz[k + 2] += v.z; zz[k + 3] += v.w;
             }
         }
@@ -217,8 +246,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     const double alpha_d = (double)(*a.Q.scale) / (double)(L - 1);
 
     if (a.mode == kGatherMu) {
-        const double num = list_norm2(a.g, a.support, a.s, shd);
         if (threadIdx.x == 0) {
+            double num = 0.0;
+            for (int c = 0; c < nchunks; ++c) num += __ldcg(a.chunk_partial + c);
             const double den = alpha_d * alpha_d * total;
             st->num = num;
             st->bt = 0;
@@ -232,8 +262,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
             }
         }
     } else if (a.mode == kGatherOmega) {
-        const double dn = list_norm2(a.coef, nullptr, count, shd);
         if (threadIdx.x == 0) {
+            double dn = 0.0;
+            for (int c = 0; c < nchunks; ++c) dn += __ldcg(a.chunk_partial + c);
             const double dd = alpha_d * alpha_d * total;
             unsigned again = 0;
             if (dn > 0.0) {

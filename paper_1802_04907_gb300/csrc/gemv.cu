@@ -15,6 +15,8 @@
 // CTA walks a contiguous range of column groups (CPW columns each); a slot of
 // TPC threads reads CPW columns at a time with coalesced vector loads, and the
 // per-column integer sums are reduced across the slot with warp reductions.
+#include <cstdlib>
+
 #include "internal.cuh"
 
 namespace qiht {
@@ -202,6 +204,335 @@ __global__ void __launch_bounds__(256) k_gemv_t(GemvTArgs a, int tpc)
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged variant. One CTA per SM walks a contiguous range of columns (its
+// bytes are contiguous in the column-packed layout). A producer warp streams
+// stages of CPSL*slots columns into a ring of shared-memory buffers with
+// cp.async.bulk (completion counted in bytes on an mbarrier); 16 consumer warps
+// hold the fixed-point residual in registers and read each code once from
+// shared memory (16-byte pieces, consecutive threads on consecutive pieces).
+// Every wait is bounded by %globaltimer; a timeout sets the status and the CTA
+// drains its own copies before leaving.
+// ---------------------------------------------------------------------------
+constexpr int kTmaConsumers = 512;
+constexpr int kTmaThreads = kTmaConsumers + 32;
+constexpr int kTmaWarps = kTmaConsumers / 32;
+constexpr int kTmaRingBytes = 196608;        // stage ring (192 KiB)
+constexpr unsigned long long kWaitBudgetNs = 200ull * 1000 * 1000;   // 0.2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete; false after the time budget.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer_ns() - t0 > kWaitBudgetNs) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kTmaConsumers) : "memory"); }
+
+__device__ __forceinline__ void report_timeout(const GemvTArgs& a)
+{
+    if (a.st) {
+        a.st->status = QIHT_ERR_TIMEOUT;
+        a.st->stop = 1;
+    }
+    if (a.err) atomicExch(a.err, 1u);
+}
+
+template <int BITS, int PPT, int CPSL>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int tpc, int nstage_buf)
+{
+    constexpr int G = 32 / BITS;
+    constexpr int E = G / 4;
+    constexpr int L = 1 << BITS;
+    constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
+    constexpr int NLW = PPT * 4 * E;            // limb words per limb per thread
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int guard = ++a.st->outer_guard;
+        cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
+                                (!a.st->stop && guard < a.st->iters + 1) ? 1u : 0u);
+    }
+    if (a.st && a.st->stop) return;
+
+    const int n = a.Q.cols, ld = a.Q.ld, m = a.Q.rows;
+    const int P = ld / 4;                        // 16-byte pieces per column
+    const unsigned colbytes = (unsigned)ld * 4u;
+    const int slots = kTmaConsumers / tpc;
+    const int cps = CPSL * slots;                // columns per stage
+    const unsigned stage_bytes = (unsigned)cps * colbytes;
+    const int NS = nstage_buf;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)NS * stage_bytes);
+    uint64_t* empty = full + NS;
+    long long* red = reinterpret_cast<long long*>(empty + NS);          // [2][warps][CPSL*3]
+    long long* red_r = red + 2 * kTmaWarps * CPSL * 3;                  // [warps]
+
+    const int c0 = (int)((long long)n * blockIdx.x / gridDim.x);
+    const int c1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
+    const int ncols = c1 - c0;
+    const int nst = (ncols + cps - 1) / cps;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kTmaWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kTmaWarps) {
+        // producer
+        if (lane == 0) {
+            int issued = 0;
+            bool ok = true;
+            for (int it = 0; it < nst; ++it) {
+                const int sb = it % NS;
+                const unsigned ph = (unsigned)(it / NS) & 1u;
+                if (it >= NS && !mbar_wait(&empty[sb], ph ^ 1u)) { ok = false; break; }
+                const int cols_here = min(cps, ncols - it * cps);
+                const unsigned bytes = (unsigned)cols_here * colbytes;
+                mbar_expect_tx(&full[sb], bytes);
+                bulk_g2s(smem + (size_t)sb * stage_bytes,
+                         reinterpret_cast<const unsigned char*>(a.Q.words) + (size_t)(c0 + it * cps) * colbytes,
+                         bytes, &full[sb]);
+                ++issued;
+            }
+            if (!ok) {
+                report_timeout(a);
+                // drain this CTA's own copies (bounded) before leaving
+                for (int it = max(0, issued - NS); it < issued; ++it)
+                    mbar_wait(&full[it % NS], (unsigned)(it / NS) & 1u);
+            }
+        }
+        return;
+    }
+
+    // consumers: fixed-point residual limbs of this thread's pieces
+    const int slot = threadIdx.x / tpc;
+    const int t = threadIdx.x % tpc;
+    const int sh = fixed_shift(*a.rmax_bits);
+    uint32_t l0[NLW], l1[NLW], l2[NLW];
+    long long rsum = 0;
+#pragma unroll
+    for (int pp = 0; pp < PPT; ++pp) {
+        const int piece = t + pp * tpc;
+#pragma unroll
+        for (int q = 0; q < 4 * E; ++q) {
+            uint32_t b0 = 0, b1 = 0, b2 = 0;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int i = piece * 4 * G + 4 * q + p;
+                int v = 0;
+                if (piece < P && i < m) v = __float2int_rn(ldexpf(__ldcg(a.r + i), sh));
+                rsum += v;
+                b0 |= (uint32_t)(v & 255) << (8 * p);
+                b1 |= (uint32_t)((v >> 8) & 255) << (8 * p);
+                b2 |= (uint32_t)((v >> 16) & 255) << (8 * p);
+            }
+            l0[pp * 4 * E + q] = b0;
+            l1[pp * 4 * E + q] = b1;
+            l2[pp * 4 * E + q] = b2;
+        }
+    }
+    {
+        long long v = (slot == 0) ? rsum : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red_r[warp] = v;
+    }
+    consumer_sync();
+    long long R = 0;
+    for (int w = 0; w < tpc / 32; ++w) R += red_r[w];
+    const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
+    const double outscale = ldexp(alpha, -sh);
+    const int wps = tpc >> 5;
+
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = 0;
+    consumer_sync();
+    for (int it = 0; it < nst; ++it) {
+        const int sb = it % NS;
+        const unsigned ph = (unsigned)(it / NS) & 1u;
+        if (!mbar_wait(&full[sb], ph)) {
+            // keep going to the barrier below so that every consumer leaves together
+            s_abort = 1;
+            report_timeout(a);
+        }
+        const int cols_here = min(cps, ncols - it * cps);
+        const unsigned char* stage = smem + (size_t)sb * stage_bytes;
+        uint32_t a0[CPSL], a1[CPSL];
+        int32_t a2[CPSL];
+#pragma unroll
+        for (int cl = 0; cl < CPSL; ++cl) {
+            a0[cl] = 0; a1[cl] = 0; a2[cl] = 0;
+            const int col = slot * CPSL + cl;
+            if (col < cols_here) {
+                const uint4* cp = reinterpret_cast<const uint4*>(stage + (size_t)col * colbytes);
+#pragma unroll
+                for (int pp = 0; pp < PPT; ++pp) {
+                    const int piece = t + pp * tpc;
+                    if (piece < P) {
+                        const uint4 v = cp[piece];
+                        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+#pragma unroll
+                            for (int k = 0; k < E; ++k) {
+                                const uint32_t x = (wv[w] >> (BITS * k)) & MASK;
+                                const int li = pp * 4 * E + w * E + k;
+                                a0[cl] = dp4a_uu(x, l0[li], a0[cl]);
+                                a1[cl] = dp4a_uu(x, l1[li], a1[cl]);
+                                a2[cl] = dp4a_us(x, l2[li], a2[cl]);
+                            }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sb]);     // this warp is done with the stage
+        long long* rb = red + (size_t)(it & 1) * kTmaWarps * CPSL * 3;
+#pragma unroll
+        for (int cl = 0; cl < CPSL; ++cl) {
+            const uint32_t s0 = __reduce_add_sync(0xffffffffu, a0[cl]);
+            const uint32_t s1 = __reduce_add_sync(0xffffffffu, a1[cl]);
+            const int32_t s2 = __reduce_add_sync(0xffffffffu, a2[cl]);
+            if (lane == 0) {
+                rb[(warp * CPSL + cl) * 3 + 0] = (long long)s0;
+                rb[(warp * CPSL + cl) * 3 + 1] = (long long)s1;
+                rb[(warp * CPSL + cl) * 3 + 2] = (long long)s2;
+            }
+        }
+        consumer_sync();
+        if (*(volatile int*)&s_abort) {
+            // drain the copies this CTA may still have in flight (bounded), then leave
+            if (threadIdx.x == 0)
+                for (int j = it; j < min(nst, it + NS); ++j) mbar_wait(&full[j % NS], (unsigned)(j / NS) & 1u);
+            break;
+        }
+        if (t < CPSL) {
+            const int cl = t;
+            const int col = slot * CPSL + cl;
+            if (col < cols_here) {
+                long long S0 = 0, S1 = 0, S2 = 0;
+                for (int w = slot * wps; w < (slot + 1) * wps; ++w) {
+                    S0 += rb[(w * CPSL + cl) * 3 + 0];
+                    S1 += rb[(w * CPSL + cl) * 3 + 1];
+                    S2 += rb[(w * CPSL + cl) * 3 + 2];
+                }
+                const long long S = S0 + (S1 << 8) + (S2 << 16);
+                const long long T = 2 * S - (long long)(L - 1) * R;
+                a.g[c0 + it * cps + col] = (float)((double)T * outscale);
+            }
+        }
+        // the double-buffered partials make a second barrier unnecessary
+    }
+}
+
+struct TmaPlan {
+    void* fn;
+    int tpc;
+    int ns;
+    size_t smem;
+    unsigned grid;
+    bool ok;
+};
+
+template <int BITS, int PPT, int CPSL>
+static void* tma_fn() { return (void*)k_gemv_t_tma<BITS, PPT, CPSL>; }
+
+static TmaPlan plan_tma(const Codes& Q, int nsm)
+{
+    TmaPlan p{};
+    const int P = Q.ld / 4;
+    int tpc = 32;
+    while (tpc < P && tpc < kTmaConsumers) tpc <<= 1;
+    const int ppt = (P + tpc - 1) / tpc;
+    const int slots = kTmaConsumers / tpc;
+    const size_t colbytes = (size_t)Q.ld * 4;
+    int cpsl = 4;
+    while (cpsl > 1 && (size_t)cpsl * slots * colbytes > 49152) cpsl >>= 1;
+    const size_t stage = (size_t)cpsl * slots * colbytes;
+    int ns = (int)(kTmaRingBytes / stage);
+    if (ns > 8) ns = 8;
+    if (ppt > 2 || ns < 2 || (Q.bits != 8 && ppt > 1)) return p;
+    void* fn = nullptr;
+#define QIHT_TMA_CASE(B, PP, C) if (Q.bits == B && ppt == PP && cpsl == C) fn = tma_fn<B, PP, C>();
+    QIHT_TMA_CASE(8, 1, 4) QIHT_TMA_CASE(8, 1, 2) QIHT_TMA_CASE(8, 1, 1)
+    QIHT_TMA_CASE(8, 2, 4) QIHT_TMA_CASE(8, 2, 2) QIHT_TMA_CASE(8, 2, 1)
+    QIHT_TMA_CASE(4, 1, 4) QIHT_TMA_CASE(4, 1, 2) QIHT_TMA_CASE(4, 1, 1)
+    QIHT_TMA_CASE(2, 1, 4) QIHT_TMA_CASE(2, 1, 2) QIHT_TMA_CASE(2, 1, 1)
+#undef QIHT_TMA_CASE
+    if (!fn) return p;
+    p.fn = fn;
+    p.tpc = tpc;
+    p.ns = ns;
+    p.smem = (size_t)ns * stage + 2 * (size_t)ns * 8 + 2 * (size_t)kTmaWarps * cpsl * 3 * 8 + kTmaWarps * 8;
+    int grid = nsm;
+    if (grid > Q.cols) grid = Q.cols;
+    p.grid = (unsigned)grid;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    p.ok = true;
+    return p;
+}
+
+static bool use_tma()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("QIHT_GEMV");
+        v = (e && e[0] == 'l') ? 0 : 1;     // "ldg" selects the register-staged kernel
+    }
+    return v == 1;
+}
+
 template <int BITS>
 static void pick(int rows_pad, int& rpt, int& tpc, void** fn)
 {
@@ -265,6 +596,21 @@ static GemvPlan plan_gemv_t(const Codes& Q, int nsm)
 
 void gemv_t_node(const GemvTArgs& a, int nsm, cudaKernelNodeParams* p, void** argbuf)
 {
+    if (use_tma()) {
+        TmaPlan tp = plan_tma(a.Q, nsm);
+        if (tp.ok) {
+            // argbuf[0] -> GemvTArgs, argbuf[1] -> int tpc, argbuf[2] -> int stages (owned by the caller)
+            *reinterpret_cast<int*>(argbuf[1]) = tp.tpc;
+            *reinterpret_cast<int*>(argbuf[2]) = tp.ns;
+            p->func = tp.fn;
+            p->gridDim = dim3(tp.grid);
+            p->blockDim = dim3(kTmaThreads);
+            p->sharedMemBytes = (unsigned)tp.smem;
+            p->kernelParams = argbuf;
+            p->extra = nullptr;
+            return;
+        }
+    }
     GemvPlan pl = plan_gemv_t(a.Q, nsm);
     // argbuf[0] -> GemvTArgs copy, argbuf[1] -> int tpc (owned by the caller)
     *reinterpret_cast<int*>(argbuf[1]) = pl.tpc;
@@ -278,6 +624,15 @@ void gemv_t_node(const GemvTArgs& a, int nsm, cudaKernelNodeParams* p, void** ar
 
 cudaError_t launch_gemv_t(const GemvTArgs& a, int nsm, cudaStream_t s)
 {
+    if (use_tma()) {
+        TmaPlan tp = plan_tma(a.Q, nsm);
+        if (tp.ok) {
+            GemvTArgs copy = a;
+            int tpc = tp.tpc, ns = tp.ns;
+            void* args[3] = {&copy, &tpc, &ns};
+            return cudaLaunchKernel(tp.fn, dim3(tp.grid), dim3(kTmaThreads), args, tp.smem, s);
+        }
+    }
     GemvPlan pl = plan_gemv_t(a.Q, nsm);
     GemvTArgs copy = a;
     int tpc = pl.tpc;

@@ -11,7 +11,7 @@ namespace qiht {
 
 constexpr int kMaxRows = 16384;   // m limit of the integer GEMV^T (32-bit lane sums cannot overflow)
 constexpr int kMaxTopN = 49152;   // n limit of the one-CTA radix select (keys held in shared memory)
-constexpr int kGatherCols = 8;    // columns per CTA in the column-subset product
+constexpr int kGatherCols = 32;   // list entries (columns) per CTA in the column-subset product
 constexpr int kGatherThreads = 256;
 
 // Device view of a quantized matrix (see the column-packed layout in qiht.h).
@@ -56,6 +56,7 @@ struct GatherArgs {
     float* z;                 // plain mode: output z (rows)
     float* partial;           // [chunks][rows_pad] partial sums
     double* rb_partial;       // [row_blocks][2] per-row-block sums
+    double* chunk_partial;    // [chunks] sums of squared coefficients per chunk (Mu, Omega)
     unsigned* counters;       // [row_blocks + 1]
     int mode;
     // solver fields (modes Mu, Omega, Resid)
@@ -83,6 +84,7 @@ struct GemvTArgs {
     float* g;
     State* st;                  // non-null in the solver: skip when st->stop
     unsigned long long h_outer; // outer-loop handle (solver loop body only): set by thread 0 of CTA 0
+    unsigned* err;              // optional: set to 1 when a device-side wait runs out (no solver state)
 };
 
 struct TopArgs {
@@ -118,7 +120,8 @@ struct InitArgs {
     qiht_trace trace;
 };
 
-// Kernel node builders (each translation unit owns its kernels).
+// Kernel node builders (each translation unit owns its kernels). gemv_t_node needs
+// argbuf[0..2] pointing at a GemvTArgs and two ints owned by the caller.
 void gemv_t_node(const GemvTArgs& a, int num_sms, cudaKernelNodeParams* p, void** argbuf);
 void gather_node(const GatherArgs& a, cudaKernelNodeParams* p, void** argbuf);
 void top_node(const TopArgs& a, cudaKernelNodeParams* p, void** argbuf);

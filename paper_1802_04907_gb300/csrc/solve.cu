@@ -205,6 +205,7 @@ qiht_status qiht_gemv_t(const qiht_codes* Q, const float* r, float* g, void* wor
     a.rmax_bits = reinterpret_cast<const unsigned*>(rmax);
     a.g = g;
     a.st = nullptr;
+    a.err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(workspace) + 4);
     if (launch_gemv_t(a, num_sms(), s) != cudaSuccess) return QIHT_ERR_CUDA;
     return QIHT_OK;
 }
@@ -300,7 +301,8 @@ qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float
 namespace {
 
 struct Plan {
-    size_t off_state, off_yhat, off_r, off_g, off_sel, off_val, off_uni, off_delta, off_partial, off_rbp, total;
+    size_t off_state, off_yhat, off_r, off_g, off_sel, off_val, off_uni, off_delta, off_partial, off_rbp, off_chunk,
+        total;
 };
 
 Plan plan_solve(int m, int n, int s)
@@ -324,6 +326,7 @@ Plan plan_solve(int m, int n, int s)
     p.off_partial = o; o += align256(fl * 4);
     const int rb = gather_row_blocks(m, 2) > gather_row_blocks(m, 8) ? gather_row_blocks(m, 2) : gather_row_blocks(m, 8);
     p.off_rbp = o; o += align256((size_t)rb * 2 * 8);
+    p.off_chunk = o; o += align256((size_t)gather_chunks(2 * s) * 8);
     p.total = o;
     return p;
 }
@@ -405,6 +408,7 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     float* delta = reinterpret_cast<float*>(ws + pl.off_delta);
     float* partial = reinterpret_cast<float*>(ws + pl.off_partial);
     double* rbp = reinterpret_cast<double*>(ws + pl.off_rbp);
+    double* chunkp = reinterpret_cast<double*>(ws + pl.off_chunk);
     qiht_trace tr{};
     if (trace) tr = *trace;
     const int nsm = num_sms();
@@ -446,8 +450,8 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     ga.g = g;
     ga.st = st;
     ga.h_outer = 0;                 // the set-up product does not steer the loop
-    int tpc = 0;
-    void* gemv_args[2] = {&ga, &tpc};
+    int tpc = 0, nstg = 0;
+    void* gemv_args[3] = {&ga, &tpc, &nstg};
     cudaKernelNodeParams gp{};
     gemv_t_node(ga, nsm, &gp, gemv_args);
     cudaGraphNode_t n_g0;
@@ -483,6 +487,7 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     base.Q = view(Q2);
     base.partial = partial;
     base.rb_partial = rbp;
+    base.chunk_partial = chunkp;
     base.st = st;
     base.g = g;
     base.support = support;
@@ -556,8 +561,8 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     TRY(add_kernel(body, &b_re, &b_w, 1, pre));
     GemvTArgs gb = ga;
     gb.h_outer = (unsigned long long)h_outer;   // the loop body's product decides whether to go on
-    int tpcb = 0;
-    void* gemvb_args[2] = {&gb, &tpcb};
+    int tpcb = 0, nstgb = 0;
+    void* gemvb_args[3] = {&gb, &tpcb, &nstgb};
     cudaKernelNodeParams gpb{};
     gemv_t_node(gb, nsm, &gpb, gemvb_args);
     TRY(add_kernel(body, &b_g, &b_re, 1, gpb));

@@ -61,11 +61,10 @@ __global__ void __launch_bounds__(kTopThreads) k_top(TopArgs a)
     const int n = a.n, s = a.s;
     const int tid = threadIdx.x;
     const float mu = a.mu ? (float)(*a.mu) : 1.0f;
-    const int per = (n + kTopThreads - 1) / kTopThreads;
-    const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
 
-    // keys of |x + mu g|
+    // keys of |x + mu g| (strided: coalesced global reads, conflict-free shared writes)
     int bad = 0;
+#pragma unroll 8
     for (int j = tid; j < n; j += kTopThreads) {
         const float x = a.x ? __ldcg(a.x + j) : 0.0f;
         const float v = fmaf(mu, __ldcg(a.g + j), x);
@@ -79,14 +78,15 @@ __global__ void __launch_bounds__(kTopThreads) k_top(TopArgs a)
         return;
     }
 
-    // radix select of the s-th largest key
+    // radix select of the s-th largest key (histograms over strided elements)
     uint32_t prefix = 0;
     int need = s;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         if (tid < 256) hist[tid] = 0;
         __syncthreads();
-        for (int j = j0; j < j1; ++j) {
+#pragma unroll 4
+        for (int j = tid; j < n; j += kTopThreads) {
             const uint32_t k = keys[j];
             if (pass == 0 || (k >> (shift + 8)) == (prefix >> (shift + 8))) atomicAdd(&hist[(k >> shift) & 255u], 1u);
         }
@@ -119,39 +119,93 @@ __global__ void __launch_bounds__(kTopThreads) k_top(TopArgs a)
     }
     const uint32_t T = prefix;    // s-th largest key; take `need` of the keys equal to T
 
-    // ordered compaction
+    // ordered compaction: warp w owns the contiguous segment [w*seg, (w+1)*seg) and walks it
+    // 32 keys at a time (lane = key), so shared reads are conflict-free and order is kept
+    const int lane = tid & 31, warp = tid >> 5;
+    const int seg = ((n + 32 * 32 - 1) / (32 * 32)) * 32;
+    const int wb = min(n, warp * seg), we = min(n, wb + seg);
+    const unsigned lt_mask = (1u << lane) - 1u;
     int gt = 0, eq = 0;
-    for (int j = j0; j < j1; ++j) { const uint32_t k = keys[j]; gt += (k > T); eq += (k == T); }
-    int eq_total;
-    const int eq_before = block_excl_scan(eq, scan_sh, &eq_total);
-    const int take_eq = max(0, min(eq, need - eq_before));
-    int sel_total;
-    int pos = block_excl_scan(gt + take_eq, scan_sh, &sel_total);
-    int taken = 0;
-    for (int j = j0; j < j1; ++j) {
-        const uint32_t k = keys[j];
-        const bool take = (k > T) || (k == T && taken < take_eq);
-        if (k == T && take) ++taken;
-        if (take) {
-            a.sel[pos] = j;
-            if (a.val) {
-                const float x = a.x ? __ldcg(a.x + j) : 0.0f;
-                a.val[pos] = fmaf(mu, __ldcg(a.g + j), x);
+    unsigned below = 0;
+    for (int b = wb; b < we; b += 32) {
+        const int j = b + lane;
+        const uint32_t k = (j < we) ? keys[j] : 0u;
+        const bool in = j < we;
+        gt += __popc(__ballot_sync(0xffffffffu, in && k > T));
+        eq += __popc(__ballot_sync(0xffffffffu, in && k == T));
+        if (in && k < T) below = max(below, k);
+    }
+    int eq_before_w = 0, eq_total = 0, pos_w = 0;
+    {
+        // scans over the 32 warp totals (warp order = index order)
+        if (lane == 0) { scan_sh[warp] = eq; }
+        __syncthreads();
+        if (warp == 0) {
+            const int v = scan_sh[lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            ++pos;
+            scan_sh[lane] = incl - v;
+            if (lane == 31) scan_sh[32] = incl;
+        }
+        __syncthreads();
+        eq_before_w = scan_sh[warp];
+        eq_total = scan_sh[32];
+        __syncthreads();
+    }
+    const int take_eq_w = max(0, min(eq, need - eq_before_w));
+    {
+        if (lane == 0) scan_sh[warp] = gt + take_eq_w;
+        __syncthreads();
+        if (warp == 0) {
+            const int v = scan_sh[lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            scan_sh[lane] = incl - v;
+            if (lane == 31) scan_sh[32] = incl;
+        }
+        __syncthreads();
+        pos_w = scan_sh[warp];
+        __syncthreads();
+    }
+    {
+        int pos = pos_w, erun = 0;
+        for (int b = wb; b < we; b += 32) {
+            const int j = b + lane;
+            const bool in = j < we;
+            const uint32_t k = in ? keys[j] : 0u;
+            const unsigned meq = __ballot_sync(0xffffffffu, in && k == T);
+            const int rank = erun + __popc(meq & lt_mask);
+            const bool take = in && (k > T || (k == T && rank < take_eq_w));
+            const unsigned mt = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                const int p = pos + __popc(mt & lt_mask);
+                a.sel[p] = j;
+                if (a.val) {
+                    const float x = a.x ? __ldcg(a.x + j) : 0.0f;
+                    a.val[p] = fmaf(mu, __ldcg(a.g + j), x);
+                }
+            }
+            pos += __popc(mt);
+            erun += __popc(meq);
         }
     }
     // (s+1)-th largest key: T again if more keys equal T than were taken, else the largest key below T
-    unsigned below = 0;
-    for (int j = j0; j < j1; ++j) { const uint32_t k = keys[j]; if (k < T) below = max(below, k); }
     below = __reduce_max_sync(0xffffffffu, below);
-    if ((tid & 31) == 0) red_u[tid >> 5] = below;
+    if (lane == 0) red_u[warp] = below;
     __syncthreads();
     float kth0 = __uint_as_float(T), kth1 = 0.0f;
     if (tid == 0) {
-        unsigned b = 0;
-        for (int w = 0; w < kTopThreads / 32; ++w) b = max(b, red_u[w]);
-        kth1 = (eq_total > need) ? __uint_as_float(T) : (s < n ? __uint_as_float(b) : 0.0f);
+        unsigned bm = 0;
+        for (int w = 0; w < kTopThreads / 32; ++w) bm = max(bm, red_u[w]);
+        kth1 = (eq_total > need) ? __uint_as_float(T) : (s < n ? __uint_as_float(bm) : 0.0f);
         if (a.kth) { a.kth[0] = kth0; a.kth[1] = kth1; }
         if (st) { st->kth0 = kth0; st->kth1 = kth1; }
     }
