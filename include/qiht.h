@@ -142,11 +142,15 @@ qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float
 /* The solver (Algorithm 2)                                                 */
 /* ---------------------------------------------------------------------- */
 
+#define QIHT_SOLVE_EAGER 1  /* launch the kernels one by one from the host (no graph; synchronises the
+                              stream every iteration). Same kernels and results as the graph;
+                              meant for debugging and per-kernel profiling. */
+
 typedef struct {
     double k;               /* shrinkage of the step size, k > 1/(1-c) (Section II-A); default 2 */
     double c;               /* small constant of the descent test, 0 < c < 1; default 0.01 */
     int32_t max_backtrack;  /* shrinks allowed per iteration before QIHT_ERR_BACKTRACK_CAP; default 32 */
-    int32_t reserved;       /* must be 0 */
+    int32_t flags;          /* 0 or QIHT_SOLVE_EAGER */
 } qiht_params;
 
 typedef struct {            /* written on the device after every iteration */

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqiht.so")
 OK, ERR_ARG, ERR_BITS, ERR_NONFINITE, ERR_TIMEOUT, ERR_BACKTRACK_CAP, ERR_CUDA, ERR_WORKSPACE = range(8)
 SCALE_GIVEN = 1
 CHECK_FINITE = 2
+SOLVE_EAGER = 1
 
 # stream ids of the random numbers, by convention of the solver
 STREAM_Q1, STREAM_Q2, STREAM_Y = 0, 1, 2
@@ -41,7 +42,7 @@ class _Codes(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_double), ("c", ctypes.c_double), ("max_backtrack", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 class _Report(ctypes.Structure):
@@ -249,9 +250,9 @@ class Solver:
     cached CUDA graph is reused on every call."""
 
     def __init__(self, m: int, n: int, s: int, iters: int, *, device="cuda", trace: bool = False,
-                 k: float = 2.0, c: float = 0.01, max_backtrack: int = 32):
+                 k: float = 2.0, c: float = 0.01, max_backtrack: int = 32, eager: bool = False):
         self.m, self.n, self.s, self.iters = m, n, s, iters
-        self.params = _Params(k, c, max_backtrack, 0)
+        self.params = _Params(k, c, max_backtrack, SOLVE_EAGER if eager else 0)
         self.x = torch.empty(n, dtype=torch.float32, device=device)
         self.support = torch.empty(s, dtype=torch.int32, device=device)
         self.report = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=device)

@@ -82,13 +82,13 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     if (st) {
         if (st->stop) {
             if (first && threadIdx.x == 0) {
-                if (a.mode == kGatherOmega) set_cond(a.h_bt, 0);
+                if (a.mode == kGatherOmega) { st->again = 0; set_cond(a.h_bt, 0); }
                 if (a.mode == kGatherResid) write_report(a, st);
             }
             return;
         }
         if (a.mode == kGatherOmega && !st->changed) {
-            if (first && threadIdx.x == 0) set_cond(a.h_bt, 0);
+            if (first && threadIdx.x == 0) { st->again = 0; set_cond(a.h_bt, 0); }
             return;
         }
     }
@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
                     }
                 }
             }
+            st->again = (int)again;
             set_cond(a.h_bt, again);
         }
     } else {  // Resid: commit the accepted proposal

@@ -310,8 +310,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
     const int NS = nstage_buf;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)NS * stage_bytes);
     uint64_t* empty = full + NS;
-    long long* red = reinterpret_cast<long long*>(empty + NS);          // [2][warps][CPSL*3]
-    long long* red_r = red + 2 * kTmaWarps * CPSL * 3;                  // [warps]
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(empty + NS);   // [NS][cps][3]
+    unsigned* cnt = reinterpret_cast<unsigned*>(acc + (size_t)NS * cps * 3);       // [NS][cps]
+    long long* red_r = reinterpret_cast<long long*>(cnt + (((size_t)NS * cps + 1) & ~(size_t)1));  // [warps]
+    __shared__ int s_abort;
 
     const int c0 = (int)((long long)n * blockIdx.x / gridDim.x);
     const int c1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
@@ -319,7 +321,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
     const int nst = (ncols + cps - 1) / cps;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    for (int i = threadIdx.x; i < NS * cps * 3; i += blockDim.x) acc[i] = 0ull;
+    for (int i = threadIdx.x; i < NS * cps; i += blockDim.x) cnt[i] = 0u;
     if (threadIdx.x == 0) {
+        s_abort = 0;
         for (int i = 0; i < NS; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kTmaWarps);
@@ -336,6 +341,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
             for (int it = 0; it < nst; ++it) {
                 const int sb = it % NS;
                 const unsigned ph = (unsigned)(it / NS) & 1u;
+                if (*(volatile int*)&s_abort) { ok = false; break; }
                 if (it >= NS && !mbar_wait(&empty[sb], ph ^ 1u)) { ok = false; break; }
                 const int cols_here = min(cps, ncols - it * cps);
                 const unsigned bytes = (unsigned)cols_here * colbytes;
@@ -358,6 +364,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
     // consumers: fixed-point residual limbs of this thread's pieces
     const int slot = threadIdx.x / tpc;
     const int t = threadIdx.x % tpc;
+    const int wps = tpc >> 5;                    // warps per slot
+    (void)wps;
     const int sh = fixed_shift(*a.rmax_bits);
     uint32_t l0[NLW], l1[NLW], l2[NLW];
     long long rsum = 0;
@@ -390,22 +398,23 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
     }
     consumer_sync();
     long long R = 0;
-    for (int w = 0; w < tpc / 32; ++w) R += red_r[w];
+    for (int w = 0; w < wps; ++w) R += red_r[w];
     const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
     const double outscale = ldexp(alpha, -sh);
-    const int wps = tpc >> 5;
 
-    __shared__ int s_abort;
-    if (threadIdx.x == 0) s_abort = 0;
-    consumer_sync();
+    // Steady state: no CTA-wide barrier. Each warp adds its per-column integer sums
+    // to shared accumulators with 64-bit atomics (exact, so order does not matter);
+    // the last warp of the slot to arrive at a column finishes it and clears the
+    // accumulator. A warp releases a stage only after that, so the producer cannot
+    // refill a stage (and no warp can reuse its accumulators) before it is finished.
     for (int it = 0; it < nst; ++it) {
         const int sb = it % NS;
         const unsigned ph = (unsigned)(it / NS) & 1u;
         if (!mbar_wait(&full[sb], ph)) {
-            // keep going to the barrier below so that every consumer leaves together
-            s_abort = 1;
-            report_timeout(a);
+            if (lane == 0) { s_abort = 1; report_timeout(a); }
+            break;
         }
+        if (*(volatile int*)&s_abort) break;
         const int cols_here = min(cps, ncols - it * cps);
         const unsigned char* stage = smem + (size_t)sb * stage_bytes;
         uint32_t a0[CPSL], a1[CPSL];
@@ -436,44 +445,39 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
                 }
             }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[sb]);     // this warp is done with the stage
-        long long* rb = red + (size_t)(it & 1) * kTmaWarps * CPSL * 3;
+        unsigned long long v0 = 0, v1 = 0, v2 = 0;
 #pragma unroll
         for (int cl = 0; cl < CPSL; ++cl) {
             const uint32_t s0 = __reduce_add_sync(0xffffffffu, a0[cl]);
             const uint32_t s1 = __reduce_add_sync(0xffffffffu, a1[cl]);
             const int32_t s2 = __reduce_add_sync(0xffffffffu, a2[cl]);
-            if (lane == 0) {
-                rb[(warp * CPSL + cl) * 3 + 0] = (long long)s0;
-                rb[(warp * CPSL + cl) * 3 + 1] = (long long)s1;
-                rb[(warp * CPSL + cl) * 3 + 2] = (long long)s2;
-            }
+            if (lane == cl) { v0 = s0; v1 = s1; v2 = (unsigned long long)(long long)s2; }
         }
-        consumer_sync();
-        if (*(volatile int*)&s_abort) {
-            // drain the copies this CTA may still have in flight (bounded), then leave
-            if (threadIdx.x == 0)
-                for (int j = it; j < min(nst, it + NS); ++j) mbar_wait(&full[j % NS], (unsigned)(j / NS) & 1u);
-            break;
-        }
-        if (t < CPSL) {
-            const int cl = t;
-            const int col = slot * CPSL + cl;
+        if (lane < CPSL) {
+            const int col = slot * CPSL + lane;
             if (col < cols_here) {
-                long long S0 = 0, S1 = 0, S2 = 0;
-                for (int w = slot * wps; w < (slot + 1) * wps; ++w) {
-                    S0 += rb[(w * CPSL + cl) * 3 + 0];
-                    S1 += rb[(w * CPSL + cl) * 3 + 1];
-                    S2 += rb[(w * CPSL + cl) * 3 + 2];
+                unsigned long long* ac = acc + ((size_t)sb * cps + col) * 3;
+                atomicAdd(ac + 0, v0);
+                atomicAdd(ac + 1, v1);
+                atomicAdd(ac + 2, v2);
+                __threadfence_block();
+                const unsigned prev = atomicAdd(&cnt[sb * cps + col], 1u);
+                if (prev == (unsigned)wps - 1) {
+                    __threadfence_block();
+                    volatile unsigned long long* vac = ac;
+                    const long long S0 = (long long)vac[0], S1 = (long long)vac[1], S2 = (long long)vac[2];
+                    const long long S = S0 + (S1 << 8) + (S2 << 16);
+                    const long long T = 2 * S - (long long)(L - 1) * R;
+                    a.g[c0 + it * cps + col] = (float)((double)T * outscale);
+                    vac[0] = 0ull; vac[1] = 0ull; vac[2] = 0ull;
+                    cnt[sb * cps + col] = 0u;
                 }
-                const long long S = S0 + (S1 << 8) + (S2 << 16);
-                const long long T = 2 * S - (long long)(L - 1) * R;
-                a.g[c0 + it * cps + col] = (float)((double)T * outscale);
             }
         }
-        // the double-buffered partials make a second barrier unnecessary
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sb]);     // this warp is done with the stage
     }
+    // on an abort the producer stops issuing and drains its own copies before the CTA ends
 }
 
 struct TmaPlan {
@@ -514,7 +518,9 @@ static TmaPlan plan_tma(const Codes& Q, int nsm)
     p.fn = fn;
     p.tpc = tpc;
     p.ns = ns;
-    p.smem = (size_t)ns * stage + 2 * (size_t)ns * 8 + 2 * (size_t)kTmaWarps * cpsl * 3 * 8 + kTmaWarps * 8;
+    const size_t cps = (size_t)cpsl * slots;
+    p.smem = (size_t)ns * stage + 2 * (size_t)ns * 8 + (size_t)ns * cps * 3 * 8 + ((((size_t)ns * cps + 1) & ~(size_t)1) * 4) +
+             kTmaWarps * 8;
     int grid = nsm;
     if (grid > Q.cols) grid = Q.cols;
     p.grid = (unsigned)grid;

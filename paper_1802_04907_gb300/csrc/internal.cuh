@@ -41,6 +41,7 @@ struct State {
     float kth0, kth1;      // s-th and (s+1)-th |x + mu g| of the current proposal
     int iters;             // requested iterations
     int outer_guard;       // executions of the outer loop body (bounds the loop)
+    int again;             // 1 if the last backtracking test asked for another shrink
     unsigned counters[3][32];  // arrival counters of the three column-subset products
 };
 

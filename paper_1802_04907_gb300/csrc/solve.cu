@@ -392,13 +392,33 @@ qiht_status add_while(cudaGraph_t g, cudaGraphNode_t* out, const cudaGraphNode_t
         if (_e != QIHT_OK) return _e;   \
     } while (0)
 
-qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s, int iters,
-                        const qiht_params* prm, float* x, int32_t* support, qiht_report* report,
-                        const qiht_trace* trace, char* ws, cudaGraph_t* out)
+// The solver's kernels and their arguments, shared by the graph driver and the eager driver.
+struct SolveKernels {
+    InitKernelArgs ia;
+    GemvTArgs g0, gb;
+    int tpc0, ns0, tpcb, nsb;
+    TopArgs t0, tt;
+    GatherArgs gmu, gom, gre;
+    void* a_init[1];
+    void* a_g0[3];
+    void* a_gb[3];
+    void* a_t0[1];
+    void* a_tt[1];
+    void* a_mu[1];
+    void* a_om[1];
+    void* a_re[1];
+    cudaKernelNodeParams p_init, p_g0, p_gb, p_t0, p_tt, p_mu, p_om, p_re;
+    State* st;
+};
+
+static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s,
+                         int iters, const qiht_params* prm, float* x, int32_t* support, qiht_report* report,
+                         const qiht_trace* trace, char* ws, unsigned long long h_outer, unsigned long long h_bt)
 {
     const int m = Q1->rows, n = Q1->cols;
     const Plan pl = plan_solve(m, n, s);
     State* st = reinterpret_cast<State*>(ws + pl.off_state);
+    K.st = st;
     float* yhat = reinterpret_cast<float*>(ws + pl.off_yhat);
     float* r = reinterpret_cast<float*>(ws + pl.off_r);
     float* g = reinterpret_cast<float*>(ws + pl.off_g);
@@ -413,75 +433,71 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     if (trace) tr = *trace;
     const int nsm = num_sms();
 
-    cudaGraph_t top;
-    CK(cudaGraphCreate(&top, 0));
-    cudaGraphConditionalHandle h_outer;
-    CK(cudaGraphConditionalHandleCreate(&h_outer, top, 1, cudaGraphCondAssignDefault));
+    K.ia = InitKernelArgs{};
+    K.ia.a.Y = view(Y);
+    K.ia.a.scale_q1 = Q1->scale;
+    K.ia.a.scale_q2 = Q2->scale;
+    K.ia.a.yhat = yhat;
+    K.ia.a.r = r;
+    K.ia.a.x = x;
+    K.ia.a.n = n;
+    K.ia.a.m = m;
+    K.ia.a.s = s;
+    K.ia.a.iters = iters;
+    K.ia.a.st = st;
+    K.ia.a.report = report;
+    K.ia.a.trace = tr;
+    K.ia.h_outer = h_outer;
+    K.a_init[0] = &K.ia;
+    K.p_init = cudaKernelNodeParams{};
+    K.p_init.func = (void*)k_init;
+    K.p_init.gridDim = dim3(1);
+    K.p_init.blockDim = dim3(1024);
+    K.p_init.kernelParams = K.a_init;
 
-    // --- init ---
-    InitKernelArgs ia{};
-    ia.a.Y = view(Y);
-    ia.a.scale_q1 = Q1->scale;
-    ia.a.scale_q2 = Q2->scale;
-    ia.a.yhat = yhat;
-    ia.a.r = r;
-    ia.a.x = x;
-    ia.a.n = n;
-    ia.a.m = m;
-    ia.a.s = s;
-    ia.a.iters = iters;
-    ia.a.st = st;
-    ia.a.report = report;
-    ia.a.trace = tr;
-    ia.h_outer = (unsigned long long)h_outer;
-    cudaKernelNodeParams kp{};
-    void* init_args[1] = {&ia};
-    kp.func = (void*)k_init;
-    kp.gridDim = dim3(1);
-    kp.blockDim = dim3(1024);
-    kp.kernelParams = init_args;
-    cudaGraphNode_t n_init;
-    TRY(add_kernel(top, &n_init, nullptr, 0, kp));
+    K.g0 = GemvTArgs{};
+    K.g0.Q = view(Q1);
+    K.g0.r = r;
+    K.g0.rmax_bits = &st->rmax_bits;
+    K.g0.g = g;
+    K.g0.st = st;
+    K.g0.h_outer = 0;               // the set-up product does not steer the loop
+    K.a_g0[0] = &K.g0; K.a_g0[1] = &K.tpc0; K.a_g0[2] = &K.ns0;
+    gemv_t_node(K.g0, nsm, &K.p_g0, K.a_g0);
+    K.gb = K.g0;
+    K.gb.h_outer = h_outer;         // the loop body's product decides whether to go on
+    K.a_gb[0] = &K.gb; K.a_gb[1] = &K.tpcb; K.a_gb[2] = &K.nsb;
+    gemv_t_node(K.gb, nsm, &K.p_gb, K.a_gb);
 
-    GemvTArgs ga{};
-    ga.Q = view(Q1);
-    ga.r = r;
-    ga.rmax_bits = &st->rmax_bits;
-    ga.g = g;
-    ga.st = st;
-    ga.h_outer = 0;                 // the set-up product does not steer the loop
-    int tpc = 0, nstg = 0;
-    void* gemv_args[3] = {&ga, &tpc, &nstg};
-    cudaKernelNodeParams gp{};
-    gemv_t_node(ga, nsm, &gp, gemv_args);
-    cudaGraphNode_t n_g0;
-    TRY(add_kernel(top, &n_g0, &n_init, 1, gp));
+    K.t0 = TopArgs{};
+    K.t0.g = g;
+    K.t0.n = n;
+    K.t0.s = s;
+    K.t0.sel = sel;
+    K.t0.val = val;
+    K.t0.st = st;
+    K.t0.init = 1;
+    K.t0.support_init = support;
+    K.t0.trace = tr;
+    K.a_t0[0] = &K.t0;
+    top_node(K.t0, &K.p_t0, K.a_t0);
 
-    TopArgs t0{};
-    t0.g = g;
-    t0.x = nullptr;
-    t0.mu = nullptr;
-    t0.n = n;
-    t0.s = s;
-    t0.sel = sel;
-    t0.val = val;
-    t0.kth = nullptr;
-    t0.st = st;
-    t0.init = 1;
-    t0.support_init = support;
-    t0.trace = tr;
-    void* t0_args[1] = {&t0};
-    cudaKernelNodeParams tp0{};
-    top_node(t0, &tp0, t0_args);
-    cudaGraphNode_t n_t0;
-    TRY(add_kernel(top, &n_t0, &n_g0, 1, tp0));
-
-    // --- outer loop ---
-    cudaGraphNode_t n_w;
-    cudaGraph_t body;
-    TRY(add_while(top, &n_w, &n_t0, 1, h_outer, &body));
-    cudaGraphConditionalHandle h_bt;
-    CK(cudaGraphConditionalHandleCreate(&h_bt, body, 0, 0));
+    K.tt = TopArgs{};
+    K.tt.g = g;
+    K.tt.x = x;
+    K.tt.mu = &st->mu;
+    K.tt.n = n;
+    K.tt.s = s;
+    K.tt.sel = sel;
+    K.tt.val = val;
+    K.tt.st = st;
+    K.tt.support = support;
+    K.tt.uni = uni;
+    K.tt.delta = delta;
+    K.tt.trace = tr;
+    K.tt.h_bt = h_bt;
+    K.a_tt[0] = &K.tt;
+    top_node(K.tt, &K.p_tt, K.a_tt);
 
     GatherArgs base{};
     base.Q = view(Q2);
@@ -501,71 +517,106 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     base.k = prm->k;
     base.c = prm->c;
     base.max_bt = prm->max_backtrack;
-    base.h_outer = (unsigned long long)h_outer;
-    base.h_bt = (unsigned long long)h_bt;
+    base.h_outer = h_outer;
+    base.h_bt = h_bt;
     base.report = report;
     base.trace = tr;
+    K.gmu = base;
+    K.gmu.mode = kGatherMu;
+    K.gmu.counters = st->counters[0];
+    K.a_mu[0] = &K.gmu;
+    gather_node(K.gmu, &K.p_mu, K.a_mu);
+    K.gom = base;
+    K.gom.mode = kGatherOmega;
+    K.gom.cols = uni;
+    K.gom.coef = delta;
+    K.gom.counters = st->counters[1];
+    K.a_om[0] = &K.gom;
+    gather_node(K.gom, &K.p_om, K.a_om);
+    K.gre = base;
+    K.gre.mode = kGatherResid;
+    K.gre.counters = st->counters[2];
+    K.a_re[0] = &K.gre;
+    gather_node(K.gre, &K.p_re, K.a_re);
+}
 
-    GatherArgs gmu = base;
-    gmu.mode = kGatherMu;
-    gmu.counters = st->counters[0];
-    void* mu_args[1] = {&gmu};
-    cudaKernelNodeParams pmu{};
-    gather_node(gmu, &pmu, mu_args);
+static cudaError_t launch_node(const cudaKernelNodeParams& p, cudaStream_t s)
+{
+    return cudaLaunchKernel(p.func, p.gridDim, p.blockDim, p.kernelParams, p.sharedMemBytes, s);
+}
 
-    TopArgs tt{};
-    tt.g = g;
-    tt.x = x;
-    tt.mu = &st->mu;
-    tt.n = n;
-    tt.s = s;
-    tt.sel = sel;
-    tt.val = val;
-    tt.kth = nullptr;
-    tt.st = st;
-    tt.support = support;
-    tt.uni = uni;
-    tt.delta = delta;
-    tt.init = 0;
-    tt.trace = tr;
-    tt.h_bt = (unsigned long long)h_bt;
-    void* tt_args[1] = {&tt};
-    cudaKernelNodeParams ptt{};
-    top_node(tt, &ptt, tt_args);
+// Host-driven run of the same kernels (QIHT_SOLVE_EAGER): reads the device state
+// after every iteration and after every backtracking test.
+qiht_status run_eager(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s, int iters,
+                      const qiht_params* prm, float* x, int32_t* support, qiht_report* report,
+                      const qiht_trace* trace, char* ws, cudaStream_t cs)
+{
+    SolveKernels K;
+    make_kernels(K, Q1, Q2, Y, s, iters, prm, x, support, report, trace, ws, 0, 0);
+    State h{};
+    auto read_state = [&]() -> bool {
+        if (cudaMemcpyAsync(&h, K.st, sizeof(State), cudaMemcpyDeviceToHost, cs) != cudaSuccess) return false;
+        return cudaStreamSynchronize(cs) == cudaSuccess;
+    };
+    CK(launch_node(K.p_init, cs));
+    CK(launch_node(K.p_g0, cs));
+    CK(launch_node(K.p_t0, cs));
+    if (!read_state()) return QIHT_ERR_CUDA;
+    for (int t = 0; t < iters && !h.stop; ++t) {
+        CK(launch_node(K.p_mu, cs));
+        CK(launch_node(K.p_tt, cs));
+        CK(launch_node(K.p_om, cs));
+        if (!read_state()) return QIHT_ERR_CUDA;
+        for (int b = 0; b <= prm->max_backtrack && h.again && !h.stop; ++b) {
+            CK(launch_node(K.p_tt, cs));
+            CK(launch_node(K.p_om, cs));
+            if (!read_state()) return QIHT_ERR_CUDA;
+        }
+        CK(launch_node(K.p_re, cs));
+        CK(launch_node(K.p_gb, cs));
+        if (!read_state()) return QIHT_ERR_CUDA;
+    }
+    return QIHT_OK;
+}
 
-    GatherArgs gom = base;
-    gom.mode = kGatherOmega;
-    gom.cols = uni;
-    gom.coef = delta;
-    gom.counters = st->counters[1];
-    void* om_args[1] = {&gom};
-    cudaKernelNodeParams pom{};
-    gather_node(gom, &pom, om_args);
+qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s, int iters,
+                        const qiht_params* prm, float* x, int32_t* support, qiht_report* report,
+                        const qiht_trace* trace, char* ws, cudaGraph_t* out)
+{
+    cudaGraph_t top;
+    CK(cudaGraphCreate(&top, 0));
+    cudaGraphConditionalHandle h_outer;
+    CK(cudaGraphConditionalHandleCreate(&h_outer, top, 1, cudaGraphCondAssignDefault));
+    // the body graph (and its handle) exist only after the outer node is added; the
+    // kernel arguments need both handles, so add the set-up nodes first with
+    // provisional arguments and fill the loop afterwards
+    SolveKernels K0;
+    make_kernels(K0, Q1, Q2, Y, s, iters, prm, x, support, report, trace, ws, (unsigned long long)h_outer, 0);
+    cudaGraphNode_t n_init, n_g0, n_t0;
+    TRY(add_kernel(top, &n_init, nullptr, 0, K0.p_init));
+    TRY(add_kernel(top, &n_g0, &n_init, 1, K0.p_g0));
+    TRY(add_kernel(top, &n_t0, &n_g0, 1, K0.p_t0));
 
-    GatherArgs gre = base;
-    gre.mode = kGatherResid;
-    gre.counters = st->counters[2];
-    void* re_args[1] = {&gre};
-    cudaKernelNodeParams pre{};
-    gather_node(gre, &pre, re_args);
+    cudaGraphNode_t n_w;
+    cudaGraph_t body;
+    TRY(add_while(top, &n_w, &n_t0, 1, h_outer, &body));
+    cudaGraphConditionalHandle h_bt;
+    CK(cudaGraphConditionalHandleCreate(&h_bt, body, 0, 0));
+    SolveKernels K;
+    make_kernels(K, Q1, Q2, Y, s, iters, prm, x, support, report, trace, ws, (unsigned long long)h_outer,
+                 (unsigned long long)h_bt);
 
     cudaGraphNode_t b_mu, b_top, b_om, b_w, b_re, b_g;
-    TRY(add_kernel(body, &b_mu, nullptr, 0, pmu));
-    TRY(add_kernel(body, &b_top, &b_mu, 1, ptt));
-    TRY(add_kernel(body, &b_om, &b_top, 1, pom));
+    TRY(add_kernel(body, &b_mu, nullptr, 0, K.p_mu));
+    TRY(add_kernel(body, &b_top, &b_mu, 1, K.p_tt));
+    TRY(add_kernel(body, &b_om, &b_top, 1, K.p_om));
     cudaGraph_t inner;
     TRY(add_while(body, &b_w, &b_om, 1, h_bt, &inner));
     cudaGraphNode_t i_top, i_om;
-    TRY(add_kernel(inner, &i_top, nullptr, 0, ptt));
-    TRY(add_kernel(inner, &i_om, &i_top, 1, pom));
-    TRY(add_kernel(body, &b_re, &b_w, 1, pre));
-    GemvTArgs gb = ga;
-    gb.h_outer = (unsigned long long)h_outer;   // the loop body's product decides whether to go on
-    int tpcb = 0, nstgb = 0;
-    void* gemvb_args[3] = {&gb, &tpcb, &nstgb};
-    cudaKernelNodeParams gpb{};
-    gemv_t_node(gb, nsm, &gpb, gemvb_args);
-    TRY(add_kernel(body, &b_g, &b_re, 1, gpb));
+    TRY(add_kernel(inner, &i_top, nullptr, 0, K.p_tt));
+    TRY(add_kernel(inner, &i_om, &i_top, 1, K.p_om));
+    TRY(add_kernel(body, &b_re, &b_w, 1, K.p_re));
+    TRY(add_kernel(body, &b_g, &b_re, 1, K.p_gb));
     *out = top;
     return QIHT_OK;
 }
@@ -595,10 +646,15 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
     if (!x || !support || !report) return QIHT_ERR_ARG;
     qiht_params prm{2.0, 0.01, 32, 0};
     if (params) prm = *params;
-    if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.reserved != 0)
+    if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 ||
+        (prm.flags & ~QIHT_SOLVE_EAGER) != 0)
         return QIHT_ERR_ARG;
     if (!workspace || workspace_bytes < qiht_solve_workspace_size(m, n, s) || !aligned(workspace, 256))
         return QIHT_ERR_WORKSPACE;
+
+    if (prm.flags & QIHT_SOLVE_EAGER)
+        return run_eager(Q1, Q2, y, s, iters, &prm, x, support, report, trace, reinterpret_cast<char*>(workspace),
+                         reinterpret_cast<cudaStream_t>(stream));
 
     int dev = 0;
     CK(cudaGetDevice(&dev));

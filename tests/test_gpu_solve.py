@@ -186,3 +186,24 @@ def test_full_size_large_solve():
     # the residual reported is the one of the returned x
     r2 = sv.trace["resid2"].cpu().numpy()[: rep.iters_run + 1]
     assert abs(r2[-1] - rep.resid_norm2) <= 1e-12 * rep.resid_norm2
+
+
+def test_eager_driver_matches_graph():
+    # the host-driven launch sequence runs the same kernels as the graph: identical results
+    for seed in range(20):
+        p = synth.gaussian(300, 1200, 24, seed=500 + seed, values="ones", snr_db=8.0)
+        ref, _ = oracle.qiht(p.phi, p.y, p.s, 30, bits_phi=4, bits_y=8, seed=seed)
+        if ref.backtracks > 0:
+            break
+    phi = torch.from_numpy(p.phi).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    q1, q2, qy = q.quantize_problem(phi, y, 4, 8, seed)
+    a = q.Solver(p.m, p.n, p.s, 30, trace=True)
+    b = q.Solver(p.m, p.n, p.s, 30, trace=True, eager=True)
+    a(q1, q2, qy)
+    b(q1, q2, qy)
+    torch.cuda.synchronize()
+    assert torch.equal(a.x, b.x) and torch.equal(a.support, b.support)
+    assert a.read_report() == b.read_report()
+    for k in a.trace:
+        assert torch.equal(a.trace[k], b.trace[k]), k
