@@ -10,9 +10,10 @@ FP32 with FP64 scalars; the oracle is FP64. The rule:
     its threshold)
   - the step size agrees to 1e-4 relative in the first three iterations and in
     every iteration whose support changes (where mu decides the selection);
-    elsewhere g_G -> 0 as x converges, mu = ||g_G||^2 / ||Q2 g_G||^2 becomes a
+    elsewhere g_G -> 0 as x converges and mu = ||g_G||^2 / ||Q2 g_G||^2 becomes a
     ratio of vanishing quantities whose relative accuracy degrades like
-    (absolute error of g) / ||g_G||, and only a 1e-2 sanity bound is checked
+    (absolute error of g) / ||g_G||, so it is not compared (its effect, the
+    step mu g_G, vanishes with it and is covered by the comparison of x)
   - when no iteration was ambiguous, the final x agrees to 1e-4 relative L2
   - otherwise both recoveries are compared against the ground truth and the
     first ambiguous iteration is reported.
@@ -58,10 +59,8 @@ def _check(sv, ref, p, label=""):
     rsup = ref.trace["support"]
     for t in range(0, T + 1):
         assert np.array_equal(sup[t], rsup[t]), f"{label}: support differs at iteration {t}"
-        if t > 0:
-            decisive = t <= 3 or not np.array_equal(rsup[t], rsup[t - 1])
-            tol = 1e-4 if decisive else 1e-2
-            assert abs(mu[t] - ref.trace["mu"][t]) <= tol * ref.trace["mu"][t], f"{label}: mu at {t}"
+        if t > 0 and (t <= 3 or not np.array_equal(rsup[t], rsup[t - 1])):
+            assert abs(mu[t] - ref.trace["mu"][t]) <= 1e-4 * ref.trace["mu"][t], f"{label}: mu at {t}"
     x = sv.x.cpu().numpy().astype(np.float64)
     assert np.count_nonzero(x) <= p.s
     truth = np.linalg.norm(p.x_true)
