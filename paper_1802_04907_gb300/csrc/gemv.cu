@@ -480,6 +480,217 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
     // on an abort the producer stops issuing and drains its own copies before the CTA ends
 }
 
+// ---------------------------------------------------------------------------
+// Column-owning TMA variant (the default). A CTA owns a contiguous range of
+// columns and walks it in groups of 32 columns; each group is streamed in row
+// chunks of 32 * RC * b / 8 bytes (one cp.async.bulk per column chunk, issued
+// by the 32 lanes of the producer warp). Consumer warp w owns columns
+// 2w, 2w+1 of every group for the whole group, so its integer sums stay in
+// registers across the row chunks and no two warps ever share a column.
+// The fixed-point residual lives in shared memory as three byte planes in a
+// lane-interleaved layout ([E][piece][4 words]), read with conflict-free 16-byte
+// loads and reused for both columns of the warp.
+// ---------------------------------------------------------------------------
+constexpr int kColsPerGroup = 32;
+constexpr int kCpw = 2;                        // columns per consumer warp (16 warps x 2 = 32)
+constexpr int kChunkBytes = 1024;              // bytes of one column chunk (32 chunks = 32 KiB per stage)
+
+template <int BITS>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int nstage_buf)
+{
+    constexpr int G = 32 / BITS;
+    constexpr int E = G / 4;                   // 16-byte limb loads per limb per piece
+    constexpr int L = 1 << BITS;
+    constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
+    constexpr int PPC = kChunkBytes / 16;      // pieces per column chunk
+    constexpr int PPL = PPC / 32;              // pieces per lane per column chunk
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int guard = ++a.st->outer_guard;
+        cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
+                                (!a.st->stop && guard < a.st->iters + 1) ? 1u : 0u);
+    }
+    if (a.st && a.st->stop) return;
+
+    const int n = a.Q.cols, ld = a.Q.ld, m = a.Q.rows;
+    const int P = ld / 4;                              // 16-byte pieces per column
+    const unsigned colbytes = (unsigned)ld * 4u;
+    const int nchunk = (int)((colbytes + kChunkBytes - 1) / kChunkBytes);
+    const int NS = nstage_buf;
+    const unsigned stage_bytes = (unsigned)kColsPerGroup * kChunkBytes;
+    uint32_t* limb = reinterpret_cast<uint32_t*>(smem + (size_t)NS * stage_bytes);   // [3][E][P][4]
+    uint64_t* full = reinterpret_cast<uint64_t*>(limb + (size_t)3 * E * P * 4);
+    uint64_t* empty = full + NS;
+    long long* red_r = reinterpret_cast<long long*>(empty + NS);
+    __shared__ int s_abort;
+
+    const int c0 = (int)((long long)n * blockIdx.x / gridDim.x);
+    const int c1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
+    const int ncols = c1 - c0;
+    const int ngroups = (ncols + kColsPerGroup - 1) / kColsPerGroup;
+    const int nst = ngroups * nchunk;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kTmaWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kTmaWarps) {
+        // producer warp: stage it = (group it / nchunk, chunk it % nchunk)
+        int issued = 0;
+        bool ok = true;
+        for (int it = 0; it < nst; ++it) {
+            const int sb = it % NS;
+            const unsigned ph = (unsigned)(it / NS) & 1u;
+            const int grp = it / nchunk, ch = it - grp * nchunk;
+            const int gc0 = c0 + grp * kColsPerGroup;
+            const int gcols = min(kColsPerGroup, c1 - gc0);
+            const unsigned off = (unsigned)ch * kChunkBytes;
+            const unsigned cb = min((unsigned)kChunkBytes, colbytes - off);
+            int stop = 0;
+            if (lane == 0) {
+                if (*(volatile int*)&s_abort) stop = 1;
+                else if (it >= NS && !mbar_wait(&empty[sb], ph ^ 1u)) stop = 1;
+                else mbar_expect_tx(&full[sb], (unsigned)gcols * cb);
+            }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (stop) { ok = false; break; }
+            if (lane < gcols)
+                bulk_g2s(smem + (size_t)sb * stage_bytes + (size_t)lane * kChunkBytes,
+                         reinterpret_cast<const unsigned char*>(a.Q.words) + (size_t)(gc0 + lane) * colbytes + off,
+                         cb, &full[sb]);
+            ++issued;
+        }
+        if (!ok && lane == 0) {
+            report_timeout(a);
+            for (int it = max(0, issued - NS); it < issued; ++it)
+                mbar_wait(&full[it % NS], (unsigned)(it / NS) & 1u);
+        }
+        return;
+    }
+
+    // consumers: residual -> fixed point byte planes in shared memory
+    const int sh = fixed_shift(*a.rmax_bits);
+    long long rsum = 0;
+    for (int lw = threadIdx.x; lw < P * G; lw += kTmaConsumers) {      // limb word lw covers rows 4lw..4lw+3
+        uint32_t b0 = 0, b1 = 0, b2 = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int i = 4 * lw + p;
+            int v = 0;
+            if (i < m) v = __float2int_rn(ldexpf(__ldcg(a.r + i), sh));
+            rsum += v;
+            b0 |= (uint32_t)(v & 255) << (8 * p);
+            b1 |= (uint32_t)((v >> 8) & 255) << (8 * p);
+            b2 |= (uint32_t)((v >> 16) & 255) << (8 * p);
+        }
+        // limb word lw = piece * G + q*4 + w  ->  index ((q * P + piece) * 4 + w)
+        const int piece = lw / G, rem = lw - piece * G, q = rem >> 2, w = rem & 3;
+        const size_t idx = ((size_t)q * P + piece) * 4 + w;
+        limb[idx] = b0;
+        limb[(size_t)E * P * 4 + idx] = b1;
+        limb[(size_t)2 * E * P * 4 + idx] = b2;
+    }
+    {
+        long long v = rsum;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red_r[warp] = v;
+    }
+    consumer_sync();
+    long long R = 0;
+    for (int w = 0; w < kTmaWarps; ++w) R += red_r[w];
+    const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
+    const double outscale = ldexp(alpha, -sh);
+    const uint4* L0 = reinterpret_cast<const uint4*>(limb);
+    const uint4* L1 = L0 + (size_t)E * P;
+    const uint4* L2 = L0 + (size_t)2 * E * P;
+
+    uint32_t a0[kCpw], a1[kCpw];
+    int32_t a2[kCpw];
+    for (int it = 0; it < nst; ++it) {
+        const int sb = it % NS;
+        const unsigned ph = (unsigned)(it / NS) & 1u;
+        const int grp = it / nchunk, ch = it - grp * nchunk;
+        const int gc0 = c0 + grp * kColsPerGroup;
+        const int gcols = min(kColsPerGroup, c1 - gc0);
+        if (ch == 0) {
+#pragma unroll
+            for (int c = 0; c < kCpw; ++c) { a0[c] = 0; a1[c] = 0; a2[c] = 0; }
+        }
+        if (!mbar_wait(&full[sb], ph)) {
+            if (lane == 0) { s_abort = 1; report_timeout(a); }
+            break;
+        }
+        if (*(volatile int*)&s_abort) break;
+        const unsigned char* stage = smem + (size_t)sb * stage_bytes;
+        const int pbase = ch * PPC;                    // first piece of this chunk in the column
+#pragma unroll
+        for (int pl = 0; pl < PPL; ++pl) {
+            const int pc = lane + 32 * pl;             // piece within the chunk
+            const int piece = pbase + pc;
+            if (piece < P) {
+                uint4 l0v[E], l1v[E], l2v[E];
+#pragma unroll
+                for (int q = 0; q < E; ++q) {
+                    l0v[q] = L0[(size_t)q * P + piece];
+                    l1v[q] = L1[(size_t)q * P + piece];
+                    l2v[q] = L2[(size_t)q * P + piece];
+                }
+#pragma unroll
+                for (int c = 0; c < kCpw; ++c) {
+                    const int col = warp * kCpw + c;
+                    if (col < gcols) {
+                        const uint4 v = reinterpret_cast<const uint4*>(stage + (size_t)col * kChunkBytes)[pc];
+                        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+#pragma unroll
+                            for (int k = 0; k < E; ++k) {
+                                const uint32_t x = (wv[w] >> (BITS * k)) & MASK;
+                                // limb word w*E + k of the piece -> plane q = (w*E+k)/4, word (w*E+k)%4
+                                const int lw = w * E + k;
+                                const uint4& A0 = l0v[lw >> 2];
+                                const uint4& A1 = l1v[lw >> 2];
+                                const uint4& A2 = l2v[lw >> 2];
+                                const int sel = lw & 3;
+                                const uint32_t y0 = sel == 0 ? A0.x : sel == 1 ? A0.y : sel == 2 ? A0.z : A0.w;
+                                const uint32_t y1 = sel == 0 ? A1.x : sel == 1 ? A1.y : sel == 2 ? A1.z : A1.w;
+                                const uint32_t y2 = sel == 0 ? A2.x : sel == 1 ? A2.y : sel == 2 ? A2.z : A2.w;
+                                a0[c] = dp4a_uu(x, y0, a0[c]);
+                                a1[c] = dp4a_uu(x, y1, a1[c]);
+                                a2[c] = dp4a_us(x, y2, a2[c]);
+                            }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sb]);
+        if (ch == nchunk - 1) {
+#pragma unroll
+            for (int c = 0; c < kCpw; ++c) {
+                const uint32_t s0 = __reduce_add_sync(0xffffffffu, a0[c]);
+                const uint32_t s1 = __reduce_add_sync(0xffffffffu, a1[c]);
+                const int32_t s2 = __reduce_add_sync(0xffffffffu, a2[c]);
+                const int col = warp * kCpw + c;
+                if (lane == c && col < gcols) {
+                    const long long S = (long long)s0 + ((long long)s1 << 8) + ((long long)s2 << 16);
+                    const long long T = 2 * S - (long long)(L - 1) * R;
+                    a.g[gc0 + col] = (float)((double)T * outscale);
+                }
+            }
+        }
+    }
+}
+
 struct TmaPlan {
     void* fn;
     int tpc;
@@ -529,15 +740,49 @@ static TmaPlan plan_tma(const Codes& Q, int nsm)
     return p;
 }
 
-static bool use_tma()
+struct ColPlan {
+    void* fn;
+    int ns;
+    size_t smem;
+    unsigned grid;
+    bool ok;
+};
+
+static ColPlan plan_col(const Codes& Q, int nsm)
 {
+    ColPlan p{};
+    const int G = 32 / Q.bits, E = G / 4;
+    const size_t P = (size_t)Q.ld / 4;
+    const size_t limb_bytes = 3 * (size_t)E * P * 16;
+    const size_t stage = (size_t)kColsPerGroup * kChunkBytes;
+    const size_t budget = 220 * 1024;
+    if (limb_bytes + 2 * stage + 1024 > budget) return p;
+    int ns = (int)((budget - limb_bytes - 1024) / stage);
+    if (ns > 6) ns = 6;
+    p.ns = ns;
+    p.smem = (size_t)ns * stage + limb_bytes + 2 * (size_t)ns * 8 + kTmaWarps * 8;
+    p.fn = Q.bits == 8 ? (void*)k_gemv_t_col<8> : Q.bits == 4 ? (void*)k_gemv_t_col<4> : (void*)k_gemv_t_col<2>;
+    int grid = nsm;
+    if (grid > Q.cols) grid = Q.cols;
+    p.grid = (unsigned)grid;
+    cudaFuncSetAttribute(p.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    p.ok = true;
+    return p;
+}
+
+static int gemv_variant()
+{
+    // QIHT_GEMV selects a kernel for measurement: "col" (default), "tma", "ldg"
     static int v = -1;
     if (v < 0) {
         const char* e = getenv("QIHT_GEMV");
-        v = (e && e[0] == 'l') ? 0 : 1;     // "ldg" selects the register-staged kernel
+        v = (e && e[0] == 'l') ? 0 : (e && e[0] == 't') ? 1 : 2;
     }
-    return v == 1;
+    return v;
 }
+
+static bool use_tma() { return gemv_variant() == 1; }
+static bool use_col() { return gemv_variant() == 2; }
 
 template <int BITS>
 static void pick(int rows_pad, int& rpt, int& tpc, void** fn)
@@ -602,6 +847,21 @@ static GemvPlan plan_gemv_t(const Codes& Q, int nsm)
 
 void gemv_t_node(const GemvTArgs& a, int nsm, cudaKernelNodeParams* p, void** argbuf)
 {
+    if (use_col()) {
+        ColPlan cp = plan_col(a.Q, nsm);
+        if (cp.ok) {
+            // kernel arguments: (GemvTArgs, int stages) -> argbuf[0], argbuf[2]
+            *reinterpret_cast<int*>(argbuf[2]) = cp.ns;
+            argbuf[1] = argbuf[2];
+            p->func = cp.fn;
+            p->gridDim = dim3(cp.grid);
+            p->blockDim = dim3(kTmaThreads);
+            p->sharedMemBytes = (unsigned)cp.smem;
+            p->kernelParams = argbuf;
+            p->extra = nullptr;
+            return;
+        }
+    }
     if (use_tma()) {
         TmaPlan tp = plan_tma(a.Q, nsm);
         if (tp.ok) {
@@ -630,6 +890,15 @@ void gemv_t_node(const GemvTArgs& a, int nsm, cudaKernelNodeParams* p, void** ar
 
 cudaError_t launch_gemv_t(const GemvTArgs& a, int nsm, cudaStream_t s)
 {
+    if (use_col()) {
+        ColPlan cp = plan_col(a.Q, nsm);
+        if (cp.ok) {
+            GemvTArgs copy = a;
+            int ns = cp.ns;
+            void* args[2] = {&copy, &ns};
+            return cudaLaunchKernel(cp.fn, dim3(cp.grid), dim3(kTmaThreads), args, cp.smem, s);
+        }
+    }
     if (use_tma()) {
         TmaPlan tp = plan_tma(a.Q, nsm);
         if (tp.ok) {

@@ -2,8 +2,8 @@
 // magnitude, ties broken by the lower index, exactly s entries.
 //
 // One CTA of 1024 threads. Keys are the float bits of |a| (monotone for
-// non-negative floats) held in shared memory. A 4-pass MSB-first radix select
-// (8-bit digits, shared-memory histograms) finds the s-th largest key T; an
+// non-negative floats) held in shared memory. A 3-pass MSB-first radix select
+// (11/11/10-bit digits, warp-aggregated shared histograms) finds the s-th largest key T; an
 // ordered compaction (two block scans) then emits every key > T plus the
 // lowest-index keys == T, in ascending index order. In the solver the same CTA
 // compares the new support G' with the current one and builds the list of
@@ -50,7 +50,7 @@ __device__ int block_excl_scan(int v, int* sh, int* total)
 __global__ void __launch_bounds__(kTopThreads) k_top(TopArgs a)
 {
     extern __shared__ uint32_t keys[];            // n keys, then n/32 bitmap words
-    __shared__ unsigned hist[256];
+    __shared__ unsigned hist[2048];
     __shared__ int scan_sh[33];
     __shared__ int sel_digit, sel_above;
     __shared__ unsigned red_u[32];
@@ -78,24 +78,36 @@ __global__ void __launch_bounds__(kTopThreads) k_top(TopArgs a)
         return;
     }
 
-    // radix select of the s-th largest key (histograms over strided elements)
+    // radix select of the s-th largest key: digits of 11, 11 and 10 bits (MSB first).
+    // Keys of similar magnitude share their top bits, so histogram updates are
+    // aggregated per warp (__match_any_sync): one shared atomic per distinct bin.
     uint32_t prefix = 0;
     int need = s;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        if (tid < 256) hist[tid] = 0;
+    for (int pass = 0; pass < 3; ++pass) {
+        const int shift = pass == 0 ? 21 : pass == 1 ? 10 : 0;
+        const int width = pass == 2 ? 10 : 11;
+        const uint32_t dmask = (1u << width) - 1u;
+        const int nbins = 1 << width;
+        for (int i = tid; i < nbins; i += kTopThreads) hist[i] = 0;
         __syncthreads();
+        const int hi = shift + width;             // bits above this digit must equal the prefix
 #pragma unroll 4
-        for (int j = tid; j < n; j += kTopThreads) {
-            const uint32_t k = keys[j];
-            if (pass == 0 || (k >> (shift + 8)) == (prefix >> (shift + 8))) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        for (int j0 = 0; j0 < n; j0 += kTopThreads) {
+            const int j = j0 + tid;
+            int bin = -1;
+            if (j < n) {
+                const uint32_t k = keys[j];
+                if (hi >= 32 || (k >> hi) == (prefix >> hi)) bin = (int)((k >> shift) & dmask);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (bin >= 0 && (__ffs(peers) - 1) == (tid & 31)) atomicAdd(&hist[bin], (unsigned)__popc(peers));
         }
         __syncthreads();
         if (tid < 32) {
-            // lane l holds digits 255-8l .. 248-8l (descending)
-            int c[8], tot = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { c[i] = (int)hist[255 - 8 * tid - i]; tot += c[i]; }
+            // lane l holds bins nbins-1-l*per .. (descending), per = nbins / 32
+            const int per = nbins >> 5;
+            int tot = 0;
+            for (int i = 0; i < per; ++i) tot += (int)hist[nbins - 1 - tid * per - i];
             int incl = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -105,10 +117,11 @@ __global__ void __launch_bounds__(kTopThreads) k_top(TopArgs a)
             const int excl = incl - tot;
             if (excl < need && need <= incl) {
                 int run = excl;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (run + c[i] >= need) { sel_digit = 255 - 8 * tid - i; sel_above = run; break; }
-                    run += c[i];
+                for (int i = 0; i < per; ++i) {
+                    const int bi = nbins - 1 - tid * per - i;
+                    const int c = (int)hist[bi];
+                    if (run + c >= need) { sel_digit = bi; sel_above = run; break; }
+                    run += c;
                 }
             }
         }
