@@ -228,27 +228,38 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     if (!flag) return;
     __threadfence();
 
-    // final scalars (one CTA)
-    double total = 0.0;
-    double mxd = 0.0;
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < nrb; ++b) {
-            total += __ldcg(a.rb_partial + 2 * b);
-            mxd = fmax(mxd, __ldcg(a.rb_partial + 2 * b + 1));
+    // final scalars (one CTA): the partials are read in parallel by warp 0 and summed with a
+    // fixed tree, so the result is deterministic
+    if (threadIdx.x < 32) {
+        double t = 0.0, mxl = 0.0, cs = 0.0;
+        for (int b = threadIdx.x; b < nrb; b += 32) {
+            t += __ldcg(a.rb_partial + 2 * b);
+            mxl = fmax(mxl, __ldcg(a.rb_partial + 2 * b + 1));
         }
-        a.counters[nrb] = 0;
-        shd[32] = total;
-        shd[31] = mxd;
+        if (a.chunk_partial && (a.mode == kGatherMu || a.mode == kGatherOmega))
+            for (int c = threadIdx.x; c < nchunks; c += 32) cs += __ldcg(a.chunk_partial + c);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            t += __shfl_xor_sync(0xffffffffu, t, o);
+            mxl = fmax(mxl, __shfl_xor_sync(0xffffffffu, mxl, o));
+            cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        }
+        if (threadIdx.x == 0) {
+            a.counters[nrb] = 0;
+            shd[32] = t;
+            shd[31] = mxl;
+            shd[30] = cs;
+        }
     }
     __syncthreads();
-    total = shd[32];
-    mxd = shd[31];
+    const double total = shd[32];
+    const double mxd = shd[31];
+    const double coef_norm2 = shd[30];
     const double alpha_d = (double)(*a.Q.scale) / (double)(L - 1);
 
     if (a.mode == kGatherMu) {
         if (threadIdx.x == 0) {
-            double num = 0.0;
-            for (int c = 0; c < nchunks; ++c) num += __ldcg(a.chunk_partial + c);
+            const double num = coef_norm2;
             const double den = alpha_d * alpha_d * total;
             st->num = num;
             st->bt = 0;
@@ -263,8 +274,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
         }
     } else if (a.mode == kGatherOmega) {
         if (threadIdx.x == 0) {
-            double dn = 0.0;
-            for (int c = 0; c < nchunks; ++c) dn += __ldcg(a.chunk_partial + c);
+            const double dn = coef_norm2;
             const double dd = alpha_d * alpha_d * total;
             unsigned again = 0;
             if (dn > 0.0) {

@@ -691,6 +691,160 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-column variant (the default). Many warps per SM (4 CTAs x 8 warps),
+// each warp owns whole columns (static round-robin over the columns), so its
+// integer sums never leave the warp. A lane loads NPL 16-byte pieces of the
+// column at once (coalesced: consecutive lanes, consecutive pieces), which keeps
+// ~128 KB of loads in flight per SM. The fixed-point residual is held once per
+// CTA in shared memory as three byte planes in a lane-interleaved layout
+// ([E][piece][4 words], conflict-free 16-byte loads).
+// Codes are extracted with one mask per four codes: (w & (mask << b k)) gives
+// the codes of position k times 2^(b k); products are summed per position and
+// the positions are combined at the end with exact right shifts.
+// ---------------------------------------------------------------------------
+template <int BITS, int NPL>
+__global__ void __launch_bounds__(256) k_gemv_t_warp(GemvTArgs a)
+{
+    constexpr int G = 32 / BITS;
+    constexpr int E = G / 4;
+    constexpr int L = 1 << BITS;
+    constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
+    extern __shared__ __align__(16) uint32_t limb[];    // [3][E][P][4]
+    __shared__ long long red_r[8];
+
+    if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int guard = ++a.st->outer_guard;
+        cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
+                                (!a.st->stop && guard < a.st->iters + 1) ? 1u : 0u);
+    }
+    if (a.st && a.st->stop) return;
+    const int n = a.Q.cols, ld = a.Q.ld, m = a.Q.rows;
+    const int P = ld / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int sh = fixed_shift(*a.rmax_bits);
+    long long rsum = 0;
+    for (int lw = threadIdx.x; lw < P * G; lw += blockDim.x) {
+        uint32_t b0 = 0, b1 = 0, b2 = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int i = 4 * lw + p;
+            int v = 0;
+            if (i < m) v = __float2int_rn(ldexpf(__ldcg(a.r + i), sh));
+            rsum += v;
+            b0 |= (uint32_t)(v & 255) << (8 * p);
+            b1 |= (uint32_t)((v >> 8) & 255) << (8 * p);
+            b2 |= (uint32_t)((v >> 16) & 255) << (8 * p);
+        }
+        const int piece = lw / G, rem = lw - piece * G, q = rem >> 2, w = rem & 3;
+        const size_t idx = ((size_t)q * P + piece) * 4 + w;
+        limb[idx] = b0;
+        limb[(size_t)E * P * 4 + idx] = b1;
+        limb[(size_t)2 * E * P * 4 + idx] = b2;
+    }
+    {
+        long long v = rsum;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red_r[warp] = v;
+    }
+    __syncthreads();
+    long long R = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) R += red_r[w];
+    const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
+    const double outscale = ldexp(alpha, -sh);
+    const uint4* L0 = reinterpret_cast<const uint4*>(limb);
+    const uint4* L1 = L0 + (size_t)E * P;
+    const uint4* L2 = L0 + (size_t)2 * E * P;
+
+    const int W = gridDim.x * (blockDim.x >> 5);
+    for (int j = blockIdx.x * (blockDim.x >> 5) + warp; j < n; j += W) {
+        const uint4* col = reinterpret_cast<const uint4*>(a.Q.words + (size_t)j * ld);
+        uint32_t s0[E], s1[E];
+        int32_t s2[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) { s0[k] = 0; s1[k] = 0; s2[k] = 0; }
+        for (int p0 = 0; p0 < P; p0 += 32 * NPL) {
+            uint4 cv[NPL];
+#pragma unroll
+            for (int u = 0; u < NPL; ++u) {
+                const int piece = p0 + lane + 32 * u;
+                if (piece < P)
+                    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w) : "l"(col + piece));
+                else
+                    cv[u] = make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < NPL; ++u) {
+                const int piece = min(p0 + lane + 32 * u, P - 1);   // out-of-range pieces have zero codes
+                const uint32_t wv[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
+#pragma unroll
+                for (int q = 0; q < E; ++q) {
+                    const uint4 A0 = L0[(size_t)q * P + piece];
+                    const uint4 A1 = L1[(size_t)q * P + piece];
+                    const uint4 A2 = L2[(size_t)q * P + piece];
+                    const uint32_t y0[4] = {A0.x, A0.y, A0.z, A0.w};
+                    const uint32_t y1[4] = {A1.x, A1.y, A1.z, A1.w};
+                    const uint32_t y2[4] = {A2.x, A2.y, A2.z, A2.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        // limb word lw = q*4 + t of the piece = word w = lw / E, position k = lw % E
+                        const int lw = q * 4 + t, w = lw / E, k = lw - w * E;
+                        const uint32_t x = wv[w] & (MASK << (BITS * k));
+                        s0[k] = dp4a_uu(x, y0[t], s0[k]);
+                        s1[k] = dp4a_uu(x, y1[t], s1[k]);
+                        s2[k] = dp4a_us(x, y2[t], s2[k]);
+                    }
+                }
+            }
+        }
+        long long S = 0;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            // position k sums carry the factor 2^(b k): exact, so shift it out after the warp sum
+            const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[k]);
+            const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[k]);
+            const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[k]);
+            S += (t0 + (t1 << 8) + (t2 << 16)) >> (BITS * k);
+        }
+        if (lane == 0) {
+            const long long T = 2 * S - (long long)(L - 1) * R;
+            a.g[j] = (float)((double)T * outscale);
+        }
+    }
+}
+
+struct WarpPlan {
+    void* fn;
+    size_t smem;
+    unsigned grid;
+    bool ok;
+};
+
+static WarpPlan plan_warp(const Codes& Q, int nsm)
+{
+    WarpPlan p{};
+    const int G = 32 / Q.bits, E = G / 4;
+    const size_t P = (size_t)Q.ld / 4;
+    p.smem = 3 * (size_t)E * P * 16;
+    if (p.smem > 48 * 1024 * 2) return p;          // keep at least two CTAs per SM
+    if (Q.bits == 8) p.fn = (void*)k_gemv_t_warp<8, 8>;
+    else if (Q.bits == 4) p.fn = (void*)k_gemv_t_warp<4, 4>;
+    else p.fn = (void*)k_gemv_t_warp<2, 2>;
+    cudaFuncSetAttribute(p.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p.fn, 256, p.smem);
+    if (occ < 1) return p;
+    long long grid = (long long)nsm * occ;
+    const long long want = ((long long)Q.cols + 7) / 8;
+    if (grid > want) grid = want;
+    p.grid = (unsigned)(grid < 1 ? 1 : grid);
+    p.ok = true;
+    return p;
+}
+
 struct TmaPlan {
     void* fn;
     int tpc;
@@ -772,14 +926,16 @@ static ColPlan plan_col(const Codes& Q, int nsm)
 
 static int gemv_variant()
 {
-    // QIHT_GEMV selects a kernel for measurement: "col" (default), "tma", "ldg"
+    // QIHT_GEMV selects a kernel for measurement: "warp" (default), "col", "tma", "ldg"
     static int v = -1;
     if (v < 0) {
         const char* e = getenv("QIHT_GEMV");
-        v = (e && e[0] == 'l') ? 0 : (e && e[0] == 't') ? 1 : 2;
+        v = (e && e[0] == 'l') ? 0 : (e && e[0] == 't') ? 1 : (e && e[0] == 'c') ? 2 : 3;
     }
     return v;
 }
+
+static bool use_warp() { return gemv_variant() == 3; }
 
 static bool use_tma() { return gemv_variant() == 1; }
 static bool use_col() { return gemv_variant() == 2; }
@@ -847,6 +1003,18 @@ static GemvPlan plan_gemv_t(const Codes& Q, int nsm)
 
 void gemv_t_node(const GemvTArgs& a, int nsm, cudaKernelNodeParams* p, void** argbuf)
 {
+    if (use_warp()) {
+        WarpPlan wp = plan_warp(a.Q, nsm);
+        if (wp.ok) {
+            p->func = wp.fn;
+            p->gridDim = dim3(wp.grid);
+            p->blockDim = dim3(256);
+            p->sharedMemBytes = (unsigned)wp.smem;
+            p->kernelParams = argbuf;        // (GemvTArgs)
+            p->extra = nullptr;
+            return;
+        }
+    }
     if (use_col()) {
         ColPlan cp = plan_col(a.Q, nsm);
         if (cp.ok) {
@@ -890,6 +1058,14 @@ void gemv_t_node(const GemvTArgs& a, int nsm, cudaKernelNodeParams* p, void** ar
 
 cudaError_t launch_gemv_t(const GemvTArgs& a, int nsm, cudaStream_t s)
 {
+    if (use_warp()) {
+        WarpPlan wp = plan_warp(a.Q, nsm);
+        if (wp.ok) {
+            GemvTArgs copy = a;
+            void* args[1] = {&copy};
+            return cudaLaunchKernel(wp.fn, dim3(wp.grid), dim3(256), args, wp.smem, s);
+        }
+    }
     if (use_col()) {
         ColPlan cp = plan_col(a.Q, nsm);
         if (cp.ok) {

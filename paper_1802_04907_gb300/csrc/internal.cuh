@@ -42,6 +42,10 @@ struct State {
     int iters;             // requested iterations
     int outer_guard;       // executions of the outer loop body (bounds the loop)
     int again;             // 1 if the last backtracking test asked for another shrink
+    unsigned tau_bits;     // candidate threshold of the next selection (float bits, 0 = none)
+    unsigned cand_count;   // keys >= tau found by the filter
+    unsigned below_max;    // largest key < tau seen by the filter
+    int pad2_;
     unsigned counters[3][32];  // arrival counters of the three column-subset products
 };
 
@@ -105,6 +109,8 @@ struct TopArgs {
     int32_t* support_init;
     qiht_trace trace;
     unsigned long long h_bt;    // backtracking-loop handle: cleared on entry, set later by the Omega product
+    unsigned long long* cand;   // candidate keys from the filter: (key << 32) | ~index
+    int cap;                    // candidate capacity (0: no filter, always the full select)
 };
 
 struct InitArgs {
@@ -126,6 +132,8 @@ struct InitArgs {
 void gemv_t_node(const GemvTArgs& a, int num_sms, cudaKernelNodeParams* p, void** argbuf);
 void gather_node(const GatherArgs& a, cudaKernelNodeParams* p, void** argbuf);
 void top_node(const TopArgs& a, cudaKernelNodeParams* p, void** argbuf);
+void top_filter_node(const TopArgs& a, cudaKernelNodeParams* p, void** argbuf);
+constexpr int kTopCandCap = 4096;
 void init_node(const InitArgs& a, cudaKernelNodeParams* p, void** argbuf);
 
 // Direct launches (building blocks).

@@ -302,7 +302,7 @@ namespace {
 
 struct Plan {
     size_t off_state, off_yhat, off_r, off_g, off_sel, off_val, off_uni, off_delta, off_partial, off_rbp, off_chunk,
-        total;
+        off_cand, total;
 };
 
 Plan plan_solve(int m, int n, int s)
@@ -327,6 +327,7 @@ Plan plan_solve(int m, int n, int s)
     const int rb = gather_row_blocks(m, 2) > gather_row_blocks(m, 8) ? gather_row_blocks(m, 2) : gather_row_blocks(m, 8);
     p.off_rbp = o; o += align256((size_t)rb * 2 * 8);
     p.off_chunk = o; o += align256((size_t)gather_chunks(2 * s) * 8);
+    p.off_cand = o; o += align256((size_t)kTopCandCap * 8);
     p.total = o;
     return p;
 }
@@ -399,6 +400,8 @@ struct SolveKernels {
     int tpc0, ns0, tpcb, nsb;
     TopArgs t0, tt;
     GatherArgs gmu, gom, gre;
+    void* a_tf[1];
+    cudaKernelNodeParams p_tf;
     void* a_init[1];
     void* a_g0[3];
     void* a_gb[3];
@@ -429,6 +432,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     float* partial = reinterpret_cast<float*>(ws + pl.off_partial);
     double* rbp = reinterpret_cast<double*>(ws + pl.off_rbp);
     double* chunkp = reinterpret_cast<double*>(ws + pl.off_chunk);
+    unsigned long long* cand = reinterpret_cast<unsigned long long*>(ws + pl.off_cand);
     qiht_trace tr{};
     if (trace) tr = *trace;
     const int nsm = num_sms();
@@ -479,6 +483,8 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     K.t0.init = 1;
     K.t0.support_init = support;
     K.t0.trace = tr;
+    K.t0.cand = cand;
+    K.t0.cap = kTopCandCap;
     K.a_t0[0] = &K.t0;
     top_node(K.t0, &K.p_t0, K.a_t0);
 
@@ -496,8 +502,12 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     K.tt.delta = delta;
     K.tt.trace = tr;
     K.tt.h_bt = h_bt;
+    K.tt.cand = cand;
+    K.tt.cap = kTopCandCap;
     K.a_tt[0] = &K.tt;
     top_node(K.tt, &K.p_tt, K.a_tt);
+    K.a_tf[0] = &K.tt;
+    top_filter_node(K.tt, &K.p_tf, K.a_tf);
 
     GatherArgs base{};
     base.Q = view(Q2);
@@ -564,10 +574,12 @@ qiht_status run_eager(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_cod
     if (!read_state()) return QIHT_ERR_CUDA;
     for (int t = 0; t < iters && !h.stop; ++t) {
         CK(launch_node(K.p_mu, cs));
+        CK(launch_node(K.p_tf, cs));
         CK(launch_node(K.p_tt, cs));
         CK(launch_node(K.p_om, cs));
         if (!read_state()) return QIHT_ERR_CUDA;
         for (int b = 0; b <= prm->max_backtrack && h.again && !h.stop; ++b) {
+            CK(launch_node(K.p_tf, cs));
             CK(launch_node(K.p_tt, cs));
             CK(launch_node(K.p_om, cs));
             if (!read_state()) return QIHT_ERR_CUDA;
@@ -606,14 +618,16 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     make_kernels(K, Q1, Q2, Y, s, iters, prm, x, support, report, trace, ws, (unsigned long long)h_outer,
                  (unsigned long long)h_bt);
 
-    cudaGraphNode_t b_mu, b_top, b_om, b_w, b_re, b_g;
+    cudaGraphNode_t b_mu, b_tf, b_top, b_om, b_w, b_re, b_g;
     TRY(add_kernel(body, &b_mu, nullptr, 0, K.p_mu));
-    TRY(add_kernel(body, &b_top, &b_mu, 1, K.p_tt));
+    TRY(add_kernel(body, &b_tf, &b_mu, 1, K.p_tf));
+    TRY(add_kernel(body, &b_top, &b_tf, 1, K.p_tt));
     TRY(add_kernel(body, &b_om, &b_top, 1, K.p_om));
     cudaGraph_t inner;
     TRY(add_while(body, &b_w, &b_om, 1, h_bt, &inner));
-    cudaGraphNode_t i_top, i_om;
-    TRY(add_kernel(inner, &i_top, nullptr, 0, K.p_tt));
+    cudaGraphNode_t i_tf, i_top, i_om;
+    TRY(add_kernel(inner, &i_tf, nullptr, 0, K.p_tf));
+    TRY(add_kernel(inner, &i_top, &i_tf, 1, K.p_tt));
     TRY(add_kernel(inner, &i_om, &i_top, 1, K.p_om));
     TRY(add_kernel(body, &b_re, &b_w, 1, K.p_re));
     TRY(add_kernel(body, &b_g, &b_re, 1, K.p_gb));
