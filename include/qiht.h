@@ -128,6 +128,23 @@ size_t qiht_gemv_cols_workspace_size(int32_t rows, int32_t count);
 qiht_status qiht_gemv_cols(const qiht_codes* Q, const int32_t* cols, const float* coef, int32_t count,
                            float* z, void* workspace, size_t workspace_bytes, qiht_stream_t stream);
 
+/* Allocation-free variant of qiht_gemv_cols. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * need the product (code running while its stream is captured into a CUDA graph,
+ * real-time loops that forbid allocation once running, plug-ins whose host owns
+ * every device allocation). Same arguments and results as qiht_gemv_cols, but
+ * the scratch is a fixed array of QIHT_STATIC_SCRATCH_BYTES inside this library,
+ * held on every GPU that loads the library until the process exits; the call
+ * allocates nothing. Limit: qiht_gemv_cols_workspace_size(Q->rows, count) must not
+ * exceed QIHT_STATIC_SCRATCH_BYTES, else QIHT_ERR_WORKSPACE is returned and nothing
+ * is launched. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture. All calls share the one array: calls whose kernels overlap
+ * on the GPU (other streams, other threads) race and give wrong results. */
+#define QIHT_STATIC_SCRATCH_BYTES (2u << 20)
+qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t* cols, const float* coef, int32_t count,
+                                  float* z, qiht_stream_t stream);
+
 /* Hard threshold H_s (Eq. NIHT): the s entries of a [device, n floats] of
  * largest magnitude, ties broken by the lower index; exactly s are kept.
  * idx [device, s int32] receives their indices in ascending order, val

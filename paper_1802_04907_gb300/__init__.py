@@ -60,7 +60,7 @@ REPORT_BYTES = ctypes.sizeof(_Report)
 
 EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_ld_words", "qiht_quantize",
            "qiht_gemv_t_workspace_size", "qiht_gemv_t", "qiht_gemv_t_prescaled",
-           "qiht_gemv_cols_workspace_size", "qiht_gemv_cols",
+           "qiht_gemv_cols_workspace_size", "qiht_gemv_cols", "qiht_gemv_cols_static",
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
            "qiht_clear_graph_cache"]
 
@@ -86,6 +86,7 @@ def lib():
             "qiht_gemv_t_prescaled": ([ctypes.POINTER(_Codes), P, P, P, P], I32),
             "qiht_gemv_cols_workspace_size": ([I32, I32], SZ),
             "qiht_gemv_cols": ([ctypes.POINTER(_Codes), P, P, I32, P, P, SZ, P], I32),
+            "qiht_gemv_cols_static": ([ctypes.POINTER(_Codes), P, P, I32, P, P], I32),
             "qiht_top_s_workspace_size": ([I32], SZ),
             "qiht_top_s": ([P, I32, I32, P, P, P, P, SZ, P], I32),
             "qiht_solve_workspace_size": ([I32, I32, I32], SZ),

@@ -12,6 +12,7 @@
 // waits on another one.
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -379,4 +380,86 @@ cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
     return cudaLaunchKernel(p.func, p.gridDim, p.blockDim, args, 0, s);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free column-subset product (qiht_gemv_cols_static).
+//
+// Some callers cannot call cudaMalloc at the moment they need this product:
+// code that runs while its stream is being captured into a CUDA graph, real-time
+// loops that forbid device allocation once they are running, or plug-ins whose
+// host application owns every device allocation and hands out no workspace.
+// For them the scratch of the product (chunk partial sums, per-row-block sums and
+// arrival counters) lives in one fixed array of this library's device memory.
+// Every GPU that loads the library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_scratch[QIHT_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_addr[256];   // device address of g_static_scratch, per device ordinal
+}
+
+// Device address of the static scratch on the current device. The host-side name
+// g_static_scratch is only a stand-in; its device address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+static cudaError_t static_scratch_address(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
 }  // namespace qiht
+
+extern "C" qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t* cols, const float* coef,
+                                             int32_t count, float* z, qiht_stream_t stream)
+{
+    using namespace qiht;
+    if (!Q || !Q->words || !Q->scale) return QIHT_ERR_ARG;
+    if (Q->bits != 2 && Q->bits != 4 && Q->bits != 8) return QIHT_ERR_BITS;
+    if (Q->rows < 1 || Q->cols < 1 || Q->ld_words != qiht_ld_words(Q->rows, Q->bits)) return QIHT_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(Q->words) & 15) != 0) return QIHT_ERR_ARG;
+    if (!cols || !coef || !z || count < 1) return QIHT_ERR_ARG;
+    // same scratch layout as qiht_gemv_cols; it must fit the fixed array
+    const size_t need = qiht_gemv_cols_workspace_size(Q->rows, count);
+    if (need > QIHT_STATIC_SCRATCH_BYTES) return QIHT_ERR_WORKSPACE;
+    void* base = nullptr;
+    if (static_scratch_address(&base) != cudaSuccess) return QIHT_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* w = reinterpret_cast<char*>(base);
+    size_t fl = 0;
+    for (int b : {2, 4, 8}) {
+        const size_t f = gather_partial_floats(Q->rows, b, count);
+        if (f > fl) fl = f;
+    }
+    const int rbmax = gather_row_blocks(Q->rows, 2) > gather_row_blocks(Q->rows, 8) ? gather_row_blocks(Q->rows, 2)
+                                                                                  : gather_row_blocks(Q->rows, 8);
+    const size_t a256 = 255;
+    const size_t off_rb = (fl * 4 + a256) & ~a256;
+    const size_t off_cnt = off_rb + (((size_t)rbmax * 2 * 8 + a256) & ~a256);
+    GatherArgs a{};
+    a.Q = Codes{Q->words, Q->scale, Q->rows, Q->cols, Q->bits, Q->ld_words};
+    a.cols = cols;
+    a.coef = coef;
+    a.count = count;
+    a.z = z;
+    a.partial = reinterpret_cast<float*>(w);
+    a.rb_partial = reinterpret_cast<double*>(w + off_rb);
+    a.counters = reinterpret_cast<unsigned*>(w + off_cnt);
+    a.mode = kGatherPlain;
+    // the array keeps the previous call's contents: the arrival counters must start at zero
+    if (cudaMemsetAsync(a.counters, 0, (size_t)(gather_row_blocks(Q->rows, Q->bits) + 1) * 4, s) != cudaSuccess)
+        return QIHT_ERR_CUDA;
+    if (launch_gather(a, s) != cudaSuccess) return QIHT_ERR_CUDA;
+    return QIHT_OK;
+}
+
