@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
 // the positions are combined at the end with exact right shifts.
 // ---------------------------------------------------------------------------
 template <int BITS, int NPL>
-__global__ void __launch_bounds__(256) k_gemv_t_warp(GemvTArgs a)
+__global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;
@@ -758,48 +758,55 @@ __global__ void __launch_bounds__(256) k_gemv_t_warp(GemvTArgs a)
     const uint4* L1 = L0 + (size_t)E * P;
     const uint4* L2 = L0 + (size_t)2 * E * P;
 
+    // Software pipeline over the warp's sequence of batches (column j, batch pb of NPL
+    // pieces per lane): the loads of the next batch are in flight while this one is used.
     const int W = gridDim.x * (blockDim.x >> 5);
-    for (int j = blockIdx.x * (blockDim.x >> 5) + warp; j < n; j += W) {
-        const uint4* col = reinterpret_cast<const uint4*>(a.Q.words + (size_t)j * ld);
-        uint32_t s0[E], s1[E];
-        int32_t s2[E];
+    const int nb = (P + 32 * NPL - 1) / (32 * NPL);     // batches per column
+    int j = blockIdx.x * (blockDim.x >> 5) + warp;
+    int pb = 0;
+    uint32_t s0[E], s1[E];
+    int32_t s2[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) { s0[k] = 0; s1[k] = 0; s2[k] = 0; }
-        for (int p0 = 0; p0 < P; p0 += 32 * NPL) {
-            uint4 cv[NPL];
+    for (int k = 0; k < E; ++k) { s0[k] = 0; s1[k] = 0; s2[k] = 0; }
+
+    auto load_batch = [&](uint4 (&cv)[NPL], int jj, int bb) {
+        const uint4* col = reinterpret_cast<const uint4*>(a.Q.words + (size_t)jj * ld);
 #pragma unroll
-            for (int u = 0; u < NPL; ++u) {
-                const int piece = p0 + lane + 32 * u;
-                if (piece < P)
-                    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                                 : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w) : "l"(col + piece));
-                else
-                    cv[u] = make_uint4(0u, 0u, 0u, 0u);
-            }
+        for (int u = 0; u < NPL; ++u) {
+            const int piece = bb * 32 * NPL + lane + 32 * u;
+            if (piece < P)
+                asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w) : "l"(col + piece));
+            else
+                cv[u] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    auto use_batch = [&](const uint4 (&cv)[NPL], int bb) {
 #pragma unroll
-            for (int u = 0; u < NPL; ++u) {
-                const int piece = min(p0 + lane + 32 * u, P - 1);   // out-of-range pieces have zero codes
-                const uint32_t wv[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
+        for (int u = 0; u < NPL; ++u) {
+            const int piece = min(bb * 32 * NPL + lane + 32 * u, P - 1);   // past the end: zero codes
+            const uint32_t wv[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
 #pragma unroll
-                for (int q = 0; q < E; ++q) {
-                    const uint4 A0 = L0[(size_t)q * P + piece];
-                    const uint4 A1 = L1[(size_t)q * P + piece];
-                    const uint4 A2 = L2[(size_t)q * P + piece];
-                    const uint32_t y0[4] = {A0.x, A0.y, A0.z, A0.w};
-                    const uint32_t y1[4] = {A1.x, A1.y, A1.z, A1.w};
-                    const uint32_t y2[4] = {A2.x, A2.y, A2.z, A2.w};
+            for (int q = 0; q < E; ++q) {
+                const uint4 A0 = L0[(size_t)q * P + piece];
+                const uint4 A1 = L1[(size_t)q * P + piece];
+                const uint4 A2 = L2[(size_t)q * P + piece];
+                const uint32_t y0[4] = {A0.x, A0.y, A0.z, A0.w};
+                const uint32_t y1[4] = {A1.x, A1.y, A1.z, A1.w};
+                const uint32_t y2[4] = {A2.x, A2.y, A2.z, A2.w};
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        // limb word lw = q*4 + t of the piece = word w = lw / E, position k = lw % E
-                        const int lw = q * 4 + t, w = lw / E, k = lw - w * E;
-                        const uint32_t x = wv[w] & (MASK << (BITS * k));
-                        s0[k] = dp4a_uu(x, y0[t], s0[k]);
-                        s1[k] = dp4a_uu(x, y1[t], s1[k]);
-                        s2[k] = dp4a_us(x, y2[t], s2[k]);
-                    }
+                for (int t = 0; t < 4; ++t) {
+                    // limb word lw = q*4 + t of the piece = word w = lw / E, position k = lw % E
+                    const int lw = q * 4 + t, w = lw / E, k = lw - w * E;
+                    const uint32_t x = wv[w] & (MASK << (BITS * k));
+                    s0[k] = dp4a_uu(x, y0[t], s0[k]);
+                    s1[k] = dp4a_uu(x, y1[t], s1[k]);
+                    s2[k] = dp4a_us(x, y2[t], s2[k]);
                 }
             }
         }
+    };
+    auto finish_column = [&](int jj) {
         long long S = 0;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
@@ -808,11 +815,33 @@ __global__ void __launch_bounds__(256) k_gemv_t_warp(GemvTArgs a)
             const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[k]);
             const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[k]);
             S += (t0 + (t1 << 8) + (t2 << 16)) >> (BITS * k);
+            s0[k] = 0; s1[k] = 0; s2[k] = 0;
         }
         if (lane == 0) {
             const long long T = 2 * S - (long long)(L - 1) * R;
-            a.g[j] = (float)((double)T * outscale);
+            a.g[jj] = (float)((double)T * outscale);
         }
+    };
+    auto advance = [&](int& jj, int& bb) {
+        if (++bb == nb) { bb = 0; jj += W; }
+    };
+
+    uint4 cA[NPL], cB[NPL];
+    if (j < n) load_batch(cA, j, pb);
+    while (j < n) {
+        int jB = j, pB = pb;
+        advance(jB, pB);
+        if (jB < n) load_batch(cB, jB, pB);
+        use_batch(cA, pb);
+        if (pb == nb - 1) finish_column(j);
+        j = jB; pb = pB;
+        if (j >= n) break;
+        int jA = j, pA = pb;
+        advance(jA, pA);
+        if (jA < n) load_batch(cA, jA, pA);
+        use_batch(cB, pb);
+        if (pb == nb - 1) finish_column(j);
+        j = jA; pb = pA;
     }
 }
 
@@ -830,9 +859,9 @@ static WarpPlan plan_warp(const Codes& Q, int nsm)
     const size_t P = (size_t)Q.ld / 4;
     p.smem = 3 * (size_t)E * P * 16;
     if (p.smem > 48 * 1024 * 2) return p;          // keep at least two CTAs per SM
-    if (Q.bits == 8) p.fn = (void*)k_gemv_t_warp<8, 8>;
-    else if (Q.bits == 4) p.fn = (void*)k_gemv_t_warp<4, 4>;
-    else p.fn = (void*)k_gemv_t_warp<2, 2>;
+    if (Q.bits == 8) p.fn = (void*)k_gemv_t_warp<8, 4>;
+    else if (Q.bits == 4) p.fn = (void*)k_gemv_t_warp<4, 2>;
+    else p.fn = (void*)k_gemv_t_warp<2, 1>;
     cudaFuncSetAttribute(p.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p.fn, 256, p.smem);

@@ -145,6 +145,17 @@ cudaError_t launch_gemv_t(const GemvTArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
 cudaError_t launch_top(const TopArgs& a, cudaStream_t s);
 
+// One iteration after the gradient product as one persistent kernel (iter.cu).
+struct IterArgs;
+constexpr size_t kIterArgsMax = 1024;     // bytes reserved for the iteration kernel's arguments
+size_t iter_smem_bytes(int n, int bits);
+int iter_grid();
+void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* support, int32_t* sel, float* val,
+               int32_t* uni, float* delta, const float* yhat, float* r, uint32_t* keys, unsigned long long* cand,
+               double* part, int n, int m, int s, double k, double c, int max_bt, qiht_report* report,
+               const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore, void** argbuf);
+size_t iter_args_bytes();
+
 int gather_row_blocks(int rows, int bits);
 int gather_chunks(int count);
 size_t gather_partial_floats(int rows, int bits, int count);

@@ -14,6 +14,7 @@
 // Control stays on the device for the whole solve. Graphs are cached per
 // argument set (pointers, sizes, parameters, device).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -302,7 +303,7 @@ namespace {
 
 struct Plan {
     size_t off_state, off_yhat, off_r, off_g, off_sel, off_val, off_uni, off_delta, off_partial, off_rbp, off_chunk,
-        off_cand, total;
+        off_cand, off_keys, off_part, total;
 };
 
 Plan plan_solve(int m, int n, int s)
@@ -328,6 +329,8 @@ Plan plan_solve(int m, int n, int s)
     p.off_rbp = o; o += align256((size_t)rb * 2 * 8);
     p.off_chunk = o; o += align256((size_t)gather_chunks(2 * s) * 8);
     p.off_cand = o; o += align256((size_t)kTopCandCap * 8);
+    p.off_keys = o; o += align256((size_t)n * 4);
+    p.off_part = o; o += align256((size_t)1024 * 4 * 8);
     p.total = o;
     return p;
 }
@@ -402,6 +405,9 @@ struct SolveKernels {
     GatherArgs gmu, gom, gre;
     void* a_tf[1];
     cudaKernelNodeParams p_tf;
+    alignas(16) unsigned char iter_store[kIterArgsMax];
+    void* a_it[1];
+    cudaKernelNodeParams p_it;
     void* a_init[1];
     void* a_g0[3];
     void* a_gb[3];
@@ -508,6 +514,9 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     top_node(K.tt, &K.p_tt, K.a_tt);
     K.a_tf[0] = &K.tt;
     top_filter_node(K.tt, &K.p_tf, K.a_tf);
+    iter_node(view(Q2), st, g, x, support, sel, val, uni, delta, yhat, r,
+              reinterpret_cast<uint32_t*>(ws + pl.off_keys), cand, reinterpret_cast<double*>(ws + pl.off_part), n, m, s,
+              prm->k, prm->c, prm->max_backtrack, report, tr, &K.p_it, K.iter_store, K.a_it);
 
     GatherArgs base{};
     base.Q = view(Q2);
@@ -555,6 +564,24 @@ static cudaError_t launch_node(const cudaKernelNodeParams& p, cudaStream_t s)
     return cudaLaunchKernel(p.func, p.gridDim, p.blockDim, p.kernelParams, p.sharedMemBytes, s);
 }
 
+// The iteration kernel waits on grid barriers, so all its CTAs must be resident at once.
+static cudaError_t launch_cooperative(const cudaKernelNodeParams& p, cudaStream_t s)
+{
+    return cudaLaunchCooperativeKernel(p.func, p.gridDim, p.blockDim, p.kernelParams, p.sharedMemBytes, s);
+}
+
+static bool multi_kernel_iteration()
+{
+    // QIHT_SOLVER=multi runs an iteration as separate kernels (step size, filter, select,
+    // backtracking test, residual) instead of the persistent iteration kernel
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("QIHT_SOLVER");
+        v = (e && e[0] == 'm') ? 1 : 0;
+    }
+    return v == 1;
+}
+
 // Host-driven run of the same kernels (QIHT_SOLVE_EAGER): reads the device state
 // after every iteration and after every backtracking test.
 qiht_status run_eager(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s, int iters,
@@ -572,6 +599,14 @@ qiht_status run_eager(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_cod
     CK(launch_node(K.p_g0, cs));
     CK(launch_node(K.p_t0, cs));
     if (!read_state()) return QIHT_ERR_CUDA;
+    if (!multi_kernel_iteration()) {
+        for (int t = 0; t < iters && !h.stop; ++t) {
+            CK(launch_cooperative(K.p_it, cs));
+            CK(launch_node(K.p_gb, cs));
+            if (!read_state()) return QIHT_ERR_CUDA;
+        }
+        return QIHT_OK;
+    }
     for (int t = 0; t < iters && !h.stop; ++t) {
         CK(launch_node(K.p_mu, cs));
         CK(launch_node(K.p_tf, cs));
@@ -617,6 +652,17 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     SolveKernels K;
     make_kernels(K, Q1, Q2, Y, s, iters, prm, x, support, report, trace, ws, (unsigned long long)h_outer,
                  (unsigned long long)h_bt);
+
+    if (!multi_kernel_iteration()) {
+        cudaGraphNode_t b_it, b_gk;
+        TRY(add_kernel(body, &b_it, nullptr, 0, K.p_it));
+        cudaLaunchAttributeValue coop{};
+        coop.cooperative = 1;
+        CK(cudaGraphKernelNodeSetAttribute(b_it, cudaLaunchAttributeCooperative, &coop));
+        TRY(add_kernel(body, &b_gk, &b_it, 1, K.p_gb));
+        *out = top;
+        return QIHT_OK;
+    }
 
     cudaGraphNode_t b_mu, b_tf, b_top, b_om, b_w, b_re, b_g;
     TRY(add_kernel(body, &b_mu, nullptr, 0, K.p_mu));
