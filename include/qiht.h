@@ -66,6 +66,10 @@ const char* qiht_status_string(int32_t status);
 /* Version of this ABI (QIHT_ABI_VERSION of the built library). */
 int32_t qiht_abi_version(void);
 
+/* Description of the last CUDA runtime failure seen by this thread inside the
+ * library (the call and the CUDA error string), or "" if there was none. */
+const char* qiht_last_error(void);
+
 /* A quantized matrix or vector in the column-packed layout (see above). */
 typedef struct {
     const uint32_t* words;   /* [device] cols * ld_words words */

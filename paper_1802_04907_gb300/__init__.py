@@ -31,7 +31,13 @@ STREAM_Q1, STREAM_Q2, STREAM_Y = 0, 1, 2
 
 class QihtError(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: {status_string(status)} ({status})")
+        detail = ""
+        if status == ERR_CUDA:
+            try:
+                detail = " [" + lib().qiht_last_error().decode() + "]"
+            except Exception:
+                pass
+        super().__init__(f"{where}: {status_string(status)} ({status}){detail}")
         self.status = status
 
 
@@ -58,7 +64,7 @@ class _Trace(ctypes.Structure):
 
 REPORT_BYTES = ctypes.sizeof(_Report)
 
-EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_ld_words", "qiht_quantize",
+EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld_words", "qiht_quantize",
            "qiht_gemv_t_workspace_size", "qiht_gemv_t", "qiht_gemv_t_prescaled",
            "qiht_gemv_cols_workspace_size", "qiht_gemv_cols", "qiht_gemv_cols_static",
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
@@ -79,6 +85,7 @@ def lib():
         sig = {
             "qiht_status_string": ([I32], ctypes.c_char_p),
             "qiht_abi_version": ([], I32),
+            "qiht_last_error": ([], ctypes.c_char_p),
             "qiht_ld_words": ([I32, I32], I32),
             "qiht_quantize": ([P, I32, I32, I64, I32, U64, U32, I32, P, I32, P, P], I32),
             "qiht_gemv_t_workspace_size": ([], SZ),

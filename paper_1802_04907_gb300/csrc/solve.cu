@@ -14,6 +14,7 @@
 // Control stays on the device for the whole solve. Graphs are cached per
 // argument set (pointers, sizes, parameters, device).
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -24,6 +25,13 @@
 #include "internal.cuh"
 
 namespace qiht {
+
+thread_local char g_last_error[256] = "";
+
+void note_cuda_error(const char* what, cudaError_t e)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+}
 
 int num_sms()
 {
@@ -154,6 +162,8 @@ const char* qiht_status_string(int32_t status)
 }
 
 int32_t qiht_abi_version(void) { return QIHT_ABI_VERSION; }
+
+const char* qiht_last_error(void) { return g_last_error; }
 
 int32_t qiht_ld_words(int32_t rows, int32_t bits)
 {
@@ -367,7 +377,11 @@ void push_codes(std::vector<uint64_t>& v, const qiht_codes* Q)
 
 #define CK(x)                                       \
     do {                                            \
-        if ((x) != cudaSuccess) return QIHT_ERR_CUDA; \
+        cudaError_t ck_e_ = (x);                    \
+        if (ck_e_ != cudaSuccess) {                 \
+            note_cuda_error(#x, ck_e_);             \
+            return QIHT_ERR_CUDA;                   \
+        }                                           \
     } while (0)
 
 qiht_status add_kernel(cudaGraph_t g, cudaGraphNode_t* out, const cudaGraphNode_t* dep, int ndep,
@@ -626,9 +640,13 @@ qiht_status run_eager(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_cod
     return QIHT_OK;
 }
 
+// cooperative: mark the iteration kernel's node as a cooperative launch. Without it
+// the kernel still finds all its CTAs resident (one CTA per SM, one per SM launched,
+// the node starts after the previous one has finished); its bounded barriers turn
+// any other case into QIHT_ERR_TIMEOUT.
 qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s, int iters,
                         const qiht_params* prm, float* x, int32_t* support, qiht_report* report,
-                        const qiht_trace* trace, char* ws, cudaGraph_t* out)
+                        const qiht_trace* trace, char* ws, bool cooperative, cudaGraph_t* out)
 {
     cudaGraph_t top;
     CK(cudaGraphCreate(&top, 0));
@@ -656,9 +674,11 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     if (!multi_kernel_iteration()) {
         cudaGraphNode_t b_it, b_gk;
         TRY(add_kernel(body, &b_it, nullptr, 0, K.p_it));
-        cudaLaunchAttributeValue coop{};
-        coop.cooperative = 1;
-        CK(cudaGraphKernelNodeSetAttribute(b_it, cudaLaunchAttributeCooperative, &coop));
+        if (cooperative) {
+            cudaLaunchAttributeValue coop{};
+            coop.cooperative = 1;
+            CK(cudaGraphKernelNodeSetAttribute(b_it, cudaLaunchAttributeCooperative, &coop));
+        }
         TRY(add_kernel(body, &b_gk, &b_it, 1, K.p_gb));
         *out = top;
         return QIHT_OK;
@@ -748,11 +768,23 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
             exec = it->second.exec;
         } else {
             cudaGraph_t graph = nullptr;
-            TRY(build_graph(Q1, Q2, y, s, iters, &prm, x, support, report, trace ? &tr : nullptr,
-                            reinterpret_cast<char*>(workspace), &graph));
-            if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-                cudaGraphDestroy(graph);
-                return QIHT_ERR_CUDA;
+            qiht_status st = QIHT_ERR_CUDA;
+            for (int coop = 1; coop >= 0 && st != QIHT_OK; --coop) {
+                if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+                st = build_graph(Q1, Q2, y, s, iters, &prm, x, support, report, trace ? &tr : nullptr,
+                                 reinterpret_cast<char*>(workspace), coop == 1, &graph);
+                if (st == QIHT_OK) {
+                    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+                    if (e != cudaSuccess) {
+                        note_cuda_error("cudaGraphInstantiate", e);
+                        st = QIHT_ERR_CUDA;
+                    }
+                }
+                if (st != QIHT_OK) cudaGetLastError();       // clear the error before the retry
+            }
+            if (st != QIHT_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
             }
             g_cache[key] = Cached{graph, exec};
         }
