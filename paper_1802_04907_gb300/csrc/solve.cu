@@ -665,8 +665,9 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
     cudaGraphNode_t n_w;
     cudaGraph_t body;
     TRY(add_while(top, &n_w, &n_t0, 1, h_outer, &body));
-    cudaGraphConditionalHandle h_bt;
-    CK(cudaGraphConditionalHandleCreate(&h_bt, body, 0, 0));
+    // the inner (backtracking) loop handle exists only when a conditional node uses it
+    cudaGraphConditionalHandle h_bt = 0;
+    if (multi_kernel_iteration()) CK(cudaGraphConditionalHandleCreate(&h_bt, body, 0, 0));
     SolveKernels K;
     make_kernels(K, Q1, Q2, Y, s, iters, prm, x, support, report, trace, ws, (unsigned long long)h_outer,
                  (unsigned long long)h_bt);
