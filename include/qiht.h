@@ -178,9 +178,13 @@ typedef struct {            /* written on the device after every iteration */
     int32_t iters_run;      /* iterations completed (an iteration that stopped early is not counted) */
     int32_t backtracks;     /* total step-size shrinks */
     int32_t support_changes;/* iterations whose accepted support differs from the previous one */
-    int32_t status;         /* qiht_status of the run: OK, NONFINITE or BACKTRACK_CAP */
+    int32_t status;         /* qiht_status of the run: OK, NONFINITE, BACKTRACK_CAP or TIMEOUT */
     double resid_norm2;     /* ||Q(y) - Q2 x||^2 of the returned x (FP64 sum of FP32 residuals) */
     double mu;              /* last accepted step size */
+    int32_t full_selects;   /* selections that ranked all n entries (the rest used the candidate list) */
+    int32_t reserved;
+    float phase_us[8];      /* diagnostics: device-clock durations of the last iteration's phases
+                               (step size, filter, select, backtracking tests, residual, commit) */
 } qiht_report;
 
 typedef struct {            /* optional per-iteration record [device]; any field may be NULL */

@@ -54,7 +54,9 @@ class _Params(ctypes.Structure):
 class _Report(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_int32), ("backtracks", ctypes.c_int32),
                 ("support_changes", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("resid_norm2", ctypes.c_double), ("mu", ctypes.c_double)]
+                ("resid_norm2", ctypes.c_double), ("mu", ctypes.c_double),
+                ("full_selects", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("phase_us", ctypes.c_float * 8)]
 
 
 class _Trace(ctypes.Structure):
@@ -244,11 +246,19 @@ class Report:
     status: int
     resid_norm2: float
     mu: float
+    full_selects: int = 0
+    phase_us: tuple = ()
+
+    def __eq__(self, other):       # the diagnostic timings differ from run to run
+        return (self.iters_run, self.backtracks, self.support_changes, self.status, self.resid_norm2, self.mu,
+                self.full_selects) == (other.iters_run, other.backtracks, other.support_changes, other.status,
+                                       other.resid_norm2, other.mu, other.full_selects)
 
 
 def report_from_bytes(buf: bytes) -> Report:
     r = _Report.from_buffer_copy(buf)
-    return Report(r.iters_run, r.backtracks, r.support_changes, r.status, r.resid_norm2, r.mu)
+    return Report(r.iters_run, r.backtracks, r.support_changes, r.status, r.resid_norm2, r.mu, r.full_selects,
+                  tuple(float(v) for v in r.phase_us))
 
 
 class Solver:

@@ -67,6 +67,7 @@ __device__ void write_report(const GatherArgs& a, const State* st)
     a.report->status = st->status;
     a.report->resid_norm2 = st->resid2;
     a.report->mu = st->mu_accepted;
+    a.report->full_selects = st->full_selects;
 }
 
 template <int BITS>

@@ -45,7 +45,8 @@ struct State {
     unsigned tau_bits;     // candidate threshold of the next selection (float bits, 0 = none)
     unsigned cand_count;   // keys >= tau found by the filter
     unsigned below_max;    // largest key < tau seen by the filter
-    int pad2_;
+    int full_selects;      // selections that ranked all n entries
+    unsigned long long t_phase[8];   // device clock at phase boundaries of the last iteration
     unsigned counters[3][32];  // arrival counters of the three column-subset products
 };
 

@@ -15,6 +15,7 @@
 // Every grid barrier is an arrive counter plus a generation word; waiting is
 // bounded by %globaltimer and a timeout sets QIHT_ERR_TIMEOUT instead of hanging.
 #include <cmath>
+#include <cstdlib>
 
 #include "internal.cuh"
 
@@ -425,6 +426,7 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
     }
     const unsigned bm = cta_max(below, sh_u);
     if (tid == 0) {
+        if (!fast) st->full_selects += 1;
         const float kth0 = __uint_as_float(T);
         const float kth1 = (eq_total > need) ? kth0 : (s < n ? __uint_as_float(bm) : 0.0f);
         st->kth0 = kth0;
@@ -479,6 +481,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     __shared__ unsigned shu[33];
     State* st = a.st;
     if (st->stop) return;                       // uniform: read before any barrier
+    const bool stamp = blockIdx.x == 0 && threadIdx.x == 0;
+    if (stamp) st->t_phase[0] = gtimer_ns();
 
     const RowBlock rb = row_block(a.Q.ld);
     int32_t* s_list = reinterpret_cast<int32_t*>(smem);
@@ -513,6 +517,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         if (tid == 0) { mypart[0] = acc; mypart[1] = num; }
     }
     if (!grid_sync(a.bar, st)) return;
+    if (stamp) st->t_phase[1] = gtimer_ns();
     double mu;
     {
         const double den = alpha * alpha * grid_partial_sum(a.part, 0, shd);
@@ -550,7 +555,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             const uint32_t tau = __ldcg(&st->tau_bits);
             const int per = (n + gridDim.x - 1) / gridDim.x;
             const int j0 = blockIdx.x * per, j1 = min(n, j0 + per);
-            const int lane = tid & 31;
+            __shared__ int scan_i[33];
+            __shared__ unsigned base_sh;
             unsigned below = 0;
             int bad = 0;
             for (int jb = j0; jb < j1; jb += blockDim.x) {
@@ -565,23 +571,27 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
                 }
                 const bool take = in && tau != 0u && k >= tau;
                 if (in && !take) below = max(below, k);
-                const unsigned mask = __ballot_sync(0xffffffffu, take);
-                if (mask) {
-                    unsigned base = 0;
-                    if (lane == __ffs(mask) - 1) base = atomicAdd(&st->cand_count, (unsigned)__popc(mask));
-                    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+                // CTA-aggregated append: one atomic per CTA and batch
+                int total;
+                const int rank = cta_excl_scan(take ? 1 : 0, scan_i, &total);
+                if (total) {
+                    if (tid == 0) base_sh = atomicAdd(&st->cand_count, (unsigned)total);
+                    __syncthreads();
                     if (take) {
-                        const unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
+                        const unsigned slot = base_sh + (unsigned)rank;
                         if (slot < (unsigned)a.cap)
                             a.cand[slot] = ((unsigned long long)k << 32) | (unsigned long long)(~(uint32_t)j);
                     }
+                    __syncthreads();
                 }
             }
-            below = __reduce_max_sync(0xffffffffu, below);
-            if (lane == 0 && below) atomicMax(&st->below_max, below);
+            // one atomic per CTA for the largest key below tau
+            const unsigned bcta = cta_max(below, shu);
+            if (tid == 0 && bcta) atomicMax(&st->below_max, bcta);
             if (__syncthreads_or(bad) && tid == 0) st->status = QIHT_ERR_NONFINITE;
         }
         if (!grid_sync(a.bar, st)) return;
+        if (stamp) st->t_phase[2] = gtimer_ns();
         if (__ldcg(&st->status) == QIHT_ERR_NONFINITE) {
             if (blockIdx.x == 0 && tid == 0) st->stop = 1;
             return;
@@ -589,6 +599,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         // ---- Select on CTA 0 ----
         if (blockIdx.x == 0) select_on_cta0(a, (float)mu, sel_smem);
         if (!grid_sync(a.bar, st)) return;
+        if (stamp) st->t_phase[3] = gtimer_ns();
         if (!__ldcg(&st->changed)) break;
 
         // ---- Omega: backtracking test on G' u G ----
@@ -638,6 +649,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     }
 
     // ---- Resid: r = Q(y) - Q2_G' x' for this CTA's rows ----
+    if (stamp) st->t_phase[4] = gtimer_ns();
     rows_product<BITS>(a, rb, a.sel, a.val, 0, s, s_list, s_coef, red, zrow);
     {
         double acc = 0.0;
@@ -655,6 +667,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         mx = cta_max(mx, shu);
         if (tid == 0) { mypart[0] = acc; mypart[1] = (double)mx; }
     }
+    if (stamp) st->t_phase[5] = gtimer_ns();
     // the last CTA to arrive commits the iteration (no CTA waits for it)
     __shared__ int last;
     __threadfence();
@@ -700,6 +713,18 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             a.report->status = st->status;
             a.report->resid_norm2 = resid2;
             a.report->mu = mu;
+            a.report->full_selects = st->full_selects;
+            // phases: step size, filter, select(s) + backtracking, residual product, commit
+            const unsigned long long t6 = gtimer_ns();
+            const unsigned long long* tp = st->t_phase;
+            a.report->phase_us[0] = (float)((tp[1] - tp[0]) * 1e-3);
+            a.report->phase_us[1] = (float)((tp[2] - tp[1]) * 1e-3);
+            a.report->phase_us[2] = (float)((tp[3] - tp[2]) * 1e-3);
+            a.report->phase_us[3] = (float)((tp[4] - tp[3]) * 1e-3);
+            a.report->phase_us[4] = (float)((tp[5] - tp[4]) * 1e-3);
+            a.report->phase_us[5] = (float)((t6 - tp[5]) * 1e-3);
+            a.report->phase_us[6] = (float)((t6 - tp[0]) * 1e-3);
+            a.report->phase_us[7] = 0.0f;
         }
     }
     __syncthreads();
@@ -766,8 +791,15 @@ size_t iter_smem_bytes(int n, int bits)
 
 int iter_grid()
 {
-    int n = num_sms();
-    return n > 1024 ? 1024 : n;
+    // QIHT_ITER_GRID overrides the number of CTAs (for measurement); default one per SM
+    static int g = -1;
+    if (g < 0) {
+        int n = num_sms();
+        const char* e = getenv("QIHT_ITER_GRID");
+        if (e && atoi(e) > 0 && atoi(e) < n) n = atoi(e);
+        g = n > 1024 ? 1024 : n;
+    }
+    return g;
 }
 
 }  // namespace qiht

@@ -102,6 +102,9 @@ __global__ void __launch_bounds__(1024) k_init(InitKernelArgs ka)
             a.report->status = st->status;
             a.report->resid_norm2 = t;
             a.report->mu = 0.0;
+            a.report->full_selects = 0;
+            a.report->reserved = 0;
+            for (int i = 0; i < 8; ++i) a.report->phase_us[i] = 0.0f;
         }
         set_cond_init(ka.h_outer, (finite && a.iters > 0) ? 1u : 0u);
     }

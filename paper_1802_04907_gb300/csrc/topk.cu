@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(kTopThreads) k_top(TopArgs a)
         kth1 = (eq_total > need) ? __uint_as_float(T) : (s < n ? __uint_as_float(bm) : 0.0f);
         if (a.kth) { a.kth[0] = kth0; a.kth[1] = kth1; }
         if (st) {
+            if (!fast) st->full_selects += 1;
             st->kth0 = kth0;
             st->kth1 = kth1;
             // next candidate threshold: a little below the current (s+1)-th magnitude
