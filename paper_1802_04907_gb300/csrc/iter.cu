@@ -176,7 +176,8 @@ __device__ __forceinline__ RowBlock row_block(int ld)
 // coef_mode: 0 = coef[jj], 1 = g[list[jj]].
 template <int BITS>
 __device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_t* list, const float* coef,
-                             int coef_mode, int count, int32_t* s_list, float* s_coef, float* red, float* zrow)
+                             int coef_mode, int count, int32_t* s_list, float* s_coef, float* red, float* zrow,
+                             double* coef_sq = nullptr)
 {
     constexpr int G = 32 / BITS;
     constexpr int L = 1 << BITS;
@@ -194,7 +195,9 @@ __device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_
         for (int i = t; i < cn; i += blockDim.x) {
             const int col = __ldcg(list + c0 + i);
             s_list[i] = col;
-            s_coef[i] = coef_mode == 1 ? __ldcg(a.g + col) : __ldcg(coef + c0 + i);
+            const float cf = coef_mode == 1 ? __ldcg(a.g + col) : __ldcg(coef + c0 + i);
+            s_coef[i] = cf;
+            if (coef_sq) *coef_sq += (double)cf * (double)cf;      // this thread's entries, in order
         }
         __syncthreads();
         if (active) {
@@ -234,9 +237,13 @@ __device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_
     __syncthreads();
     if (t < rb.wpc * G) {
         const int w = t / G, k = t % G;
-        float acc = 0.0f;
-        for (int s2 = 0; s2 < rb.nsl; ++s2) acc += red[(s2 * rb.wpc + w) * G + k];
-        zrow[t] = acc;
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};     // four interleaved partial sums, then in order
+        int s2 = 0;
+        for (; s2 + 4 <= rb.nsl; s2 += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += red[((s2 + u) * rb.wpc + w) * G + k];
+        for (; s2 < rb.nsl; ++s2) acc[0] += red[(s2 * rb.wpc + w) * G + k];
+        zrow[t] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     __syncthreads();
 }
@@ -321,8 +328,15 @@ __device__ int cta_excl_scan(int v, int* sh, int* total)
     return r;
 }
 
-// H_s on CTA 0: candidates if they are enough, else all keys. Writes sel/val ascending,
-// the gap values, the next threshold, G' != G and the x' - x list.
+// H_s on CTA 0. Candidates (keys >= tau) are ranked directly when there are at
+// least s of them and no more than kRankMax: the rank of a candidate is the number
+// of candidates ahead of it in the order (|a| descending, index ascending), read
+// from one packed 64-bit key, so ties resolve exactly as in the full ranking.
+// Otherwise the s-th largest of all n keys is found by a radix select. Either way
+// the selection is marked in a bitmap and emitted in ascending index order; the
+// x' - x list over G' u G is built from the same bitmap.
+constexpr int kRankMax = 1024;
+
 __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
 {
     State* st = a.st;
@@ -331,43 +345,40 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
     unsigned* hist = reinterpret_cast<unsigned*>(smem);                       // 2048
     uint32_t* bitmap = hist + 2048;                                           // n bits
     const int nbw = (n + 31) / 32;
-    uint32_t* ckey = bitmap + ((nbw + 3) & ~3);                               // cap
-    uint32_t* cidx = ckey + a.cap;                                            // cap
+    unsigned long long* cv = reinterpret_cast<unsigned long long*>(bitmap + ((nbw + 3) & ~3));   // cap
     __shared__ int sh_i[36];
     __shared__ unsigned sh_u[33];
+    __shared__ unsigned long long sh_k[2];
 
-    int need = 0;
+    const int cnt = (int)__ldcg(&st->cand_count);
+    const unsigned below_filter = __ldcg(&st->below_max);
+    const bool use_rank = a.cap > 0 && __ldcg(&st->tau_bits) != 0u && cnt >= s && cnt <= min(a.cap, kRankMax);
+    for (int w = tid; w < nbw; w += blockDim.x) bitmap[w] = 0u;
+    if (tid < 2) sh_k[tid] = 0ull;
     uint32_t T = 0;
-    int eq_total = 0;
+    int need = 0, eq_total = 0;
     unsigned below = 0;
-    const int cnt = (int)st->cand_count;
-    bool fast = a.cap > 0 && st->tau_bits != 0u && cnt >= s && cnt <= a.cap;
-    if (fast) {
+    float kth0 = 0.0f, kth1 = 0.0f;
+    if (use_rank) {
+        for (int i = tid; i < cnt; i += blockDim.x) cv[i] = __ldcg(a.cand + i);
+        __syncthreads();
         for (int i = tid; i < cnt; i += blockDim.x) {
-            const unsigned long long v = __ldcg(a.cand + i);
-            ckey[i] = (uint32_t)(v >> 32);
-            cidx[i] = ~(uint32_t)v;
+            const unsigned long long mine = cv[i];
+            int rank = 0;
+#pragma unroll 8
+            for (int q = 0; q < cnt; ++q) rank += (cv[q] > mine);
+            if (rank < s) {
+                const uint32_t j = ~(uint32_t)mine;
+                atomicOr(&bitmap[j >> 5], 1u << (j & 31));
+            }
+            if (rank == s - 1) sh_k[0] = mine;
+            if (rank == s) sh_k[1] = mine;
         }
         __syncthreads();
-        T = select_kth([&](int j) { return ckey[j]; }, cnt, s, hist, sh_i, &need);
-        int eq = 0;
-        for (int i = tid; i < cnt; i += blockDim.x) {
-            eq += (ckey[i] == T);
-            if (ckey[i] < T) below = max(below, ckey[i]);
-        }
-        int tot;
-        cta_excl_scan(eq, sh_i, &tot);
-        eq_total = tot;
-        fast = (eq_total == need);      // a tie straddling the threshold: use the full path
-    }
-    for (int w = tid; w < nbw; w += blockDim.x) bitmap[w] = 0u;
-    __syncthreads();
-    if (fast) {
-        for (int i = tid; i < cnt; i += blockDim.x)
-            if (ckey[i] >= T) atomicOr(&bitmap[cidx[i] >> 5], 1u << (cidx[i] & 31));
-        below = max(below, st->below_max);
+        kth0 = __uint_as_float((uint32_t)(sh_k[0] >> 32));
+        kth1 = cnt > s ? __uint_as_float((uint32_t)(sh_k[1] >> 32)) : __uint_as_float(below_filter);
     } else {
-        below = 0;
+        __syncthreads();
         T = select_kth([&](int j) { return __ldcg(a.keys + j); }, n, s, hist, sh_i, &need);
         // mark keys > T, and the `need` lowest-index keys == T, walking the keys in index order
         const int warp = tid >> 5, nw = blockDim.x >> 5;
@@ -402,9 +413,13 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
             if (take) atomicOr(&bitmap[j >> 5], 1u << (j & 31));
             erun += __popc(meq);
         }
+        const unsigned bm = cta_max(below, sh_u);
+        kth0 = __uint_as_float(T);
+        kth1 = (eq_total > need) ? kth0 : (s < n ? __uint_as_float(bm) : 0.0f);
     }
     __syncthreads();
-    // emit the selected indices in ascending order
+    // emit G' in ascending order with x'; the first s entries of the x' - x list are G'
+    int diff = 0;
     {
         const int wpt = (nbw + blockDim.x - 1) / blockDim.x;
         const int w0 = min(nbw, tid * wpt), w1 = min(nbw, w0 + wpt);
@@ -418,56 +433,48 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int j = w * 32 + b;
+                const float xj = __ldcg(a.x + j);
+                const float v = fmaf(mu, __ldcg(a.g + j), xj);
+                diff |= (j != __ldcg(a.support + pos));
                 a.sel[pos] = j;
-                a.val[pos] = fmaf(mu, __ldcg(a.g + j), __ldcg(a.x + j));
+                a.val[pos] = v;
+                a.uni[pos] = j;
+                a.delta[pos] = v - xj;
                 ++pos;
             }
         }
     }
-    const unsigned bm = cta_max(below, sh_u);
-    if (tid == 0) {
-        if (!fast) st->full_selects += 1;
-        const float kth0 = __uint_as_float(T);
-        const float kth1 = (eq_total > need) ? kth0 : (s < n ? __uint_as_float(bm) : 0.0f);
-        st->kth0 = kth0;
-        st->kth1 = kth1;
-        st->tau_bits = (a.cap > 0 && kth1 > 0.0f) ? __float_as_uint(kth1 * 0.9375f) : 0u;
-        st->cand_count = 0u;
-        st->below_max = 0u;
-    }
-    __syncthreads();
-    // G' vs G and the x' - x list over G' u G (G' first, then G \ G' in support order)
-    for (int w = tid; w < nbw; w += blockDim.x) bitmap[w] = 0u;
-    __syncthreads();
-    int diff = 0;
-    for (int q = tid; q < s; q += blockDim.x) {
-        const int j = __ldcg(a.sel + q);
-        diff |= (j != __ldcg(a.support + q));
-        atomicOr(&bitmap[j >> 5], 1u << (j & 31));
-        a.uni[q] = j;
-        a.delta[q] = __ldcg(a.val + q) - __ldcg(a.x + j);
-    }
     diff = __syncthreads_or(diff);
-    const int sper = (s + blockDim.x - 1) / blockDim.x;
-    const int q0 = min(s, tid * sper), q1 = min(s, q0 + sper);
-    int cntx = 0;
-    for (int q = q0; q < q1; ++q) {
-        const int j = __ldcg(a.support + q);
-        cntx += !((bitmap[j >> 5] >> (j & 31)) & 1u);
-    }
-    int extra;
-    int p = cta_excl_scan(cntx, sh_i, &extra);
-    for (int q = q0; q < q1; ++q) {
-        const int j = __ldcg(a.support + q);
-        if (!((bitmap[j >> 5] >> (j & 31)) & 1u)) {
-            a.uni[s + p] = j;
-            a.delta[s + p] = -__ldcg(a.x + j);
-            ++p;
+    // G \ G' after G', in support order
+    {
+        const int sper = (s + blockDim.x - 1) / blockDim.x;
+        const int q0 = min(s, tid * sper), q1 = min(s, q0 + sper);
+        int cntx = 0;
+        for (int q = q0; q < q1; ++q) {
+            const int j = __ldcg(a.support + q);
+            cntx += !((bitmap[j >> 5] >> (j & 31)) & 1u);
         }
-    }
-    if (tid == 0) {
-        st->changed = diff ? 1 : 0;
-        st->union_count = s + extra;
+        int extra;
+        int p = cta_excl_scan(cntx, sh_i, &extra);
+        for (int q = q0; q < q1; ++q) {
+            const int j = __ldcg(a.support + q);
+            if (!((bitmap[j >> 5] >> (j & 31)) & 1u)) {
+                a.uni[s + p] = j;
+                a.delta[s + p] = -__ldcg(a.x + j);
+                ++p;
+            }
+        }
+        if (tid == 0) {
+            if (!use_rank) st->full_selects += 1;
+            st->kth0 = kth0;
+            st->kth1 = kth1;
+            // next candidate threshold: a little below the current (s+1)-th magnitude
+            st->tau_bits = (a.cap > 0 && kth1 > 0.0f) ? __float_as_uint(kth1 * 0.9375f) : 0u;
+            st->cand_count = 0u;
+            st->below_max = 0u;
+            st->changed = diff ? 1 : 0;
+            st->union_count = s + extra;
+        }
     }
 }
 
@@ -497,7 +504,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     double* mypart = a.part + 4 * blockIdx.x;
 
     // ---- Mu: z = Q2_G g_G, den = alpha^2 ||z||^2, num = ||g_G||^2 ----
-    rows_product<BITS>(a, rb, a.support, nullptr, 1, s, s_list, s_coef, red, zrow);
+    double gsq = 0.0;
+    rows_product<BITS>(a, rb, a.support, nullptr, 1, s, s_list, s_coef, red, zrow, &gsq);
     {
         double acc = 0.0;
         if (tid < rb.wpc * G) {
@@ -505,15 +513,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             if (rb.w0 + tid / G < rb.w1 && row < m) acc = (double)zrow[tid] * (double)zrow[tid];
         }
         acc = cta_sum(acc, shd);
-        double num = 0.0;
-        if (blockIdx.x == 0) {
-            double v = 0.0;
-            for (int q = tid; q < s; q += blockDim.x) {
-                const float gq = __ldcg(a.g + __ldcg(a.support + q));
-                v += (double)gq * (double)gq;
-            }
-            num = cta_sum(v, shd);
-        }
+        const double num = cta_sum(gsq, shd);                // ||g_G||^2 from the staged coefficients
         if (tid == 0) { mypart[0] = acc; mypart[1] = num; }
     }
     if (!grid_sync(a.bar, st)) return;
@@ -604,7 +604,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
 
         // ---- Omega: backtracking test on G' u G ----
         const int cu = __ldcg(&st->union_count);
-        rows_product<BITS>(a, rb, a.uni, a.delta, 0, cu, s_list, s_coef, red, zrow);
+        double dsq = 0.0;
+        rows_product<BITS>(a, rb, a.uni, a.delta, 0, cu, s_list, s_coef, red, zrow, &dsq);
         {
             double acc = 0.0;
             if (tid < rb.wpc * G) {
@@ -612,15 +613,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
                 if (rb.w0 + tid / G < rb.w1 && row < m) acc = (double)zrow[tid] * (double)zrow[tid];
             }
             acc = cta_sum(acc, shd);
-            double dn = 0.0;
-            if (blockIdx.x == 0) {
-                double v = 0.0;
-                for (int q = tid; q < cu; q += blockDim.x) {
-                    const float d = __ldcg(a.delta + q);
-                    v += (double)d * (double)d;
-                }
-                dn = cta_sum(v, shd);
-            }
+            const double dn = cta_sum(dsq, shd);             // ||x' - x||^2 from the staged list
             if (tid == 0) { mypart[2] = acc; mypart[3] = dn; }
         }
         if (!grid_sync(a.bar, st)) return;
@@ -678,14 +671,38 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     __threadfence();
     const double resid2 = grid_partial_sum(a.part, 0, shd);
     const double rmax = grid_partial_max(a.part, 1, shd);
-    for (int q = tid; q < s; q += blockDim.x) a.x[__ldcg(a.support + q)] = 0.0f;
-    __syncthreads();
-    for (int q = tid; q < s; q += blockDim.x) {
-        const int j = __ldcg(a.sel + q);
-        a.x[j] = __ldcg(a.val + q);
-        a.support[q] = j;
+    {
+        // zero the old support everywhere first, then write the new one (entries may be in both)
+        constexpr int kPer = 8;
+        for (int q0 = 0; q0 < s; q0 += kPer * kIterThreads) {
+            int oldj[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int q = q0 + u * kIterThreads + tid;
+                oldj[u] = q < s ? __ldcg(a.support + q) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kPer; ++u)
+                if (oldj[u] >= 0) a.x[oldj[u]] = 0.0f;
+        }
+        __syncthreads();
+        for (int q0 = 0; q0 < s; q0 += kPer * kIterThreads) {
+            int newj[kPer];
+            float newv[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int q = q0 + u * kIterThreads + tid;
+                newj[u] = q < s ? __ldcg(a.sel + q) : -1;
+                newv[u] = q < s ? __ldcg(a.val + q) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int q = q0 + u * kIterThreads + tid;
+                if (newj[u] >= 0) { a.x[newj[u]] = newv[u]; a.support[q] = newj[u]; }
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (tid == 0) {
         a.bar[2] = 0u;
         const int it = st->iter + 1;
