@@ -769,14 +769,19 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
 #pragma unroll
     for (int k = 0; k < E; ++k) { s0[k] = 0; s1[k] = 0; s2[k] = 0; }
 
+    // the code stream is read once per call: mark it first to leave L2, so that the small
+    // working set of the rest of the iteration (support columns of Q2, g, x, r) stays there
+    uint64_t stream_policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_policy));
     auto load_batch = [&](uint4 (&cv)[NPL], int jj, int bb) {
         const uint4* col = reinterpret_cast<const uint4*>(a.Q.words + (size_t)jj * ld);
 #pragma unroll
         for (int u = 0; u < NPL; ++u) {
             const int piece = bb * 32 * NPL + lane + 32 * u;
             if (piece < P)
-                asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                             : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w) : "l"(col + piece));
+                asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                             : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w)
+                             : "l"(col + piece), "l"(stream_policy));
             else
                 cv[u] = make_uint4(0u, 0u, 0u, 0u);
         }

@@ -47,7 +47,8 @@ struct State {
     unsigned below_max;    // largest key < tau seen by the filter
     int full_selects;      // selections that ranked all n entries
     unsigned long long t_phase[8];   // device clock at phase boundaries of the last iteration
-    unsigned counters[3][32];  // arrival counters of the three column-subset products
+    unsigned counters[2][1024];  // arrival counters of the column-subset products; iteration-kernel
+                                 // barrier words (row 0) and per-CTA barrier epochs (row 1)
 };
 
 // Column-subset product modes (one epilogue each).

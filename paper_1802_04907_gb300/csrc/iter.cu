@@ -32,27 +32,63 @@ __device__ __forceinline__ unsigned long long gtimer_ns()
     return t;
 }
 
-// Grid barrier. bar[0] = arrivals, bar[1] = generation. Returns false on timeout
-// (then the state is marked and the caller leaves).
-__device__ bool grid_sync(unsigned* bar, State* st)
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier without contended atomics: CTA c release-stores the barrier's epoch in
+// its own flag; CTA 0 acquires every flag (in parallel) and then releases the epoch in
+// the generation word, which every CTA acquires. Epochs only grow (wrap-safe
+// comparisons), so flags never need resetting. Waiting is bounded by %globaltimer;
+// a timeout marks the state and returns false.
+__device__ bool grid_sync(unsigned* flags, unsigned* gen, unsigned& epoch, State* st)
 {
     __shared__ int ok_sh;
+    ++epoch;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g0 = *gen;
         __threadfence();
-        const unsigned prev = atomicAdd(bar, 1u);
+        st_release(flags + blockIdx.x, epoch);
+        ok_sh = 1;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) {
         int ok = 1;
-        if (prev == gridDim.x - 1) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
+            if ((int)(ld_acquire(flags + c) - epoch) < 0) {
+                const unsigned long long t0 = gtimer_ns();
+                while ((int)(ld_acquire(flags + c) - epoch) < 0) {
+                    if (gtimer_ns() - t0 > kBarrierBudgetNs) { ok = 0; break; }
+                }
+            }
+        }
+        ok = __syncthreads_and(ok);
+        if (threadIdx.x == 0) {
+            if (ok) {
+                __threadfence();
+                st_release(gen, epoch);
+            } else {
+                st->status = QIHT_ERR_TIMEOUT;
+                st->stop = 1;
+                ok_sh = 0;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && ok_sh) {
+        if ((int)(ld_acquire(gen) - epoch) < 0) {
             const unsigned long long t0 = gtimer_ns();
-            while (*gen == g0) {
+            while ((int)(ld_acquire(gen) - epoch) < 0) {
                 if (gtimer_ns() - t0 > kBarrierBudgetNs) {
-                    ok = 0;
+                    ok_sh = 0;
                     st->status = QIHT_ERR_TIMEOUT;
                     st->stop = 1;
                     break;
@@ -60,7 +96,6 @@ __device__ bool grid_sync(unsigned* bar, State* st)
             }
         }
         __threadfence();
-        ok_sh = ok;
     }
     __syncthreads();
     return ok_sh != 0;
@@ -146,7 +181,10 @@ struct IterArgs {
     unsigned long long* cand;   // filter candidates
     int cap;
     double* part;               // [grid][4] per-CTA partials
-    unsigned* bar;              // grid barrier words [2] + commit counter [1]
+    unsigned* bar;              // [0] generation of the grid barrier, [2] commit counter
+    unsigned* flags;            // [grid] barrier epoch of every CTA
+    float* cand_val;            // x + mu g of each candidate (same slot as cand)
+    float* cand_x;              // x of each candidate
     int n, m, s;
     double k, c;
     int max_bt;
@@ -336,16 +374,23 @@ __device__ int cta_excl_scan(int v, int* sh, int* total)
 // the selection is marked in a bitmap and emitted in ascending index order; the
 // x' - x list over G' u G is built from the same bitmap.
 constexpr int kRankMax = 1024;
+constexpr int kSupportSmem = 4096;       // supports up to this size are staged in shared memory
 
 __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
 {
     State* st = a.st;
     const int n = a.n, s = a.s, tid = threadIdx.x;
     const int lane = tid & 31;
-    unsigned* hist = reinterpret_cast<unsigned*>(smem);                       // 2048
-    uint32_t* bitmap = hist + 2048;                                           // n bits
     const int nbw = (n + 31) / 32;
-    unsigned long long* cv = reinterpret_cast<unsigned long long*>(bitmap + ((nbw + 3) & ~3));   // cap
+    const int nbw4 = (nbw + 3) & ~3;
+    unsigned* hist = reinterpret_cast<unsigned*>(smem);                       // 2048
+    uint32_t* bitmap = hist + 2048;                                           // nbw4
+    int* wpre = reinterpret_cast<int*>(bitmap + nbw4);                        // nbw4: selected before word w
+    unsigned long long* cv = reinterpret_cast<unsigned long long*>(wpre + nbw4);   // cap
+    float* cval = reinterpret_cast<float*>(cv + a.cap);                       // cap
+    float* cx = cval + a.cap;                                                 // cap
+    int32_t* sup = reinterpret_cast<int32_t*>(cx + a.cap);                    // s (if it fits)
+    const bool sup_sm = s <= kSupportSmem;
     __shared__ int sh_i[36];
     __shared__ unsigned sh_u[33];
     __shared__ unsigned long long sh_k[2];
@@ -353,14 +398,17 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
     const int cnt = (int)__ldcg(&st->cand_count);
     const unsigned below_filter = __ldcg(&st->below_max);
     const bool use_rank = a.cap > 0 && __ldcg(&st->tau_bits) != 0u && cnt >= s && cnt <= min(a.cap, kRankMax);
-    for (int w = tid; w < nbw; w += blockDim.x) bitmap[w] = 0u;
+    for (int w = tid; w < nbw4; w += blockDim.x) bitmap[w] = 0u;
     if (tid < 2) sh_k[tid] = 0ull;
-    uint32_t T = 0;
-    int need = 0, eq_total = 0;
-    unsigned below = 0;
+    if (sup_sm)
+        for (int q = tid; q < s; q += blockDim.x) sup[q] = __ldcg(a.support + q);
     float kth0 = 0.0f, kth1 = 0.0f;
     if (use_rank) {
-        for (int i = tid; i < cnt; i += blockDim.x) cv[i] = __ldcg(a.cand + i);
+        for (int i = tid; i < cnt; i += blockDim.x) {
+            cv[i] = __ldcg(a.cand + i);
+            cval[i] = __ldcg(a.cand_val + i);
+            cx[i] = __ldcg(a.cand_x + i);
+        }
         __syncthreads();
         for (int i = tid; i < cnt; i += blockDim.x) {
             const unsigned long long mine = cv[i];
@@ -379,12 +427,14 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
         kth1 = cnt > s ? __uint_as_float((uint32_t)(sh_k[1] >> 32)) : __uint_as_float(below_filter);
     } else {
         __syncthreads();
-        T = select_kth([&](int j) { return __ldcg(a.keys + j); }, n, s, hist, sh_i, &need);
+        int need = 0;
+        const uint32_t T = select_kth([&](int j) { return __ldcg(a.keys + j); }, n, s, hist, sh_i, &need);
         // mark keys > T, and the `need` lowest-index keys == T, walking the keys in index order
         const int warp = tid >> 5, nw = blockDim.x >> 5;
         const int seg = ((n + 32 * nw - 1) / (32 * nw)) * 32;
         const int wb = min(n, warp * seg), we = min(n, wb + seg);
         int eq = 0;
+        unsigned below = 0;
         for (int b = wb; b < we; b += 32) {
             const int j = b + lane;
             const bool in = j < we;
@@ -396,9 +446,8 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
         __syncthreads();
         int eq_before = 0;
         for (int w = 0; w < warp; ++w) eq_before += sh_i[w];
-        int tot = 0;
-        for (int w = 0; w < nw; ++w) tot += sh_i[w];
-        eq_total = tot;
+        int eq_total = 0;
+        for (int w = 0; w < nw; ++w) eq_total += sh_i[w];
         __syncthreads();
         const int take_w = max(0, min(eq, need - eq_before));
         int erun = 0;
@@ -418,29 +467,42 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
         kth1 = (eq_total > need) ? kth0 : (s < n ? __uint_as_float(bm) : 0.0f);
     }
     __syncthreads();
-    // emit G' in ascending order with x'; the first s entries of the x' - x list are G'
-    int diff = 0;
+    // selected entries before each bitmap word (exclusive scan over the words)
     {
         const int wpt = (nbw + blockDim.x - 1) / blockDim.x;
         const int w0 = min(nbw, tid * wpt), w1 = min(nbw, w0 + wpt);
         int c = 0;
         for (int w = w0; w < w1; ++w) c += __popc(bitmap[w]);
         int total;
-        int pos = cta_excl_scan(c, sh_i, &total);
-        for (int w = w0; w < w1; ++w) {
+        int pre = cta_excl_scan(c, sh_i, &total);
+        for (int w = w0; w < w1; ++w) { wpre[w] = pre; pre += __popc(bitmap[w]); }
+    }
+    __syncthreads();
+    // emit G' (ascending) with x'; the first s entries of the x' - x list are G'
+    int diff = 0;
+    auto emit = [&](int j, float v, float xj) {
+        const int w = j >> 5;
+        const int pos = wpre[w] + __popc(bitmap[w] & ((1u << (j & 31)) - 1u));
+        diff |= (j != (sup_sm ? sup[pos] : __ldcg(a.support + pos)));
+        a.sel[pos] = j;
+        a.val[pos] = v;
+        a.uni[pos] = j;
+        a.delta[pos] = v - xj;
+    };
+    if (use_rank) {
+        for (int i = tid; i < cnt; i += blockDim.x) {
+            const uint32_t j = ~(uint32_t)cv[i];
+            if ((bitmap[j >> 5] >> (j & 31)) & 1u) emit((int)j, cval[i], cx[i]);
+        }
+    } else {
+        for (int w = tid; w < nbw; w += blockDim.x) {
             uint32_t bits = bitmap[w];
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int j = w * 32 + b;
                 const float xj = __ldcg(a.x + j);
-                const float v = fmaf(mu, __ldcg(a.g + j), xj);
-                diff |= (j != __ldcg(a.support + pos));
-                a.sel[pos] = j;
-                a.val[pos] = v;
-                a.uni[pos] = j;
-                a.delta[pos] = v - xj;
-                ++pos;
+                emit(j, fmaf(mu, __ldcg(a.g + j), xj), xj);
             }
         }
     }
@@ -451,13 +513,13 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
         const int q0 = min(s, tid * sper), q1 = min(s, q0 + sper);
         int cntx = 0;
         for (int q = q0; q < q1; ++q) {
-            const int j = __ldcg(a.support + q);
+            const int j = sup_sm ? sup[q] : __ldcg(a.support + q);
             cntx += !((bitmap[j >> 5] >> (j & 31)) & 1u);
         }
         int extra;
         int p = cta_excl_scan(cntx, sh_i, &extra);
         for (int q = q0; q < q1; ++q) {
-            const int j = __ldcg(a.support + q);
+            const int j = sup_sm ? sup[q] : __ldcg(a.support + q);
             if (!((bitmap[j >> 5] >> (j & 31)) & 1u)) {
                 a.uni[s + p] = j;
                 a.delta[s + p] = -__ldcg(a.x + j);
@@ -490,6 +552,9 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     if (st->stop) return;                       // uniform: read before any barrier
     const bool stamp = blockIdx.x == 0 && threadIdx.x == 0;
     if (stamp) st->t_phase[0] = gtimer_ns();
+    // barrier epochs continue from the generation left by the previous launch; no CTA can
+    // move it on before every CTA has arrived at the first barrier, so all read the same value
+    unsigned epoch = ld_acquire(a.bar);
 
     const RowBlock rb = row_block(a.Q.ld);
     int32_t* s_list = reinterpret_cast<int32_t*>(smem);
@@ -516,7 +581,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         const double num = cta_sum(gsq, shd);                // ||g_G||^2 from the staged coefficients
         if (tid == 0) { mypart[0] = acc; mypart[1] = num; }
     }
-    if (!grid_sync(a.bar, st)) return;
+    if (!grid_sync(a.flags, a.bar, epoch, st)) return;
     if (stamp) st->t_phase[1] = gtimer_ns();
     double mu;
     {
@@ -562,9 +627,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             for (int jb = j0; jb < j1; jb += blockDim.x) {
                 const int j = jb + tid;
                 uint32_t k = 0;
+                float v = 0.0f, xj = 0.0f;
                 const bool in = j < j1;
                 if (in) {
-                    const float v = fmaf(muf, __ldcg(a.g + j), __ldcg(a.x + j));
+                    xj = __ldcg(a.x + j);
+                    v = fmaf(muf, __ldcg(a.g + j), xj);
                     k = __float_as_uint(v) & 0x7fffffffu;
                     bad |= (k > 0x7f800000u);
                     a.keys[j] = k;
@@ -579,8 +646,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
                     __syncthreads();
                     if (take) {
                         const unsigned slot = base_sh + (unsigned)rank;
-                        if (slot < (unsigned)a.cap)
+                        if (slot < (unsigned)a.cap) {
                             a.cand[slot] = ((unsigned long long)k << 32) | (unsigned long long)(~(uint32_t)j);
+                            a.cand_val[slot] = v;
+                            a.cand_x[slot] = xj;
+                        }
                     }
                     __syncthreads();
                 }
@@ -590,7 +660,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             if (tid == 0 && bcta) atomicMax(&st->below_max, bcta);
             if (__syncthreads_or(bad) && tid == 0) st->status = QIHT_ERR_NONFINITE;
         }
-        if (!grid_sync(a.bar, st)) return;
+        if (!grid_sync(a.flags, a.bar, epoch, st)) return;
         if (stamp) st->t_phase[2] = gtimer_ns();
         if (__ldcg(&st->status) == QIHT_ERR_NONFINITE) {
             if (blockIdx.x == 0 && tid == 0) st->stop = 1;
@@ -598,7 +668,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         }
         // ---- Select on CTA 0 ----
         if (blockIdx.x == 0) select_on_cta0(a, (float)mu, sel_smem);
-        if (!grid_sync(a.bar, st)) return;
+        if (!grid_sync(a.flags, a.bar, epoch, st)) return;
         if (stamp) st->t_phase[3] = gtimer_ns();
         if (!__ldcg(&st->changed)) break;
 
@@ -616,7 +686,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             const double dn = cta_sum(dsq, shd);             // ||x' - x||^2 from the staged list
             if (tid == 0) { mypart[2] = acc; mypart[3] = dn; }
         }
-        if (!grid_sync(a.bar, st)) return;
+        if (!grid_sync(a.flags, a.bar, epoch, st)) return;
         const double dd = alpha * alpha * grid_partial_sum(a.part, 2, shd);
         const double dn = __ldcg(a.part + 3);
         if (!(dn > 0.0)) break;                               // nothing moves: accept
@@ -777,6 +847,9 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
     a->cap = kTopCandCap;
     a->part = part;
     a->bar = &st->counters[0][0];
+    a->flags = &st->counters[1][0];
+    a->cand_val = reinterpret_cast<float*>(cand + kTopCandCap);
+    a->cand_x = reinterpret_cast<float*>(cand + kTopCandCap) + kTopCandCap;
     a->n = n;
     a->m = m;
     a->s = s;
@@ -802,7 +875,7 @@ size_t iter_smem_bytes(int n, int bits)
     const int G = 32 / bits;
     const size_t gather = (size_t)kListChunk * 8 + (size_t)kIterThreads * G * 4 + (size_t)kIterThreads * 4;
     const size_t nbw = ((size_t)(n + 31) / 32 + 3) & ~(size_t)3;
-    const size_t select = 2048 * 4 + nbw * 4 + 2 * (size_t)kTopCandCap * 4;
+    const size_t select = 2048 * 4 + 2 * nbw * 4 + (size_t)kTopCandCap * 16 + (size_t)kSupportSmem * 4;
     return gather > select ? gather : select;
 }
 

@@ -341,7 +341,7 @@ Plan plan_solve(int m, int n, int s)
     const int rb = gather_row_blocks(m, 2) > gather_row_blocks(m, 8) ? gather_row_blocks(m, 2) : gather_row_blocks(m, 8);
     p.off_rbp = o; o += align256((size_t)rb * 2 * 8);
     p.off_chunk = o; o += align256((size_t)gather_chunks(2 * s) * 8);
-    p.off_cand = o; o += align256((size_t)kTopCandCap * 8);
+    p.off_cand = o; o += align256((size_t)kTopCandCap * 16);     // keys, then values and old x
     p.off_keys = o; o += align256((size_t)n * 4);
     p.off_part = o; o += align256((size_t)1024 * 4 * 8);
     p.total = o;
@@ -566,12 +566,12 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     K.gom.mode = kGatherOmega;
     K.gom.cols = uni;
     K.gom.coef = delta;
-    K.gom.counters = st->counters[1];
+    K.gom.counters = st->counters[0] + 32;
     K.a_om[0] = &K.gom;
     gather_node(K.gom, &K.p_om, K.a_om);
     K.gre = base;
     K.gre.mode = kGatherResid;
-    K.gre.counters = st->counters[2];
+    K.gre.counters = st->counters[0] + 64;
     K.a_re[0] = &K.gre;
     gather_node(K.gre, &K.p_re, K.a_re);
 }
