@@ -40,7 +40,7 @@ import synth  # noqa: E402
 M, N, S, ITERS = 8192, 32768, 256, 300
 METRIC = "NIHT iterations/s"
 UNIT = "iterations/s"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemv_t_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemv_t_traffic.txt")
 
 
 def parse():
@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gemv-launches", type=int, default=200)
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the solver's kernels one by one instead of one graph (for kernel profilers, "
+                         "which do not see the kernels of graphs with conditional nodes)")
     return ap.parse_args()
 
 
@@ -195,15 +198,22 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_for_kernel(bits):
-    """DRAM bytes per launch of the gradient kernel from a committed ncu summary,
-    only while the kernel source is unchanged since the capture."""
+def traffic_for_kernel(bits, m, n):
+    """DRAM bytes per launch of the gradient kernel from the committed ncu summary
+    (profiles/gemv_t_traffic.txt), only while the kernel source is unchanged since
+    the capture and for the captured shape."""
     try:
-        d = json.load(open(TRAFFIC_FILE))
+        d = {}
+        for line in open(TRAFFIC_FILE):
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                d[k] = v
         src = open(os.path.join(ROOT, "paper_1802_04907_gb300", "csrc", "gemv.cu"), "rb").read()
         if d.get("gemv_cu_sha1") != hashlib.sha1(src).hexdigest():
             return None
-        return d.get("bytes_per_launch", {}).get(str(bits))
+        v = d.get(f"bits{bits}_m{m}_n{n}")
+        return int(v) if v is not None else None
     except Exception:
         return None
 
@@ -231,7 +241,7 @@ def run_ours(args):
     y = y_h.to(dev)
     bits = args.bits
     codes = q.quantize_problem(phi, y, bits, bits, seed=rank)
-    solver = q.Solver(args.m, args.n, args.s, args.iters, device=dev)
+    solver = q.Solver(args.m, args.n, args.s, args.iters, device=dev, eager=args.eager)
 
     def step():
         q.quantize_problem(phi, y, bits, bits, seed=rank, out=codes)
@@ -302,7 +312,7 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (gemv_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_for_kernel(bits), "kernel": "k_gemv_t (g = Q1^T r)",
+                "traffic": traffic_for_kernel(bits, args.m, args.n), "kernel": "k_gemv_t (g = Q1^T r)",
                 "avg_launch_us": gemv_ms * 1e3, "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
@@ -337,10 +347,9 @@ def run_ours(args):
                "h2d_bytes_per_step": int(p.phi.nbytes + p.y.nbytes),
                "d2h_bytes_per_step": int(4 * args.n + 4 * args.s + q.REPORT_BYTES)}
 
-    # kernels launched per step: 2 max-abs + 3 quantize, 3 in the solver's set-up,
-    # 5 per iteration (step size, threshold, backtracking test, residual, gradient)
-    # plus 2 per step-size shrink
-    launches_per_step = 5 + 3 + 5 * iters_done + 2 * rep.backtracks
+    # kernels launched per step: 2 max-abs + 3 quantize, 3 in the solver's set-up, then per
+    # iteration the persistent iteration kernel and the gradient kernel (shrinks stay inside)
+    launches_per_step = 5 + 3 + 2 * iters_done
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(p, bits, args.iters)
@@ -357,7 +366,10 @@ def run_ours(args):
                 "arith": "codes x 24-bit fixed-point residual via dp4a, exact int accumulation; FP32 vectors; "
                          "FP64 step size and norms",
                 "report": {"iters_run": rep.iters_run, "backtracks": rep.backtracks,
-                           "support_changes": rep.support_changes, "resid_norm2": rep.resid_norm2}}
+                           "support_changes": rep.support_changes, "resid_norm2": rep.resid_norm2,
+                           "full_selects": rep.full_selects,
+                           "iteration_phases_us": [round(v, 2) for v in rep.phase_us[:7]]},
+                "driver": "eager launches" if args.eager else "one CUDA graph per solve"}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
