@@ -702,6 +702,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
 // Codes are extracted with one mask per four codes: (w & (mask << b k)) gives
 // the codes of position k times 2^(b k); products are summed per position and
 // the positions are combined at the end with exact right shifts.
+// In the solver's loop the epilogue also prepares the next threshold: g on the
+// support goes to its support position, and a column outside the support with
+// |g| >= tau_g is appended to the candidate list (the largest |g| below tau_g is
+// kept per CTA and merged with one atomic).
 // ---------------------------------------------------------------------------
 template <int BITS, int NPL>
 __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
@@ -712,6 +716,8 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
     constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
     extern __shared__ __align__(16) uint32_t limb[];    // [3][E][P][4]
     __shared__ long long red_r[8];
+    __shared__ unsigned bmax_cta;
+    __shared__ double outscale_sh;
 
     if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
         const int guard = ++a.st->outer_guard;
@@ -749,11 +755,20 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red_r[warp] = v;
     }
+    if (threadIdx.x == 0) bmax_cta = 0u;
+    if (threadIdx.x == 32) {
+        // alpha 2^-sh, once per CTA: FP64 division is slow on this GPU, and every warp
+        // that did it would hold back its first loads
+        const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
+        outscale_sh = ldexp(alpha, -sh);
+    }
     __syncthreads();
+    // candidate filter of the solver's next threshold (off: tau_g == 0 or no position map)
+    const uint32_t tau_g = a.pos ? a.st->tau_g_bits : 0u;
+    unsigned bmax = 0;
+    int pos_cur = -1;
     long long R = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) R += red_r[w];
-    const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
-    const double outscale = ldexp(alpha, -sh);
     const uint4* L0 = reinterpret_cast<const uint4*>(limb);
     const uint4* L1 = L0 + (size_t)E * P;
     const uint4* L2 = L0 + (size_t)2 * E * P;
@@ -824,8 +839,25 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
         }
         if (lane == 0) {
             const long long T = 2 * S - (long long)(L - 1) * R;
-            a.g[jj] = (float)((double)T * outscale);
+            const float gv = (float)((double)T * outscale_sh);
+            a.g[jj] = gv;
+            if (pos_cur >= 0) {
+                a.gsup[pos_cur] = gv;
+            } else if (tau_g) {
+                const uint32_t kb = __float_as_uint(gv) & 0x7fffffffu;
+                if (kb >= tau_g) {
+                    const unsigned slot = atomicAdd(&a.st->gcand_count, 1u);
+                    if (slot < (unsigned)a.gcap)
+                        a.gcand[slot] = ((unsigned long long)__float_as_uint(gv) << 32) | (unsigned)jj;
+                } else {
+                    bmax = max(bmax, kb);
+                }
+            }
         }
+    };
+    // support position of column jj (lane 0 only; read early, used by finish_column)
+    auto fetch_pos = [&](int jj) {
+        if (a.pos && lane == 0) pos_cur = __ldg(a.pos + jj);
     };
     auto advance = [&](int& jj, int& bb) {
         if (++bb == nb) { bb = 0; jj += W; }
@@ -837,6 +869,7 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
         int jB = j, pB = pb;
         advance(jB, pB);
         if (jB < n) load_batch(cB, jB, pB);
+        if (pb == 0) fetch_pos(j);
         use_batch(cA, pb);
         if (pb == nb - 1) finish_column(j);
         j = jB; pb = pB;
@@ -844,9 +877,15 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
         int jA = j, pA = pb;
         advance(jA, pA);
         if (jA < n) load_batch(cA, jA, pA);
+        if (pb == 0) fetch_pos(j);
         use_batch(cB, pb);
         if (pb == nb - 1) finish_column(j);
         j = jA; pb = pA;
+    }
+    if (tau_g) {
+        if (lane == 0 && bmax) atomicMax(&bmax_cta, bmax);
+        __syncthreads();
+        if (threadIdx.x == 0 && bmax_cta) atomicMax(&a.st->bmax_g, bmax_cta);
     }
 }
 

@@ -46,9 +46,13 @@ struct State {
     unsigned cand_count;   // keys >= tau found by the filter
     unsigned below_max;    // largest key < tau seen by the filter
     int full_selects;      // selections that ranked all n entries
+    unsigned tau_g_bits;   // |g| threshold of the gradient kernel's candidates (float bits, 0 = off)
+    unsigned gcand_count;  // entries outside G with |g| >= tau_g appended by the gradient kernel
+    unsigned bmax_g;       // largest |g| (float bits) outside G below tau_g
     unsigned long long t_phase[8];   // device clock at phase boundaries of the last iteration
-    unsigned counters[2][1024];  // arrival counters of the column-subset products; iteration-kernel
-                                 // barrier words (row 0) and per-CTA barrier epochs (row 1)
+    unsigned long long bar_count;    // grid-barrier arrivals of the iteration kernel (only grows)
+    unsigned counters[2][1024];  // arrival counters of the column-subset products (row 0; the
+                                 // iteration kernel's commit counter is word 2)
 };
 
 // Column-subset product modes (one epilogue each).
@@ -92,6 +96,11 @@ struct GemvTArgs {
     State* st;                  // non-null in the solver: skip when st->stop
     unsigned long long h_outer; // outer-loop handle (solver loop body only): set by thread 0 of CTA 0
     unsigned* err;              // optional: set to 1 when a device-side wait runs out (no solver state)
+    // solver loop body with the fast-path iteration kernel (nullptr elsewhere)
+    const int32_t* pos;         // position of every column in the support G, -1 outside
+    float* gsup;                // out: g on G, by position
+    unsigned long long* gcand;  // out: columns outside G with |g| >= st->tau_g_bits: (g bits << 32) | column
+    int gcap;                   // capacity of gcand (st->gcand_count counts past it)
 };
 
 struct TopArgs {
@@ -123,6 +132,7 @@ struct InitArgs {
     float* yhat;
     float* r;
     float* x;
+    int32_t* pos;               // optional: position map of the fast path, set to -1
     int n, m, s, iters;
     State* st;
     qiht_report* report;
@@ -150,12 +160,21 @@ cudaError_t launch_top(const TopArgs& a, cudaStream_t s);
 // One iteration after the gradient product as one persistent kernel (iter.cu).
 struct IterArgs;
 constexpr size_t kIterArgsMax = 1024;     // bytes reserved for the iteration kernel's arguments
-size_t iter_smem_bytes(int n, int bits);
+constexpr int kPartStride = 8;            // doubles of per-CTA partials of the iteration kernel
 int iter_grid();
+bool iter_fast(int s);                    // the fast-path iteration kernel serves this support size
+// Buffers of the fast path (ignored by the other kernel).
+struct IterFastBufs {
+    int32_t* pos;                         // n
+    float* xs;                            // s
+    float* gsup;                          // s
+    unsigned long long* gcand;            // gcap
+    int gcap;
+};
 void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* support, int32_t* sel, float* val,
                int32_t* uni, float* delta, const float* yhat, float* r, uint32_t* keys, unsigned long long* cand,
-               double* part, int n, int m, int s, double k, double c, int max_bt, qiht_report* report,
-               const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore, void** argbuf);
+               double* part, const IterFastBufs& fb, int n, int m, int s, double k, double c, int max_bt,
+               qiht_report* report, const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore, void** argbuf);
 size_t iter_args_bytes();
 
 int gather_row_blocks(int rows, int bits);

@@ -32,87 +32,75 @@ __device__ __forceinline__ unsigned long long gtimer_ns()
     return t;
 }
 
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-// Grid barrier without contended atomics: CTA c release-stores the barrier's epoch in
-// its own flag; CTA 0 acquires every flag (in parallel) and then releases the epoch in
-// the generation word, which every CTA acquires. Epochs only grow (wrap-safe
-// comparisons), so flags never need resetting. Waiting is bounded by %globaltimer;
-// a timeout marks the state and returns false.
-__device__ bool grid_sync(unsigned* flags, unsigned* gen, unsigned& epoch, State* st)
+// Grid barrier on one 64-bit arrival counter that only grows: thread 0 of every CTA
+// adds 1 with release semantics and waits (acquire) until the counter reaches the
+// barrier's target, a multiple of the grid size. Only thread 0 of a CTA holds the
+// target. Waiting is bounded by %globaltimer; a timeout marks the state and returns false.
+__device__ bool grid_sync(unsigned long long* cnt, unsigned long long& target, State* st)
 {
     __shared__ int ok_sh;
-    ++epoch;
     __syncthreads();
     if (threadIdx.x == 0) {
+        target += gridDim.x;
         __threadfence();
-        st_release(flags + blockIdx.x, epoch);
-        ok_sh = 1;
-    }
-    __syncthreads();
-    if (blockIdx.x == 0) {
+        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
         int ok = 1;
-        for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
-            if ((int)(ld_acquire(flags + c) - epoch) < 0) {
-                const unsigned long long t0 = gtimer_ns();
-                while ((int)(ld_acquire(flags + c) - epoch) < 0) {
-                    if (gtimer_ns() - t0 > kBarrierBudgetNs) { ok = 0; break; }
-                }
-            }
-        }
-        ok = __syncthreads_and(ok);
-        if (threadIdx.x == 0) {
-            if (ok) {
-                __threadfence();
-                st_release(gen, epoch);
-            } else {
-                st->status = QIHT_ERR_TIMEOUT;
-                st->stop = 1;
-                ok_sh = 0;
-            }
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && ok_sh) {
-        if ((int)(ld_acquire(gen) - epoch) < 0) {
+        if ((long long)(ld_acquire64(cnt) - target) < 0) {
             const unsigned long long t0 = gtimer_ns();
-            while ((int)(ld_acquire(gen) - epoch) < 0) {
-                if (gtimer_ns() - t0 > kBarrierBudgetNs) {
-                    ok_sh = 0;
-                    st->status = QIHT_ERR_TIMEOUT;
-                    st->stop = 1;
-                    break;
-                }
+            while ((long long)(ld_acquire64(cnt) - target) < 0) {
+                if (gtimer_ns() - t0 > kBarrierBudgetNs) { ok = 0; break; }
             }
         }
-        __threadfence();
+        if (!ok) {
+            st->status = QIHT_ERR_TIMEOUT;
+            st->stop = 1;
+        }
+        ok_sh = ok;
     }
     __syncthreads();
     return ok_sh != 0;
 }
 
-// Deterministic sum of one double per thread (fixed shuffle tree, warps in order).
-__device__ double cta_sum(double v, double* sh)
+// Barrier target of the launch's first barrier: the counter is a multiple of the grid
+// size between launches, and no CTA can complete the first barrier before this one arrives.
+__device__ __forceinline__ unsigned long long barrier_base(const unsigned long long* cnt)
+{
+    unsigned long long c;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(cnt) : "memory");
+    return c - c % gridDim.x;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic sum of one double per thread over threads [0, nact) (the others are not
+// read); fixed shuffle trees, and only the warps that hold values do FP64 work (FP64
+// throughput is low on this GPU). Every thread gets the result.
+__device__ double cta_sum_n(double v, int nact, double* sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = min((nact + 31) >> 5, (int)(blockDim.x >> 5));
+    if (w < nw) {
+        if ((int)threadIdx.x >= nact) v = 0.0;
+        v = warp_sum_d(v);
+        if (lane == 0) sh[w] = v;
+    }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
-        sh[32] = t;
+    if (w == 0) {
+        double t = lane < nw ? sh[lane] : 0.0;
+        t = warp_sum_d(t);
+        if (lane == 0) sh[32] = t;
     }
     __syncthreads();
     const double r = sh[32];
@@ -120,16 +108,18 @@ __device__ double cta_sum(double v, double* sh)
     return r;
 }
 
+__device__ double cta_sum(double v, double* sh) { return cta_sum_n(v, blockDim.x, sh); }
+
 __device__ unsigned cta_max(unsigned v, unsigned* sh)
 {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     v = __reduce_max_sync(0xffffffffu, v);
+    if (lane == 0) sh[w] = v;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = max(t, sh[i]);
-        sh[32] = t;
+    if (w == 0) {
+        unsigned t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+        t = __reduce_max_sync(0xffffffffu, t);
+        if (lane == 0) sh[32] = t;
     }
     __syncthreads();
     const unsigned r = sh[32];
@@ -137,27 +127,78 @@ __device__ unsigned cta_max(unsigned v, unsigned* sh)
     return r;
 }
 
-// Sum over CTAs of partial slot `k` of the per-CTA partials (every CTA gets the same value).
+// Sum over CTAs of partial slot `k` (warp 0 loads them, eight per lane in flight, and
+// adds them in a fixed order); every thread gets the same value.
 __device__ double grid_partial_sum(const double* part, int k, double* sh)
 {
-    double v = 0.0;
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) v += __ldcg(part + 4 * c + k);
-    return cta_sum(v, sh);
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int c0 = lane; c0 < (int)gridDim.x; c0 += 32 * 8) {
+            double t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + 32 * u;
+                t[u] = c < (int)gridDim.x ? __ldcg(part + kPartStride * c + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v += t[u];
+        }
+        v = warp_sum_d(v);
+        if (lane == 0) sh[32] = v;
+    }
+    __syncthreads();
+    const double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Sum of slot ks and maximum of slot km over CTAs in one pass (warp 0).
+__device__ void grid_partial_sum_max(const double* part, int ks, int km, double* sh, double* sum, double* mx)
+{
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        double v = 0.0, w = 0.0;
+        for (int c0 = lane; c0 < (int)gridDim.x; c0 += 32 * 4) {
+            double t[4], u[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int c = c0 + 32 * i;
+                t[i] = c < (int)gridDim.x ? __ldcg(part + kPartStride * c + ks) : 0.0;
+                u[i] = c < (int)gridDim.x ? __ldcg(part + kPartStride * c + km) : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { v += t[i]; w = fmax(w, u[i]); }
+        }
+        v = warp_sum_d(v);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (lane == 0) { sh[30] = v; sh[31] = w; }
+    }
+    __syncthreads();
+    *sum = sh[30];
+    *mx = sh[31];
+    __syncthreads();
 }
 
 __device__ double grid_partial_max(const double* part, int k, double* sh)
 {
-    double v = 0.0;
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) v = fmax(v, __ldcg(part + 4 * c + k));
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int c0 = lane; c0 < (int)gridDim.x; c0 += 32 * 8) {
+            double t[8];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmax(t, sh[i]);
-        sh[32] = t;
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + 32 * u;
+                t[u] = c < (int)gridDim.x ? __ldcg(part + kPartStride * c + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v = fmax(v, t[u]);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) sh[32] = v;
     }
     __syncthreads();
     const double r = sh[32];
@@ -180,11 +221,17 @@ struct IterArgs {
     uint32_t* keys;             // |x + mu g| of every entry (fallback select)
     unsigned long long* cand;   // filter candidates
     int cap;
-    double* part;               // [grid][4] per-CTA partials
-    unsigned* bar;              // [0] generation of the grid barrier, [2] commit counter
-    unsigned* flags;            // [grid] barrier epoch of every CTA
+    double* part;               // [grid][kPartStride] per-CTA partials
+    unsigned* bar;              // [2] commit counter
+    unsigned long long* gbar;   // grid-barrier arrival counter
     float* cand_val;            // x + mu g of each candidate (same slot as cand)
     float* cand_x;              // x of each candidate
+    // fast-path iteration kernel (k_iter_fast)
+    int32_t* pos;               // position of every entry in the support G, -1 outside
+    float* xs;                  // x on G, in support order
+    const float* gsup;          // g on G, by position (written by the gradient kernel)
+    const unsigned long long* gcand;   // gradient-kernel candidates: (g bits << 32) | index
+    int gcap;                   // capacity of gcand
     int n, m, s;
     double k, c;
     int max_bt;
@@ -208,65 +255,44 @@ __device__ __forceinline__ RowBlock row_block(int ld)
     return b;
 }
 
-// z (for this CTA's rows) = sum over the list of coef_j * code column j, in list order
-// per slice and slices in order; the result stays in red[t*G + k] of the reducer threads:
-// row word wl = t / G, row in word k = t % G, valid for t < wpc*G.
-// coef_mode: 0 = coef[jj], 1 = g[list[jj]].
+// z (for this CTA's rows) += sum over a list in shared memory of coef_j * code column j:
+// slice sl takes entries sl, sl + nsl, ... in order (four loads in flight per step).
 template <int BITS>
-__device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_t* list, const float* coef,
-                             int coef_mode, int count, int32_t* s_list, float* s_coef, float* red, float* zrow,
-                             double* coef_sq = nullptr)
+__device__ __forceinline__ void rows_accum(const IterArgs& a, const RowBlock& rb, const int32_t* s_list,
+                                           const float* s_coef, int cn, int sl, int q, float (&z)[32 / BITS])
 {
     constexpr int G = 32 / BITS;
     constexpr int L = 1 << BITS;
-    const int t = threadIdx.x;
-    const int wl = t % rb.wpc, sl = t / rb.wpc;
-    const int q = rb.w0 + wl;
-    const bool active = sl < rb.nsl && q < rb.w1;
+    constexpr int U = 8;                       // entries of a slice whose loads are in flight together
     const int ld = a.Q.ld;
-    float z[G];
+    for (int jj = sl; jj < cn; jj += U * rb.nsl) {
+        uint32_t w[U];
+        float cf[U];
 #pragma unroll
-    for (int k = 0; k < G; ++k) z[k] = 0.0f;
-    for (int c0 = 0; c0 < count; c0 += kListChunk) {
-        const int cn = min(kListChunk, count - c0);
-        __syncthreads();
-        for (int i = t; i < cn; i += blockDim.x) {
-            const int col = __ldcg(list + c0 + i);
-            s_list[i] = col;
-            const float cf = coef_mode == 1 ? __ldcg(a.g + col) : __ldcg(coef + c0 + i);
-            s_coef[i] = cf;
-            if (coef_sq) *coef_sq += (double)cf * (double)cf;      // this thread's entries, in order
+        for (int u = 0; u < U; ++u) {
+            const int e = jj + u * rb.nsl;
+            const bool in = e < cn;
+            w[u] = in ? __ldg(a.Q.words + (size_t)s_list[e] * ld + q) : 0u;
+            cf[u] = in ? s_coef[e] : 0.0f;         // past the end: adds exact zeros
         }
-        __syncthreads();
-        if (active) {
-            int jj = sl;
-            for (; jj + 3 * rb.nsl < cn; jj += 4 * rb.nsl) {
-                uint32_t w[4];
-                float cf[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    w[u] = __ldg(a.Q.words + (size_t)s_list[jj + u * rb.nsl] * ld + q);
-                    cf[u] = s_coef[jj + u * rb.nsl];
-                }
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int k = 0; k < G; ++k) {
-                        const int code = (int)((w[u] >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
-                        z[k] = fmaf((float)(2 * code - (L - 1)), cf[u], z[k]);
-                    }
+            for (int k = 0; k < G; ++k) {
+                const int code = (int)((w[u] >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
+                z[k] = fmaf((float)(2 * code - (L - 1)), cf[u], z[k]);
             }
-            for (; jj < cn; jj += rb.nsl) {
-                const uint32_t w = __ldg(a.Q.words + (size_t)s_list[jj] * ld + q);
-                const float cf = s_coef[jj];
-#pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    const int code = (int)((w >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
-                    z[k] = fmaf((float)(2 * code - (L - 1)), cf, z[k]);
-                }
-            }
-        }
     }
+}
+
+// Sum of the slices in slice order; the result stays in zrow[t] of the reducer threads:
+// row word wl = t / G, row in word k = t % G, valid for t < wpc*G.
+template <int BITS>
+__device__ __forceinline__ void rows_reduce(const RowBlock& rb, int sl, const float (&z)[32 / BITS], float* red,
+                                            float* zrow)
+{
+    constexpr int G = 32 / BITS;
+    const int t = threadIdx.x;
     __syncthreads();
     if (sl < rb.nsl) {
 #pragma unroll
@@ -284,6 +310,54 @@ __device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_
         zrow[t] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     __syncthreads();
+}
+
+// z (for this CTA's rows) = sum over a list in global memory of coef_j * code column j,
+// staged through shared memory in chunks of kListChunk entries.
+// coef_mode: 0 = coef[jj], 1 = g[list[jj]].
+template <int BITS>
+__device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_t* list, const float* coef,
+                             int coef_mode, int count, int32_t* s_list, float* s_coef, float* red, float* zrow,
+                             double* coef_sq = nullptr)
+{
+    constexpr int G = 32 / BITS;
+    const int t = threadIdx.x;
+    const int wl = t % rb.wpc, sl = t / rb.wpc;
+    const int q = rb.w0 + wl;
+    const bool active = sl < rb.nsl && q < rb.w1;
+    float z[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) z[k] = 0.0f;
+    for (int c0 = 0; c0 < count; c0 += kListChunk) {
+        const int cn = min(kListChunk, count - c0);
+        __syncthreads();
+        for (int i = t; i < cn; i += blockDim.x) {
+            const int col = __ldcg(list + c0 + i);
+            s_list[i] = col;
+            const float cf = coef_mode == 1 ? __ldcg(a.g + col) : __ldcg(coef + c0 + i);
+            s_coef[i] = cf;
+            if (coef_sq) *coef_sq += (double)cf * (double)cf;      // this thread's entries, in order
+        }
+        __syncthreads();
+        if (active) rows_accum<BITS>(a, rb, s_list, s_coef, cn, sl, q, z);
+    }
+    rows_reduce<BITS>(rb, sl, z, red, zrow);
+}
+
+// The same product for a list already in shared memory (no staging).
+template <int BITS>
+__device__ void rows_product_sm(const IterArgs& a, const RowBlock& rb, const int32_t* list_sm, const float* coef_sm,
+                                int count, float* red, float* zrow)
+{
+    constexpr int G = 32 / BITS;
+    const int t = threadIdx.x;
+    const int wl = t % rb.wpc, sl = t / rb.wpc;
+    const int q = rb.w0 + wl;
+    float z[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) z[k] = 0.0f;
+    if (sl < rb.nsl && q < rb.w1) rows_accum<BITS>(a, rb, list_sm, coef_sm, count, sl, q, z);
+    rows_reduce<BITS>(rb, sl, z, red, zrow);
 }
 
 // Radix select of the s-th largest of cnt keys (11/11/10-bit digits), keys read through ld().
@@ -376,20 +450,46 @@ __device__ int cta_excl_scan(int v, int* sh, int* total)
 constexpr int kRankMax = 1024;
 constexpr int kSupportSmem = 4096;       // supports up to this size are staged in shared memory
 
-__device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
+// Shared-memory arrays of the one-CTA select.
+struct SelSmem {
+    unsigned* hist;                  // 2048
+    uint32_t* bitmap;                // ceil(n / 32) rounded up to 4
+    int* wpre;                       // same
+    unsigned long long* cv;          // cap (rank path only)
+    float* cval;                     // cap (rank path only)
+    float* cx;                       // cap (rank path only)
+    int32_t* sup;                    // s (if s <= kSupportSmem)
+};
+
+__device__ __forceinline__ SelSmem sel_smem_layout(const IterArgs& a, unsigned char* smem)
+{
+    const int nbw4 = (((a.n + 31) / 32) + 3) & ~3;
+    SelSmem m;
+    m.hist = reinterpret_cast<unsigned*>(smem);
+    m.bitmap = m.hist + 2048;
+    m.wpre = reinterpret_cast<int*>(m.bitmap + nbw4);
+    m.cv = reinterpret_cast<unsigned long long*>(m.wpre + nbw4);
+    m.cval = reinterpret_cast<float*>(m.cv + a.cap);
+    m.cx = m.cval + a.cap;
+    m.sup = reinterpret_cast<int32_t*>(m.cx + a.cap);
+    return m;
+}
+
+// allow_rank = false: always the radix select over all n keys.
+__device__ void select_on_cta0(const IterArgs& a, float mu, const SelSmem& sm, bool allow_rank)
 {
     State* st = a.st;
     const int n = a.n, s = a.s, tid = threadIdx.x;
     const int lane = tid & 31;
     const int nbw = (n + 31) / 32;
     const int nbw4 = (nbw + 3) & ~3;
-    unsigned* hist = reinterpret_cast<unsigned*>(smem);                       // 2048
-    uint32_t* bitmap = hist + 2048;                                           // nbw4
-    int* wpre = reinterpret_cast<int*>(bitmap + nbw4);                        // nbw4: selected before word w
-    unsigned long long* cv = reinterpret_cast<unsigned long long*>(wpre + nbw4);   // cap
-    float* cval = reinterpret_cast<float*>(cv + a.cap);                       // cap
-    float* cx = cval + a.cap;                                                 // cap
-    int32_t* sup = reinterpret_cast<int32_t*>(cx + a.cap);                    // s (if it fits)
+    unsigned* hist = sm.hist;
+    uint32_t* bitmap = sm.bitmap;
+    int* wpre = sm.wpre;
+    unsigned long long* cv = sm.cv;
+    float* cval = sm.cval;
+    float* cx = sm.cx;
+    int32_t* sup = sm.sup;
     const bool sup_sm = s <= kSupportSmem;
     __shared__ int sh_i[36];
     __shared__ unsigned sh_u[33];
@@ -397,7 +497,8 @@ __device__ void select_on_cta0(const IterArgs& a, float mu, unsigned char* smem)
 
     const int cnt = (int)__ldcg(&st->cand_count);
     const unsigned below_filter = __ldcg(&st->below_max);
-    const bool use_rank = a.cap > 0 && __ldcg(&st->tau_bits) != 0u && cnt >= s && cnt <= min(a.cap, kRankMax);
+    const bool use_rank =
+        allow_rank && a.cap > 0 && __ldcg(&st->tau_bits) != 0u && cnt >= s && cnt <= min(a.cap, kRankMax);
     for (int w = tid; w < nbw4; w += blockDim.x) bitmap[w] = 0u;
     if (tid < 2) sh_k[tid] = 0ull;
     if (sup_sm)
@@ -552,9 +653,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     if (st->stop) return;                       // uniform: read before any barrier
     const bool stamp = blockIdx.x == 0 && threadIdx.x == 0;
     if (stamp) st->t_phase[0] = gtimer_ns();
-    // barrier epochs continue from the generation left by the previous launch; no CTA can
-    // move it on before every CTA has arrived at the first barrier, so all read the same value
-    unsigned epoch = ld_acquire(a.bar);
+    unsigned long long target = threadIdx.x == 0 ? barrier_base(a.gbar) : 0ull;
 
     const RowBlock rb = row_block(a.Q.ld);
     int32_t* s_list = reinterpret_cast<int32_t*>(smem);
@@ -562,11 +661,17 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     float* red = s_coef + kListChunk;                           // kIterThreads * G
     float* zrow = red + kIterThreads * G;                       // kIterThreads
     unsigned char* sel_smem = smem;                             // CTA 0's select reuses the buffer
-    const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
-    const float alpha_f = (float)alpha;
+    // alpha = scale / (L - 1) once per CTA (FP64 division is slow on this GPU); the
+    // first product's barriers publish it
+    __shared__ double s_alpha;
+    __shared__ float s_alpha_f;
+    if (threadIdx.x == 32) {
+        s_alpha = (double)(*a.Q.scale) / (double)(L - 1);
+        s_alpha_f = (float)s_alpha;
+    }
     const int m = a.m, s = a.s, n = a.n;
     const int tid = threadIdx.x;
-    double* mypart = a.part + 4 * blockIdx.x;
+    double* mypart = a.part + kPartStride * blockIdx.x;
 
     // ---- Mu: z = Q2_G g_G, den = alpha^2 ||z||^2, num = ||g_G||^2 ----
     double gsq = 0.0;
@@ -581,11 +686,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         const double num = cta_sum(gsq, shd);                // ||g_G||^2 from the staged coefficients
         if (tid == 0) { mypart[0] = acc; mypart[1] = num; }
     }
-    if (!grid_sync(a.flags, a.bar, epoch, st)) return;
+    if (!grid_sync(a.gbar, target, st)) return;
     if (stamp) st->t_phase[1] = gtimer_ns();
     double mu;
     {
-        const double den = alpha * alpha * grid_partial_sum(a.part, 0, shd);
+        const double den = s_alpha * s_alpha * grid_partial_sum(a.part, 0, shd);
         const double num = __ldcg(a.part + 1);                 // CTA 0's slot
         bool stop = false;
         if (!isfinite(num) || !isfinite(den)) {
@@ -660,15 +765,15 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             if (tid == 0 && bcta) atomicMax(&st->below_max, bcta);
             if (__syncthreads_or(bad) && tid == 0) st->status = QIHT_ERR_NONFINITE;
         }
-        if (!grid_sync(a.flags, a.bar, epoch, st)) return;
+        if (!grid_sync(a.gbar, target, st)) return;
         if (stamp) st->t_phase[2] = gtimer_ns();
         if (__ldcg(&st->status) == QIHT_ERR_NONFINITE) {
             if (blockIdx.x == 0 && tid == 0) st->stop = 1;
             return;
         }
         // ---- Select on CTA 0 ----
-        if (blockIdx.x == 0) select_on_cta0(a, (float)mu, sel_smem);
-        if (!grid_sync(a.flags, a.bar, epoch, st)) return;
+        if (blockIdx.x == 0) select_on_cta0(a, (float)mu, sel_smem_layout(a, sel_smem), true);
+        if (!grid_sync(a.gbar, target, st)) return;
         if (stamp) st->t_phase[3] = gtimer_ns();
         if (!__ldcg(&st->changed)) break;
 
@@ -686,8 +791,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             const double dn = cta_sum(dsq, shd);             // ||x' - x||^2 from the staged list
             if (tid == 0) { mypart[2] = acc; mypart[3] = dn; }
         }
-        if (!grid_sync(a.flags, a.bar, epoch, st)) return;
-        const double dd = alpha * alpha * grid_partial_sum(a.part, 2, shd);
+        if (!grid_sync(a.gbar, target, st)) return;
+        const double dd = s_alpha * s_alpha * grid_partial_sum(a.part, 2, shd);
         const double dn = __ldcg(a.part + 3);
         if (!(dn > 0.0)) break;                               // nothing moves: accept
         const double omega = dd > 0.0 ? dn / dd : INFINITY;
@@ -720,7 +825,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         if (tid < rb.wpc * G) {
             const int row = (rb.w0 + tid / G) * G + tid % G;
             if (rb.w0 + tid / G < rb.w1 && row < m) {
-                const float ri = fmaf(-alpha_f, zrow[tid], __ldcg(a.yhat + row));
+                const float ri = fmaf(-s_alpha_f, zrow[tid], __ldcg(a.yhat + row));
                 a.r[row] = ri;
                 acc = (double)ri * (double)ri;
                 mx = __float_as_uint(ri) & 0x7fffffffu;
@@ -821,13 +926,617 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Fast-path iteration kernel. The threshold's candidates come from the gradient
+// kernel: an entry outside G has x_j = 0, so its key |x_j + mu g_j| = fl(mu |g_j|)
+// orders like |g_j| whatever mu is, and the gradient kernel can keep the entries
+// with |g_j| >= tau_g (and the largest |g_j| below) before mu is known. Every CTA
+// then ranks G together with the candidates in its own shared memory and gets the
+// same H_s, so no grid barrier separates the step size from the residual when the
+// support does not move. The selection is provably the full one when the s-th key
+// of the ranked set exceeds fl(mu max_rejected |g|); otherwise (and in the first
+// iteration, before the gradient kernel has a support to filter against) the keys
+// of all n entries go to the one-CTA radix select as in k_iter.
+// Every CTA commits its own slice of x and of the position map; the last CTA to
+// finish writes G, x_G and the scalars.
+// ---------------------------------------------------------------------------
+constexpr int kFastMaxS = 1024;          // largest s of the fast path (lists held in shared memory)
+constexpr int kTieMax = 64;              // ties at the s-th key ranked by index in shared memory
+
+struct FastSm {
+    uint32_t* key;                       // [s + gcap] |x + mu g| of G, then of the candidates
+    int32_t* el_idx;                     // [s + gcap]
+    float* el_x;                         // [s + gcap]
+    float* el_g;                         // [s + gcap]
+    uint32_t* bitmap;                    // [nbw4] selection
+    int* wpre;                           // [nbw4]
+    int32_t* u_idx;                      // [2s] G' (ascending), then G \ G'
+    float* u_val;                        // [s]  x' on G'
+    float* u_delta;                      // [2s] x' - x on the u_idx list
+    unsigned* hist;                      // [256]
+    int32_t* tie;                        // [kTieMax]
+    float* red;                          // [kIterThreads * G]
+    float* zrow;                         // [kIterThreads]
+};
+
+__host__ __device__ inline size_t fast_smem_bytes(int n, int s, int gcap, int G)
+{
+    const size_t el = (size_t)s + (size_t)gcap;
+    const size_t nbw4 = ((size_t)(n + 31) / 32 + 3) & ~(size_t)3;
+    return el * 16 + nbw4 * 8 + (size_t)s * 20 + 256 * 4 + (size_t)kTieMax * 4 + (size_t)kIterThreads * G * 4 +
+           (size_t)kIterThreads * 4;
+}
+
+__device__ __forceinline__ FastSm fast_smem_layout(const IterArgs& a, unsigned char* smem, int G)
+{
+    const int el = a.s + a.gcap;
+    const int nbw4 = (((a.n + 31) / 32) + 3) & ~3;
+    FastSm m;
+    m.key = reinterpret_cast<uint32_t*>(smem);
+    m.el_idx = reinterpret_cast<int32_t*>(m.key + el);
+    m.el_x = reinterpret_cast<float*>(m.el_idx + el);
+    m.el_g = m.el_x + el;
+    m.bitmap = reinterpret_cast<uint32_t*>(m.el_g + el);
+    m.wpre = reinterpret_cast<int*>(m.bitmap + nbw4);
+    m.u_idx = reinterpret_cast<int32_t*>(m.wpre + nbw4);
+    m.u_val = reinterpret_cast<float*>(m.u_idx + 2 * a.s);
+    m.u_delta = m.u_val + a.s;
+    m.hist = reinterpret_cast<unsigned*>(m.u_delta + 2 * a.s);
+    m.tie = reinterpret_cast<int32_t*>(m.hist + 256);
+    m.red = reinterpret_cast<float*>(m.tie + kTieMax);
+    m.zrow = m.red + kIterThreads * G;
+    return m;
+}
+
+// Radix select (8-bit digits, most significant first) of the s-th largest of cnt keys
+// in shared memory. Stops early when the digit's bucket holds exactly the keys still
+// needed (then every key of the bucket is selected): *depth_out = last digit examined
+// (3 = all four), and the return value has the digits found so far. Otherwise the
+// result is the s-th key itself and *need_out says how many keys equal to it belong
+// to the s largest.
+__device__ uint32_t radix_select8(const uint32_t* key, int cnt, int s, unsigned* hist, int* sh_i, int* need_out,
+                                  int* depth_out)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint32_t prefix = 0;
+    int need = s;
+    int depth = 3;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        if (tid < 256) hist[tid] = 0;
+        __syncthreads();
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const uint32_t k = key[e];
+            if (pass == 0 || (k >> (shift + 8)) == (prefix >> (shift + 8))) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // lane l holds bins 255 - 8l down to 248 - 8l (descending key order)
+            int c[8];
+            int tot = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { c[i] = (int)hist[255 - 8 * lane - i]; tot += c[i]; }
+            int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int excl = incl - tot;
+            if (excl < need && need <= incl) {
+                int run = excl;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (run + c[i] >= need) {
+                        sh_i[0] = 255 - 8 * lane - i;
+                        sh_i[1] = run;
+                        sh_i[2] = (run + c[i] == need);        // the whole bucket is taken
+                        break;
+                    }
+                    run += c[i];
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)sh_i[0] << shift;
+        need -= sh_i[1];
+        if (sh_i[2] && pass < 3) { depth = pass; break; }
+    }
+    __syncthreads();
+    *need_out = need;
+    *depth_out = depth;
+    return prefix;
+}
+
+struct SelResult {
+    int changed, uc;
+    float kth0, kth1;
+};
+
+// H_s over G and the gradient kernel's candidates, in this CTA. Returns false (the
+// same in every CTA) when the ranked set cannot be shown to hold the full selection.
+// When G' = G the lists are G itself (no bitmap is built).
+__device__ bool select_fast(const IterArgs& a, const FastSm& sm, int cnt, float muf, uint32_t outside_max,
+                            SelResult& out)
+{
+    const int s = a.s, n = a.n, tid = threadIdx.x;
+    __shared__ int sh_i[36];
+    __shared__ unsigned sh_u[33];
+    __shared__ int tie_n;
+    int bad = 0;
+    for (int e = tid; e < cnt; e += blockDim.x) {
+        const uint32_t k = __float_as_uint(fmaf(muf, sm.el_g[e], sm.el_x[e])) & 0x7fffffffu;
+        bad |= k > 0x7f800000u;
+        sm.key[e] = k;
+    }
+    if (tid == 0) tie_n = 0;
+    if (__syncthreads_or(bad)) return false;                   // NaN: the full select reports it
+    int need = 0, depth = 3;
+    const uint32_t P = radix_select8(sm.key, cnt, s, sm.hist, sh_i, &need, &depth);
+    uint32_t T;
+    int eq_total = 0;
+    bool tie_rank = false;
+    unsigned below = 0;
+    if (depth < 3) {
+        // every key of the bucket (top 8 (depth + 1) bits = P's) is taken: T = its smallest key
+        const int shift = 24 - 8 * depth;
+        unsigned inv = 0;
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const uint32_t k = sm.key[e];
+            if ((k >> shift) == (P >> shift)) inv = max(inv, ~k);
+        }
+        T = ~cta_max(inv, sh_u);
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const uint32_t k = sm.key[e];
+            if (k < T) below = max(below, k);
+        }
+        below = cta_max(below, sh_u);
+        if (!(T > outside_max)) return false;
+    } else {
+        T = P;
+        int eq = 0;
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const uint32_t k = sm.key[e];
+            eq += (k == T);
+            if (k < T) below = max(below, k);
+        }
+        (void)cta_excl_scan(eq, sh_i, &eq_total);
+        below = cta_max(below, sh_u);
+        // every key outside the set is <= outside_max: the set decides H_s if its s-th key is larger
+        if (!(T > outside_max) || (eq_total > need && eq_total > kTieMax)) return false;
+        tie_rank = eq_total > need;
+        if (tie_rank) {
+            for (int e = tid; e < cnt; e += blockDim.x)
+                if (sm.key[e] == T) sm.tie[atomicAdd(&tie_n, 1)] = sm.el_idx[e];
+            __syncthreads();
+        }
+    }
+    auto taken = [&](int e) -> bool {
+        const uint32_t k = sm.key[e];
+        if (k != T) return k > T;
+        if (!tie_rank) return true;
+        const int j = sm.el_idx[e];
+        int r = 0;                                             // equal keys: lower index first
+        for (int i = 0; i < eq_total; ++i) r += sm.tie[i] < j;
+        return r < need;
+    };
+    out.kth0 = __uint_as_float(T);
+    out.kth1 = tie_rank ? __uint_as_float(T) : __uint_as_float(max(below, outside_max));
+    // G' = G exactly when every entry of G is taken (s are taken in all)
+    int left = 0;
+    for (int q = tid; q < s; q += blockDim.x) left |= !taken(q);
+    const int diff = __syncthreads_or(left);
+    out.changed = diff;
+    if (!diff) {
+        for (int q = tid; q < s; q += blockDim.x) {
+            sm.u_idx[q] = sm.el_idx[q];
+            sm.u_val[q] = fmaf(muf, sm.el_g[q], sm.el_x[q]);
+        }
+        out.uc = s;
+        __syncthreads();
+        return true;
+    }
+    const int nbw = (n + 31) / 32;
+    const int nbw4 = (nbw + 3) & ~3;
+    for (int w = tid; w < nbw4; w += blockDim.x) sm.bitmap[w] = 0u;
+    __syncthreads();
+    for (int e = tid; e < cnt; e += blockDim.x)
+        if (taken(e)) {
+            const int j = sm.el_idx[e];
+            atomicOr(&sm.bitmap[j >> 5], 1u << (j & 31));
+        }
+    __syncthreads();
+    {
+        const int wpt = (nbw + blockDim.x - 1) / blockDim.x;
+        const int w0 = min(nbw, tid * wpt), w1 = min(nbw, w0 + wpt);
+        int c = 0;
+        for (int w = w0; w < w1; ++w) c += __popc(sm.bitmap[w]);
+        int total;
+        int pre = cta_excl_scan(c, sh_i, &total);
+        for (int w = w0; w < w1; ++w) { sm.wpre[w] = pre; pre += __popc(sm.bitmap[w]); }
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt; e += blockDim.x) {
+        const int j = sm.el_idx[e];
+        const int w = j >> 5;
+        const uint32_t bm = sm.bitmap[w];
+        if ((bm >> (j & 31)) & 1u) {
+            const int p = sm.wpre[w] + __popc(bm & ((1u << (j & 31)) - 1u));
+            const float xj = sm.el_x[e];
+            const float v = fmaf(muf, sm.el_g[e], xj);
+            sm.u_idx[p] = j;
+            sm.u_val[p] = v;
+            sm.u_delta[p] = v - xj;
+        }
+    }
+    int extra = 0;
+    {
+        // G \ G' after G', in support order
+        const int sper = (s + blockDim.x - 1) / blockDim.x;
+        const int q0 = min(s, tid * sper), q1 = min(s, q0 + sper);
+        int cntx = 0;
+        for (int q = q0; q < q1; ++q) {
+            const int j = sm.el_idx[q];
+            cntx += !((sm.bitmap[j >> 5] >> (j & 31)) & 1u);
+        }
+        int p = cta_excl_scan(cntx, sh_i, &extra);
+        for (int q = q0; q < q1; ++q) {
+            const int j = sm.el_idx[q];
+            if (!((sm.bitmap[j >> 5] >> (j & 31)) & 1u)) {
+                sm.u_idx[s + p] = j;
+                sm.u_delta[s + p] = -sm.el_x[q];
+                ++p;
+            }
+        }
+    }
+    __syncthreads();
+    out.uc = s + extra;
+    return true;
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
+{
+    constexpr int G = 32 / BITS;
+    constexpr int L = 1 << BITS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double shd[33];
+    __shared__ unsigned shu[33];
+    __shared__ double s_alpha;
+    __shared__ float s_alpha_f, s_muf;
+    __shared__ int s_code;
+    State* st = a.st;
+    if (st->stop) return;                       // uniform: read before any barrier
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool stamp = blockIdx.x == 0 && tid == 0;
+    if (stamp) st->t_phase[0] = gtimer_ns();
+    // FP64 work (low throughput on this GPU) is done by single threads or single warps
+    unsigned long long target = 0;
+    if (tid == 0) target = barrier_base(a.gbar);
+    if (tid == 32) {
+        const double al = (double)(*a.Q.scale) / (double)(L - 1);
+        s_alpha = al;
+        s_alpha_f = (float)al;
+    }
+
+    const RowBlock rb = row_block(a.Q.ld);
+    const FastSm sm = fast_smem_layout(a, smem, G);
+    const int m = a.m, s = a.s, n = a.n;
+    double* mypart = a.part + kPartStride * blockIdx.x;
+    const int nbw4 = (((n + 31) / 32) + 3) & ~3;
+    const int nrow_thr = rb.wpc * G;            // threads that hold one row of this CTA
+
+    // ---- G, x_G, g_G and the candidates into shared memory ----
+    const bool first = __ldcg(&st->iter) == 0;   // the gradient kernel has not filtered yet
+    const uint32_t tau_g = __ldcg(&st->tau_g_bits);
+    const unsigned ncand = __ldcg(&st->gcand_count);
+    const bool cand_ok = !first && tau_g != 0u && ncand <= (unsigned)a.gcap;
+    const int cnt = cand_ok ? (int)ncand : 0;
+    const uint32_t bmax_g = __ldcg(&st->bmax_g);
+    for (int q = tid; q < s; q += blockDim.x) {
+        const int j = __ldcg(a.support + q);
+        sm.el_idx[q] = j;
+        sm.el_x[q] = first ? __ldcg(a.x + j) : __ldcg(a.xs + q);
+        sm.el_g[q] = first ? __ldcg(a.g + j) : __ldcg(a.gsup + q);
+    }
+    for (int i = tid; i < cnt; i += blockDim.x) {
+        const unsigned long long c = __ldcg(a.gcand + i);
+        sm.el_idx[s + i] = (int)(uint32_t)c;
+        sm.el_x[s + i] = 0.0f;
+        sm.el_g[s + i] = __uint_as_float((uint32_t)(c >> 32));
+    }
+    __syncthreads();
+    const float alpha_f = s_alpha_f;
+
+    // ---- Mu: z = Q2_G g_G, den = alpha^2 ||z||^2, num = ||g_G||^2 (CTA 0's warp 0) ----
+    {
+        double num = 0.0;
+        if (blockIdx.x == 0 && tid < 32) {
+            for (int q = lane; q < s; q += 32) num += (double)sm.el_g[q] * (double)sm.el_g[q];
+            num = warp_sum_d(num);
+        }
+        rows_product_sm<BITS>(a, rb, sm.el_idx, sm.el_g, s, sm.red, sm.zrow);
+        double acc = 0.0;
+        if (tid < nrow_thr) {
+            const int row = (rb.w0 + tid / G) * G + tid % G;
+            if (rb.w0 + tid / G < rb.w1 && row < m) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
+        }
+        acc = cta_sum_n(acc, nrow_thr, shd);
+        if (tid == 0) {
+            mypart[0] = acc;
+            if (blockIdx.x == 0) mypart[1] = num;
+        }
+    }
+    if (!grid_sync(a.gbar, target, st)) return;
+    if (stamp) st->t_phase[1] = gtimer_ns();
+    double mu = 0.0;                             // meaningful in thread 0
+    {
+        const double densum = grid_partial_sum(a.part, 0, shd);
+        if (tid == 0) {
+            const double den = s_alpha * s_alpha * densum;
+            const double num = __ldcg(a.part + 1);             // CTA 0's slot
+            int code = 0;
+            if (!isfinite(num) || !isfinite(den)) {
+                code = 1;
+                if (blockIdx.x == 0) st->status = QIHT_ERR_NONFINITE;
+            } else if (num == 0.0 || den == 0.0) {
+                code = 1;                                      // converged: x stays
+            } else {
+                mu = num / den;
+            }
+            if (code && blockIdx.x == 0) {
+                st->stop = 1;
+                if (a.report) {
+                    a.report->iters_run = st->iter;
+                    a.report->backtracks = st->backtracks_total;
+                    a.report->support_changes = st->support_changes_total;
+                    a.report->status = st->status;
+                    a.report->resid_norm2 = st->resid2;
+                    a.report->mu = st->mu_accepted;
+                }
+            }
+            s_code = code;
+            s_muf = (float)mu;
+        }
+        __syncthreads();
+        if (s_code) return;                                    // uniform across CTAs
+    }
+
+    int bt = 0;
+    SelResult sr{};
+    for (;;) {
+        const float muf = s_muf;
+        const uint32_t outside = __float_as_uint(fmaf(muf, __uint_as_float(bmax_g), 0.0f)) & 0x7fffffffu;
+        const bool exact = cand_ok && select_fast(a, sm, s + cnt, muf, outside, sr);
+        if (!exact) {
+            // keys of all n entries, then the one-CTA radix select
+            const int per = (n + gridDim.x - 1) / gridDim.x;
+            const int j0 = min(n, (int)blockIdx.x * per), j1 = min(n, j0 + per);
+            int bad = 0;
+            for (int j = j0 + tid; j < j1; j += blockDim.x) {
+                const uint32_t k = __float_as_uint(fmaf(muf, __ldcg(a.g + j), __ldcg(a.x + j))) & 0x7fffffffu;
+                bad |= k > 0x7f800000u;
+                a.keys[j] = k;
+            }
+            if (__syncthreads_or(bad) && tid == 0) st->status = QIHT_ERR_NONFINITE;
+            if (!grid_sync(a.gbar, target, st)) return;
+            if (__ldcg(&st->status) == QIHT_ERR_NONFINITE) {
+                if (blockIdx.x == 0 && tid == 0) st->stop = 1;
+                return;
+            }
+            if (blockIdx.x == 0) {
+                SelSmem fs{};
+                fs.hist = sm.key;                              // s + gcap >= 2048 entries
+                fs.bitmap = sm.bitmap;
+                fs.wpre = sm.wpre;
+                fs.sup = sm.u_idx;
+                select_on_cta0(a, muf, fs, false);
+            }
+            if (!grid_sync(a.gbar, target, st)) return;
+            sr.changed = __ldcg(&st->changed);
+            sr.uc = __ldcg(&st->union_count);
+            sr.kth0 = __ldcg(&st->kth0);
+            sr.kth1 = __ldcg(&st->kth1);
+            for (int i = tid; i < sr.uc; i += blockDim.x) {
+                sm.u_idx[i] = __ldcg(a.uni + i);
+                sm.u_delta[i] = __ldcg(a.delta + i);
+            }
+            for (int q = tid; q < s; q += blockDim.x) sm.u_val[q] = __ldcg(a.val + q);
+            for (int w = tid; w < nbw4; w += blockDim.x) sm.bitmap[w] = 0u;
+            __syncthreads();
+            for (int q = tid; q < s; q += blockDim.x) {
+                const int j = sm.u_idx[q];
+                atomicOr(&sm.bitmap[j >> 5], 1u << (j & 31));
+            }
+            __syncthreads();
+        }
+        if (stamp && bt == 0) st->t_phase[2] = gtimer_ns();
+        if (!sr.changed) break;
+
+        // ---- Omega: backtracking test on G' u G (partial slots alternate with the round) ----
+        const int ko = (bt & 1) ? 6 : 2;
+        {
+            double dsq = 0.0;
+            if (blockIdx.x == 0 && tid < 32) {
+                for (int i = lane; i < sr.uc; i += 32) dsq += (double)sm.u_delta[i] * (double)sm.u_delta[i];
+                dsq = warp_sum_d(dsq);
+            }
+            rows_product_sm<BITS>(a, rb, sm.u_idx, sm.u_delta, sr.uc, sm.red, sm.zrow);
+            double acc = 0.0;
+            if (tid < nrow_thr) {
+                const int row = (rb.w0 + tid / G) * G + tid % G;
+                if (rb.w0 + tid / G < rb.w1 && row < m) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
+            }
+            acc = cta_sum_n(acc, nrow_thr, shd);
+            if (tid == 0) {
+                mypart[ko] = acc;
+                if (blockIdx.x == 0) mypart[ko + 1] = dsq;
+            }
+        }
+        if (!grid_sync(a.gbar, target, st)) return;
+        const double ddsum = grid_partial_sum(a.part, ko, shd);
+        if (tid == 0) {
+            const double dd = s_alpha * s_alpha * ddsum;
+            const double dn = __ldcg(a.part + ko + 1);
+            int code = 0;                                      // 0 accept, 1 shrink, 2 give up
+            if (dn > 0.0) {                                    // else nothing moves: accept
+                const double omega = dd > 0.0 ? dn / dd : INFINITY;
+                if (!(mu <= (1.0 - a.c) * omega)) {            // insufficient decrease
+                    if (bt >= a.max_bt) {
+                        code = 2;
+                        if (blockIdx.x == 0) {
+                            st->status = QIHT_ERR_BACKTRACK_CAP;
+                            st->stop = 1;
+                            if (a.report) {
+                                a.report->iters_run = st->iter;
+                                a.report->backtracks = st->backtracks_total;
+                                a.report->support_changes = st->support_changes_total;
+                                a.report->status = st->status;
+                                a.report->resid_norm2 = st->resid2;
+                                a.report->mu = st->mu_accepted;
+                            }
+                        }
+                    } else {
+                        code = 1;
+                        mu = mu / (a.k * (1.0 - a.c));
+                        s_muf = (float)mu;
+                    }
+                }
+            }
+            s_code = code;
+        }
+        __syncthreads();
+        if (s_code == 0) break;
+        if (s_code == 2) return;
+        ++bt;
+    }
+
+    // ---- Resid: r = Q(y) - Q2_G' x' for this CTA's rows ----
+    if (stamp) st->t_phase[3] = gtimer_ns();
+    rows_product_sm<BITS>(a, rb, sm.u_idx, sm.u_val, s, sm.red, sm.zrow);
+    {
+        double acc = 0.0;
+        unsigned mx = 0;
+        if (tid < nrow_thr) {
+            const int row = (rb.w0 + tid / G) * G + tid % G;
+            if (rb.w0 + tid / G < rb.w1 && row < m) {
+                const float ri = fmaf(-alpha_f, sm.zrow[tid], __ldcg(a.yhat + row));
+                a.r[row] = ri;
+                acc = (double)ri * (double)ri;
+                mx = __float_as_uint(ri) & 0x7fffffffu;
+            }
+        }
+        acc = cta_sum_n(acc, nrow_thr, shd);
+        mx = cta_max(mx, shu);
+        if (tid == 0) { mypart[4] = acc; mypart[5] = (double)mx; }
+    }
+    if (stamp) st->t_phase[4] = gtimer_ns();
+    // ---- this CTA's slice of x and of the position map ----
+    {
+        const int per = (n + gridDim.x - 1) / gridDim.x;
+        const int j0 = min(n, (int)blockIdx.x * per), j1 = min(n, j0 + per);
+        for (int q = tid; q < s; q += blockDim.x) {
+            if (sr.changed) {
+                const int jo = sm.el_idx[q];
+                if (jo >= j0 && jo < j1 && !((sm.bitmap[jo >> 5] >> (jo & 31)) & 1u)) {
+                    a.x[jo] = 0.0f;
+                    a.pos[jo] = -1;
+                }
+            }
+            const int jn = sm.u_idx[q];
+            if (jn >= j0 && jn < j1) {
+                a.x[jn] = sm.u_val[q];
+                if (sr.changed || first) a.pos[jn] = q;     // the initial support has no positions yet
+            }
+        }
+    }
+    // the last CTA to arrive commits the scalars, G and x_G (no CTA waits for it)
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(a.bar + 2, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double resid2, rmax;
+    grid_partial_sum_max(a.part, 4, 5, shd, &resid2, &rmax);
+    const int it = __ldcg(&st->iter) + 1;
+    for (int q = tid; q < s; q += blockDim.x) {
+        a.support[q] = sm.u_idx[q];
+        a.xs[q] = sm.u_val[q];
+        if (a.trace.support) a.trace.support[(size_t)it * s + q] = sm.u_idx[q];
+    }
+    if (tid == 0) {
+        // every state word this thread needs, read at once
+        const int bt_total = st->backtracks_total + bt;
+        const int sc_total = st->support_changes_total + sr.changed;
+        const int iters = st->iters;
+        int status = st->status;
+        const int fsel = st->full_selects;
+        unsigned long long tp[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) tp[i] = st->t_phase[i];
+        a.bar[2] = 0u;
+        st->iter = it;
+        st->mu = mu;
+        st->mu_accepted = mu;
+        st->bt = bt;
+        st->resid2 = resid2;
+        st->rmax_bits = (unsigned)rmax;
+        st->backtracks_total = bt_total;
+        st->support_changes_total = sc_total;
+        st->changed = sr.changed;
+        st->kth0 = sr.kth0;
+        st->kth1 = sr.kth1;
+        // candidates of the next gradient: a little below the (s+1)-th key, in units of |g|
+        const float tg = sr.kth1 > 0.0f ? 0.8f * sr.kth1 / (float)mu : 0.0f;
+        st->tau_g_bits = (isfinite(tg) && tg > 0.0f) ? __float_as_uint(tg) : 0u;
+        st->gcand_count = 0u;
+        st->bmax_g = 0u;
+        int stop = it >= iters;
+        if (!isfinite(resid2)) {
+            status = QIHT_ERR_NONFINITE;
+            st->status = status;
+            stop = 1;
+        }
+        if (stop) st->stop = 1;
+        if (a.trace.kth) { a.trace.kth[2 * it] = sr.kth0; a.trace.kth[2 * it + 1] = sr.kth1; }
+        if (a.trace.mu) a.trace.mu[it] = mu;
+        if (a.trace.bt) a.trace.bt[it] = bt;
+        if (a.trace.resid2) a.trace.resid2[it] = resid2;
+        if (a.report) {
+            a.report->iters_run = it;
+            a.report->backtracks = bt_total;
+            a.report->support_changes = sc_total;
+            a.report->status = status;
+            a.report->resid_norm2 = resid2;
+            a.report->mu = mu;
+            a.report->full_selects = fsel;
+            // phases: step size, (filter: in the gradient kernel), select, backtracking,
+            // residual product, commit, whole kernel
+            const unsigned long long t6 = gtimer_ns();
+            a.report->phase_us[0] = (float)(tp[1] - tp[0]) * 1e-3f;
+            a.report->phase_us[1] = 0.0f;
+            a.report->phase_us[2] = (float)(tp[2] - tp[1]) * 1e-3f;
+            a.report->phase_us[3] = (float)(tp[3] - tp[2]) * 1e-3f;
+            a.report->phase_us[4] = (float)(tp[4] - tp[3]) * 1e-3f;
+            a.report->phase_us[5] = (float)(t6 - tp[4]) * 1e-3f;
+            a.report->phase_us[6] = (float)(t6 - tp[0]) * 1e-3f;
+            a.report->phase_us[7] = 0.0f;
+        }
+    }
+}
+
 static_assert(sizeof(IterArgs) <= kIterArgsMax, "iteration kernel arguments exceed their storage");
 size_t iter_args_bytes() { return sizeof(IterArgs); }
 
+static size_t iter_smem_bytes(int n, int bits);
+
 void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* support, int32_t* sel, float* val,
                int32_t* uni, float* delta, const float* yhat, float* r, uint32_t* keys, unsigned long long* cand,
-               double* part, int n, int m, int s, double k, double c, int max_bt, qiht_report* report,
-               const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore, void** argbuf)
+               double* part, const IterFastBufs& fb, int n, int m, int s, double k, double c, int max_bt,
+               qiht_report* report, const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore, void** argbuf)
 {
     IterArgs* a = reinterpret_cast<IterArgs*>(argstore);
     *a = IterArgs{};
@@ -847,9 +1556,14 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
     a->cap = kTopCandCap;
     a->part = part;
     a->bar = &st->counters[0][0];
-    a->flags = &st->counters[1][0];
+    a->gbar = &st->bar_count;
     a->cand_val = reinterpret_cast<float*>(cand + kTopCandCap);
     a->cand_x = reinterpret_cast<float*>(cand + kTopCandCap) + kTopCandCap;
+    a->pos = fb.pos;
+    a->xs = fb.xs;
+    a->gsup = fb.gsup;
+    a->gcand = fb.gcand;
+    a->gcap = fb.gcap;
     a->n = n;
     a->m = m;
     a->s = s;
@@ -859,8 +1573,16 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
     a->report = report;
     a->trace = trace;
     argbuf[0] = a;
-    void* fn = Q2.bits == 8 ? (void*)k_iter<8> : Q2.bits == 4 ? (void*)k_iter<4> : (void*)k_iter<2>;
-    const size_t smem = iter_smem_bytes(n, Q2.bits);
+    const int G = 32 / Q2.bits;
+    void* fn;
+    size_t smem;
+    if (iter_fast(s)) {
+        fn = Q2.bits == 8 ? (void*)k_iter_fast<8> : Q2.bits == 4 ? (void*)k_iter_fast<4> : (void*)k_iter_fast<2>;
+        smem = fast_smem_bytes(n, s, fb.gcap, G);
+    } else {
+        fn = Q2.bits == 8 ? (void*)k_iter<8> : Q2.bits == 4 ? (void*)k_iter<4> : (void*)k_iter<2>;
+        smem = iter_smem_bytes(n, Q2.bits);
+    }
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     p->func = fn;
     p->gridDim = dim3(iter_grid());
@@ -870,13 +1592,24 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
     p->extra = nullptr;
 }
 
-size_t iter_smem_bytes(int n, int bits)
+static size_t iter_smem_bytes(int n, int bits)
 {
     const int G = 32 / bits;
     const size_t gather = (size_t)kListChunk * 8 + (size_t)kIterThreads * G * 4 + (size_t)kIterThreads * 4;
     const size_t nbw = ((size_t)(n + 31) / 32 + 3) & ~(size_t)3;
     const size_t select = 2048 * 4 + 2 * nbw * 4 + (size_t)kTopCandCap * 16 + (size_t)kSupportSmem * 4;
     return gather > select ? gather : select;
+}
+
+bool iter_fast(int s)
+{
+    // QIHT_ITER=base selects k_iter (filter and select phases inside the kernel) for measurement
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("QIHT_ITER");
+        v = (e && e[0] == 'b') ? 0 : 1;
+    }
+    return v == 1 && s <= kFastMaxS;
 }
 
 int iter_grid()

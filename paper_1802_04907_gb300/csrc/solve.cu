@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(1024) k_init(InitKernelArgs ka)
         mx = max(mx, __float_as_uint(v) & 0x7fffffffu);
     }
     for (int j = threadIdx.x; j < a.n; j += blockDim.x) a.x[j] = 0.0f;
+    if (a.pos)
+        for (int j = threadIdx.x; j < a.n; j += blockDim.x) a.pos[j] = -1;
     // deterministic block reductions
 #pragma unroll
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -316,7 +318,7 @@ namespace {
 
 struct Plan {
     size_t off_state, off_yhat, off_r, off_g, off_sel, off_val, off_uni, off_delta, off_partial, off_rbp, off_chunk,
-        off_cand, off_keys, off_part, total;
+        off_cand, off_keys, off_part, off_pos, off_xs, off_gsup, off_gcand, total;
 };
 
 Plan plan_solve(int m, int n, int s)
@@ -343,7 +345,11 @@ Plan plan_solve(int m, int n, int s)
     p.off_chunk = o; o += align256((size_t)gather_chunks(2 * s) * 8);
     p.off_cand = o; o += align256((size_t)kTopCandCap * 16);     // keys, then values and old x
     p.off_keys = o; o += align256((size_t)n * 4);
-    p.off_part = o; o += align256((size_t)1024 * 4 * 8);
+    p.off_part = o; o += align256((size_t)1024 * kPartStride * 8);
+    p.off_pos = o; o += align256((size_t)n * 4);
+    p.off_xs = o; o += align256((size_t)s * 4);
+    p.off_gsup = o; o += align256((size_t)s * 4);
+    p.off_gcand = o; o += align256((size_t)kTopCandCap * 8);
     p.total = o;
     return p;
 }
@@ -413,6 +419,8 @@ qiht_status add_while(cudaGraph_t g, cudaGraphNode_t* out, const cudaGraphNode_t
         if (_e != QIHT_OK) return _e;   \
     } while (0)
 
+static bool multi_kernel_iteration();
+
 // The solver's kernels and their arguments, shared by the graph driver and the eager driver.
 struct SolveKernels {
     InitKernelArgs ia;
@@ -459,6 +467,15 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     qiht_trace tr{};
     if (trace) tr = *trace;
     const int nsm = num_sms();
+    const bool fast = !multi_kernel_iteration() && iter_fast(s);
+    IterFastBufs fb{};
+    if (fast) {
+        fb.pos = reinterpret_cast<int32_t*>(ws + pl.off_pos);
+        fb.xs = reinterpret_cast<float*>(ws + pl.off_xs);
+        fb.gsup = reinterpret_cast<float*>(ws + pl.off_gsup);
+        fb.gcand = reinterpret_cast<unsigned long long*>(ws + pl.off_gcand);
+        fb.gcap = kTopCandCap;
+    }
 
     K.ia = InitKernelArgs{};
     K.ia.a.Y = view(Y);
@@ -467,6 +484,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     K.ia.a.yhat = yhat;
     K.ia.a.r = r;
     K.ia.a.x = x;
+    K.ia.a.pos = fb.pos;
     K.ia.a.n = n;
     K.ia.a.m = m;
     K.ia.a.s = s;
@@ -493,6 +511,10 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     gemv_t_node(K.g0, nsm, &K.p_g0, K.a_g0);
     K.gb = K.g0;
     K.gb.h_outer = h_outer;         // the loop body's product decides whether to go on
+    K.gb.pos = fb.pos;              // and prepares the fast path's next threshold
+    K.gb.gsup = fb.gsup;
+    K.gb.gcand = fb.gcand;
+    K.gb.gcap = fb.gcap;
     K.a_gb[0] = &K.gb; K.a_gb[1] = &K.tpcb; K.a_gb[2] = &K.nsb;
     gemv_t_node(K.gb, nsm, &K.p_gb, K.a_gb);
 
@@ -532,7 +554,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     K.a_tf[0] = &K.tt;
     top_filter_node(K.tt, &K.p_tf, K.a_tf);
     iter_node(view(Q2), st, g, x, support, sel, val, uni, delta, yhat, r,
-              reinterpret_cast<uint32_t*>(ws + pl.off_keys), cand, reinterpret_cast<double*>(ws + pl.off_part), n, m, s,
+              reinterpret_cast<uint32_t*>(ws + pl.off_keys), cand, reinterpret_cast<double*>(ws + pl.off_part), fb, n, m, s,
               prm->k, prm->c, prm->max_backtrack, report, tr, &K.p_it, K.iter_store, K.a_it);
 
     GatherArgs base{};
