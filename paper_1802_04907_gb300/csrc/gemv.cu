@@ -730,24 +730,75 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int sh = fixed_shift(*a.rmax_bits);
-    long long rsum = 0;
-    for (int lw = threadIdx.x; lw < P * G; lw += blockDim.x) {
-        uint32_t b0 = 0, b1 = 0, b2 = 0;
+
+    // Software pipeline over the warp's sequence of batches (column j, batch pb of NPL
+    // pieces per lane): the loads of the next batch are in flight while this one is used.
+    // The first batch is requested before the residual is staged, so its DRAM latency
+    // overlaps the staging.
+    const int W = gridDim.x * (blockDim.x >> 5);
+    const int nb = (P + 32 * NPL - 1) / (32 * NPL);     // batches per column
+    int j = blockIdx.x * (blockDim.x >> 5) + warp;
+    int pb = 0;
+    // the code stream is read once per call: mark it first to leave L2, so that the small
+    // working set of the rest of the iteration (support columns of Q2, g, x, r) stays there
+    uint64_t stream_policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_policy));
+    auto load_batch = [&](uint4 (&cv)[NPL], int jj, int bb) {
+        const uint4* col = reinterpret_cast<const uint4*>(a.Q.words + (size_t)jj * ld);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int i = 4 * lw + p;
-            int v = 0;
-            if (i < m) v = __float2int_rn(ldexpf(__ldcg(a.r + i), sh));
-            rsum += v;
-            b0 |= (uint32_t)(v & 255) << (8 * p);
-            b1 |= (uint32_t)((v >> 8) & 255) << (8 * p);
-            b2 |= (uint32_t)((v >> 16) & 255) << (8 * p);
+        for (int u = 0; u < NPL; ++u) {
+            const int piece = bb * 32 * NPL + lane + 32 * u;
+            if (piece < P)
+                asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                             : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w)
+                             : "l"(col + piece), "l"(stream_policy));
+            else
+                cv[u] = make_uint4(0u, 0u, 0u, 0u);
         }
-        const int piece = lw / G, rem = lw - piece * G, q = rem >> 2, w = rem & 3;
-        const size_t idx = ((size_t)q * P + piece) * 4 + w;
-        limb[idx] = b0;
-        limb[(size_t)E * P * 4 + idx] = b1;
-        limb[(size_t)2 * E * P * 4 + idx] = b2;
+    };
+    uint4 cA[NPL], cB[NPL];
+    if (j < n) load_batch(cA, j, pb);
+
+    // residual to 24-bit fixed point, as three byte planes; four rows (one float4) per limb
+    // word, UR words of a thread in flight at once
+    constexpr int UR = 4;
+    const bool r_vec = (reinterpret_cast<uintptr_t>(a.r) & 15) == 0;
+    const int nlw = P * G;
+    long long rsum = 0;
+    for (int lw0 = threadIdx.x; lw0 < nlw; lw0 += blockDim.x * UR) {
+        float rv[UR][4];
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            const int lw = lw0 + u * (int)blockDim.x;
+            const int i = 4 * lw;
+            if (lw < nlw && r_vec && i + 3 < m) {
+                const float4 t = __ldcg(reinterpret_cast<const float4*>(a.r) + lw);
+                rv[u][0] = t.x; rv[u][1] = t.y; rv[u][2] = t.z; rv[u][3] = t.w;
+            } else {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) rv[u][p] = (lw < nlw && i + p < m) ? __ldcg(a.r + i + p) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            const int lw = lw0 + u * (int)blockDim.x;
+            if (lw < nlw) {
+                uint32_t b0 = 0, b1 = 0, b2 = 0;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int v = __float2int_rn(ldexpf(rv[u][p], sh));   // rows past m are 0
+                    rsum += v;
+                    b0 |= (uint32_t)(v & 255) << (8 * p);
+                    b1 |= (uint32_t)((v >> 8) & 255) << (8 * p);
+                    b2 |= (uint32_t)((v >> 16) & 255) << (8 * p);
+                }
+                const int piece = lw / G, rem = lw - piece * G, q = rem >> 2, w = rem & 3;
+                const size_t idx = ((size_t)q * P + piece) * 4 + w;
+                limb[idx] = b0;
+                limb[(size_t)E * P * 4 + idx] = b1;
+                limb[(size_t)2 * E * P * 4 + idx] = b2;
+            }
+        }
     }
     {
         long long v = rsum;
@@ -773,34 +824,11 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
     const uint4* L1 = L0 + (size_t)E * P;
     const uint4* L2 = L0 + (size_t)2 * E * P;
 
-    // Software pipeline over the warp's sequence of batches (column j, batch pb of NPL
-    // pieces per lane): the loads of the next batch are in flight while this one is used.
-    const int W = gridDim.x * (blockDim.x >> 5);
-    const int nb = (P + 32 * NPL - 1) / (32 * NPL);     // batches per column
-    int j = blockIdx.x * (blockDim.x >> 5) + warp;
-    int pb = 0;
     uint32_t s0[E], s1[E];
     int32_t s2[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) { s0[k] = 0; s1[k] = 0; s2[k] = 0; }
 
-    // the code stream is read once per call: mark it first to leave L2, so that the small
-    // working set of the rest of the iteration (support columns of Q2, g, x, r) stays there
-    uint64_t stream_policy;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_policy));
-    auto load_batch = [&](uint4 (&cv)[NPL], int jj, int bb) {
-        const uint4* col = reinterpret_cast<const uint4*>(a.Q.words + (size_t)jj * ld);
-#pragma unroll
-        for (int u = 0; u < NPL; ++u) {
-            const int piece = bb * 32 * NPL + lane + 32 * u;
-            if (piece < P)
-                asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                             : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w)
-                             : "l"(col + piece), "l"(stream_policy));
-            else
-                cv[u] = make_uint4(0u, 0u, 0u, 0u);
-        }
-    };
     auto use_batch = [&](const uint4 (&cv)[NPL], int bb) {
 #pragma unroll
         for (int u = 0; u < NPL; ++u) {
@@ -863,8 +891,6 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
         if (++bb == nb) { bb = 0; jj += W; }
     };
 
-    uint4 cA[NPL], cB[NPL];
-    if (j < n) load_batch(cA, j, pb);
     while (j < n) {
         int jB = j, pB = pb;
         advance(jB, pB);

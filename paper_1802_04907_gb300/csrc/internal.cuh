@@ -49,8 +49,11 @@ struct State {
     unsigned tau_g_bits;   // |g| threshold of the gradient kernel's candidates (float bits, 0 = off)
     unsigned gcand_count;  // entries outside G with |g| >= tau_g appended by the gradient kernel
     unsigned bmax_g;       // largest |g| (float bits) outside G below tau_g
+    unsigned omega_uses;   // backtracking-test rounds of the fast iteration kernel so far
+    unsigned dec_uses;     // uses of the fast iteration kernel's decision word so far
     unsigned long long t_phase[8];   // device clock at phase boundaries of the last iteration
     unsigned long long bar_count;    // grid-barrier arrivals of the iteration kernel (only grows)
+    unsigned long long dec_word;     // fast iteration kernel: CTA 0's tagged decision (starts with tag 1)
     unsigned counters[2][1024];  // arrival counters of the column-subset products (row 0; the
                                  // iteration kernel's commit counter is word 2)
 };
@@ -133,6 +136,7 @@ struct InitArgs {
     float* r;
     float* x;
     int32_t* pos;               // optional: position map of the fast path, set to -1
+    double* part;               // optional: tagged partial slots of the fast path, set to tag 1
     int n, m, s, iters;
     State* st;
     qiht_report* report;
@@ -160,7 +164,9 @@ cudaError_t launch_top(const TopArgs& a, cudaStream_t s);
 // One iteration after the gradient product as one persistent kernel (iter.cu).
 struct IterArgs;
 constexpr size_t kIterArgsMax = 1024;     // bytes reserved for the iteration kernel's arguments
-constexpr int kPartStride = 8;            // doubles of per-CTA partials of the iteration kernel
+constexpr int kPartSlots = 8;             // kinds of per-CTA partials of the iteration kernel
+constexpr int kSlotCtas = 256;            // CTAs per partial kind (largest iteration grid)
+constexpr int kSlotPerLane = kSlotCtas / 32;
 int iter_grid();
 bool iter_fast(int s);                    // the fast-path iteration kernel serves this support size
 // Buffers of the fast path (ignored by the other kernel).

@@ -139,7 +139,7 @@ __device__ double grid_partial_sum(const double* part, int k, double* sh)
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int c = c0 + 32 * u;
-                t[u] = c < (int)gridDim.x ? __ldcg(part + kPartStride * c + k) : 0.0;
+                t[u] = c < (int)gridDim.x ? __ldcg(part + k * kSlotCtas + c) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) v += t[u];
@@ -164,8 +164,8 @@ __device__ void grid_partial_sum_max(const double* part, int ks, int km, double*
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int c = c0 + 32 * i;
-                t[i] = c < (int)gridDim.x ? __ldcg(part + kPartStride * c + ks) : 0.0;
-                u[i] = c < (int)gridDim.x ? __ldcg(part + kPartStride * c + km) : 0.0;
+                t[i] = c < (int)gridDim.x ? __ldcg(part + ks * kSlotCtas + c) : 0.0;
+                u[i] = c < (int)gridDim.x ? __ldcg(part + km * kSlotCtas + c) : 0.0;
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) { v += t[i]; w = fmax(w, u[i]); }
@@ -191,7 +191,7 @@ __device__ double grid_partial_max(const double* part, int k, double* sh)
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int c = c0 + 32 * u;
-                t[u] = c < (int)gridDim.x ? __ldcg(part + kPartStride * c + k) : 0.0;
+                t[u] = c < (int)gridDim.x ? __ldcg(part + k * kSlotCtas + c) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) v = fmax(v, t[u]);
@@ -204,6 +204,151 @@ __device__ double grid_partial_max(const double* part, int k, double* sh)
     const double r = sh[32];
     __syncthreads();
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// Tagged exchange slots. A per-CTA partial that is a sum of squares (>= 0, or NaN)
+// travels in one 64-bit word whose sign bit holds a tag: the parity of how often
+// that slot has been written. A reader knows the tag it waits for, so the word
+// itself says whether it is fresh, and no barrier or flag has to be read first.
+// The slot schedule rewrites a slot only after every CTA has read its previous
+// value, so one tag bit tells the current write from the previous one. Slots start
+// with tag 1 (set by the solver's set-up kernel); their first writes carry tag 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void slot_put(double* p, double v, unsigned tag)
+{
+    const unsigned long long b = ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) |
+                                 ((unsigned long long)(tag & 1u) << 63);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(b) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long slot_ld(const double* p)
+{
+    unsigned long long b;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(b) : "l"(p) : "memory");
+    return b;
+}
+
+// Warp 0 waits until slot ks (and km, when >= 0) of every CTA, and slot ke of CTA 0
+// (when >= 0), carry `tag`; then the sum over CTAs of slot ks (lane l adds CTAs l,
+// l + 32, ... in order, then a fixed shuffle tree), the maximum of slot km and CTA 0's
+// slot ke go to every thread. Each polling round re-reads all stale words of a lane at
+// once. Waiting is bounded by %globaltimer; false on timeout.
+
+__device__ bool slot_gather(const double* part, int ks, int km, int ke, unsigned tag, double* sum, double* mx,
+                            double* ext, State* st, double* sh)
+{
+    __shared__ int ok_sh;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        constexpr unsigned long long M = 0x7fffffffffffffffull;
+        const unsigned long long want = (unsigned long long)(tag & 1u) << 63;
+        const int grid = (int)gridDim.x;
+        unsigned long long bs[kSlotPerLane], bm[kSlotPerLane], be = want;
+        unsigned pend = 0;                       // bit u: sum word u stale; bit 8 + u: max word u; bit 16: extra
+#pragma unroll
+        for (int u = 0; u < kSlotPerLane; ++u) {
+            bs[u] = want;
+            bm[u] = want;
+            const int c = lane + 32 * u;
+            if (c < grid) {
+                pend |= 1u << u;
+                if (km >= 0) pend |= 1u << (8 + u);
+            }
+        }
+        if (ke >= 0 && lane == 0) pend |= 1u << 16;
+        const unsigned long long t0 = gtimer_ns();
+        int ok = 1;
+        while (pend) {
+#pragma unroll
+            for (int u = 0; u < kSlotPerLane; ++u) {
+                const int c = lane + 32 * u;
+                if (pend & (1u << u)) bs[u] = slot_ld(part + ks * kSlotCtas + c);
+                if (pend & (1u << (8 + u))) bm[u] = slot_ld(part + km * kSlotCtas + c);
+            }
+            if (pend & (1u << 16)) be = slot_ld(part + ke * kSlotCtas);
+#pragma unroll
+            for (int u = 0; u < kSlotPerLane; ++u) {
+                if ((bs[u] & ~M) == want) pend &= ~(1u << u);
+                if ((bm[u] & ~M) == want) pend &= ~(1u << (8 + u));
+            }
+            if ((be & ~M) == want) pend &= ~(1u << 16);
+            if (pend && gtimer_ns() - t0 > kBarrierBudgetNs) { ok = 0; break; }
+        }
+        double v = 0.0, w = 0.0;
+#pragma unroll
+        for (int u = 0; u < kSlotPerLane; ++u) {
+            v += __longlong_as_double((long long)(bs[u] & M));
+            w = fmax(w, __longlong_as_double((long long)(bm[u] & M)));
+        }
+        const double e = __longlong_as_double((long long)(be & M));
+        ok = __all_sync(0xffffffffu, ok);
+        v = warp_sum_d(v);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (lane == 0) {
+            sh[29] = v;
+            sh[30] = w;
+            sh[31] = e;
+            ok_sh = ok;
+            if (!ok) {
+                st->status = QIHT_ERR_TIMEOUT;
+                st->stop = 1;
+            }
+        }
+    }
+    __syncthreads();
+    *sum = sh[29];
+    if (mx) *mx = sh[30];
+    if (ext) *ext = sh[31];
+    const int ok = ok_sh;
+    __syncthreads();
+    return ok != 0;
+}
+
+// Decision word: CTA 0 publishes, after gathering the partials of an exchange, what
+// every CTA needs from it (a code and the float step size) in one tagged 64-bit word:
+// bit 63 tag, bits 32-33 code, bits 0-31 the float. The word is rewritten only after
+// every CTA has read it (each CTA reads it before writing its next partial, and CTA 0
+// gathers all of those before writing again); tags alternate with every use.
+__device__ __forceinline__ void dec_put(unsigned long long* p, unsigned tag, unsigned code, float v)
+{
+    const unsigned long long w =
+        ((unsigned long long)(tag & 1u) << 63) | ((unsigned long long)(code & 3u) << 32) | __float_as_uint(v);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+// Thread 0 polls the decision word until it carries `tag`; every thread gets code and value.
+__device__ bool dec_wait(const unsigned long long* p, unsigned tag, unsigned* code, float* v, State* st)
+{
+    __shared__ unsigned long long sw;
+    __shared__ int ok_sh;
+    if (threadIdx.x == 0) {
+        const unsigned long long want = (unsigned long long)(tag & 1u);
+        unsigned long long w;
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+        int ok = 1;
+        if ((w >> 63) != want) {
+            const unsigned long long t0 = gtimer_ns();
+            do {
+                if (gtimer_ns() - t0 > kBarrierBudgetNs) { ok = 0; break; }
+                asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+            } while ((w >> 63) != want);
+        }
+        if (!ok) {
+            st->status = QIHT_ERR_TIMEOUT;
+            st->stop = 1;
+        }
+        sw = w;
+        ok_sh = ok;
+    }
+    __syncthreads();
+    const unsigned long long w = sw;
+    const int ok = ok_sh;
+    __syncthreads();
+    *code = (unsigned)(w >> 32) & 3u;
+    *v = __uint_as_float((uint32_t)w);
+    return ok != 0;
 }
 
 struct IterArgs {
@@ -221,7 +366,7 @@ struct IterArgs {
     uint32_t* keys;             // |x + mu g| of every entry (fallback select)
     unsigned long long* cand;   // filter candidates
     int cap;
-    double* part;               // [grid][kPartStride] per-CTA partials
+    double* part;               // [kPartSlots][kSlotCtas] per-CTA partials (CTA index fastest)
     unsigned* bar;              // [2] commit counter
     unsigned long long* gbar;   // grid-barrier arrival counter
     float* cand_val;            // x + mu g of each candidate (same slot as cand)
@@ -671,7 +816,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     }
     const int m = a.m, s = a.s, n = a.n;
     const int tid = threadIdx.x;
-    double* mypart = a.part + kPartStride * blockIdx.x;
+    double* mypart = a.part + blockIdx.x;       // slot k of this CTA: mypart[k * kSlotCtas]
 
     // ---- Mu: z = Q2_G g_G, den = alpha^2 ||z||^2, num = ||g_G||^2 ----
     double gsq = 0.0;
@@ -684,14 +829,14 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         }
         acc = cta_sum(acc, shd);
         const double num = cta_sum(gsq, shd);                // ||g_G||^2 from the staged coefficients
-        if (tid == 0) { mypart[0] = acc; mypart[1] = num; }
+        if (tid == 0) { mypart[0 * kSlotCtas] = acc; mypart[1 * kSlotCtas] = num; }
     }
     if (!grid_sync(a.gbar, target, st)) return;
     if (stamp) st->t_phase[1] = gtimer_ns();
     double mu;
     {
         const double den = s_alpha * s_alpha * grid_partial_sum(a.part, 0, shd);
-        const double num = __ldcg(a.part + 1);                 // CTA 0's slot
+        const double num = __ldcg(a.part + 1 * kSlotCtas);     // CTA 0's slot
         bool stop = false;
         if (!isfinite(num) || !isfinite(den)) {
             stop = true;
@@ -789,11 +934,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             }
             acc = cta_sum(acc, shd);
             const double dn = cta_sum(dsq, shd);             // ||x' - x||^2 from the staged list
-            if (tid == 0) { mypart[2] = acc; mypart[3] = dn; }
+            if (tid == 0) { mypart[2 * kSlotCtas] = acc; mypart[3 * kSlotCtas] = dn; }
         }
         if (!grid_sync(a.gbar, target, st)) return;
         const double dd = s_alpha * s_alpha * grid_partial_sum(a.part, 2, shd);
-        const double dn = __ldcg(a.part + 3);
+        const double dn = __ldcg(a.part + 3 * kSlotCtas);
         if (!(dn > 0.0)) break;                               // nothing moves: accept
         const double omega = dd > 0.0 ? dn / dd : INFINITY;
         if (mu <= (1.0 - a.c) * omega) break;                 // sufficient decrease: accept
@@ -833,7 +978,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         }
         acc = cta_sum(acc, shd);
         mx = cta_max(mx, shu);
-        if (tid == 0) { mypart[0] = acc; mypart[1] = (double)mx; }
+        if (tid == 0) { mypart[0 * kSlotCtas] = acc; mypart[1 * kSlotCtas] = (double)mx; }
     }
     if (stamp) st->t_phase[5] = gtimer_ns();
     // the last CTA to arrive commits the iteration (no CTA waits for it)
@@ -1195,6 +1340,9 @@ __device__ bool select_fast(const IterArgs& a, const FastSm& sm, int cnt, float 
     return true;
 }
 
+// Per-CTA partial slots (CTA index fastest, tagged; see slot_put), gathered by CTA 0:
+// 0 ||z||^2 of the step size, 2 ||Q2 d||^2 of a backtracking test, 4 ||r||^2 and
+// 5 max |r| of the residual. CTA 0 answers the first two with the decision word.
 template <int BITS>
 __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
 {
@@ -1207,10 +1355,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     __shared__ float s_alpha_f, s_muf;
     __shared__ int s_code;
     State* st = a.st;
-    if (st->stop) return;                       // uniform: read before any barrier
+    if (st->stop) return;                       // uniform: read before any exchange
     const int tid = threadIdx.x, lane = tid & 31;
-    const bool stamp = blockIdx.x == 0 && tid == 0;
-    if (stamp) st->t_phase[0] = gtimer_ns();
+    const bool cta0 = blockIdx.x == 0;
+    unsigned long long tp[5] = {0, 0, 0, 0, 0};  // CTA 0, thread 0: phase clock
+    if (cta0 && tid == 0) tp[0] = gtimer_ns();
     // FP64 work (low throughput on this GPU) is done by single threads or single warps
     unsigned long long target = 0;
     if (tid == 0) target = barrier_base(a.gbar);
@@ -1223,87 +1372,117 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     const RowBlock rb = row_block(a.Q.ld);
     const FastSm sm = fast_smem_layout(a, smem, G);
     const int m = a.m, s = a.s, n = a.n;
-    double* mypart = a.part + kPartStride * blockIdx.x;
+    double* mypart = a.part + blockIdx.x;       // slot k of this CTA: mypart[k * kSlotCtas]
     const int nbw4 = (((n + 31) / 32) + 3) & ~3;
     const int nrow_thr = rb.wpc * G;            // threads that hold one row of this CTA
 
-    // ---- G, x_G, g_G and the candidates into shared memory ----
-    const bool first = __ldcg(&st->iter) == 0;   // the gradient kernel has not filtered yet
+    // ---- state, G, x_G, g_G, the first candidates and Q(y) of this CTA's rows, all at once ----
+    const int iter0 = __ldcg(&st->iter);
+    const unsigned omega_uses = __ldcg(&st->omega_uses);
+    const unsigned dec_uses = __ldcg(&st->dec_uses);
     const uint32_t tau_g = __ldcg(&st->tau_g_bits);
     const unsigned ncand = __ldcg(&st->gcand_count);
+    const uint32_t bmax_g = __ldcg(&st->bmax_g);
+    int st_bt = 0, st_sc = 0, st_iters = 0, st_status = 0, st_fsel = 0;
+    if (cta0 && tid == 0) {
+        st_bt = st->backtracks_total;
+        st_sc = st->support_changes_total;
+        st_iters = st->iters;
+        st_status = st->status;
+        st_fsel = st->full_selects;
+    }
+    float yrow = 0.0f;
+    int row_ok = 0, row = 0;
+    if (tid < nrow_thr) {
+        row = (rb.w0 + tid / G) * G + tid % G;
+        row_ok = rb.w0 + tid / G < rb.w1 && row < m;
+        if (row_ok) yrow = __ldcg(a.yhat + row);
+    }
+    unsigned long long cspec = 0;
+    if (tid < a.gcap) cspec = __ldcg(a.gcand + tid);   // speculative: used if tid < count
+    const bool first = iter0 == 0;              // the gradient kernel has not filtered yet
     const bool cand_ok = !first && tau_g != 0u && ncand <= (unsigned)a.gcap;
     const int cnt = cand_ok ? (int)ncand : 0;
-    const uint32_t bmax_g = __ldcg(&st->bmax_g);
     for (int q = tid; q < s; q += blockDim.x) {
         const int j = __ldcg(a.support + q);
+        const float xv = __ldcg(a.xs + q);
+        const float gv = __ldcg(a.gsup + q);
         sm.el_idx[q] = j;
-        sm.el_x[q] = first ? __ldcg(a.x + j) : __ldcg(a.xs + q);
-        sm.el_g[q] = first ? __ldcg(a.g + j) : __ldcg(a.gsup + q);
+        sm.el_x[q] = first ? __ldcg(a.x + j) : xv;
+        sm.el_g[q] = first ? __ldcg(a.g + j) : gv;
     }
     for (int i = tid; i < cnt; i += blockDim.x) {
-        const unsigned long long c = __ldcg(a.gcand + i);
+        const unsigned long long c = i == tid ? cspec : __ldcg(a.gcand + i);
         sm.el_idx[s + i] = (int)(uint32_t)c;
         sm.el_x[s + i] = 0.0f;
         sm.el_g[s + i] = __uint_as_float((uint32_t)(c >> 32));
     }
     __syncthreads();
     const float alpha_f = s_alpha_f;
+    const unsigned tag = (unsigned)iter0 & 1u;  // step-size and residual slots: once per iteration
 
     // ---- Mu: z = Q2_G g_G, den = alpha^2 ||z||^2, num = ||g_G||^2 (CTA 0's warp 0) ----
+    double num = 0.0;                            // CTA 0, warp 0
     {
-        double num = 0.0;
-        if (blockIdx.x == 0 && tid < 32) {
+        if (cta0 && tid < 32) {
             for (int q = lane; q < s; q += 32) num += (double)sm.el_g[q] * (double)sm.el_g[q];
             num = warp_sum_d(num);
         }
         rows_product_sm<BITS>(a, rb, sm.el_idx, sm.el_g, s, sm.red, sm.zrow);
         double acc = 0.0;
-        if (tid < nrow_thr) {
-            const int row = (rb.w0 + tid / G) * G + tid % G;
-            if (rb.w0 + tid / G < rb.w1 && row < m) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
-        }
+        if (row_ok) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
         acc = cta_sum_n(acc, nrow_thr, shd);
-        if (tid == 0) {
-            mypart[0] = acc;
-            if (blockIdx.x == 0) mypart[1] = num;
-        }
+        if (tid == 0) slot_put(mypart + 0 * kSlotCtas, acc, tag);
     }
-    if (!grid_sync(a.gbar, target, st)) return;
-    if (stamp) st->t_phase[1] = gtimer_ns();
-    double mu = 0.0;                             // meaningful in thread 0
+    // CTA 0 gathers the partials and publishes mu (code 1: stop); the others wait for it
+    double mu = 0.0;                             // meaningful in CTA 0's thread 0
+    unsigned dec_use = dec_uses;                 // uses of the decision word so far
     {
-        const double densum = grid_partial_sum(a.part, 0, shd);
-        if (tid == 0) {
-            const double den = s_alpha * s_alpha * densum;
-            const double num = __ldcg(a.part + 1);             // CTA 0's slot
-            int code = 0;
-            if (!isfinite(num) || !isfinite(den)) {
-                code = 1;
-                if (blockIdx.x == 0) st->status = QIHT_ERR_NONFINITE;
-            } else if (num == 0.0 || den == 0.0) {
-                code = 1;                                      // converged: x stays
-            } else {
-                mu = num / den;
-            }
-            if (code && blockIdx.x == 0) {
-                st->stop = 1;
-                if (a.report) {
-                    a.report->iters_run = st->iter;
-                    a.report->backtracks = st->backtracks_total;
-                    a.report->support_changes = st->support_changes_total;
-                    a.report->status = st->status;
-                    a.report->resid_norm2 = st->resid2;
-                    a.report->mu = st->mu_accepted;
+        unsigned code = 0;
+        float muf = 0.0f;
+        if (cta0) {
+            double densum = 0.0;
+            if (!slot_gather(a.part, 0, -1, -1, tag, &densum, nullptr, nullptr, st, shd)) return;
+            if (tid == 0) {
+                tp[1] = gtimer_ns();
+                const double den = s_alpha * s_alpha * densum;
+                if (!isfinite(num) || !isfinite(den)) {
+                    code = 1;
+                    st->status = QIHT_ERR_NONFINITE;
+                } else if (num == 0.0 || den == 0.0) {
+                    code = 1;                                  // converged: x stays
+                } else {
+                    mu = num / den;
                 }
+                muf = (float)mu;
+                dec_put(&st->dec_word, dec_use, code, muf);
+                if (code) {
+                    st->stop = 1;
+                    if (a.report) {
+                        a.report->iters_run = iter0;
+                        a.report->backtracks = st_bt;
+                        a.report->support_changes = st_sc;
+                        a.report->status = st->status;
+                        a.report->resid_norm2 = st->resid2;
+                        a.report->mu = st->mu_accepted;
+                    }
+                }
+                s_code = (int)code;
+                s_muf = muf;
             }
-            s_code = code;
-            s_muf = (float)mu;
+            __syncthreads();
+            code = (unsigned)s_code;
+            muf = s_muf;
+        } else {
+            if (!dec_wait(&st->dec_word, dec_use, &code, &muf, st)) return;
+            if (tid == 0) s_muf = muf;
         }
+        ++dec_use;
+        if (code) return;                                      // uniform across CTAs
         __syncthreads();
-        if (s_code) return;                                    // uniform across CTAs
     }
 
-    int bt = 0;
+    int bt = 0, rounds = 0, full_here = 0;
     SelResult sr{};
     for (;;) {
         const float muf = s_muf;
@@ -1311,6 +1490,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         const bool exact = cand_ok && select_fast(a, sm, s + cnt, muf, outside, sr);
         if (!exact) {
             // keys of all n entries, then the one-CTA radix select
+            ++full_here;
             const int per = (n + gridDim.x - 1) / gridDim.x;
             const int j0 = min(n, (int)blockIdx.x * per), j1 = min(n, j0 + per);
             int bad = 0;
@@ -1322,10 +1502,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
             if (__syncthreads_or(bad) && tid == 0) st->status = QIHT_ERR_NONFINITE;
             if (!grid_sync(a.gbar, target, st)) return;
             if (__ldcg(&st->status) == QIHT_ERR_NONFINITE) {
-                if (blockIdx.x == 0 && tid == 0) st->stop = 1;
+                if (cta0 && tid == 0) st->stop = 1;
                 return;
             }
-            if (blockIdx.x == 0) {
+            if (cta0) {
                 SelSmem fs{};
                 fs.hist = sm.key;                              // s + gcap >= 2048 entries
                 fs.bitmap = sm.bitmap;
@@ -1351,87 +1531,91 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
             }
             __syncthreads();
         }
-        if (stamp && bt == 0) st->t_phase[2] = gtimer_ns();
+        if (cta0 && tid == 0 && bt == 0) tp[2] = gtimer_ns();
         if (!sr.changed) break;
 
-        // ---- Omega: backtracking test on G' u G (partial slots alternate with the round) ----
-        const int ko = (bt & 1) ? 6 : 2;
+        // ---- Omega: backtracking test on G' u G; CTA 0 decides, the others wait ----
+        const unsigned otag = (omega_uses + (unsigned)rounds) & 1u;
+        ++rounds;
+        double dsq = 0.0;                                      // CTA 0, warp 0
         {
-            double dsq = 0.0;
-            if (blockIdx.x == 0 && tid < 32) {
+            if (cta0 && tid < 32) {
                 for (int i = lane; i < sr.uc; i += 32) dsq += (double)sm.u_delta[i] * (double)sm.u_delta[i];
                 dsq = warp_sum_d(dsq);
             }
             rows_product_sm<BITS>(a, rb, sm.u_idx, sm.u_delta, sr.uc, sm.red, sm.zrow);
             double acc = 0.0;
-            if (tid < nrow_thr) {
-                const int row = (rb.w0 + tid / G) * G + tid % G;
-                if (rb.w0 + tid / G < rb.w1 && row < m) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
-            }
+            if (row_ok) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
             acc = cta_sum_n(acc, nrow_thr, shd);
-            if (tid == 0) {
-                mypart[ko] = acc;
-                if (blockIdx.x == 0) mypart[ko + 1] = dsq;
-            }
+            if (tid == 0) slot_put(mypart + 2 * kSlotCtas, acc, otag);
         }
-        if (!grid_sync(a.gbar, target, st)) return;
-        const double ddsum = grid_partial_sum(a.part, ko, shd);
-        if (tid == 0) {
-            const double dd = s_alpha * s_alpha * ddsum;
-            const double dn = __ldcg(a.part + ko + 1);
-            int code = 0;                                      // 0 accept, 1 shrink, 2 give up
-            if (dn > 0.0) {                                    // else nothing moves: accept
-                const double omega = dd > 0.0 ? dn / dd : INFINITY;
-                if (!(mu <= (1.0 - a.c) * omega)) {            // insufficient decrease
-                    if (bt >= a.max_bt) {
-                        code = 2;
-                        if (blockIdx.x == 0) {
+        unsigned code = 0;                                     // 0 accept, 1 shrink, 2 give up
+        float mnew = 0.0f;
+        if (cta0) {
+            double ddsum = 0.0;
+            if (!slot_gather(a.part, 2, -1, -1, otag, &ddsum, nullptr, nullptr, st, shd)) return;
+            if (tid == 0) {
+                const double dd = s_alpha * s_alpha * ddsum;
+                const double dn = dsq;
+                if (dn > 0.0) {                                // else nothing moves: accept
+                    const double omega = dd > 0.0 ? dn / dd : INFINITY;
+                    if (!(mu <= (1.0 - a.c) * omega)) {        // insufficient decrease
+                        if (bt >= a.max_bt) {
+                            code = 2;
                             st->status = QIHT_ERR_BACKTRACK_CAP;
                             st->stop = 1;
                             if (a.report) {
-                                a.report->iters_run = st->iter;
-                                a.report->backtracks = st->backtracks_total;
-                                a.report->support_changes = st->support_changes_total;
-                                a.report->status = st->status;
+                                a.report->iters_run = iter0;
+                                a.report->backtracks = st_bt;
+                                a.report->support_changes = st_sc;
+                                a.report->status = QIHT_ERR_BACKTRACK_CAP;
                                 a.report->resid_norm2 = st->resid2;
                                 a.report->mu = st->mu_accepted;
                             }
+                        } else {
+                            code = 1;
+                            mu = mu / (a.k * (1.0 - a.c));
                         }
-                    } else {
-                        code = 1;
-                        mu = mu / (a.k * (1.0 - a.c));
-                        s_muf = (float)mu;
                     }
                 }
+                mnew = (float)mu;
+                dec_put(&st->dec_word, dec_use, code, mnew);
+                s_code = (int)code;
+                s_muf = mnew;
             }
-            s_code = code;
+            __syncthreads();
+            code = (unsigned)s_code;
+        } else {
+            if (!dec_wait(&st->dec_word, dec_use, &code, &mnew, st)) return;
+            if (tid == 0) s_muf = mnew;
         }
+        ++dec_use;
         __syncthreads();
-        if (s_code == 0) break;
-        if (s_code == 2) return;
+        if (code == 0) break;
+        if (code == 2) return;
         ++bt;
     }
 
     // ---- Resid: r = Q(y) - Q2_G' x' for this CTA's rows ----
-    if (stamp) st->t_phase[3] = gtimer_ns();
+    if (cta0 && tid == 0) tp[3] = gtimer_ns();
     rows_product_sm<BITS>(a, rb, sm.u_idx, sm.u_val, s, sm.red, sm.zrow);
     {
         double acc = 0.0;
         unsigned mx = 0;
-        if (tid < nrow_thr) {
-            const int row = (rb.w0 + tid / G) * G + tid % G;
-            if (rb.w0 + tid / G < rb.w1 && row < m) {
-                const float ri = fmaf(-alpha_f, sm.zrow[tid], __ldcg(a.yhat + row));
-                a.r[row] = ri;
-                acc = (double)ri * (double)ri;
-                mx = __float_as_uint(ri) & 0x7fffffffu;
-            }
+        if (row_ok) {
+            const float ri = fmaf(-alpha_f, sm.zrow[tid], yrow);
+            a.r[row] = ri;
+            acc = (double)ri * (double)ri;
+            mx = __float_as_uint(ri) & 0x7fffffffu;
         }
         acc = cta_sum_n(acc, nrow_thr, shd);
         mx = cta_max(mx, shu);
-        if (tid == 0) { mypart[4] = acc; mypart[5] = (double)mx; }
+        if (tid == 0) {
+            slot_put(mypart + 4 * kSlotCtas, acc, tag);
+            slot_put(mypart + 5 * kSlotCtas, (double)mx, tag);
+        }
     }
-    if (stamp) st->t_phase[4] = gtimer_ns();
+    if (cta0 && tid == 0) tp[4] = gtimer_ns();
     // ---- this CTA's slice of x and of the position map ----
     {
         const int per = (n + gridDim.x - 1) / gridDim.x;
@@ -1451,34 +1635,23 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
             }
         }
     }
-    // the last CTA to arrive commits the scalars, G and x_G (no CTA waits for it)
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = (atomicAdd(a.bar + 2, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double resid2, rmax;
-    grid_partial_sum_max(a.part, 4, 5, shd, &resid2, &rmax);
-    const int it = __ldcg(&st->iter) + 1;
+    // ---- CTA 0 commits the scalars, G and x_G once every residual partial is in ----
+    if (!cta0) return;
+    double resid2 = 0.0, rmax = 0.0;
+    if (!slot_gather(a.part, 4, 5, -1, tag, &resid2, &rmax, nullptr, st, shd)) return;
+    const int it = iter0 + 1;
     for (int q = tid; q < s; q += blockDim.x) {
         a.support[q] = sm.u_idx[q];
         a.xs[q] = sm.u_val[q];
         if (a.trace.support) a.trace.support[(size_t)it * s + q] = sm.u_idx[q];
     }
     if (tid == 0) {
-        // every state word this thread needs, read at once
-        const int bt_total = st->backtracks_total + bt;
-        const int sc_total = st->support_changes_total + sr.changed;
-        const int iters = st->iters;
-        int status = st->status;
-        const int fsel = st->full_selects;
-        unsigned long long tp[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) tp[i] = st->t_phase[i];
-        a.bar[2] = 0u;
+        const int bt_total = st_bt + bt;
+        const int sc_total = st_sc + sr.changed;
+        int status = st_status;
         st->iter = it;
+        st->omega_uses = omega_uses + (unsigned)rounds;
+        st->dec_uses = dec_use;
         st->mu = mu;
         st->mu_accepted = mu;
         st->bt = bt;
@@ -1494,7 +1667,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         st->tau_g_bits = (isfinite(tg) && tg > 0.0f) ? __float_as_uint(tg) : 0u;
         st->gcand_count = 0u;
         st->bmax_g = 0u;
-        int stop = it >= iters;
+        int stop = it >= st_iters;
         if (!isfinite(resid2)) {
             status = QIHT_ERR_NONFINITE;
             st->status = status;
@@ -1512,9 +1685,9 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
             a.report->status = status;
             a.report->resid_norm2 = resid2;
             a.report->mu = mu;
-            a.report->full_selects = fsel;
-            // phases: step size, (filter: in the gradient kernel), select, backtracking,
-            // residual product, commit, whole kernel
+            a.report->full_selects = st_fsel + full_here;
+            // phases (CTA 0's clock): step size, (filter: in the gradient kernel), select,
+            // backtracking, residual product, commit, whole kernel
             const unsigned long long t6 = gtimer_ns();
             a.report->phase_us[0] = (float)(tp[1] - tp[0]) * 1e-3f;
             a.report->phase_us[1] = 0.0f;
@@ -1620,7 +1793,7 @@ int iter_grid()
         int n = num_sms();
         const char* e = getenv("QIHT_ITER_GRID");
         if (e && atoi(e) > 0 && atoi(e) < n) n = atoi(e);
-        g = n > 1024 ? 1024 : n;
+        g = n > kSlotCtas ? kSlotCtas : n;     // partial slots hold up to kSlotCtas CTAs
     }
     return g;
 }

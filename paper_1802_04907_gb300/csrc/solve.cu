@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(1024) k_init(InitKernelArgs ka)
     for (int j = threadIdx.x; j < a.n; j += blockDim.x) a.x[j] = 0.0f;
     if (a.pos)
         for (int j = threadIdx.x; j < a.n; j += blockDim.x) a.pos[j] = -1;
+    if (a.part)       // -0.0: tag bit set, value 0 (the first writes carry tag 0)
+        for (int i = threadIdx.x; i < kPartSlots * kSlotCtas; i += blockDim.x) a.part[i] = -0.0;
     // deterministic block reductions
 #pragma unroll
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(1024) k_init(InitKernelArgs ka)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += shd[w]; b = max(b, shu[w]); }
         memset(st, 0, sizeof(State));
         st->iters = a.iters;
+        st->dec_word = 1ull << 63;     // tag 1: the first decision carries tag 0
         st->resid2 = t;
         st->rmax_bits = b;
         st->status = finite ? QIHT_OK : QIHT_ERR_NONFINITE;
@@ -345,7 +348,7 @@ Plan plan_solve(int m, int n, int s)
     p.off_chunk = o; o += align256((size_t)gather_chunks(2 * s) * 8);
     p.off_cand = o; o += align256((size_t)kTopCandCap * 16);     // keys, then values and old x
     p.off_keys = o; o += align256((size_t)n * 4);
-    p.off_part = o; o += align256((size_t)1024 * kPartStride * 8);
+    p.off_part = o; o += align256((size_t)kPartSlots * kSlotCtas * 8);
     p.off_pos = o; o += align256((size_t)n * 4);
     p.off_xs = o; o += align256((size_t)s * 4);
     p.off_gsup = o; o += align256((size_t)s * 4);
@@ -485,6 +488,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     K.ia.a.r = r;
     K.ia.a.x = x;
     K.ia.a.pos = fb.pos;
+    K.ia.a.part = fast ? reinterpret_cast<double*>(ws + pl.off_part) : nullptr;
     K.ia.a.n = n;
     K.ia.a.m = m;
     K.ia.a.s = s;
