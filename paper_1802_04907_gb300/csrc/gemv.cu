@@ -85,12 +85,13 @@ __global__ void __launch_bounds__(256) k_gemv_t(GemvTArgs a, int tpc)
     constexpr int NW = RPT / G;           // words per thread per column
     constexpr int NL = RPT / 4;           // limb words per limb per thread
 
+    griddep_wait();
     if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
         // the solver's outer loop continues while not stopped, and never more than
         // iters + 1 times even if a stop were missed
         const int guard = ++a.st->outer_guard;
         cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
-                                (!a.st->stop && guard < a.st->iters + 1) ? 1u : 0u);
+                                (!a.st->stop && guard < a.guard_limit) ? 1u : 0u);
     }
     if (a.st && a.st->stop) return;
     const int m = a.Q.rows, n = a.Q.cols, ld = a.Q.ld;
@@ -294,10 +295,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
     constexpr int NLW = PPT * 4 * E;            // limb words per limb per thread
 
     extern __shared__ __align__(128) unsigned char smem[];
+    griddep_wait();
     if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
         const int guard = ++a.st->outer_guard;
         cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
-                                (!a.st->stop && guard < a.st->iters + 1) ? 1u : 0u);
+                                (!a.st->stop && guard < a.guard_limit) ? 1u : 0u);
     }
     if (a.st && a.st->stop) return;
 
@@ -506,10 +508,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
     constexpr int PPL = PPC / 32;              // pieces per lane per column chunk
 
     extern __shared__ __align__(128) unsigned char smem[];
+    griddep_wait();
     if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
         const int guard = ++a.st->outer_guard;
         cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
-                                (!a.st->stop && guard < a.st->iters + 1) ? 1u : 0u);
+                                (!a.st->stop && guard < a.guard_limit) ? 1u : 0u);
     }
     if (a.st && a.st->stop) return;
 
@@ -692,7 +695,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
 }
 
 // ---------------------------------------------------------------------------
-// Warp-per-column variant (the default). Many warps per SM (4 CTAs x 8 warps),
+// Warp-per-column variant (the default). Many warps per SM (2 CTAs x 16 warps),
 // each warp owns whole columns (static round-robin over the columns), so its
 // integer sums never leave the warp. A lane loads NPL 16-byte pieces of the
 // column at once (coalesced: consecutive lanes, consecutive pieces), which keeps
@@ -707,29 +710,23 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
 // |g| >= tau_g is appended to the candidate list (the largest |g| below tau_g is
 // kept per CTA and merged with one atomic).
 // ---------------------------------------------------------------------------
+constexpr int kWarpThreads = 512;           // 16 warps per CTA, two CTAs per SM
+
 template <int BITS, int NPL>
-__global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
+__global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;
     constexpr int L = 1 << BITS;
     constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
     extern __shared__ __align__(16) uint32_t limb[];    // [3][E][P][4]
-    __shared__ long long red_r[8];
+    __shared__ long long red_r[16];
     __shared__ unsigned bmax_cta;
     __shared__ double outscale_sh;
 
-    if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
-        const int guard = ++a.st->outer_guard;
-        cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
-                                (!a.st->stop && guard < a.st->iters + 1) ? 1u : 0u);
-    }
-    if (a.st && a.st->stop) return;
     const int n = a.Q.cols, ld = a.Q.ld, m = a.Q.rows;
     const int P = ld / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    const int sh = fixed_shift(*a.rmax_bits);
 
     // Software pipeline over the warp's sequence of batches (column j, batch pb of NPL
     // pieces per lane): the loads of the next batch are in flight while this one is used.
@@ -758,6 +755,18 @@ __global__ void __launch_bounds__(256, 4) k_gemv_t_warp(GemvTArgs a)
     };
     uint4 cA[NPL], cB[NPL];
     if (j < n) load_batch(cA, j, pb);
+
+    // everything above reads only the codes; r, max |r| and the solver state come from
+    // the previous kernel
+    griddep_wait();
+    griddep_launch();
+    if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int guard = ++a.st->outer_guard;
+        cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
+                                (!a.st->stop && guard < a.guard_limit) ? 1u : 0u);
+    }
+    if (a.st && a.st->stop) return;
+    const int sh = fixed_shift(*a.rmax_bits);
 
     // residual to 24-bit fixed point, as three byte planes; four rows (one float4) per limb
     // word, UR words of a thread in flight at once
@@ -934,10 +943,10 @@ static WarpPlan plan_warp(const Codes& Q, int nsm)
     else p.fn = (void*)k_gemv_t_warp<2, 1>;
     cudaFuncSetAttribute(p.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p.fn, 256, p.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p.fn, kWarpThreads, p.smem);
     if (occ < 1) return p;
     long long grid = (long long)nsm * occ;
-    const long long want = ((long long)Q.cols + 7) / 8;
+    const long long want = ((long long)Q.cols + kWarpThreads / 32 - 1) / (kWarpThreads / 32);
     if (grid > want) grid = want;
     p.grid = (unsigned)(grid < 1 ? 1 : grid);
     p.ok = true;
@@ -1107,7 +1116,7 @@ void gemv_t_node(const GemvTArgs& a, int nsm, cudaKernelNodeParams* p, void** ar
         if (wp.ok) {
             p->func = wp.fn;
             p->gridDim = dim3(wp.grid);
-            p->blockDim = dim3(256);
+            p->blockDim = dim3(kWarpThreads);
             p->sharedMemBytes = (unsigned)wp.smem;
             p->kernelParams = argbuf;        // (GemvTArgs)
             p->extra = nullptr;
@@ -1162,7 +1171,7 @@ cudaError_t launch_gemv_t(const GemvTArgs& a, int nsm, cudaStream_t s)
         if (wp.ok) {
             GemvTArgs copy = a;
             void* args[1] = {&copy};
-            return cudaLaunchKernel(wp.fn, dim3(wp.grid), dim3(256), args, wp.smem, s);
+            return cudaLaunchKernel(wp.fn, dim3(wp.grid), dim3(kWarpThreads), args, wp.smem, s);
         }
     }
     if (use_col()) {

@@ -14,6 +14,13 @@ constexpr int kMaxTopN = 49152;   // n limit of the one-CTA radix select (keys h
 constexpr int kGatherCols = 32;   // list entries (columns) per CTA in the column-subset product
 constexpr int kGatherThreads = 256;
 
+// Programmatic dependent launch: a kernel launched with a programmatic edge may start
+// while its upstream kernel still runs; griddep_wait() returns once the upstream grid
+// has completed and its memory is visible (a no-op for an ordinary launch), and
+// griddep_launch() lets the downstream kernel start early.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Device view of a quantized matrix (see the column-packed layout in qiht.h).
 struct Codes {
     const uint32_t* words;
@@ -98,6 +105,7 @@ struct GemvTArgs {
     float* g;
     State* st;                  // non-null in the solver: skip when st->stop
     unsigned long long h_outer; // outer-loop handle (solver loop body only): set by thread 0 of CTA 0
+    int guard_limit;            // loop-body executions allowed (bounds the outer loop)
     unsigned* err;              // optional: set to 1 when a device-side wait runs out (no solver state)
     // solver loop body with the fast-path iteration kernel (nullptr elsewhere)
     const int32_t* pos;         // position of every column in the support G, -1 outside

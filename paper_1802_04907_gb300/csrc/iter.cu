@@ -795,6 +795,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     __shared__ double shd[33];
     __shared__ unsigned shu[33];
     State* st = a.st;
+    griddep_wait();                             // the previous kernels' results are visible
+    griddep_launch();
     if (st->stop) return;                       // uniform: read before any barrier
     const bool stamp = blockIdx.x == 0 && threadIdx.x == 0;
     if (stamp) st->t_phase[0] = gtimer_ns();
@@ -1355,26 +1357,35 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     __shared__ float s_alpha_f, s_muf;
     __shared__ int s_code;
     State* st = a.st;
-    if (st->stop) return;                       // uniform: read before any exchange
     const int tid = threadIdx.x, lane = tid & 31;
     const bool cta0 = blockIdx.x == 0;
-    unsigned long long tp[5] = {0, 0, 0, 0, 0};  // CTA 0, thread 0: phase clock
-    if (cta0 && tid == 0) tp[0] = gtimer_ns();
     // FP64 work (low throughput on this GPU) is done by single threads or single warps
-    unsigned long long target = 0;
-    if (tid == 0) target = barrier_base(a.gbar);
     if (tid == 32) {
         const double al = (double)(*a.Q.scale) / (double)(L - 1);
         s_alpha = al;
         s_alpha_f = (float)al;
     }
-
     const RowBlock rb = row_block(a.Q.ld);
     const FastSm sm = fast_smem_layout(a, smem, G);
     const int m = a.m, s = a.s, n = a.n;
     double* mypart = a.part + blockIdx.x;       // slot k of this CTA: mypart[k * kSlotCtas]
     const int nbw4 = (((n + 31) / 32) + 3) & ~3;
     const int nrow_thr = rb.wpc * G;            // threads that hold one row of this CTA
+    float yrow = 0.0f;                          // Q(y) of this thread's row (fixed during the solve)
+    int row_ok = 0, row = 0;
+    if (tid < nrow_thr) {
+        row = (rb.w0 + tid / G) * G + tid % G;
+        row_ok = rb.w0 + tid / G < rb.w1 && row < m;
+        if (row_ok) yrow = __ldcg(a.yhat + row);
+    }
+    // everything above is fixed during the solve; the rest comes from the previous kernels
+    griddep_wait();
+    griddep_launch();
+    if (st->stop) return;                       // uniform: read before any exchange
+    unsigned long long tp[5] = {0, 0, 0, 0, 0};  // CTA 0, thread 0: phase clock
+    if (cta0 && tid == 0) tp[0] = gtimer_ns();
+    unsigned long long target = 0;
+    if (tid == 0) target = barrier_base(a.gbar);
 
     // ---- state, G, x_G, g_G, the first candidates and Q(y) of this CTA's rows, all at once ----
     const int iter0 = __ldcg(&st->iter);
@@ -1390,13 +1401,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         st_iters = st->iters;
         st_status = st->status;
         st_fsel = st->full_selects;
-    }
-    float yrow = 0.0f;
-    int row_ok = 0, row = 0;
-    if (tid < nrow_thr) {
-        row = (rb.w0 + tid / G) * G + tid % G;
-        row_ok = rb.w0 + tid / G < rb.w1 && row < m;
-        if (row_ok) yrow = __ldcg(a.yhat + row);
     }
     unsigned long long cspec = 0;
     if (tid < a.gcap) cspec = __ldcg(a.gcand + tid);   // speculative: used if tid < count

@@ -424,6 +424,30 @@ qiht_status add_while(cudaGraph_t g, cudaGraphNode_t* out, const cudaGraphNode_t
 
 static bool multi_kernel_iteration();
 
+// QIHT_PDL=0 turns the programmatic edges of the loop body off; QIHT_UNROLL sets the
+// iterations per body execution with them (default 8). For measurement.
+static bool use_pdl()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("QIHT_PDL");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+static int body_unroll()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("QIHT_UNROLL");
+        v = e ? atoi(e) : 8;
+        if (v < 1) v = 1;
+        if (v > 16) v = 16;
+    }
+    return v;
+}
+
 // The solver's kernels and their arguments, shared by the graph driver and the eager driver.
 struct SolveKernels {
     InitKernelArgs ia;
@@ -515,6 +539,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     gemv_t_node(K.g0, nsm, &K.p_g0, K.a_g0);
     K.gb = K.g0;
     K.gb.h_outer = h_outer;         // the loop body's product decides whether to go on
+    K.gb.guard_limit = iters + 1;
     K.gb.pos = fb.pos;              // and prepares the fast path's next threshold
     K.gb.gsup = fb.gsup;
     K.gb.gcand = fb.gcand;
@@ -675,7 +700,7 @@ qiht_status run_eager(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_cod
 // any other case into QIHT_ERR_TIMEOUT.
 qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s, int iters,
                         const qiht_params* prm, float* x, int32_t* support, qiht_report* report,
-                        const qiht_trace* trace, char* ws, bool cooperative, cudaGraph_t* out)
+                        const qiht_trace* trace, char* ws, bool cooperative, bool pdl, int unroll, cudaGraph_t* out)
 {
     cudaGraph_t top;
     CK(cudaGraphCreate(&top, 0));
@@ -702,14 +727,38 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
                  (unsigned long long)h_bt);
 
     if (!multi_kernel_iteration()) {
-        cudaGraphNode_t b_it, b_gk;
-        TRY(add_kernel(body, &b_it, nullptr, 0, K.p_it));
-        if (cooperative) {
-            cudaLaunchAttributeValue coop{};
-            coop.cooperative = 1;
-            CK(cudaGraphKernelNodeSetAttribute(b_it, cudaLaunchAttributeCooperative, &coop));
+        // `unroll` iterations per body execution; with `pdl`, programmatic edges let each
+        // kernel start (and issue its loads that do not depend on the previous kernel)
+        // while the previous one finishes
+        GemvTArgs inner = K.gb;
+        inner.h_outer = 0;                           // only the body's last product steers the loop
+        void* inner_args[3] = {&inner, &K.tpcb, &K.nsb};
+        cudaKernelNodeParams p_inner = K.p_gb;
+        p_inner.kernelParams = inner_args;
+        GemvTArgs last = K.gb;
+        last.guard_limit = (iters + unroll - 1) / unroll + 1;
+        void* last_args[3] = {&last, &K.tpcb, &K.nsb};
+        cudaKernelNodeParams p_last = K.p_gb;
+        p_last.kernelParams = last_args;
+        cudaGraphEdgeData prog{};
+        prog.from_port = cudaGraphKernelNodePortProgrammatic;
+        prog.to_port = cudaGraphKernelNodePortDefault;
+        prog.type = cudaGraphDependencyTypeProgrammatic;
+        cudaGraphNode_t prev = nullptr;
+        for (int u = 0; u < unroll; ++u) {
+            cudaGraphNode_t b_it, b_gk;
+            TRY(add_kernel(body, &b_it, pdl || !prev ? nullptr : &prev, pdl || !prev ? 0 : 1, K.p_it));
+            if (pdl && prev) CK(cudaGraphAddDependencies(body, &prev, &b_it, &prog, 1));
+            if (cooperative) {
+                cudaLaunchAttributeValue coop{};
+                coop.cooperative = 1;
+                CK(cudaGraphKernelNodeSetAttribute(b_it, cudaLaunchAttributeCooperative, &coop));
+            }
+            const cudaKernelNodeParams& pg = u == unroll - 1 ? p_last : p_inner;
+            TRY(add_kernel(body, &b_gk, pdl ? nullptr : &b_it, pdl ? 0 : 1, pg));
+            if (pdl) CK(cudaGraphAddDependencies(body, &b_it, &b_gk, &prog, 1));
+            prev = b_gk;
         }
-        TRY(add_kernel(body, &b_gk, &b_it, 1, K.p_gb));
         *out = top;
         return QIHT_OK;
     }
@@ -799,10 +848,16 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
         } else {
             cudaGraph_t graph = nullptr;
             qiht_status st = QIHT_ERR_CUDA;
-            for (int coop = 1; coop >= 0 && st != QIHT_OK; --coop) {
+            // preferred first: programmatic edges with the cooperative attribute, then without
+            // either; the kernels are correct under all four
+            const int unroll = body_unroll();
+            for (int attempt = 0; attempt < 4 && st != QIHT_OK; ++attempt) {
+                const bool pdl = attempt < 2 && use_pdl();
+                const bool coop = (attempt & 1) == 0;
+                if (!use_pdl() && attempt < 2) continue;
                 if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
                 st = build_graph(Q1, Q2, y, s, iters, &prm, x, support, report, trace ? &tr : nullptr,
-                                 reinterpret_cast<char*>(workspace), coop == 1, &graph);
+                                 reinterpret_cast<char*>(workspace), coop, pdl, pdl ? unroll : 1, &graph);
                 if (st == QIHT_OK) {
                     const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
                     if (e != cudaSuccess) {
