@@ -41,6 +41,8 @@ M, N, S, ITERS = 8192, 32768, 256, 300
 METRIC = "NIHT iterations/s"
 UNIT = "iterations/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemv_t_traffic.txt")
+# iterations per execution of the solver graph's loop body (the library's default)
+BODY_UNROLL = int(os.environ.get("QIHT_UNROLL", "8"))
 
 
 def parse():
@@ -348,8 +350,11 @@ def run_ours(args):
                "d2h_bytes_per_step": int(4 * args.n + 4 * args.s + q.REPORT_BYTES)}
 
     # kernels launched per step: 2 max-abs + 3 quantize, 3 in the solver's set-up, then per
-    # iteration the persistent iteration kernel and the gradient kernel (shrinks stay inside)
-    launches_per_step = 5 + 3 + 2 * iters_done
+    # iteration the persistent iteration kernel and the gradient kernel (shrinks stay inside);
+    # the graph runs its loop body (BODY_UNROLL iterations) whole, the kernels after the
+    # last iteration return at once
+    unroll = 1 if args.eager else BODY_UNROLL
+    launches_per_step = 5 + 3 + 2 * unroll * -(-iters_done // unroll)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(p, bits, args.iters)

@@ -167,11 +167,17 @@ qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float
                               stream every iteration). Same kernels and results as the graph;
                               meant for debugging and per-kernel profiling. */
 
+#define QIHT_SOLVE_TEST_TIMEOUT 2  /* test hook, not part of the method: the iteration kernel's CTA 0
+                                     withholds its first step-size decision, so every other CTA's
+                                     bounded wait on it runs out (about 0.2 s) and the solve stops
+                                     with QIHT_ERR_TIMEOUT in the report; the CUDA context stays
+                                     usable. Honoured by the kernel used for s <= 1024. */
+
 typedef struct {
     double k;               /* shrinkage of the step size, k > 1/(1-c) (Section II-A); default 2 */
     double c;               /* small constant of the descent test, 0 < c < 1; default 0.01 */
     int32_t max_backtrack;  /* shrinks allowed per iteration before QIHT_ERR_BACKTRACK_CAP; default 32 */
-    int32_t flags;          /* 0 or QIHT_SOLVE_EAGER */
+    int32_t flags;          /* 0 or QIHT_SOLVE_EAGER, QIHT_SOLVE_TEST_TIMEOUT */
 } qiht_params;
 
 typedef struct {            /* written on the device after every iteration */

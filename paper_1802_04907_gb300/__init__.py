@@ -24,6 +24,7 @@ OK, ERR_ARG, ERR_BITS, ERR_NONFINITE, ERR_TIMEOUT, ERR_BACKTRACK_CAP, ERR_CUDA, 
 SCALE_GIVEN = 1
 CHECK_FINITE = 2
 SOLVE_EAGER = 1
+SOLVE_TEST_TIMEOUT = 2
 
 # stream ids of the random numbers, by convention of the solver
 STREAM_Q1, STREAM_Q2, STREAM_Y = 0, 1, 2
@@ -268,9 +269,11 @@ class Solver:
     cached CUDA graph is reused on every call."""
 
     def __init__(self, m: int, n: int, s: int, iters: int, *, device="cuda", trace: bool = False,
-                 k: float = 2.0, c: float = 0.01, max_backtrack: int = 32, eager: bool = False):
+                 k: float = 2.0, c: float = 0.01, max_backtrack: int = 32, eager: bool = False,
+                 test_timeout: bool = False):
         self.m, self.n, self.s, self.iters = m, n, s, iters
-        self.params = _Params(k, c, max_backtrack, SOLVE_EAGER if eager else 0)
+        self.params = _Params(k, c, max_backtrack,
+                              (SOLVE_EAGER if eager else 0) | (SOLVE_TEST_TIMEOUT if test_timeout else 0))
         self.x = torch.empty(n, dtype=torch.float32, device=device)
         self.support = torch.empty(s, dtype=torch.int32, device=device)
         self.report = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=device)

@@ -188,7 +188,8 @@ struct IterFastBufs {
 void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* support, int32_t* sel, float* val,
                int32_t* uni, float* delta, const float* yhat, float* r, uint32_t* keys, unsigned long long* cand,
                double* part, const IterFastBufs& fb, int n, int m, int s, double k, double c, int max_bt,
-               qiht_report* report, const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore, void** argbuf);
+               int flags, qiht_report* report, const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore,
+               void** argbuf);
 size_t iter_args_bytes();
 
 int gather_row_blocks(int rows, int bits);

@@ -39,11 +39,19 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
     return v;
 }
 
+// A bounded wait ran out: stop the solve and say so in the state and the report.
+__device__ __forceinline__ void report_timeout(State* st, qiht_report* rep)
+{
+    st->status = QIHT_ERR_TIMEOUT;
+    st->stop = 1;
+    if (rep) rep->status = QIHT_ERR_TIMEOUT;
+}
+
 // Grid barrier on one 64-bit arrival counter that only grows: thread 0 of every CTA
 // adds 1 with release semantics and waits (acquire) until the counter reaches the
 // barrier's target, a multiple of the grid size. Only thread 0 of a CTA holds the
 // target. Waiting is bounded by %globaltimer; a timeout marks the state and returns false.
-__device__ bool grid_sync(unsigned long long* cnt, unsigned long long& target, State* st)
+__device__ bool grid_sync(unsigned long long* cnt, unsigned long long& target, State* st, qiht_report* rep)
 {
     __shared__ int ok_sh;
     __syncthreads();
@@ -58,10 +66,7 @@ __device__ bool grid_sync(unsigned long long* cnt, unsigned long long& target, S
                 if (gtimer_ns() - t0 > kBarrierBudgetNs) { ok = 0; break; }
             }
         }
-        if (!ok) {
-            st->status = QIHT_ERR_TIMEOUT;
-            st->stop = 1;
-        }
+        if (!ok) report_timeout(st, rep);
         ok_sh = ok;
     }
     __syncthreads();
@@ -236,7 +241,7 @@ __device__ __forceinline__ unsigned long long slot_ld(const double* p)
 // once. Waiting is bounded by %globaltimer; false on timeout.
 
 __device__ bool slot_gather(const double* part, int ks, int km, int ke, unsigned tag, double* sum, double* mx,
-                            double* ext, State* st, double* sh)
+                            double* ext, State* st, qiht_report* rep, double* sh)
 {
     __shared__ int ok_sh;
     const int lane = threadIdx.x & 31;
@@ -291,10 +296,7 @@ __device__ bool slot_gather(const double* part, int ks, int km, int ke, unsigned
             sh[30] = w;
             sh[31] = e;
             ok_sh = ok;
-            if (!ok) {
-                st->status = QIHT_ERR_TIMEOUT;
-                st->stop = 1;
-            }
+            if (!ok) report_timeout(st, rep);
         }
     }
     __syncthreads();
@@ -319,7 +321,8 @@ __device__ __forceinline__ void dec_put(unsigned long long* p, unsigned tag, uns
 }
 
 // Thread 0 polls the decision word until it carries `tag`; every thread gets code and value.
-__device__ bool dec_wait(const unsigned long long* p, unsigned tag, unsigned* code, float* v, State* st)
+__device__ bool dec_wait(const unsigned long long* p, unsigned tag, unsigned* code, float* v, State* st,
+                         qiht_report* rep)
 {
     __shared__ unsigned long long sw;
     __shared__ int ok_sh;
@@ -335,10 +338,7 @@ __device__ bool dec_wait(const unsigned long long* p, unsigned tag, unsigned* co
                 asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
             } while ((w >> 63) != want);
         }
-        if (!ok) {
-            st->status = QIHT_ERR_TIMEOUT;
-            st->stop = 1;
-        }
+        if (!ok) report_timeout(st, rep);
         sw = w;
         ok_sh = ok;
     }
@@ -380,6 +380,7 @@ struct IterArgs {
     int n, m, s;
     double k, c;
     int max_bt;
+    int flags;                  // QIHT_SOLVE_* (the test hook QIHT_SOLVE_TEST_TIMEOUT)
     qiht_report* report;
     qiht_trace trace;
 };
@@ -833,7 +834,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         const double num = cta_sum(gsq, shd);                // ||g_G||^2 from the staged coefficients
         if (tid == 0) { mypart[0 * kSlotCtas] = acc; mypart[1 * kSlotCtas] = num; }
     }
-    if (!grid_sync(a.gbar, target, st)) return;
+    if (!grid_sync(a.gbar, target, st, a.report)) return;
     if (stamp) st->t_phase[1] = gtimer_ns();
     double mu;
     {
@@ -912,7 +913,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             if (tid == 0 && bcta) atomicMax(&st->below_max, bcta);
             if (__syncthreads_or(bad) && tid == 0) st->status = QIHT_ERR_NONFINITE;
         }
-        if (!grid_sync(a.gbar, target, st)) return;
+        if (!grid_sync(a.gbar, target, st, a.report)) return;
         if (stamp) st->t_phase[2] = gtimer_ns();
         if (__ldcg(&st->status) == QIHT_ERR_NONFINITE) {
             if (blockIdx.x == 0 && tid == 0) st->stop = 1;
@@ -920,7 +921,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         }
         // ---- Select on CTA 0 ----
         if (blockIdx.x == 0) select_on_cta0(a, (float)mu, sel_smem_layout(a, sel_smem), true);
-        if (!grid_sync(a.gbar, target, st)) return;
+        if (!grid_sync(a.gbar, target, st, a.report)) return;
         if (stamp) st->t_phase[3] = gtimer_ns();
         if (!__ldcg(&st->changed)) break;
 
@@ -938,7 +939,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
             const double dn = cta_sum(dsq, shd);             // ||x' - x||^2 from the staged list
             if (tid == 0) { mypart[2 * kSlotCtas] = acc; mypart[3 * kSlotCtas] = dn; }
         }
-        if (!grid_sync(a.gbar, target, st)) return;
+        if (!grid_sync(a.gbar, target, st, a.report)) return;
         const double dd = s_alpha * s_alpha * grid_partial_sum(a.part, 2, shd);
         const double dn = __ldcg(a.part + 3 * kSlotCtas);
         if (!(dn > 0.0)) break;                               // nothing moves: accept
@@ -1446,7 +1447,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         float muf = 0.0f;
         if (cta0) {
             double densum = 0.0;
-            if (!slot_gather(a.part, 0, -1, -1, tag, &densum, nullptr, nullptr, st, shd)) return;
+            if (!slot_gather(a.part, 0, -1, -1, tag, &densum, nullptr, nullptr, st, a.report, shd)) return;
             if (tid == 0) {
                 tp[1] = gtimer_ns();
                 const double den = s_alpha * s_alpha * densum;
@@ -1459,7 +1460,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
                     mu = num / den;
                 }
                 muf = (float)mu;
-                dec_put(&st->dec_word, dec_use, code, muf);
+                // test hook: withhold the first decision so that the other CTAs' waits run out
+                if (!((a.flags & QIHT_SOLVE_TEST_TIMEOUT) && iter0 == 0)) dec_put(&st->dec_word, dec_use, code, muf);
                 if (code) {
                     st->stop = 1;
                     if (a.report) {
@@ -1478,7 +1480,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
             code = (unsigned)s_code;
             muf = s_muf;
         } else {
-            if (!dec_wait(&st->dec_word, dec_use, &code, &muf, st)) return;
+            if (!dec_wait(&st->dec_word, dec_use, &code, &muf, st, a.report)) return;
             if (tid == 0) s_muf = muf;
         }
         ++dec_use;
@@ -1504,7 +1506,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
                 a.keys[j] = k;
             }
             if (__syncthreads_or(bad) && tid == 0) st->status = QIHT_ERR_NONFINITE;
-            if (!grid_sync(a.gbar, target, st)) return;
+            if (!grid_sync(a.gbar, target, st, a.report)) return;
             if (__ldcg(&st->status) == QIHT_ERR_NONFINITE) {
                 if (cta0 && tid == 0) st->stop = 1;
                 return;
@@ -1517,7 +1519,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
                 fs.sup = sm.u_idx;
                 select_on_cta0(a, muf, fs, false);
             }
-            if (!grid_sync(a.gbar, target, st)) return;
+            if (!grid_sync(a.gbar, target, st, a.report)) return;
             sr.changed = __ldcg(&st->changed);
             sr.uc = __ldcg(&st->union_count);
             sr.kth0 = __ldcg(&st->kth0);
@@ -1557,7 +1559,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         float mnew = 0.0f;
         if (cta0) {
             double ddsum = 0.0;
-            if (!slot_gather(a.part, 2, -1, -1, otag, &ddsum, nullptr, nullptr, st, shd)) return;
+            if (!slot_gather(a.part, 2, -1, -1, otag, &ddsum, nullptr, nullptr, st, a.report, shd)) return;
             if (tid == 0) {
                 const double dd = s_alpha * s_alpha * ddsum;
                 const double dn = dsq;
@@ -1590,7 +1592,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
             __syncthreads();
             code = (unsigned)s_code;
         } else {
-            if (!dec_wait(&st->dec_word, dec_use, &code, &mnew, st)) return;
+            if (!dec_wait(&st->dec_word, dec_use, &code, &mnew, st, a.report)) return;
             if (tid == 0) s_muf = mnew;
         }
         ++dec_use;
@@ -1642,7 +1644,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     // ---- CTA 0 commits the scalars, G and x_G once every residual partial is in ----
     if (!cta0) return;
     double resid2 = 0.0, rmax = 0.0;
-    if (!slot_gather(a.part, 4, 5, -1, tag, &resid2, &rmax, nullptr, st, shd)) return;
+    if (!slot_gather(a.part, 4, 5, -1, tag, &resid2, &rmax, nullptr, st, a.report, shd)) return;
     const int it = iter0 + 1;
     for (int q = tid; q < s; q += blockDim.x) {
         a.support[q] = sm.u_idx[q];
@@ -1713,7 +1715,8 @@ static size_t iter_smem_bytes(int n, int bits);
 void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* support, int32_t* sel, float* val,
                int32_t* uni, float* delta, const float* yhat, float* r, uint32_t* keys, unsigned long long* cand,
                double* part, const IterFastBufs& fb, int n, int m, int s, double k, double c, int max_bt,
-               qiht_report* report, const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore, void** argbuf)
+               int flags, qiht_report* report, const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore,
+               void** argbuf)
 {
     IterArgs* a = reinterpret_cast<IterArgs*>(argstore);
     *a = IterArgs{};
@@ -1747,6 +1750,7 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
     a->k = k;
     a->c = c;
     a->max_bt = max_bt;
+    a->flags = flags;
     a->report = report;
     a->trace = trace;
     argbuf[0] = a;

@@ -584,7 +584,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     top_filter_node(K.tt, &K.p_tf, K.a_tf);
     iter_node(view(Q2), st, g, x, support, sel, val, uni, delta, yhat, r,
               reinterpret_cast<uint32_t*>(ws + pl.off_keys), cand, reinterpret_cast<double*>(ws + pl.off_part), fb, n, m, s,
-              prm->k, prm->c, prm->max_backtrack, report, tr, &K.p_it, K.iter_store, K.a_it);
+              prm->k, prm->c, prm->max_backtrack, prm->flags, report, tr, &K.p_it, K.iter_store, K.a_it);
 
     GatherArgs base{};
     base.Q = view(Q2);
@@ -806,7 +806,7 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
     qiht_params prm{2.0, 0.01, 32, 0};
     if (params) prm = *params;
     if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 ||
-        (prm.flags & ~QIHT_SOLVE_EAGER) != 0)
+        (prm.flags & ~(QIHT_SOLVE_EAGER | QIHT_SOLVE_TEST_TIMEOUT)) != 0)
         return QIHT_ERR_ARG;
     if (!workspace || workspace_bytes < qiht_solve_workspace_size(m, n, s) || !aligned(workspace, 256))
         return QIHT_ERR_WORKSPACE;
@@ -827,6 +827,7 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
     key.v.push_back(dbits(prm.k));
     key.v.push_back(dbits(prm.c));
     key.v.push_back((uint64_t)prm.max_backtrack);
+    key.v.push_back((uint64_t)prm.flags);
     key.v.push_back(reinterpret_cast<uint64_t>(x));
     key.v.push_back(reinterpret_cast<uint64_t>(support));
     key.v.push_back(reinterpret_cast<uint64_t>(report));

@@ -130,6 +130,24 @@ def interferometry(n_ant: int = 48, grid: int = 128, n_src: int = 50, s: int = 6
 
 
 # Named workloads (sizes from the configurations this library is measured on).
+def duplicated_pm1(m: int, base: int, dup: int, s: int, seed: int) -> Problem:
+    """Phi with +-1 entries whose `base` distinct columns each appear `dup` times in a row
+    (column k * dup + d is distinct column k); x has s nonzeros +-U(0.5, 1.5), each on copy 2
+    (or the last copy) of a distinct column; y = Phi x (noiseless). Entries +-1 sit on the
+    quantizer's end levels, so duplicated columns keep identical codes: a workload with exact
+    ties in the gradient."""
+    rng = _rng(seed)
+    cols = rng.choice(np.array([-1.0, 1.0], dtype=np.float32), size=(m, base))
+    phi = np.ascontiguousarray(np.repeat(cols, dup, axis=1))
+    picks = np.sort(rng.choice(base, size=s, replace=False))
+    support = picks * dup + min(2, dup - 1)
+    x = np.zeros(base * dup)
+    x[support] = rng.uniform(0.5, 1.5, size=s) * rng.choice([-1.0, 1.0], size=s)
+    y = (phi.astype(np.float64) @ x).astype(np.float32)
+    return Problem(phi=phi, y=y, x_true=x, support=support.astype(np.int64), s=s,
+                   name=f"duplicated_pm1_{m}x{base * dup}_s{s}_seed{seed}")
+
+
 def small_noiseless(seed: int = 0) -> Problem:
     """m=256, n=1024, s=16, N(0,1) nonzeros, noiseless (shape of Section IV-A)."""
     return gaussian(256, 1024, 16, seed, snr_db=None, values="normal", name="gaussian_256x1024_s16")

@@ -206,3 +206,67 @@ def test_eager_driver_matches_graph():
     assert a.read_report() == b.read_report()
     for k in a.trace:
         assert torch.equal(a.trace[k], b.trace[k]), k
+
+
+def test_large_support_uses_the_general_iteration_kernel():
+    # s above the shared-memory lists of the fast iteration kernel (1024): the general kernel
+    # (filter and one-CTA select inside the kernel) runs every iteration
+    p = synth.gaussian(3000, 6000, 1100, seed=9, snr_db=30.0, values="pm_u")
+    sv, ref = _run_pair(p, 8, 8, 25, seed=4)
+    _check(sv, ref, p, "s=1100")
+
+
+def test_fast_and_general_iteration_kernels_agree(tmp_path):
+    # the same solve through both iteration kernels (QIHT_ITER=base selects the general one;
+    # it is read once per process, hence the subprocess)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "solve.py"
+    script.write_text(
+        "import sys, numpy as np, torch\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "import paper_1802_04907_gb300 as q, synth\n"
+        "p = synth.gaussian(900, 3000, 30, seed=21, snr_db=25.0, values='pm_u')\n"
+        "phi = torch.from_numpy(p.phi).cuda(); y = torch.from_numpy(p.y).cuda()\n"
+        "q1, q2, qy = q.quantize_problem(phi, y, 8, 8, 6)\n"
+        "sv = q.niht_solve(q1, q2, qy, p.s, 60, trace=True)\n"
+        "torch.cuda.synchronize()\n"
+        "r = sv.read_report()\n"
+        "np.savez(sys.argv[1], x=sv.x.cpu().numpy(), sup=sv.trace['support'].cpu().numpy(),\n"
+        "         iters=r.iters_run, status=r.status)\n")
+    outs = {}
+    for kind in ("base", "fast"):
+        env = dict(os.environ)
+        if kind == "base":
+            env["QIHT_ITER"] = "base"
+        else:
+            env.pop("QIHT_ITER", None)
+        out = tmp_path / f"{kind}.npz"
+        subprocess.run([sys.executable, str(script), str(out)], env=env, check=True, timeout=300)
+        outs[kind] = np.load(out)
+    a, b = outs["base"], outs["fast"]
+    assert int(a["status"]) == int(b["status"]) == q.OK
+    assert int(a["iters"]) == int(b["iters"])
+    assert np.array_equal(a["sup"], b["sup"])
+    rel = np.linalg.norm(a["x"] - b["x"]) / np.linalg.norm(a["x"])
+    assert rel < 1e-5, rel
+
+
+def test_exact_ties_resolve_by_index():
+    # +-1 entries quantize deterministically (they sit on the two end levels), so duplicated
+    # columns have identical codes and identical gradients: H_s must break the ties by the
+    # lower index, on both sides, in every iteration
+    dup = 4
+    p = synth.duplicated_pm1(64, 96, dup, 5, seed=17)
+    sv, ref = _run_pair(p, 8, 8, 30, seed=3)
+    rep = sv.read_report()
+    assert rep.status == ref.status == q.OK
+    assert rep.iters_run == ref.iters_run
+    sup = sv.trace["support"].cpu().numpy()
+    for t in range(ref.iters_run + 1):
+        assert np.array_equal(sup[t], ref.trace["support"][t]), f"support differs at iteration {t}"
+    xg = sv.x.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
+    assert rel < 1e-4, rel
