@@ -92,18 +92,21 @@ def test_top_s_all_equal_and_zeros():
         assert kth[0].item() == abs(a[0]) and kth[1].item() == abs(a[0])
 
 
-def test_gemv_t_full_size_sampled():
-    # 8192 x 32768 at 8 bits (the large single-solve workload): sampled columns against the oracle
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_gemv_t_full_size_sampled(bits):
+    # 8192 x 32768 (the large single-solve workload) at every width, in the launch shape the
+    # solver uses: sampled columns against the oracle
     p = synth.large_noisy(seed=0)
     r = synth.random_floats(p.m, seed=77, scale=0.01)
-    Q = q.quantize(torch.from_numpy(p.phi).cuda(), 8, 5, 0)
+    L = (1 << bits) - 1
+    Q = q.quantize(torch.from_numpy(p.phi).cuda(), bits, 5, 0)
     g = q.gemv_t(Q, torch.from_numpy(r).cuda()).cpu().numpy().astype(np.float64)
     c, _ = oracle.absmax(p.phi)
     e = np.frexp(np.max(np.abs(r)).astype(np.float64))[1]
     rng = np.random.Generator(np.random.PCG64(1))
     for j in np.concatenate([[0, p.n - 1], rng.choice(p.n, 30, replace=False)]):
-        codes, _ = oracle.quantize(np.ascontiguousarray(p.phi[:, j]), 8, 5, 0, c, col0=int(j), rows_total=p.m)
-        col = oracle.dequantize(codes, 8, c)
+        codes, _ = oracle.quantize(np.ascontiguousarray(p.phi[:, j]), bits, 5, 0, c, col0=int(j), rows_total=p.m)
+        col = oracle.dequantize(codes, bits, c)
         ref = float(oracle.gemv_t(col[:, None], r.astype(np.float64))[0])
-        bound = ((c / 255) * np.abs(2.0 * codes - 255).sum() * 2.0 ** (e - 23) + 2.0**-24 * abs(ref)) * (1 + 2.0**-20)
+        bound = ((c / L) * np.abs(2.0 * codes - L).sum() * 2.0 ** (e - 23) + 2.0**-24 * abs(ref)) * (1 + 2.0**-20)
         assert abs(g[j] - ref) <= bound, j

@@ -98,6 +98,16 @@ def test_mixed_precision(bits_phi, bits_y):
     _check(sv, ref, p, f"{bits_phi}/{bits_y}")
 
 
+@pytest.mark.parametrize("bits", [4, 8])
+def test_interferometry_full_size(bits):
+    # the interferometry workload at full size: 48 antennas, 2256 baselines, 128 x 128 grid,
+    # stacked real 4512 x 16384, 50 sources, 20 dB, s = 64; 20 iterations against the oracle
+    p = synth.interferometry(seed=0)
+    assert p.phi.shape == (4512, 16384)
+    sv, ref = _run_pair(p, bits, bits, 20, seed=2)
+    _check(sv, ref, p, f"interferometry-{bits}")
+
+
 def test_interferometry_small():
     p = synth.interferometry(n_ant=12, grid=32, n_src=6, s=8, snr_db=20.0, seed=2)
     sv, ref = _run_pair(p, 8, 8, 60, seed=1)
