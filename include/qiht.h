@@ -103,6 +103,17 @@ qiht_status qiht_quantize(const float* in, int32_t rows, int32_t cols, int64_t l
                           uint64_t seed, uint32_t stream_id, int32_t flags,
                           uint32_t* words, int32_t ld_words, float* scale, qiht_stream_t stream);
 
+/* Two independent quantizations of the same matrix in one pass over `in` (the double
+ * sampling of Algorithm 2: Q1 and Q2 of Phi, sharing the scale c). Element by element
+ * the result is bit-identical to two qiht_quantize calls with stream_a -> words_a and
+ * stream_b -> words_b (same seed and scale); the rounding decision, which does not
+ * depend on the random number, is computed once. Arguments as for qiht_quantize;
+ * words_a and words_b are distinct buffers of cols * ld_words words each. */
+qiht_status qiht_quantize_pair(const float* in, int32_t rows, int32_t cols, int64_t ld_in, int32_t bits,
+                               uint64_t seed, uint32_t stream_a, uint32_t stream_b, int32_t flags,
+                               uint32_t* words_a, uint32_t* words_b, int32_t ld_words, float* scale,
+                               qiht_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Building blocks of one iteration (exposed for tests and measurement)     */
 /* ---------------------------------------------------------------------- */

@@ -68,6 +68,7 @@ class _Trace(ctypes.Structure):
 REPORT_BYTES = ctypes.sizeof(_Report)
 
 EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld_words", "qiht_quantize",
+           "qiht_quantize_pair",
            "qiht_gemv_t_workspace_size", "qiht_gemv_t", "qiht_gemv_t_prescaled",
            "qiht_gemv_cols_workspace_size", "qiht_gemv_cols", "qiht_gemv_cols_static",
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
@@ -91,6 +92,7 @@ def lib():
             "qiht_last_error": ([], ctypes.c_char_p),
             "qiht_ld_words": ([I32, I32], I32),
             "qiht_quantize": ([P, I32, I32, I64, I32, U64, U32, I32, P, I32, P, P], I32),
+            "qiht_quantize_pair": ([P, I32, I32, I64, I32, U64, U32, U32, I32, P, P, I32, P, P], I32),
             "qiht_gemv_t_workspace_size": ([], SZ),
             "qiht_gemv_t": ([ctypes.POINTER(_Codes), P, P, P, SZ, P], I32),
             "qiht_gemv_t_prescaled": ([ctypes.POINTER(_Codes), P, P, P, P], I32),
@@ -312,17 +314,35 @@ def niht_solve(Q1: Codes, Q2: Codes, y: Codes, s: int, iters: int, *, trace: boo
     return sv(Q1, Q2, y, stream=stream)
 
 
+def quantize_pair(v: torch.Tensor, bits: int, seed: int, stream_a: int, stream_b: int, *,
+                  out: tuple | None = None, stream=None) -> tuple:
+    """qiht_quantize_pair: two independent quantizations of one matrix in one pass (shared scale)."""
+    assert v.is_cuda and v.dtype == torch.float32 and v.dim() == 2 and v.stride(1) == 1
+    rows, cols = v.shape
+    ld = v.stride(0)
+    ldw = ld_words(rows, bits) if bits in (2, 4, 8) else 4
+    if out is None:
+        sc = torch.zeros(1, dtype=torch.float32, device=v.device)
+        out = (Codes(torch.empty(cols * ldw, dtype=torch.int32, device=v.device), sc, rows, cols, bits),
+               Codes(torch.empty(cols * ldw, dtype=torch.int32, device=v.device), sc, rows, cols, bits))
+    qa, qb = out
+    st = lib().qiht_quantize_pair(v.data_ptr(), rows, cols, ld, bits, seed & (2**64 - 1), stream_a, stream_b, 0,
+                                  qa.words.data_ptr(), qb.words.data_ptr(), ldw, qa.scale.data_ptr(),
+                                  _stream(stream))
+    _check(st, "qiht_quantize_pair")
+    qb.scale = qa.scale
+    return qa, qb
+
+
 def quantize_problem(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: int, seed: int, *,
                      out: tuple | None = None, stream=None):
-    """Q1, Q2 (two independent quantizations of Phi, sharing its scale) and Q(y)."""
+    """Q1, Q2 (two independent quantizations of Phi, sharing its scale, in one pass) and Q(y)."""
     if out is None:
-        q1 = quantize(phi, bits_phi, seed, STREAM_Q1, stream=stream)
-        q2 = quantize(phi, bits_phi, seed, STREAM_Q2, scale=q1.scale, scale_given=True, stream=stream)
+        q1, q2 = quantize_pair(phi, bits_phi, seed, STREAM_Q1, STREAM_Q2, stream=stream)
         qy = quantize(y, bits_y, seed, STREAM_Y, stream=stream)
         return q1, q2, qy
     q1, q2, qy = out
-    quantize(phi, bits_phi, seed, STREAM_Q1, out=q1, stream=stream)
-    quantize(phi, bits_phi, seed, STREAM_Q2, scale=q1.scale, scale_given=True, out=q2, stream=stream)
+    quantize_pair(phi, bits_phi, seed, STREAM_Q1, STREAM_Q2, out=(q1, q2), stream=stream)
     quantize(y, bits_y, seed, STREAM_Y, out=qy, stream=stream)
     return q1, q2, qy
 

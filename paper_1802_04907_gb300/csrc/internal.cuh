@@ -162,9 +162,10 @@ void init_node(const InitArgs& a, cudaKernelNodeParams* p, void** argbuf);
 
 // Direct launches (building blocks).
 cudaError_t launch_absmax(const float* in, int rows, int cols, int64_t ld, float* scale, cudaStream_t s);
+// words2 != nullptr: a second quantization (stream_id2) of the same input in the same pass.
 cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int bits, uint64_t seed,
                             uint32_t stream_id, uint32_t* words, int ld_words, const float* scale,
-                            cudaStream_t s);
+                            cudaStream_t s, uint32_t stream_id2 = 0, uint32_t* words2 = nullptr);
 cudaError_t launch_gemv_t(const GemvTArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
 cudaError_t launch_top(const TopArgs& a, cudaStream_t s);

@@ -64,34 +64,48 @@ __global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ in, in
 }
 
 // One rounding decision in binary32, every operation correctly rounded:
-// t = (v / c + 1) * (L-1)/2, code = floor(t) + (u < t - floor(t)).
-__device__ __forceinline__ uint32_t quant_code(float v, float c, float half, int L, float u)
+// t = (v / c + 1) * (L-1)/2, clamped to [0, L-1]; fi = floor(t), f = t - fi.
+// The code is fi + (u < f) (at most L-1); the decision does not depend on u, so
+// several quantizations of the same value share it.
+struct Decision {
+    float fi, f;
+};
+
+__device__ __forceinline__ Decision quant_decide(float v, float c, float half, int L)
 {
     const float vt = (c > 0.0f) ? __fdiv_rn(v, c) : 0.0f;
     float t = __fmul_rn(__fadd_rn(vt, 1.0f), half);
     t = fminf(fmaxf(t, 0.0f), (float)(L - 1));
     const float fi = floorf(t);
-    const float f = __fsub_rn(t, fi);
-    int code = (int)fi + (u < f ? 1 : 0);
+    return Decision{fi, __fsub_rn(t, fi)};
+}
+
+__device__ __forceinline__ uint32_t quant_code(const Decision& d, int L, float u)
+{
+    const int code = (int)d.fi + (u < d.f ? 1 : 0);
     return (uint32_t)min(code, L - 1);
 }
 
 constexpr int kQTileRows = 128;
 constexpr int kQTileCols = 32;
 
-// Quantize tiles of 128 rows x 32 columns: the tile is staged transposed in
-// shared memory (coalesced reads of the row-major input), then every thread
-// packs whole words of one column (coalesced writes of the column-packed output).
-template <int BITS>
+// Quantize tiles of 128 rows x 32 columns with NS independent random streams at once
+// (NS = 2: the two quantizations Q1, Q2 of the same matrix in one pass). The tile is
+// read as float4 (coalesced, row-major input), staged transposed in shared memory, and
+// every thread packs whole words of one column (coalesced writes of the column-packed
+// output); the next tile's loads are in flight while this one is packed. The rounding
+// decision of an element is computed once and shared by the streams.
+template <int BITS, int NS>
 __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, int rows, int cols,
-                                                  long long ld, uint64_t seed, uint32_t stream_id,
-                                                  uint32_t* __restrict__ words, int ldw,
-                                                  const float* __restrict__ scale_p)
+                                                  long long ld, uint64_t seed, uint32_t stream0, uint32_t stream1,
+                                                  uint32_t* __restrict__ words0, uint32_t* __restrict__ words1,
+                                                  int ldw, const float* __restrict__ scale_p)
 {
     constexpr int G = 32 / BITS;
     constexpr int L = 1 << BITS;
     constexpr int WPC = kQTileRows / G;                   // words per column per tile
     constexpr int WPT = WPC * kQTileCols / 256;           // words per thread per tile
+    constexpr int F4 = kQTileRows * kQTileCols / 4 / 256; // float4 loads per thread per tile
     __shared__ float tile[kQTileCols][kQTileRows + 1];
 
     const float c = *scale_p;
@@ -100,19 +114,46 @@ __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, 
     const int row_tiles = (ldw * G + kQTileRows - 1) / kQTileRows;
     const int col_tiles = (cols + kQTileCols - 1) / kQTileCols;
     const long long ntiles = (long long)row_tiles * col_tiles;
+    const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
 
-    for (long long tile_id = blockIdx.x; tile_id < ntiles; tile_id += gridDim.x) {
+    // thread t reads float4 f = t + 256 k: row f / 8 of the tile, columns 4 (f % 8) .. + 3
+    auto fetch = [&](long long tid, float4 (&v)[F4]) {
+        const int rt = (int)(tid % row_tiles), ct = (int)(tid / row_tiles);
+        const int r0 = rt * kQTileRows, c0 = ct * kQTileCols;
+#pragma unroll
+        for (int k = 0; k < F4; ++k) {
+            const int f = threadIdx.x + 256 * k;
+            const int i = r0 + (f >> 3), j = c0 + 4 * (f & 7);
+            const float* src = in + (long long)i * ld + j;
+            if (vec && i < rows && j + 3 < cols) {
+                asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                             : "=f"(v[k].x), "=f"(v[k].y), "=f"(v[k].z), "=f"(v[k].w) : "l"(src));
+            } else {
+                v[k].x = (i < rows && j < cols) ? src[0] : 0.0f;
+                v[k].y = (i < rows && j + 1 < cols) ? src[1] : 0.0f;
+                v[k].z = (i < rows && j + 2 < cols) ? src[2] : 0.0f;
+                v[k].w = (i < rows && j + 3 < cols) ? src[3] : 0.0f;
+            }
+        }
+    };
+    float4 pre[F4];
+    long long tile_id = blockIdx.x;
+    if (tile_id < ntiles) fetch(tile_id, pre);
+    for (; tile_id < ntiles; tile_id += gridDim.x) {
         const int rt = (int)(tile_id % row_tiles);
         const int ct = (int)(tile_id / row_tiles);
         const int r0 = rt * kQTileRows, c0 = ct * kQTileCols;
-#pragma unroll 4
-        for (int k = 0; k < kQTileRows * kQTileCols / 256; ++k) {
-            const int idx = threadIdx.x + 256 * k;
-            const int rr = idx >> 5, cc = idx & 31;
-            const int i = r0 + rr, j = c0 + cc;
-            tile[cc][rr] = (i < rows && j < cols) ? in[(long long)i * ld + j] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < F4; ++k) {
+            const int f = threadIdx.x + 256 * k;
+            const int rr = f >> 3, cq = 4 * (f & 7);
+            tile[cq][rr] = pre[k].x;
+            tile[cq + 1][rr] = pre[k].y;
+            tile[cq + 2][rr] = pre[k].z;
+            tile[cq + 3][rr] = pre[k].w;
         }
         __syncthreads();
+        if (tile_id + gridDim.x < ntiles) fetch(tile_id + gridDim.x, pre);
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
             const int w = threadIdx.x + 256 * k;
@@ -123,26 +164,35 @@ __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, 
                 const int i0 = qg * G;
                 const uint64_t e0 = (uint64_t)j * (uint64_t)rows + (uint64_t)i0;
                 uint64_t cur = ~0ull;
-                uint4 rnd = make_uint4(0, 0, 0, 0);
-                uint32_t word = 0;
+                uint4 rnd[NS];
+                uint32_t word[NS];
+#pragma unroll
+                for (int st = 0; st < NS; ++st) { rnd[st] = make_uint4(0, 0, 0, 0); word[st] = 0; }
 #pragma unroll
                 for (int kk = 0; kk < G; ++kk) {
                     if (i0 + kk < rows) {
                         const uint64_t e = e0 + kk;
                         const uint64_t qq = e >> 2;
                         if (qq != cur) {
-                            rnd = philox4x32_10(make_uint4((uint32_t)qq, (uint32_t)(qq >> 32), stream_id, 0u),
-                                                key0, key1);
+#pragma unroll
+                            for (int st = 0; st < NS; ++st)
+                                rnd[st] = philox4x32_10(
+                                    make_uint4((uint32_t)qq, (uint32_t)(qq >> 32), st == 0 ? stream0 : stream1, 0u),
+                                    key0, key1);
                             cur = qq;
                         }
                         const uint32_t sel = e & 3;
-                        const uint32_t rw = sel == 0 ? rnd.x : sel == 1 ? rnd.y : sel == 2 ? rnd.z : rnd.w;
-                        const float u = (float)(rw >> 8) * 0x1p-24f;
-                        const uint32_t code = quant_code(tile[cc][q * G + kk], c, half, L, u);
-                        word |= code << (8 * (kk & 3) + BITS * (kk >> 2));
+                        const Decision d = quant_decide(tile[cc][q * G + kk], c, half, L);
+#pragma unroll
+                        for (int st = 0; st < NS; ++st) {
+                            const uint32_t rw = sel == 0 ? rnd[st].x : sel == 1 ? rnd[st].y : sel == 2 ? rnd[st].z : rnd[st].w;
+                            const float u = (float)(rw >> 8) * 0x1p-24f;
+                            word[st] |= quant_code(d, L, u) << (8 * (kk & 3) + BITS * (kk >> 2));
+                        }
                     }
                 }
-                words[(size_t)j * ldw + qg] = word;
+                words0[(size_t)j * ldw + qg] = word[0];
+                if (NS == 2) words1[(size_t)j * ldw + qg] = word[NS - 1];
             }
         }
         __syncthreads();
@@ -164,7 +214,7 @@ cudaError_t launch_absmax(const float* in, int rows, int cols, int64_t ld, float
 
 cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int bits, uint64_t seed,
                             uint32_t stream_id, uint32_t* words, int ld_words, const float* scale,
-                            cudaStream_t s)
+                            cudaStream_t s, uint32_t stream_id2, uint32_t* words2)
 {
     const int G = 32 / bits;
     const long long tiles = (long long)((ld_words * G + kQTileRows - 1) / kQTileRows) *
@@ -172,10 +222,21 @@ cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int
     long long blocks = tiles;
     const long long cap = (long long)num_sms() * 8;
     if (blocks > cap) blocks = cap;
+    const unsigned nb = (unsigned)blocks;
+    const bool two = words2 != nullptr;
     switch (bits) {
-    case 2: k_quantize<2><<<(unsigned)blocks, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, words, ld_words, scale); break;
-    case 4: k_quantize<4><<<(unsigned)blocks, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, words, ld_words, scale); break;
-    case 8: k_quantize<8><<<(unsigned)blocks, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, words, ld_words, scale); break;
+    case 2:
+        if (two) k_quantize<2, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale);
+        else k_quantize<2, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale);
+        break;
+    case 4:
+        if (two) k_quantize<4, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale);
+        else k_quantize<4, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale);
+        break;
+    case 8:
+        if (two) k_quantize<8, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale);
+        else k_quantize<8, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

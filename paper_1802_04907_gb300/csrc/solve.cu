@@ -181,19 +181,22 @@ int32_t qiht_ld_words(int32_t rows, int32_t bits)
     return (w + 3) & ~3;
 }
 
-qiht_status qiht_quantize(const float* in, int32_t rows, int32_t cols, int64_t ld_in, int32_t bits,
-                          uint64_t seed, uint32_t stream_id, int32_t flags,
-                          uint32_t* words, int32_t ld_words, float* scale, qiht_stream_t stream)
+static qiht_status quantize_impl(const float* in, int32_t rows, int32_t cols, int64_t ld_in, int32_t bits,
+                                 uint64_t seed, uint32_t stream_id, uint32_t stream_id2, int32_t flags,
+                                 uint32_t* words, uint32_t* words2, int32_t ld_words, float* scale,
+                                 qiht_stream_t stream)
 {
     if (!bits_ok(bits)) return QIHT_ERR_BITS;
     if (!in || !words || !scale || rows < 1 || cols < 1 || ld_in < cols) return QIHT_ERR_ARG;
     if (ld_words != qiht_ld_words(rows, bits) || !aligned(words, 16)) return QIHT_ERR_ARG;
+    if (words2 && (!aligned(words2, 16) || words2 == words)) return QIHT_ERR_ARG;
     if (flags & ~(QIHT_SCALE_GIVEN | QIHT_CHECK_FINITE)) return QIHT_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!(flags & QIHT_SCALE_GIVEN)) {
         if (launch_absmax(in, rows, cols, ld_in, scale, s) != cudaSuccess) return QIHT_ERR_CUDA;
     }
-    if (launch_quantize(in, rows, cols, ld_in, bits, seed, stream_id, words, ld_words, scale, s) != cudaSuccess)
+    if (launch_quantize(in, rows, cols, ld_in, bits, seed, stream_id, words, ld_words, scale, s, stream_id2,
+                        words2) != cudaSuccess)
         return QIHT_ERR_CUDA;
     if (flags & QIHT_CHECK_FINITE) {
         float h = 0.0f;
@@ -202,6 +205,24 @@ qiht_status qiht_quantize(const float* in, int32_t rows, int32_t cols, int64_t l
         if (!std::isfinite(h)) return QIHT_ERR_NONFINITE;
     }
     return QIHT_OK;
+}
+
+qiht_status qiht_quantize(const float* in, int32_t rows, int32_t cols, int64_t ld_in, int32_t bits,
+                          uint64_t seed, uint32_t stream_id, int32_t flags,
+                          uint32_t* words, int32_t ld_words, float* scale, qiht_stream_t stream)
+{
+    return quantize_impl(in, rows, cols, ld_in, bits, seed, stream_id, 0u, flags, words, nullptr, ld_words, scale,
+                         stream);
+}
+
+qiht_status qiht_quantize_pair(const float* in, int32_t rows, int32_t cols, int64_t ld_in, int32_t bits,
+                               uint64_t seed, uint32_t stream_a, uint32_t stream_b, int32_t flags,
+                               uint32_t* words_a, uint32_t* words_b, int32_t ld_words, float* scale,
+                               qiht_stream_t stream)
+{
+    if (!words_b) return QIHT_ERR_ARG;
+    return quantize_impl(in, rows, cols, ld_in, bits, seed, stream_a, stream_b, flags, words_a, words_b, ld_words,
+                         scale, stream);
 }
 
 size_t qiht_gemv_t_workspace_size(void) { return 256; }

@@ -96,3 +96,34 @@ def test_full_size_sampled_columns(bits):
         want, _ = oracle.quantize(np.ascontiguousarray(p.phi[:, j]), bits, 12345, 0, c, col0=int(j), rows_total=p.m)
         got = layout.unpack(words[j].cpu().numpy(), p.m, 1, bits)[:, 0]
         assert np.array_equal(got, want), j
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_pair_equals_two_single_quantizations(bits, shape):
+    # qiht_quantize_pair (Q1 and Q2 in one pass) is element by element the two single calls
+    m, n = shape
+    v = torch.from_numpy(synth.random_floats((m, n), seed=m + 3 * n + bits)).cuda()
+    qa, qb = q.quantize_pair(v, bits, 1234567, 0, 1)
+    sa = q.quantize(v, bits, 1234567, 0)
+    sb = q.quantize(v, bits, 1234567, 1, scale=sa.scale.clone(), scale_given=True)
+    torch.cuda.synchronize()
+    assert qa.scale.item() == sa.scale.item()
+    assert torch.equal(qa.words, sa.words) and torch.equal(qb.words, sb.words)
+    assert not torch.equal(qa.words, qb.words) or m * n < 4
+
+
+@pytest.mark.parametrize("offset,ld", [(8, 96), (10, 90), (0, 64)])
+def test_pair_strided_input(offset, ld):
+    # aligned strides take the float4 path, odd ones the element path; ragged last columns
+    big = synth.random_floats((301, ld), seed=offset + ld)
+    cols = min(57, ld - offset)
+    t = torch.from_numpy(big).cuda()[:, offset:offset + cols]
+    qa, qb = q.quantize_pair(t, 8, 77, 0, 1)
+    torch.cuda.synchronize()
+    sub = np.ascontiguousarray(big[:, offset:offset + cols])
+    wa, c = oracle.quantize(sub, 8, 77, 0)
+    wb, _ = oracle.quantize(sub, 8, 77, 1, c)
+    assert qa.scale.item() == c
+    assert np.array_equal(layout.unpack(qa.words.cpu().numpy(), 301, cols, 8), wa)
+    assert np.array_equal(layout.unpack(qb.words.cpu().numpy(), 301, cols, 8), wb)
