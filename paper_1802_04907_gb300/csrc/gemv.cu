@@ -757,25 +757,28 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
     if (j < n) load_batch(cA, j, pb);
 
     // everything above reads only the codes; r, max |r| and the solver state come from
-    // the previous kernel
+    // the previous kernel. The state words are read by one thread per CTA and shared (all
+    // threads reading them would pile requests onto one L2 line); the first chunk of r is
+    // requested at the same time.
     griddep_wait();
     griddep_launch();
-    if (a.h_outer && blockIdx.x == 0 && threadIdx.x == 0) {
-        const int guard = ++a.st->outer_guard;
-        cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
-                                (!a.st->stop && guard < a.guard_limit) ? 1u : 0u);
+    __shared__ unsigned s_st[3];
+    if (threadIdx.x == 0) {
+        s_st[0] = a.st ? (unsigned)a.st->stop : 0u;
+        s_st[1] = *a.rmax_bits;
+        s_st[2] = (a.pos && a.st) ? a.st->tau_g_bits : 0u;
+        if (a.h_outer && blockIdx.x == 0) {
+            const int guard = ++a.st->outer_guard;
+            cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
+                                    (!a.st->stop && guard < a.guard_limit) ? 1u : 0u);
+        }
     }
-    if (a.st && a.st->stop) return;
-    const int sh = fixed_shift(*a.rmax_bits);
-
     // residual to 24-bit fixed point, as three byte planes; four rows (one float4) per limb
     // word, UR words of a thread in flight at once
     constexpr int UR = 4;
     const bool r_vec = (reinterpret_cast<uintptr_t>(a.r) & 15) == 0;
     const int nlw = P * G;
-    long long rsum = 0;
-    for (int lw0 = threadIdx.x; lw0 < nlw; lw0 += blockDim.x * UR) {
-        float rv[UR][4];
+    auto load_r = [&](float (&rv)[UR][4], int lw0) {
 #pragma unroll
         for (int u = 0; u < UR; ++u) {
             const int lw = lw0 + u * (int)blockDim.x;
@@ -788,6 +791,15 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
                 for (int p = 0; p < 4; ++p) rv[u][p] = (lw < nlw && i + p < m) ? __ldcg(a.r + i + p) : 0.0f;
             }
         }
+    };
+    float rv[UR][4];
+    load_r(rv, threadIdx.x);
+    __syncthreads();
+    if (s_st[0]) return;                        // uniform
+    const int sh = fixed_shift(s_st[1]);
+    long long rsum = 0;
+    for (int lw0 = threadIdx.x; lw0 < nlw; lw0 += blockDim.x * UR) {
+        if (lw0 != (int)threadIdx.x) load_r(rv, lw0);
 #pragma unroll
         for (int u = 0; u < UR; ++u) {
             const int lw = lw0 + u * (int)blockDim.x;
@@ -824,7 +836,7 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
     }
     __syncthreads();
     // candidate filter of the solver's next threshold (off: tau_g == 0 or no position map)
-    const uint32_t tau_g = a.pos ? a.st->tau_g_bits : 0u;
+    const uint32_t tau_g = s_st[2];
     unsigned bmax = 0;
     int pos_cur = -1;
     long long R = 0;

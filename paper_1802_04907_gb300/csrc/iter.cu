@@ -1089,7 +1089,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
 // Every CTA commits its own slice of x and of the position map; the last CTA to
 // finish writes G, x_G and the scalars.
 // ---------------------------------------------------------------------------
-constexpr int kFastMaxS = 1024;          // largest s of the fast path (lists held in shared memory)
+constexpr int kFastMaxS = 2 * 512;       // largest s of the fast path (lists held in shared memory)
 constexpr int kTieMax = 64;              // ties at the s-th key ranked by index in shared memory
 
 struct FastSm {
@@ -1382,19 +1382,22 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     // everything above is fixed during the solve; the rest comes from the previous kernels
     griddep_wait();
     griddep_launch();
-    if (st->stop) return;                       // uniform: read before any exchange
+    // the state words are read by one thread per CTA (every thread of every CTA reading the
+    // same line would queue thousands of requests on one L2 slice) and shared below
+    __shared__ unsigned s_state[8];
+    if (tid == 0) {
+        s_state[0] = (unsigned)__ldcg(&st->stop);
+        s_state[1] = (unsigned)__ldcg(&st->iter);
+        s_state[2] = __ldcg(&st->omega_uses);
+        s_state[3] = __ldcg(&st->dec_uses);
+        s_state[4] = __ldcg(&st->tau_g_bits);
+        s_state[5] = __ldcg(&st->gcand_count);
+        s_state[6] = __ldcg(&st->bmax_g);
+    }
     unsigned long long tp[5] = {0, 0, 0, 0, 0};  // CTA 0, thread 0: phase clock
     if (cta0 && tid == 0) tp[0] = gtimer_ns();
     unsigned long long target = 0;
     if (tid == 0) target = barrier_base(a.gbar);
-
-    // ---- state, G, x_G, g_G, the first candidates and Q(y) of this CTA's rows, all at once ----
-    const int iter0 = __ldcg(&st->iter);
-    const unsigned omega_uses = __ldcg(&st->omega_uses);
-    const unsigned dec_uses = __ldcg(&st->dec_uses);
-    const uint32_t tau_g = __ldcg(&st->tau_g_bits);
-    const unsigned ncand = __ldcg(&st->gcand_count);
-    const uint32_t bmax_g = __ldcg(&st->bmax_g);
     int st_bt = 0, st_sc = 0, st_iters = 0, st_status = 0, st_fsel = 0;
     if (cta0 && tid == 0) {
         st_bt = st->backtracks_total;
@@ -1403,18 +1406,41 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         st_status = st->status;
         st_fsel = st->full_selects;
     }
+    // G, x_G, g_G in support order and the first candidates, requested before the state
+    // is known (s <= 2 x 512; the candidate list has room for 512 reads)
+    int jq[2] = {0, 0};
+    float xq[2] = {0.0f, 0.0f}, gq[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int q = tid + u * kIterThreads;
+        if (q < s) {
+            jq[u] = __ldcg(a.support + q);
+            xq[u] = __ldcg(a.xs + q);
+            gq[u] = __ldcg(a.gsup + q);
+        }
+    }
     unsigned long long cspec = 0;
-    if (tid < a.gcap) cspec = __ldcg(a.gcand + tid);   // speculative: used if tid < count
+    if (tid < a.gcap) cspec = __ldcg(a.gcand + tid);
+    __syncthreads();
+    if (s_state[0]) return;                      // uniform: read before any exchange
+    const int iter0 = (int)s_state[1];
+    const unsigned omega_uses = s_state[2];
+    const unsigned dec_uses = s_state[3];
+    const uint32_t tau_g = s_state[4];
+    const unsigned ncand = s_state[5];
+    const uint32_t bmax_g = s_state[6];
     const bool first = iter0 == 0;              // the gradient kernel has not filtered yet
     const bool cand_ok = !first && tau_g != 0u && ncand <= (unsigned)a.gcap;
     const int cnt = cand_ok ? (int)ncand : 0;
-    for (int q = tid; q < s; q += blockDim.x) {
-        const int j = __ldcg(a.support + q);
-        const float xv = __ldcg(a.xs + q);
-        const float gv = __ldcg(a.gsup + q);
-        sm.el_idx[q] = j;
-        sm.el_x[q] = first ? __ldcg(a.x + j) : xv;
-        sm.el_g[q] = first ? __ldcg(a.g + j) : gv;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int q = tid + u * kIterThreads;
+        if (q < s) {
+            sm.el_idx[q] = jq[u];
+            // first iteration: x and g through G (x_G, g_G are not kept in support order yet)
+            sm.el_x[q] = first ? __ldcg(a.x + jq[u]) : xq[u];
+            sm.el_g[q] = first ? __ldcg(a.g + jq[u]) : gq[u];
+        }
     }
     for (int i = tid; i < cnt; i += blockDim.x) {
         const unsigned long long c = i == tid ? cspec : __ldcg(a.gcand + i);
