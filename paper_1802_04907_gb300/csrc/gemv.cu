@@ -712,6 +712,53 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
 // ---------------------------------------------------------------------------
 constexpr int kWarpThreads = 512;           // 16 warps per CTA, two CTAs per SM
 
+// Warp 0 of a GEMV^T CTA: stop flag, max |r| (fast path: from the iteration kernel's
+// residual partials, whose non-finite maximum stops the solve), candidate threshold, the
+// loop condition (CTA 0) and, after the last iteration, its ||r||^2 (CTA 0). Kept out of
+// line: it runs once per CTA and its registers would otherwise crowd the streaming loop.
+__device__ __noinline__ void warp_prologue(const GemvTArgs& a, unsigned* s_st)
+{
+    // max |r|: from the iteration kernel's residual partials (fast path) or the state
+    unsigned rmx = 0;
+    if (a.rpart) rmx = (unsigned)slot_max_complete(a.rpart, kSlotRmax, a.rgrid);
+    if (threadIdx.x == 0) {
+        int stop = a.st ? a.st->stop : 0;
+        if (!a.rpart) rmx = *a.rmax_bits;
+        if (a.rpart && !stop && rmx >= 0x7f800000u) {
+            // a residual entry is not finite: the solve stops (the CTAs all see it)
+            stop = 1;
+            if (blockIdx.x == 0) {
+                a.st->status = QIHT_ERR_NONFINITE;
+                a.st->stop = 1;
+                if (a.report) a.report->status = QIHT_ERR_NONFINITE;
+            }
+        }
+        s_st[0] = (unsigned)stop;
+        s_st[1] = rmx;
+        s_st[2] = (a.pos && a.st) ? a.st->tau_g_bits : 0u;
+        if (a.h_outer && blockIdx.x == 0) {
+            const int guard = ++a.st->outer_guard;
+            cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
+                                    (!stop && guard < a.guard_limit) ? 1u : 0u);
+        }
+    }
+    // ||r||^2 of the iteration the iteration kernel just completed (it leaves the record to
+    // this kernel, so that none of its CTAs waits for the others at the end)
+    if (a.rpart && blockIdx.x == 0) {
+        const int st_iter = __shfl_sync(0xffffffffu, a.st->iter, 0);
+        const int logged = __shfl_sync(0xffffffffu, a.st->resid_logged, 0);
+        if (st_iter > logged) {
+            const double r2 = slot_sum_complete(a.rpart, kSlotResid, a.rgrid);
+            if (threadIdx.x == 0) {
+                a.st->resid2 = r2;
+                a.st->resid_logged = st_iter;
+                if (a.trace_resid2) a.trace_resid2[st_iter] = r2;
+                if (a.report) a.report->resid_norm2 = r2;
+            }
+        }
+    }
+}
+
 template <int BITS, int NPL>
 __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
 {
@@ -763,16 +810,7 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
     griddep_wait();
     griddep_launch();
     __shared__ unsigned s_st[3];
-    if (threadIdx.x == 0) {
-        s_st[0] = a.st ? (unsigned)a.st->stop : 0u;
-        s_st[1] = *a.rmax_bits;
-        s_st[2] = (a.pos && a.st) ? a.st->tau_g_bits : 0u;
-        if (a.h_outer && blockIdx.x == 0) {
-            const int guard = ++a.st->outer_guard;
-            cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
-                                    (!a.st->stop && guard < a.guard_limit) ? 1u : 0u);
-        }
-    }
+    if (threadIdx.x < 32) warp_prologue(a, s_st);
     // residual to 24-bit fixed point, as three byte planes; four rows (one float4) per limb
     // word, UR words of a thread in flight at once
     constexpr int UR = 4;

@@ -21,6 +21,53 @@ constexpr int kGatherThreads = 256;
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+constexpr int kPartSlots = 8;             // kinds of per-CTA partials of the iteration kernel
+constexpr int kSlotCtas = 256;            // CTAs per partial kind (largest iteration grid)
+constexpr int kSlotPerLane = kSlotCtas / 32;
+constexpr int kSlotResid = 4;             // ||r||^2 of the CTA's rows
+constexpr int kSlotRmax = 5;              // max |r| (float bits) of the CTA's rows
+
+// Value of a tagged partial slot word (the sign bit carries the tag).
+__device__ __forceinline__ double slot_value(unsigned long long b)
+{
+    return __longlong_as_double((long long)(b & 0x7fffffffffffffffull));
+}
+
+// Warp 0 (all 32 lanes call it): sum (kind ks) or maximum (kind km) over the first `grid`
+// CTAs of complete partial slots (no tag check: the kernel that wrote them has finished),
+// lane l taking CTAs l, l + 32, ... in order, then a fixed shuffle tree.
+__device__ __forceinline__ double slot_sum_complete(const double* part, int ks, int grid)
+{
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+#pragma unroll
+    for (int u = 0; u < kSlotPerLane; ++u) {
+        const int c = lane + 32 * u;
+        const double t = c < grid ? slot_value(__ldcg(reinterpret_cast<const unsigned long long*>(part) +
+                                                      (size_t)ks * kSlotCtas + c))
+                                  : 0.0;
+        v += t;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double slot_max_complete(const double* part, int km, int grid)
+{
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+#pragma unroll
+    for (int u = 0; u < kSlotPerLane; ++u) {
+        const int c = lane + 32 * u;
+        if (c < grid)
+            v = fmax(v, slot_value(__ldcg(reinterpret_cast<const unsigned long long*>(part) + (size_t)km * kSlotCtas + c)));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // Device view of a quantized matrix (see the column-packed layout in qiht.h).
 struct Codes {
     const uint32_t* words;
@@ -58,6 +105,7 @@ struct State {
     unsigned bmax_g;       // largest |g| (float bits) outside G below tau_g
     unsigned omega_uses;   // backtracking-test rounds of the fast iteration kernel so far
     unsigned dec_uses;     // uses of the fast iteration kernel's decision word so far
+    int resid_logged;      // last iteration whose ||r||^2 is in resid2, the trace and the report
     unsigned long long t_phase[8];   // device clock at phase boundaries of the last iteration
     unsigned long long bar_count;    // grid-barrier arrivals of the iteration kernel (only grows)
     unsigned long long dec_word;     // fast iteration kernel: CTA 0's tagged decision (starts with tag 1)
@@ -112,6 +160,12 @@ struct GemvTArgs {
     float* gsup;                // out: g on G, by position
     unsigned long long* gcand;  // out: columns outside G with |g| >= st->tau_g_bits: (g bits << 32) | column
     int gcap;                   // capacity of gcand (st->gcand_count counts past it)
+    // fast path: max |r| comes from the iteration kernel's residual partial slots (instead of
+    // st->rmax_bits), and after the last iteration the first product records ||r||^2
+    const double* rpart;        // partial slots [kPartSlots][kSlotCtas] (nullptr: use rmax_bits)
+    int rgrid;                  // CTAs of the iteration kernel
+    qiht_report* report;
+    double* trace_resid2;       // optional
 };
 
 struct TopArgs {
@@ -173,9 +227,7 @@ cudaError_t launch_top(const TopArgs& a, cudaStream_t s);
 // One iteration after the gradient product as one persistent kernel (iter.cu).
 struct IterArgs;
 constexpr size_t kIterArgsMax = 1024;     // bytes reserved for the iteration kernel's arguments
-constexpr int kPartSlots = 8;             // kinds of per-CTA partials of the iteration kernel
-constexpr int kSlotCtas = 256;            // CTAs per partial kind (largest iteration grid)
-constexpr int kSlotPerLane = kSlotCtas / 32;
+
 int iter_grid();
 bool iter_fast(int s);                    // the fast-path iteration kernel serves this support size
 // Buffers of the fast path (ignored by the other kernel).

@@ -1628,8 +1628,57 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         ++bt;
     }
 
+    // ---- CTA 0 commits G, x_G and the scalars (the next kernel records ||r||^2 from the
+    // residual partials, so that no CTA waits for the others at the end) ----
+    const int it = iter0 + 1;
+    if (cta0) {
+        for (int q = tid; q < s; q += blockDim.x) {
+            a.support[q] = sm.u_idx[q];
+            a.xs[q] = sm.u_val[q];
+            if (a.trace.support) a.trace.support[(size_t)it * s + q] = sm.u_idx[q];
+        }
+        if (tid == 0) {
+            tp[3] = gtimer_ns();
+            const int bt_total = st_bt + bt;
+            const int sc_total = st_sc + sr.changed;
+            st->iter = it;
+            st->omega_uses = omega_uses + (unsigned)rounds;
+            st->dec_uses = dec_use;
+            st->mu = mu;
+            st->mu_accepted = mu;
+            st->bt = bt;
+            st->backtracks_total = bt_total;
+            st->support_changes_total = sc_total;
+            st->changed = sr.changed;
+            st->kth0 = sr.kth0;
+            st->kth1 = sr.kth1;
+            // candidates of the next gradient: a little below the (s+1)-th key, in units of |g|
+            const float tg = sr.kth1 > 0.0f ? 0.8f * sr.kth1 / (float)mu : 0.0f;
+            st->tau_g_bits = (isfinite(tg) && tg > 0.0f) ? __float_as_uint(tg) : 0u;
+            st->gcand_count = 0u;
+            st->bmax_g = 0u;
+            if (it >= st_iters) st->stop = 1;
+            if (a.trace.kth) { a.trace.kth[2 * it] = sr.kth0; a.trace.kth[2 * it + 1] = sr.kth1; }
+            if (a.trace.mu) a.trace.mu[it] = mu;
+            if (a.trace.bt) a.trace.bt[it] = bt;
+            if (a.report) {
+                a.report->iters_run = it;
+                a.report->backtracks = bt_total;
+                a.report->support_changes = sc_total;
+                a.report->status = st_status;
+                a.report->mu = mu;
+                a.report->full_selects = st_fsel + full_here;
+                // phases (CTA 0's clock): step size, (filter: in the gradient kernel), select,
+                // backtracking, commit, residual and this CTA's slices, whole kernel
+                a.report->phase_us[0] = (float)(tp[1] - tp[0]) * 1e-3f;
+                a.report->phase_us[1] = 0.0f;
+                a.report->phase_us[2] = (float)(tp[2] - tp[1]) * 1e-3f;
+                a.report->phase_us[3] = (float)(tp[3] - tp[2]) * 1e-3f;
+            }
+        }
+    }
+
     // ---- Resid: r = Q(y) - Q2_G' x' for this CTA's rows ----
-    if (cta0 && tid == 0) tp[3] = gtimer_ns();
     rows_product_sm<BITS>(a, rb, sm.u_idx, sm.u_val, s, sm.red, sm.zrow);
     {
         double acc = 0.0;
@@ -1643,11 +1692,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         acc = cta_sum_n(acc, nrow_thr, shd);
         mx = cta_max(mx, shu);
         if (tid == 0) {
-            slot_put(mypart + 4 * kSlotCtas, acc, tag);
-            slot_put(mypart + 5 * kSlotCtas, (double)mx, tag);
+            slot_put(mypart + kSlotResid * kSlotCtas, acc, tag);
+            slot_put(mypart + kSlotRmax * kSlotCtas, (double)mx, tag);
         }
     }
-    if (cta0 && tid == 0) tp[4] = gtimer_ns();
     // ---- this CTA's slice of x and of the position map ----
     {
         const int per = (n + gridDim.x - 1) / gridDim.x;
@@ -1667,69 +1715,12 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
             }
         }
     }
-    // ---- CTA 0 commits the scalars, G and x_G once every residual partial is in ----
-    if (!cta0) return;
-    double resid2 = 0.0, rmax = 0.0;
-    if (!slot_gather(a.part, 4, 5, -1, tag, &resid2, &rmax, nullptr, st, a.report, shd)) return;
-    const int it = iter0 + 1;
-    for (int q = tid; q < s; q += blockDim.x) {
-        a.support[q] = sm.u_idx[q];
-        a.xs[q] = sm.u_val[q];
-        if (a.trace.support) a.trace.support[(size_t)it * s + q] = sm.u_idx[q];
-    }
-    if (tid == 0) {
-        const int bt_total = st_bt + bt;
-        const int sc_total = st_sc + sr.changed;
-        int status = st_status;
-        st->iter = it;
-        st->omega_uses = omega_uses + (unsigned)rounds;
-        st->dec_uses = dec_use;
-        st->mu = mu;
-        st->mu_accepted = mu;
-        st->bt = bt;
-        st->resid2 = resid2;
-        st->rmax_bits = (unsigned)rmax;
-        st->backtracks_total = bt_total;
-        st->support_changes_total = sc_total;
-        st->changed = sr.changed;
-        st->kth0 = sr.kth0;
-        st->kth1 = sr.kth1;
-        // candidates of the next gradient: a little below the (s+1)-th key, in units of |g|
-        const float tg = sr.kth1 > 0.0f ? 0.8f * sr.kth1 / (float)mu : 0.0f;
-        st->tau_g_bits = (isfinite(tg) && tg > 0.0f) ? __float_as_uint(tg) : 0u;
-        st->gcand_count = 0u;
-        st->bmax_g = 0u;
-        int stop = it >= st_iters;
-        if (!isfinite(resid2)) {
-            status = QIHT_ERR_NONFINITE;
-            st->status = status;
-            stop = 1;
-        }
-        if (stop) st->stop = 1;
-        if (a.trace.kth) { a.trace.kth[2 * it] = sr.kth0; a.trace.kth[2 * it + 1] = sr.kth1; }
-        if (a.trace.mu) a.trace.mu[it] = mu;
-        if (a.trace.bt) a.trace.bt[it] = bt;
-        if (a.trace.resid2) a.trace.resid2[it] = resid2;
-        if (a.report) {
-            a.report->iters_run = it;
-            a.report->backtracks = bt_total;
-            a.report->support_changes = sc_total;
-            a.report->status = status;
-            a.report->resid_norm2 = resid2;
-            a.report->mu = mu;
-            a.report->full_selects = st_fsel + full_here;
-            // phases (CTA 0's clock): step size, (filter: in the gradient kernel), select,
-            // backtracking, residual product, commit, whole kernel
-            const unsigned long long t6 = gtimer_ns();
-            a.report->phase_us[0] = (float)(tp[1] - tp[0]) * 1e-3f;
-            a.report->phase_us[1] = 0.0f;
-            a.report->phase_us[2] = (float)(tp[2] - tp[1]) * 1e-3f;
-            a.report->phase_us[3] = (float)(tp[3] - tp[2]) * 1e-3f;
-            a.report->phase_us[4] = (float)(tp[4] - tp[3]) * 1e-3f;
-            a.report->phase_us[5] = (float)(t6 - tp[4]) * 1e-3f;
-            a.report->phase_us[6] = (float)(t6 - tp[0]) * 1e-3f;
-            a.report->phase_us[7] = 0.0f;
-        }
+    if (cta0 && tid == 0 && a.report) {
+        const unsigned long long t6 = gtimer_ns();
+        a.report->phase_us[4] = (float)(t6 - tp[3]) * 1e-3f;
+        a.report->phase_us[5] = 0.0f;
+        a.report->phase_us[6] = (float)(t6 - tp[0]) * 1e-3f;
+        a.report->phase_us[7] = 0.0f;
     }
 }
 

@@ -565,6 +565,12 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     K.gb.gsup = fb.gsup;
     K.gb.gcand = fb.gcand;
     K.gb.gcap = fb.gcap;
+    if (fast) {                     // max |r| from the iteration kernel's partials; final ||r||^2
+        K.gb.rpart = reinterpret_cast<const double*>(ws + pl.off_part);
+        K.gb.rgrid = iter_grid();
+        K.gb.report = report;
+        K.gb.trace_resid2 = tr.resid2;
+    }
     K.a_gb[0] = &K.gb; K.a_gb[1] = &K.tpcb; K.a_gb[2] = &K.nsb;
     gemv_t_node(K.gb, nsm, &K.p_gb, K.a_gb);
 
