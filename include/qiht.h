@@ -143,6 +143,7 @@ size_t qiht_gemv_cols_workspace_size(int32_t rows, int32_t count);
 qiht_status qiht_gemv_cols(const qiht_codes* Q, const int32_t* cols, const float* coef, int32_t count,
                            float* z, void* workspace, size_t workspace_bytes, qiht_stream_t stream);
 
+
 /* Allocation-free variant of qiht_gemv_cols. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they
  * need the product (code running while its stream is captured into a CUDA graph,
@@ -234,6 +235,41 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
 
 /* Drop every cached solver graph (e.g. before freeing buffers they reference). */
 void qiht_clear_graph_cache(void);
+
+/* ---------------------------------------------------------------------- */
+/* Many independent problems in one launch (the batched workload of the    */
+/* solver: Algorithm 2 applied to each problem separately)                  */
+/* ---------------------------------------------------------------------- */
+
+#define QIHT_BATCH_MAX_ROWS 2048   /* m of every problem of a batch */
+#define QIHT_BATCH_MAX_COLS 8192   /* n */
+#define QIHT_BATCH_MAX_S 256       /* s */
+
+typedef struct {
+    qiht_codes Q1, Q2, y;   /* as for qiht_niht_solve; Q1 and Q2 of every problem of a batch have the same bits */
+    int32_t s;              /* sparsity, 1 <= s <= min(m, n, QIHT_BATCH_MAX_S) */
+    int32_t reserved;       /* 0 */
+    float* x;               /* [device] n: the returned x (dense) */
+    int32_t* support;       /* [device] s: its support, ascending */
+    qiht_report* report;    /* [device] the problem's report (phase_us zero) */
+} qiht_problem;
+
+/* Bytes of workspace for a batch of nprob problems (0 if nprob < 1). */
+size_t qiht_solve_batched_workspace_size(int32_t nprob);
+
+/* qiht_niht_solve for each of nprob independent problems (`problems`: a HOST array,
+ * read during the call; all buffers it points to are device memory), `iters` iterations
+ * each, in one persistent launch: every CTA solves whole problems, largest first,
+ * entirely in its shared memory (the limits above keep a problem's vectors there).
+ * Results per problem are those of the same algorithm and arithmetic as
+ * qiht_niht_solve (exact-integer gradient, FP32 products, FP64 step size; the order of
+ * some FP32 sums differs). Errors: QIHT_ERR_ARG (a problem out of the limits, mixed bits,
+ * bad pointers), QIHT_ERR_BITS, QIHT_ERR_WORKSPACE, QIHT_ERR_CUDA; per-problem numeric
+ * failures are in the problem's report. Asynchronous on `stream` after the descriptor
+ * copy. */
+qiht_status qiht_niht_solve_batched(const qiht_problem* problems, int32_t nprob, int32_t iters,
+                                    const qiht_params* params, void* workspace, size_t workspace_bytes,
+                                    qiht_stream_t stream);
 
 #ifdef __cplusplus
 }

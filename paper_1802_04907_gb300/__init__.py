@@ -47,6 +47,11 @@ class _Codes(ctypes.Structure):
                 ("cols", ctypes.c_int32), ("bits", ctypes.c_int32), ("ld_words", ctypes.c_int32)]
 
 
+class _Problem(ctypes.Structure):
+    _fields_ = [("Q1", _Codes), ("Q2", _Codes), ("y", _Codes), ("s", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("x", ctypes.c_void_p), ("support", ctypes.c_void_p), ("report", ctypes.c_void_p)]
+
+
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_double), ("c", ctypes.c_double), ("max_backtrack", ctypes.c_int32),
                 ("flags", ctypes.c_int32)]
@@ -72,7 +77,7 @@ EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld
            "qiht_gemv_t_workspace_size", "qiht_gemv_t", "qiht_gemv_t_prescaled",
            "qiht_gemv_cols_workspace_size", "qiht_gemv_cols", "qiht_gemv_cols_static",
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
-           "qiht_clear_graph_cache"]
+           "qiht_clear_graph_cache", "qiht_solve_batched_workspace_size", "qiht_niht_solve_batched"]
 
 _lib = None
 
@@ -105,6 +110,8 @@ def lib():
             "qiht_niht_solve": ([ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), I32, I32,
                                  ctypes.POINTER(_Params), P, P, P, ctypes.POINTER(_Trace), P, SZ, P], I32),
             "qiht_clear_graph_cache": ([], None),
+            "qiht_solve_batched_workspace_size": ([I32], SZ),
+            "qiht_niht_solve_batched": ([ctypes.POINTER(_Problem), I32, I32, ctypes.POINTER(_Params), P, SZ, P], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -312,6 +319,43 @@ def niht_solve(Q1: Codes, Q2: Codes, y: Codes, s: int, iters: int, *, trace: boo
     """One QIHT solve (Algorithm 2). Returns the Solver holding x, support, report (and trace)."""
     sv = Solver(Q1.rows, Q1.cols, s, iters, device=Q1.words.device, trace=trace, **kw)
     return sv(Q1, Q2, y, stream=stream)
+
+
+BATCH_MAX_ROWS, BATCH_MAX_COLS, BATCH_MAX_S = 2048, 8192, 256
+
+
+class BatchResult:
+    """Outputs of qiht_niht_solve_batched: x[i] (n_i), support[i] (s_i), report(i)."""
+
+    def __init__(self, xs, sups, reports, workspace):
+        self.x, self.support, self.reports, self.workspace = xs, sups, reports, workspace
+
+    def report(self, i: int) -> Report:
+        return report_from_bytes(bytes(self.reports[i].cpu().numpy().tobytes()))
+
+    def all_reports(self) -> list:
+        host = self.reports.cpu().numpy()
+        return [report_from_bytes(bytes(host[i].tobytes())) for i in range(host.shape[0])]
+
+
+def niht_solve_batched(problems: list, iters: int, *, k: float = 2.0, c: float = 0.01, max_backtrack: int = 32,
+                       stream=None) -> BatchResult:
+    """qiht_niht_solve_batched: problems is a list of (Q1, Q2, y, s) with Codes Q1, Q2, y."""
+    nprob = len(problems)
+    dev = problems[0][0].words.device
+    xs = [torch.empty(pr[0].cols, dtype=torch.float32, device=dev) for pr in problems]
+    sups = [torch.empty(pr[3], dtype=torch.int32, device=dev) for pr in problems]
+    reports = torch.zeros((nprob, REPORT_BYTES), dtype=torch.uint8, device=dev)
+    arr = (_Problem * nprob)()
+    for i, (q1, q2, qy, s) in enumerate(problems):
+        arr[i] = _Problem(q1.c_struct(), q2.c_struct(), qy.c_struct(), int(s), 0, xs[i].data_ptr(),
+                          sups[i].data_ptr(), reports[i].data_ptr())
+    ws = _ws(lib().qiht_solve_batched_workspace_size(nprob), dev)
+    params = _Params(k, c, max_backtrack, 0)
+    st = lib().qiht_niht_solve_batched(arr, nprob, iters, ctypes.byref(params), ws.data_ptr(), ws.numel(),
+                                       _stream(stream))
+    _check(st, "qiht_niht_solve_batched")
+    return BatchResult(xs, sups, reports, ws)
 
 
 def quantize_pair(v: torch.Tensor, bits: int, seed: int, stream_a: int, stream_b: int, *,

@@ -245,6 +245,11 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
                void** argbuf);
 size_t iter_args_bytes();
 
+// Many independent problems in one persistent launch (batched.cu).
+size_t batched_smem();
+cudaError_t launch_batched(const qiht_problem* probs, const int* order, int nprob, int bits, int iters, double k,
+                           double c, int max_bt, unsigned* next, cudaStream_t s);
+
 int gather_row_blocks(int rows, int bits);
 int gather_chunks(int count);
 size_t gather_partial_floats(int rows, int bits, int count);

@@ -13,6 +13,7 @@
 //          g = Q1^T r                              (gemv_t)
 // Control stays on the device for the whole solve. Graphs are cached per
 // argument set (pointers, sizes, parameters, device).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -903,6 +904,55 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
         }
     }
     CK(cudaGraphLaunch(exec, reinterpret_cast<cudaStream_t>(stream)));
+    return QIHT_OK;
+}
+
+size_t qiht_solve_batched_workspace_size(int32_t nprob)
+{
+    if (nprob < 1) return 0;
+    return align256((size_t)nprob * sizeof(qiht_problem)) + align256((size_t)nprob * 4) + 256;
+}
+
+qiht_status qiht_niht_solve_batched(const qiht_problem* problems, int32_t nprob, int32_t iters,
+                                    const qiht_params* params, void* workspace, size_t workspace_bytes,
+                                    qiht_stream_t stream)
+{
+    if (!problems || nprob < 1 || iters < 0) return QIHT_ERR_ARG;
+    qiht_params prm{2.0, 0.01, 32, 0};
+    if (params) prm = *params;
+    if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.flags != 0)
+        return QIHT_ERR_ARG;
+    const int bits = problems[0].Q1.bits;
+    for (int i = 0; i < nprob; ++i) {
+        const qiht_problem& P = problems[i];
+        TRY(check_codes(&P.Q1));
+        TRY(check_codes(&P.Q2));
+        TRY(check_codes(&P.y));
+        const int m = P.Q1.rows, n = P.Q1.cols;
+        if (P.Q1.bits != bits || P.Q2.bits != bits) return QIHT_ERR_ARG;
+        if (P.Q2.rows != m || P.Q2.cols != n || P.y.rows != m || P.y.cols != 1) return QIHT_ERR_ARG;
+        if (m > QIHT_BATCH_MAX_ROWS || n > QIHT_BATCH_MAX_COLS) return QIHT_ERR_ARG;
+        if (P.s < 1 || P.s > m || P.s > n || P.s > QIHT_BATCH_MAX_S) return QIHT_ERR_ARG;
+        if (!P.x || !P.support || !P.report) return QIHT_ERR_ARG;
+    }
+    if (!workspace || workspace_bytes < qiht_solve_batched_workspace_size(nprob) || !aligned(workspace, 256))
+        return QIHT_ERR_WORKSPACE;
+    // largest problems first (m n, then index): the persistent CTAs take them in this order
+    std::vector<int> order((size_t)nprob);
+    for (int i = 0; i < nprob; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)problems[a].Q1.rows * problems[a].Q1.cols > (long long)problems[b].Q1.rows * problems[b].Q1.cols;
+    });
+    char* ws = reinterpret_cast<char*>(workspace);
+    qiht_problem* d_probs = reinterpret_cast<qiht_problem*>(ws);
+    int* d_order = reinterpret_cast<int*>(ws + align256((size_t)nprob * sizeof(qiht_problem)));
+    unsigned* d_next = reinterpret_cast<unsigned*>(ws + align256((size_t)nprob * sizeof(qiht_problem)) +
+                                                   align256((size_t)nprob * 4));
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    // host -> device from pageable memory: both copies are staged before the calls return
+    CK(cudaMemcpyAsync(d_probs, problems, (size_t)nprob * sizeof(qiht_problem), cudaMemcpyHostToDevice, cs));
+    CK(cudaMemcpyAsync(d_order, order.data(), (size_t)nprob * 4, cudaMemcpyHostToDevice, cs));
+    CK(launch_batched(d_probs, d_order, nprob, bits, iters, prm.k, prm.c, prm.max_backtrack, d_next, cs));
     return QIHT_OK;
 }
 

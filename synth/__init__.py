@@ -148,6 +148,21 @@ def duplicated_pm1(m: int, base: int, dup: int, s: int, seed: int) -> Problem:
                    name=f"duplicated_pm1_{m}x{base * dup}_s{s}_seed{seed}")
 
 
+def batch_gaussian(count: int, seed: int, *, m_range=(128, 2048), n_per_m: int = 4, s_range=(8, 128),
+                   snr_db: float | None = None, values: str = "normal") -> list:
+    """Independent Gaussian problems of uneven sizes (the batched workload): m uniform in
+    m_range, n = n_per_m m, s uniform in s_range (at most m), each drawn by gaussian()
+    with its own seed."""
+    rng = _rng(seed)
+    out = []
+    for i in range(count):
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        s = int(min(m, rng.integers(s_range[0], s_range[1] + 1)))
+        out.append(gaussian(m, n_per_m * m, s, seed=int(rng.integers(0, 2**31 - 1)), snr_db=snr_db, values=values,
+                            name=f"batch{seed}_{i}"))
+    return out
+
+
 def small_noiseless(seed: int = 0) -> Problem:
     """m=256, n=1024, s=16, N(0,1) nonzeros, noiseless (shape of Section IV-A)."""
     return gaussian(256, 1024, 16, seed, snr_db=None, values="normal", name="gaussian_256x1024_s16")

@@ -84,6 +84,21 @@ def test_argument_errors_return_before_launch(lib):
                  P(16), P(16), None, P(256), 1 << 40, None) == q.ERR_ARG
     # top_s: s > n
     assert lib.qiht_top_s(P(16), 10, 11, P(16), None, None, None, 0, None) == q.ERR_ARG
+    # batched: empty batch, a problem above the limits, mixed widths, null outputs, no workspace
+    assert lib.qiht_solve_batched_workspace_size(0) == 0 and lib.qiht_solve_batched_workspace_size(3) > 0
+    pb = q._Problem(c, c, cy, 4, 0, 16, 16, 16)
+    arr = (q._Problem * 1)(pb)
+    assert lib.qiht_niht_solve_batched(arr, 0, 5, ctypes.byref(prm), P(256), 1 << 20, None) == q.ERR_ARG
+    cbig = q._Codes(16, 16, q.BATCH_MAX_ROWS + 4, 8, 8, q.ld_words(q.BATCH_MAX_ROWS + 4, 8))
+    cbigy = q._Codes(16, 16, q.BATCH_MAX_ROWS + 4, 1, 8, q.ld_words(q.BATCH_MAX_ROWS + 4, 8))
+    arr2 = (q._Problem * 2)(pb, q._Problem(cbig, cbig, cbigy, 4, 0, 16, 16, 16))
+    assert lib.qiht_niht_solve_batched(arr2, 2, 5, ctypes.byref(prm), P(256), 1 << 20, None) == q.ERR_ARG
+    c4 = q._Codes(16, 16, 64, 128, 4, q.ld_words(64, 4))
+    arr3 = (q._Problem * 2)(pb, q._Problem(c4, c4, cy, 4, 0, 16, 16, 16))
+    assert lib.qiht_niht_solve_batched(arr3, 2, 5, ctypes.byref(prm), P(256), 1 << 20, None) == q.ERR_ARG
+    arr4 = (q._Problem * 1)(q._Problem(c, c, cy, 4, 0, 16, 0, 16))
+    assert lib.qiht_niht_solve_batched(arr4, 1, 5, ctypes.byref(prm), P(256), 1 << 20, None) == q.ERR_ARG
+    assert lib.qiht_niht_solve_batched(arr, 1, 5, ctypes.byref(prm), None, 0, None) == q.ERR_WORKSPACE
 
 
 def test_package_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -1,0 +1,117 @@
+"""Many independent problems in one launch (qiht_niht_solve_batched) against the CPU
+oracle, problem by problem, and against the single-solve path.
+
+Every problem is quantized with its own seed (codes bit-exact, see
+test_gpu_quantize.py); both sides run the same number of iterations. The parity
+rule is the one of test_gpu_solve.py: supports identical while the oracle's selections
+are unambiguous, final x within 1e-4 relative L2, otherwise both recoveries compared
+with the ground truth."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1802_04907_gb300 as q
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GAP = 1e-5
+
+
+def _quantized(problems, bits, base_seed):
+    out = []
+    for i, p in enumerate(problems):
+        q1, q2, qy = q.quantize_problem(torch.from_numpy(p.phi).cuda(), torch.from_numpy(p.y).cuda(), bits, bits,
+                                        base_seed + i)
+        out.append((q1, q2, qy, p.s))
+    return out
+
+
+def _ambiguous(ref):
+    tr = ref.trace
+    return any(tr["min_gap"][t] < GAP or tr["min_margin"][t] < GAP for t in range(ref.iters_run + 1))
+
+
+def _check_against_oracle(res, problems, bits, base_seed, iters, idx):
+    for i in idx:
+        p = problems[i]
+        ref, _ = oracle.qiht(p.phi, p.y, p.s, iters, bits_phi=bits, bits_y=bits, seed=base_seed + i, trace=True)
+        rep = res.report(i)
+        assert rep.status == ref.status, (i, rep, ref.status)
+        x = res.x[i].cpu().numpy().astype(np.float64)
+        assert np.count_nonzero(x) <= p.s
+        if not _ambiguous(ref):
+            assert rep.iters_run == ref.iters_run, i
+            assert np.array_equal(np.sort(res.support[i].cpu().numpy()), ref.support), i
+            rel = np.linalg.norm(x - ref.x) / max(np.linalg.norm(ref.x), 1e-300)
+            assert rel <= 1e-4, (i, rel)
+        else:
+            truth = np.linalg.norm(p.x_true)
+            e_gpu = np.linalg.norm(x - p.x_true) / truth
+            e_ref = np.linalg.norm(ref.x - p.x_true) / truth
+            assert e_gpu <= max(1.5 * e_ref, e_ref + 0.02), (i, e_gpu, e_ref)
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_batch_against_oracle(bits):
+    # ragged sizes (m not a multiple of the codes per word, n = 4m); at 2 bits fewer nonzeros
+    # per measurement, where the method converges
+    s_range = (3, 12) if bits == 2 else (3, 40)
+    problems = synth.batch_gaussian(14, seed=40 + bits, m_range=(48, 700), s_range=s_range, snr_db=30.0,
+                                    values="pm_u")
+    qs = _quantized(problems, bits, 1000)
+    res = q.niht_solve_batched(qs, 30)
+    torch.cuda.synchronize()
+    _check_against_oracle(res, problems, bits, 1000, 30, range(len(problems)))
+
+
+def test_batch_equals_single_solves():
+    # the same problems through qiht_niht_solve one by one: same supports, x within FP32 noise
+    problems = synth.batch_gaussian(6, seed=7, m_range=(200, 900), s_range=(5, 30), snr_db=30.0, values="pm_u")
+    qs = _quantized(problems, 8, 55)
+    res = q.niht_solve_batched(qs, 40)
+    singles = [q.niht_solve(q1, q2, qy, s, 40) for (q1, q2, qy, s) in qs]
+    torch.cuda.synchronize()
+    for i, sv in enumerate(singles):
+        rb, rs = res.report(i), sv.read_report()
+        assert rb.status == rs.status and rb.iters_run == rs.iters_run, (i, rb, rs)
+        assert torch.equal(res.support[i], sv.support), i
+        xb, xs = res.x[i].double(), sv.x.double()
+        assert float(torch.linalg.norm(xb - xs) / torch.linalg.norm(xs)) < 1e-5, i
+
+
+def test_batch_shaped_like_the_batched_workload():
+    # sizes of the batched workload (m in [128, 2048], n = 4m, s in [8, 128], 4-bit, noiseless),
+    # fewer problems; invariants for all, oracle parity for three of them
+    problems = synth.batch_gaussian(24, seed=3)
+    qs = _quantized(problems, 4, 9000)
+    res = q.niht_solve_batched(qs, 25)
+    torch.cuda.synchronize()
+    reps = res.all_reports()
+    for i, p in enumerate(problems):
+        assert reps[i].status in (q.OK, q.ERR_BACKTRACK_CAP), (i, reps[i])
+        sup = res.support[i].cpu().numpy()
+        assert len(np.unique(sup)) == p.s and np.all(np.diff(sup) > 0) and sup.min() >= 0 and sup.max() < p.n
+        x = res.x[i].cpu().numpy()
+        assert np.all(np.isfinite(x)) and set(np.flatnonzero(x)) <= set(sup)
+    sizes = np.array([p.m for p in problems])
+    pick = [int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2]), int(np.argmax(sizes))]
+    _check_against_oracle(res, problems, 4, 9000, 25, pick)
+
+
+def test_batch_limits_are_checked():
+    ok = synth.gaussian(64, 256, 4, seed=1)
+    big = synth.gaussian(q.BATCH_MAX_ROWS + 8, 40, 4, seed=2)
+    qok = _quantized([ok], 8, 1)[0]
+    qbig = _quantized([big], 8, 2)[0]
+    with pytest.raises(q.QihtError) as e:
+        q.niht_solve_batched([qok, qbig], 5)
+    assert e.value.status == q.ERR_ARG
+    q4 = _quantized([ok], 4, 3)[0]
+    with pytest.raises(q.QihtError) as e:
+        q.niht_solve_batched([qok, q4], 5)                 # mixed widths
+    assert e.value.status == q.ERR_ARG
+    with pytest.raises(q.QihtError) as e:
+        q.niht_solve_batched([(qok[0], qok[1], qok[2], q.BATCH_MAX_S + 1)], 5)
+    assert e.value.status == q.ERR_ARG
