@@ -8,6 +8,7 @@ library of the package and never imports it.
 Functions mirror the paper's steps:
   philox4x32_10, uniform         random numbers of the stochastic quantizer
   absmax                         c_v = max |v| (Appendix, quantization lemma)
+  levels                         grid size: 2^b (Section III-A) or 2^(b-1)+1 (Appendix remark)
   quantize / dequantize          Q(v, b) of Section III-A, and its value c * q_code
   gemv_t, gemv_cols              plain FP64 products
   top_s                          hard threshold H_s (Eq. NIHT)
@@ -121,13 +122,22 @@ def absmax(v: np.ndarray) -> tuple[float, int]:
     return float(np.float32(c)), int(bad.value)
 
 
+def levels(bits: int, odd: bool = False) -> int:
+    """Number of quantization levels of b bits: 2^b equally spaced levels on [-1, 1]
+    (Section III-A), or, with odd=True, the 2^(b-1) + 1 levels of spacing 1/2^(b-2)
+    that the Appendix's remark on fixed-point hardware uses (0 is then a level)."""
+    return 2 ** (bits - 1) + 1 if odd else 2**bits
+
+
 def quantize(v: np.ndarray, bits: int, seed: int, stream: int, scale: float | None = None, *,
-             row0: int = 0, col0: int = 0, rows_total: int | None = None) -> tuple[np.ndarray, float]:
+             row0: int = 0, col0: int = 0, rows_total: int | None = None,
+             odd: bool = False) -> tuple[np.ndarray, float]:
     """Q(v, b) elementwise on a matrix (m x n) or vector (m,). Returns (codes, scale).
 
     codes have the shape of v (uint16). scale is c = max |v| unless given (for
     a block of a larger matrix, pass the whole matrix's scale, the block's
-    position and the whole matrix's row count).
+    position and the whole matrix's row count). odd selects the grid of
+    levels(bits, odd=True).
     """
     v = np.asarray(v, dtype=np.float32)
     vec = v.ndim == 1
@@ -140,16 +150,16 @@ def quantize(v: np.ndarray, bits: int, seed: int, stream: int, scale: float | No
     codes = np.zeros((rows, cols), dtype=np.uint16)
     st = lib().qo_quantize(_ptr(v2), rows, cols, cols, row0, col0,
                            rows if rows_total is None else rows_total,
-                           bits, seed, stream, np.float32(scale), _ptr(codes))
+                           levels(bits, odd), seed, stream, np.float32(scale), _ptr(codes))
     if st != OK:
         raise ValueError(f"qo_quantize status {st}")
     return (codes.reshape(-1) if vec else codes), float(np.float32(scale))
 
 
-def dequantize(codes: np.ndarray, bits: int, scale: float) -> np.ndarray:
+def dequantize(codes: np.ndarray, bits: int, scale: float, *, odd: bool = False) -> np.ndarray:
     c = np.ascontiguousarray(codes, dtype=np.uint16)
     out = np.zeros(c.shape, dtype=np.float64)
-    lib().qo_dequantize(_ptr(c), c.size, bits, np.float32(scale), _ptr(out))
+    lib().qo_dequantize(_ptr(c), c.size, levels(bits, odd), np.float32(scale), _ptr(out))
     return out
 
 
@@ -227,16 +237,17 @@ def niht(A1: np.ndarray, A2: np.ndarray, y: np.ndarray, s: int, iters: int, *, k
 
 
 def qiht(phi: np.ndarray, y: np.ndarray, s: int, iters: int, *, bits_phi: int, bits_y: int,
-         seed: int, **kw):
+         seed: int, odd: bool = False, **kw):
     """Quantize Phi twice (streams 0 and 1) and y once (stream 2), then run Algorithm 2.
+    odd=True quantizes all three on the odd grids of levels(bits, odd=True).
 
     Returns (NihtResult, dict with codes and scales)."""
-    c1, sphi = quantize(phi, bits_phi, seed, 0)
-    c2, _ = quantize(phi, bits_phi, seed, 1, sphi)
-    cy, sy = quantize(y, bits_y, seed, 2)
-    A1 = dequantize(c1, bits_phi, sphi)
-    A2 = dequantize(c2, bits_phi, sphi)
-    yq = dequantize(cy, bits_y, sy)
+    c1, sphi = quantize(phi, bits_phi, seed, 0, odd=odd)
+    c2, _ = quantize(phi, bits_phi, seed, 1, sphi, odd=odd)
+    cy, sy = quantize(y, bits_y, seed, 2, odd=odd)
+    A1 = dequantize(c1, bits_phi, sphi, odd=odd)
+    A2 = dequantize(c2, bits_phi, sphi, odd=odd)
+    yq = dequantize(cy, bits_y, sy, odd=odd)
     res = niht(A1, A2, yq, s, iters, **kw)
     return res, {"codes1": c1, "codes2": c2, "codes_y": cy, "scale_phi": sphi, "scale_y": sy,
                  "A1": A1, "A2": A2, "yq": yq}

@@ -20,6 +20,10 @@
  *
  * Readings of the paper (where it is silent or garbled):
  *   - 2^b equally spaced levels on [-1, 1], spacing 2/(2^b - 1)   (Section III-A)
+ *   - the Appendix's remark on fixed-point hardware gives a second grid of
+ *     2^(b-1) + 1 levels, spacing 1/2^(b-2), on which 0 is a level; the
+ *     quantizer takes the number of levels as an argument and treats both
+ *     grids (and any other level count) with the same rule
  *   - scale c = max |v| over the whole matrix / vector; c = 0 -> the
  *     normalised value is taken as 0 (the dequantised value is 0 anyway)
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), one stream per
@@ -103,12 +107,13 @@ float qo_absmax(const float* v, int64_t count, int64_t* nonfinite)
 }
 
 /* One quantisation decision, Section III-A.
- * Levels q_k = -1 + 2k/(L-1), k = 0..L-1, L = 2^b. With t = (v/c + 1)(L-1)/2,
- * v lies between q_i and q_{i+1} for i = floor(t); it is rounded up to q_{i+1}
- * with probability f = t - i (so E[Q(v)] = v) and down to q_i otherwise. */
-static int qo_code(float v, float c, int bits, float u)
+ * Levels q_k = -1 + 2k/(L-1), k = 0..L-1, for a grid of L levels (L = 2^b in
+ * the main text; L = 2^(b-1) + 1 for the odd grid of the Appendix's remark).
+ * With t = (v/c + 1)(L-1)/2, v lies between q_i and q_{i+1} for i = floor(t);
+ * it is rounded up to q_{i+1} with probability f = t - i (so E[Q(v)] = v) and
+ * down to q_i otherwise. */
+static int qo_code(float v, float c, int L, float u)
 {
-    const int L = 1 << bits;
     const float half = (QO_MUTANT == 2) ? (float)L * 0.5f : (float)(L - 1) * 0.5f;  /* exact */
     float vt = (c > 0.0f) ? v / c : 0.0f;               /* binary32, round to nearest */
     float t = (vt + 1.0f) * half;
@@ -121,31 +126,32 @@ static int qo_code(float v, float c, int bits, float u)
     return code;
 }
 
-/* Quantise a block of a matrix. The block is rows x cols, row-major with row
- * stride ld, and sits at (row0, col0) of a matrix with rows_total rows. The
- * random number of element (i, j) is the one of logical index e = j*rows_total + i
- * (column-major numbering), so the codes depend only on (i, j, seed, stream).
+/* Quantise a block of a matrix on a grid of `levels` levels (2 <= levels <=
+ * 65536). The block is rows x cols, row-major with row stride ld, and sits at
+ * (row0, col0) of a matrix with rows_total rows. The random number of element
+ * (i, j) is the one of logical index e = j*rows_total + i (column-major
+ * numbering), so the codes depend only on (i, j, seed, stream).
  * codes: rows x cols, row-major. A vector is a matrix with one column. */
 int qo_quantize(const float* v, int64_t rows, int64_t cols, int64_t ld,
                 int64_t row0, int64_t col0, int64_t rows_total,
-                int bits, uint64_t seed, uint32_t stream, float scale, uint16_t* codes)
+                int levels, uint64_t seed, uint32_t stream, float scale, uint16_t* codes)
 {
-    if (bits < 1 || bits > 16) return QO_ERR_BITS;
+    if (levels < 2 || levels > 65536) return QO_ERR_BITS;
     if (!(scale >= 0.0f) || !isfinite(scale)) return QO_ERR_NONFINITE;
     for (int64_t i = 0; i < rows; ++i) {
         for (int64_t j = 0; j < cols; ++j) {
             uint64_t e = (uint64_t)(col0 + j) * (uint64_t)rows_total + (uint64_t)(row0 + i);
             float u = qo_uniform(seed, stream, e);
-            codes[i * cols + j] = (uint16_t)qo_code(v[i * ld + j], scale, bits, u);
+            codes[i * cols + j] = (uint16_t)qo_code(v[i * ld + j], scale, levels, u);
         }
     }
     return QO_OK;
 }
 
 /* Dequantised value c * q_code = (c / (L-1)) * (2 code - (L-1)), in FP64. */
-void qo_dequantize(const uint16_t* codes, int64_t count, int bits, float scale, double* out)
+void qo_dequantize(const uint16_t* codes, int64_t count, int levels, float scale, double* out)
 {
-    const double lm1 = (double)((1 << bits) - 1);
+    const double lm1 = (double)(levels - 1);
     const double alpha = (double)scale / lm1;
     for (int64_t i = 0; i < count; ++i)
         out[i] = alpha * (2.0 * (double)codes[i] - ((QO_MUTANT == 9) ? lm1 + 1.0 : lm1));

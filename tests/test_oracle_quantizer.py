@@ -5,7 +5,9 @@ Each check is fixed by the paper's definition or by mathematics, not by the
 oracle itself: codes on the 2^b grid, deterministic results where the value is
 a grid point, unbiasedness E[Q(v)] = v, the rounding-up probability, the error
 bound of the quantization lemma, and independence of the random numbers from
-the storage layout.
+the storage layout. The odd grid of 2^(b-1) + 1 levels (the Appendix's remark on
+fixed-point hardware) is pinned by its level set, its exact zero, the ternary
+case b = 2 worked by hand, and the lemma's bound, which that grid's spacing gives.
 """
 import numpy as np
 import pytest
@@ -62,18 +64,20 @@ def test_endpoints_and_exact_grid_points_are_deterministic(bits):
     assert np.array_equal(codes, want)
 
 
+@pytest.mark.parametrize("odd", [False, True])
 @pytest.mark.parametrize("bits", [2, 4, 8])
-def test_unbiased(bits):
+def test_unbiased(bits, odd):
     # E[Q(v)] = v (Section III-A): mean over many independent draws within 5 sigma
     v = synth.random_floats(48, seed=20 + bits)
     v[0] = np.abs(v).max() * 1.5          # fixes the scale
     reps = 4000
     mat = np.repeat(v[:, None], reps, axis=1)
-    codes, c = oracle.quantize(mat, bits, seed=123, stream=0)
-    deq = oracle.dequantize(codes, bits, c)
+    codes, c = oracle.quantize(mat, bits, seed=123, stream=0, odd=odd)
+    deq = oracle.dequantize(codes, bits, c, odd=odd)
     mean = deq.mean(axis=1)
-    spacing = 2.0 * c / (2**bits - 1)
-    t = (v.astype(np.float64) / c + 1) * (2**bits - 1) / 2
+    lm1 = 2 ** (bits - 1) if odd else 2**bits - 1
+    spacing = 2.0 * c / lm1
+    t = (v.astype(np.float64) / c + 1) * lm1 / 2
     f = t - np.floor(t)
     sd = spacing * np.sqrt(f * (1 - f) / reps) + 1e-12
     z = np.abs(mean - v) / sd
@@ -144,3 +148,72 @@ def test_zero_scale_gives_zero_values():
     codes, c = oracle.quantize(v, 4, seed=0, stream=0)
     assert c == 0.0
     assert np.all(oracle.dequantize(codes, 4, c) == 0.0)
+
+
+# ---- the odd grid of the Appendix's remark: 2^(b-1) + 1 levels, spacing 1/2^(b-2) ----
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_odd_grid_codes_on_grid(bits):
+    nlev = 2 ** (bits - 1) + 1
+    assert oracle.levels(bits, odd=True) == nlev and oracle.levels(bits) == 2**bits
+    v = synth.random_floats((37, 53), seed=40 + bits)
+    v[0, 0] = np.abs(v).max()
+    v[0, 1] = -v[0, 0]
+    codes, c = oracle.quantize(v, bits, seed=6, stream=1, odd=True)
+    assert codes.max() <= nlev - 1 and codes.min() >= 0
+    deq = oracle.dequantize(codes, bits, c, odd=True)
+    # levels -1, -1 + 1/2^(b-2), ..., 1 (times c), written from the remark's spacing
+    grid = c * (-1.0 + np.arange(nlev) / 2.0 ** (bits - 2))
+    assert grid[-1] == c
+    assert np.all(np.isin(np.round(deq, 12), np.round(grid, 12)))
+    # each value goes to one of the two grid points around it
+    assert np.all(np.abs(deq - v) <= c / 2.0 ** (bits - 2) * (1 + 1e-6))
+    # +-c go to the end levels
+    assert codes[0, 0] == nlev - 1 and codes[0, 1] == 0
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_odd_grid_has_an_exact_zero(bits):
+    # 0 is a level of the odd grid: zero inputs quantize to it for every random number,
+    # whereas the 2^b grid (an even number of levels) has no zero level
+    v = np.zeros(4000, dtype=np.float32)
+    v[0] = np.float32(2.5)                     # sets c
+    codes, c = oracle.quantize(v, bits, seed=11, stream=0, odd=True)
+    assert np.all(codes[1:] == 2 ** (bits - 2))
+    assert np.all(oracle.dequantize(codes[1:], bits, c, odd=True) == 0.0)
+    codes_e, _ = oracle.quantize(v, bits, seed=11, stream=0)
+    deq_e = oracle.dequantize(codes_e[1:], bits, c)
+    assert np.all(deq_e != 0.0) and abs(deq_e.mean()) < 0.1 * c
+
+
+def test_odd_grid_two_bits_is_ternary():
+    # b = 2: levels {-c, 0, c}. v = c/4 lies between 0 and c with f = 1/4 exactly, so its
+    # code is 1 + (u < 1/4) for the element's own uniform u (the generator is pinned
+    # separately against Philox4x32-10)
+    n = 3000
+    v = np.full(n, 0.25, dtype=np.float32)
+    v[0] = np.float32(1.0)
+    seed, stream = 21, 2
+    codes, c = oracle.quantize(v, 2, seed=seed, stream=stream, odd=True)
+    assert c == 1.0 and codes[0] == 2
+    u = np.array([oracle.uniform(seed, stream, e) for e in range(n)])
+    assert np.array_equal(codes[1:], 1 + (u[1:] < 0.25))
+    assert np.array_equal(np.unique(oracle.dequantize(codes, 2, c, odd=True)), [0.0, 1.0])
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_odd_grid_error_bound_of_quantization_lemma(bits):
+    # The lemma's bound E||Q(v, b) - v||_2 <= c_v sqrt(M) / 2^(b-1) comes from the odd grid's
+    # spacing 1/2^(b-2): half a spacing squared, summed over M entries. It holds here, and the
+    # per-draw error stays below the worst case sqrt(M) * spacing / 2.
+    M = 512
+    v = synth.random_floats(M, seed=60 + bits)
+    c = float(np.abs(v).max())
+    errs = []
+    for seed in range(60):
+        codes, _ = oracle.quantize(v, bits, seed=seed, stream=2, odd=True)
+        errs.append(np.linalg.norm(oracle.dequantize(codes, bits, c, odd=True) - v))
+    assert max(errs) <= c * np.sqrt(M) / 2 ** (bits - 1) * (1 + 1e-9)
+    e = np.mean(errs)
+    assert e <= c * np.sqrt(M) / 2 ** (bits - 1)
+    assert e > 0.1 * c * np.sqrt(M) / 2 ** (bits - 1)
