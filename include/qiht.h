@@ -6,6 +6,7 @@
  * Thresholding with Low Precision Data Representation", IEEE TSP 2020.
  *   problem      y = Phi x + e, minimise ||y - Phi x||^2 s.t. ||x||_0 <= s     (Section I-A)
  *   quantizer    Q(v, b): 2^b levels on [-1, 1], stochastic rounding            (Section III-A)
+ *                or 2^(b-1) + 1 levels, 0 among them                          (Appendix, remark on FPGAs)
  *   iteration    x <- H_s(x + mu Q1^T (Q(y) - Q2 x)), adaptive mu, backtracking (Algorithm 2)
  *
  * Conventions (every entry point):
@@ -25,14 +26,18 @@
  * q of a column holds rows q*G .. q*G+G-1; the code of row q*G + 4k + p
  * (k = 0 .. G/4-1, p = 0..3) sits at bit 8p + bits*k. Rows past `rows` hold
  * code 0 and never contribute. A vector is a matrix with one column.
- * The value of code c is scale * (2c - (2^bits - 1)) / (2^bits - 1).
+ * Grids: L = 2^bits levels (Section III-A; the default), or the odd grid of
+ * L = 2^(bits-1) + 1 levels with spacing 1/2^(bits-2) on [-1, 1] (the
+ * Appendix's remark on fixed-point hardware; 0 is a level), stored in the same
+ * bits (codes 0 .. L-1). The value of code c is scale * (2c - (L - 1)) / (L - 1).
  *
  * Random numbers of the quantizer: Philox4x32-10 (Salmon et al., SC'11) with
  * key (seed low 32 bits, seed high 32 bits) and counter (e>>2 low, e>>2 high,
  * stream_id, 0), where e = j * rows + i is the column-major index of element
  * (i, j); element e uses output word e & 3 and u = (word >> 8) * 2^-24.
- * The rounding decision is taken in binary32: t = (v / c + 1) * (2^b - 1) / 2,
- * code = floor(t) + (u < t - floor(t)), each operation correctly rounded.
+ * The rounding decision is taken in binary32: t = (v / c + 1) * (L - 1) / 2,
+ * clamped to [0, L - 1], code = floor(t) + (u < t - floor(t)) (at most L - 1),
+ * each operation correctly rounded.
  */
 #ifndef QIHT_H
 #define QIHT_H
@@ -44,7 +49,7 @@
 extern "C" {
 #endif
 
-#define QIHT_ABI_VERSION 1
+#define QIHT_ABI_VERSION 2
 
 /* Same type as cudaStream_t. */
 typedef struct CUstream_st* qiht_stream_t;
@@ -78,6 +83,10 @@ typedef struct {
     int32_t cols;            /* columns (1 for a vector) */
     int32_t bits;            /* 2, 4 or 8 */
     int32_t ld_words;        /* words per column; must equal qiht_ld_words(rows, bits) */
+    int32_t levels;          /* grid the codes were made on: 0 or 2^bits (the default grid),
+                                or 2^(bits-1) + 1 (the odd grid, QIHT_ODD_LEVELS); any other
+                                value is QIHT_ERR_ARG */
+    int32_t reserved;        /* 0 */
 } qiht_codes;
 
 /* Words per column of the column-packed layout: ceil(rows / (32/bits)) rounded
@@ -91,6 +100,8 @@ int32_t qiht_ld_words(int32_t rows, int32_t bits);
 
 #define QIHT_SCALE_GIVEN   1  /* use *scale as it is (do not compute max |v|) */
 #define QIHT_CHECK_FINITE  2  /* synchronise `stream` and return QIHT_ERR_NONFINITE if the scale is not finite */
+#define QIHT_ODD_LEVELS    4  /* quantize on the odd grid of 2^(bits-1) + 1 levels; the codes are then
+                                 described by a qiht_codes with levels = 2^(bits-1) + 1 */
 
 /* Quantize a rows x cols float32 matrix `in` [device], row-major with row
  * stride ld_in >= cols (floats), to `bits`-bit codes in the column-packed

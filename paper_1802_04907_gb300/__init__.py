@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqiht.so")
 OK, ERR_ARG, ERR_BITS, ERR_NONFINITE, ERR_TIMEOUT, ERR_BACKTRACK_CAP, ERR_CUDA, ERR_WORKSPACE = range(8)
 SCALE_GIVEN = 1
 CHECK_FINITE = 2
+ODD_LEVELS = 4
 SOLVE_EAGER = 1
 SOLVE_TEST_TIMEOUT = 2
 
@@ -44,7 +45,8 @@ class QihtError(RuntimeError):
 
 class _Codes(ctypes.Structure):
     _fields_ = [("words", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("rows", ctypes.c_int32),
-                ("cols", ctypes.c_int32), ("bits", ctypes.c_int32), ("ld_words", ctypes.c_int32)]
+                ("cols", ctypes.c_int32), ("bits", ctypes.c_int32), ("ld_words", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _Problem(ctypes.Structure):
@@ -154,6 +156,11 @@ def ld_words(rows: int, bits: int) -> int:
     return int(lib().qiht_ld_words(rows, bits))
 
 
+def odd_levels(bits: int) -> int:
+    """Levels of the odd grid of b bits: 2^(b-1) + 1, spacing 1/2^(b-2) (0 is a level)."""
+    return 2 ** (bits - 1) + 1
+
+
 @dataclass
 class Codes:
     """A quantized matrix (rows x cols) or vector (cols = 1) in the column-packed layout."""
@@ -162,13 +169,19 @@ class Codes:
     rows: int
     cols: int
     bits: int
+    levels: int = 0          # 0 (= 2^bits, the default grid) or odd_levels(bits)
 
     @property
     def ld_words(self) -> int:
         return ld_words(self.rows, self.bits)
 
+    @property
+    def odd(self) -> bool:
+        return self.levels == odd_levels(self.bits) and self.levels != 2**self.bits
+
     def c_struct(self) -> _Codes:
-        return _Codes(self.words.data_ptr(), self.scale.data_ptr(), self.rows, self.cols, self.bits, self.ld_words)
+        return _Codes(self.words.data_ptr(), self.scale.data_ptr(), self.rows, self.cols, self.bits, self.ld_words,
+                      self.levels, 0)
 
     @property
     def nbytes(self) -> int:
@@ -177,8 +190,9 @@ class Codes:
 
 def quantize(v: torch.Tensor, bits: int, seed: int, stream_id: int, *, scale: torch.Tensor | None = None,
              scale_given: bool = False, check_finite: bool = False, out: Codes | None = None,
-             stream=None) -> Codes:
-    """qiht_quantize: Q(v, b) of a float32 matrix (rows x cols, row-major) or vector."""
+             odd: bool = False, stream=None) -> Codes:
+    """qiht_quantize: Q(v, b) of a float32 matrix (rows x cols, row-major) or vector.
+    odd=True quantizes on the odd grid of odd_levels(bits) levels."""
     assert v.is_cuda and v.dtype == torch.float32
     if v.dim() == 1:
         rows, cols, ld = v.shape[0], 1, 1
@@ -193,7 +207,8 @@ def quantize(v: torch.Tensor, bits: int, seed: int, stream_id: int, *, scale: to
         out = Codes(words, sc, rows, cols, bits)
     elif scale is not None:
         out.scale = scale
-    flags = (SCALE_GIVEN if scale_given else 0) | (CHECK_FINITE if check_finite else 0)
+    out.levels = odd_levels(bits) if odd else 0
+    flags = (SCALE_GIVEN if scale_given else 0) | (CHECK_FINITE if check_finite else 0) | (ODD_LEVELS if odd else 0)
     st = lib().qiht_quantize(v.data_ptr(), rows, cols, ld, bits, seed & (2**64 - 1), stream_id, flags,
                              out.words.data_ptr(), ldw, out.scale.data_ptr(), _stream(stream))
     _check(st, "qiht_quantize")
@@ -359,7 +374,7 @@ def niht_solve_batched(problems: list, iters: int, *, k: float = 2.0, c: float =
 
 
 def quantize_pair(v: torch.Tensor, bits: int, seed: int, stream_a: int, stream_b: int, *,
-                  out: tuple | None = None, stream=None) -> tuple:
+                  out: tuple | None = None, odd: bool = False, stream=None) -> tuple:
     """qiht_quantize_pair: two independent quantizations of one matrix in one pass (shared scale)."""
     assert v.is_cuda and v.dtype == torch.float32 and v.dim() == 2 and v.stride(1) == 1
     rows, cols = v.shape
@@ -370,7 +385,9 @@ def quantize_pair(v: torch.Tensor, bits: int, seed: int, stream_a: int, stream_b
         out = (Codes(torch.empty(cols * ldw, dtype=torch.int32, device=v.device), sc, rows, cols, bits),
                Codes(torch.empty(cols * ldw, dtype=torch.int32, device=v.device), sc, rows, cols, bits))
     qa, qb = out
-    st = lib().qiht_quantize_pair(v.data_ptr(), rows, cols, ld, bits, seed & (2**64 - 1), stream_a, stream_b, 0,
+    qa.levels = qb.levels = odd_levels(bits) if odd else 0
+    st = lib().qiht_quantize_pair(v.data_ptr(), rows, cols, ld, bits, seed & (2**64 - 1), stream_a, stream_b,
+                                  ODD_LEVELS if odd else 0,
                                   qa.words.data_ptr(), qb.words.data_ptr(), ldw, qa.scale.data_ptr(),
                                   _stream(stream))
     _check(st, "qiht_quantize_pair")
@@ -379,15 +396,16 @@ def quantize_pair(v: torch.Tensor, bits: int, seed: int, stream_a: int, stream_b
 
 
 def quantize_problem(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: int, seed: int, *,
-                     out: tuple | None = None, stream=None):
-    """Q1, Q2 (two independent quantizations of Phi, sharing its scale, in one pass) and Q(y)."""
+                     out: tuple | None = None, odd: bool = False, stream=None):
+    """Q1, Q2 (two independent quantizations of Phi, sharing its scale, in one pass) and Q(y);
+    odd=True puts all three on the odd grids."""
     if out is None:
-        q1, q2 = quantize_pair(phi, bits_phi, seed, STREAM_Q1, STREAM_Q2, stream=stream)
-        qy = quantize(y, bits_y, seed, STREAM_Y, stream=stream)
+        q1, q2 = quantize_pair(phi, bits_phi, seed, STREAM_Q1, STREAM_Q2, odd=odd, stream=stream)
+        qy = quantize(y, bits_y, seed, STREAM_Y, odd=odd, stream=stream)
         return q1, q2, qy
     q1, q2, qy = out
-    quantize_pair(phi, bits_phi, seed, STREAM_Q1, STREAM_Q2, out=(q1, q2), stream=stream)
-    quantize(y, bits_y, seed, STREAM_Y, out=qy, stream=stream)
+    quantize_pair(phi, bits_phi, seed, STREAM_Q1, STREAM_Q2, out=(q1, q2), odd=odd, stream=stream)
+    quantize(y, bits_y, seed, STREAM_Y, out=qy, odd=odd, stream=stream)
     return q1, q2, qy
 
 

@@ -201,9 +201,9 @@ __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;
-    constexpr int L = 1 << BITS;
-    constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
+    constexpr uint32_t MASK = 0x01010101u * (uint32_t)((1 << BITS) - 1);
     const int m = Q.rows, n = Q.cols, ld = Q.ld_words;
+    const long long lm1 = grid_levels(BITS, Q.levels) - 1;   // levels - 1 of the grid
     const int P = ld / 4;                              // 16-byte pieces per column
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -229,7 +229,7 @@ __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
         sm.limb[E * P * 4 + idx] = b1;
         sm.limb[2 * E * P * 4 + idx] = b2;
     }
-    const long long R = bsum_ll(rsum, sh.ll);          // also orders the limb stores
+    const long long R = lm1 * bsum_ll(rsum, sh.ll);    // (L-1) sum_i r_i; also orders the limb stores
     const double outscale = ldexp(sh.alpha1, -shf);
     const uint4* L0 = reinterpret_cast<const uint4*>(sm.limb);
     const uint4* L1 = L0 + E * P;
@@ -291,7 +291,7 @@ __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
                     s0[k] = 0; s1[k] = 0; s2[k] = 0;
                 }
                 if (lane == 0) {
-                    const long long T = 2 * S - (long long)(L - 1) * R;
+                    const long long T = 2 * S - R;
                     sm.g[warp + kcol * kBWarps] = (float)((double)T * outscale);
                 }
             }
@@ -301,15 +301,16 @@ __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
 }
 
 // z[0..m) = sum over the list (indices and coefficients in shared memory, in list order)
-// of coef_j * (2 c_ij - (L-1)) for the problem's Q2. Thread t owns code word t % ld of
+// of coef_j * (2 c_ij - (L-1)) for the problem's Q2 (L levels). Thread t owns code word t % ld of
 // every column (G rows) and the list entries of slice t / ld; the slices are summed in
 // order.
 template <int BITS>
 __device__ void bcols(const qiht_codes& Q, const int* list, const float* coef, int count, const BSm& sm)
 {
     constexpr int G = 32 / BITS;
-    constexpr int L = 1 << BITS;
+    constexpr uint32_t MASK = (1u << BITS) - 1;
     const int ld = Q.ld_words, m = Q.rows;
+    const int lm1 = grid_levels(BITS, Q.levels) - 1;
     const int tid = threadIdx.x;
     const int nsl = kBT / ld;                          // ld <= 512 under the batch limits
     const int wr = tid % ld, sl = tid / ld;
@@ -331,8 +332,8 @@ __device__ void bcols(const qiht_codes& Q, const int* list, const float* coef, i
             for (int u = 0; u < kBItems; ++u)
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
-                    const int code = (int)((w[u] >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
-                    zk[k] = fmaf((float)(2 * code - (L - 1)), cf[u], zk[k]);
+                    const int code = (int)((w[u] >> (8 * (k & 3) + BITS * (k >> 2))) & MASK);
+                    zk[k] = fmaf((float)(2 * code - lm1), cf[u], zk[k]);
                 }
         }
 #pragma unroll
@@ -487,17 +488,17 @@ template <int BITS>
 __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc, int max_bt, const BSm& sm,
                           BShared& sh)
 {
-    constexpr int L = 1 << BITS;
     const int tid = threadIdx.x;
     const int m = P.Q1.rows, n = P.Q1.cols, s = P.s;
-    const int Ly = 1 << P.y.bits, Gy = 32 / P.y.bits;
+    const uint32_t ymask = (1u << P.y.bits) - 1;
+    const int lm1y = grid_levels(P.y.bits, P.y.levels) - 1, Gy = 32 / P.y.bits;
     if (tid == 0) {
         const float c1 = *P.Q1.scale, c2 = *P.Q2.scale, cy = *P.y.scale;
         sh.code = (isfinite(c1) && isfinite(c2) && isfinite(cy)) ? 0 : 1;
-        sh.alpha1 = (double)c1 / (double)(L - 1);
-        sh.alpha2 = (double)c2 / (double)(L - 1);
+        sh.alpha1 = (double)c1 / (double)(grid_levels(BITS, P.Q1.levels) - 1);
+        sh.alpha2 = (double)c2 / (double)(grid_levels(BITS, P.Q2.levels) - 1);
         sh.alpha2f = (float)sh.alpha2;
-        sh.d[33] = (double)cy / (double)(Ly - 1);      // alpha of y
+        sh.d[33] = (double)cy / (double)lm1y;          // alpha of y
     }
     __syncthreads();
     const double alpha_y = sh.d[33];
@@ -507,8 +508,8 @@ __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc
     for (int i = tid; i < m; i += kBT) {
         const uint32_t w = __ldg(P.y.words + i / Gy);
         const int k = i % Gy;
-        const int code = (int)((w >> (8 * (k & 3) + P.y.bits * (k >> 2))) & (uint32_t)(Ly - 1));
-        const float v = (float)(alpha_y * (double)(2 * code - (Ly - 1)));
+        const int code = (int)((w >> (8 * (k & 3) + P.y.bits * (k >> 2))) & ymask);
+        const float v = (float)(alpha_y * (double)(2 * code - lm1y));
         sm.yhat[i] = v;
         sm.r[i] = v;
         acc += (double)v * (double)v;

@@ -74,7 +74,7 @@ template <int BITS>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
 {
     constexpr int G = 32 / BITS;
-    constexpr int L = 1 << BITS;
+    const int lm1 = a.Q.lm1;
     __shared__ double shd[33];
     __shared__ unsigned shu[33];
     __shared__ int flag;
@@ -142,8 +142,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
                     const float cf = s_cf[c];
 #pragma unroll
                     for (int k = 0; k < G; ++k) {
-                        const int code = (int)((w[c] >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
-                        z[k] = fmaf((float)(2 * code - (L - 1)), cf, z[k]);
+                        const int code = (int)((w[c] >> (8 * (k & 3) + BITS * (k >> 2))) & ((1u << BITS) - 1));
+                        z[k] = fmaf((float)(2 * code - lm1), cf, z[k]);
                     }
                 }
             }
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     if (!flag) return;
     __threadfence();
 
-    const float alpha = (float)((double)(*a.Q.scale) / (double)(L - 1));
+    const float alpha = (float)((double)(*a.Q.scale) / (double)a.Q.lm1);
     double acc = 0.0;
     unsigned mx = 0;
     if (q < ld) {
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     const double total = shd[32];
     const double mxd = shd[31];
     const double coef_norm2 = shd[30];
-    const double alpha_d = (double)(*a.Q.scale) / (double)(L - 1);
+    const double alpha_d = (double)(*a.Q.scale) / (double)a.Q.lm1;
 
     if (a.mode == kGatherMu) {
         if (threadIdx.x == 0) {
@@ -428,6 +428,7 @@ extern "C" qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t*
     if (!Q || !Q->words || !Q->scale) return QIHT_ERR_ARG;
     if (Q->bits != 2 && Q->bits != 4 && Q->bits != 8) return QIHT_ERR_BITS;
     if (Q->rows < 1 || Q->cols < 1 || Q->ld_words != qiht_ld_words(Q->rows, Q->bits)) return QIHT_ERR_ARG;
+    if (grid_levels(Q->bits, Q->levels) < 0) return QIHT_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(Q->words) & 15) != 0) return QIHT_ERR_ARG;
     if (!cols || !coef || !z || count < 1) return QIHT_ERR_ARG;
     // same scratch layout as qiht_gemv_cols; it must fit the fixed array
@@ -448,7 +449,7 @@ extern "C" qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t*
     const size_t off_rb = (fl * 4 + a256) & ~a256;
     const size_t off_cnt = off_rb + (((size_t)rbmax * 2 * 8 + a256) & ~a256);
     GatherArgs a{};
-    a.Q = Codes{Q->words, Q->scale, Q->rows, Q->cols, Q->bits, Q->ld_words};
+    a.Q = Codes{Q->words, Q->scale, Q->rows, Q->cols, Q->bits, Q->ld_words, grid_levels(Q->bits, Q->levels) - 1};
     a.cols = cols;
     a.coef = coef;
     a.count = count;

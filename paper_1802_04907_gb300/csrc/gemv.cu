@@ -1,7 +1,8 @@
 // g = Q^T r over column-packed b-bit codes: the gradient product of Algorithm 2
 // (g = Q1^T (Q(y) - Q2 x)), one full pass over the codes per call.
 //
-// Arithmetic. The value of code c is alpha * (2c - (L-1)), alpha = scale / (L-1),
+// Arithmetic. On a grid of L levels (2^b, or 2^(b-1) + 1 on the odd grid) the value of
+// code c is alpha * (2c - (L-1)), alpha = scale / (L-1),
 // so  g_j = alpha * (2 * sum_i c_ij r_i - (L-1) * sum_i r_i).
 // r is converted once per call to 24-bit block fixed point, r_i ~ rf_i * 2^-sh
 // with a power-of-two scale from max |r| (|rf_i| < 2^22), and rf_i is split into
@@ -80,8 +81,7 @@ __global__ void __launch_bounds__(256) k_gemv_t(GemvTArgs a, int tpc)
 {
     constexpr int G = 32 / BITS;          // codes per word
     constexpr int E = G / 4;              // 4-code extractions per word
-    constexpr int L = 1 << BITS;
-    constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
+    constexpr uint32_t MASK = 0x01010101u * ((1u << BITS) - 1);
     constexpr int NW = RPT / G;           // words per thread per column
     constexpr int NL = RPT / 4;           // limb words per limb per thread
 
@@ -134,8 +134,9 @@ __global__ void __launch_bounds__(256) k_gemv_t(GemvTArgs a, int tpc)
     const int wps = tpc >> 5;                     // warps per slot (tpc >= 32)
     long long R = 0;
     for (int w = 0; w < wps; ++w) R += red_r[w];  // slot 0's rows = all rows
+    R *= a.Q.lm1;                                 // (L-1) sum_i r_i
 
-    const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
+    const double alpha = (double)(*a.Q.scale) / (double)a.Q.lm1;
     const double outscale = ldexp(alpha, -sh);
 
     const int ncg = (n + CPW - 1) / CPW;
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(256) k_gemv_t(GemvTArgs a, int tpc)
                     S2 += red_c[buf][slot * wps + w][3 * c + 2];
                 }
                 const long long S = S0 + (S1 << 8) + (S2 << 16);
-                const long long T = 2 * S - (long long)(L - 1) * R;
+                const long long T = 2 * S - R;
                 a.g[j] = (float)((double)T * outscale);
             }
         }
@@ -290,8 +291,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;
-    constexpr int L = 1 << BITS;
-    constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
+    constexpr uint32_t MASK = 0x01010101u * ((1u << BITS) - 1);
     constexpr int NLW = PPT * 4 * E;            // limb words per limb per thread
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -401,7 +401,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
     consumer_sync();
     long long R = 0;
     for (int w = 0; w < wps; ++w) R += red_r[w];
-    const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
+    R *= a.Q.lm1;                                 // (L-1) sum_i r_i
+    const double alpha = (double)(*a.Q.scale) / (double)a.Q.lm1;
     const double outscale = ldexp(alpha, -sh);
 
     // Steady state: no CTA-wide barrier. Each warp adds its per-column integer sums
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_tma(GemvTArgs a, int 
                     volatile unsigned long long* vac = ac;
                     const long long S0 = (long long)vac[0], S1 = (long long)vac[1], S2 = (long long)vac[2];
                     const long long S = S0 + (S1 << 8) + (S2 << 16);
-                    const long long T = 2 * S - (long long)(L - 1) * R;
+                    const long long T = 2 * S - R;
                     a.g[c0 + it * cps + col] = (float)((double)T * outscale);
                     vac[0] = 0ull; vac[1] = 0ull; vac[2] = 0ull;
                     cnt[sb * cps + col] = 0u;
@@ -502,8 +503,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;                   // 16-byte limb loads per limb per piece
-    constexpr int L = 1 << BITS;
-    constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
+    constexpr uint32_t MASK = 0x01010101u * ((1u << BITS) - 1);
     constexpr int PPC = kChunkBytes / 16;      // pieces per column chunk
     constexpr int PPL = PPC / 32;              // pieces per lane per column chunk
 
@@ -610,7 +610,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
     consumer_sync();
     long long R = 0;
     for (int w = 0; w < kTmaWarps; ++w) R += red_r[w];
-    const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
+    R *= a.Q.lm1;                                 // (L-1) sum_i r_i
+    const double alpha = (double)(*a.Q.scale) / (double)a.Q.lm1;
     const double outscale = ldexp(alpha, -sh);
     const uint4* L0 = reinterpret_cast<const uint4*>(limb);
     const uint4* L1 = L0 + (size_t)E * P;
@@ -686,7 +687,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_gemv_t_col(GemvTArgs a, int 
                 const int col = warp * kCpw + c;
                 if (lane == c && col < gcols) {
                     const long long S = (long long)s0 + ((long long)s1 << 8) + ((long long)s2 << 16);
-                    const long long T = 2 * S - (long long)(L - 1) * R;
+                    const long long T = 2 * S - R;
                     a.g[gc0 + col] = (float)((double)T * outscale);
                 }
             }
@@ -764,8 +765,7 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;
-    constexpr int L = 1 << BITS;
-    constexpr uint32_t MASK = 0x01010101u * (uint32_t)(L - 1);
+    constexpr uint32_t MASK = 0x01010101u * ((1u << BITS) - 1);
     extern __shared__ __align__(16) uint32_t limb[];    // [3][E][P][4]
     __shared__ long long red_r[16];
     __shared__ unsigned bmax_cta;
@@ -863,13 +863,13 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
         long long v = rsum;
 #pragma unroll
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red_r[warp] = v;
+        if (lane == 0) red_r[warp] = v * a.Q.lm1;    // (L-1) times the warp's sum of r
     }
     if (threadIdx.x == 0) bmax_cta = 0u;
     if (threadIdx.x == 32) {
         // alpha 2^-sh, once per CTA: FP64 division is slow on this GPU, and every warp
         // that did it would hold back its first loads
-        const double alpha = (double)(*a.Q.scale) / (double)(L - 1);
+        const double alpha = (double)(*a.Q.scale) / (double)a.Q.lm1;
         outscale_sh = ldexp(alpha, -sh);
     }
     __syncthreads();
@@ -925,7 +925,7 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
             s0[k] = 0; s1[k] = 0; s2[k] = 0;
         }
         if (lane == 0) {
-            const long long T = 2 * S - (long long)(L - 1) * R;
+            const long long T = 2 * S - R;
             const float gv = (float)((double)T * outscale_sh);
             a.g[jj] = gv;
             if (pos_cur >= 0) {

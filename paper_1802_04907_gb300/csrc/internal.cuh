@@ -69,11 +69,24 @@ __device__ __forceinline__ double slot_max_complete(const double* part, int km, 
 }
 
 // Device view of a quantized matrix (see the column-packed layout in qiht.h).
+// lm1 = levels - 1 of its grid: 2^bits - 1 by default, 2^(bits-1) on the odd grid.
+// Codes are extracted with the bits-wide mask; lm1 enters only the affine term
+// 2c - lm1 of a value and the scale alpha = c / lm1.
 struct Codes {
     const uint32_t* words;
     const float* scale;
     int rows, cols, bits, ld;
+    int lm1;
 };
+
+// Number of levels of a grid given as in qiht_codes (0 = 2^bits); -1 unless it is
+// 2^bits or 2^(bits-1) + 1.
+__host__ __device__ inline int grid_levels(int bits, int levels)
+{
+    if (levels == 0 || levels == (1 << bits)) return 1 << bits;
+    if (levels == (1 << (bits - 1)) + 1) return levels;
+    return -1;
+}
 
 __host__ __device__ inline int codes_per_word(int bits) { return 32 / bits; }
 
@@ -219,7 +232,8 @@ cudaError_t launch_absmax(const float* in, int rows, int cols, int64_t ld, float
 // words2 != nullptr: a second quantization (stream_id2) of the same input in the same pass.
 cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int bits, uint64_t seed,
                             uint32_t stream_id, uint32_t* words, int ld_words, const float* scale,
-                            cudaStream_t s, uint32_t stream_id2 = 0, uint32_t* words2 = nullptr);
+                            cudaStream_t s, uint32_t stream_id2 = 0, uint32_t* words2 = nullptr,
+                            int levels = 0);
 cudaError_t launch_gemv_t(const GemvTArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
 cudaError_t launch_top(const TopArgs& a, cudaStream_t s);

@@ -408,9 +408,8 @@ __device__ __forceinline__ void rows_accum(const IterArgs& a, const RowBlock& rb
                                            const float* s_coef, int cn, int sl, int q, float (&z)[32 / BITS])
 {
     constexpr int G = 32 / BITS;
-    constexpr int L = 1 << BITS;
     constexpr int U = 8;                       // entries of a slice whose loads are in flight together
-    const int ld = a.Q.ld;
+    const int ld = a.Q.ld, lm1 = a.Q.lm1;
     for (int jj = sl; jj < cn; jj += U * rb.nsl) {
         uint32_t w[U];
         float cf[U];
@@ -425,8 +424,8 @@ __device__ __forceinline__ void rows_accum(const IterArgs& a, const RowBlock& rb
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int k = 0; k < G; ++k) {
-                const int code = (int)((w[u] >> (8 * (k & 3) + BITS * (k >> 2))) & (uint32_t)(L - 1));
-                z[k] = fmaf((float)(2 * code - (L - 1)), cf[u], z[k]);
+                const int code = (int)((w[u] >> (8 * (k & 3) + BITS * (k >> 2))) & ((1u << BITS) - 1));
+                z[k] = fmaf((float)(2 * code - lm1), cf[u], z[k]);
             }
     }
 }
@@ -791,7 +790,6 @@ template <int BITS>
 __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
 {
     constexpr int G = 32 / BITS;
-    constexpr int L = 1 << BITS;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double shd[33];
     __shared__ unsigned shu[33];
@@ -809,12 +807,12 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     float* red = s_coef + kListChunk;                           // kIterThreads * G
     float* zrow = red + kIterThreads * G;                       // kIterThreads
     unsigned char* sel_smem = smem;                             // CTA 0's select reuses the buffer
-    // alpha = scale / (L - 1) once per CTA (FP64 division is slow on this GPU); the
+    // alpha = scale / (levels - 1) once per CTA (FP64 division is slow on this GPU); the
     // first product's barriers publish it
     __shared__ double s_alpha;
     __shared__ float s_alpha_f;
     if (threadIdx.x == 32) {
-        s_alpha = (double)(*a.Q.scale) / (double)(L - 1);
+        s_alpha = (double)(*a.Q.scale) / (double)a.Q.lm1;
         s_alpha_f = (float)s_alpha;
     }
     const int m = a.m, s = a.s, n = a.n;
@@ -1350,7 +1348,6 @@ template <int BITS>
 __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
 {
     constexpr int G = 32 / BITS;
-    constexpr int L = 1 << BITS;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double shd[33];
     __shared__ unsigned shu[33];
@@ -1362,7 +1359,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     const bool cta0 = blockIdx.x == 0;
     // FP64 work (low throughput on this GPU) is done by single threads or single warps
     if (tid == 32) {
-        const double al = (double)(*a.Q.scale) / (double)(L - 1);
+        const double al = (double)(*a.Q.scale) / (double)a.Q.lm1;
         s_alpha = al;
         s_alpha_f = (float)al;
     }

@@ -63,27 +63,27 @@ __global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ in, in
     }
 }
 
-// One rounding decision in binary32, every operation correctly rounded:
-// t = (v / c + 1) * (L-1)/2, clamped to [0, L-1]; fi = floor(t), f = t - fi.
-// The code is fi + (u < f) (at most L-1); the decision does not depend on u, so
-// several quantizations of the same value share it.
+// One rounding decision in binary32, every operation correctly rounded, on a grid of
+// `levels` points (lm1 = levels - 1 intervals): t = (v / c + 1) * lm1/2, clamped to
+// [0, lm1]; fi = floor(t), f = t - fi. The code is fi + (u < f) (at most lm1); the
+// decision does not depend on u, so several quantizations of the same value share it.
 struct Decision {
     float fi, f;
 };
 
-__device__ __forceinline__ Decision quant_decide(float v, float c, float half, int L)
+__device__ __forceinline__ Decision quant_decide(float v, float c, float half, int lm1)
 {
     const float vt = (c > 0.0f) ? __fdiv_rn(v, c) : 0.0f;
     float t = __fmul_rn(__fadd_rn(vt, 1.0f), half);
-    t = fminf(fmaxf(t, 0.0f), (float)(L - 1));
+    t = fminf(fmaxf(t, 0.0f), (float)lm1);
     const float fi = floorf(t);
     return Decision{fi, __fsub_rn(t, fi)};
 }
 
-__device__ __forceinline__ uint32_t quant_code(const Decision& d, int L, float u)
+__device__ __forceinline__ uint32_t quant_code(const Decision& d, int lm1, float u)
 {
     const int code = (int)d.fi + (u < d.f ? 1 : 0);
-    return (uint32_t)min(code, L - 1);
+    return (uint32_t)min(code, lm1);
 }
 
 constexpr int kQTileRows = 128;
@@ -99,17 +99,16 @@ template <int BITS, int NS>
 __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, int rows, int cols,
                                                   long long ld, uint64_t seed, uint32_t stream0, uint32_t stream1,
                                                   uint32_t* __restrict__ words0, uint32_t* __restrict__ words1,
-                                                  int ldw, const float* __restrict__ scale_p)
+                                                  int ldw, const float* __restrict__ scale_p, int lm1)
 {
     constexpr int G = 32 / BITS;
-    constexpr int L = 1 << BITS;
     constexpr int WPC = kQTileRows / G;                   // words per column per tile
     constexpr int WPT = WPC * kQTileCols / 256;           // words per thread per tile
     constexpr int F4 = kQTileRows * kQTileCols / 4 / 256; // float4 loads per thread per tile
     __shared__ float tile[kQTileCols][kQTileRows + 1];
 
     const float c = *scale_p;
-    const float half = (float)(L - 1) * 0.5f;
+    const float half = (float)lm1 * 0.5f;
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
     const int row_tiles = (ldw * G + kQTileRows - 1) / kQTileRows;
     const int col_tiles = (cols + kQTileCols - 1) / kQTileCols;
@@ -182,12 +181,12 @@ __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, 
                             cur = qq;
                         }
                         const uint32_t sel = e & 3;
-                        const Decision d = quant_decide(tile[cc][q * G + kk], c, half, L);
+                        const Decision d = quant_decide(tile[cc][q * G + kk], c, half, lm1);
 #pragma unroll
                         for (int st = 0; st < NS; ++st) {
                             const uint32_t rw = sel == 0 ? rnd[st].x : sel == 1 ? rnd[st].y : sel == 2 ? rnd[st].z : rnd[st].w;
                             const float u = (float)(rw >> 8) * 0x1p-24f;
-                            word[st] |= quant_code(d, L, u) << (8 * (kk & 3) + BITS * (kk >> 2));
+                            word[st] |= quant_code(d, lm1, u) << (8 * (kk & 3) + BITS * (kk >> 2));
                         }
                     }
                 }
@@ -214,8 +213,10 @@ cudaError_t launch_absmax(const float* in, int rows, int cols, int64_t ld, float
 
 cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int bits, uint64_t seed,
                             uint32_t stream_id, uint32_t* words, int ld_words, const float* scale,
-                            cudaStream_t s, uint32_t stream_id2, uint32_t* words2)
+                            cudaStream_t s, uint32_t stream_id2, uint32_t* words2, int levels)
 {
+    if (levels <= 0) levels = 1 << bits;
+    const int lm1 = levels - 1;
     const int G = 32 / bits;
     const long long tiles = (long long)((ld_words * G + kQTileRows - 1) / kQTileRows) *
                             ((cols + kQTileCols - 1) / kQTileCols);
@@ -226,16 +227,16 @@ cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int
     const bool two = words2 != nullptr;
     switch (bits) {
     case 2:
-        if (two) k_quantize<2, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale);
-        else k_quantize<2, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale);
+        if (two) k_quantize<2, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
+        else k_quantize<2, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale, lm1);
         break;
     case 4:
-        if (two) k_quantize<4, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale);
-        else k_quantize<4, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale);
+        if (two) k_quantize<4, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
+        else k_quantize<4, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale, lm1);
         break;
     case 8:
-        if (two) k_quantize<8, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale);
-        else k_quantize<8, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale);
+        if (two) k_quantize<8, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
+        else k_quantize<8, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale, lm1);
         break;
     default: return cudaErrorInvalidValue;
     }

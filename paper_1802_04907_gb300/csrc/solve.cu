@@ -59,18 +59,19 @@ __global__ void __launch_bounds__(1024) k_init(InitKernelArgs ka)
     State* st = a.st;
     __shared__ double shd[33];
     __shared__ unsigned shu[33];
-    const int Ly = 1 << a.Y.bits;
+    const uint32_t ymask = (1u << a.Y.bits) - 1;
+    const int lm1y = a.Y.lm1;
     const int Gy = 32 / a.Y.bits;
     const float sy = *a.Y.scale, s1 = *a.scale_q1, s2 = *a.scale_q2;
     const bool finite = isfinite(sy) && isfinite(s1) && isfinite(s2);
-    const double alpha_y = (double)sy / (double)(Ly - 1);
+    const double alpha_y = (double)sy / (double)lm1y;
     double acc = 0.0;
     unsigned mx = 0;
     for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
         const uint32_t w = a.Y.words[i / Gy];
         const int k = i % Gy;
-        const int code = (int)((w >> (8 * (k & 3) + a.Y.bits * (k >> 2))) & (uint32_t)(Ly - 1));
-        const float v = (float)(alpha_y * (double)(2 * code - (Ly - 1)));
+        const int code = (int)((w >> (8 * (k & 3) + a.Y.bits * (k >> 2))) & ymask);
+        const float v = (float)(alpha_y * (double)(2 * code - lm1y));
         a.yhat[i] = v;
         a.r[i] = v;
         acc += (double)v * (double)v;
@@ -137,6 +138,7 @@ static qiht_status check_codes(const qiht_codes* Q)
     if (!bits_ok(Q->bits)) return QIHT_ERR_BITS;
     if (Q->rows < 1 || Q->cols < 1) return QIHT_ERR_ARG;
     if (Q->ld_words != qiht_ld_words(Q->rows, Q->bits)) return QIHT_ERR_ARG;
+    if (grid_levels(Q->bits, Q->levels) < 0) return QIHT_ERR_ARG;
     if (!aligned(Q->words, 16)) return QIHT_ERR_ARG;
     return QIHT_OK;
 }
@@ -150,6 +152,7 @@ static Codes view(const qiht_codes* Q)
     c.cols = Q->cols;
     c.bits = Q->bits;
     c.ld = Q->ld_words;
+    c.lm1 = grid_levels(Q->bits, Q->levels) - 1;
     return c;
 }
 
@@ -191,13 +194,14 @@ static qiht_status quantize_impl(const float* in, int32_t rows, int32_t cols, in
     if (!in || !words || !scale || rows < 1 || cols < 1 || ld_in < cols) return QIHT_ERR_ARG;
     if (ld_words != qiht_ld_words(rows, bits) || !aligned(words, 16)) return QIHT_ERR_ARG;
     if (words2 && (!aligned(words2, 16) || words2 == words)) return QIHT_ERR_ARG;
-    if (flags & ~(QIHT_SCALE_GIVEN | QIHT_CHECK_FINITE)) return QIHT_ERR_ARG;
+    if (flags & ~(QIHT_SCALE_GIVEN | QIHT_CHECK_FINITE | QIHT_ODD_LEVELS)) return QIHT_ERR_ARG;
+    const int levels = (flags & QIHT_ODD_LEVELS) ? (1 << (bits - 1)) + 1 : (1 << bits);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!(flags & QIHT_SCALE_GIVEN)) {
         if (launch_absmax(in, rows, cols, ld_in, scale, s) != cudaSuccess) return QIHT_ERR_CUDA;
     }
     if (launch_quantize(in, rows, cols, ld_in, bits, seed, stream_id, words, ld_words, scale, s, stream_id2,
-                        words2) != cudaSuccess)
+                        words2, levels) != cudaSuccess)
         return QIHT_ERR_CUDA;
     if (flags & QIHT_CHECK_FINITE) {
         float h = 0.0f;
@@ -407,6 +411,7 @@ void push_codes(std::vector<uint64_t>& v, const qiht_codes* Q)
     v.push_back((uint64_t)Q->cols);
     v.push_back((uint64_t)Q->bits);
     v.push_back((uint64_t)Q->ld_words);
+    v.push_back((uint64_t)grid_levels(Q->bits, Q->levels));
 }
 
 #define CK(x)                                       \

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_host_only_entry_points(lib):
-    assert lib.qiht_abi_version() == 1
+    assert lib.qiht_abi_version() == 2
     assert q.status_string(q.OK) == "QIHT_OK"
     assert q.status_string(q.ERR_BACKTRACK_CAP) == "QIHT_ERR_BACKTRACK_CAP"
     # words per column: ceil(rows / (32/bits)) rounded up to a multiple of 4
@@ -99,6 +99,45 @@ def test_argument_errors_return_before_launch(lib):
     arr4 = (q._Problem * 1)(q._Problem(c, c, cy, 4, 0, 16, 0, 16))
     assert lib.qiht_niht_solve_batched(arr4, 1, 5, ctypes.byref(prm), P(256), 1 << 20, None) == q.ERR_ARG
     assert lib.qiht_niht_solve_batched(arr, 1, 5, ctypes.byref(prm), None, 0, None) == q.ERR_WORKSPACE
+
+
+def test_grid_levels_are_checked(lib):
+    P = ctypes.c_void_p
+    ld = q.ld_words(64, 8)
+    prm = q._Params(2.0, 0.01, 32, 0)
+    solve = lib.qiht_niht_solve
+    for bits in (2, 4, 8):
+        ldb = q.ld_words(64, bits)
+        cy = q._Codes(16, 16, 64, 1, 8, ld)
+        valid = {0, 2**bits, q.odd_levels(bits)}
+        for levels in sorted(valid | {1, 2**bits - 1, q.odd_levels(bits) + 1, 2**bits + 1, -1}):
+            ok = levels in valid
+            c = q._Codes(16, 16, 64, 128, bits, ldb, levels, 0)
+            # a valid grid gets as far as the workspace check; any other level count is an argument error
+            want = q.ERR_WORKSPACE if ok else q.ERR_ARG
+            assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 4, 10, ctypes.byref(prm), P(16),
+                         P(16), P(16), None, None, 0, None) == want, (bits, levels)
+            assert lib.qiht_gemv_t(ctypes.byref(c), P(16), P(16), None, 0, None) == want, (bits, levels)
+    # the odd-grid flag is a known quantize flag (null input still fails the argument check)
+    assert lib.qiht_quantize(None, 4, 4, 4, 8, 0, 0, q.ODD_LEVELS, P(16), 4, P(16), None) == q.ERR_ARG
+    assert lib.qiht_quantize(P(16), 4, 4, 4, 8, 0, 0, 8, P(16), 4, P(16), None) == q.ERR_ARG
+
+
+def test_struct_layout_matches_header(tmp_path):
+    # the binding's ctypes structures have the sizes and field offsets the C compiler gives the header's
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "qiht.h"\n'
+        'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(qiht_codes), offsetof(qiht_codes, levels),'
+        ' sizeof(qiht_problem), offsetof(qiht_problem, s), offsetof(qiht_problem, x), sizeof(qiht_report),'
+        ' sizeof(qiht_params)); return 0; }\n')
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(q._Codes), q._Codes.levels.offset, ctypes.sizeof(q._Problem), q._Problem.s.offset,
+            q._Problem.x.offset, ctypes.sizeof(q._Report), ctypes.sizeof(q._Params)]
+    assert got == want
 
 
 def test_package_fails_loudly_without_library(monkeypatch, tmp_path):

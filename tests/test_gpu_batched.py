@@ -19,11 +19,11 @@ pytestmark = pytest.mark.gpu
 GAP = 1e-5
 
 
-def _quantized(problems, bits, base_seed):
+def _quantized(problems, bits, base_seed, odd=False):
     out = []
     for i, p in enumerate(problems):
         q1, q2, qy = q.quantize_problem(torch.from_numpy(p.phi).cuda(), torch.from_numpy(p.y).cuda(), bits, bits,
-                                        base_seed + i)
+                                        base_seed + i, odd=odd)
         out.append((q1, q2, qy, p.s))
     return out
 
@@ -33,10 +33,11 @@ def _ambiguous(ref):
     return any(tr["min_gap"][t] < GAP or tr["min_margin"][t] < GAP for t in range(ref.iters_run + 1))
 
 
-def _check_against_oracle(res, problems, bits, base_seed, iters, idx):
+def _check_against_oracle(res, problems, bits, base_seed, iters, idx, odd=False):
     for i in idx:
         p = problems[i]
-        ref, _ = oracle.qiht(p.phi, p.y, p.s, iters, bits_phi=bits, bits_y=bits, seed=base_seed + i, trace=True)
+        ref, _ = oracle.qiht(p.phi, p.y, p.s, iters, bits_phi=bits, bits_y=bits, seed=base_seed + i, trace=True,
+                             odd=odd)
         rep = res.report(i)
         assert rep.status == ref.status, (i, rep, ref.status)
         x = res.x[i].cpu().numpy().astype(np.float64)
@@ -115,3 +116,15 @@ def test_batch_limits_are_checked():
     with pytest.raises(q.QihtError) as e:
         q.niht_solve_batched([(qok[0], qok[1], qok[2], q.BATCH_MAX_S + 1)], 5)
     assert e.value.status == q.ERR_ARG
+
+
+@pytest.mark.parametrize("bits", [2, 8])
+def test_batch_odd_grid_against_oracle(bits):
+    # every problem on the odd grid of 2^(b-1) + 1 levels, equal-magnitude nonzeros
+    s_range = (3, 10) if bits == 2 else (3, 30)
+    problems = synth.batch_gaussian(10, seed=60 + bits, m_range=(64, 600), s_range=s_range, snr_db=30.0,
+                                    values="ones")
+    qs = _quantized(problems, bits, 2000, odd=True)
+    res = q.niht_solve_batched(qs, 30)
+    torch.cuda.synchronize()
+    _check_against_oracle(res, problems, bits, 2000, 30, range(len(problems)), odd=True)

@@ -110,3 +110,43 @@ def test_gemv_t_full_size_sampled(bits):
         ref = float(oracle.gemv_t(col[:, None], r.astype(np.float64))[0])
         bound = ((c / L) * np.abs(2.0 * codes - L).sum() * 2.0 ** (e - 23) + 2.0**-24 * abs(ref)) * (1 + 2.0**-20)
         assert abs(g[j] - ref) <= bound, j
+
+
+# ---- products on the odd grid (2^(b-1) + 1 levels): the same bounds with L - 1 = 2^(b-1) ----
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+@pytest.mark.parametrize("shape", [(17, 5), (1000, 333), (4512, 640), (16384, 64)])
+def test_gemv_t_odd_grid(bits, shape):
+    m, n = shape
+    v = synth.random_floats((m, n), seed=m + 2 * n)
+    r = synth.random_floats(m, seed=m * 5 + 2, scale=0.41)
+    r[m // 2] *= 40.0
+    Q = q.quantize(torch.from_numpy(v).cuda(), bits, 6, 1, odd=True)
+    g = q.gemv_t(Q, torch.from_numpy(r).cuda()).cpu().numpy().astype(np.float64)
+    codes, c = oracle.quantize(v, bits, 6, 1, odd=True)
+    A = oracle.dequantize(codes, bits, c, odd=True)
+    ref = oracle.gemv_t(A, r.astype(np.float64))
+    lm1 = 2 ** (bits - 1)
+    alpha = c / lm1
+    e = np.frexp(np.max(np.abs(r)).astype(np.float64))[1]
+    absW = np.abs(2.0 * codes.astype(np.float64) - lm1)
+    bound = (alpha * absW.sum(axis=0) * 2.0 ** (e - 23) + 2.0**-24 * np.abs(ref)) * (1 + 2.0**-20) + 1e-30
+    err = np.abs(g - ref)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_gemv_cols_odd_grid(bits):
+    m, n, count = 1000, 500, 77
+    v = synth.random_floats((m, n), seed=n + 1)
+    rng = np.random.Generator(np.random.PCG64(count + 1))
+    cols = rng.choice(n, count, replace=False).astype(np.int32)
+    coef = rng.standard_normal(count).astype(np.float32)
+    Q = q.quantize(torch.from_numpy(v).cuda(), bits, 9, 1, odd=True)
+    z = q.gemv_cols(Q, torch.from_numpy(cols).cuda(), torch.from_numpy(coef).cuda()).cpu().numpy()
+    codes, c = oracle.quantize(v, bits, 9, 1, odd=True)
+    A = oracle.dequantize(codes, bits, c, odd=True)
+    ref = oracle.gemv_cols(A, cols, coef.astype(np.float64))
+    mag = np.abs(A[:, cols]) @ np.abs(coef.astype(np.float64))
+    bound = 1.1 * (2 * count + 4) * 2.0**-24 * mag + 1e-30
+    assert np.all(np.abs(z - ref) <= bound), (np.abs(z - ref) / bound).max()

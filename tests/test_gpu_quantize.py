@@ -127,3 +127,43 @@ def test_pair_strided_input(offset, ld):
     assert qa.scale.item() == c
     assert np.array_equal(layout.unpack(qa.words.cpu().numpy(), 301, cols, 8), wa)
     assert np.array_equal(layout.unpack(qb.words.cpu().numpy(), 301, cols, 8), wb)
+
+
+# ---- the odd grid (2^(b-1) + 1 levels, the Appendix's remark on fixed-point hardware) ----
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+@pytest.mark.parametrize("shape", [(3, 5), (257, 100), (4512, 64), (129, 1)])
+def test_odd_grid_codes_bit_exact(bits, shape):
+    m, n = shape
+    v = synth.random_floats((m, n), seed=m * 3 + n + bits)
+    v[m // 2, :] = 0.0                      # zeros land on the zero level
+    seed = 0x5EED0DD + bits
+    Q = q.quantize(torch.from_numpy(v).cuda(), bits, seed, 2, odd=True)
+    torch.cuda.synchronize()
+    want, c = oracle.quantize(v, bits, seed, 2, odd=True)
+    assert Q.scale.item() == c and Q.levels == q.odd_levels(bits) and Q.odd
+    words = Q.words.cpu().numpy()
+    got = layout.unpack(words, m, n, bits)
+    assert np.array_equal(got, want)
+    assert got.max() <= 2 ** (bits - 1)
+    if c > 0:
+        assert np.all(got[m // 2, :] == 2 ** (bits - 2))
+    assert layout.padding_is_zero(words, m, n, bits)
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_odd_grid_problem_quantization(bits):
+    m, n = 1001, 77
+    v = synth.random_floats((m, n), seed=15)
+    y = synth.random_floats(m, seed=16)
+    q1, q2, qy = q.quantize_problem(torch.from_numpy(v).cuda(), torch.from_numpy(y).cuda(), bits, bits, seed=3,
+                                    odd=True)
+    torch.cuda.synchronize()
+    c1, c = oracle.quantize(v, bits, 3, 0, odd=True)
+    c2, _ = oracle.quantize(v, bits, 3, 1, c, odd=True)
+    cy, sy = oracle.quantize(y, bits, 3, 2, odd=True)
+    assert np.array_equal(layout.unpack(q1.words.cpu().numpy(), m, n, bits), c1)
+    assert np.array_equal(layout.unpack(q2.words.cpu().numpy(), m, n, bits), c2)
+    assert np.array_equal(layout.unpack(qy.words.cpu().numpy(), m, 1, bits)[:, 0], cy)
+    assert q1.levels == q2.levels == qy.levels == q.odd_levels(bits)
+    assert qy.scale.item() == sy and q1.scale.item() == c

@@ -31,13 +31,14 @@ pytestmark = pytest.mark.gpu
 GAP = 1e-5
 
 
-def _run_pair(p, bits_phi, bits_y, iters, seed, **kw):
+def _run_pair(p, bits_phi, bits_y, iters, seed, odd=False, **kw):
     phi = torch.from_numpy(p.phi).cuda()
     y = torch.from_numpy(p.y).cuda()
-    q1, q2, qy = q.quantize_problem(phi, y, bits_phi, bits_y, seed)
+    q1, q2, qy = q.quantize_problem(phi, y, bits_phi, bits_y, seed, odd=odd)
     sv = q.niht_solve(q1, q2, qy, p.s, iters, trace=True, **kw)
     torch.cuda.synchronize()
-    ref, _ = oracle.qiht(p.phi, p.y, p.s, iters, bits_phi=bits_phi, bits_y=bits_y, seed=seed, trace=True, **kw)
+    ref, _ = oracle.qiht(p.phi, p.y, p.s, iters, bits_phi=bits_phi, bits_y=bits_y, seed=seed, trace=True,
+                         odd=odd, **kw)
     return sv, ref
 
 
@@ -280,3 +281,28 @@ def test_exact_ties_resolve_by_index():
     xg = sv.x.cpu().numpy().astype(np.float64)
     rel = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
     assert rel < 1e-4, rel
+
+
+# ---- the odd grid (2^(b-1) + 1 levels with a zero level, the Appendix's remark) ----
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_odd_grid_noisy_ragged(bits):
+    p = synth.gaussian(1000, 3001, 25, seed=10 + bits, snr_db=30.0, values="pm_u")
+    sv, ref = _run_pair(p, bits, bits, 80, seed=13, odd=True)
+    _check(sv, ref, p, f"odd-ragged-{bits}")
+
+
+@pytest.mark.parametrize("bits_phi,bits_y", [(2, 8), (4, 4)])
+def test_odd_grid_equal_magnitudes(bits_phi, bits_y):
+    # nonzeros of x all equal to 1 (the paper's harder synthetic case), mixed widths
+    p = synth.gaussian(512, 2048, 20, seed=7, snr_db=25.0, values="ones")
+    sv, ref = _run_pair(p, bits_phi, bits_y, 60, seed=4, odd=True)
+    _check(sv, ref, p, f"odd-ones-{bits_phi}/{bits_y}")
+
+
+def test_odd_grid_interferometry_full_size():
+    # the interferometry workload at full size (stacked real 4512 x 16384, s = 64) on the 8-bit
+    # odd grid (129 levels): 20 iterations against the oracle
+    p = synth.interferometry(seed=0)
+    sv, ref = _run_pair(p, 8, 8, 20, seed=3, odd=True)
+    _check(sv, ref, p, "odd-interferometry")
