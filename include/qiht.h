@@ -172,6 +172,22 @@ qiht_status qiht_gemv_cols(const qiht_codes* Q, const int32_t* cols, const float
 qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t* cols, const float* coef, int32_t count,
                                   float* z, qiht_stream_t stream);
 
+/* G = Q^T R for nrhs residual vectors at once: the gradient products of Algorithm 2 for
+ * many right-hand sides sharing one quantized matrix (many observations y_k of the same
+ * Phi), a dense contraction run on the tensor cores. R [device] nrhs x ldr floats (row k
+ * = residual k, Q->rows entries used, ldr >= Q->rows), G [device] nrhs x ldg floats
+ * (row k = Q^T r_k, Q->cols entries written, ldg >= Q->cols). Arithmetic: the centred
+ * codes 2c - (L-1) are exact in f16; each residual is scaled by a power of two and split
+ * into two f16 parts (hi + lo, about 22 significant bits); the products are exact and
+ * summed in FP32, then scaled once. Requires Q->rows <= 16384. status [device, one
+ * int32, may be NULL] is set to QIHT_ERR_TIMEOUT if a device-side wait ran out (and
+ * left as it was otherwise). Launches two kernels.
+ * Workspace: qiht_gemv_t_multi_workspace_size(Q->rows, nrhs) bytes, 256-byte aligned. */
+size_t qiht_gemv_t_multi_workspace_size(int32_t rows, int32_t nrhs);
+qiht_status qiht_gemv_t_multi(const qiht_codes* Q, const float* R, int64_t ldr, int32_t nrhs, float* G,
+                              int64_t ldg, int32_t* status, void* workspace, size_t workspace_bytes,
+                              qiht_stream_t stream);
+
 /* Hard threshold H_s (Eq. NIHT): the s entries of a [device, n floats] of
  * largest magnitude, ties broken by the lower index; exactly s are kept.
  * idx [device, s int32] receives their indices in ascending order, val

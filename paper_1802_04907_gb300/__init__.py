@@ -79,7 +79,8 @@ EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld
            "qiht_gemv_t_workspace_size", "qiht_gemv_t", "qiht_gemv_t_prescaled",
            "qiht_gemv_cols_workspace_size", "qiht_gemv_cols", "qiht_gemv_cols_static",
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
-           "qiht_clear_graph_cache", "qiht_solve_batched_workspace_size", "qiht_niht_solve_batched"]
+           "qiht_clear_graph_cache", "qiht_solve_batched_workspace_size", "qiht_niht_solve_batched",
+           "qiht_gemv_t_multi_workspace_size", "qiht_gemv_t_multi"]
 
 _lib = None
 
@@ -114,6 +115,8 @@ def lib():
             "qiht_clear_graph_cache": ([], None),
             "qiht_solve_batched_workspace_size": ([I32], SZ),
             "qiht_niht_solve_batched": ([ctypes.POINTER(_Problem), I32, I32, ctypes.POINTER(_Params), P, SZ, P], I32),
+            "qiht_gemv_t_multi_workspace_size": ([I32, I32], SZ),
+            "qiht_gemv_t_multi": ([ctypes.POINTER(_Codes), P, I64, I32, P, I64, P, P, SZ, P], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -225,6 +228,21 @@ def gemv_t(Q: Codes, r: torch.Tensor, g: torch.Tensor | None = None, *, workspac
     _check(lib().qiht_gemv_t(ctypes.byref(c), r.data_ptr(), g.data_ptr(), ws.data_ptr(), ws.numel(),
                              _stream(stream)), "qiht_gemv_t")
     return g
+
+
+def gemv_t_multi(Q: Codes, R: torch.Tensor, G: torch.Tensor | None = None, *, status: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """qiht_gemv_t_multi: G = Q^T R for the rows of R (nrhs x rows residuals) on the tensor cores."""
+    assert R.dim() == 2 and R.dtype == torch.float32 and R.stride(1) == 1
+    nrhs = R.shape[0]
+    if G is None:
+        G = torch.empty((nrhs, Q.cols), dtype=torch.float32, device=R.device)
+    ws = workspace if workspace is not None else _ws(lib().qiht_gemv_t_multi_workspace_size(Q.rows, nrhs), R.device)
+    c = Q.c_struct()
+    _check(lib().qiht_gemv_t_multi(ctypes.byref(c), R.data_ptr(), R.stride(0), nrhs, G.data_ptr(), G.stride(0),
+                                   status.data_ptr() if status is not None else None, ws.data_ptr(), ws.numel(),
+                                   _stream(stream)), "qiht_gemv_t_multi")
+    return G
 
 
 def gemv_t_prescaled(Q: Codes, r: torch.Tensor, rmax: torch.Tensor, g: torch.Tensor, *, stream=None):

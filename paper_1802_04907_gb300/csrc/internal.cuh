@@ -264,6 +264,22 @@ size_t batched_smem();
 cudaError_t launch_batched(const qiht_problem* probs, const int* order, int nprob, int bits, int iters, double k,
                            double c, int max_bt, unsigned* next, cudaStream_t s);
 
+// Host-side checks shared by the entry points (solve.cu).
+qiht_status check_codes(const qiht_codes* Q);   // pointers, bits, sizes, ld_words, levels, alignment
+Codes view(const qiht_codes* Q);
+void note_cuda_error(const char* what, cudaError_t e);
+
+// Gradient of many right-hand sides on the tensor cores (mrhs_gemm.cu).
+size_t mrhs_gemm_smem();
+int mrhs_pad_rhs(int nrhs);               // right-hand sides rounded up to the N tile
+int mrhs_pad_rows(int m);                 // rows rounded up to the K stage
+constexpr size_t kMrhsMapBytes = 128;     // a CUtensorMap
+cudaError_t mrhs_make_map(void* map, const void* R16, int mk, int rows);
+cudaError_t launch_mrhs_split(const float* R, long long ldr, int m, int nrhs, void* R16, float* sc,
+                              const float* scale, int lm1, cudaStream_t s);
+cudaError_t launch_mrhs_gemm(const Codes& Q, const void* map, const float* sc, float* G, long long ldg, int nrhs,
+                             int* status, cudaStream_t s);
+
 int gather_row_blocks(int rows, int bits);
 int gather_chunks(int count);
 size_t gather_partial_floats(int rows, int bits, int count);

@@ -132,7 +132,7 @@ static bool bits_ok(int b) { return b == 2 || b == 4 || b == 8; }
 
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-static qiht_status check_codes(const qiht_codes* Q)
+qiht_status qiht::check_codes(const qiht_codes* Q)
 {
     if (!Q || !Q->words || !Q->scale) return QIHT_ERR_ARG;
     if (!bits_ok(Q->bits)) return QIHT_ERR_BITS;
@@ -143,7 +143,7 @@ static qiht_status check_codes(const qiht_codes* Q)
     return QIHT_OK;
 }
 
-static Codes view(const qiht_codes* Q)
+Codes qiht::view(const qiht_codes* Q)
 {
     Codes c;
     c.words = Q->words;
