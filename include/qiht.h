@@ -298,6 +298,36 @@ qiht_status qiht_niht_solve_batched(const qiht_problem* problems, int32_t nprob,
                                     const qiht_params* params, void* workspace, size_t workspace_bytes,
                                     qiht_stream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* Many right-hand sides sharing one quantized matrix (Algorithm 2 run for  */
+/* many observations y_k of the same Phi)                                   */
+/* ---------------------------------------------------------------------- */
+
+#define QIHT_MULTI_MAX_ROWS 16384  /* m */
+#define QIHT_MULTI_MAX_COLS 32768  /* n */
+#define QIHT_MULTI_MAX_S 256       /* s */
+
+/* Bytes of workspace for qiht_niht_solve_multi (0 if a size is out of range). */
+size_t qiht_solve_multi_workspace_size(int32_t m, int32_t n, int32_t s, int32_t nrhs);
+
+/* qiht_niht_solve for nrhs observations y[k] (a HOST array of nrhs vector descriptors,
+ * each of Q1->rows entries, read during the call) sharing Q1 and Q2, `iters` iterations
+ * each. One iteration computes the gradients of all right-hand sides as one tensor-core
+ * product (qiht_gemv_t_multi), then the step size, H_s with backtracking and the
+ * residual of every right-hand side (one CTA each). Results: X [device] nrhs x n (row k
+ * = x of y[k], dense), support [device] nrhs x s (ascending), reports [device] nrhs.
+ * Arithmetic: that of qiht_niht_solve except the gradient (f16 products of the exact
+ * codes with a two-part f16 split of the residual, FP32 sums; see qiht_gemv_t_multi).
+ * Requires m <= QIHT_MULTI_MAX_ROWS, n <= QIHT_MULTI_MAX_COLS, 1 <= s <= min(m, n,
+ * QIHT_MULTI_MAX_S); params->flags must be 0. Errors as for qiht_niht_solve; numeric
+ * failures of a right-hand side are in its report, a device-side timeout of the
+ * gradient product (QIHT_ERR_TIMEOUT) in every report. Asynchronous on `stream` after
+ * the descriptor copy. */
+qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* y, int32_t nrhs,
+                                  int32_t s, int32_t iters, const qiht_params* params, float* X,
+                                  int32_t* support, qiht_report* reports, void* workspace, size_t workspace_bytes,
+                                  qiht_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,7 +80,8 @@ EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld
            "qiht_gemv_cols_workspace_size", "qiht_gemv_cols", "qiht_gemv_cols_static",
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
            "qiht_clear_graph_cache", "qiht_solve_batched_workspace_size", "qiht_niht_solve_batched",
-           "qiht_gemv_t_multi_workspace_size", "qiht_gemv_t_multi"]
+           "qiht_gemv_t_multi_workspace_size", "qiht_gemv_t_multi", "qiht_solve_multi_workspace_size",
+           "qiht_niht_solve_multi"]
 
 _lib = None
 
@@ -117,6 +118,9 @@ def lib():
             "qiht_niht_solve_batched": ([ctypes.POINTER(_Problem), I32, I32, ctypes.POINTER(_Params), P, SZ, P], I32),
             "qiht_gemv_t_multi_workspace_size": ([I32, I32], SZ),
             "qiht_gemv_t_multi": ([ctypes.POINTER(_Codes), P, I64, I32, P, I64, P, P, SZ, P], I32),
+            "qiht_solve_multi_workspace_size": ([I32, I32, I32, I32], SZ),
+            "qiht_niht_solve_multi": ([ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), I32,
+                                       I32, I32, ctypes.POINTER(_Params), P, P, P, P, SZ, P], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -389,6 +393,47 @@ def niht_solve_batched(problems: list, iters: int, *, k: float = 2.0, c: float =
                                        _stream(stream))
     _check(st, "qiht_niht_solve_batched")
     return BatchResult(xs, sups, reports, ws)
+
+
+MULTI_MAX_ROWS, MULTI_MAX_COLS, MULTI_MAX_S = 16384, 32768, 256
+
+
+class MultiResult:
+    """Outputs of qiht_niht_solve_multi: x (nrhs x n), support (nrhs x s), report(k)."""
+
+    def __init__(self, x, support, reports, workspace):
+        self.x, self.support, self.reports, self.workspace = x, support, reports, workspace
+
+    def report(self, k: int) -> Report:
+        return report_from_bytes(bytes(self.reports[k].cpu().numpy().tobytes()))
+
+    def all_reports(self) -> list:
+        host = self.reports.cpu().numpy()
+        return [report_from_bytes(bytes(host[i].tobytes())) for i in range(host.shape[0])]
+
+
+def niht_solve_multi(Q1: Codes, Q2: Codes, ys: list, s: int, iters: int, *, k: float = 2.0, c: float = 0.01,
+                     max_backtrack: int = 32, workspace: torch.Tensor | None = None, out: tuple | None = None,
+                     stream=None) -> MultiResult:
+    """qiht_niht_solve_multi: Algorithm 2 for every observation in ys (Codes vectors) sharing Q1, Q2."""
+    nrhs = len(ys)
+    dev = Q1.words.device
+    if out is None:
+        X = torch.empty((nrhs, Q1.cols), dtype=torch.float32, device=dev)
+        sup = torch.empty((nrhs, s), dtype=torch.int32, device=dev)
+        reports = torch.zeros((nrhs, REPORT_BYTES), dtype=torch.uint8, device=dev)
+    else:
+        X, sup, reports = out
+    ws = workspace if workspace is not None else _ws(lib().qiht_solve_multi_workspace_size(Q1.rows, Q1.cols, s,
+                                                                                          nrhs), dev)
+    arr = (_Codes * nrhs)(*[y.c_struct() for y in ys])
+    c1, c2 = Q1.c_struct(), Q2.c_struct()
+    params = _Params(k, c, max_backtrack, 0)
+    st = lib().qiht_niht_solve_multi(ctypes.byref(c1), ctypes.byref(c2), arr, nrhs, s, iters, ctypes.byref(params),
+                                     X.data_ptr(), sup.data_ptr(), reports.data_ptr(), ws.data_ptr(), ws.numel(),
+                                     _stream(stream))
+    _check(st, "qiht_niht_solve_multi")
+    return MultiResult(X, sup, reports, ws)
 
 
 def quantize_pair(v: torch.Tensor, bits: int, seed: int, stream_a: int, stream_b: int, *,

@@ -18,6 +18,7 @@ LIB = os.path.join(BUILD, "libqiht.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["quantize.cu", "gemv.cu", "gather.cu", "topk.cu", "iter.cu", "solve.cu", "batched.cu", "mrhs_gemm.cu",
+           "mrhs_step.cu",
            "mrhs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",

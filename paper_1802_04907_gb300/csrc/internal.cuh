@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the QIHT CUDA library.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -279,6 +280,38 @@ cudaError_t launch_mrhs_split(const float* R, long long ldr, int m, int nrhs, vo
                               const float* scale, int lm1, cudaStream_t s);
 cudaError_t launch_mrhs_gemm(const Codes& Q, const void* map, const float* sc, float* G, long long ldg, int nrhs,
                              int* status, cudaStream_t s);
+
+// Per-right-hand-side iterations after the gradient product (mrhs_step.cu).
+struct MrhsState {
+    double mu;                // last accepted step size
+    double resid2;            // ||Q(y) - Q2 x||^2 of the current iterate
+    int stop;                 // 0 running, 1 converged, 2 stopped by an error (status)
+    int status;
+    int iters_run, backtracks, changes, pad;
+};
+struct MrhsStepArgs {
+    Codes Q2;
+    const float* scale1;      // scale of Q1 (alpha1 of the next gradient product)
+    int lm1_1;                // levels - 1 of Q1
+    const qiht_codes* ydesc;  // nrhs observation codes [device]
+    const float* G;           // nrhs x n gradients
+    int32_t* sup;             // nrhs x s supports (ascending)
+    float* xs;                // nrhs x s values on them
+    __half* R16;              // f16 residual parts: rows k (hi) and rhi + k (lo), mk halves each
+    float* sc;                // alpha1 2^e_k
+    int mk, rhi;
+    MrhsState* st;
+    int n, m, s, nrhs;
+    double kk, cc;
+    int max_bt;
+    int mode;                 // 0: initial support, 1: an iteration
+    int last;                 // 1: no gradient product follows (skip the split)
+};
+size_t mrhs_step_smem(int n, int mk, int s);
+cudaError_t launch_mrhs_init(const MrhsStepArgs& a, cudaStream_t s);
+cudaError_t launch_mrhs_step(const MrhsStepArgs& a, int bits, cudaStream_t s);
+cudaError_t launch_mrhs_final(const MrhsStepArgs& a, float* X, qiht_report* reports, const int* gemm_status,
+                              cudaStream_t s);
 
 int gather_row_blocks(int rows, int bits);
 int gather_chunks(int count);

@@ -1,5 +1,5 @@
 // Entry points for many right-hand sides sharing one quantized matrix: the tensor-core
-// gradient product (qiht_gemv_t_multi).
+// gradient product (qiht_gemv_t_multi) and the solver built on it (qiht_niht_solve_multi).
 #include <cstring>
 
 #include "internal.cuh"
@@ -56,6 +56,109 @@ qiht_status qiht_gemv_t_multi(const qiht_codes* Q, const float* R, int64_t ldr, 
     alignas(64) unsigned char map[kMrhsMapBytes];
     CK(mrhs_make_map(map, r16, mk, 2 * np));
     CK(launch_mrhs_gemm(c, map, sc, G, ldg, nrhs, status, s));
+    return QIHT_OK;
+}
+
+struct MultiLayout {
+    size_t ydesc, r16, sc, g, xs, st, status, total;
+};
+
+static MultiLayout multi_layout(int m, int n, int s, int nrhs)
+{
+    const size_t np = (size_t)mrhs_pad_rhs(nrhs), mk = (size_t)mrhs_pad_rows(m);
+    MultiLayout L;
+    size_t o = 0;
+    L.ydesc = o; o += align256((size_t)nrhs * sizeof(qiht_codes));
+    L.r16 = o; o += align256(2 * np * mk * 2);
+    L.sc = o; o += align256(np * 4);
+    L.g = o; o += align256((size_t)nrhs * n * 4);
+    L.xs = o; o += align256((size_t)nrhs * s * 4);
+    L.st = o; o += align256((size_t)nrhs * sizeof(MrhsState));
+    L.status = o; o += 256;
+    L.total = o;
+    return L;
+}
+
+static bool multi_sizes_ok(int m, int n, int s, int nrhs)
+{
+    return m >= 1 && n >= 1 && nrhs >= 1 && s >= 1 && s <= m && s <= n && m <= QIHT_MULTI_MAX_ROWS &&
+           n <= QIHT_MULTI_MAX_COLS && s <= QIHT_MULTI_MAX_S;
+}
+
+size_t qiht_solve_multi_workspace_size(int32_t m, int32_t n, int32_t s, int32_t nrhs)
+{
+    if (!multi_sizes_ok(m, n, s, nrhs)) return 0;
+    return multi_layout(m, n, s, nrhs).total;
+}
+
+qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* y, int32_t nrhs,
+                                  int32_t s, int32_t iters, const qiht_params* params, float* X,
+                                  int32_t* support, qiht_report* reports, void* workspace, size_t workspace_bytes,
+                                  qiht_stream_t stream)
+{
+    qiht_status e = check_codes(Q1);
+    if (e != QIHT_OK) return e;
+    if ((e = check_codes(Q2)) != QIHT_OK) return e;
+    const int m = Q1->rows, n = Q1->cols;
+    if (Q2->rows != m || Q2->cols != n || Q2->bits != Q1->bits) return QIHT_ERR_ARG;
+    if (!y || !X || !support || !reports || iters < 0) return QIHT_ERR_ARG;
+    if (!multi_sizes_ok(m, n, s, nrhs)) return QIHT_ERR_ARG;
+    for (int k = 0; k < nrhs; ++k) {
+        if ((e = check_codes(&y[k])) != QIHT_OK) return e;
+        if (y[k].rows != m || y[k].cols != 1) return QIHT_ERR_ARG;
+    }
+    qiht_params prm{2.0, 0.01, 32, 0};
+    if (params) prm = *params;
+    if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.flags != 0)
+        return QIHT_ERR_ARG;
+    const MultiLayout L = multi_layout(m, n, s, nrhs);
+    if (!workspace || workspace_bytes < L.total || !aligned256(workspace)) return QIHT_ERR_WORKSPACE;
+    const int mk = mrhs_pad_rows(m), np = mrhs_pad_rhs(nrhs);
+    if (mrhs_step_smem(n, mk, s) > (size_t)227 * 1024 - 1024) return QIHT_ERR_ARG;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    char* w = reinterpret_cast<char*>(workspace);
+    qiht_codes* d_y = reinterpret_cast<qiht_codes*>(w + L.ydesc);
+    int* gstatus = reinterpret_cast<int*>(w + L.status);
+    CK(cudaMemcpyAsync(d_y, y, (size_t)nrhs * sizeof(qiht_codes), cudaMemcpyHostToDevice, cs));
+    CK(cudaMemsetAsync(gstatus, 0, sizeof(int), cs));
+
+    MrhsStepArgs a{};
+    a.Q2 = view(Q2);
+    a.scale1 = Q1->scale;
+    a.lm1_1 = view(Q1).lm1;
+    a.ydesc = d_y;
+    a.G = reinterpret_cast<float*>(w + L.g);
+    a.sup = support;
+    a.xs = reinterpret_cast<float*>(w + L.xs);
+    a.R16 = reinterpret_cast<__half*>(w + L.r16);
+    a.sc = reinterpret_cast<float*>(w + L.sc);
+    a.mk = mk;
+    a.rhi = np;
+    a.st = reinterpret_cast<MrhsState*>(w + L.st);
+    a.n = n;
+    a.m = m;
+    a.s = s;
+    a.nrhs = nrhs;
+    a.kk = prm.k;
+    a.cc = prm.c;
+    a.max_bt = prm.max_backtrack;
+    alignas(64) unsigned char map[kMrhsMapBytes];
+    CK(mrhs_make_map(map, a.R16, mk, 2 * np));
+    const Codes c1 = view(Q1);
+    float* G = reinterpret_cast<float*>(w + L.g);
+
+    CK(launch_mrhs_init(a, cs));
+    CK(launch_mrhs_gemm(c1, map, a.sc, G, n, nrhs, gstatus, cs));
+    a.mode = 0;
+    a.last = iters == 0;
+    CK(launch_mrhs_step(a, Q1->bits, cs));
+    for (int it = 1; it <= iters; ++it) {
+        a.mode = 1;
+        a.last = it == iters;
+        CK(launch_mrhs_step(a, Q1->bits, cs));
+        if (!a.last) CK(launch_mrhs_gemm(c1, map, a.sc, G, n, nrhs, gstatus, cs));
+    }
+    CK(launch_mrhs_final(a, X, reports, gstatus, cs));
     return QIHT_OK;
 }
 

@@ -163,6 +163,49 @@ def batch_gaussian(count: int, seed: int, *, m_range=(128, 2048), n_per_m: int =
     return out
 
 
+@dataclass
+class MultiProblem:
+    """Many observations of one matrix: Y[k] = Phi X[k] + E[k] (rows of Y and X)."""
+
+    phi: np.ndarray          # float32, m x n
+    Y: np.ndarray            # float32, nrhs x m
+    X_true: np.ndarray       # float64, nrhs x n (s nonzeros per row)
+    s: int
+    name: str
+
+    def problem(self, k: int) -> Problem:
+        sup = np.flatnonzero(self.X_true[k])
+        return Problem(phi=self.phi, y=self.Y[k], x_true=self.X_true[k], support=sup, s=self.s,
+                       name=f"{self.name}_rhs{k}")
+
+
+def multi_gaussian(m: int, n: int, s: int, nrhs: int, seed: int, *, snr_db: float | None = None,
+                   values: str = "normal") -> MultiProblem:
+    """One Gaussian Phi (entries N(0, 1/m)) and nrhs independent s-sparse signals with their
+    observations (the many-right-hand-sides workload): supports uniform without replacement,
+    nonzeros as in gaussian(), noise per observation at snr_db."""
+    rng = _rng(seed)
+    phi = rng.standard_normal((m, n), dtype=np.float32)
+    phi *= np.float32(1.0 / np.sqrt(m))
+    X = np.zeros((nrhs, n))
+    Y = np.zeros((nrhs, m), dtype=np.float32)
+    for k in range(nrhs):
+        sup = np.sort(rng.choice(n, size=s, replace=False))
+        if values == "normal":
+            X[k, sup] = rng.standard_normal(s)
+        elif values == "pm_u":
+            X[k, sup] = np.where(rng.random(s) < 0.5, -1.0, 1.0) * rng.uniform(0.5, 1.5, size=s)
+        elif values == "ones":
+            X[k, sup] = 1.0
+        else:
+            raise ValueError(f"unknown values kind {values!r}")
+        clean = phi[:, sup].astype(np.float64) @ X[k, sup]
+        if snr_db is not None:
+            clean = clean + _noise_sigma(clean, snr_db) * rng.standard_normal(m)
+        Y[k] = clean.astype(np.float32)
+    return MultiProblem(phi=phi, Y=Y, X_true=X, s=s, name=f"multi_{m}x{n}_s{s}_r{nrhs}")
+
+
 def small_noiseless(seed: int = 0) -> Problem:
     """m=256, n=1024, s=16, N(0,1) nonzeros, noiseless (shape of Section IV-A)."""
     return gaussian(256, 1024, 16, seed, snr_db=None, values="normal", name="gaussian_256x1024_s16")

@@ -73,3 +73,117 @@ def test_gemv_t_multi_odd_grid():
     ref = np.stack([oracle.gemv_t(A, R[k].astype(np.float64)) for k in range(nrhs)])
     bound = _multi_bound(codes, 2**3, c, R, ref)
     assert np.all(np.abs(G - ref) <= bound)
+
+
+# ---- the solver for many right-hand sides (qiht_niht_solve_multi) ----
+
+GAP = 1e-5
+
+
+def _multi_run(mp, bits_phi, bits_y, iters, seed, odd=False, **kw):
+    phi = torch.from_numpy(mp.phi).cuda()
+    q1, q2 = q.quantize_pair(phi, bits_phi, seed, q.STREAM_Q1, q.STREAM_Q2, odd=odd)
+    ys = [q.quantize(torch.from_numpy(mp.Y[k]).cuda(), bits_y, seed, q.STREAM_Y, odd=odd)
+          for k in range(mp.Y.shape[0])]
+    res = q.niht_solve_multi(q1, q2, ys, mp.s, iters, **kw)
+    torch.cuda.synchronize()
+    return res, (q1, q2, ys)
+
+
+def _ambiguous(ref):
+    tr = ref.trace
+    return any(tr["min_gap"][t] < GAP or tr["min_margin"][t] < GAP for t in range(ref.iters_run + 1))
+
+
+def _check_rhs(res, mp, k, ref, tol=1e-4):
+    rep = res.report(k)
+    assert rep.status == ref.status, (k, rep, ref.status)
+    x = res.x[k].cpu().numpy().astype(np.float64)
+    assert np.count_nonzero(x) <= mp.s
+    sup = res.support[k].cpu().numpy()
+    assert np.all(np.diff(sup) > 0)
+    if not _ambiguous(ref):
+        assert rep.iters_run == ref.iters_run, k
+        assert np.array_equal(sup, ref.support), k
+        rel = np.linalg.norm(x - ref.x) / max(np.linalg.norm(ref.x), 1e-300)
+        assert rel <= tol, (k, rel)
+        return False
+    truth = np.linalg.norm(mp.X_true[k])
+    e_gpu = np.linalg.norm(x - mp.X_true[k]) / truth
+    e_ref = np.linalg.norm(ref.x - mp.X_true[k]) / truth
+    assert e_gpu <= max(1.5 * e_ref, e_ref + 0.02), (k, e_gpu, e_ref)
+    return True
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8])
+def test_multi_against_oracle(bits):
+    # 24 observations of one 512 x 2048 Gaussian matrix, s = 20 (8 at 2 bits), 30 dB
+    s = 8 if bits == 2 else 20
+    mp = synth.multi_gaussian(512, 2048, s, 24, seed=bits, snr_db=30.0, values="pm_u")
+    res, _ = _multi_run(mp, bits, bits, 40, seed=9)
+    amb = 0
+    for k in range(mp.Y.shape[0]):
+        p = mp.problem(k)
+        ref, _ = oracle.qiht(p.phi, p.y, s, 40, bits_phi=bits, bits_y=bits, seed=9, trace=True)
+        amb += _check_rhs(res, mp, k, ref)
+    assert amb < mp.Y.shape[0] // 2
+
+
+def test_multi_ragged_two_tiles_mixed_widths():
+    # 300 right-hand sides (two N tiles, the second ragged), m and n off every tile size,
+    # 4-bit Phi with 8-bit observations; a sample of them against the oracle
+    mp = synth.multi_gaussian(1000, 3001, 15, 300, seed=5, snr_db=25.0, values="normal")
+    res, _ = _multi_run(mp, 4, 8, 30, seed=2)
+    reps = res.all_reports()
+    assert all(r.status == q.OK for r in reps)
+    for k in (0, 1, 137, 255, 256, 299):
+        p = mp.problem(k)
+        ref, _ = oracle.qiht(p.phi, p.y, mp.s, 30, bits_phi=4, bits_y=8, seed=2, trace=True)
+        _check_rhs(res, mp, k, ref)
+
+
+def test_multi_matches_single_solves():
+    # the same observations through qiht_niht_solve one by one: same supports, x close
+    mp = synth.multi_gaussian(768, 4096, 24, 16, seed=11, snr_db=30.0, values="pm_u")
+    res, (q1, q2, ys) = _multi_run(mp, 8, 8, 50, seed=4)
+    for k in range(16):
+        sv = q.niht_solve(q1, q2, ys[k], mp.s, 50)
+        torch.cuda.synchronize()
+        rs, rm = sv.read_report(), res.report(k)
+        assert rs.status == rm.status == q.OK and rs.iters_run == rm.iters_run, (k, rs, rm)
+        assert torch.equal(torch.sort(sv.support).values, res.support[k]), k
+        xs, xm = sv.x.double(), res.x[k].double()
+        assert (torch.linalg.norm(xs - xm) / torch.linalg.norm(xs)).item() <= 1e-4, k
+
+
+def test_multi_odd_grid_and_equal_magnitudes():
+    mp = synth.multi_gaussian(512, 2048, 16, 12, seed=21, snr_db=30.0, values="ones")
+    res, _ = _multi_run(mp, 8, 8, 40, seed=6, odd=True)
+    for k in range(12):
+        p = mp.problem(k)
+        ref, _ = oracle.qiht(p.phi, p.y, mp.s, 40, bits_phi=8, bits_y=8, seed=6, trace=True, odd=True)
+        _check_rhs(res, mp, k, ref)
+
+
+def test_multi_nonfinite_observation_stops_only_that_one():
+    mp = synth.multi_gaussian(256, 1024, 8, 6, seed=3, snr_db=30.0)
+    mp.Y[2, 17] = np.inf
+    phi = torch.from_numpy(mp.phi).cuda()
+    q1, q2 = q.quantize_pair(phi, 8, 1, q.STREAM_Q1, q.STREAM_Q2)
+    ys = [q.quantize(torch.from_numpy(mp.Y[k]).cuda(), 8, 1, q.STREAM_Y) for k in range(6)]
+    res = q.niht_solve_multi(q1, q2, ys, mp.s, 20)
+    torch.cuda.synchronize()
+    reps = res.all_reports()
+    assert reps[2].status == q.ERR_NONFINITE and reps[2].iters_run == 0
+    assert torch.all(res.x[2] == 0)
+    assert all(reps[k].status == q.OK and reps[k].iters_run == 20 for k in (0, 1, 3, 4, 5))
+
+
+def test_multi_zero_iterations_gives_initial_supports():
+    mp = synth.multi_gaussian(256, 1024, 10, 5, seed=8)
+    res, (q1, q2, ys) = _multi_run(mp, 8, 8, 0, seed=3)
+    for k in range(5):
+        sv = q.niht_solve(q1, q2, ys[k], mp.s, 0)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.sort(sv.support).values, res.support[k])
+        assert torch.all(res.x[k] == 0)
