@@ -59,9 +59,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gemv-launches", type=int, default=200)
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
-                    help="single: the large single solve (default); batched: 512 independent problems in one launch")
+    ap.add_argument("--workload", choices=["single", "batched", "multi"], default="single",
+                    help="single: the large single solve (default); batched: 512 independent problems in one "
+                         "launch; multi: 1024 right-hand sides sharing the large matrix (tensor-core gradient)")
     ap.add_argument("--nprob", type=int, default=512)
+    ap.add_argument("--nrhs", type=int, default=1024)
+    ap.add_argument("--plain-sample", type=int, default=16)
     ap.add_argument("--eager", action="store_true",
                     help="launch the solver's kernels one by one instead of one graph (for kernel profilers, "
                          "which do not see the kernels of graphs with conditional nodes)")
@@ -490,12 +493,132 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+def run_multi(args):
+    """nrhs right-hand sides sharing the large Gaussian matrix (8192 x 32768, N(0, 1/m)), each
+    x_k with s = 256 N(0,1) nonzeros at a uniform support, y_k = Phi x_k + noise at 30 dB, Phi
+    and y_k quantized to 8 bits, 300 iterations each; inputs generated on the device from seeds.
+    value = solves/s of qiht_niht_solve_multi; a sample of the right-hand sides solved one by one
+    with qiht_niht_solve gives the plain rate; median recovery errors of both are reported (equal
+    error). The roofline is the tensor-core gradient product timed alone (residual split + GEMM)
+    against the measured dense bf16 rate (f16 and bf16 run at the same rate)."""
+    import torch
+
+    import paper_1802_04907_gb300 as q
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    m, n, s, bits, iters, nrhs = args.m, args.n, args.s, args.bits, args.iters, args.nrhs
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4242)
+    phi = torch.randn(m, n, generator=gen, device=dev, dtype=torch.float32) / float(np.sqrt(m))
+    X = torch.zeros(nrhs, n, device=dev, dtype=torch.float32)
+    for k in range(nrhs):
+        sup = torch.randperm(n, generator=gen, device=dev)[:s]
+        X[k, sup] = torch.randn(s, generator=gen, device=dev, dtype=torch.float32)
+    Yc = (X @ phi.t()).contiguous()                     # nrhs x m, FP32
+    sig = torch.sqrt((Yc.double() ** 2).sum(dim=1) / (m * 10.0 ** 3.0)).float()
+    Y = (Yc + sig[:, None] * torch.randn(nrhs, m, generator=gen, device=dev, dtype=torch.float32)).contiguous()
+    q1, q2 = q.quantize_pair(phi, bits, 7, q.STREAM_Q1, q.STREAM_Q2)
+    ys = [q.quantize(Y[k], bits, 7, q.STREAM_Y) for k in range(nrhs)]
+    del phi, Yc
+    torch.cuda.synchronize()
+    ws = q._ws(q.lib().qiht_solve_multi_workspace_size(m, n, s, nrhs), dev)
+    out = (torch.empty(nrhs, n, device=dev), torch.empty(nrhs, s, dtype=torch.int32, device=dev),
+           torch.zeros(nrhs, q.REPORT_BYTES, dtype=torch.uint8, device=dev))
+    for _ in range(max(1, args.warmup)):
+        res = q.niht_solve_multi(q1, q2, ys, s, iters, workspace=ws, out=out)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record()
+    for _ in range(args.steps):
+        res = q.niht_solve_multi(q1, q2, ys, s, iters, workspace=ws, out=out)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    reps = res.all_reports()
+
+    def rel(xs, idx):
+        return [float(torch.linalg.norm(xs[i] - X[k]) / torch.linalg.norm(X[k])) for i, k in enumerate(idx)]
+
+    err_m = rel(res.x, range(nrhs))
+    # plain: a sample of the right-hand sides through qiht_niht_solve (graph cached by a first pass)
+    sample = list(range(0, nrhs, max(1, nrhs // args.plain_sample)))[: args.plain_sample]
+    sv = q.Solver(m, n, s, iters, device=dev)
+    sv(q1, q2, ys[sample[0]])
+    torch.cuda.synchronize()
+    xs_plain = []
+    t_plain = 0.0
+    for k in sample:
+        ev0.record()
+        sv(q1, q2, ys[k])
+        ev1.record()
+        torch.cuda.synchronize()
+        t_plain += ev0.elapsed_time(ev1)
+        xs_plain.append(sv.x.clone())
+    err_p = rel(xs_plain, sample)
+    # the gradient product alone: residual split + tcgen05 GEMM over all right-hand sides
+    R = torch.randn(nrhs, m, generator=gen, device=dev, dtype=torch.float32)
+    G = torch.empty(nrhs, n, device=dev)
+    wsg = q._ws(q.lib().qiht_gemv_t_multi_workspace_size(m, nrhs), dev)
+    for _ in range(3):
+        q.gemv_t_multi(q1, R, G, workspace=wsg)
+    torch.cuda.synchronize()
+    reps_g = 10
+    ev0.record()
+    for _ in range(reps_g):
+        q.gemv_t_multi(q1, R, G, workspace=wsg)
+    ev1.record()
+    torch.cuda.synchronize()
+    gemm_us = ev0.elapsed_time(ev1) / reps_g * 1e3
+    flops = 2.0 * m * n * nrhs
+    tflops = flops / (gemm_us * 1e-6) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    launches = 3 + 2 * iters                          # init, GEMMs, step kernels, final
+    line = {"metric": "multi-RHS solves/s", "value": nrhs / (ms / 1e3), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": f"u{bits}", "data": "synthetic",
+            "config": {"workload": f"{nrhs} right-hand sides sharing Gaussian Phi {m}x{n} N(0,1/m), s={s} "
+                                   f"N(0,1) nonzeros each, 30 dB, {bits}-bit Phi and y, {iters} iterations",
+                       "nrhs": nrhs, "m": m, "n": n, "s": s, "bits": bits, "iters_per_step": iters,
+                       "l2": "inputs larger than L2: Q1 codes 256 MiB read by every gradient product"},
+            "iterations_per_s": sum(r.iters_run for r in reps) / (ms / 1e3),
+            "ms_per_iteration_all_rhs": ms / max(1, iters),
+            "plain": {"solves_per_s": len(sample) / (t_plain / 1e3), "ms_per_solve": t_plain / len(sample),
+                      "sample": len(sample), "how": "qiht_niht_solve per right-hand side, graph cached"},
+            "speedup_vs_plain": (nrhs / (ms / 1e3)) / (len(sample) / (t_plain / 1e3)),
+            "equal_error": {"multi_median_rel_err": float(np.median(err_m)),
+                            "multi_median_rel_err_on_sample": float(np.median([err_m[k] for k in sample])),
+                            "plain_median_rel_err_on_sample": float(np.median(err_p))},
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "traffic": None,
+                         "kernel": "k_mrhs_gemm (G = Q1^T R, f16 tcgen05, hi + lo parts)",
+                         "avg_launch_us": gemm_us, "algorithmic_flops_per_launch": flops,
+                         "note": "2 m n nrhs flops (R counted once; the hi and lo parts double the MMA work); "
+                                 "timed with the residual split; peak: measured dense bf16 burst (f16 rate equal)"},
+            "gpu_launches": launches * args.steps,
+            "clocks": clk,
+            "statuses": {str(k): sum(1 for r in reps if r.status == k) for k in sorted({r.status for r in reps})}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "multi":
+        run_multi(args)
     else:
         run_ours(args)
 
