@@ -294,6 +294,9 @@ struct MrhsStepArgs {
     const float* scale1;      // scale of Q1 (alpha1 of the next gradient product)
     int lm1_1;                // levels - 1 of Q1
     const qiht_codes* ydesc;  // nrhs observation codes [device]
+    float* yhat;              // nrhs x m dequantized observations (written by the init kernel)
+    float* resid;             // nrhs x m residuals
+    float* zmu;               // nrhs x m: Q2_G g_G of the current step size (unscaled)
     const float* G;           // nrhs x n gradients
     int32_t* sup;             // nrhs x s supports (ascending)
     float* xs;                // nrhs x s values on them
@@ -306,6 +309,7 @@ struct MrhsStepArgs {
     int max_bt;
     int mode;                 // 0: initial support, 1: an iteration
     int last;                 // 1: no gradient product follows (skip the split)
+    int refresh;              // 1: form the residual directly (else update it)
 };
 size_t mrhs_step_smem(int n, int mk, int s);
 cudaError_t launch_mrhs_init(const MrhsStepArgs& a, cudaStream_t s);

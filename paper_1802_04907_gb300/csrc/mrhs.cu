@@ -59,8 +59,12 @@ qiht_status qiht_gemv_t_multi(const qiht_codes* Q, const float* R, int64_t ldr, 
     return QIHT_OK;
 }
 
+// the residual is formed directly every kMultiRefresh iterations (and on the last), else
+// updated from the step's product
+constexpr int kMultiRefresh = 32;
+
 struct MultiLayout {
-    size_t ydesc, r16, sc, g, xs, st, status, total;
+    size_t ydesc, yhat, resid, zmu, r16, sc, g, xs, st, status, total;
 };
 
 static MultiLayout multi_layout(int m, int n, int s, int nrhs)
@@ -69,6 +73,9 @@ static MultiLayout multi_layout(int m, int n, int s, int nrhs)
     MultiLayout L;
     size_t o = 0;
     L.ydesc = o; o += align256((size_t)nrhs * sizeof(qiht_codes));
+    L.yhat = o; o += align256((size_t)nrhs * m * 4);
+    L.resid = o; o += align256((size_t)nrhs * m * 4);
+    L.zmu = o; o += align256((size_t)nrhs * m * 4);
     L.r16 = o; o += align256(2 * np * mk * 2);
     L.sc = o; o += align256(np * 4);
     L.g = o; o += align256((size_t)nrhs * n * 4);
@@ -127,6 +134,9 @@ qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, co
     a.scale1 = Q1->scale;
     a.lm1_1 = view(Q1).lm1;
     a.ydesc = d_y;
+    a.yhat = reinterpret_cast<float*>(w + L.yhat);
+    a.resid = reinterpret_cast<float*>(w + L.resid);
+    a.zmu = reinterpret_cast<float*>(w + L.zmu);
     a.G = reinterpret_cast<float*>(w + L.g);
     a.sup = support;
     a.xs = reinterpret_cast<float*>(w + L.xs);
@@ -155,6 +165,7 @@ qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, co
     for (int it = 1; it <= iters; ++it) {
         a.mode = 1;
         a.last = it == iters;
+        a.refresh = a.last || it % kMultiRefresh == 0;
         CK(launch_mrhs_step(a, Q1->bits, cs));
         if (!a.last) CK(launch_mrhs_gemm(c1, map, a.sc, G, n, nrhs, gstatus, cs));
     }

@@ -6,8 +6,11 @@
 // arithmetic: the step size mu = ||g_G||^2 / ||Q2_G g_G||^2 (FP64 sums of FP32 products
 // with column subsets of Q2, summed in list order), H_s as a radix select over the
 // binary32 keys |fmaf(mu, g, x)| with ties to the lower index, the backtracking test
-// omega = ||x' - x||^2 / ||Q2 (x' - x)||^2, and the residual r = Q(y) - Q2_G' x' formed
-// directly. The CTA then splits r into the scaled f16 parts the next GEMM reads.
+// omega = ||x' - x||^2 / ||Q2 (x' - x)||^2, and the residual r = Q(y) - Q2_G' x', updated
+// from the product the step already formed (Q2 (x' - x) of the backtracking test, or
+// mu Q2_G g_G when the support is unchanged), and directly as Q(y) - Q2_G' x' every few
+// iterations and on the last. The CTA then splits r into the scaled f16 parts the next
+// GEMM reads.
 // The iterate of a right-hand side is kept sparse (its support and the values on it).
 #include <cuda_fp16.h>
 
@@ -259,9 +262,11 @@ __device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, S
             const bool in = j < n;
             const uint32_t k = in ? sm.keys[j] : 0u;
             const bool take = in && (pass == 0 || (k >> (shift + 8)) == (prefix >> (shift + 8)));
+            if (!__any_sync(0xffffffffu, take)) continue;   // later passes: most steps have no candidate
             const unsigned bin = (k >> shift) & 255u;
-            // lanes with the same bin add once (most keys share the few top bins)
-            const unsigned peers = __match_any_sync(0xffffffffu, take ? bin : 0x100u + (unsigned)lane);
+            // lanes with the same bin add once (keys crowd into few bins); the other lanes share
+            // one value so that the match stays cheap
+            const unsigned peers = __match_any_sync(0xffffffffu, take ? bin : 0x100u);
             if (take && lane == __ffs(peers) - 1) atomicAdd(&sm.hist[bin], (unsigned)__popc(peers));
         }
         __syncthreads();
@@ -417,13 +422,10 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
     const float* g = a.G + (size_t)k * n;
     int32_t* gsup = a.sup + (size_t)k * s;
     float* gxs = a.xs + (size_t)k * s;
-    const qiht_codes Y = a.ydesc[k];
-    const int lm1y = grid_levels(Y.bits, Y.levels) - 1;
     if (tid == 0) {
         sh.alpha1 = (double)(*a.scale1) / (double)a.lm1_1;
         sh.alpha2 = (double)(*a.Q2.scale) / (double)a.Q2.lm1;
         sh.alpha2f = (float)sh.alpha2;
-        sh.alpha_y = (double)(*Y.scale) / (double)lm1y;
     }
     const int nbw = (n + 31) / 32;
     for (int w = tid; w < nbw; w += kST) sm.gbit[w] = 0u;
@@ -461,7 +463,11 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
     }
     mcols<BITS>(a.Q2, sm.sup, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
     double zz = 0.0;
-    for (int i = tid; i < m; i += kST) zz += (double)sm.z[i] * (double)sm.z[i];
+    float* zmu = a.zmu + (size_t)k * m;             // kept for the residual update
+    for (int i = tid; i < m; i += kST) {
+        zz += (double)sm.z[i] * (double)sm.z[i];
+        zmu[i] = sm.z[i];
+    }
     zz = ssum(zz, sh.d);
     if (tid == 0) {
         const double den = sh.alpha2 * sh.alpha2 * zz;
@@ -529,13 +535,35 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
         gsup[q] = sm.sel[q];
         gxs[q] = sm.val[q];
     }
-    // residual r = Q(y) - alpha2 Q2_G' x'
-    mcols<BITS>(a.Q2, sm.sel, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
+    // residual: r - alpha2 Q2 (x' - x) with the product already formed for this step (the
+    // backtracking test's Q2 (x' - x) if G' != G, else mu Q2_G g_G of the step size), or
+    // directly r = Q(y) - alpha2 Q2_G' x' on refresh iterations (periodically and on the last)
     double rr = 0.0;
-    for (int i = tid; i < m; i += kST) {
-        const float ri = fmaf(-sh.alpha2f, sm.z[i], yhat_at(Y, lm1y, sh.alpha_y, i));
-        sm.z[i] = ri;
-        rr += (double)ri * (double)ri;
+    float* rk = a.resid + (size_t)k * m;
+    if (a.refresh) {
+        mcols<BITS>(a.Q2, sm.sel, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
+        const float* yk = a.yhat + (size_t)k * m;
+        for (int i = tid; i < m; i += kST) {
+            const float ri = fmaf(-sh.alpha2f, sm.z[i], __ldg(yk + i));
+            sm.z[i] = ri;
+            rk[i] = ri;
+            rr += (double)ri * (double)ri;
+        }
+    } else if (changed) {
+        for (int i = tid; i < m; i += kST) {
+            const float ri = fmaf(-sh.alpha2f, sm.z[i], rk[i]);
+            sm.z[i] = ri;
+            rk[i] = ri;
+            rr += (double)ri * (double)ri;
+        }
+    } else {
+        const float cz = sh.alpha2f * sh.muf;
+        for (int i = tid; i < m; i += kST) {
+            const float ri = fmaf(-cz, zmu[i], rk[i]);
+            sm.z[i] = ri;
+            rk[i] = ri;
+            rr += (double)ri * (double)ri;
+        }
     }
     rr = ssum(rr, sh.d);
     if (tid == 0) {
@@ -579,6 +607,8 @@ __global__ void __launch_bounds__(kST) k_mrhs_init(MrhsStepArgs a)
     for (int i = tid; i < m; i += kST) {
         const float v = yhat_at(Y, lm1y, sh.alpha_y, i);
         r[i] = v;
+        a.yhat[(size_t)k * m + i] = v;
+        a.resid[(size_t)k * m + i] = v;
         acc += (double)v * (double)v;
     }
     acc = ssum(acc, sh.d);
