@@ -14,11 +14,12 @@
 // Products of an f16 code and an f16 part are exact; the only roundings are the FP32
 // accumulation and the final scaling.
 //
-// Tile: 128 columns of Q (M) x 256 right-hand sides (N), K steps of 32 rows held in a
+// Tile: 256 columns of Q (two MMA tiles of M = 128 sharing every R tile, two accumulators
+// filling the 512 tensor-memory columns) x 256 right-hand sides (N), K steps of 32 rows in a
 // 4-stage ring; operands in shared memory in the K-major layout with 64-byte swizzle.
 // Warp roles: warp 0 loads the R tiles with TMA, warp 1 allocates tensor memory and
-// issues the MMAs (one thread), warps 2..5 expand the codes and, at the end, read the
-// accumulator out of tensor memory. Every wait is bounded by %globaltimer; a timeout
+// issues the MMAs (one thread), warps 2..9 expand the codes (one column of Q each) and,
+// at the end, read the accumulators out of tensor memory. Every wait is bounded by %globaltimer; a timeout
 // records QIHT_ERR_TIMEOUT, stops the CTA's roles, waits for the copies and MMAs it
 // issued and frees its tensor memory before returning.
 #include <cuda.h>
@@ -31,15 +32,17 @@
 namespace qiht {
 namespace {
 
-constexpr int kTM = 128;                       // columns of Q per tile (MMA M)
+constexpr int kTM = 128;                       // columns of Q per MMA tile (MMA M)
+constexpr int kMT = 2;                         // MMA tiles per CTA (they share the R tiles)
 constexpr int kTN = 256;                       // right-hand sides per tile (MMA N)
 constexpr int kTK = 32;                        // rows of Q per stage: 64 bytes of f16
 constexpr int kStages = 4;
-constexpr int kGemmThreads = 192;
-constexpr uint32_t kABytes = kTM * kTK * 2;    // 8 KB
+constexpr int kConvWarps = kMT * 4;            // one thread per column of Q
+constexpr int kGemmThreads = 64 + 32 * kConvWarps;
+constexpr uint32_t kABytes = kTM * kTK * 2;    // 8 KB per MMA tile
 constexpr uint32_t kBBytes = kTN * kTK * 2;    // 16 KB (hi or lo)
-constexpr uint32_t kStageBytes = kABytes + 2 * kBBytes;
-constexpr uint32_t kTmemCols = kTN;            // FP32 accumulator: 128 lanes x 256 columns
+constexpr uint32_t kStageBytes = kMT * kABytes + 2 * kBBytes;
+constexpr uint32_t kTmemCols = kMT * kTN;      // FP32 accumulators: 128 lanes x 512 columns
 constexpr unsigned long long kGemmWaitNs = 250ull * 1000 * 1000;
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B f16, both K-major,
@@ -196,12 +199,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tm = blockIdx.x / a.ntn, tn = blockIdx.x % a.ntn;
-    const int m0 = tm * kTM, n0 = tn * kTN;
+    const int m0 = tm * kTM * kMT, n0 = tn * kTN;
     const int nk = a.nk;
 
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
-            bar_init(&full_a[i], 4);
+            bar_init(&full_a[i], kConvWarps);
             bar_init(&full_b[i], 1);
             bar_init(&empty[i], 1);
         }
@@ -220,8 +223,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     auto stage_a = [&](int s) { return smem + (size_t)s * kStageBytes; };
-    auto stage_bh = [&](int s) { return smem + (size_t)s * kStageBytes + kABytes; };
-    auto stage_bl = [&](int s) { return smem + (size_t)s * kStageBytes + kABytes + kBBytes; };
+    auto stage_bh = [&](int s) { return smem + (size_t)s * kStageBytes + kMT * kABytes; };
+    auto stage_bl = [&](int s) { return smem + (size_t)s * kStageBytes + kMT * kABytes + kBBytes; };
 
     if (warp == 0) {
         // ---- TMA producer of the R tiles (hi and lo parts) ----
@@ -254,9 +257,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
                 const uint32_t ab = s_u32(stage_a(s)), bh = s_u32(stage_bh(s)), bl = s_u32(stage_bl(s));
 #pragma unroll
                 for (int kk = 0; kk < kTK / 16; ++kk) {
-                    const uint64_t ad = sw64_desc(ab + 32 * kk);
-                    mma_f16(tmem, ad, sw64_desc(bh + 32 * kk), (it | kk) != 0);
-                    mma_f16(tmem, ad, sw64_desc(bl + 32 * kk), 1u);
+                    const uint64_t bhd = sw64_desc(bh + 32 * kk), bld = sw64_desc(bl + 32 * kk);
+#pragma unroll
+                    for (int t = 0; t < kMT; ++t) {
+                        const uint64_t ad = sw64_desc(ab + t * kABytes + 32 * kk);
+                        mma_f16(tmem + (uint32_t)(t * kTN), ad, bhd, (it | kk) != 0);
+                        mma_f16(tmem + (uint32_t)(t * kTN), ad, bld, 1u);
+                    }
                 }
                 mma_commit(&empty[s]);
             }
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
         __syncwarp();
     } else {
         // ---- converters (A tiles), then the epilogue ----
-        const int ct = tid - 64;               // row of the A tile = column m0 + ct of Q
+        const int ct = tid - 64;               // column m0 + ct of Q: row ct % 128 of A tile ct / 128
         const int j = m0 + ct;
         const bool colok = j < a.Q.cols;
         const uint32_t* col = a.Q.words + (size_t)(colok ? j : 0) * a.Q.ld;
@@ -318,26 +325,26 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
                     codes4_to_h2(plane, two, m2048, lm1h, h[k / 2], h[k / 2 + 1]);
                 }
             }
-            unsigned char* A = stage_a(s);
-            const int sw = (ct >> 1) & 3;
+            unsigned char* A = stage_a(s) + (ct / kTM) * kABytes;
+            const int row = ct % kTM, sw = (row >> 1) & 3;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                *reinterpret_cast<uint4*>(A + ct * 64 + ((c ^ sw) << 4)) =
+                *reinterpret_cast<uint4*>(A + row * 64 + ((c ^ sw) << 4)) =
                     make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(&full_a[s]);
         }
-        // ---- epilogue: accumulator rows of this warp's lane quarter ----
+        // ---- epilogue: the rows of this warp's lane quarter of accumulator (warp - 2) / 4 ----
         const bool fin = __all_sync(0xffffffffu, bar_drain(&done, 0u));
         tc_fence_after();
         if (__all_sync(0xffffffffu, fin && !s_abort)) {
-            const int quarter = warp & 3;
+            const int quarter = warp & 3, t = (warp - 2) / 4;
             const int row = 32 * quarter + lane;
-            const int jj = m0 + row;
+            const int jj = m0 + t * kTM + row;
             for (int c0 = 0; c0 < kTN; c0 += 16) {
                 uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
+                tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * kTN + c0), v);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int k = n0 + c0 + i;
@@ -445,7 +452,7 @@ cudaError_t launch_mrhs_gemm(const Codes& Q, const void* map, const float* sc, f
     a.ntn = mrhs_pad_rhs(nrhs) / kTN;
     a.rhi = mrhs_pad_rhs(nrhs);
     a.status = status;
-    const int ntm = (Q.cols + kTM - 1) / kTM;
+    const int ntm = (Q.cols + kTM * kMT - 1) / (kTM * kMT);
     const size_t smem = mrhs_gemm_smem();
     void* fn = Q.bits == 8 ? (void*)k_mrhs_gemm<8> : Q.bits == 4 ? (void*)k_mrhs_gemm<4> : (void*)k_mrhs_gemm<2>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
