@@ -12,7 +12,8 @@ Functions mirror the paper's steps:
   quantize / dequantize          Q(v, b) of Section III-A, and its value c * q_code
   gemv_t, gemv_cols              plain FP64 products
   top_s                          hard threshold H_s (Eq. NIHT)
-  niht                           Algorithm 2 (Algorithm 1 when both matrices are Phi)
+  niht, niht_seq                 Algorithm 2 (Algorithm 1 when both matrices are Phi); niht_seq
+                                 with one realization per iteration (qiht_fresh)
 """
 from __future__ import annotations
 
@@ -95,6 +96,9 @@ def lib():
                               ctypes.POINTER(_Params), P, P, ctypes.POINTER(_Trace),
                               ctypes.POINTER(_Report)]
         L.qo_niht.restype = ctypes.c_int
+        L.qo_niht_seq.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.POINTER(_Params), P, P, ctypes.POINTER(_Trace), ctypes.POINTER(_Report)]
+        L.qo_niht_seq.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -209,9 +213,19 @@ def niht(A1: np.ndarray, A2: np.ndarray, y: np.ndarray, s: int, iters: int, *, k
 
     trace=True records supports, gaps, step sizes and residuals per iteration;
     trace="x" also records every iterate."""
-    A1 = np.ascontiguousarray(A1, dtype=np.float64)
-    A2 = A1 if A2 is A1 else np.ascontiguousarray(A2, dtype=np.float64)
-    y = np.ascontiguousarray(y, dtype=np.float64)
+    return niht_seq([A1], [A2], [y], s, iters, k=k, c=c, max_backtrack=max_backtrack, trace=trace)
+
+
+def niht_seq(A1s: list, A2s: list, ys: list, s: int, iters: int, *, k: float = 2.0, c: float = 0.01,
+             max_backtrack: int = 32, trace: bool | str = False) -> NihtResult:
+    """Algorithm 2 with one realization per iteration: iteration t (1..iters) uses A1s[t], A2s[t],
+    ys[t]; index 0 gives the initial support. Lists of length 1 repeat their one entry."""
+    def full(lst):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in lst]
+        return arrs if len(arrs) > 1 else arrs * (iters + 1)
+    A1l, A2l, yl = full(A1s), full(A2s), full(ys)
+    assert len(A1l) == len(A2l) == len(yl) == iters + 1
+    A1 = A1l[0]
     m, n = A1.shape
     x = np.zeros(n, dtype=np.float64)
     sup = np.zeros(s, dtype=np.int32)
@@ -226,14 +240,49 @@ def niht(A1: np.ndarray, A2: np.ndarray, y: np.ndarray, s: int, iters: int, *, k
                   "min_margin": np.zeros(T), "resid2": np.zeros(T),
                   "x": np.zeros((T, n)) if trace == "x" else None}
         tr = _Trace(*[_ptr(arrays[f]) if arrays[f] is not None else None for f, _ in _Trace._fields_])
-    lib().qo_niht(_ptr(A1), _ptr(A2), _ptr(y), m, n, s, iters, ctypes.byref(p), _ptr(x), _ptr(sup),
-                  ctypes.byref(tr) if tr is not None else None, ctypes.byref(rep))
+    ptrs = [(ctypes.c_void_p * (iters + 1))(*[_ptr(a) for a in lst]) for lst in (A1l, A2l, yl)]
+    lib().qo_niht_seq(ptrs[0], ptrs[1], ptrs[2], m, n, s, iters, ctypes.byref(p), _ptr(x), _ptr(sup),
+                      ctypes.byref(tr) if tr is not None else None, ctypes.byref(rep))
     if arrays is not None:
         T = rep.iters_run + 1
         arrays = {kk: vv[:T] for kk, vv in arrays.items() if vv is not None}
     return NihtResult(x=x, support=sup, status=rep.status, iters_run=rep.iters_run,
                       backtracks=rep.backtracks, support_changes=rep.support_changes,
                       resid_norm2=rep.resid_norm2, mu=rep.mu, trace=arrays)
+
+
+def phi_stream(k: int) -> int:
+    """Random-number stream of the k-th realization of Q(Phi) (k = 1, 2, ...): 0 and 1 for the
+    first two (the fixed quantizations Q1, Q2), then 0x1000 + k."""
+    return k - 1 if k <= 2 else 0x1000 + k
+
+
+def y_stream(t: int) -> int:
+    """Stream of the t-th realization of Q(y) (t = 1, 2, ...): 2 for the first, then 0x2000 + t."""
+    return 2 if t == 1 else 0x2000 + t
+
+
+def qiht_fresh(phi: np.ndarray, y: np.ndarray, s: int, iters: int, *, bits_phi: int, bits_y: int,
+               seed: int, odd: bool = False, **kw):
+    """Algorithm 2 as written: iteration t uses fresh realizations Phi-hat_{2t-1} (gradient),
+    Phi-hat_{2t} (A2 x, step size, backtracking test) and y-hat_t; the initial support comes
+    from Phi-hat_1 and y-hat_1. Realization k of Q(Phi) uses stream phi_stream(k), realization t
+    of Q(y) stream y_stream(t); every realization of Phi shares the scale max |Phi|."""
+    _, sphi = quantize(phi, bits_phi, seed, 0, odd=odd)
+    _, sy = quantize(y, bits_y, seed, 2, odd=odd)
+
+    def dphi(k):
+        cds, _ = quantize(phi, bits_phi, seed, phi_stream(k), sphi, odd=odd)
+        return dequantize(cds, bits_phi, sphi, odd=odd)
+
+    def dy(t):
+        cds, _ = quantize(y, bits_y, seed, y_stream(t), sy, odd=odd)
+        return dequantize(cds, bits_y, sy, odd=odd)
+
+    A1s = [dphi(1)] + [dphi(2 * t - 1) for t in range(1, iters + 1)]
+    A2s = [dphi(2)] + [dphi(2 * t) for t in range(1, iters + 1)]
+    ys = [dy(1)] + [dy(t) for t in range(1, iters + 1)]
+    return niht_seq(A1s, A2s, ys, s, iters, **kw), {"scale_phi": sphi, "scale_y": sy}
 
 
 def qiht(phi: np.ndarray, y: np.ndarray, s: int, iters: int, *, bits_phi: int, bits_y: int,

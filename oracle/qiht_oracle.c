@@ -276,13 +276,19 @@ static double qo_resid2(const double* A2, const double* y, int32_t m, int32_t n,
     return acc;
 }
 
-/* A1, A2: m x n row-major (the two dequantised matrices, or Phi twice).
- * y: m. x: n (output, s-sparse). support: s (output, ascending).
- * Returns a status code; rep is filled in any case. */
-int qo_niht(const double* A1, const double* A2, const double* y, int32_t m, int32_t n, int32_t s,
-            int32_t iters, const qo_params* p, double* x, int32_t* support, qo_trace* tr,
-            qo_report* rep)
+/* Algorithm 2 with one realization of the matrices and observation per iteration:
+ * A1s[t], A2s[t], ys[t] (t = 1..iters) are the matrices of iteration t (Phi-hat_{2t-1} for the
+ * gradient, Phi-hat_{2t} for A2 x, the step size and the backtracking test) and its
+ * observation y-hat_t; A1s[0], ys[0] give the initial support. Each A is m x n row-major.
+ * x: n (output, s-sparse). support: s (output, ascending). The residual recorded after
+ * iteration t is ||ys[t] - A2s[t] x||^2. Returns a status code; rep is filled in any case. */
+int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double* const* ys, int32_t m,
+                int32_t n, int32_t s, int32_t iters, const qo_params* p, double* x, int32_t* support,
+                qo_trace* tr, qo_report* rep)
 {
+    const double* A1 = A1s[0];
+    const double* A2 = A2s[0];
+    const double* y = ys[0];
     memset(rep, 0, sizeof(*rep));
     if (m <= 0 || n <= 0 || s <= 0 || s > n || s > m || iters < 0) {
         rep->status = QO_ERR_ARG;
@@ -318,6 +324,9 @@ int qo_niht(const double* A1, const double* A2, const double* y, int32_t m, int3
 
     int32_t t;
     for (t = 1; t <= iters; ++t) {
+        A1 = A1s[t];
+        A2 = A2s[t];
+        y = ys[t];
         /* g = A1^T (y - A2 x) */
         for (int32_t q = 0; q < s; ++q) coef[q] = x[support[q]];
         qo_gemv_cols(A2, m, n, support, coef, s, z);
@@ -405,4 +414,20 @@ int qo_niht(const double* A1, const double* A2, const double* y, int32_t m, int3
 
     free(g); free(a); free(r); free(z); free(xn); free(coef); free(uni); free(sel); free(work);
     return status;
+}
+
+/* A1, A2: m x n row-major (the two dequantised matrices, or Phi twice), the same in every
+ * iteration; y: m. Arguments and results as for qo_niht_seq. */
+int qo_niht(const double* A1, const double* A2, const double* y, int32_t m, int32_t n, int32_t s,
+            int32_t iters, const qo_params* p, double* x, int32_t* support, qo_trace* tr,
+            qo_report* rep)
+{
+    const int32_t cnt = (iters > 0 ? iters : 0) + 1;
+    const double** a1 = (const double**)malloc(sizeof(double*) * (size_t)cnt);
+    const double** a2 = (const double**)malloc(sizeof(double*) * (size_t)cnt);
+    const double** yy = (const double**)malloc(sizeof(double*) * (size_t)cnt);
+    for (int32_t t = 0; t < cnt; ++t) { a1[t] = A1; a2[t] = A2; yy[t] = y; }
+    const int st = qo_niht_seq(a1, a2, yy, m, n, s, iters, p, x, support, tr, rep);
+    free(a1); free(a2); free(yy);
+    return st;
 }

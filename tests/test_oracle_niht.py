@@ -253,3 +253,60 @@ def test_gradient_uses_first_matrix_and_step_uses_second():
     two = oracle.niht(2.0 * A2, A2, y, 5, 1)
     assert np.array_equal(one.support, two.support)
     assert np.array_equal(2.0 * one.x, two.x)
+
+
+# ---- fresh realizations per iteration (Algorithm 2 as written: 2n* matrices, n* observations) ----
+
+def test_fresh_realizations_are_distinct_streams():
+    T = 400
+    phis = [oracle.phi_stream(k) for k in range(1, 2 * T + 1)]
+    ys = [oracle.y_stream(t) for t in range(1, T + 1)]
+    assert phis[:2] == [0, 1] and ys[0] == 2          # the first realizations are the fixed ones
+    assert len(set(phis)) == len(phis) and len(set(ys)) == len(ys)
+    assert not set(phis) & set(ys)
+
+
+def test_fresh_gradient_is_unbiased_over_iterations():
+    # one seed, the gradients Phi-hat_{2t-1}^T (y-hat_t - Phi-hat_{2t} x) of iterations t = 1..T at a
+    # fixed x are independent draws whose mean is Phi^T (y - Phi x) (the double-sampling identity
+    # stated before Algorithm 2)
+    p = synth.gaussian(24, 32, 3, seed=5, snr_db=20.0)
+    phi = p.phi.astype(np.float64)
+    x = p.x_true * 0.6
+    exact = phi.T @ (p.y.astype(np.float64) - phi @ x)
+    bits, seed = 2, 77
+    _, sphi = oracle.quantize(p.phi, bits, seed, 0)
+    _, sy = oracle.quantize(p.y, bits, seed, 2)
+    draws = []
+    for t in range(1, 1201):
+        c1, _ = oracle.quantize(p.phi, bits, seed, oracle.phi_stream(2 * t - 1), sphi)
+        c2, _ = oracle.quantize(p.phi, bits, seed, oracle.phi_stream(2 * t), sphi)
+        cy, _ = oracle.quantize(p.y, bits, seed, oracle.y_stream(t), sy)
+        A1, A2 = oracle.dequantize(c1, bits, sphi), oracle.dequantize(c2, bits, sphi)
+        draws.append(oracle.gemv_t(A1, oracle.dequantize(cy, bits, sy) - A2 @ x))
+    draws = np.array(draws)
+    z = np.abs(draws.mean(axis=0) - exact) / (draws.std(axis=0, ddof=1) / np.sqrt(len(draws)))
+    assert np.max(z) < 5.0, np.max(z)
+
+
+def test_fresh_first_iteration_is_the_fixed_one():
+    # iteration 1 uses Phi-hat_1, Phi-hat_2 and y-hat_1 in both modes
+    p = synth.gaussian(96, 384, 6, seed=12, snr_db=25.0)
+    fx, _ = oracle.qiht(p.phi, p.y, p.s, 1, bits_phi=4, bits_y=4, seed=3, trace=True)
+    fr, _ = oracle.qiht_fresh(p.phi, p.y, p.s, 1, bits_phi=4, bits_y=4, seed=3, trace=True)
+    assert np.array_equal(fx.trace["support"], fr.trace["support"])
+    assert np.array_equal(fx.x, fr.x) and fx.trace["mu"][1] == fr.trace["mu"][1]
+    # and later iterations draw new realizations
+    fx, _ = oracle.qiht(p.phi, p.y, p.s, 6, bits_phi=4, bits_y=4, seed=3, trace=True)
+    fr, _ = oracle.qiht_fresh(p.phi, p.y, p.s, 6, bits_phi=4, bits_y=4, seed=3, trace=True)
+    assert not np.array_equal(fx.trace["resid2"][2:], fr.trace["resid2"][2:])
+
+
+def test_fresh_noiseless_recovers_and_approaches_niht_with_many_bits():
+    p = synth.gaussian(128, 512, 8, seed=4)
+    res, _ = oracle.qiht_fresh(p.phi, p.y, 8, 80, bits_phi=8, bits_y=8, seed=1)
+    assert res.status == oracle.OK and np.array_equal(res.support, p.support)
+    assert np.linalg.norm(res.x - p.x_true) / np.linalg.norm(p.x_true) < 0.05
+    ref = oracle.niht(p.phi, p.phi, p.y, 8, 60)
+    r16, _ = oracle.qiht_fresh(p.phi, p.y, 8, 60, bits_phi=16, bits_y=16, seed=2)
+    assert np.linalg.norm(r16.x - ref.x) / np.linalg.norm(ref.x) < 1e-3
