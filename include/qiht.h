@@ -264,6 +264,33 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
 void qiht_clear_graph_cache(void);
 
 /* ---------------------------------------------------------------------- */
+/* Fresh realizations per iteration (Algorithm 2 as written: 2 n* matrix    */
+/* realizations and n* observation realizations)                           */
+/* ---------------------------------------------------------------------- */
+
+/* Workspace bytes for qiht_niht_solve_fresh (0 if a size is out of range). */
+size_t qiht_solve_fresh_workspace_size(int32_t m, int32_t n, int32_t s, int32_t bits_phi, int32_t bits_y);
+
+/* Algorithm 2 with a new quantization of Phi and y in every iteration: iteration t
+ * (1..iters) forms g = Phi-hat_{2t-1}^T (y-hat_t - Phi-hat_{2t} x), the step size and the
+ * backtracking test with Phi-hat_{2t}, and records ||y-hat_t - Phi-hat_{2t} x||^2; the initial
+ * support comes from Phi-hat_1^T y-hat_1. Realization k of Q(Phi) uses random-number stream
+ * (k <= 2 ? k - 1 : 0x1000 + k), realization t of Q(y) stream (t == 1 ? 2 : 0x2000 + t), all with
+ * `seed` and the scales max |Phi|, max |y| (so iteration 1 equals qiht_niht_solve's on the
+ * quantizations with streams 0, 1, 2). phi [device] m x n row-major (row stride ld_phi
+ * >= n floats), y [device] m floats; quant_flags 0 or QIHT_ODD_LEVELS. Outputs and
+ * params as for qiht_niht_solve (params->flags must be 0). Every iteration re-quantizes
+ * Phi twice (one pass over the FP32 matrix) and y, then runs the iteration as separate
+ * kernels; the host reads the solver state after every iteration and backtracking test,
+ * so the call returns when the solve is done (the stream is synchronised). Requires
+ * m <= 16384, n <= 49152. */
+qiht_status qiht_niht_solve_fresh(const float* phi, int64_t ld_phi, const float* y, int32_t m, int32_t n,
+                                  int32_t bits_phi, int32_t bits_y, uint64_t seed, int32_t quant_flags, int32_t s,
+                                  int32_t iters, const qiht_params* params, float* x, int32_t* support,
+                                  qiht_report* report, const qiht_trace* trace, void* workspace,
+                                  size_t workspace_bytes, qiht_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Many independent problems in one launch (the batched workload of the    */
 /* solver: Algorithm 2 applied to each problem separately)                  */
 /* ---------------------------------------------------------------------- */

@@ -81,7 +81,7 @@ EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
            "qiht_clear_graph_cache", "qiht_solve_batched_workspace_size", "qiht_niht_solve_batched",
            "qiht_gemv_t_multi_workspace_size", "qiht_gemv_t_multi", "qiht_solve_multi_workspace_size",
-           "qiht_niht_solve_multi"]
+           "qiht_niht_solve_multi", "qiht_solve_fresh_workspace_size", "qiht_niht_solve_fresh"]
 
 _lib = None
 
@@ -119,6 +119,9 @@ def lib():
             "qiht_gemv_t_multi_workspace_size": ([I32, I32], SZ),
             "qiht_gemv_t_multi": ([ctypes.POINTER(_Codes), P, I64, I32, P, I64, P, P, SZ, P], I32),
             "qiht_solve_multi_workspace_size": ([I32, I32, I32, I32], SZ),
+            "qiht_solve_fresh_workspace_size": ([I32, I32, I32, I32, I32], SZ),
+            "qiht_niht_solve_fresh": ([P, I64, P, I32, I32, I32, I32, U64, I32, I32, I32, ctypes.POINTER(_Params),
+                                       P, P, P, ctypes.POINTER(_Trace), P, SZ, P], I32),
             "qiht_niht_solve_multi": ([ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), I32,
                                        I32, I32, ctypes.POINTER(_Params), P, P, P, P, SZ, P], I32),
         }
@@ -356,6 +359,30 @@ def niht_solve(Q1: Codes, Q2: Codes, y: Codes, s: int, iters: int, *, trace: boo
     """One QIHT solve (Algorithm 2). Returns the Solver holding x, support, report (and trace)."""
     sv = Solver(Q1.rows, Q1.cols, s, iters, device=Q1.words.device, trace=trace, **kw)
     return sv(Q1, Q2, y, stream=stream)
+
+
+def niht_solve_fresh(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: int, seed: int, s: int, iters: int,
+                     *, odd: bool = False, trace: bool = False, k: float = 2.0, c: float = 0.01,
+                     max_backtrack: int = 32, stream=None) -> Solver:
+    """qiht_niht_solve_fresh: Algorithm 2 with new quantizations of Phi and y in every iteration.
+    Returns a Solver-like object holding x, support, report (and trace)."""
+    assert phi.is_cuda and phi.dtype == torch.float32 and phi.dim() == 2 and phi.stride(1) == 1
+    m, n = phi.shape
+    sv = Solver(m, n, s, iters, device=phi.device, trace=trace, k=k, c=c, max_backtrack=max_backtrack)
+    ws = _ws(lib().qiht_solve_fresh_workspace_size(m, n, s, bits_phi, bits_y), phi.device)
+    tr = None
+    if sv.trace is not None:
+        t = sv.trace
+        tr = _Trace(t["support"].data_ptr(), t["kth"].data_ptr(), t["mu"].data_ptr(), t["bt"].data_ptr(),
+                    t["resid2"].data_ptr())
+    st = lib().qiht_niht_solve_fresh(phi.data_ptr(), phi.stride(0), y.data_ptr(), m, n, bits_phi, bits_y,
+                                     seed & (2**64 - 1), ODD_LEVELS if odd else 0, s, iters, ctypes.byref(sv.params),
+                                     sv.x.data_ptr(), sv.support.data_ptr(), sv.report.data_ptr(),
+                                     ctypes.byref(tr) if tr is not None else None, ws.data_ptr(), ws.numel(),
+                                     _stream(stream))
+    _check(st, "qiht_niht_solve_fresh")
+    sv.workspace = ws
+    return sv
 
 
 BATCH_MAX_ROWS, BATCH_MAX_COLS, BATCH_MAX_S = 2048, 8192, 256

@@ -372,6 +372,45 @@ void gather_node(const GatherArgs& a, cudaKernelNodeParams* p, void** argbuf)
     p->extra = nullptr;
 }
 
+// Residual of a fresh realization: the observation codes Y (one column) are dequantized
+// into yhat, r = yhat - z with z = alpha Q2_G x_G already formed, and max |r| is folded into
+// *rmax_bits (reset by the caller) for the next gradient product.
+__global__ void __launch_bounds__(256) k_fresh_resid(Codes Y, const float* __restrict__ z, float* __restrict__ yhat,
+                                                     float* __restrict__ r, int m, unsigned* rmax_bits)
+{
+    __shared__ unsigned wmax[8];
+    const int Gy = 32 / Y.bits;
+    const double alpha_y = (double)(*Y.scale) / (double)Y.lm1;
+    unsigned mx = 0;
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < m; i += gridDim.x * 256) {
+        const uint32_t w = __ldg(Y.words + i / Gy);
+        const int k = i % Gy;
+        const int code = (int)((w >> (8 * (k & 3) + Y.bits * (k >> 2))) & ((1u << Y.bits) - 1));
+        const float v = (float)(alpha_y * (double)(2 * code - Y.lm1));
+        yhat[i] = v;
+        const float ri = v - z[i];
+        r[i] = ri;
+        mx = max(mx, __float_as_uint(ri) & 0x7fffffffu);
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned b = 0;
+        for (int w = 0; w < 8; ++w) b = max(b, wmax[w]);
+        atomicMax(rmax_bits, b);
+    }
+}
+
+cudaError_t launch_fresh_resid(const Codes& Y, const float* z, float* yhat, float* r, int m, unsigned* rmax_bits,
+                               cudaStream_t s)
+{
+    int blocks = (m + 255) / 256;
+    if (blocks > 152) blocks = 152;
+    k_fresh_resid<<<blocks, 256, 0, s>>>(Y, z, yhat, r, m, rmax_bits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
 {
     cudaKernelNodeParams p{};

@@ -237,6 +237,8 @@ cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int
                             int levels = 0);
 cudaError_t launch_gemv_t(const GemvTArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+cudaError_t launch_fresh_resid(const Codes& Y, const float* z, float* yhat, float* r, int m, unsigned* rmax_bits,
+                               cudaStream_t s);
 cudaError_t launch_top(const TopArgs& a, cudaStream_t s);
 
 // One iteration after the gradient product as one persistent kernel (iter.cu).

@@ -501,7 +501,8 @@ struct SolveKernels {
 
 static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* Y, int s,
                          int iters, const qiht_params* prm, float* x, int32_t* support, qiht_report* report,
-                         const qiht_trace* trace, char* ws, unsigned long long h_outer, unsigned long long h_bt)
+                         const qiht_trace* trace, char* ws, unsigned long long h_outer, unsigned long long h_bt,
+                         bool force_multi = false)
 {
     const int m = Q1->rows, n = Q1->cols;
     const Plan pl = plan_solve(m, n, s);
@@ -521,7 +522,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     qiht_trace tr{};
     if (trace) tr = *trace;
     const int nsm = num_sms();
-    const bool fast = !multi_kernel_iteration() && iter_fast(s);
+    const bool fast = !force_multi && !multi_kernel_iteration() && iter_fast(s);
     IterFastBufs fb{};
     if (fast) {
         fb.pos = reinterpret_cast<int32_t*>(ws + pl.off_pos);
@@ -909,6 +910,130 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
         }
     }
     CK(cudaGraphLaunch(exec, reinterpret_cast<cudaStream_t>(stream)));
+    return QIHT_OK;
+}
+
+// ---- fresh realizations per iteration (Algorithm 2 as written) ----
+
+static int phi_stream(int k) { return k <= 2 ? k - 1 : 0x1000 + k; }
+static int y_stream(int t) { return t == 1 ? 2 : 0x2000 + t; }
+
+struct FreshLayout {
+    size_t solve, q1, q2, qy, scales, z, total;
+};
+
+static FreshLayout fresh_layout(int m, int n, int s, int bits_phi, int bits_y)
+{
+    FreshLayout L{};
+    size_t o = 0;
+    L.solve = o; o += align256(plan_solve(m, n, s).total);
+    const size_t wq = (size_t)n * qiht_ld_words(m, bits_phi) * 4;
+    L.q1 = o; o += align256(wq);
+    L.q2 = o; o += align256(wq);
+    L.qy = o; o += align256((size_t)qiht_ld_words(m, bits_y) * 4);
+    L.scales = o; o += 256;
+    L.z = o; o += align256((size_t)qiht_ld_words(m, 2) * 16 * 4);
+    L.total = o;
+    return L;
+}
+
+size_t qiht_solve_fresh_workspace_size(int32_t m, int32_t n, int32_t s, int32_t bits_phi, int32_t bits_y)
+{
+    if (m < 1 || n < 1 || s < 1 || s > m || s > n || !bits_ok(bits_phi) || !bits_ok(bits_y)) return 0;
+    return fresh_layout(m, n, s, bits_phi, bits_y).total;
+}
+
+qiht_status qiht_niht_solve_fresh(const float* phi, int64_t ld_phi, const float* y, int32_t m, int32_t n,
+                                  int32_t bits_phi, int32_t bits_y, uint64_t seed, int32_t quant_flags, int32_t s,
+                                  int32_t iters, const qiht_params* params, float* x, int32_t* support,
+                                  qiht_report* report, const qiht_trace* trace, void* workspace,
+                                  size_t workspace_bytes, qiht_stream_t stream)
+{
+    if (!bits_ok(bits_phi) || !bits_ok(bits_y)) return QIHT_ERR_BITS;
+    if (!phi || !y || !x || !support || !report || m < 1 || n < 1 || ld_phi < n) return QIHT_ERR_ARG;
+    if (s < 1 || s > m || s > n || iters < 0 || m > kMaxRows || n > kMaxTopN) return QIHT_ERR_ARG;
+    if (quant_flags & ~QIHT_ODD_LEVELS) return QIHT_ERR_ARG;
+    qiht_params prm{2.0, 0.01, 32, 0};
+    if (params) prm = *params;
+    if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.flags != 0)
+        return QIHT_ERR_ARG;
+    const FreshLayout L = fresh_layout(m, n, s, bits_phi, bits_y);
+    if (!workspace || workspace_bytes < L.total || !aligned(workspace, 256)) return QIHT_ERR_WORKSPACE;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    char* w = reinterpret_cast<char*>(workspace);
+    uint32_t* w1 = reinterpret_cast<uint32_t*>(w + L.q1);
+    uint32_t* w2 = reinterpret_cast<uint32_t*>(w + L.q2);
+    uint32_t* wy = reinterpret_cast<uint32_t*>(w + L.qy);
+    float* sc = reinterpret_cast<float*>(w + L.scales);          // [0] max |Phi|, [1] max |y|
+    float* z = reinterpret_cast<float*>(w + L.z);
+    const bool odd = (quant_flags & QIHT_ODD_LEVELS) != 0;
+    const int lev_phi = odd ? (1 << (bits_phi - 1)) + 1 : (1 << bits_phi);
+    const int lev_y = odd ? (1 << (bits_y - 1)) + 1 : (1 << bits_y);
+    const int ldp = qiht_ld_words(m, bits_phi), ldy = qiht_ld_words(m, bits_y);
+    const qiht_codes q1{w1, sc, m, n, bits_phi, ldp, lev_phi, 0};
+    const qiht_codes q2{w2, sc, m, n, bits_phi, ldp, lev_phi, 0};
+    const qiht_codes qy{wy, sc + 1, m, 1, bits_y, ldy, lev_y, 0};
+    auto quantize_iteration = [&](int t) -> cudaError_t {
+        cudaError_t e = launch_quantize(phi, m, n, ld_phi, bits_phi, seed, (uint32_t)phi_stream(2 * t - 1), w1, ldp,
+                                        sc, cs, (uint32_t)phi_stream(2 * t), w2, lev_phi);
+        if (e != cudaSuccess) return e;
+        return launch_quantize(y, m, 1, 1, bits_y, seed, (uint32_t)y_stream(t), wy, ldy, sc + 1, cs, 0, nullptr,
+                               lev_y);
+    };
+    CK(launch_absmax(phi, m, n, ld_phi, sc, cs));
+    CK(launch_absmax(y, m, 1, 1, sc + 1, cs));
+    CK(quantize_iteration(1));
+
+    char* ws = w + L.solve;
+    SolveKernels K;
+    make_kernels(K, &q1, &q2, &qy, s, iters, &prm, x, support, report, trace, ws, 0, 0, true);
+    const Plan pl = plan_solve(m, n, s);
+    GatherArgs ga{};
+    ga.Q = view(&q2);
+    ga.cols = support;                   // the committed support and the values on it
+    ga.coef = reinterpret_cast<const float*>(ws + pl.off_val);
+    ga.count = s;
+    ga.z = z;
+    ga.partial = reinterpret_cast<float*>(ws + pl.off_partial);
+    ga.rb_partial = reinterpret_cast<double*>(ws + pl.off_rbp);
+    ga.counters = K.st->counters[1];
+    ga.mode = kGatherPlain;
+    CK(cudaMemsetAsync(ga.counters, 0, sizeof(unsigned) * 1024, cs));
+    float* yhat = reinterpret_cast<float*>(ws + pl.off_yhat);
+    float* r = reinterpret_cast<float*>(ws + pl.off_r);
+
+    State h{};
+    auto read_state = [&]() -> bool {
+        if (cudaMemcpyAsync(&h, K.st, sizeof(State), cudaMemcpyDeviceToHost, cs) != cudaSuccess) return false;
+        return cudaStreamSynchronize(cs) == cudaSuccess;
+    };
+    CK(launch_node(K.p_init, cs));
+    CK(launch_node(K.p_g0, cs));
+    CK(launch_node(K.p_t0, cs));
+    if (!read_state()) return QIHT_ERR_CUDA;
+    for (int t = 1; t <= iters && !h.stop; ++t) {
+        if (t >= 2) {
+            // this iteration's realizations, its residual y-hat_t - Phi-hat_{2t} x, the gradient
+            CK(quantize_iteration(t));
+            CK(launch_gather(ga, cs));
+            CK(cudaMemsetAsync(&K.st->rmax_bits, 0, sizeof(unsigned), cs));
+            CK(launch_fresh_resid(view(&qy), z, yhat, r, m, &K.st->rmax_bits, cs));
+            CK(launch_node(K.p_gb, cs));
+        }
+        CK(launch_node(K.p_mu, cs));
+        CK(launch_node(K.p_tf, cs));
+        CK(launch_node(K.p_tt, cs));
+        CK(launch_node(K.p_om, cs));
+        if (!read_state()) return QIHT_ERR_CUDA;
+        for (int b = 0; b <= prm.max_backtrack && h.again && !h.stop; ++b) {
+            CK(launch_node(K.p_tf, cs));
+            CK(launch_node(K.p_tt, cs));
+            CK(launch_node(K.p_om, cs));
+            if (!read_state()) return QIHT_ERR_CUDA;
+        }
+        CK(launch_node(K.p_re, cs));
+        if (!read_state()) return QIHT_ERR_CUDA;
+    }
     return QIHT_OK;
 }
 
