@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gemv-launches", type=int, default=200)
-    ap.add_argument("--workload", choices=["single", "batched", "multi"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "multi", "fresh"], default="single",
                     help="single: the large single solve (default); batched: 512 independent problems in one "
                          "launch; multi: 1024 right-hand sides sharing the large matrix (tensor-core gradient)")
     ap.add_argument("--nprob", type=int, default=512)
@@ -611,6 +611,61 @@ def run_multi(args):
     print(json.dumps(line))
 
 
+def run_fresh(args):
+    """The large single solve with fresh realizations of Q(Phi) and Q(y) in every iteration
+    (Algorithm 2 as written): 8192 x 32768, s = 256, 30 dB, 8-bit, --iters iterations (default
+    here 60). value = iterations/s of qiht_niht_solve_fresh (Phi resident in HBM; every iteration
+    re-quantizes it twice). The fixed-quantization solve of the same problem is timed beside it."""
+    import torch
+
+    import paper_1802_04907_gb300 as q
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    m, n, s, bits = args.m, args.n, args.s, args.bits
+    iters = args.iters if args.iters != ITERS else 60
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(99)
+    phi = torch.randn(m, n, generator=gen, device=dev, dtype=torch.float32) / float(np.sqrt(m))
+    sup = torch.randperm(n, generator=gen, device=dev)[:s]
+    xt = torch.zeros(n, device=dev)
+    xt[sup] = (torch.rand(s, generator=gen, device=dev) + 0.5) * torch.sign(torch.randn(s, generator=gen, device=dev))
+    yc = phi @ xt
+    y = yc + torch.sqrt((yc.double() ** 2).sum() / (m * 1e3)).float() * torch.randn(m, generator=gen, device=dev)
+    for _ in range(max(1, args.warmup)):
+        sv = q.niht_solve_fresh(phi, y, bits, bits, 5, s, iters)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        sv = q.niht_solve_fresh(phi, y, bits, bits, 5, s, iters)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    rep = sv.read_report()
+    err = float(torch.linalg.norm(sv.x - xt) / torch.linalg.norm(xt))
+    q1, q2, qy = q.quantize_problem(phi, y, bits, bits, 5)
+    fx = q.Solver(m, n, s, iters, device=dev)
+    fx(q1, q2, qy)
+    torch.cuda.synchronize()
+    ev0.record()
+    fx(q1, q2, qy)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_fx = ev0.elapsed_time(ev1)
+    err_fx = float(torch.linalg.norm(fx.x - xt) / torch.linalg.norm(xt))
+    line = {"metric": "NIHT iterations/s (fresh realizations)", "value": rep.iters_run / (ms / 1e3),
+            "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"u{bits}",
+            "data": "synthetic",
+            "config": {"workload": f"single solve {m}x{n}, s={s}, +-U(0.5,1.5), 30 dB, {bits}-bit, {iters} iterations, "
+                                   "fresh Q(Phi) x2 and Q(y) per iteration",
+                       "l2": "inputs larger than L2: Phi FP32 1 GiB read by every re-quantization"},
+            "ms_per_iteration": ms / max(1, rep.iters_run),
+            "fixed_quantizations": {"iterations_per_s": iters / (ms_fx / 1e3), "rel_err": err_fx},
+            "rel_err": err, "status": rep.status, "gpu_launches": None}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -619,6 +674,8 @@ def main():
         run_batched(args)
     elif args.workload == "multi":
         run_multi(args)
+    elif args.workload == "fresh":
+        run_fresh(args)
     else:
         run_ours(args)
 

@@ -355,6 +355,37 @@ qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, co
                                   int32_t* support, qiht_report* reports, void* workspace, size_t workspace_bytes,
                                   qiht_stream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* K unrolled iterations and their adjoint (calibration of a per-row gain)   */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of workspace for qiht_unrolled_forward / _backward (0 if a size is out of range). */
+size_t qiht_unrolled_workspace_size(int32_t nprob, int32_t m, int32_t n, int32_t s, int32_t K);
+
+/* K iterations of Algorithm 2 without the backtracking test, for nprob problems sharing m,
+ * n and bits: Q1[p], Q2[p] (HOST arrays of descriptors, read during the call) are the two
+ * quantizations of problem p's Phi; the operator is the stacked real system
+ * A_i = [diag(a); diag(b)] Q_i (2m x n) of the per-row complex gain g = a + i b
+ * (gain_re = a, gain_im = b: [device] nprob x m floats); y [device] nprob x 2m floats (not
+ * quantized). With x_0 = 0: r_t = y - A2 x_t, h_t = A1^T r_t, G_t = supp H_s(h_0) for t = 0
+ * and the support of x_t after, mu_t = ||h_t on G_t||^2 / ||A2 (h_t on G_t)||^2,
+ * x_{t+1} = H_s(x_t + mu_t h_t). X [device] nprob x n receives x_K. The workspace keeps the
+ * state every ceil(sqrt(K)) steps for qiht_unrolled_backward. Requires m <= 16384,
+ * n <= 32768, s <= 256. Asynchronous on `stream` after the descriptor copies. */
+qiht_status qiht_unrolled_forward(const qiht_codes* Q1, const qiht_codes* Q2, int32_t nprob, const float* y,
+                                  const float* gain_re, const float* gain_im, int32_t s, int32_t K, float* X,
+                                  void* workspace, size_t workspace_bytes, qiht_stream_t stream);
+
+/* The adjoint of qiht_unrolled_forward with the supports held fixed: from Xbar = dL/dx_K
+ * [device, nprob x n] it writes ybar = dL/dy (nprob x 2m), gain_re_bar = dL/da and
+ * gain_im_bar = dL/db (nprob x m each). Call it after qiht_unrolled_forward with the same
+ * arguments and workspace: each segment between checkpoints is recomputed, recording what
+ * the reverse steps need. FP32 products, FP64 scalars. Asynchronous on `stream`. */
+qiht_status qiht_unrolled_backward(const qiht_codes* Q1, const qiht_codes* Q2, int32_t nprob, const float* y,
+                                   const float* gain_re, const float* gain_im, int32_t s, int32_t K, const float* Xbar,
+                                   float* ybar, float* gain_re_bar, float* gain_im_bar, void* workspace,
+                                   size_t workspace_bytes, qiht_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

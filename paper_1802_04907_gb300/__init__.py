@@ -81,7 +81,8 @@ EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
            "qiht_clear_graph_cache", "qiht_solve_batched_workspace_size", "qiht_niht_solve_batched",
            "qiht_gemv_t_multi_workspace_size", "qiht_gemv_t_multi", "qiht_solve_multi_workspace_size",
-           "qiht_niht_solve_multi", "qiht_solve_fresh_workspace_size", "qiht_niht_solve_fresh"]
+           "qiht_niht_solve_multi", "qiht_solve_fresh_workspace_size", "qiht_niht_solve_fresh",
+           "qiht_unrolled_workspace_size", "qiht_unrolled_forward", "qiht_unrolled_backward"]
 
 _lib = None
 
@@ -120,6 +121,11 @@ def lib():
             "qiht_gemv_t_multi": ([ctypes.POINTER(_Codes), P, I64, I32, P, I64, P, P, SZ, P], I32),
             "qiht_solve_multi_workspace_size": ([I32, I32, I32, I32], SZ),
             "qiht_solve_fresh_workspace_size": ([I32, I32, I32, I32, I32], SZ),
+            "qiht_unrolled_workspace_size": ([I32, I32, I32, I32, I32], SZ),
+            "qiht_unrolled_forward": ([ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), I32, P, P, P, I32, I32, P, P,
+                                       SZ, P], I32),
+            "qiht_unrolled_backward": ([ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), I32, P, P, P, I32, I32, P, P,
+                                        P, P, P, SZ, P], I32),
             "qiht_niht_solve_fresh": ([P, I64, P, I32, I32, I32, I32, U64, I32, I32, I32, ctypes.POINTER(_Params),
                                        P, P, P, ctypes.POINTER(_Trace), P, SZ, P], I32),
             "qiht_niht_solve_multi": ([ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), I32,
@@ -383,6 +389,63 @@ def niht_solve_fresh(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: 
     _check(st, "qiht_niht_solve_fresh")
     sv.workspace = ws
     return sv
+
+
+class Unrolled:
+    """K unrolled QIHT iterations (frozen support masks, no backtracking test) for nprob problems
+    sharing m, n, bits: qiht_unrolled_forward / qiht_unrolled_backward with one workspace (the
+    forward keeps the sqrt(K) checkpoints the backward recomputes from)."""
+
+    def __init__(self, Q1s: list, Q2s: list, s: int, K: int):
+        self.Q1s, self.Q2s, self.s, self.K = Q1s, Q2s, s, K
+        self.P = len(Q1s)
+        self.m, self.n = Q1s[0].rows, Q1s[0].cols
+        dev = Q1s[0].words.device
+        self.c1 = (_Codes * self.P)(*[q.c_struct() for q in Q1s])
+        self.c2 = (_Codes * self.P)(*[q.c_struct() for q in Q2s])
+        self.ws = _ws(lib().qiht_unrolled_workspace_size(self.P, self.m, self.n, s, K), dev)
+
+    def forward(self, y: torch.Tensor, gre: torch.Tensor, gim: torch.Tensor, stream=None) -> torch.Tensor:
+        """x_K for every problem (P x n) from y (P x 2m) and the gains (P x m each)."""
+        X = torch.empty(self.P, self.n, dtype=torch.float32, device=y.device)
+        _check(lib().qiht_unrolled_forward(self.c1, self.c2, self.P, y.data_ptr(), gre.data_ptr(), gim.data_ptr(),
+                                           self.s, self.K, X.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
+                                           _stream(stream)), "qiht_unrolled_forward")
+        return X
+
+    def backward(self, y: torch.Tensor, gre: torch.Tensor, gim: torch.Tensor, Xbar: torch.Tensor, stream=None):
+        """(dL/dy, dL/dRe g, dL/dIm g) from dL/dx_K, after forward() on the same inputs."""
+        yb = torch.empty_like(y)
+        ab = torch.empty_like(gre)
+        bb = torch.empty_like(gim)
+        _check(lib().qiht_unrolled_backward(self.c1, self.c2, self.P, y.data_ptr(), gre.data_ptr(), gim.data_ptr(),
+                                            self.s, self.K, Xbar.contiguous().data_ptr(), yb.data_ptr(),
+                                            ab.data_ptr(), bb.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
+                                            _stream(stream)), "qiht_unrolled_backward")
+        return yb, ab, bb
+
+
+class UnrolledQIHT(torch.autograd.Function):
+    """x_K = unrolled QIHT(y, gain) with the hand-written adjoint as its backward."""
+
+    @staticmethod
+    def forward(ctx, y, gre, gim, op):
+        y, gre, gim = y.contiguous(), gre.contiguous(), gim.contiguous()
+        X = op.forward(y, gre, gim)
+        ctx.op = op
+        ctx.save_for_backward(y, gre, gim)
+        return X
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        y, gre, gim = ctx.saved_tensors
+        yb, ab, bb = ctx.op.backward(y, gre, gim, grad_x)
+        return yb, ab, bb, None
+
+
+def unrolled_qiht(y: torch.Tensor, gre: torch.Tensor, gim: torch.Tensor, op: Unrolled) -> torch.Tensor:
+    """Differentiable x_K (P x n) of the unrolled iterations in y (P x 2m) and the gain (P x m, P x m)."""
+    return UnrolledQIHT.apply(y, gre, gim, op)
 
 
 BATCH_MAX_ROWS, BATCH_MAX_COLS, BATCH_MAX_S = 2048, 8192, 256

@@ -319,6 +319,41 @@ cudaError_t launch_mrhs_step(const MrhsStepArgs& a, int bits, cudaStream_t s);
 cudaError_t launch_mrhs_final(const MrhsStepArgs& a, float* X, qiht_report* reports, const int* gemm_status,
                               cudaStream_t s);
 
+// K unrolled iterations and their adjoint for many problems (unrolled.cu).
+struct UdArgs {
+    const qiht_codes* q1;     // nprob descriptors [device]
+    const qiht_codes* q2;
+    const float* y;           // P x 2m observations
+    const float* ga;          // P x m gains (real parts)
+    const float* gb;          // P x m gains (imaginary parts)
+    int P, m, n, s, mk;
+    int32_t* sup;             // P x s: support of the current iterate (ascending)
+    float* xs;                // P x s: its values
+    float* vin;               // P x m: a r_top + b r_bot of the current iterate
+    float* r;                 // P x 2m: y - A2 x
+    float* q;                 // P x m: Phi2 x
+    float* h;                 // P x n: the current gradient A1^T r
+    // record of a segment (rec_r == nullptr: not recording); slot = step - first step
+    float* rec_r;             // P x c x 2m
+    float* rec_q;             // P x c x m
+    float* rec_u;             // P x c x m: Phi2 P h
+    int32_t* rec_G;           // P x c x s
+    int32_t* rec_Gn;          // P x c x s
+    float* rec_hG;            // P x c x s: h on G_t
+    float* rec_hGn;           // P x c x s: h on G_{t+1}
+    double* rec_sc;           // P x c x 4: mu, ||P h||^2, ||A2 P h||^2
+    int c, slot, t;
+};
+size_t ud_fwd_smem(int n, int mk, int s);
+size_t ud_bwd_smem(int n, int mk, int s);
+cudaError_t launch_ud_init(const UdArgs& a, cudaStream_t s);
+cudaError_t launch_ud_xout(const UdArgs& a, float* X, cudaStream_t s);
+cudaError_t launch_ud_gemvt(const qiht_codes* Qs, int bits, const float* v, const float* base, float sign, float* out,
+                            int P, int m, int n, int ldw, cudaStream_t s);
+cudaError_t launch_ud_fwd(const UdArgs& a, int bits, cudaStream_t s);
+cudaError_t launch_ud_bwd(const UdArgs& a, int bits, const float* xbar, float* vbase, float* vv, float* ybar,
+                          float* gabar, float* gbbar, cudaStream_t s);
+
 int gather_row_blocks(int rows, int bits);
 int gather_chunks(int count);
 size_t gather_partial_floats(int rows, int bits, int count);

@@ -16,365 +16,12 @@
 
 #include <cmath>
 
-#include "internal.cuh"
+#include "cta_ops.cuh"
 
 namespace qiht {
 namespace {
 
-constexpr int kST = 1024;                 // threads per CTA
-constexpr int kSW = kST / 32;
-
-struct SSh {
-    double d[34];
-    int i[36];
-    double mu, alpha1, alpha2, alpha_y;
-    float muf, alpha2f;
-    int code;
-};
-
-// Shared memory of one right-hand side.
-struct MSm {
-    uint32_t* keys;      // max(n, 16384): selection keys; scratch of the column products
-    uint32_t* bitmap;    // n / 32: selected set
-    uint32_t* gbit;      // n / 32: current support
-    int* wpre;           // n / 32
-    float* z;            // mk: column-subset product, then the residual
-    int* sup;            // s: G (ascending)
-    float* xs;           // s: x on G
-    int* sel;            // s: G'
-    float* val;          // s: x' on G'
-    int* uni;            // 2s: G' then G \ G'
-    float* dlt;          // 2s: x' - x on uni
-    unsigned* hist;      // 256
-};
-
-__host__ __device__ inline size_t mrhs_keys_words(int n) { return (size_t)(n > 16384 ? n : 16384); }
-
-__host__ __device__ inline size_t mrhs_step_smem_bytes(int n, int mk, int s)
-{
-    const size_t nb = (size_t)(n + 31) / 32;
-    return mrhs_keys_words(n) * 4 + 3 * nb * 4 + (size_t)mk * 4 + (size_t)s * 4 * 4 + (size_t)s * 2 * 4 * 2 +
-           256 * 4 + 64;
-}
-
-__device__ MSm msm_layout(unsigned char* p, int n, int mk, int s)
-{
-    const size_t nb = (size_t)(n + 31) / 32;
-    MSm m;
-    m.keys = reinterpret_cast<uint32_t*>(p);
-    m.bitmap = m.keys + mrhs_keys_words(n);
-    m.gbit = m.bitmap + nb;
-    m.wpre = reinterpret_cast<int*>(m.gbit + nb);
-    m.z = reinterpret_cast<float*>(m.wpre + nb);
-    m.sup = reinterpret_cast<int*>(m.z + mk);
-    m.xs = reinterpret_cast<float*>(m.sup + s);
-    m.sel = reinterpret_cast<int*>(m.xs + s);
-    m.val = reinterpret_cast<float*>(m.sel + s);
-    m.uni = reinterpret_cast<int*>(m.val + s);
-    m.dlt = reinterpret_cast<float*>(m.uni + 2 * s);
-    m.hist = reinterpret_cast<unsigned*>(m.dlt + 2 * s);
-    return m;
-}
-
-// ---- deterministic CTA reductions ----
-__device__ double ssum(double v, double* sh)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        double t = sh[lane];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) sh[32] = t;
-    }
-    __syncthreads();
-    const double r = sh[32];
-    __syncthreads();
-    return r;
-}
-
-__device__ unsigned smax(unsigned v, int* sh)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    v = __reduce_max_sync(0xffffffffu, v);
-    if (lane == 0) sh[w] = (int)v;
-    __syncthreads();
-    if (w == 0) {
-        unsigned t = (unsigned)sh[lane];
-        t = __reduce_max_sync(0xffffffffu, t);
-        if (lane == 0) sh[32] = (int)t;
-    }
-    __syncthreads();
-    const unsigned r = (unsigned)sh[32];
-    __syncthreads();
-    return r;
-}
-
-__device__ int sscan(int v, int* sh, int* total)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sh[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        const int sv = sh[lane];
-        int t = sv;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        sh[lane] = t - sv;
-        if (lane == 31) sh[32] = t;
-    }
-    __syncthreads();
-    const int r = sh[w] + x - v;
-    *total = sh[32];
-    __syncthreads();
-    return r;
-}
-
-// z[0..m) = sum over the list (in list order) of coef_e * (2 c_{i, list_e} - (L-1)).
-// Thread t takes 16-row group t % ngr of every column and the list entries of slice
-// t / ngr; several slices are summed in slice order.
-template <int BITS>
-__device__ void mcols(const Codes& Q, const int* list, const float* coef, int count, float* z, float* part)
-{
-    constexpr int G = 32 / BITS;
-    constexpr int WG = 16 / G;                // words per 16-row group
-    constexpr uint32_t MASK = (1u << BITS) - 1;
-    constexpr int kSU = BITS == 8 ? 4 : 8;    // list entries of a thread in flight (64 registers per thread)
-    const int ld = Q.ld, m = Q.rows, lm1 = Q.lm1;
-    const int ngr = ld / WG;                  // <= kST under the row limit
-    const int nsl = kST / ngr;
-    const int tid = threadIdx.x, gi = tid % ngr, sl = tid / ngr;
-    float acc[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) acc[r] = 0.0f;
-    if (sl < nsl) {
-        const uint32_t* base = Q.words + (size_t)gi * WG;
-        for (int e0 = sl; e0 < count; e0 += kSU * nsl) {
-            uint32_t w[kSU][WG];
-            float cf[kSU];
-#pragma unroll
-            for (int u = 0; u < kSU; ++u) {
-                const int e = e0 + u * nsl;
-                const bool in = e < count;
-                const uint32_t* src = base + (size_t)(in ? list[e] : 0) * ld;
-                if (WG == 4) {
-                    const uint4 v = in ? __ldg(reinterpret_cast<const uint4*>(src)) : make_uint4(0, 0, 0, 0);
-                    w[u][0] = v.x; w[u][WG > 1 ? 1 : 0] = v.y; w[u][WG > 2 ? 2 : 0] = v.z; w[u][WG > 3 ? 3 : 0] = v.w;
-                } else if (WG == 2) {
-                    const uint2 v = in ? __ldg(reinterpret_cast<const uint2*>(src)) : make_uint2(0, 0);
-                    w[u][0] = v.x; w[u][WG > 1 ? 1 : 0] = v.y;
-                } else {
-                    w[u][0] = in ? __ldg(src) : 0u;
-                }
-                cf[u] = in ? coef[e] : 0.0f;          // past the end: exact zeros
-            }
-#pragma unroll
-            for (int u = 0; u < kSU; ++u)
-#pragma unroll
-                for (int q = 0; q < WG; ++q)
-#pragma unroll
-                    for (int k = 0; k < G; ++k) {
-                        const int code = (int)((w[u][q] >> (8 * (k & 3) + BITS * (k >> 2))) & MASK);
-                        acc[q * G + k] = fmaf((float)(2 * code - lm1), cf[u], acc[q * G + k]);
-                    }
-        }
-    }
-    if (nsl == 1) {
-        if (sl == 0)
-#pragma unroll
-            for (int r = 0; r < 16; ++r)
-                if (gi * 16 + r < m) z[gi * 16 + r] = acc[r];
-        __syncthreads();
-        return;
-    }
-    if (sl < nsl)
-#pragma unroll
-        for (int r = 0; r < 16; ++r) part[(sl * ngr + gi) * 16 + r] = acc[r];
-    __syncthreads();
-    for (int i = tid; i < m; i += kST) {
-        const int g2 = i / 16, r = i % 16;
-        float a = 0.0f;
-        for (int t = 0; t < nsl; ++t) a += part[(t * ngr + g2) * 16 + r];
-        z[i] = a;
-    }
-    __syncthreads();
-}
-
-// x_j of the current iterate (0 off the support): binary search of the ascending support
-__device__ __forceinline__ float x_at(const MSm& sm, int s, int j)
-{
-    if (!((sm.gbit[j >> 5] >> (j & 31)) & 1u)) return 0.0f;
-    int lo = 0, hi = s - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (sm.sup[mid] < j) lo = mid + 1;
-        else hi = mid;
-    }
-    return sm.xs[lo];
-}
-
-// keys |fmaf(mu, g_j, x_j)| for all j (x is 0 off the support); returns 1 if one is not finite
-__device__ int mkeys(int n, int s, float muf, const float* g, const MSm& sm)
-{
-    const int tid = threadIdx.x;
-    int bad = 0;
-    for (int j = tid; j < n; j += kST) {
-        const uint32_t k = __float_as_uint(fmaf(muf, __ldg(g + j), 0.0f)) & 0x7fffffffu;
-        sm.keys[j] = k;
-        bad |= k > 0x7f800000u;
-    }
-    __syncthreads();
-    for (int q = tid; q < s; q += kST) {
-        const int j = sm.sup[q];
-        const uint32_t k = __float_as_uint(fmaf(muf, __ldg(g + j), sm.xs[q])) & 0x7fffffffu;
-        sm.keys[j] = k;
-        bad |= k > 0x7f800000u;
-    }
-    return __syncthreads_or(bad);
-}
-
-// H_s over the keys: the s largest, ties to the lower index. G' ascending in sel / val
-// (val = x'), the list x' - x over G' u G in uni / dlt (G \ G' after G', in support
-// order; only with with_old). Returns 1 if G' != G, else 0; *uc = entries of the list.
-__device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, SSh& sh, int* uc, bool with_old)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t prefix = 0;
-    int need = s;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        if (tid < 256) sm.hist[tid] = 0;
-        __syncthreads();
-        for (int b = warp * 32; b < n; b += kST) {
-            const int j = b + lane;
-            const bool in = j < n;
-            const uint32_t k = in ? sm.keys[j] : 0u;
-            const bool take = in && (pass == 0 || (k >> (shift + 8)) == (prefix >> (shift + 8)));
-            if (!__any_sync(0xffffffffu, take)) continue;   // later passes: most steps have no candidate
-            const unsigned bin = (k >> shift) & 255u;
-            // lanes with the same bin add once (keys crowd into few bins); the other lanes share
-            // one value so that the match stays cheap
-            const unsigned peers = __match_any_sync(0xffffffffu, take ? bin : 0x100u);
-            if (take && lane == __ffs(peers) - 1) atomicAdd(&sm.hist[bin], (unsigned)__popc(peers));
-        }
-        __syncthreads();
-        if (warp == 0) {
-            int c[8];
-            int tot = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { c[i] = (int)sm.hist[255 - 8 * lane - i]; tot += c[i]; }
-            int incl = tot;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int excl = incl - tot;
-            if (excl < need && need <= incl) {
-                int run = excl;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (run + c[i] >= need) { sh.i[0] = 255 - 8 * lane - i; sh.i[1] = run; break; }
-                    run += c[i];
-                }
-            }
-        }
-        __syncthreads();
-        prefix |= (uint32_t)sh.i[0] << shift;
-        need -= sh.i[1];
-        __syncthreads();
-    }
-    const uint32_t T = prefix;
-    const int nbw = (n + 31) / 32;
-    for (int w = tid; w < nbw; w += kST) sm.bitmap[w] = 0u;
-    const int seg = ((n + 32 * kSW - 1) / (32 * kSW)) * 32;
-    const int wb = min(n, warp * seg), we = min(n, wb + seg);
-    int eq = 0;
-    for (int b = wb; b < we; b += 32) {
-        const int j = b + lane;
-        eq += __popc(__ballot_sync(0xffffffffu, j < we && sm.keys[j] == T));
-    }
-    if (lane == 0) sh.i[warp] = eq;
-    __syncthreads();
-    int eq_before = 0;
-    for (int w = 0; w < warp; ++w) eq_before += sh.i[w];
-    const int take_w = max(0, min(eq, need - eq_before));
-    int erun = 0;
-    for (int b = wb; b < we; b += 32) {
-        const int j = b + lane;
-        const bool in = j < we;
-        const uint32_t k = in ? sm.keys[j] : 0u;
-        const unsigned meq = __ballot_sync(0xffffffffu, in && k == T);
-        const int rank = erun + __popc(meq & ((1u << lane) - 1u));
-        if (in && (k > T || (k == T && rank < take_w))) atomicOr(&sm.bitmap[j >> 5], 1u << (j & 31));
-        erun += __popc(meq);
-    }
-    __syncthreads();
-    {
-        const int wpt = (nbw + kST - 1) / kST;
-        const int w0 = min(nbw, tid * wpt), w1 = min(nbw, w0 + wpt);
-        int c = 0;
-        for (int w = w0; w < w1; ++w) c += __popc(sm.bitmap[w]);
-        int total;
-        int pre = sscan(c, sh.i, &total);
-        for (int w = w0; w < w1; ++w) { sm.wpre[w] = pre; pre += __popc(sm.bitmap[w]); }
-    }
-    __syncthreads();
-    for (int w = tid; w < nbw; w += kST) {
-        uint32_t bits = sm.bitmap[w];
-        int p = sm.wpre[w];
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int j = w * 32 + b;
-            const float xj = x_at(sm, s, j);
-            const float v = fmaf(muf, __ldg(g + j), xj);
-            sm.sel[p] = j;
-            sm.val[p] = v;
-            sm.uni[p] = j;
-            sm.dlt[p] = v - xj;
-            ++p;
-        }
-    }
-    __syncthreads();
-    int diff = 0;
-    *uc = s;
-    if (with_old) {
-        const int sper = (s + kST - 1) / kST;
-        const int q0 = min(s, tid * sper), q1 = min(s, q0 + sper);
-        int cntx = 0;
-        for (int q = q0; q < q1; ++q) {
-            const int j = sm.sup[q];
-            cntx += !((sm.bitmap[j >> 5] >> (j & 31)) & 1u);
-        }
-        int extra;
-        int p = sscan(cntx, sh.i, &extra);
-        for (int q = q0; q < q1; ++q) {
-            const int j = sm.sup[q];
-            if (!((sm.bitmap[j >> 5] >> (j & 31)) & 1u)) {
-                sm.uni[s + p] = j;
-                sm.dlt[s + p] = -sm.xs[q];
-                ++p;
-            }
-        }
-        diff = extra > 0;
-        *uc = s + extra;
-    }
-    __syncthreads();
-    return diff;
-}
+using namespace cta;
 
 // dequantized observation value of row i (FP64 product, rounded once)
 __device__ __forceinline__ float yhat_at(const qiht_codes& Y, int lm1y, double alpha_y, int i)

@@ -1,0 +1,705 @@
+// K unrolled QIHT iterations and their adjoint, for many problems at once.
+//
+// For each problem (codes Q1, Q2 of Phi, m x n; observation y of 2m entries; per-row complex
+// gain a + i b) the operator is the stacked real system A_i = [diag(a); diag(b)] Phi-hat_i.
+// With x_0 = 0, step t computes
+//     h_t = A1^T r_t,  r_t = y - A2 x_t,
+//     G_t = supp H_s(h_0) (t = 0) or the support of x_t,
+//     mu_t = ||P h_t||^2 / ||A2 P h_t||^2 (P: restriction to G_t),
+//     x_{t+1} = P_{t+1}(x_t + mu_t h_t),  G_{t+1} = supp H_s(x_t + mu_t h_t),
+// i.e. the iteration of Algorithm 2 without the backtracking test, and the adjoint maps
+// dL/dx_K to dL/dy, dL/da, dL/db with the supports held fixed. The adjoint of a step is
+//     v = P_{t+1} xbar_{t+1},  mubar = <v, h_t>,
+//     hbar = mu v + mubar (2/D)(P h - mu P A2^T A2 P h)      (sparse: on G_{t+1} u G_t),
+//     rbar = A1 hbar,  ybar += rbar,  xbar_t = v - A2^T rbar,
+// and the gains collect r hbar^T, -rbar x^T and -(2 mubar mu / D) (A2 P h)(P h)^T through
+// the rows they scale.
+//
+// Kernels: a batched dense product out = base + sign A^T v (grid over columns x problems, one
+// warp per column, FP32), and one CTA (1024 threads) per problem for everything else of a
+// step (column-subset products of the s columns, FP64 sums, H_s over all n keys in shared
+// memory). The forward keeps the state every ceil(sqrt K) steps; the adjoint recomputes each
+// segment from its checkpoint, recording what the reverse steps need.
+#include <cmath>
+
+#include "cta_ops.cuh"
+
+namespace qiht {
+namespace {
+
+using namespace cta;
+
+constexpr int kUdColsPerWarp = 8;
+constexpr int kUdWarps = 8;
+
+// out[p][j] = (base ? base[p][j] : 0) + sign * alpha * sum_i (2 c_ij - (L-1)) v[p][i]
+template <int BITS>
+__global__ void __launch_bounds__(256) k_ud_gemvt(const qiht_codes* __restrict__ Qs, const float* __restrict__ v,
+                                                  const float* __restrict__ base, float sign, float* __restrict__ out,
+                                                  int m, int n)
+{
+    constexpr int G = 32 / BITS;
+    constexpr uint32_t MASK = (1u << BITS) - 1;
+    extern __shared__ float vs[];               // v of this problem, padded to the column length
+    const int p = blockIdx.y;
+    const qiht_codes Q = Qs[p];
+    const int ld = Q.ld_words;
+    const int lm1 = grid_levels(BITS, Q.levels) - 1;
+    const float alpha = (float)((double)(*Q.scale) / (double)lm1);
+    const float* vp = v + (size_t)p * m;
+    for (int i = threadIdx.x; i < ld * G; i += 256) vs[i] = i < m ? vp[i] : 0.0f;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j0 = (blockIdx.x * kUdWarps + warp) * kUdColsPerWarp;
+    for (int jj = 0; jj < kUdColsPerWarp; ++jj) {
+        const int j = j0 + jj;
+        if (j >= n) break;
+        const uint4* col = reinterpret_cast<const uint4*>(Q.words + (size_t)j * ld);
+        float acc = 0.0f;
+        for (int w4 = lane; w4 < ld / 4; w4 += 32) {
+            const uint4 c4 = __ldg(col + w4);
+            const uint32_t wd[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float* vr = vs + (size_t)(w4 * 4 + u) * G;
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const int code = (int)((wd[u] >> (8 * (k & 3) + BITS * (k >> 2))) & MASK);
+                    acc = fmaf((float)(2 * code - lm1), vr[k], acc);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const float b0 = base ? base[(size_t)p * n + j] : 0.0f;
+            out[(size_t)p * n + j] = fmaf(sign * alpha, acc, b0);
+        }
+    }
+}
+
+// dot products of the columns in `list` with vec (m entries, shared memory): out[e] =
+// alpha * sum_i (2 c_{i, list_e} - (L-1)) vec_i, one warp per column
+template <int BITS>
+__device__ void ucol_dots(const Codes& Q, const int* list, int count, const float* vec, float* out)
+{
+    constexpr int G = 32 / BITS;
+    constexpr uint32_t MASK = (1u << BITS) - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float alpha = (float)((double)(*Q.scale) / (double)Q.lm1);
+    for (int e = warp; e < count; e += kST / 32) {
+        const uint4* col = reinterpret_cast<const uint4*>(Q.words + (size_t)list[e] * Q.ld);
+        float acc = 0.0f;
+        for (int w4 = lane; w4 < Q.ld / 4; w4 += 32) {
+            const uint4 c4 = __ldg(col + w4);
+            const uint32_t wd[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const int row = (w4 * 4 + u) * G + k;
+                    const int code = (int)((wd[u] >> (8 * (k & 3) + BITS * (k >> 2))) & MASK);
+                    acc = fmaf((float)(2 * code - Q.lm1), row < Q.rows ? vec[row] : 0.0f, acc);
+                }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[e] = alpha * acc;
+    }
+    __syncthreads();
+}
+
+struct UdSh {
+    double d[34];
+    int i[36];
+    double mu, N, D, mubar;
+    float muf;
+    int code;
+};
+
+__device__ Codes codes_of(const qiht_codes& q)
+{
+    return Codes{q.words, q.scale, q.rows, q.cols, q.bits, q.ld_words, grid_levels(q.bits, q.levels) - 1};
+}
+
+// One forward step for problem blockIdx.x: h_t is in a.h (from the batched product).
+template <int BITS>
+__global__ void __launch_bounds__(kST, 1) k_ud_fwd(UdArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SSh sh;
+    __shared__ UdSh us;
+    const int p = blockIdx.x, tid = threadIdx.x;
+    const int m = a.m, n = a.n, s = a.s;
+    const MSm sm = msm_layout(smem, n, a.mk, s);
+    const Codes Q2 = codes_of(a.q2[p]);
+    const float* h = a.h + (size_t)p * n;
+    const float* ga = a.ga + (size_t)p * m;
+    const float* gb = a.gb + (size_t)p * m;
+    int32_t* gsup = a.sup + (size_t)p * s;
+    float* gxs = a.xs + (size_t)p * s;
+    const int nbw = (n + 31) / 32;
+    for (int w = tid; w < nbw; w += kST) sm.gbit[w] = 0u;
+    __syncthreads();
+    int uc = 0;
+    if (a.t == 0) {
+        // initial support H_s(h_0) (x_0 = 0)
+        mkeys(n, 0, 1.0f, h, sm);
+        mselect(n, s, 1.0f, h, sm, sh, &uc, false);
+        for (int q = tid; q < s; q += kST) { sm.sup[q] = sm.sel[q]; sm.xs[q] = 0.0f; }
+    } else {
+        for (int q = tid; q < s; q += kST) { sm.sup[q] = gsup[q]; sm.xs[q] = gxs[q]; }
+    }
+    __syncthreads();
+    for (int q = tid; q < s; q += kST) atomicOr(&sm.gbit[sm.sup[q] >> 5], 1u << (sm.sup[q] & 31));
+    // P h on G_t, N, u = Phi2 P h, D = sum (a^2 + b^2) u^2, mu
+    for (int q = tid; q < s; q += kST) sm.val[q] = __ldg(h + sm.sup[q]);
+    __syncthreads();
+    double N = 0.0;
+    if (tid < 32) {
+        for (int q = tid; q < s; q += 32) N += (double)sm.val[q] * (double)sm.val[q];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) N += __shfl_xor_sync(0xffffffffu, N, o);
+    }
+    mcols<BITS>(Q2, sm.sup, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
+    const float alpha2 = (float)((double)(*Q2.scale) / (double)Q2.lm1);
+    double D = 0.0;
+    for (int i = tid; i < m; i += kST) {
+        const float ui = alpha2 * sm.z[i];
+        sm.z[i] = ui;
+        const double g2 = (double)ga[i] * ga[i] + (double)gb[i] * gb[i];
+        D += g2 * (double)ui * (double)ui;
+    }
+    D = ssum(D, sh.d);
+    if (tid == 0) {
+        us.N = N;
+        us.D = D;
+        us.mu = D > 0.0 ? N / D : 0.0;
+        us.muf = (float)us.mu;
+    }
+    __syncthreads();
+    if (a.rec_r) {
+        const size_t slot = (size_t)p * a.c + a.slot;
+        for (int i = tid; i < m; i += kST) {
+            a.rec_u[slot * m + i] = sm.z[i];
+            a.rec_q[slot * m + i] = a.q[(size_t)p * m + i];
+        }
+        for (int i = tid; i < 2 * m; i += kST) a.rec_r[slot * 2 * m + i] = a.r[(size_t)p * 2 * m + i];
+        for (int q = tid; q < s; q += kST) {
+            a.rec_G[slot * s + q] = sm.sup[q];
+            a.rec_hG[slot * s + q] = sm.val[q];
+        }
+        if (tid == 0) {
+            a.rec_sc[slot * 4 + 0] = us.mu;
+            a.rec_sc[slot * 4 + 1] = us.N;
+            a.rec_sc[slot * 4 + 2] = us.D;
+        }
+    }
+    // x_{t+1} = H_s(x_t + mu h_t)
+    mkeys(n, s, us.muf, h, sm);
+    mselect(n, s, us.muf, h, sm, sh, &uc, false);
+    if (a.rec_r) {
+        const size_t slot = (size_t)p * a.c + a.slot;
+        for (int q = tid; q < s; q += kST) {
+            a.rec_Gn[slot * s + q] = sm.sel[q];
+            a.rec_hGn[slot * s + q] = __ldg(h + sm.sel[q]);
+        }
+    }
+    for (int q = tid; q < s; q += kST) {
+        gsup[q] = sm.sel[q];
+        gxs[q] = sm.val[q];
+    }
+    // the next step's q = Phi2 x, r = y - [a q; b q] and v = a r_top + b r_bot
+    mcols<BITS>(Q2, sm.sel, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
+    const float* y = a.y + (size_t)p * 2 * m;
+    for (int i = tid; i < m; i += kST) {
+        const float qi = alpha2 * sm.z[i];
+        const float rt = fmaf(-ga[i], qi, y[i]);
+        const float rb = fmaf(-gb[i], qi, y[m + i]);
+        a.q[(size_t)p * m + i] = qi;
+        a.r[(size_t)p * 2 * m + i] = rt;
+        a.r[(size_t)p * 2 * m + m + i] = rb;
+        a.vin[(size_t)p * m + i] = fmaf(ga[i], rt, gb[i] * rb);
+    }
+}
+
+// One adjoint step for problem blockIdx.x from the record of its forward step.
+template <int BITS>
+__global__ void __launch_bounds__(kST, 1) k_ud_bwd(UdArgs a, const float* __restrict__ xbar, float* __restrict__ vbase,
+                                                   float* __restrict__ vv, float* ybar, float* gabar, float* gbbar)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SSh sh;
+    __shared__ UdSh us;
+    const int p = blockIdx.x, tid = threadIdx.x;
+    const int m = a.m, n = a.n, s = a.s;
+    const MSm sm = msm_layout(smem, n, a.mk, s);
+    float* w2 = reinterpret_cast<float*>(smem + msm_bytes(n, a.mk, s));     // m: (a^2 + b^2) u
+    float* cG = w2 + a.mk;                                                   // s: (A2^T A2 P h) on G
+    const Codes Q1 = codes_of(a.q1[p]);
+    const Codes Q2 = codes_of(a.q2[p]);
+    const float* ga = a.ga + (size_t)p * m;
+    const float* gb = a.gb + (size_t)p * m;
+    const size_t slot = (size_t)p * a.c + a.slot;
+    const float* ru = a.rec_u + slot * m;
+    const float* rq = a.rec_q + slot * m;
+    const float* rr = a.rec_r + slot * 2 * m;
+    const int nbw = (n + 31) / 32;
+    for (int w = tid; w < nbw; w += kST) sm.bitmap[w] = 0u;
+    if (tid == 0) {
+        us.mu = a.rec_sc[slot * 4 + 0];
+        us.N = a.rec_sc[slot * 4 + 1];
+        us.D = a.rec_sc[slot * 4 + 2];
+    }
+    __syncthreads();
+    // v on G_{t+1} (sel) and mubar = <v, h>
+    const float* xb = xbar + (size_t)p * n;
+    for (int q = tid; q < s; q += kST) {
+        const int j = a.rec_Gn[slot * s + q];
+        sm.sel[q] = j;
+        sm.val[q] = __ldg(xb + j);                        // v_j
+        sm.sup[q] = a.rec_G[slot * s + q];
+        sm.xs[q] = a.rec_hG[slot * s + q];                // h on G_t
+        atomicOr(&sm.bitmap[j >> 5], 1u << (j & 31));
+    }
+    __syncthreads();
+    double mb = 0.0;
+    if (tid < 32) {
+        for (int q = tid; q < s; q += 32) mb += (double)sm.val[q] * (double)a.rec_hGn[slot * s + q];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mb += __shfl_xor_sync(0xffffffffu, mb, o);
+        if (tid == 0) us.mubar = mb;
+    }
+    // c = (A2^T A2 P h) on G_t = Phi2^T ((a^2 + b^2) u) there
+    for (int i = tid; i < a.mk; i += kST) {
+        const float g2 = i < m ? fmaf(ga[i], ga[i], gb[i] * gb[i]) : 0.0f;
+        w2[i] = i < m ? g2 * ru[i] : 0.0f;
+    }
+    __syncthreads();
+    ucol_dots<BITS>(Q2, sm.sup, s, w2, cG);
+    // hbar on G_{t+1} u G_t: the union list (G_{t+1}, then G_t \ G_{t+1}) with its coefficients
+    const double mu = us.mu, D = us.D, mubar = us.mubar;
+    const double k2 = D > 0.0 ? mubar * 2.0 / D : 0.0;
+    for (int q = tid; q < s; q += kST) {
+        sm.uni[q] = sm.sel[q];
+        sm.dlt[q] = (float)(mu * (double)sm.val[q]);
+    }
+    __syncthreads();
+    // G_t entries: inside G_{t+1} they add to that entry, outside they are appended in order
+    {
+        const int sper = (s + kST - 1) / kST;
+        const int q0 = min(s, tid * sper), q1 = min(s, q0 + sper);
+        int cnt = 0;
+        for (int q = q0; q < q1; ++q) {
+            const int j = sm.sup[q];
+            cnt += !((sm.bitmap[j >> 5] >> (j & 31)) & 1u);
+        }
+        int extra;
+        int pos = sscan(cnt, sh.i, &extra);
+        for (int q = q0; q < q1; ++q) {
+            const int j = sm.sup[q];
+            const float add = (float)(k2 * ((double)sm.xs[q] - mu * (double)cG[q]));
+            if ((sm.bitmap[j >> 5] >> (j & 31)) & 1u) {
+                // position of j in G_{t+1} (ascending): binary search
+                int lo = 0, hi = s - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sm.sel[mid] < j) lo = mid + 1;
+                    else hi = mid;
+                }
+                atomicAdd(&sm.dlt[lo], add);
+            } else {
+                sm.uni[s + pos] = j;
+                sm.dlt[s + pos] = add;
+                ++pos;
+            }
+        }
+        if (tid == 0) us.code = s + extra;
+    }
+    __syncthreads();
+    const int uc = us.code;
+    // p = Phi1 hbar; rbar = [a p; b p]
+    mcols<BITS>(Q1, sm.uni, sm.dlt, uc, sm.z, reinterpret_cast<float*>(sm.keys));
+    const float alpha1 = (float)((double)(*Q1.scale) / (double)Q1.lm1);
+    const float c3 = D > 0.0 ? (float)(-2.0 * mubar * mu / D) : 0.0f;
+    float* yb = ybar + (size_t)p * 2 * m;
+    float* gab = gabar + (size_t)p * m;
+    float* gbb = gbbar + (size_t)p * m;
+    for (int i = tid; i < m; i += kST) {
+        const float pi = alpha1 * sm.z[i];
+        const float rbt = ga[i] * pi, rbb = gb[i] * pi;
+        yb[i] += rbt;
+        yb[m + i] += rbb;
+        const float ui = ru[i];
+        gab[i] += rr[i] * pi - rbt * rq[i] + c3 * ga[i] * ui * ui;
+        gbb[i] += rr[m + i] * pi - rbb * rq[i] + c3 * gb[i] * ui * ui;
+        vv[(size_t)p * m + i] = fmaf(ga[i], rbt, gb[i] * rbb);
+    }
+    // the base of xbar_t: v on G_{t+1}, zero elsewhere
+    float* vb = vbase + (size_t)p * n;
+    for (int j = tid; j < n; j += kST) vb[j] = 0.0f;
+    __syncthreads();
+    for (int q = tid; q < s; q += kST) vb[sm.sel[q]] = sm.val[q];
+}
+
+// x_0 = 0: q = 0, r = y, v = a y_top + b y_bot; a valid placeholder support
+__global__ void __launch_bounds__(256) k_ud_init(UdArgs a)
+{
+    const int p = blockIdx.x, m = a.m;
+    const float* y = a.y + (size_t)p * 2 * m;
+    for (int i = threadIdx.x; i < m; i += 256) {
+        a.q[(size_t)p * m + i] = 0.0f;
+        a.r[(size_t)p * 2 * m + i] = y[i];
+        a.r[(size_t)p * 2 * m + m + i] = y[m + i];
+        a.vin[(size_t)p * m + i] = fmaf(a.ga[(size_t)p * m + i], y[i], a.gb[(size_t)p * m + i] * y[m + i]);
+    }
+    for (int q = threadIdx.x; q < a.s; q += 256) {
+        a.sup[(size_t)p * a.s + q] = q;
+        a.xs[(size_t)p * a.s + q] = 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ud_xout(UdArgs a, float* X)
+{
+    const int p = blockIdx.x;
+    float* x = X + (size_t)p * a.n;
+    for (int j = threadIdx.x; j < a.n; j += 256) x[j] = 0.0f;
+    __syncthreads();
+    for (int q = threadIdx.x; q < a.s; q += 256) x[a.sup[(size_t)p * a.s + q]] = a.xs[(size_t)p * a.s + q];
+}
+
+template <typename F>
+cudaError_t set_smem(F* fn, size_t bytes)
+{
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+}
+
+}  // namespace
+
+size_t ud_fwd_smem(int n, int mk, int s) { return msm_bytes(n, mk, s); }
+size_t ud_bwd_smem(int n, int mk, int s) { return msm_bytes(n, mk, s) + (size_t)mk * 4 + (size_t)s * 4 + 64; }
+
+cudaError_t launch_ud_init(const UdArgs& a, cudaStream_t s)
+{
+    k_ud_init<<<a.P, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ud_xout(const UdArgs& a, float* X, cudaStream_t s)
+{
+    k_ud_xout<<<a.P, 256, 0, s>>>(a, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ud_gemvt(const qiht_codes* Qs, int bits, const float* v, const float* base, float sign, float* out,
+                            int P, int m, int n, int ldw, cudaStream_t s)
+{
+    const int G = 32 / bits;
+    const size_t smem = (size_t)ldw * G * 4;
+    const dim3 grid((unsigned)((n + kUdWarps * kUdColsPerWarp - 1) / (kUdWarps * kUdColsPerWarp)), (unsigned)P);
+    cudaError_t e;
+    switch (bits) {
+    case 8:
+        if ((e = set_smem(k_ud_gemvt<8>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<8><<<grid, 256, smem, s>>>(Qs, v, base, sign, out, m, n);
+        break;
+    case 4:
+        if ((e = set_smem(k_ud_gemvt<4>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<4><<<grid, 256, smem, s>>>(Qs, v, base, sign, out, m, n);
+        break;
+    default:
+        if ((e = set_smem(k_ud_gemvt<2>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<2><<<grid, 256, smem, s>>>(Qs, v, base, sign, out, m, n);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ud_fwd(const UdArgs& a, int bits, cudaStream_t s)
+{
+    const size_t smem = ud_fwd_smem(a.n, a.mk, a.s);
+    cudaError_t e;
+    switch (bits) {
+    case 8:
+        if ((e = set_smem(k_ud_fwd<8>, smem)) != cudaSuccess) return e;
+        k_ud_fwd<8><<<a.P, kST, smem, s>>>(a);
+        break;
+    case 4:
+        if ((e = set_smem(k_ud_fwd<4>, smem)) != cudaSuccess) return e;
+        k_ud_fwd<4><<<a.P, kST, smem, s>>>(a);
+        break;
+    default:
+        if ((e = set_smem(k_ud_fwd<2>, smem)) != cudaSuccess) return e;
+        k_ud_fwd<2><<<a.P, kST, smem, s>>>(a);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ud_bwd(const UdArgs& a, int bits, const float* xbar, float* vbase, float* vv, float* ybar,
+                          float* gabar, float* gbbar, cudaStream_t s)
+{
+    const size_t smem = ud_bwd_smem(a.n, a.mk, a.s);
+    cudaError_t e;
+    switch (bits) {
+    case 8:
+        if ((e = set_smem(k_ud_bwd<8>, smem)) != cudaSuccess) return e;
+        k_ud_bwd<8><<<a.P, kST, smem, s>>>(a, xbar, vbase, vv, ybar, gabar, gbbar);
+        break;
+    case 4:
+        if ((e = set_smem(k_ud_bwd<4>, smem)) != cudaSuccess) return e;
+        k_ud_bwd<4><<<a.P, kST, smem, s>>>(a, xbar, vbase, vv, ybar, gabar, gbbar);
+        break;
+    default:
+        if ((e = set_smem(k_ud_bwd<2>, smem)) != cudaSuccess) return e;
+        k_ud_bwd<2><<<a.P, kST, smem, s>>>(a, xbar, vbase, vv, ybar, gabar, gbbar);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qiht
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+using namespace qiht;
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int ud_ckpt_every(int K)
+{
+    int c = 1;
+    while (c * c < K) ++c;
+    return c;
+}
+
+struct UdLayout {
+    size_t q1, q2, sup, xs, vin, r, q, h, ck, rec_r, rec_q, rec_u, rec_G, rec_Gn, rec_hG, rec_hGn, rec_sc, xa, xb,
+        vbase, vv, total;
+    int c, nseg;
+    size_t ck_stride;           // bytes of one checkpoint
+};
+
+UdLayout ud_layout(int P, int m, int n, int s, int K)
+{
+    UdLayout L{};
+    L.c = ud_ckpt_every(K > 0 ? K : 1);
+    L.nseg = (K + L.c - 1) / L.c;
+    const size_t Ps = (size_t)P * s, Pm = (size_t)P * m, Pn = (size_t)P * n, Pc = (size_t)P * L.c;
+    size_t o = 0;
+    L.q1 = o; o += al256((size_t)P * sizeof(qiht_codes));
+    L.q2 = o; o += al256((size_t)P * sizeof(qiht_codes));
+    L.sup = o; o += al256(Ps * 4);
+    L.xs = o; o += al256(Ps * 4);
+    L.vin = o; o += al256(Pm * 4);
+    L.r = o; o += al256(Pm * 8);
+    L.q = o; o += al256(Pm * 4);
+    L.h = o; o += al256(Pn * 4);
+    L.ck_stride = al256(Ps * 4) * 2 + al256(Pm * 4) * 2 + al256(Pm * 8);
+    L.ck = o; o += L.ck_stride * (size_t)(L.nseg > 0 ? L.nseg : 1);
+    L.rec_r = o; o += al256(Pc * m * 8);
+    L.rec_q = o; o += al256(Pc * m * 4);
+    L.rec_u = o; o += al256(Pc * m * 4);
+    L.rec_G = o; o += al256(Pc * s * 4);
+    L.rec_Gn = o; o += al256(Pc * s * 4);
+    L.rec_hG = o; o += al256(Pc * s * 4);
+    L.rec_hGn = o; o += al256(Pc * s * 4);
+    L.rec_sc = o; o += al256(Pc * 4 * 8);
+    L.xa = o; o += al256(Pn * 4);
+    L.xb = o; o += al256(Pn * 4);
+    L.vbase = o; o += al256(Pn * 4);
+    L.vv = o; o += al256(Pm * 4);
+    L.total = o;
+    return L;
+}
+
+bool ud_sizes_ok(int P, int m, int n, int s, int K)
+{
+    return P >= 1 && m >= 1 && n >= 1 && s >= 1 && s <= m && s <= n && K >= 0 && m <= QIHT_MULTI_MAX_ROWS &&
+           n <= QIHT_MULTI_MAX_COLS && s <= QIHT_MULTI_MAX_S;
+}
+
+#define UCK(x)                                \
+    do {                                      \
+        cudaError_t ck_e_ = (x);              \
+        if (ck_e_ != cudaSuccess) {           \
+            note_cuda_error(#x, ck_e_);       \
+            return QIHT_ERR_CUDA;             \
+        }                                     \
+    } while (0)
+
+qiht_status ud_check(const qiht_codes* Q1, const qiht_codes* Q2, int P, int s, int K)
+{
+    if (!Q1 || !Q2 || P < 1) return QIHT_ERR_ARG;
+    const int m = Q1[0].rows, n = Q1[0].cols, bits = Q1[0].bits;
+    for (int p = 0; p < P; ++p) {
+        qiht_status e = check_codes(&Q1[p]);
+        if (e != QIHT_OK) return e;
+        if ((e = check_codes(&Q2[p])) != QIHT_OK) return e;
+        if (Q1[p].rows != m || Q1[p].cols != n || Q2[p].rows != m || Q2[p].cols != n) return QIHT_ERR_ARG;
+        if (Q1[p].bits != bits || Q2[p].bits != bits) return QIHT_ERR_ARG;
+    }
+    if (!ud_sizes_ok(P, m, n, s, K)) return QIHT_ERR_ARG;
+    const int mk = mrhs_pad_rows(m);
+    if (ud_bwd_smem(n, mk, s) > (size_t)227 * 1024 - 2048) return QIHT_ERR_ARG;
+    return QIHT_OK;
+}
+
+// the state arrays of checkpoint k (sup, xs, vin, q, r)
+struct UdCk {
+    int32_t* sup;
+    float *xs, *vin, *q, *r;
+};
+
+UdCk ud_ck(char* w, const UdLayout& L, int P, int m, int s, int k)
+{
+    char* b = w + L.ck + L.ck_stride * (size_t)k;
+    const size_t Ps = (size_t)P * s, Pm = (size_t)P * m;
+    UdCk c;
+    c.sup = reinterpret_cast<int32_t*>(b);
+    c.xs = reinterpret_cast<float*>(b + al256(Ps * 4));
+    c.vin = reinterpret_cast<float*>(b + al256(Ps * 4) * 2);
+    c.q = reinterpret_cast<float*>(b + al256(Ps * 4) * 2 + al256(Pm * 4));
+    c.r = reinterpret_cast<float*>(b + al256(Ps * 4) * 2 + al256(Pm * 4) * 2);
+    return c;
+}
+
+cudaError_t ud_copy_state(const UdArgs& a, const UdCk& c, bool save, cudaStream_t s)
+{
+    const size_t Ps = (size_t)a.P * a.s * 4, Pm = (size_t)a.P * a.m * 4;
+    auto cp = [&](void* ck, void* st, size_t bytes) {
+        return save ? cudaMemcpyAsync(ck, st, bytes, cudaMemcpyDeviceToDevice, s)
+                    : cudaMemcpyAsync(st, ck, bytes, cudaMemcpyDeviceToDevice, s);
+    };
+    cudaError_t e;
+    if ((e = cp(c.sup, a.sup, Ps)) != cudaSuccess) return e;
+    if ((e = cp(c.xs, a.xs, Ps)) != cudaSuccess) return e;
+    if ((e = cp(c.vin, a.vin, Pm)) != cudaSuccess) return e;
+    if ((e = cp(c.q, a.q, Pm)) != cudaSuccess) return e;
+    return cp(c.r, a.r, 2 * Pm);
+}
+
+UdArgs ud_args(char* w, const UdLayout& L, const qiht_codes* Q1, int P, int s, const float* y, const float* ga,
+               const float* gb)
+{
+    UdArgs a{};
+    a.q1 = reinterpret_cast<const qiht_codes*>(w + L.q1);
+    a.q2 = reinterpret_cast<const qiht_codes*>(w + L.q2);
+    a.y = y;
+    a.ga = ga;
+    a.gb = gb;
+    a.P = P;
+    a.m = Q1[0].rows;
+    a.n = Q1[0].cols;
+    a.s = s;
+    a.mk = mrhs_pad_rows(a.m);
+    a.sup = reinterpret_cast<int32_t*>(w + L.sup);
+    a.xs = reinterpret_cast<float*>(w + L.xs);
+    a.vin = reinterpret_cast<float*>(w + L.vin);
+    a.r = reinterpret_cast<float*>(w + L.r);
+    a.q = reinterpret_cast<float*>(w + L.q);
+    a.h = reinterpret_cast<float*>(w + L.h);
+    a.c = L.c;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qiht_unrolled_workspace_size(int32_t nprob, int32_t m, int32_t n, int32_t s, int32_t K)
+{
+    if (!ud_sizes_ok(nprob, m, n, s, K)) return 0;
+    return ud_layout(nprob, m, n, s, K).total;
+}
+
+qiht_status qiht_unrolled_forward(const qiht_codes* Q1, const qiht_codes* Q2, int32_t nprob, const float* y,
+                                  const float* gain_re, const float* gain_im, int32_t s, int32_t K, float* X,
+                                  void* workspace, size_t workspace_bytes, qiht_stream_t stream)
+{
+    qiht_status e = ud_check(Q1, Q2, nprob, s, K);
+    if (e != QIHT_OK) return e;
+    if (!y || !gain_re || !gain_im || !X) return QIHT_ERR_ARG;
+    const int m = Q1[0].rows, n = Q1[0].cols, bits = Q1[0].bits;
+    const UdLayout L = ud_layout(nprob, m, n, s, K);
+    if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return QIHT_ERR_WORKSPACE;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    char* w = reinterpret_cast<char*>(workspace);
+    UCK(cudaMemcpyAsync(w + L.q1, Q1, (size_t)nprob * sizeof(qiht_codes), cudaMemcpyHostToDevice, cs));
+    UCK(cudaMemcpyAsync(w + L.q2, Q2, (size_t)nprob * sizeof(qiht_codes), cudaMemcpyHostToDevice, cs));
+    UdArgs a = ud_args(w, L, Q1, nprob, s, y, gain_re, gain_im);
+    UCK(launch_ud_init(a, cs));
+    for (int t = 0; t < K; ++t) {
+        if (t % L.c == 0) UCK(ud_copy_state(a, ud_ck(w, L, nprob, m, s, t / L.c), true, cs));
+        a.t = t;
+        UCK(launch_ud_gemvt(a.q1, bits, a.vin, nullptr, 1.0f, a.h, nprob, m, n, Q1[0].ld_words, cs));
+        UCK(launch_ud_fwd(a, bits, cs));
+    }
+    UCK(launch_ud_xout(a, X, cs));
+    return QIHT_OK;
+}
+
+qiht_status qiht_unrolled_backward(const qiht_codes* Q1, const qiht_codes* Q2, int32_t nprob, const float* y,
+                                   const float* gain_re, const float* gain_im, int32_t s, int32_t K, const float* Xbar,
+                                   float* ybar, float* gain_re_bar, float* gain_im_bar, void* workspace,
+                                   size_t workspace_bytes, qiht_stream_t stream)
+{
+    qiht_status e = ud_check(Q1, Q2, nprob, s, K);
+    if (e != QIHT_OK) return e;
+    if (!y || !gain_re || !gain_im || !Xbar || !ybar || !gain_re_bar || !gain_im_bar) return QIHT_ERR_ARG;
+    const int m = Q1[0].rows, n = Q1[0].cols, bits = Q1[0].bits;
+    const UdLayout L = ud_layout(nprob, m, n, s, K);
+    if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return QIHT_ERR_WORKSPACE;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    char* w = reinterpret_cast<char*>(workspace);
+    UCK(cudaMemcpyAsync(w + L.q1, Q1, (size_t)nprob * sizeof(qiht_codes), cudaMemcpyHostToDevice, cs));
+    UCK(cudaMemcpyAsync(w + L.q2, Q2, (size_t)nprob * sizeof(qiht_codes), cudaMemcpyHostToDevice, cs));
+    UdArgs a = ud_args(w, L, Q1, nprob, s, y, gain_re, gain_im);
+    a.rec_r = reinterpret_cast<float*>(w + L.rec_r);
+    a.rec_q = reinterpret_cast<float*>(w + L.rec_q);
+    a.rec_u = reinterpret_cast<float*>(w + L.rec_u);
+    a.rec_G = reinterpret_cast<int32_t*>(w + L.rec_G);
+    a.rec_Gn = reinterpret_cast<int32_t*>(w + L.rec_Gn);
+    a.rec_hG = reinterpret_cast<float*>(w + L.rec_hG);
+    a.rec_hGn = reinterpret_cast<float*>(w + L.rec_hGn);
+    a.rec_sc = reinterpret_cast<double*>(w + L.rec_sc);
+    float* xa = reinterpret_cast<float*>(w + L.xa);
+    float* xb = reinterpret_cast<float*>(w + L.xb);
+    float* vbase = reinterpret_cast<float*>(w + L.vbase);
+    float* vv = reinterpret_cast<float*>(w + L.vv);
+    const size_t Pn = (size_t)nprob * n, Pm = (size_t)nprob * m;
+    UCK(cudaMemsetAsync(ybar, 0, Pm * 2 * 4, cs));
+    UCK(cudaMemsetAsync(gain_re_bar, 0, Pm * 4, cs));
+    UCK(cudaMemsetAsync(gain_im_bar, 0, Pm * 4, cs));
+    UCK(cudaMemcpyAsync(xa, Xbar, Pn * 4, cudaMemcpyDeviceToDevice, cs));
+    for (int seg = L.nseg - 1; seg >= 0; --seg) {
+        const int t0 = seg * L.c, t1 = (t0 + L.c < K) ? t0 + L.c : K;
+        // recompute the segment from its checkpoint, recording every step
+        UCK(ud_copy_state(a, ud_ck(w, L, nprob, m, s, seg), false, cs));
+        for (int t = t0; t < t1; ++t) {
+            a.t = t;
+            a.slot = t - t0;
+            UCK(launch_ud_gemvt(a.q1, bits, a.vin, nullptr, 1.0f, a.h, nprob, m, n, Q1[0].ld_words, cs));
+            UCK(launch_ud_fwd(a, bits, cs));
+        }
+        // reverse steps: xbar_t = v - A2^T rbar
+        for (int t = t1 - 1; t >= t0; --t) {
+            a.t = t;
+            a.slot = t - t0;
+            UCK(launch_ud_bwd(a, bits, xa, vbase, vv, ybar, gain_re_bar, gain_im_bar, cs));
+            UCK(launch_ud_gemvt(a.q2, bits, vv, vbase, -1.0f, xb, nprob, m, n, Q1[0].ld_words, cs));
+            float* tmp = xa;
+            xa = xb;
+            xb = tmp;
+        }
+    }
+    return QIHT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+"""K unrolled QIHT iterations and their adjoint on the GPU (qiht_unrolled_forward/_backward)
+against the CPU oracle (oracle/unrolled.py, whose adjoint is pinned by finite differences).
+
+Both sides use the same quantized codes (bit-exact, see test_gpu_quantize.py). Tolerances:
+x_K within 1e-4 relative L2 (FP32 products of s columns, FP64 sums), with identical supports;
+the gradients within 2e-3 relative L2 (FP32 products in every one of the K adjoint steps and
+the recomputed forward). Problems whose selections the oracle finds ambiguous (relative gap
+between the s-th and (s+1)-th magnitude below 1e-5) are excluded from the support check."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import unrolled
+import paper_1802_04907_gb300 as q
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems(P, m, n, s, bits, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for p in range(P):
+        phi = (rng.standard_normal((m, n)) / np.sqrt(m)).astype(np.float32)
+        x = np.zeros(n)
+        x[rng.choice(n, s, replace=False)] = rng.standard_normal(s)
+        mag, ph = rng.uniform(0.9, 1.1, m), rng.uniform(-0.1, 0.1, m)
+        a, b = mag * np.cos(ph), mag * np.sin(ph)
+        clean = unrolled.stacked(phi.astype(np.float64), a, b) @ x
+        y = clean + np.sqrt(clean @ clean / (2 * m * 1e3)) * rng.standard_normal(2 * m)
+        out.append((phi, x, a.astype(np.float32), b.astype(np.float32), y.astype(np.float32)))
+    return out
+
+
+def _setup(P, m, n, s, bits, K, seed):
+    probs = _problems(P, m, n, s, bits, seed)
+    Q1s, Q2s, refs = [], [], []
+    for p, (phi, x, a, b, y) in enumerate(probs):
+        t = torch.from_numpy(phi).cuda()
+        q1, q2 = q.quantize_pair(t, bits, 100 + p, q.STREAM_Q1, q.STREAM_Q2)
+        Q1s.append(q1)
+        Q2s.append(q2)
+        c1, sc = oracle.quantize(phi, bits, 100 + p, 0)
+        c2, _ = oracle.quantize(phi, bits, 100 + p, 1, sc)
+        refs.append((oracle.dequantize(c1, bits, sc), oracle.dequantize(c2, bits, sc)))
+    Y = torch.from_numpy(np.stack([pr[4] for pr in probs])).cuda()
+    GA = torch.from_numpy(np.stack([pr[2] for pr in probs])).cuda()
+    GB = torch.from_numpy(np.stack([pr[3] for pr in probs])).cuda()
+    XT = torch.from_numpy(np.stack([pr[1] for pr in probs]).astype(np.float32)).cuda()
+    op = q.Unrolled(Q1s, Q2s, s, K)
+    return probs, refs, op, Y, GA, GB, XT
+
+
+def _min_gap(steps, s):
+    g = np.inf
+    for st in steps:
+        z = np.abs(st.x + st.mu * st.h)
+        srt = np.sort(z)[::-1]
+        if srt[s - 1] > 0:
+            g = min(g, (srt[s - 1] - srt[s]) / srt[s - 1])
+    return g
+
+
+@pytest.mark.parametrize("bits,K", [(4, 6), (8, 12), (2, 5)])
+def test_forward_and_adjoint_match_oracle(bits, K):
+    P, m, n, s = 4, 256, 1024, 12
+    probs, refs, op, Y, GA, GB, XT = _setup(P, m, n, s, bits, K, seed=bits * 10 + K)
+    X = op.forward(Y, GA, GB)
+    Xbar = 2.0 * (X - XT)
+    yb, ab, bb = op.backward(Y, GA, GB, Xbar)
+    torch.cuda.synchronize()
+    X, yb, ab, bb = (t.cpu().numpy().astype(np.float64) for t in (X, yb, ab, bb))
+    checked = 0
+    for p, (phi, x, a, b, y) in enumerate(probs):
+        P1, P2 = refs[p]
+        xK, steps = unrolled.forward(P1, P2, y, a, b, s, K)
+        if _min_gap(steps, s) < 1e-5:
+            continue
+        checked += 1
+        assert np.array_equal(np.flatnonzero(X[p]), np.flatnonzero(xK)), p
+        assert np.linalg.norm(X[p] - xK) <= 1e-4 * np.linalg.norm(xK), p
+        gy, ga, gb = unrolled.backward(P1, P2, a, b, steps, 2.0 * (xK - x))
+        for got, want, name in ((yb[p], gy, "y"), (ab[p], ga, "a"), (bb[p], gb, "b")):
+            rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
+            assert rel <= 2e-3, (p, name, rel)
+    assert checked >= 2
+
+
+def test_checkpointed_segments_long_unroll():
+    # K = 50: ceil(sqrt(50)) = 8-step segments (the last one short), each recomputed in the adjoint
+    P, m, n, s, K = 3, 192, 768, 10, 50
+    probs, refs, op, Y, GA, GB, XT = _setup(P, m, n, s, 4, K, seed=77)
+    X = op.forward(Y, GA, GB)
+    yb, ab, bb = op.backward(Y, GA, GB, 2.0 * (X - XT))
+    torch.cuda.synchronize()
+    X, yb, ab, bb = (t.cpu().numpy().astype(np.float64) for t in (X, yb, ab, bb))
+    checked = 0
+    for p, (phi, x, a, b, y) in enumerate(probs):
+        P1, P2 = refs[p]
+        xK, steps = unrolled.forward(P1, P2, y, a, b, s, K)
+        if _min_gap(steps, s) < 1e-5:
+            continue
+        checked += 1
+        assert np.linalg.norm(X[p] - xK) <= 1e-4 * np.linalg.norm(xK), p
+        gy, ga, gb = unrolled.backward(P1, P2, a, b, steps, 2.0 * (xK - x))
+        for got, want in ((yb[p], gy), (ab[p], ga), (bb[p], gb)):
+            assert np.linalg.norm(got - want) <= 5e-3 * np.linalg.norm(want), p
+    assert checked >= 1
+
+
+def test_autograd_function_and_repeat_calls():
+    P, m, n, s, K = 2, 128, 512, 8, 7
+    probs, refs, op, Y, GA, GB, XT = _setup(P, m, n, s, 8, K, seed=5)
+    y = Y.clone().requires_grad_(True)
+    ga = GA.clone().requires_grad_(True)
+    gb = GB.clone().requires_grad_(True)
+    X = q.unrolled_qiht(y, ga, gb, op)
+    loss = ((X - XT) ** 2).sum()
+    loss.backward()
+    X2 = op.forward(Y, GA, GB)
+    yb, ab, bb = op.backward(Y, GA, GB, 2.0 * (X2 - XT))
+    torch.cuda.synchronize()
+    assert torch.equal(X.detach(), X2)
+    assert torch.equal(y.grad, yb) and torch.equal(ga.grad, ab) and torch.equal(gb.grad, bb)
