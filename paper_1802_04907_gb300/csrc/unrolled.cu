@@ -31,76 +31,96 @@ using namespace cta;
 
 constexpr int kUdColsPerWarp = 8;
 constexpr int kUdWarps = 8;
+constexpr int kUdGroup = 4;                     // columns of a warp whose loads are in flight together
 
-// out[p][j] = (base ? base[p][j] : 0) + sign * alpha * sum_i (2 c_ij - (L-1)) v[p][i]
+// out[p][j] = (base ? base[p][j] : 0) + sign * alpha * sum_i (2 c_ij - (L-1)) v[p][i].
+// Lane l of a warp takes the 16-byte pieces l, l + 32, ... of every column; v sits in shared
+// memory transposed by piece (entry k of piece w at k * npieces + w), so the lanes of a warp
+// read consecutive words. A code c becomes the float 2c - (L-1) through the exact bit
+// pattern of 2^23 + c.
 template <int BITS>
 __global__ void __launch_bounds__(256) k_ud_gemvt(const qiht_codes* __restrict__ Qs, const float* __restrict__ v,
                                                   const float* __restrict__ base, float sign, float* __restrict__ out,
                                                   int m, int n)
 {
     constexpr int G = 32 / BITS;
+    constexpr int RP = 4 * G;                   // rows per 16-byte piece
     constexpr uint32_t MASK = (1u << BITS) - 1;
-    extern __shared__ float vs[];               // v of this problem, padded to the column length
+    extern __shared__ float vT[];
     const int p = blockIdx.y;
     const qiht_codes Q = Qs[p];
-    const int ld = Q.ld_words;
-    const int lm1 = grid_levels(BITS, Q.levels) - 1;
-    const float alpha = (float)((double)(*Q.scale) / (double)lm1);
+    const int ld = Q.ld_words, np4 = ld / 4;
+    const float lm1f = (float)(grid_levels(BITS, Q.levels) - 1);
+    const float alpha = (float)((double)(*Q.scale) / (double)(grid_levels(BITS, Q.levels) - 1));
     const float* vp = v + (size_t)p * m;
-    for (int i = threadIdx.x; i < ld * G; i += 256) vs[i] = i < m ? vp[i] : 0.0f;
+    for (int i = threadIdx.x; i < np4 * RP; i += 256) {
+        const int w4 = i / RP, k = i % RP;
+        vT[k * np4 + w4] = i < m ? vp[i] : 0.0f;
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j0 = (blockIdx.x * kUdWarps + warp) * kUdColsPerWarp;
-    for (int jj = 0; jj < kUdColsPerWarp; ++jj) {
-        const int j = j0 + jj;
-        if (j >= n) break;
-        const uint4* col = reinterpret_cast<const uint4*>(Q.words + (size_t)j * ld);
-        float acc = 0.0f;
-        for (int w4 = lane; w4 < ld / 4; w4 += 32) {
-            const uint4 c4 = __ldg(col + w4);
-            const uint32_t wd[4] = {c4.x, c4.y, c4.z, c4.w};
+    for (int jg = 0; jg < kUdColsPerWarp; jg += kUdGroup) {
+        float acc[kUdGroup];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float* vr = vs + (size_t)(w4 * 4 + u) * G;
+        for (int c = 0; c < kUdGroup; ++c) acc[c] = 0.0f;
+        for (int w4 = lane; w4 < np4; w4 += 32) {
+            uint4 c4[kUdGroup];
+#pragma unroll
+            for (int c = 0; c < kUdGroup; ++c) {
+                const int j = j0 + jg + c;
+                c4[c] = j < n ? __ldg(reinterpret_cast<const uint4*>(Q.words + (size_t)j * ld) + w4)
+                              : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
-                    const int code = (int)((wd[u] >> (8 * (k & 3) + BITS * (k >> 2))) & MASK);
-                    acc = fmaf((float)(2 * code - lm1), vr[k], acc);
+                    const float vk = vT[(u * G + k) * np4 + w4];
+#pragma unroll
+                    for (int c = 0; c < kUdGroup; ++c) {
+                        const uint32_t wd = u == 0 ? c4[c].x : u == 1 ? c4[c].y : u == 2 ? c4[c].z : c4[c].w;
+                        const uint32_t code = (wd >> (8 * (k & 3) + BITS * (k >> 2))) & MASK;
+                        const float cf = __uint_as_float(0x4B000000u | code) - 8388608.0f;   // exact
+                        acc[c] = fmaf(fmaf(cf, 2.0f, -lm1f), vk, acc[c]);
+                    }
                 }
-            }
         }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            const float b0 = base ? base[(size_t)p * n + j] : 0.0f;
-            out[(size_t)p * n + j] = fmaf(sign * alpha, acc, b0);
+        for (int c = 0; c < kUdGroup; ++c) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+            const int j = j0 + jg + c;
+            if (lane == 0 && j < n) {
+                const float b0 = base ? base[(size_t)p * n + j] : 0.0f;
+                out[(size_t)p * n + j] = fmaf(sign * alpha, acc[c], b0);
+            }
         }
     }
 }
 
-// dot products of the columns in `list` with vec (m entries, shared memory): out[e] =
-// alpha * sum_i (2 c_{i, list_e} - (L-1)) vec_i, one warp per column
+// dot products of the columns in `list` with a vector held transposed in shared memory
+// (entry k of word w at k * ld + w, zero past the rows): out[e] = alpha * sum_i
+// (2 c_{i, list_e} - (L-1)) vec_i, one warp per column, one 32-bit word per lane
 template <int BITS>
-__device__ void ucol_dots(const Codes& Q, const int* list, int count, const float* vec, float* out)
+__device__ void ucol_dots(const Codes& Q, const int* list, int count, const float* vecT, float* out)
 {
     constexpr int G = 32 / BITS;
     constexpr uint32_t MASK = (1u << BITS) - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float alpha = (float)((double)(*Q.scale) / (double)Q.lm1);
+    const float lm1f = (float)Q.lm1;
     for (int e = warp; e < count; e += kST / 32) {
-        const uint4* col = reinterpret_cast<const uint4*>(Q.words + (size_t)list[e] * Q.ld);
+        const uint32_t* col = Q.words + (size_t)list[e] * Q.ld;
         float acc = 0.0f;
-        for (int w4 = lane; w4 < Q.ld / 4; w4 += 32) {
-            const uint4 c4 = __ldg(col + w4);
-            const uint32_t wd[4] = {c4.x, c4.y, c4.z, c4.w};
+        for (int w = lane; w < Q.ld; w += 32) {
+            const uint32_t wd = __ldg(col + w);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    const int row = (w4 * 4 + u) * G + k;
-                    const int code = (int)((wd[u] >> (8 * (k & 3) + BITS * (k >> 2))) & MASK);
-                    acc = fmaf((float)(2 * code - Q.lm1), row < Q.rows ? vec[row] : 0.0f, acc);
-                }
+            for (int k = 0; k < G; ++k) {
+                const uint32_t code = (wd >> (8 * (k & 3) + BITS * (k >> 2))) & MASK;
+                const float cf = __uint_as_float(0x4B000000u | code) - 8388608.0f;
+                acc = fmaf(fmaf(cf, 2.0f, -lm1f), vecT[k * Q.ld + w], acc);
+            }
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -234,8 +254,8 @@ __global__ void __launch_bounds__(kST, 1) k_ud_bwd(UdArgs a, const float* __rest
     const int p = blockIdx.x, tid = threadIdx.x;
     const int m = a.m, n = a.n, s = a.s;
     const MSm sm = msm_layout(smem, n, a.mk, s);
-    float* w2 = reinterpret_cast<float*>(smem + msm_bytes(n, a.mk, s));     // m: (a^2 + b^2) u
-    float* cG = w2 + a.mk;                                                   // s: (A2^T A2 P h) on G
+    float* w2 = reinterpret_cast<float*>(smem + msm_bytes(n, a.mk, s));     // (a^2 + b^2) u, transposed by word
+    float* cG = w2 + a.mk + 64;                                              // s: (A2^T A2 P h) on G
     const Codes Q1 = codes_of(a.q1[p]);
     const Codes Q2 = codes_of(a.q2[p]);
     const float* ga = a.ga + (size_t)p * m;
@@ -271,9 +291,13 @@ __global__ void __launch_bounds__(kST, 1) k_ud_bwd(UdArgs a, const float* __rest
         if (tid == 0) us.mubar = mb;
     }
     // c = (A2^T A2 P h) on G_t = Phi2^T ((a^2 + b^2) u) there
-    for (int i = tid; i < a.mk; i += kST) {
-        const float g2 = i < m ? fmaf(ga[i], ga[i], gb[i] * gb[i]) : 0.0f;
-        w2[i] = i < m ? g2 * ru[i] : 0.0f;
+    {
+        constexpr int G = 32 / BITS;
+        const int ldw = Q2.ld;
+        for (int i = tid; i < ldw * G; i += kST) {
+            const float g2 = i < m ? fmaf(ga[i], ga[i], gb[i] * gb[i]) : 0.0f;
+            w2[(i % G) * ldw + i / G] = i < m ? g2 * ru[i] : 0.0f;
+        }
     }
     __syncthreads();
     ucol_dots<BITS>(Q2, sm.sup, s, w2, cG);
@@ -378,7 +402,7 @@ cudaError_t set_smem(F* fn, size_t bytes)
 }  // namespace
 
 size_t ud_fwd_smem(int n, int mk, int s) { return msm_bytes(n, mk, s); }
-size_t ud_bwd_smem(int n, int mk, int s) { return msm_bytes(n, mk, s) + (size_t)mk * 4 + (size_t)s * 4 + 64; }
+size_t ud_bwd_smem(int n, int mk, int s) { return msm_bytes(n, mk, s) + (size_t)(mk + 64) * 4 + (size_t)s * 4 + 64; }
 
 cudaError_t launch_ud_init(const UdArgs& a, cudaStream_t s)
 {
@@ -396,7 +420,7 @@ cudaError_t launch_ud_gemvt(const qiht_codes* Qs, int bits, const float* v, cons
                             int P, int m, int n, int ldw, cudaStream_t s)
 {
     const int G = 32 / bits;
-    const size_t smem = (size_t)ldw * G * 4;
+    const size_t smem = (size_t)ldw * G * 4;          // v transposed by 16-byte piece
     const dim3 grid((unsigned)((n + kUdWarps * kUdColsPerWarp - 1) / (kUdWarps * kUdColsPerWarp)), (unsigned)P);
     cudaError_t e;
     switch (bits) {
