@@ -192,20 +192,25 @@ struct BShared {          // small scalars shared by the CTA
 };
 
 // g = Q1^T r for the whole problem, inside the CTA (the single-solve arithmetic): the
-// residual becomes 24-bit fixed point in three byte planes in shared memory; warp w
-// takes columns w, w + 32, ...; a lane walks its 16-byte pieces of the warp's column
-// sequence kBItems at a time (that many loads in flight), multiplies the codes by dp4a and the
-// warp reduces each finished column's integer sums.
-template <int BITS>
+// residual becomes 24-bit fixed point in three byte planes in shared memory; each warp takes
+// columns w, w + 32, ... in groups of 32 / LPC, one group of LPC lanes per column; a lane walks
+// its 16-byte pieces (lane % LPC, + LPC, ...) of its columns kBItems at a time (that many loads
+// in flight), multiplies the codes by dp4a, and each lane group reduces its finished column's
+// integer sums. LPC (lanes per column) is the tile shape the batch's autotuner picks per
+// problem size (one kernel per shape): short columns (few 16-byte pieces) keep more lanes
+// busy with small groups.
+template <int BITS, int LPC>
 __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;
+    constexpr int CPW = 32 / LPC;                      // columns a warp works on at once
     constexpr uint32_t MASK = 0x01010101u * (uint32_t)((1 << BITS) - 1);
     const int m = Q.rows, n = Q.cols, ld = Q.ld_words;
     const long long lm1 = grid_levels(BITS, Q.levels) - 1;   // levels - 1 of the grid
     const int P = ld / 4;                              // 16-byte pieces per column
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sub = lane / LPC, sl = lane % LPC;
 
     unsigned mx = 0;
     for (int i = tid; i < m; i += kBT) mx = max(mx, __float_as_uint(sm.r[i]) & 0x7fffffffu);
@@ -235,10 +240,12 @@ __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
     const uint4* L1 = L0 + E * P;
     const uint4* L2 = L0 + 2 * E * P;
 
-    // the warp's items: column k (k-th of its columns) and piece lane + 32 t
-    const int ppl = (P + 31) / 32;                     // pieces per lane and column
+    // the warp's items: column group kg (columns warp + kBWarps (kg CPW + sub)) and piece
+    // sl + LPC t of this lane's column
+    const int ppl = (P + LPC - 1) / LPC;               // pieces per lane and column
     const int ncol_w = warp < n ? (n - warp + kBWarps - 1) / kBWarps : 0;
-    const int nitem = ncol_w * ppl;
+    const int ngrp = (ncol_w + CPW - 1) / CPW;
+    const int nitem = ngrp * ppl;
     uint32_t s0[E], s1[E];
     int32_t s2[E];
 #pragma unroll
@@ -248,10 +255,11 @@ __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
 #pragma unroll
         for (int u = 0; u < kBItems; ++u) {
             const int it = i0 + u;
-            const int kcol = it / ppl, t = it - kcol * ppl;
-            const int piece = lane + 32 * t;
-            const int j = warp + kcol * kBWarps;
-            if (it < nitem && piece < P)
+            const int kg = it / ppl, t = it - kg * ppl;
+            const int piece = sl + LPC * t;
+            const int kc = kg * CPW + sub;
+            const int j = warp + kc * kBWarps;
+            if (it < nitem && piece < P && kc < ncol_w)
                 cv[u] = __ldg(reinterpret_cast<const uint4*>(Q.words + (size_t)j * ld) + piece);
             else
                 cv[u] = make_uint4(0u, 0u, 0u, 0u);
@@ -260,8 +268,8 @@ __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
         for (int u = 0; u < kBItems; ++u) {
             const int it = i0 + u;
             if (it >= nitem) break;                    // uniform within the warp
-            const int kcol = it / ppl, t = it - kcol * ppl;
-            const int piece = min(lane + 32 * t, P - 1);   // lanes past P hold zero codes
+            const int kg = it / ppl, t = it - kg * ppl;
+            const int piece = min(sl + LPC * t, P - 1);    // lanes past P hold zero codes
             const uint32_t wv[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
 #pragma unroll
             for (int q = 0; q < E; ++q) {
@@ -280,19 +288,31 @@ __device__ void bgemv_t(const qiht_codes& Q, const BSm& sm, BShared& sh)
                     s2[k] = bdp4a_us(x, y2[tt], s2[k]);
                 }
             }
-            if (t == ppl - 1) {                        // the column is complete
+            if (t == ppl - 1) {                        // the group's columns are complete
                 long long S = 0;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
-                    const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[k]);
-                    const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[k]);
-                    const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[k]);
-                    S += (t0 + (t1 << 8) + (t2 << 16)) >> (BITS * k);
+                    uint32_t t0 = s0[k], t1 = s1[k];
+                    int32_t t2 = s2[k];
+                    if (LPC == 32) {                   // the whole warp: one reduction instruction
+                        t0 = __reduce_add_sync(0xffffffffu, t0);
+                        t1 = __reduce_add_sync(0xffffffffu, t1);
+                        t2 = __reduce_add_sync(0xffffffffu, t2);
+                    } else {
+#pragma unroll
+                        for (int o = LPC / 2; o; o >>= 1) {   // exact: the sums stay below 2^32
+                            t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+                            t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+                            t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+                        }
+                    }
+                    S += ((long long)t0 + ((long long)t1 << 8) + ((long long)t2 << 16)) >> (BITS * k);
                     s0[k] = 0; s1[k] = 0; s2[k] = 0;
                 }
-                if (lane == 0) {
+                const int kc = kg * CPW + sub;
+                if (sl == 0 && kc < ncol_w) {
                     const long long T = 2 * S - R;
-                    sm.g[warp + kcol * kBWarps] = (float)((double)T * outscale);
+                    sm.g[warp + kc * kBWarps] = (float)((double)T * outscale);
                 }
             }
         }
@@ -484,7 +504,7 @@ __device__ int bselect(int n, int s, float muf, const BSm& sm, BShared& sh, int*
     return diff;
 }
 
-template <int BITS>
+template <int BITS, int LPC>
 __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc, int max_bt, const BSm& sm,
                           BShared& sh)
 {
@@ -521,7 +541,7 @@ __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc
     double mu_acc = 0.0;
     int uc = 0;
     if (finite) {
-        bgemv_t<BITS>(P.Q1, sm, sh);
+        bgemv_t<BITS, LPC>(P.Q1, sm, sh);
         // initial support: H_s(g)
         const int sel0 = bselect(n, s, 1.0f, sm, sh, &uc, false);   // x = 0: the keys are |g|
         if (sel0 < 0) {
@@ -622,7 +642,7 @@ __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc
         changes += changed;
         mu_acc = sh.mu;
         if (!isfinite(resid2)) { status = QIHT_ERR_NONFINITE; break; }
-        if (it < iters) bgemv_t<BITS>(P.Q1, sm, sh);
+        if (it < iters) bgemv_t<BITS, LPC>(P.Q1, sm, sh);
     }
     // outputs
     for (int j = tid; j < n; j += kBT) P.x[j] = sm.x[j];
@@ -642,7 +662,7 @@ __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc
     __syncthreads();
 }
 
-template <int BITS>
+template <int BITS, int LPC>
 __global__ void __launch_bounds__(kBT, 1) k_batched(const qiht_problem* __restrict__ probs,
                                                     const int* __restrict__ order, int nprob, int iters, double kk,
                                                     double cc, int max_bt, unsigned* next)
@@ -661,7 +681,7 @@ __global__ void __launch_bounds__(kBT, 1) k_batched(const qiht_problem* __restri
         const int w = s_pid;
         __syncthreads();
         if (w >= nprob) return;
-        solve_one<BITS>(P, iters, kk, cc, max_bt, sm, sh);
+        solve_one<BITS, LPC>(P, iters, kk, cc, max_bt, sm, sh);
     }
 }
 
@@ -669,11 +689,22 @@ __global__ void __launch_bounds__(kBT, 1) k_batched(const qiht_problem* __restri
 
 size_t batched_smem() { return batched_smem_bytes(); }
 
-cudaError_t launch_batched(const qiht_problem* probs, const int* order, int nprob, int bits, int iters, double k,
-                           double c, int max_bt, unsigned* next, cudaStream_t s)
+template <int BITS>
+static void* batched_fn(int lpc)
+{
+    switch (lpc) {
+    case 4: return (void*)k_batched<BITS, 4>;
+    case 8: return (void*)k_batched<BITS, 8>;
+    case 16: return (void*)k_batched<BITS, 16>;
+    default: return (void*)k_batched<BITS, 32>;
+    }
+}
+
+cudaError_t launch_batched(const qiht_problem* probs, const int* order, int nprob, int bits, int lpc, int iters,
+                           double k, double c, int max_bt, unsigned* next, cudaStream_t s)
 {
     const size_t smem = batched_smem_bytes();
-    void* fn = bits == 8 ? (void*)k_batched<8> : bits == 4 ? (void*)k_batched<4> : (void*)k_batched<2>;
+    void* fn = bits == 8 ? batched_fn<8>(lpc) : bits == 4 ? batched_fn<4>(lpc) : batched_fn<2>(lpc);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(next, 0, sizeof(unsigned), s);

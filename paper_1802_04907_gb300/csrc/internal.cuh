@@ -264,8 +264,10 @@ size_t iter_args_bytes();
 
 // Many independent problems in one persistent launch (batched.cu).
 size_t batched_smem();
-cudaError_t launch_batched(const qiht_problem* probs, const int* order, int nprob, int bits, int iters, double k,
-                           double c, int max_bt, unsigned* next, cudaStream_t s);
+// lpc: lanes per column (4, 8, 16 or 32) of the gradient product, the tile shape the
+// autotuner picked for these problems' size.
+cudaError_t launch_batched(const qiht_problem* probs, const int* order, int nprob, int bits, int lpc, int iters,
+                           double k, double c, int max_bt, unsigned* next, cudaStream_t s);
 
 // Host-side checks shared by the entry points (solve.cu).
 qiht_status check_codes(const qiht_codes* Q);   // pointers, bits, sizes, ld_words, levels, alignment

@@ -1043,6 +1043,57 @@ size_t qiht_solve_batched_workspace_size(int32_t nprob)
     return align256((size_t)nprob * sizeof(qiht_problem)) + align256((size_t)nprob * 4) + 256;
 }
 
+// ---- tile shape of the batched gradient product: lanes per column, picked per size bucket ----
+
+// bucket of a problem: ceil(log2(16-byte pieces per column of Q1))
+static int shape_bucket(const qiht_problem& P)
+{
+    const int pieces = P.Q1.ld_words / 4;
+    int b = 0;
+    while ((1 << b) < pieces) ++b;
+    return b;
+}
+
+// without tuning: the smallest group that covers a column's pieces (4 to 32 lanes)
+static int shape_default(int bucket)
+{
+    const int p2 = 1 << bucket;
+    return p2 < 4 ? 4 : p2 > 32 ? 32 : p2;
+}
+
+static std::mutex g_shape_mu;
+static std::map<std::pair<int, int>, int> g_shape;           // (bits, bucket) -> lanes per column
+
+static int shape_forced()
+{
+    const char* e = getenv("QIHT_BATCH_SHAPE");             // measurement and tests: one shape for all
+    if (!e) return 0;
+    const int v = atoi(e);
+    return (v == 4 || v == 8 || v == 16 || v == 32) ? v : 0;
+}
+
+static bool shape_tuning()
+{
+    const char* e = getenv("QIHT_BATCH_TUNE");
+    return !(e && e[0] == '0');
+}
+
+// side streams of this device for the concurrent shape groups (created once, never destroyed)
+static cudaStream_t side_stream(int k)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, cudaStream_t> streams;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = streams.find({dev, k});
+    if (it != streams.end()) return it->second;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    streams[{dev, k}] = st;
+    return st;
+}
+
 qiht_status qiht_niht_solve_batched(const qiht_problem* problems, int32_t nprob, int32_t iters,
                                     const qiht_params* params, void* workspace, size_t workspace_bytes,
                                     qiht_stream_t stream)
@@ -1077,12 +1128,104 @@ qiht_status qiht_niht_solve_batched(const qiht_problem* problems, int32_t nprob,
     qiht_problem* d_probs = reinterpret_cast<qiht_problem*>(ws);
     int* d_order = reinterpret_cast<int*>(ws + align256((size_t)nprob * sizeof(qiht_problem)));
     unsigned* d_next = reinterpret_cast<unsigned*>(ws + align256((size_t)nprob * sizeof(qiht_problem)) +
-                                                   align256((size_t)nprob * 4));
+                                                   align256((size_t)nprob * 4));      // one counter per group
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    // host -> device from pageable memory: both copies are staged before the calls return
+    // host -> device from pageable memory: the copies are staged before the calls return
     CK(cudaMemcpyAsync(d_probs, problems, (size_t)nprob * sizeof(qiht_problem), cudaMemcpyHostToDevice, cs));
-    CK(cudaMemcpyAsync(d_order, order.data(), (size_t)nprob * 4, cudaMemcpyHostToDevice, cs));
-    CK(launch_batched(d_probs, d_order, nprob, bits, iters, prm.k, prm.c, prm.max_backtrack, d_next, cs));
+
+    // tile shapes: forced, tuned (first batch with a new (bits, size bucket): every shape is
+    // timed on up to 64 of the bucket's problems for a few iterations and the fastest kept; all
+    // shapes give bit-identical results, the problems' outputs are overwritten below), or the
+    // default covering a column's pieces
+    const int forced = shape_forced();
+    std::map<int, std::vector<int>> by_bucket;
+    for (int i = 0; i < nprob; ++i) by_bucket[shape_bucket(problems[order[(size_t)i]])].push_back(order[(size_t)i]);
+    std::map<int, int> pick;
+    for (auto& kv : by_bucket) {
+        const int b = kv.first;
+        int lpc = forced ? forced : shape_default(b);
+        if (!forced && shape_tuning() && iters > 0) {
+            int cached = 0;
+            {
+                std::lock_guard<std::mutex> lock(g_shape_mu);
+                auto it = g_shape.find({bits, b});
+                if (it != g_shape.end()) cached = it->second;
+            }
+            if (cached) {
+                lpc = cached;
+            } else {
+                const int cnt = (int)std::min<size_t>(kv.second.size(), 64);
+                const int titers = std::min(iters, 8);
+                cudaEvent_t e0, e1;
+                CK(cudaEventCreate(&e0));
+                CK(cudaEventCreate(&e1));
+                float best = 0.0f;
+                CK(cudaMemcpyAsync(d_order, kv.second.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, cs));
+                for (int cand : {4, 8, 16, 32}) {
+                    CK(cudaEventRecord(e0, cs));
+                    CK(launch_batched(d_probs, d_order, cnt, bits, cand, titers, prm.k, prm.c, prm.max_backtrack,
+                                      d_next, cs));
+                    CK(cudaEventRecord(e1, cs));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.0f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (best == 0.0f || ms < best) { best = ms; lpc = cand; }
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                std::lock_guard<std::mutex> lock(g_shape_mu);
+                g_shape[{bits, b}] = lpc;
+            }
+        }
+        pick[b] = lpc;
+    }
+    // one persistent launch per shape (each kernel compiled for its shape), largest problems first
+    // within a group; the groups run concurrently on streams forked from `stream`
+    std::map<int, std::vector<int>> groups;
+    for (int i = 0; i < nprob; ++i) {
+        const int p = order[(size_t)i];
+        groups[pick[shape_bucket(problems[p])]].push_back(p);
+    }
+    std::vector<int> flat;
+    std::vector<std::pair<int, std::pair<int, int>>> seg;   // (shape, (offset, count))
+    for (auto& g : groups) {
+        seg.push_back({g.first, {(int)flat.size(), (int)g.second.size()}});
+        flat.insert(flat.end(), g.second.begin(), g.second.end());
+    }
+    std::sort(seg.begin(), seg.end(), [&](const auto& a, const auto& b) {
+        const qiht_problem& pa = problems[flat[(size_t)a.second.first]];
+        const qiht_problem& pb = problems[flat[(size_t)b.second.first]];
+        return (long long)pa.Q1.rows * pa.Q1.cols > (long long)pb.Q1.rows * pb.Q1.cols;
+    });
+    CK(cudaMemcpyAsync(d_order, flat.data(), (size_t)nprob * 4, cudaMemcpyHostToDevice, cs));
+    if (seg.size() == 1) {
+        CK(launch_batched(d_probs, d_order, nprob, bits, seg[0].first, iters, prm.k, prm.c, prm.max_backtrack,
+                          d_next, cs));
+        return QIHT_OK;
+    }
+    cudaEvent_t fork;
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CK(cudaEventRecord(fork, cs));
+    std::vector<cudaEvent_t> joins;
+    for (size_t g = 0; g < seg.size(); ++g) {
+        cudaStream_t gs = g == 0 ? cs : side_stream((int)g);    // cs may be the legacy stream (NULL)
+        if (g > 0 && !gs) {
+            note_cuda_error("cudaStreamCreateWithFlags", cudaErrorUnknown);
+            return QIHT_ERR_CUDA;
+        }
+        if (g > 0) CK(cudaStreamWaitEvent(gs, fork, 0));
+        CK(launch_batched(d_probs, d_order + seg[g].second.first, seg[g].second.second, bits, seg[g].first, iters,
+                          prm.k, prm.c, prm.max_backtrack, d_next + g, gs));
+        if (g > 0) {
+            cudaEvent_t j;
+            CK(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+            CK(cudaEventRecord(j, gs));
+            CK(cudaStreamWaitEvent(cs, j, 0));
+            joins.push_back(j);
+        }
+    }
+    cudaEventDestroy(fork);
+    for (cudaEvent_t j : joins) cudaEventDestroy(j);
     return QIHT_OK;
 }
 

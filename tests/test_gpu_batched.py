@@ -128,3 +128,23 @@ def test_batch_odd_grid_against_oracle(bits):
     res = q.niht_solve_batched(qs, 30)
     torch.cuda.synchronize()
     _check_against_oracle(res, problems, bits, 2000, 30, range(len(problems)), odd=True)
+
+
+def test_tile_shapes_give_identical_results(monkeypatch):
+    # the gradient's tile shape (lanes per column) changes only the order of exact integer sums:
+    # every shape the autotuner can pick gives bit-identical solves
+    problems = synth.batch_gaussian(12, seed=91, m_range=(64, 2048), s_range=(4, 40), snr_db=30.0, values="pm_u")
+    qs = _quantized(problems, 4, 300)
+    outs = []
+    for shape in ("4", "8", "16", "32"):
+        monkeypatch.setenv("QIHT_BATCH_SHAPE", shape)
+        res = q.niht_solve_batched(qs, 25)
+        torch.cuda.synchronize()
+        outs.append(([x.clone() for x in res.x], [r.iters_run for r in res.all_reports()]))
+    monkeypatch.delenv("QIHT_BATCH_SHAPE")
+    tuned = q.niht_solve_batched(qs, 25)                     # the autotuner's choice
+    torch.cuda.synchronize()
+    outs.append((tuned.x, [r.iters_run for r in tuned.all_reports()]))
+    for xs, its in outs[1:]:
+        assert its == outs[0][1]
+        assert all(torch.equal(a, b) for a, b in zip(xs, outs[0][0]))
