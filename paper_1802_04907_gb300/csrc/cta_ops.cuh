@@ -239,56 +239,125 @@ __device__ int mkeys(int n, int s, float muf, const float* g, const MSm& sm)
 // H_s over the keys: the s largest, ties to the lower index. G' ascending in sel / val
 // (val = x'), the list x' - x over G' u G in uni / dlt (G \ G' after G', in support
 // order; only with with_old). Returns 1 if G' != G, else 0; *uc = entries of the list.
-__device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, SSh& sh, int* uc, bool with_old)
+// bin of the next radix digit from the histogram in sm.hist (warp 0): the digit whose bucket
+// holds the need-th largest key; sh.i[0] = digit, sh.i[1] = keys in higher buckets,
+// sh.i[2] = keys in the digit's bucket
+__device__ void radix_pick(const MSm& sm, SSh& sh, int need)
+{
+    const int lane = threadIdx.x & 31;
+    if ((threadIdx.x >> 5) == 0) {
+        int c[8];
+        int tot = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { c[i] = (int)sm.hist[255 - 8 * lane - i]; tot += c[i]; }
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - tot;
+        if (excl < need && need <= incl) {
+            int run = excl;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (run + c[i] >= need) { sh.i[0] = 255 - 8 * lane - i; sh.i[1] = run; sh.i[2] = c[i]; break; }
+                run += c[i];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// H_s over the keys: the s largest, ties to the lower index. G' ascending in sel / val
+// (val = x'), the list x' - x over G' u G in uni / dlt (G \ G' after G', in support
+// order; only with with_old). Returns 1 if G' != G, else 0; *uc = entries of the list.
+// list (capacity listcap ints, free shared memory) holds the candidates of the top digit's
+// bucket: the three later radix passes run over them only.
+__device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, SSh& sh, int* uc, bool with_old,
+                       int* list, int listcap)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t prefix = 0;
-    int need = s;
-    for (int pass = 0; pass < 4; ++pass) {
+    // first digit (top 8 bits) over all keys
+    if (tid < 256) sm.hist[tid] = 0;
+    __syncthreads();
+    for (int b = warp * 32; b < n; b += kST) {
+        const int j = b + lane;
+        const bool in = j < n;
+        const uint32_t k = in ? sm.keys[j] : 0u;
+        const unsigned bin = k >> 24;
+        // lanes with the same bin add once (keys crowd into few bins)
+        const unsigned peers = __match_any_sync(0xffffffffu, in ? bin : 0x100u);
+        if (in && lane == __ffs(peers) - 1) atomicAdd(&sm.hist[bin], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    radix_pick(sm, sh, s);
+    uint32_t prefix = (uint32_t)sh.i[0] << 24;
+    int need = s - sh.i[1];
+    const int c0 = sh.i[2];
+    const bool compact = c0 <= listcap;
+    int cnt = 0;
+    __syncthreads();
+    if (compact) {
+        // the bucket's keys into the list (order does not matter for the histograms)
+        if (tid == 0) sh.i[3] = 0;
+        __syncthreads();
+        const uint32_t top = prefix >> 24;
+        for (int b = warp * 32; b < n; b += kST) {
+            const int j = b + lane;
+            const bool hit = j < n && (sm.keys[j] >> 24) == top;
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (!bal) continue;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&sh.i[3], __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (hit) list[base + __popc(bal & ((1u << lane) - 1u))] = j;
+        }
+        __syncthreads();
+        cnt = sh.i[3];
+        __syncthreads();
+    }
+    for (int pass = 1; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         if (tid < 256) sm.hist[tid] = 0;
         __syncthreads();
-        for (int b = warp * 32; b < n; b += kST) {
-            const int j = b + lane;
-            const bool in = j < n;
-            const uint32_t k = in ? sm.keys[j] : 0u;
-            const bool take = in && (pass == 0 || (k >> (shift + 8)) == (prefix >> (shift + 8)));
-            if (!__any_sync(0xffffffffu, take)) continue;   // later passes: most steps have no candidate
-            const unsigned bin = (k >> shift) & 255u;
-            // lanes with the same bin add once (keys crowd into few bins); the other lanes share
-            // one value so that the match stays cheap
-            const unsigned peers = __match_any_sync(0xffffffffu, take ? bin : 0x100u);
-            if (take && lane == __ffs(peers) - 1) atomicAdd(&sm.hist[bin], (unsigned)__popc(peers));
-        }
-        __syncthreads();
-        if (warp == 0) {
-            int c[8];
-            int tot = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { c[i] = (int)sm.hist[255 - 8 * lane - i]; tot += c[i]; }
-            int incl = tot;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+        if (compact) {
+            for (int e = tid; e < cnt; e += kST) {
+                const uint32_t k = sm.keys[list[e]];
+                if ((k >> (shift + 8)) == (prefix >> (shift + 8))) atomicAdd(&sm.hist[(k >> shift) & 255u], 1u);
             }
-            const int excl = incl - tot;
-            if (excl < need && need <= incl) {
-                int run = excl;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (run + c[i] >= need) { sh.i[0] = 255 - 8 * lane - i; sh.i[1] = run; break; }
-                    run += c[i];
-                }
+        } else {
+            for (int b = warp * 32; b < n; b += kST) {
+                const int j = b + lane;
+                const bool in = j < n;
+                const uint32_t k = in ? sm.keys[j] : 0u;
+                const bool take = in && (k >> (shift + 8)) == (prefix >> (shift + 8));
+                if (!__any_sync(0xffffffffu, take)) continue;
+                const unsigned bin = (k >> shift) & 255u;
+                const unsigned peers = __match_any_sync(0xffffffffu, take ? bin : 0x100u);
+                if (take && lane == __ffs(peers) - 1) atomicAdd(&sm.hist[bin], (unsigned)__popc(peers));
             }
         }
         __syncthreads();
+        radix_pick(sm, sh, need);
         prefix |= (uint32_t)sh.i[0] << shift;
         need -= sh.i[1];
         __syncthreads();
     }
     const uint32_t T = prefix;
     const int nbw = (n + 31) / 32;
+    // every key equal to T taken (the usual case, T's bucket at the last digit holds exactly
+    // `need` keys): the selection is every key >= T, marked in one pass
+    const bool all_ties = sh.i[2] == need;
+    __syncthreads();
+    if (all_ties) {
+        for (int b = warp * 32; b < n; b += kST) {
+            const int j = b + lane;
+            const unsigned bal = __ballot_sync(0xffffffffu, j < n && sm.keys[j] >= T);
+            if (lane == 0 && b < n) sm.bitmap[b >> 5] = bal;
+        }
+        __syncthreads();
+    } else {
     for (int w = tid; w < nbw; w += kST) sm.bitmap[w] = 0u;
     const int seg = ((n + 32 * kSW - 1) / (32 * kSW)) * 32;
     const int wb = min(n, warp * seg), we = min(n, wb + seg);
@@ -313,6 +382,7 @@ __device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, S
         erun += __popc(meq);
     }
     __syncthreads();
+    }
     {
         const int wpt = (nbw + kST - 1) / kST;
         const int w0 = min(nbw, tid * wpt), w1 = min(nbw, w0 + wpt);

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
         if (mkeys(n, 0, 1.0f, g, sm)) {
             status = QIHT_ERR_NONFINITE;
         } else {
-            mselect(n, s, 1.0f, g, sm, sh, &uc, false);
+            mselect(n, s, 1.0f, g, sm, sh, &uc, false, reinterpret_cast<int*>(sm.z), a.mk);
             for (int q = tid; q < s; q += kST) { gsup[q] = sm.sel[q]; gxs[q] = 0.0f; }
         }
         if (tid == 0 && status != QIHT_OK) { st->status = status; st->stop = 2; }
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
     int bt = 0, changed = 0;
     for (;;) {
         if (mkeys(n, s, sh.muf, g, sm)) { changed = -1; break; }
-        changed = mselect(n, s, sh.muf, g, sm, sh, &uc, true);
+        changed = mselect(n, s, sh.muf, g, sm, sh, &uc, true, reinterpret_cast<int*>(sm.z), a.mk);
         if (!changed) break;
         // backtracking test on G' u G
         double dn = 0.0;

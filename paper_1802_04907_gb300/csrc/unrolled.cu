@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kST, 1) k_ud_fwd(UdArgs a)
     if (a.t == 0) {
         // initial support H_s(h_0) (x_0 = 0)
         mkeys(n, 0, 1.0f, h, sm);
-        mselect(n, s, 1.0f, h, sm, sh, &uc, false);
+        mselect(n, s, 1.0f, h, sm, sh, &uc, false, reinterpret_cast<int*>(sm.z), a.mk);
         for (int q = tid; q < s; q += kST) { sm.sup[q] = sm.sel[q]; sm.xs[q] = 0.0f; }
     } else {
         for (int q = tid; q < s; q += kST) { sm.sup[q] = gsup[q]; sm.xs[q] = gxs[q]; }
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kST, 1) k_ud_fwd(UdArgs a)
     }
     // x_{t+1} = H_s(x_t + mu h_t)
     mkeys(n, s, us.muf, h, sm);
-    mselect(n, s, us.muf, h, sm, sh, &uc, false);
+    mselect(n, s, us.muf, h, sm, sh, &uc, false, reinterpret_cast<int*>(sm.z), a.mk);
     if (a.rec_r) {
         const size_t slot = (size_t)p * a.c + a.slot;
         for (int q = tid; q < s; q += kST) {

@@ -187,3 +187,18 @@ def test_multi_zero_iterations_gives_initial_supports():
         torch.cuda.synchronize()
         assert torch.equal(torch.sort(sv.support).values, res.support[k])
         assert torch.all(res.x[k] == 0)
+
+
+def test_multi_exact_ties_resolve_by_index():
+    # +-1 columns duplicated: identical codes and gradients, ties at the s-th key broken by index;
+    # every right-hand side the same observation, each against the oracle at every iteration
+    p = synth.duplicated_pm1(256, 96, 4, 6, seed=3)
+    Y = np.stack([p.y] * 3)
+    mp = synth.MultiProblem(phi=p.phi, Y=Y, X_true=np.stack([p.x_true] * 3), s=p.s, name="dup")
+    res, _ = _multi_run(mp, 8, 8, 12, seed=1)
+    ref, _ = oracle.qiht(p.phi, p.y, p.s, 12, bits_phi=8, bits_y=8, seed=1, trace=True)
+    for k in range(3):
+        assert res.report(k).status == ref.status
+        assert np.array_equal(res.support[k].cpu().numpy(), ref.support)
+        x = res.x[k].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(x - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
