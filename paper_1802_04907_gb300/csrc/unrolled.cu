@@ -16,7 +16,7 @@
 // the rows they scale.
 //
 // Kernels: a batched dense product out = base + sign A^T v (grid over columns x problems, one
-// warp per column, FP32), and one CTA (1024 threads) per problem for everything else of a
+// warp per column, exact integer sums of the codes with v in 24-bit fixed point), and one CTA (1024 threads) per problem for everything else of a
 // step (column-subset products of the s columns, FP64 sums, H_s over all n keys in shared
 // memory). The forward keeps the state every ceil(sqrt K) steps; the adjoint recomputes each
 // segment from its checkpoint, recording what the reverse steps need.
@@ -29,42 +29,99 @@ namespace {
 
 using namespace cta;
 
-constexpr int kUdColsPerWarp = 8;
+constexpr int kUdColsPerWarp = 16;
 constexpr int kUdWarps = 8;
 constexpr int kUdGroup = 4;                     // columns of a warp whose loads are in flight together
 
-// out[p][j] = (base ? base[p][j] : 0) + sign * alpha * sum_i (2 c_ij - (L-1)) v[p][i].
-// Lane l of a warp takes the 16-byte pieces l, l + 32, ... of every column; v sits in shared
-// memory transposed by piece (entry k of piece w at k * npieces + w), so the lanes of a warp
-// read consecutive words. A code c becomes the float 2c - (L-1) through the exact bit
-// pattern of 2^23 + c.
+__device__ __forceinline__ uint32_t ud_dp4a_uu(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+__device__ __forceinline__ int32_t ud_dp4a_us(uint32_t a, uint32_t b, int32_t c)
+{
+    int32_t d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// out[p][j] = (base ? base[p][j] : 0) + sign * alpha * sum_i (2 c_ij - (L-1)) v[p][i], in exact
+// integer sums: v becomes 24-bit block fixed point (|v| 2^sh < 2^22, sh from max |v|) held as
+// three byte planes in shared memory, the codes of a column multiply them by dp4a, and
+// T = 2 sum c v~ - (L-1) sum v~ is scaled once by alpha 2^-sh. The planes are laid out by code
+// plane (plane e of word w at e * ld + w) so that the lanes of a warp, each taking four
+// consecutive words of a column, read consecutive shared-memory words.
 template <int BITS>
 __global__ void __launch_bounds__(256) k_ud_gemvt(const qiht_codes* __restrict__ Qs, const float* __restrict__ v,
                                                   const float* __restrict__ base, float sign, float* __restrict__ out,
                                                   int m, int n)
 {
     constexpr int G = 32 / BITS;
-    constexpr int RP = 4 * G;                   // rows per 16-byte piece
-    constexpr uint32_t MASK = (1u << BITS) - 1;
-    extern __shared__ float vT[];
+    constexpr int E = G / 4;                    // 4-code planes per word
+    constexpr uint32_t MASK8 = 0x01010101u * ((1u << BITS) - 1);
+    extern __shared__ uint32_t planes[];        // 3 x E x ld words
+    __shared__ unsigned s_max[8];
+    __shared__ long long s_sum[8];
     const int p = blockIdx.y;
     const qiht_codes Q = Qs[p];
-    const int ld = Q.ld_words, np4 = ld / 4;
-    const float lm1f = (float)(grid_levels(BITS, Q.levels) - 1);
-    const float alpha = (float)((double)(*Q.scale) / (double)(grid_levels(BITS, Q.levels) - 1));
+    const int ld = Q.ld_words;
+    const long long lm1 = grid_levels(BITS, Q.levels) - 1;
     const float* vp = v + (size_t)p * m;
-    for (int i = threadIdx.x; i < np4 * RP; i += 256) {
-        const int w4 = i / RP, k = i % RP;
-        vT[k * np4 + w4] = i < m ? vp[i] : 0.0f;
-    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned mx = 0;
+    for (int i = tid; i < m; i += 256) mx = max(mx, __float_as_uint(vp[i]) & 0x7fffffffu);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) s_max[warp] = mx;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j0 = (blockIdx.x * kUdWarps + warp) * kUdColsPerWarp;
-    for (int jg = 0; jg < kUdColsPerWarp; jg += kUdGroup) {
-        float acc[kUdGroup];
+    mx = 0;
+    for (int w = 0; w < 8; ++w) mx = max(mx, s_max[w]);
+    int sh = 0;
+    const float M = __uint_as_float(mx);
+    if (M > 0.0f && isfinite(M)) {
+        int ex;
+        frexpf(M, &ex);
+        sh = 22 - ex;
+    }
+    // v in fixed point: limb group g (rows 4g .. 4g + 3) = plane g % E of word g / E
+    long long rsum = 0;
+    uint32_t* P0 = planes;
+    uint32_t* P1 = planes + E * ld;
+    uint32_t* P2 = planes + 2 * E * ld;
+    for (int g = tid; g < E * ld; g += 256) {
+        uint32_t b0 = 0, b1 = 0, b2 = 0;
 #pragma unroll
-        for (int c = 0; c < kUdGroup; ++c) acc[c] = 0.0f;
-        for (int w4 = lane; w4 < np4; w4 += 32) {
+        for (int q = 0; q < 4; ++q) {
+            const int i = 4 * g + q;
+            const int vi = i < m ? __float2int_rn(ldexpf(vp[i], sh)) : 0;
+            rsum += vi;
+            b0 |= (uint32_t)(vi & 255) << (8 * q);
+            b1 |= (uint32_t)((vi >> 8) & 255) << (8 * q);
+            b2 |= (uint32_t)((vi >> 16) & 255) << (8 * q);
+        }
+        const int idx = (g % E) * ld + g / E;
+        P0[idx] = b0;
+        P1[idx] = b1;
+        P2[idx] = b2;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+    if (lane == 0) s_sum[warp] = rsum;
+    __syncthreads();
+    long long R = 0;
+    for (int w = 0; w < 8; ++w) R += s_sum[w];
+    const double outscale = ldexp((double)(*Q.scale) / (double)lm1, -sh) * (double)sign;
+    const int j0 = (blockIdx.x * kUdWarps + warp) * kUdColsPerWarp;
+    const int n4 = ld / 4;                      // 16-byte pieces per column
+    for (int jg = 0; jg < kUdColsPerWarp; jg += kUdGroup) {
+        uint32_t s0[kUdGroup][E], s1[kUdGroup][E];
+        int32_t s2[kUdGroup][E];
+#pragma unroll
+        for (int c = 0; c < kUdGroup; ++c)
+#pragma unroll
+            for (int e = 0; e < E; ++e) { s0[c][e] = 0; s1[c][e] = 0; s2[c][e] = 0; }
+        for (int w4 = lane; w4 < n4; w4 += 32) {
             uint4 c4[kUdGroup];
 #pragma unroll
             for (int c = 0; c < kUdGroup; ++c) {
@@ -73,27 +130,41 @@ __global__ void __launch_bounds__(256) k_ud_gemvt(const qiht_codes* __restrict__
                               : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int e = 0; e < E; ++e) {
+                const uint4 A0 = *reinterpret_cast<const uint4*>(P0 + e * ld + 4 * w4);
+                const uint4 A1 = *reinterpret_cast<const uint4*>(P1 + e * ld + 4 * w4);
+                const uint4 A2 = *reinterpret_cast<const uint4*>(P2 + e * ld + 4 * w4);
+                const uint32_t y0[4] = {A0.x, A0.y, A0.z, A0.w};
+                const uint32_t y1[4] = {A1.x, A1.y, A1.z, A1.w};
+                const uint32_t y2[4] = {A2.x, A2.y, A2.z, A2.w};
 #pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    const float vk = vT[(u * G + k) * np4 + w4];
+                for (int c = 0; c < kUdGroup; ++c) {
+                    const uint32_t wd[4] = {c4[c].x, c4[c].y, c4[c].z, c4[c].w};
 #pragma unroll
-                    for (int c = 0; c < kUdGroup; ++c) {
-                        const uint32_t wd = u == 0 ? c4[c].x : u == 1 ? c4[c].y : u == 2 ? c4[c].z : c4[c].w;
-                        const uint32_t code = (wd >> (8 * (k & 3) + BITS * (k >> 2))) & MASK;
-                        const float cf = __uint_as_float(0x4B000000u | code) - 8388608.0f;   // exact
-                        acc[c] = fmaf(fmaf(cf, 2.0f, -lm1f), vk, acc[c]);
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t x = (wd[u] >> (BITS * e)) & MASK8;
+                        s0[c][e] = ud_dp4a_uu(x, y0[u], s0[c][e]);
+                        s1[c][e] = ud_dp4a_uu(x, y1[u], s1[c][e]);
+                        s2[c][e] = ud_dp4a_us(x, y2[u], s2[c][e]);
                     }
                 }
+            }
         }
 #pragma unroll
         for (int c = 0; c < kUdGroup; ++c) {
+            long long S = 0;
 #pragma unroll
-            for (int o = 16; o; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+            for (int e = 0; e < E; ++e) {
+                const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[c][e]);
+                const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[c][e]);
+                const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[c][e]);
+                S += t0 + (t1 << 8) + (t2 << 16);
+            }
             const int j = j0 + jg + c;
             if (lane == 0 && j < n) {
+                const long long T = 2 * S - lm1 * R;
                 const float b0 = base ? base[(size_t)p * n + j] : 0.0f;
-                out[(size_t)p * n + j] = fmaf(sign * alpha, acc[c], b0);
+                out[(size_t)p * n + j] = (float)((double)b0 + (double)T * outscale);
             }
         }
     }
@@ -419,8 +490,7 @@ cudaError_t launch_ud_xout(const UdArgs& a, float* X, cudaStream_t s)
 cudaError_t launch_ud_gemvt(const qiht_codes* Qs, int bits, const float* v, const float* base, float sign, float* out,
                             int P, int m, int n, int ldw, cudaStream_t s)
 {
-    const int G = 32 / bits;
-    const size_t smem = (size_t)ldw * G * 4;          // v transposed by 16-byte piece
+    const size_t smem = (size_t)3 * (32 / bits / 4) * ldw * 4;   // the three byte planes of v
     const dim3 grid((unsigned)((n + kUdWarps * kUdColsPerWarp - 1) / (kUdWarps * kUdColsPerWarp)), (unsigned)P);
     cudaError_t e;
     switch (bits) {
