@@ -226,6 +226,15 @@ def traffic_for_kernel(bits, m, n):
         return None
 
 
+def replica_throughput(ms_local: float, units_local: float, reduce_max, reduce_sum):
+    """Whole-job throughput of independent replicas (one per rank, no collective in the data
+    path): the units every rank processed, summed, over the slowest rank's time. reduce_max /
+    reduce_sum combine a float over the ranks (identity on one rank)."""
+    ms_max = reduce_max(ms_local)
+    units = reduce_sum(units_local)
+    return units / (ms_max / 1e3), ms_max
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -286,11 +295,16 @@ def run_ours(args):
     clocks = clk.stop()
     rep = solver.read_report()
     iters_done = rep.iters_run
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps * iters_done / (ms_max / 1e3)
+    def reduce_with(op):
+        def f(v):
+            t = torch.tensor([v], dtype=torch.float64, device=dev)
+            if world > 1:
+                dist.all_reduce(t, op=op)
+            return float(t.item())
+        return f
+
+    value, ms_max = replica_throughput(ms, args.steps * iters_done, reduce_with(dist.ReduceOp.MAX),
+                                       reduce_with(dist.ReduceOp.SUM))
 
     # solve only (quantization excluded), same buffers
     barrier()
