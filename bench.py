@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -741,6 +742,10 @@ def run_unrolled(args):
     codes = sum(qq.nbytes for qq in Q1s) + sum(qq.nbytes for qq in Q2s)
     # dense products per forward + backward: K forward, K recomputed, K adjoint (A^T v over all n)
     passes = 3 * K
+    # launches of this library per step: forward = init, planes, K x (product, step), output;
+    # backward = per checkpoint segment one planes kernel, then K x 2 recomputed, K x 2 adjoint
+    c = math.isqrt(K - 1) + 1 if K > 1 else 1
+    ud_launches = args.steps * ((3 + 2 * K) + (-(-K // c) + 4 * K))
     achieved = passes * (codes / 2) / (ms / 1e3) / 1e9
     peak, _ = load_peaks()
     line = {"metric": "unrolled forward+backward problems/s", "value": P / (ms / 1e3), "unit": "problems/s",
@@ -754,7 +759,7 @@ def run_unrolled(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "note": "3K dense code passes (forward, recomputation, adjoint) over the step time; "
                                  "the per-problem step kernels are not counted"},
-            "gpu_launches": 2 + 2 * K + 2 * K + 2 * K + 2}
+            "gpu_launches": ud_launches}
     print(json.dumps(line))
 
 

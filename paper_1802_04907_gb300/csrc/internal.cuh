@@ -345,13 +345,20 @@ struct UdArgs {
     float* rec_hGn;           // P x c x s: h on G_{t+1}
     double* rec_sc;           // P x c x 4: mu, ||P h||^2, ||A2 P h||^2
     int c, slot, t;
+    // operand of the next dense product: the vector in fixed point (byte planes, shift, sum)
+    uint32_t* pl;             // P x pl_stride words
+    size_t pl_stride;
+    int* pl_sh;               // P
+    long long* pl_rs;         // P
+    int gx;                   // CTAs per problem of the dense product
 };
 size_t ud_fwd_smem(int n, int mk, int s);
 size_t ud_bwd_smem(int n, int mk, int s);
 cudaError_t launch_ud_init(const UdArgs& a, cudaStream_t s);
 cudaError_t launch_ud_xout(const UdArgs& a, float* X, cudaStream_t s);
-cudaError_t launch_ud_gemvt(const qiht_codes* Qs, int bits, const float* v, const float* base, float sign, float* out,
-                            int P, int m, int n, int ldw, cudaStream_t s);
+cudaError_t launch_ud_planes(const UdArgs& a, int bits, const float* v, cudaStream_t s);
+cudaError_t launch_ud_gemvt(const UdArgs& a, const qiht_codes* Qs, int bits, const float* base, float sign, float* out,
+                            int ldw, cudaStream_t s);
 cudaError_t launch_ud_fwd(const UdArgs& a, int bits, cudaStream_t s);
 cudaError_t launch_ud_bwd(const UdArgs& a, int bits, const float* xbar, float* vbase, float* vv, float* ybar,
                           float* gabar, float* gbbar, cudaStream_t s);

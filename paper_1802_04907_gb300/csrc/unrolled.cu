@@ -29,9 +29,6 @@ namespace {
 
 using namespace cta;
 
-constexpr int kUdColsPerWarp = 16;
-constexpr int kUdWarps = 8;
-constexpr int kUdGroup = 4;                     // columns of a warp whose loads are in flight together
 
 __device__ __forceinline__ uint32_t ud_dp4a_uu(uint32_t a, uint32_t b, uint32_t c)
 {
@@ -47,36 +44,25 @@ __device__ __forceinline__ int32_t ud_dp4a_us(uint32_t a, uint32_t b, int32_t c)
     return d;
 }
 
-// out[p][j] = (base ? base[p][j] : 0) + sign * alpha * sum_i (2 c_ij - (L-1)) v[p][i], in exact
-// integer sums: v becomes 24-bit block fixed point (|v| 2^sh < 2^22, sh from max |v|) held as
-// three byte planes in shared memory, the codes of a column multiply them by dp4a, and
-// T = 2 sum c v~ - (L-1) sum v~ is scaled once by alpha 2^-sh. The planes are laid out by code
-// plane (plane e of word w at e * ld + w) so that the lanes of a warp, each taking four
-// consecutive words of a column, read consecutive shared-memory words.
+// v (m floats in global memory, written by this CTA before a barrier) -> the operand of the
+// batched dense product: 24-bit block fixed point (|v| 2^sh < 2^22, sh from max |v|) as three
+// byte planes laid out by code plane (plane e of word w at e * ld + w: limb group g = rows
+// 4g .. 4g + 3 is plane g % E of word g / E), its shift and the integer sum of its entries.
 template <int BITS>
-__global__ void __launch_bounds__(256) k_ud_gemvt(const qiht_codes* __restrict__ Qs, const float* __restrict__ v,
-                                                  const float* __restrict__ base, float sign, float* __restrict__ out,
-                                                  int m, int n)
+__device__ void ud_planes(const float* v, int m, int ld, uint32_t* planes, int* shift_out, long long* rsum_out)
 {
     constexpr int G = 32 / BITS;
-    constexpr int E = G / 4;                    // 4-code planes per word
-    constexpr uint32_t MASK8 = 0x01010101u * ((1u << BITS) - 1);
-    extern __shared__ uint32_t planes[];        // 3 x E x ld words
-    __shared__ unsigned s_max[8];
-    __shared__ long long s_sum[8];
-    const int p = blockIdx.y;
-    const qiht_codes Q = Qs[p];
-    const int ld = Q.ld_words;
-    const long long lm1 = grid_levels(BITS, Q.levels) - 1;
-    const float* vp = v + (size_t)p * m;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int E = G / 4;
+    __shared__ unsigned s_mx[32];
+    __shared__ long long s_rs[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
     unsigned mx = 0;
-    for (int i = tid; i < m; i += 256) mx = max(mx, __float_as_uint(vp[i]) & 0x7fffffffu);
+    for (int i = tid; i < m; i += blockDim.x) mx = max(mx, __float_as_uint(v[i]) & 0x7fffffffu);
     mx = __reduce_max_sync(0xffffffffu, mx);
-    if (lane == 0) s_max[warp] = mx;
+    if (lane == 0) s_mx[warp] = mx;
     __syncthreads();
     mx = 0;
-    for (int w = 0; w < 8; ++w) mx = max(mx, s_max[w]);
+    for (int w = 0; w < nw; ++w) mx = max(mx, s_mx[w]);
     int sh = 0;
     const float M = __uint_as_float(mx);
     if (M > 0.0f && isfinite(M)) {
@@ -84,89 +70,172 @@ __global__ void __launch_bounds__(256) k_ud_gemvt(const qiht_codes* __restrict__
         frexpf(M, &ex);
         sh = 22 - ex;
     }
-    // v in fixed point: limb group g (rows 4g .. 4g + 3) = plane g % E of word g / E
     long long rsum = 0;
-    uint32_t* P0 = planes;
-    uint32_t* P1 = planes + E * ld;
-    uint32_t* P2 = planes + 2 * E * ld;
-    for (int g = tid; g < E * ld; g += 256) {
+    for (int g = tid; g < E * ld; g += blockDim.x) {
         uint32_t b0 = 0, b1 = 0, b2 = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i = 4 * g + q;
-            const int vi = i < m ? __float2int_rn(ldexpf(vp[i], sh)) : 0;
+            const int vi = i < m ? __float2int_rn(ldexpf(v[i], sh)) : 0;
             rsum += vi;
             b0 |= (uint32_t)(vi & 255) << (8 * q);
             b1 |= (uint32_t)((vi >> 8) & 255) << (8 * q);
             b2 |= (uint32_t)((vi >> 16) & 255) << (8 * q);
         }
         const int idx = (g % E) * ld + g / E;
-        P0[idx] = b0;
-        P1[idx] = b1;
-        P2[idx] = b2;
+        planes[idx] = b0;
+        planes[E * ld + idx] = b1;
+        planes[2 * E * ld + idx] = b2;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
-    if (lane == 0) s_sum[warp] = rsum;
+    if (lane == 0) s_rs[warp] = rsum;
     __syncthreads();
-    long long R = 0;
-    for (int w = 0; w < 8; ++w) R += s_sum[w];
-    const double outscale = ldexp((double)(*Q.scale) / (double)lm1, -sh) * (double)sign;
-    const int j0 = (blockIdx.x * kUdWarps + warp) * kUdColsPerWarp;
-    const int n4 = ld / 4;                      // 16-byte pieces per column
-    for (int jg = 0; jg < kUdColsPerWarp; jg += kUdGroup) {
-        uint32_t s0[kUdGroup][E], s1[kUdGroup][E];
-        int32_t s2[kUdGroup][E];
+    if (tid == 0) {
+        long long R = 0;
+        for (int w = 0; w < nw; ++w) R += s_rs[w];
+        *shift_out = sh;
+        *rsum_out = R;
+    }
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(256) k_ud_planes(const float* __restrict__ v, UdArgs a)
+{
+    const int p = blockIdx.x;
+    const int ld = a.q1[p].ld_words;
+    ud_planes<BITS>(v + (size_t)p * a.m, a.m, ld, a.pl + (size_t)p * a.pl_stride, a.pl_sh + p, a.pl_rs + p);
+}
+
+// out[p][j] = (base ? base[p][j] : 0) + sign * alpha * sum_i (2 c_ij - (L-1)) v[p][i], in exact
+// integer sums. The three byte planes of v (written once per problem by its producer) are
+// copied to shared memory; the codes of a column multiply them by dp4a and
+// T = 2 sum c v~ - (L-1) sum v~ is scaled once by alpha 2^-sh. Grid: gridDim.x CTAs per problem
+// (blockIdx.y), 16 warps each, two CTAs per SM; a warp owns whole columns (stride: the
+// problem's warps) and streams each in batches of NPL 16-byte pieces per lane, the loads of the
+// next batch in flight while the current one is used. Codes are extracted with one mask per
+// four codes, (w & (mask << b e)) = the codes of position e times 2^(b e); the position sums are
+// exact and are shifted back after the warp sum. With the planes laid out by code plane, the
+// lanes of a warp, taking consecutive pieces, read consecutive 16-byte words of shared memory.
+constexpr int kUdThreads = 512;
+
+template <int BITS, int NPL>
+__global__ void __launch_bounds__(kUdThreads, 2) k_ud_gemvt(const qiht_codes* __restrict__ Qs,
+                                                            const uint32_t* __restrict__ pl, size_t pl_stride,
+                                                            const int* __restrict__ pl_sh,
+                                                            const long long* __restrict__ pl_rs,
+                                                            const float* __restrict__ base, float sign,
+                                                            float* __restrict__ out, int n)
+{
+    constexpr int G = 32 / BITS;
+    constexpr int E = G / 4;                    // 4-code positions per word
+    constexpr uint32_t MASK = 0x01010101u * ((1u << BITS) - 1);
+    extern __shared__ __align__(16) uint32_t planes[];   // 3 x E x ld words
+    __shared__ double s_outscale;
+    __shared__ long long s_R;
+    const int p = blockIdx.y;
+    const uint32_t* words = Qs[p].words;
+    const int ld = Qs[p].ld_words;
+    const int P4 = ld / 4;                      // 16-byte pieces per column
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = gridDim.x * (kUdThreads / 32);
+    const int nb = (P4 + 32 * NPL - 1) / (32 * NPL);     // batches per column
+    int j = blockIdx.x * (kUdThreads / 32) + warp;
+    int pb = 0;
+    uint64_t policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+    auto load_batch = [&](uint4 (&cv)[NPL], int jj, int bb) {
+        const uint4* col = reinterpret_cast<const uint4*>(words + (size_t)jj * ld);
 #pragma unroll
-        for (int c = 0; c < kUdGroup; ++c)
+        for (int u = 0; u < NPL; ++u) {
+            const int piece = bb * 32 * NPL + lane + 32 * u;
+            if (piece < P4)
+                asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                             : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w)
+                             : "l"(col + piece), "l"(policy));
+            else
+                cv[u] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    uint4 cA[NPL], cB[NPL];
+    if (j < n) load_batch(cA, j, pb);           // in flight while the planes are copied
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(pl + (size_t)p * pl_stride);
+        uint4* dst = reinterpret_cast<uint4*>(planes);
+        for (int i = threadIdx.x; i < 3 * E * P4; i += kUdThreads) dst[i] = __ldcg(src + i);
+    }
+    if (threadIdx.x == 0) {
+        // alpha 2^-sh and (L-1) sum v~, once per CTA
+        const long long lm1 = grid_levels(BITS, Qs[p].levels) - 1;
+        s_outscale = ldexp((double)(*Qs[p].scale) / (double)lm1, -pl_sh[p]) * (double)sign;
+        s_R = lm1 * pl_rs[p];
+    }
+    __syncthreads();
+    const uint4* L0 = reinterpret_cast<const uint4*>(planes);
+    const uint4* L1 = L0 + (size_t)E * P4;
+    const uint4* L2 = L0 + (size_t)2 * E * P4;
+    uint32_t s0[E], s1[E];
+    int32_t s2[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) { s0[c][e] = 0; s1[c][e] = 0; s2[c][e] = 0; }
-        for (int w4 = lane; w4 < n4; w4 += 32) {
-            uint4 c4[kUdGroup];
+    for (int e = 0; e < E; ++e) { s0[e] = 0; s1[e] = 0; s2[e] = 0; }
+
+    auto use_batch = [&](const uint4 (&cv)[NPL], int bb) {
 #pragma unroll
-            for (int c = 0; c < kUdGroup; ++c) {
-                const int j = j0 + jg + c;
-                c4[c] = j < n ? __ldg(reinterpret_cast<const uint4*>(Q.words + (size_t)j * ld) + w4)
-                              : make_uint4(0, 0, 0, 0);
-            }
+        for (int u = 0; u < NPL; ++u) {
+            const int piece = min(bb * 32 * NPL + lane + 32 * u, P4 - 1);   // past the end: zero codes
+            const uint32_t wv[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const uint4 A0 = *reinterpret_cast<const uint4*>(P0 + e * ld + 4 * w4);
-                const uint4 A1 = *reinterpret_cast<const uint4*>(P1 + e * ld + 4 * w4);
-                const uint4 A2 = *reinterpret_cast<const uint4*>(P2 + e * ld + 4 * w4);
+                const uint4 A0 = L0[(size_t)e * P4 + piece];
+                const uint4 A1 = L1[(size_t)e * P4 + piece];
+                const uint4 A2 = L2[(size_t)e * P4 + piece];
                 const uint32_t y0[4] = {A0.x, A0.y, A0.z, A0.w};
                 const uint32_t y1[4] = {A1.x, A1.y, A1.z, A1.w};
                 const uint32_t y2[4] = {A2.x, A2.y, A2.z, A2.w};
 #pragma unroll
-                for (int c = 0; c < kUdGroup; ++c) {
-                    const uint32_t wd[4] = {c4[c].x, c4[c].y, c4[c].z, c4[c].w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t x = (wd[u] >> (BITS * e)) & MASK8;
-                        s0[c][e] = ud_dp4a_uu(x, y0[u], s0[c][e]);
-                        s1[c][e] = ud_dp4a_uu(x, y1[u], s1[c][e]);
-                        s2[c][e] = ud_dp4a_us(x, y2[u], s2[c][e]);
-                    }
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t x = wv[t] & (MASK << (BITS * e));
+                    s0[e] = ud_dp4a_uu(x, y0[t], s0[e]);
+                    s1[e] = ud_dp4a_uu(x, y1[t], s1[e]);
+                    s2[e] = ud_dp4a_us(x, y2[t], s2[e]);
                 }
             }
         }
+    };
+    auto finish_column = [&](int jj) {
+        long long S = 0;
 #pragma unroll
-        for (int c = 0; c < kUdGroup; ++c) {
-            long long S = 0;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[c][e]);
-                const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[c][e]);
-                const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[c][e]);
-                S += t0 + (t1 << 8) + (t2 << 16);
-            }
-            const int j = j0 + jg + c;
-            if (lane == 0 && j < n) {
-                const long long T = 2 * S - lm1 * R;
-                const float b0 = base ? base[(size_t)p * n + j] : 0.0f;
-                out[(size_t)p * n + j] = (float)((double)b0 + (double)T * outscale);
-            }
+        for (int e = 0; e < E; ++e) {
+            const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[e]);
+            const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[e]);
+            const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[e]);
+            S += (t0 + (t1 << 8) + (t2 << 16)) >> (BITS * e);
+            s0[e] = 0; s1[e] = 0; s2[e] = 0;
         }
+        if (lane == 0) {
+            // scale and offset from shared memory: registers are the limit of the streaming loop
+            const long long T = 2 * S - s_R;
+            const float b0 = base ? base[(size_t)p * n + jj] : 0.0f;
+            out[(size_t)p * n + jj] = (float)((double)b0 + (double)T * s_outscale);
+        }
+    };
+    auto advance = [&](int& jj, int& bb) {
+        if (++bb == nb) { bb = 0; jj += W; }
+    };
+    while (j < n) {
+        int jB = j, pB = pb;
+        advance(jB, pB);
+        if (jB < n) load_batch(cB, jB, pB);
+        use_batch(cA, pb);
+        if (pb == nb - 1) finish_column(j);
+        j = jB; pb = pB;
+        if (j >= n) break;
+        int jA = j, pA = pb;
+        advance(jA, pA);
+        if (jA < n) load_batch(cA, jA, pA);
+        use_batch(cB, pb);
+        if (pb == nb - 1) finish_column(j);
+        j = jA; pb = pA;
     }
 }
 
@@ -312,6 +381,8 @@ __global__ void __launch_bounds__(kST, 1) k_ud_fwd(UdArgs a)
         a.r[(size_t)p * 2 * m + m + i] = rb;
         a.vin[(size_t)p * m + i] = fmaf(ga[i], rt, gb[i] * rb);
     }
+    __syncthreads();
+    ud_planes<BITS>(a.vin + (size_t)p * m, m, Q2.ld, a.pl + (size_t)p * a.pl_stride, a.pl_sh + p, a.pl_rs + p);
 }
 
 // One adjoint step for problem blockIdx.x from the record of its forward step.
@@ -430,6 +501,8 @@ __global__ void __launch_bounds__(kST, 1) k_ud_bwd(UdArgs a, const float* __rest
         gbb[i] += rr[m + i] * pi - rbb * rq[i] + c3 * gb[i] * ui * ui;
         vv[(size_t)p * m + i] = fmaf(ga[i], rbt, gb[i] * rbb);
     }
+    __syncthreads();
+    ud_planes<BITS>(vv + (size_t)p * m, m, Q2.ld, a.pl + (size_t)p * a.pl_stride, a.pl_sh + p, a.pl_rs + p);
     // the base of xbar_t: v on G_{t+1}, zero elsewhere
     float* vb = vbase + (size_t)p * n;
     for (int j = tid; j < n; j += kST) vb[j] = 0.0f;
@@ -487,24 +560,52 @@ cudaError_t launch_ud_xout(const UdArgs& a, float* X, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_ud_gemvt(const qiht_codes* Qs, int bits, const float* v, const float* base, float sign, float* out,
-                            int P, int m, int n, int ldw, cudaStream_t s)
+cudaError_t launch_ud_planes(const UdArgs& a, int bits, const float* v, cudaStream_t s)
+{
+    switch (bits) {
+    case 8: k_ud_planes<8><<<a.P, 256, 0, s>>>(v, a); break;
+    case 4: k_ud_planes<4><<<a.P, 256, 0, s>>>(v, a); break;
+    default: k_ud_planes<2><<<a.P, 256, 0, s>>>(v, a); break;
+    }
+    return cudaGetLastError();
+}
+
+// CTAs per problem of the batched product: the count whose waves (two CTAs per SM) times the
+// time of a CTA (its columns per warp, plus about two columns' time for copying the planes)
+// is smallest, the fewer CTAs on a tie
+int ud_gemvt_ctas(int P, int n)
+{
+    const long long slots = 2LL * num_sms();
+    const int maxx = (n + kUdThreads / 32 - 1) / (kUdThreads / 32);
+    long long best = -1;
+    int bx = 1;
+    for (int x = 1; x <= maxx; ++x) {
+        const long long waves = ((long long)P * x + slots - 1) / slots;
+        const long long cpw = ((long long)n + (long long)x * (kUdThreads / 32) - 1) / ((long long)x * (kUdThreads / 32));
+        const long long t = waves * (cpw + 2);
+        if (best < 0 || t < best) { best = t; bx = x; }
+    }
+    return bx;
+}
+
+cudaError_t launch_ud_gemvt(const UdArgs& a, const qiht_codes* Qs, int bits, const float* base, float sign, float* out,
+                            int ldw, cudaStream_t s)
 {
     const size_t smem = (size_t)3 * (32 / bits / 4) * ldw * 4;   // the three byte planes of v
-    const dim3 grid((unsigned)((n + kUdWarps * kUdColsPerWarp - 1) / (kUdWarps * kUdColsPerWarp)), (unsigned)P);
+    const dim3 grid((unsigned)a.gx, (unsigned)a.P);
     cudaError_t e;
     switch (bits) {
     case 8:
-        if ((e = set_smem(k_ud_gemvt<8>, smem)) != cudaSuccess) return e;
-        k_ud_gemvt<8><<<grid, 256, smem, s>>>(Qs, v, base, sign, out, m, n);
+        if ((e = set_smem(k_ud_gemvt<8, 4>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<8, 4><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.n);
         break;
     case 4:
-        if ((e = set_smem(k_ud_gemvt<4>, smem)) != cudaSuccess) return e;
-        k_ud_gemvt<4><<<grid, 256, smem, s>>>(Qs, v, base, sign, out, m, n);
+        if ((e = set_smem(k_ud_gemvt<4, 2>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<4, 2><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.n);
         break;
     default:
-        if ((e = set_smem(k_ud_gemvt<2>, smem)) != cudaSuccess) return e;
-        k_ud_gemvt<2><<<grid, 256, smem, s>>>(Qs, v, base, sign, out, m, n);
+        if ((e = set_smem(k_ud_gemvt<2, 1>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<2, 1><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.n);
         break;
     }
     return cudaGetLastError();
@@ -573,7 +674,8 @@ int ud_ckpt_every(int K)
 
 struct UdLayout {
     size_t q1, q2, sup, xs, vin, r, q, h, ck, rec_r, rec_q, rec_u, rec_G, rec_Gn, rec_hG, rec_hGn, rec_sc, xa, xb,
-        vbase, vv, total;
+        vbase, vv, pl, pl_sh, pl_rs, total;
+    size_t pl_stride;           // words of one problem's planes
     int c, nseg;
     size_t ck_stride;           // bytes of one checkpoint
 };
@@ -607,6 +709,10 @@ UdLayout ud_layout(int P, int m, int n, int s, int K)
     L.xb = o; o += al256(Pn * 4);
     L.vbase = o; o += al256(Pn * 4);
     L.vv = o; o += al256(Pm * 4);
+    L.pl_stride = (size_t)3 * qiht_ld_words(m, 2) * 16 / 4;      // the widest padding of the three widths
+    L.pl = o; o += al256((size_t)P * L.pl_stride * 4);
+    L.pl_sh = o; o += al256((size_t)P * 4);
+    L.pl_rs = o; o += al256((size_t)P * 8);
     L.total = o;
     return L;
 }
@@ -698,6 +804,11 @@ UdArgs ud_args(char* w, const UdLayout& L, const qiht_codes* Q1, int P, int s, c
     a.q = reinterpret_cast<float*>(w + L.q);
     a.h = reinterpret_cast<float*>(w + L.h);
     a.c = L.c;
+    a.pl = reinterpret_cast<uint32_t*>(w + L.pl);
+    a.pl_stride = L.pl_stride;
+    a.pl_sh = reinterpret_cast<int*>(w + L.pl_sh);
+    a.pl_rs = reinterpret_cast<long long*>(w + L.pl_rs);
+    a.gx = ud_gemvt_ctas(P, a.n);
     return a;
 }
 
@@ -728,10 +839,11 @@ qiht_status qiht_unrolled_forward(const qiht_codes* Q1, const qiht_codes* Q2, in
     UCK(cudaMemcpyAsync(w + L.q2, Q2, (size_t)nprob * sizeof(qiht_codes), cudaMemcpyHostToDevice, cs));
     UdArgs a = ud_args(w, L, Q1, nprob, s, y, gain_re, gain_im);
     UCK(launch_ud_init(a, cs));
+    UCK(launch_ud_planes(a, bits, a.vin, cs));
     for (int t = 0; t < K; ++t) {
         if (t % L.c == 0) UCK(ud_copy_state(a, ud_ck(w, L, nprob, m, s, t / L.c), true, cs));
         a.t = t;
-        UCK(launch_ud_gemvt(a.q1, bits, a.vin, nullptr, 1.0f, a.h, nprob, m, n, Q1[0].ld_words, cs));
+        UCK(launch_ud_gemvt(a, a.q1, bits, nullptr, 1.0f, a.h, Q1[0].ld_words, cs));
         UCK(launch_ud_fwd(a, bits, cs));
     }
     UCK(launch_ud_xout(a, X, cs));
@@ -776,10 +888,11 @@ qiht_status qiht_unrolled_backward(const qiht_codes* Q1, const qiht_codes* Q2, i
         const int t0 = seg * L.c, t1 = (t0 + L.c < K) ? t0 + L.c : K;
         // recompute the segment from its checkpoint, recording every step
         UCK(ud_copy_state(a, ud_ck(w, L, nprob, m, s, seg), false, cs));
+        UCK(launch_ud_planes(a, bits, a.vin, cs));
         for (int t = t0; t < t1; ++t) {
             a.t = t;
             a.slot = t - t0;
-            UCK(launch_ud_gemvt(a.q1, bits, a.vin, nullptr, 1.0f, a.h, nprob, m, n, Q1[0].ld_words, cs));
+            UCK(launch_ud_gemvt(a, a.q1, bits, nullptr, 1.0f, a.h, Q1[0].ld_words, cs));
             UCK(launch_ud_fwd(a, bits, cs));
         }
         // reverse steps: xbar_t = v - A2^T rbar
@@ -787,7 +900,7 @@ qiht_status qiht_unrolled_backward(const qiht_codes* Q1, const qiht_codes* Q2, i
             a.t = t;
             a.slot = t - t0;
             UCK(launch_ud_bwd(a, bits, xa, vbase, vv, ybar, gain_re_bar, gain_im_bar, cs));
-            UCK(launch_ud_gemvt(a.q2, bits, vv, vbase, -1.0f, xb, nprob, m, n, Q1[0].ld_words, cs));
+            UCK(launch_ud_gemvt(a, a.q2, bits, vbase, -1.0f, xb, Q1[0].ld_words, cs));
             float* tmp = xa;
             xa = xb;
             xb = tmp;
