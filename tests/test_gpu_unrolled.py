@@ -61,9 +61,13 @@ def _min_gap(steps, s):
     return g
 
 
-@pytest.mark.parametrize("bits,K", [(4, 6), (8, 12), (2, 5)])
-def test_forward_and_adjoint_match_oracle(bits, K):
-    P, m, n, s = 4, 256, 1024, 12
+@pytest.mark.parametrize("bits,K,P,m,n,s", [(4, 6, 4, 256, 1024, 12), (8, 12, 4, 256, 1024, 12),
+                                            (2, 5, 4, 256, 1024, 12),
+                                            # ragged: columns off the 4-column groups, rows off a
+                                            # 512-byte batch, problems split across CTAs
+                                            (4, 5, 5, 333, 1001, 9), (2, 4, 7, 700, 1003, 11),
+                                            (8, 4, 3, 1500, 2047, 16)])
+def test_forward_and_adjoint_match_oracle(bits, K, P, m, n, s):
     probs, refs, op, Y, GA, GB, XT = _setup(P, m, n, s, bits, K, seed=bits * 10 + K)
     X = op.forward(Y, GA, GB)
     Xbar = 2.0 * (X - XT)
