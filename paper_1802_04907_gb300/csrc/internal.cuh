@@ -3,6 +3,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -87,6 +88,75 @@ __host__ __device__ inline int grid_levels(int bits, int levels)
     if (levels == 0 || levels == (1 << bits)) return 1 << bits;
     if (levels == (1 << (bits - 1)) + 1) return levels;
     return -1;
+}
+
+// ---- b0 + T d for an exact integer sum T, without the FP64 pipe ----
+// The FP64 pipe of this GPU is narrow: a warp-wide FP64 instruction occupies it for ~16 SM
+// clocks, so per-column epilogues that scaled their integer sums in double were bound by it.
+// Scale2f holds a double constant d as (hi + lo) 2^e: hi + lo is d's significand in [0.5, 1)
+// to ~48 bits, split in two floats. A power-of-two rescaling of d is an integer add to e.
+struct Scale2f {
+    float hi, lo;
+    int e;
+};
+
+__host__ __device__ inline Scale2f scale2f_make(double d)
+{
+    int e = 0;
+    const double m = (d == 0.0) ? 0.0 : frexp(d, &e);
+    Scale2f s;
+    s.hi = (float)m;
+    s.lo = (float)(m - (double)s.hi);
+    s.e = e;
+    return s;
+}
+
+// 2^k as a float for k in [-126, 127] (integer operations only)
+__device__ __forceinline__ float pow2f(int k)
+{
+    k = k < -126 ? -126 : (k > 127 ? 127 : k);
+    return __uint_as_float((uint32_t)(k + 127) << 23);
+}
+
+// b0 + T d in FP32 arithmetic, for any T with |T| < 2^63. |T| = F2 + F1 + F0, F_k = c_k 2^(23k)
+// with 0 <= c_k < 2^23 (c_2 < 2^17): exact floats. The three products with hi are formed with
+// their exact FMA errors and summed by TwoSum, the lo terms are added to the error term, the
+// pair is scaled by 2^e in two power-of-two steps (exact unless the result is subnormal), added to
+// b0 by a last TwoSum; one final rounding. Before that rounding the value is within ~2^-44 of
+// b0 + T d relative to |T d| + |b0|.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
+{
+    const float bb = __fsub_rn(s, a);
+    return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float scale2f_apply(long long T, const Scale2f& s, float b0)
+{
+    const bool neg = T < 0;
+    const unsigned long long A = neg ? 0ull - (unsigned long long)T : (unsigned long long)T;
+    auto chunk = [](uint32_t c) { return __fsub_rn(__uint_as_float(0x4B000000u | c), 8388608.0f); };
+    const float F0 = chunk((uint32_t)(A & 0x7fffffu));
+    const float F1 = __fmul_rn(chunk((uint32_t)((A >> 23) & 0x7fffffu)), 8388608.0f);
+    const float F2 = __fmul_rn(chunk((uint32_t)(A >> 46)), 70368744177664.0f);
+    const float h = neg ? -s.hi : s.hi;
+    const float l = neg ? -s.lo : s.lo;
+    const float q2 = __fmul_rn(F2, h), r2 = __fmaf_rn(F2, h, -q2);
+    const float q1 = __fmul_rn(F1, h), r1 = __fmaf_rn(F1, h, -q1);
+    const float q0 = __fmul_rn(F0, h), r0 = __fmaf_rn(F0, h, -q0);
+    const float u1 = __fadd_rn(q2, q1);
+    float t = two_sum_err(q2, q1, u1);
+    const float u = __fadd_rn(u1, q0);
+    t = __fadd_rn(t, two_sum_err(u1, q0, u));
+    t = __fadd_rn(t, __fadd_rn(__fadd_rn(r2, r1), r0));
+    t = __fmaf_rn(F2, l, t);
+    t = __fmaf_rn(F1, l, t);
+    t = __fmaf_rn(F0, l, t);
+    const int e1 = s.e >> 1;
+    const float p1 = pow2f(e1), p2 = pow2f(s.e - e1);       // 2^e in two exact steps
+    const float U = __fmul_rn(__fmul_rn(u, p1), p2);
+    const float V = __fmul_rn(__fmul_rn(t, p1), p2);
+    const float w = __fadd_rn(U, b0);
+    return __fadd_rn(w, __fadd_rn(two_sum_err(U, b0, w), V));
 }
 
 __host__ __device__ inline int codes_per_word(int bits) { return 32 / bits; }

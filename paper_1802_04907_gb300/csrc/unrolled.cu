@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kUdThreads, 2) k_ud_gemvt(const qiht_codes* __
     constexpr int E = G / 4;                    // 4-code positions per word
     constexpr uint32_t MASK = 0x01010101u * ((1u << BITS) - 1);
     extern __shared__ __align__(16) uint32_t planes[];   // 3 x E x ld words
-    __shared__ double s_outscale;
+    __shared__ Scale2f s_outscale;
     __shared__ long long s_R;
     const int p = blockIdx.y;
     const uint32_t* words = Qs[p].words;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kUdThreads, 2) k_ud_gemvt(const qiht_codes* __
     if (threadIdx.x == 0) {
         // alpha 2^-sh and (L-1) sum v~, once per CTA
         const long long lm1 = grid_levels(BITS, Qs[p].levels) - 1;
-        s_outscale = ldexp((double)(*Qs[p].scale) / (double)lm1, -pl_sh[p]) * (double)sign;
+        s_outscale = scale2f_make(ldexp((double)(*Qs[p].scale) / (double)lm1, -pl_sh[p]) * (double)sign);
         s_R = lm1 * pl_rs[p];
     }
     __syncthreads();
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kUdThreads, 2) k_ud_gemvt(const qiht_codes* __
             // scale and offset from shared memory: registers are the limit of the streaming loop
             const long long T = 2 * S - s_R;
             const float b0 = base ? base[(size_t)p * n + jj] : 0.0f;
-            out[(size_t)p * n + jj] = (float)((double)b0 + (double)T * s_outscale);
+            out[(size_t)p * n + jj] = scale2f_apply(T, s_outscale, b0);
         }
     };
     auto advance = [&](int& jj, int& bb) {
