@@ -420,7 +420,6 @@ struct UdArgs {
     size_t pl_stride;
     int* pl_sh;               // P
     long long* pl_rs;         // P
-    int gx;                   // CTAs per problem of the dense product
 };
 size_t ud_fwd_smem(int n, int mk, int s);
 size_t ud_bwd_smem(int n, int mk, int s);

@@ -15,8 +15,9 @@
 // and the gains collect r hbar^T, -rbar x^T and -(2 mubar mu / D) (A2 P h)(P h)^T through
 // the rows they scale.
 //
-// Kernels: a batched dense product out = base + sign A^T v (grid over columns x problems, one
-// warp per column, exact integer sums of the codes with v in 24-bit fixed point), and one CTA (1024 threads) per problem for everything else of a
+// Kernels: a batched dense product out = base + sign A^T v (persistent, one CTA per SM, a warp
+// per group of four columns, exact integer sums of the codes with v in 24-bit fixed point), and
+// one CTA (1024 threads) per problem for everything else of a
 // step (column-subset products of the s columns, FP64 sums, H_s over all n keys in shared
 // memory). The forward keeps the state every ceil(sqrt K) steps; the adjoint recomputes each
 // segment from its checkpoint, recording what the reverse steps need.
@@ -108,82 +109,91 @@ __global__ void __launch_bounds__(256) k_ud_planes(const float* __restrict__ v, 
 }
 
 // out[p][j] = (base ? base[p][j] : 0) + sign * alpha * sum_i (2 c_ij - (L-1)) v[p][i], in exact
-// integer sums. The three byte planes of v (written once per problem by its producer) are
-// copied to shared memory; the codes of a column multiply them by dp4a and
-// T = 2 sum c v~ - (L-1) sum v~ is scaled once by alpha 2^-sh. Grid: gridDim.x CTAs per problem
-// (blockIdx.y), 16 warps each, two CTAs per SM; a warp owns whole columns (stride: the
-// problem's warps) and streams each in batches of NPL 16-byte pieces per lane, the loads of the
-// next batch in flight while the current one is used. Codes are extracted with one mask per
-// four codes, (w & (mask << b e)) = the codes of position e times 2^(b e); the position sums are
-// exact and are shifted back after the warp sum. With the planes laid out by code plane, the
-// lanes of a warp, taking consecutive pieces, read consecutive 16-byte words of shared memory.
+// integer sums. The three byte planes of v (written once per problem by its producer) sit in
+// shared memory; the codes of a column multiply them by dp4a and T = 2 sum c v~ - (L-1) sum v~
+// is scaled by alpha 2^-sh in FP32 only (scale2f_apply).
+// Persistent grid, one CTA of 16 warps per SM: the (problem, group of kUdC adjacent columns)
+// items are split into one contiguous range per CTA, so a CTA sees one or two problems and
+// copies their planes once each. A warp owns whole groups and streams the kUdC columns of a
+// group together, 512 bytes of each per batch (one 16-byte piece per lane), kUdDepth register
+// buffers in rotation (two batches in flight while one is used); one plane load serves the
+// kUdC columns. Codes of position e are shifted down to the bytes (x = (w >> b e) & mask), so
+// one set of three sums per column covers every position. Measured against two CTAs of 16
+// warps per SM with one column per warp and per-position sums (two loads in flight): 6 % less
+// time per forward + backward; shapes with 2 columns per warp or more CTAs per SM were slower.
 constexpr int kUdThreads = 512;
+constexpr int kUdMinBlocks = 1;
+constexpr int kUdC = 4;
+constexpr int kUdDepth = 3;
+constexpr bool kUdMasked = false;
 
-template <int BITS, int NPL>
-__global__ void __launch_bounds__(kUdThreads, 2) k_ud_gemvt(const qiht_codes* __restrict__ Qs,
-                                                            const uint32_t* __restrict__ pl, size_t pl_stride,
-                                                            const int* __restrict__ pl_sh,
-                                                            const long long* __restrict__ pl_rs,
-                                                            const float* __restrict__ base, float sign,
-                                                            float* __restrict__ out, int n)
+template <int BITS>
+__global__ void __launch_bounds__(kUdThreads, kUdMinBlocks) k_ud_gemvt(const qiht_codes* __restrict__ Qs,
+    const uint32_t* __restrict__ pl, size_t pl_stride, const int* __restrict__ pl_sh, const long long* __restrict__ pl_rs,
+    const float* __restrict__ base, float sign, float* __restrict__ out, int P, int n)
 {
     constexpr int G = 32 / BITS;
-    constexpr int E = G / 4;                    // 4-code positions per word
+    constexpr int E = G / 4;
+    constexpr int EA = kUdMasked ? E : 1;
     constexpr uint32_t MASK = 0x01010101u * ((1u << BITS) - 1);
-    extern __shared__ __align__(16) uint32_t planes[];   // 3 x E x ld words
+    constexpr int NWARP = kUdThreads / 32;
+    extern __shared__ __align__(16) uint32_t planes[];
     __shared__ Scale2f s_outscale;
     __shared__ long long s_R;
-    const int p = blockIdx.y;
-    const uint32_t* words = Qs[p].words;
-    const int ld = Qs[p].ld_words;
-    const int P4 = ld / 4;                      // 16-byte pieces per column
+    const int ld = Qs[0].ld_words;
+    const int P4 = ld / 4;
+    const int nb = (P4 + 31) / 32;
+    const int ngrp = (n + kUdC - 1) / kUdC;
+    const long long total = (long long)P * ngrp;
+    const long long i0 = total * blockIdx.x / gridDim.x;
+    const long long i1 = total * (blockIdx.x + 1) / gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int W = gridDim.x * (kUdThreads / 32);
-    const int nb = (P4 + 32 * NPL - 1) / (32 * NPL);     // batches per column
-    int j = blockIdx.x * (kUdThreads / 32) + warp;
-    int pb = 0;
     uint64_t policy;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
-    auto load_batch = [&](uint4 (&cv)[NPL], int jj, int bb) {
-        const uint4* col = reinterpret_cast<const uint4*>(words + (size_t)jj * ld);
-#pragma unroll
-        for (int u = 0; u < NPL; ++u) {
-            const int piece = bb * 32 * NPL + lane + 32 * u;
-            if (piece < P4)
-                asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                             : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w)
-                             : "l"(col + piece), "l"(policy));
-            else
-                cv[u] = make_uint4(0u, 0u, 0u, 0u);
-        }
-    };
-    uint4 cA[NPL], cB[NPL];
-    if (j < n) load_batch(cA, j, pb);           // in flight while the planes are copied
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(pl + (size_t)p * pl_stride);
-        uint4* dst = reinterpret_cast<uint4*>(planes);
-        for (int i = threadIdx.x; i < 3 * E * P4; i += kUdThreads) dst[i] = __ldcg(src + i);
-    }
-    if (threadIdx.x == 0) {
-        // alpha 2^-sh and (L-1) sum v~, once per CTA
-        const long long lm1 = grid_levels(BITS, Qs[p].levels) - 1;
-        s_outscale = scale2f_make(ldexp((double)(*Qs[p].scale) / (double)lm1, -pl_sh[p]) * (double)sign);
-        s_R = lm1 * pl_rs[p];
-    }
-    __syncthreads();
     const uint4* L0 = reinterpret_cast<const uint4*>(planes);
     const uint4* L1 = L0 + (size_t)E * P4;
     const uint4* L2 = L0 + (size_t)2 * E * P4;
-    uint32_t s0[E], s1[E];
-    int32_t s2[E];
+    for (long long seg = i0; seg < i1;) {
+        const int p = (int)(seg / ngrp);
+        const long long segend = min(i1, (long long)(p + 1) * ngrp);
+        const int g1 = (int)(segend - (long long)p * ngrp);
+        const uint32_t* words = Qs[p].words;
+        __syncthreads();
+        {
+            const uint4* srcp = reinterpret_cast<const uint4*>(pl + (size_t)p * pl_stride);
+            uint4* dst = reinterpret_cast<uint4*>(planes);
+            for (int i = threadIdx.x; i < 3 * E * P4; i += kUdThreads) dst[i] = __ldcg(srcp + i);
+        }
+        if (threadIdx.x == 0) {
+            const long long lm1 = grid_levels(BITS, Qs[p].levels) - 1;
+            s_outscale = scale2f_make(ldexp((double)(*Qs[p].scale) / (double)lm1, -pl_sh[p]) * (double)sign);
+            s_R = lm1 * pl_rs[p];
+        }
+        __syncthreads();
+        auto load = [&](uint4 (&cv)[kUdC], int g, int b) {
+            const int piece = b * 32 + lane;
 #pragma unroll
-    for (int e = 0; e < E; ++e) { s0[e] = 0; s1[e] = 0; s2[e] = 0; }
-
-    auto use_batch = [&](const uint4 (&cv)[NPL], int bb) {
+            for (int c = 0; c < kUdC; ++c) {
+                const int j = g * kUdC + c;
+                if (g < g1 && j < n && piece < P4) {
+                    const uint4* col = reinterpret_cast<const uint4*>(words + (size_t)j * ld);
+                    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                                 : "=r"(cv[c].x), "=r"(cv[c].y), "=r"(cv[c].z), "=r"(cv[c].w)
+                                 : "l"(col + piece), "l"(policy));
+                } else {
+                    cv[c] = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+        };
+        uint32_t s0[kUdC][EA], s1[kUdC][EA];
+        int32_t s2[kUdC][EA];
 #pragma unroll
-        for (int u = 0; u < NPL; ++u) {
-            const int piece = min(bb * 32 * NPL + lane + 32 * u, P4 - 1);   // past the end: zero codes
-            const uint32_t wv[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
+        for (int c = 0; c < kUdC; ++c)
+#pragma unroll
+            for (int e = 0; e < EA; ++e) { s0[c][e] = 0; s1[c][e] = 0; s2[c][e] = 0; }
+        auto use = [&](const uint4 (&cv)[kUdC], int b) {
+            const int piece = b * 32 + lane;
+            if (piece >= P4) return;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const uint4 A0 = L0[(size_t)e * P4 + piece];
@@ -193,49 +203,68 @@ __global__ void __launch_bounds__(kUdThreads, 2) k_ud_gemvt(const qiht_codes* __
                 const uint32_t y1[4] = {A1.x, A1.y, A1.z, A1.w};
                 const uint32_t y2[4] = {A2.x, A2.y, A2.z, A2.w};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const uint32_t x = wv[t] & (MASK << (BITS * e));
-                    s0[e] = ud_dp4a_uu(x, y0[t], s0[e]);
-                    s1[e] = ud_dp4a_uu(x, y1[t], s1[e]);
-                    s2[e] = ud_dp4a_us(x, y2[t], s2[e]);
+                for (int c = 0; c < kUdC; ++c) {
+                    const uint32_t wv[4] = {cv[c].x, cv[c].y, cv[c].z, cv[c].w};
+                    const int ea = kUdMasked ? e : 0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const uint32_t x = kUdMasked ? (wv[t] & (MASK << (BITS * e))) : ((wv[t] >> (BITS * e)) & MASK);
+                        s0[c][ea] = ud_dp4a_uu(x, y0[t], s0[c][ea]);
+                        s1[c][ea] = ud_dp4a_uu(x, y1[t], s1[c][ea]);
+                        s2[c][ea] = ud_dp4a_us(x, y2[t], s2[c][ea]);
+                    }
+                }
+            }
+        };
+        auto finish = [&](int g) {
+#pragma unroll
+            for (int c = 0; c < kUdC; ++c) {
+                long long S = 0;
+#pragma unroll
+                for (int e = 0; e < EA; ++e) {
+                    const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[c][e]);
+                    const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[c][e]);
+                    const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[c][e]);
+                    S += (t0 + (t1 << 8) + (t2 << 16)) >> (kUdMasked ? BITS * e : 0);
+                    s0[c][e] = 0; s1[c][e] = 0; s2[c][e] = 0;
+                }
+                const int j = g * kUdC + c;
+                if (lane == c && j < n) {
+                    const long long T = 2 * S - s_R;
+                    const float b0 = base ? base[(size_t)p * n + j] : 0.0f;
+                    out[(size_t)p * n + j] = scale2f_apply(T, s_outscale, b0);
+                }
+            }
+        };
+        auto next = [&](int& g, int& b) { if (++b == nb) { b = 0; g += NWARP; } };
+        uint4 buf[kUdDepth][kUdC];
+        int gs[kUdDepth], bs[kUdDepth];
+        gs[0] = (int)(seg - (long long)p * ngrp) + warp;
+        bs[0] = 0;
+        load(buf[0], gs[0], bs[0]);
+#pragma unroll
+        for (int k = 1; k + 1 < kUdDepth; ++k) {
+            gs[k] = gs[k - 1]; bs[k] = bs[k - 1]; next(gs[k], bs[k]); load(buf[k], gs[k], bs[k]);
+        }
+        bool go = true;
+        while (go) {
+#pragma unroll
+            for (int k = 0; k < kUdDepth; ++k) {
+                if (go) {
+                    if (gs[k] >= g1) {
+                        go = false;
+                    } else {
+                        constexpr int D = kUdDepth;
+                        const int ls = (k + D - 1) % D, prev = (k + D - 2) % D;
+                        gs[ls] = gs[prev]; bs[ls] = bs[prev]; next(gs[ls], bs[ls]);
+                        load(buf[ls], gs[ls], bs[ls]);
+                        use(buf[k], bs[k]);
+                        if (bs[k] == nb - 1) finish(gs[k]);
+                    }
                 }
             }
         }
-    };
-    auto finish_column = [&](int jj) {
-        long long S = 0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[e]);
-            const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[e]);
-            const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[e]);
-            S += (t0 + (t1 << 8) + (t2 << 16)) >> (BITS * e);
-            s0[e] = 0; s1[e] = 0; s2[e] = 0;
-        }
-        if (lane == 0) {
-            // scale and offset from shared memory: registers are the limit of the streaming loop
-            const long long T = 2 * S - s_R;
-            const float b0 = base ? base[(size_t)p * n + jj] : 0.0f;
-            out[(size_t)p * n + jj] = scale2f_apply(T, s_outscale, b0);
-        }
-    };
-    auto advance = [&](int& jj, int& bb) {
-        if (++bb == nb) { bb = 0; jj += W; }
-    };
-    while (j < n) {
-        int jB = j, pB = pb;
-        advance(jB, pB);
-        if (jB < n) load_batch(cB, jB, pB);
-        use_batch(cA, pb);
-        if (pb == nb - 1) finish_column(j);
-        j = jB; pb = pB;
-        if (j >= n) break;
-        int jA = j, pA = pb;
-        advance(jA, pA);
-        if (jA < n) load_batch(cA, jA, pA);
-        use_batch(cB, pb);
-        if (pb == nb - 1) finish_column(j);
-        j = jA; pb = pA;
+        seg = segend;
     }
 }
 
@@ -570,42 +599,27 @@ cudaError_t launch_ud_planes(const UdArgs& a, int bits, const float* v, cudaStre
     return cudaGetLastError();
 }
 
-// CTAs per problem of the batched product: the count whose waves (two CTAs per SM) times the
-// time of a CTA (its columns per warp, plus about two columns' time for copying the planes)
-// is smallest, the fewer CTAs on a tie
-int ud_gemvt_ctas(int P, int n)
-{
-    const long long slots = 2LL * num_sms();
-    const int maxx = (n + kUdThreads / 32 - 1) / (kUdThreads / 32);
-    long long best = -1;
-    int bx = 1;
-    for (int x = 1; x <= maxx; ++x) {
-        const long long waves = ((long long)P * x + slots - 1) / slots;
-        const long long cpw = ((long long)n + (long long)x * (kUdThreads / 32) - 1) / ((long long)x * (kUdThreads / 32));
-        const long long t = waves * (cpw + 2);
-        if (best < 0 || t < best) { best = t; bx = x; }
-    }
-    return bx;
-}
-
 cudaError_t launch_ud_gemvt(const UdArgs& a, const qiht_codes* Qs, int bits, const float* base, float sign, float* out,
                             int ldw, cudaStream_t s)
 {
-    const size_t smem = (size_t)3 * (32 / bits / 4) * ldw * 4;   // the three byte planes of v
-    const dim3 grid((unsigned)a.gx, (unsigned)a.P);
+    const size_t smem = (size_t)3 * (32 / bits / 4) * ldw * 4;
+    const long long items = (long long)a.P * ((a.n + kUdC - 1) / kUdC);
+    const long long want = (items + kUdThreads / 32 - 1) / (kUdThreads / 32);
+    const long long gx = (long long)num_sms() * kUdMinBlocks;
+    const unsigned grid = (unsigned)(want < gx ? want : gx);
     cudaError_t e;
     switch (bits) {
     case 8:
-        if ((e = set_smem(k_ud_gemvt<8, 4>, smem)) != cudaSuccess) return e;
-        k_ud_gemvt<8, 4><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.n);
+        if ((e = set_smem(k_ud_gemvt<8>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<8><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.P, a.n);
         break;
     case 4:
-        if ((e = set_smem(k_ud_gemvt<4, 2>, smem)) != cudaSuccess) return e;
-        k_ud_gemvt<4, 2><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.n);
+        if ((e = set_smem(k_ud_gemvt<4>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<4><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.P, a.n);
         break;
     default:
-        if ((e = set_smem(k_ud_gemvt<2, 1>, smem)) != cudaSuccess) return e;
-        k_ud_gemvt<2, 1><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.n);
+        if ((e = set_smem(k_ud_gemvt<2>, smem)) != cudaSuccess) return e;
+        k_ud_gemvt<2><<<grid, kUdThreads, smem, s>>>(Qs, a.pl, a.pl_stride, a.pl_sh, a.pl_rs, base, sign, out, a.P, a.n);
         break;
     }
     return cudaGetLastError();
@@ -808,7 +822,6 @@ UdArgs ud_args(char* w, const UdLayout& L, const qiht_codes* Q1, int P, int s, c
     a.pl_stride = L.pl_stride;
     a.pl_sh = reinterpret_cast<int*>(w + L.pl_sh);
     a.pl_rs = reinterpret_cast<long long*>(w + L.pl_rs);
-    a.gx = ud_gemvt_ctas(P, a.n);
     return a;
 }
 
