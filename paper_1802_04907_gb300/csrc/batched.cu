@@ -17,6 +17,9 @@ namespace {
 
 constexpr int kBT = 1024;                 // threads per CTA
 constexpr int kBWarps = kBT / 32;
+// bmax, bsum_ll and bexcl_scan combine one partial per warp in warp 0, lane w reading warp w's
+// slot: they need exactly 32 warps (with fewer, the upper lanes would read stale slots)
+static_assert(kBWarps == 32, "the CTA reductions take one partial from each of 32 warps");
 constexpr int kBItems = 4;                // loads of a lane in flight (64 registers per thread)
 
 __device__ __forceinline__ uint32_t bdp4a_uu(uint32_t a, uint32_t b, uint32_t c)
