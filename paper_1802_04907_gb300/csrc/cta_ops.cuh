@@ -11,6 +11,9 @@ namespace cta {
 namespace {                               // internal linkage in every including unit
 
 constexpr int kST = 1024;                 // threads per CTA
+// ssum, smax and sscan combine one partial per warp in warp 0 (lane w reads warp w's slot):
+// every kernel that calls them runs kST threads, 32 warps
+static_assert(kST == 1024, "the CTA reductions take one partial from each of 32 warps");
 constexpr int kSW = kST / 32;
 
 struct SSh {
