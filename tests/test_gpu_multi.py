@@ -49,6 +49,30 @@ def test_gemv_t_multi(bits, m, n, nrhs):
     assert np.all(G[nrhs // 2] == 0.0)
 
 
+def test_gemv_t_multi_full_size_sampled():
+    # the product of the many-right-hand-side workload at full size, in the launch the solver makes
+    # every iteration: Q1 of the 8192 x 32768 matrix (8-bit) against 1024 residuals; sampled
+    # columns of G against the oracle for every right-hand side
+    p = synth.large_noisy(seed=0)
+    nrhs = 1024
+    R = synth.random_floats((nrhs, p.m), seed=91, scale=0.05)
+    R[:, p.m // 5] *= 40.0                                    # wide dynamic range
+    Q = q.quantize(torch.from_numpy(p.phi).cuda(), 8, 5, 0)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    G = q.gemv_t_multi(Q, torch.from_numpy(R).cuda(), status=status).cpu().numpy().astype(np.float64)
+    assert status.item() == q.OK and G.shape == (nrhs, p.n)
+    c, _ = oracle.absmax(p.phi)
+    rng = np.random.Generator(np.random.PCG64(5))
+    R64 = R.astype(np.float64)
+    for j in np.concatenate([[0, 255, 256, p.n - 1], rng.choice(p.n, 16, replace=False)]):
+        codes, _ = oracle.quantize(np.ascontiguousarray(p.phi[:, j]), 8, 5, 0, c, col0=int(j), rows_total=p.m)
+        col = oracle.dequantize(codes, 8, c)
+        ref = (R64 @ col)[:, None]                            # nrhs x 1
+        bound = _multi_bound(codes[:, None], 255, c, R, ref)
+        err = np.abs(G[:, j:j + 1] - ref)
+        assert np.all(err <= bound), (j, (err / bound).max())
+
+
 def test_gemv_t_multi_matches_single_products():
     # the same residuals through the exact integer GEMV^T one by one
     m, n, nrhs = 2048, 1000, 40

@@ -126,3 +126,58 @@ def test_autograd_function_and_repeat_calls():
     torch.cuda.synchronize()
     assert torch.equal(X.detach(), X2)
     assert torch.equal(y.grad, yb) and torch.equal(ga.grad, ab) and torch.equal(gb.grad, bb)
+
+
+def test_full_size_sampled_problems():
+    # the differentiation workload at full size, in the launch configuration of the benchmark:
+    # 64 problems, Gaussian Phi 2048 x 8192 N(0, 1/m), s = 64, 4-bit codes, per-row complex gain,
+    # 30 dB, K = 50 unrolled iterations with sqrt(K) checkpoints; three sampled problems (first,
+    # middle, last) against the oracle's forward and adjoint
+    P, m, n, s, K, bits = 64, 2048, 8192, 64, 50, 4
+    pick = (0, 31, 63)
+    rng = np.random.Generator(np.random.PCG64(2048))
+    Q1s, Q2s, Y, GA, GB, XT, keep = [], [], [], [], [], [], {}
+    for p in range(P):
+        phi = rng.standard_normal((m, n), dtype=np.float32) * np.float32(1.0 / np.sqrt(m))
+        sup = rng.choice(n, s, replace=False)
+        x = np.zeros(n)
+        x[sup] = rng.standard_normal(s)
+        mag, ph = rng.uniform(0.9, 1.1, m), rng.uniform(-0.1, 0.1, m)
+        a, b = (mag * np.cos(ph)).astype(np.float32), (mag * np.sin(ph)).astype(np.float32)
+        px = phi[:, sup].astype(np.float64) @ x[sup]
+        clean = np.concatenate([a * px, b * px])
+        y = (clean + np.sqrt(clean @ clean / (2 * m * 1e3)) * rng.standard_normal(2 * m)).astype(np.float32)
+        q1, q2 = q.quantize_pair(torch.from_numpy(phi).cuda(), bits, 100 + p, q.STREAM_Q1, q.STREAM_Q2)
+        Q1s.append(q1)
+        Q2s.append(q2)
+        Y.append(y)
+        GA.append(a)
+        GB.append(b)
+        XT.append(x.astype(np.float32))
+        if p in pick:
+            keep[p] = (phi, x, a, b, y)
+    Yt, GAt, GBt, XTt = (torch.from_numpy(np.stack(v)).cuda() for v in (Y, GA, GB, XT))
+    op = q.Unrolled(Q1s, Q2s, s, K)
+    X = op.forward(Yt, GAt, GBt)
+    yb, ab, bb = op.backward(Yt, GAt, GBt, 2.0 * (X - XTt))
+    torch.cuda.synchronize()
+    X, yb, ab, bb = (t.cpu().numpy().astype(np.float64) for t in (X, yb, ab, bb))
+    assert np.all(np.isfinite(X)) and np.all(np.isfinite(yb)) and np.all(np.isfinite(ab))
+    assert all(np.count_nonzero(X[p]) <= s for p in range(P))
+    checked = 0
+    for p in pick:
+        phi, x, a, b, y = keep[p]
+        c1, sc = oracle.quantize(phi, bits, 100 + p, 0)
+        c2, _ = oracle.quantize(phi, bits, 100 + p, 1, sc)
+        P1, P2 = oracle.dequantize(c1, bits, sc), oracle.dequantize(c2, bits, sc)
+        xK, steps = unrolled.forward(P1, P2, y, a, b, s, K)
+        if _min_gap(steps, s) < 1e-5:
+            continue
+        checked += 1
+        assert np.array_equal(np.flatnonzero(X[p]), np.flatnonzero(xK)), p
+        assert np.linalg.norm(X[p] - xK) <= 1e-4 * np.linalg.norm(xK), p
+        gy, ga, gb = unrolled.backward(P1, P2, a, b, steps, 2.0 * (xK - x))
+        for got, want, name in ((yb[p], gy, "y"), (ab[p], ga, "a"), (bb[p], gb, "b")):
+            rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
+            assert rel <= 5e-3, (p, name, rel)
+    assert checked >= 2
