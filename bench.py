@@ -220,6 +220,20 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def start_clocks(dev):
+    """nvidia-smi clock sampling of this GPU, started before a timed region."""
+    import torch
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clk = Clocks(uuid)
+    clk.start()
+    time.sleep(0.3)
+    return clk
+
+
 def traffic_for_kernel(bits, m, n):
     """DRAM bytes per launch of the gradient kernel from the committed ncu summary
     (profiles/gemv_t_traffic.txt), only while the kernel source is unchanged since
@@ -491,6 +505,8 @@ def run_batched(args):
     for _ in range(max(1, args.warmup)):
         res = q.niht_solve_batched(probs, iters)
     torch.cuda.synchronize()
+    clk = start_clocks(torch.device("cuda", torch.cuda.current_device()))
+    torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for _ in range(args.steps):
@@ -498,6 +514,7 @@ def run_batched(args):
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = clk.stop()
     reps = res.all_reports()
     it_done = sum(r.iters_run for r in reps)
     err_b = rel_err(res.x)
@@ -531,6 +548,7 @@ def run_batched(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "note": "Q1 code bytes streamed per iteration over the launch time"},
             "statuses": {str(k): sum(1 for r in reps if r.status == k) for k in sorted({r.status for r in reps})}}
+    line["clocks"] = clocks
     print(json.dumps(line))
 
 
@@ -675,6 +693,8 @@ def run_fresh(args):
     for _ in range(max(1, args.warmup)):
         sv = q.niht_solve_fresh(phi, y, bits, bits, 5, s, iters)
     torch.cuda.synchronize()
+    clk = start_clocks(torch.device("cuda", torch.cuda.current_device()))
+    torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for _ in range(args.steps):
@@ -682,6 +702,7 @@ def run_fresh(args):
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = clk.stop()
     rep = sv.read_report()
     err = float(torch.linalg.norm(sv.x - xt) / torch.linalg.norm(xt))
     q1, q2, qy = q.quantize_problem(phi, y, bits, bits, 5)
@@ -704,6 +725,7 @@ def run_fresh(args):
             "ms_per_iteration": ms / max(1, rep.iters_run),
             "fixed_quantizations": {"iterations_per_s": iters / (ms_fx / 1e3), "rel_err": err_fx},
             "rel_err": err, "status": rep.status, "gpu_launches": None}
+    line["clocks"] = clocks
     print(json.dumps(line))
 
 
@@ -751,6 +773,8 @@ def run_unrolled(args):
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize()
+    clk = start_clocks(torch.device("cuda", torch.cuda.current_device()))
+    torch.cuda.synchronize()
     ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     t_fwd = t_all = 0.0
     for _ in range(args.steps):
@@ -763,6 +787,7 @@ def run_unrolled(args):
         t_fwd += ev0.elapsed_time(ev1)
         t_all += ev0.elapsed_time(ev2)
     ms = t_all / args.steps
+    clocks = clk.stop()
     loss = float(((X - XT) ** 2).sum())
     rel = float(torch.linalg.norm(X - XT) / torch.linalg.norm(XT))
     codes = sum(qq.nbytes for qq in Q1s) + sum(qq.nbytes for qq in Q2s)
@@ -785,7 +810,7 @@ def run_unrolled(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "note": "3K dense code passes (forward, recomputation, adjoint) over the step time; "
                                  "the per-problem step kernels are not counted"},
-            "gpu_launches": ud_launches}
+            "clocks": clocks, "gpu_launches": ud_launches}
     print(json.dumps(line))
 
 
