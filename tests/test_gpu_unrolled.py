@@ -181,3 +181,39 @@ def test_full_size_sampled_problems():
             rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
             assert rel <= 5e-3, (p, name, rel)
     assert checked >= 2
+
+
+def test_zero_iterations_give_zero_output_and_gradients():
+    P, m, n, s = 2, 64, 200, 5
+    probs, refs, op, Y, GA, GB, XT = _setup(P, m, n, s, 8, 0, seed=3)
+    X = op.forward(Y, GA, GB)
+    yb, ab, bb = op.backward(Y, GA, GB, 2.0 * (X - XT))
+    torch.cuda.synchronize()
+    assert torch.all(X == 0)
+    assert torch.all(yb == 0) and torch.all(ab == 0) and torch.all(bb == 0)
+
+
+@pytest.mark.parametrize("bits,K,P,m,n,s", [(8, 1, 3, 40, 37, 1),      # one step, s = 1, n off every tile
+                                            (4, 2, 2, 16, 64, 16),     # s = m
+                                            (2, 3, 2, 33, 129, 7)])
+def test_edge_shapes_against_oracle(bits, K, P, m, n, s):
+    probs, refs, op, Y, GA, GB, XT = _setup(P, m, n, s, bits, K, seed=bits + 7 * K + m)
+    X = op.forward(Y, GA, GB)
+    yb, ab, bb = op.backward(Y, GA, GB, 2.0 * (X - XT))
+    torch.cuda.synchronize()
+    X, yb, ab, bb = (t.cpu().numpy().astype(np.float64) for t in (X, yb, ab, bb))
+    checked = 0
+    for p, (phi, x, a, b, y) in enumerate(probs):
+        P1, P2 = refs[p]
+        xK, steps = unrolled.forward(P1, P2, y, a, b, s, K)
+        assert np.count_nonzero(X[p]) <= s
+        if s < n and _min_gap(steps, s) < 1e-5:
+            continue
+        checked += 1
+        assert np.array_equal(np.flatnonzero(X[p]), np.flatnonzero(xK)), p
+        assert np.linalg.norm(X[p] - xK) <= 1e-4 * max(np.linalg.norm(xK), 1e-30), p
+        gy, ga, gb = unrolled.backward(P1, P2, a, b, steps, 2.0 * (xK - x))
+        for got, want, name in ((yb[p], gy, "y"), (ab[p], ga, "a"), (bb[p], gb, "b")):
+            rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
+            assert rel <= 2e-3, (p, name, rel)
+    assert checked >= 1
