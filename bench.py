@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gemv-launches", type=int, default=200)
-    ap.add_argument("--workload", choices=["single", "interferometry", "batched", "multi", "fresh", "unrolled"], default="single",
+    ap.add_argument("--workload", choices=["single", "interferometry", "mri", "batched", "multi", "fresh", "unrolled"], default="single",
                     help="single: the large single solve (default); batched: 512 independent problems in one "
                          "launch; multi: 1024 right-hand sides sharing the large matrix (tensor-core gradient)")
     ap.add_argument("--nprob", type=int, default=512)
@@ -81,6 +81,17 @@ def dist_env():
 
 
 def config(args, world):
+    if args.workload == "mri":
+        return {"workload": f"MRI-shaped single solve: radial k-space samples (a third of a 128x128 grid) of the "
+                            f"orthonormal 2D DFT of a 2D Haar synthesis, stacked real {args.m}x{args.n}, synthetic "
+                            f"head image with its s={args.s} largest Haar coefficients, 30 dB, Phi quantized to "
+                            f"{args.bits} bits, y to {args.bits_y or args.bits} bits, {args.iters} iterations",
+                "m": args.m, "n": args.n, "s": args.s, "bits_phi": args.bits, "bits_y": args.bits_y or args.bits,
+                "iters_per_step": args.iters, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                "l2": "Q1 codes %.0f MiB per iteration; L2 flushed between timed steps by the quantization "
+                      "of Phi (%.0f MiB of FP32 read)" % (args.m * args.n * args.bits / 8 / 2**20,
+                                                          args.m * args.n * 4 / 2**20),
+                "step": "max|Phi|, max|y|, quantize Q1, Q2, Q(y), one solve (one graph launch)"}
     if args.workload == "interferometry":
         return {"workload": f"interferometry-shaped single solve: 48 antennas uniform in a 1 km disk, "
                             f"Phi_kp = exp(-2 pi i (u_k l_p + v_k m_p)) over 2256 baselines x 128x128 pixels, "
@@ -281,6 +292,9 @@ def run_ours(args):
 
     if args.workload == "interferometry":
         p = synth.interferometry(seed=rank)
+        args.m, args.n, args.s = p.phi.shape[0], p.phi.shape[1], p.s
+    elif args.workload == "mri":
+        p = synth.mri(seed=rank)
         args.m, args.n, args.s = p.phi.shape[0], p.phi.shape[1], p.s
     else:
         p = synth.large_noisy(seed=rank, m=args.m, n=args.n, s=args.s)

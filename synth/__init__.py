@@ -12,7 +12,9 @@ Workloads follow the shapes and distributions of the paper's experiments
 noisy observations at a stated SNR, and a radio-interferometry measurement
 matrix built from antenna positions and a pixel grid (Section IV-B, radio
 astronomy). The LOFAR recordings are not available, so the interferometry
-workload is synthetic: random antenna layout, point sources at random pixels.
+workload is synthetic: random antenna layout, point sources at random pixels. The MRI
+workload (Section IV-B, magnetic resonance imaging) samples k-space of a Haar-sparse
+synthetic head image on radial lines; the paper's brain image is not available either.
 """
 from __future__ import annotations
 
@@ -127,6 +129,100 @@ def interferometry(n_ant: int = 48, grid: int = 128, n_src: int = 50, s: int = 6
                    name=name or f"interferometry_{2 * k}x{n}_s{s}",
                    meta={"snr_db": snr_db, "n_ant": n_ant, "grid": grid, "n_src": n_src,
                          "seed": seed, "wavelength_m": wavelength_m})
+
+
+def haar_synthesis(N: int) -> np.ndarray:
+    """Orthonormal multilevel 1D Haar basis as an N x N synthesis matrix (N a power of two): a
+    signal is H^T-analysed to coefficients c = H v and rebuilt as v = H^T c. Built by the usual
+    recursion: the rows of H_2N are the rows of H_N with every entry duplicated (coarse
+    functions), then the N finest differences, all scaled by 1/sqrt(2)."""
+    if N < 1 or N & (N - 1):
+        raise ValueError("N must be a power of two")
+    H = np.ones((1, 1))
+    while H.shape[0] < N:
+        k = H.shape[0]
+        coarse = np.kron(H, np.array([[1.0, 1.0]]))
+        fine = np.kron(np.eye(k), np.array([[1.0, -1.0]]))
+        H = np.vstack([coarse, fine]) / np.sqrt(2.0)
+    return H.T                                   # columns = basis vectors (synthesis)
+
+
+def radial_mask(N: int, fraction: float = 1.0 / 3.0) -> np.ndarray:
+    """k-space positions (k1, k2) in DFT index order (0 .. N-1) on radial lines through the
+    centre, closed under reflection through the centre, with as few equally spaced lines as
+    reach the given fraction of the N x N grid (the paper undersamples k-space by a factor of 3
+    with a radial mask, Section IV-B)."""
+    c = N // 2
+    r = np.arange(-c, c, 0.5)
+    for lines in range(1, 4 * N):
+        th = np.pi * np.arange(lines) / lines
+        u = np.rint(np.outer(np.cos(th), r)).astype(np.int64).ravel()
+        v = np.rint(np.outer(np.sin(th), r)).astype(np.int64).ravel()
+        keep = (u >= -c) & (u <= c) & (v >= -c) & (v <= c)
+        u, v = u[keep] % N, v[keep] % N
+        # with each position its reflection through the centre (the k-space of a real image is
+        # conjugate-symmetric, and the lines pass through the centre)
+        pos = np.unique(np.concatenate([u * N + v, ((-u) % N) * N + ((-v) % N)]))
+        if pos.size >= fraction * N * N:
+            return np.stack([pos // N, pos % N], axis=1)
+    raise RuntimeError("mask fraction not reached")
+
+
+def head_phantom(N: int) -> np.ndarray:
+    """A piecewise-constant head-like image (N x N): an outer shell, a darker interior and a few
+    small ellipses of different intensities (a stand-in for the paper's brain image)."""
+    yy, xx = np.mgrid[-1:1:complex(0, N), -1:1:complex(0, N)]
+    img = np.zeros((N, N))
+    # (intensity, centre x, centre y, half axis a, half axis b, angle in degrees)
+    for val, x0, y0, a, b, ang in [(1.0, 0.0, 0.0, 0.70, 0.92, 0), (-0.75, 0.0, -0.02, 0.65, 0.86, 0),
+                                   (-0.2, 0.2, 0.05, 0.12, 0.30, -16), (-0.2, -0.22, 0.05, 0.16, 0.38, 16),
+                                   (0.15, 0.0, 0.38, 0.22, 0.26, 0), (0.1, 0.0, -0.55, 0.05, 0.05, 0),
+                                   (0.1, -0.08, -0.6, 0.05, 0.025, 0), (0.1, 0.06, -0.6, 0.025, 0.05, 0),
+                                   (0.12, 0.3, -0.25, 0.06, 0.1, 30)]:
+        t = np.deg2rad(ang)
+        xr = (xx - x0) * np.cos(t) + (yy - y0) * np.sin(t)
+        yr = -(xx - x0) * np.sin(t) + (yy - y0) * np.cos(t)
+        img[(xr / a) ** 2 + (yr / b) ** 2 <= 1.0] += val
+    return img
+
+
+def mri(grid: int = 128, s: int = 512, snr_db: float = 30.0, seed: int = 0, *,
+        fraction: float = 1.0 / 3.0, name: str | None = None) -> Problem:
+    """MRI-shaped instance (Section IV-B, magnetic resonance imaging), stacked to a real system.
+
+    Phi = S F W^-1: W^-1 the 2D orthonormal Haar synthesis (tensor product of the 1D basis of
+    haar_synthesis), F the orthonormal 2D DFT, S the radial k-space mask of radial_mask (a third
+    of the grid). With A = F_1 H^T (N x N, unitary), the k-space sample at (k1, k2) of the
+    coefficient image C is sum A[k1, j1] A[k2, j2] C[j1, j2], so the row of Phi for that sample
+    is kron(A[k1], A[k2]) over the coefficient index j1 N + j2. The real and imaginary parts are
+    stacked: [Re Phi; Im Phi] x = [Re y; Im y]. x is the s largest Haar coefficients of
+    head_phantom (exactly s-sparse); y = Phi x + complex Gaussian noise at the given SNR. The
+    paper's brain image and SparseMRI are not available, so the image is synthetic.
+    """
+    N = grid
+    H = haar_synthesis(N)
+    F = np.exp(-2j * np.pi * np.outer(np.arange(N), np.arange(N)) / N) / np.sqrt(N)
+    A = F @ H                                            # N x N, unitary
+    ks = radial_mask(N, fraction)
+    k = ks.shape[0]
+    n = N * N
+    phi = np.empty((2 * k, n), dtype=np.float32)
+    for b0 in range(0, k, 512):
+        b1 = min(k, b0 + 512)
+        rows = (A[ks[b0:b1, 0]][:, :, None] * A[ks[b0:b1, 1]][:, None, :]).reshape(b1 - b0, n)
+        phi[b0:b1] = rows.real
+        phi[k + b0:k + b1] = rows.imag
+    coef = H.T @ head_phantom(N) @ H                     # analysis: C = H_a X H_a^T, H_a = H^T
+    flat = coef.ravel()
+    support = np.sort(np.argsort(-np.abs(flat), kind="stable")[:s]).astype(np.int64)
+    x = np.zeros(n)
+    x[support] = flat[support]
+    clean = phi[:, support].astype(np.float64) @ x[support]
+    rng = _rng(seed)
+    y = clean + _noise_sigma(clean, snr_db) * rng.standard_normal(2 * k)
+    return Problem(phi=phi, y=y.astype(np.float32), x_true=x, support=support, s=s,
+                   name=name or f"mri_{2 * k}x{n}_s{s}",
+                   meta={"snr_db": snr_db, "grid": N, "fraction": fraction, "samples": k, "seed": seed})
 
 
 # Named workloads (sizes from the configurations this library is measured on).

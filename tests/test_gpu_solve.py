@@ -50,7 +50,7 @@ def _first_ambiguous(ref):
     return None
 
 
-def _check(sv, ref, p, label=""):
+def _check(sv, ref, p, label="", mu_tol=1e-4):
     rep = sv.read_report()
     assert rep.status == ref.status, (rep, ref.status)
     amb = _first_ambiguous(ref)
@@ -61,7 +61,7 @@ def _check(sv, ref, p, label=""):
     for t in range(0, T + 1):
         assert np.array_equal(sup[t], rsup[t]), f"{label}: support differs at iteration {t}"
         if t > 0 and (t <= 3 or not np.array_equal(rsup[t], rsup[t - 1])):
-            assert abs(mu[t] - ref.trace["mu"][t]) <= 1e-4 * ref.trace["mu"][t], f"{label}: mu at {t}"
+            assert abs(mu[t] - ref.trace["mu"][t]) <= mu_tol * ref.trace["mu"][t], f"{label}: mu at {t}"
     x = sv.x.cpu().numpy().astype(np.float64)
     assert np.count_nonzero(x) <= p.s
     truth = np.linalg.norm(p.x_true)
@@ -113,6 +113,27 @@ def test_interferometry_small():
     p = synth.interferometry(n_ant=12, grid=32, n_src=6, s=8, snr_db=20.0, seed=2)
     sv, ref = _run_pair(p, 8, 8, 60, seed=1)
     _check(sv, ref, p, "interferometry")
+
+
+def test_mri_small():
+    # MRI-shaped: radial k-space samples (a third of a 32 x 32 grid) of a Haar-sparse head image,
+    # stacked real 696 x 1024, s = 48, 30 dB, 8-bit
+    p = synth.mri(grid=32, s=48, seed=1)
+    sv, ref = _run_pair(p, 8, 8, 100, seed=3)
+    # on this operator the iteration amplifies rounding in mu: a CPU emulation of the FP32 vectors
+    # and the 24-bit fixed-point residual drifts from the FP64 iteration by 1e-4 in mu after ~30
+    # iterations and 2.5e-4 after 96, while x stays within 1.1e-6; supports and x are checked as
+    # everywhere, mu to 1e-3
+    _check(sv, ref, p, "mri-32", mu_tol=1e-3)
+
+
+def test_mri_full_size():
+    # the MRI-shaped workload at full size: 128 x 128 image, stacked real 11364 x 16384, s = 512,
+    # 30 dB, 8-bit; 20 iterations against the oracle
+    p = synth.mri(seed=0)
+    assert p.phi.shape == (11364, 16384)
+    sv, ref = _run_pair(p, 8, 8, 20, seed=2)
+    _check(sv, ref, p, "mri-128")
 
 
 def test_backtracking_instance():
