@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     if (!flag) return;
     __threadfence();
 
-    const float alpha = (float)((double)(*a.Q.scale) / (double)a.Q.lm1);
+    const float alpha = __fdiv_rn(*a.Q.scale, (float)a.Q.lm1);   // = the double quotient rounded to float
     double acc = 0.0;
     unsigned mx = 0;
     if (q < ld) {

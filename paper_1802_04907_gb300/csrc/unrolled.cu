@@ -277,7 +277,7 @@ __device__ void ucol_dots(const Codes& Q, const int* list, int count, const floa
     constexpr int G = 32 / BITS;
     constexpr uint32_t MASK = (1u << BITS) - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float alpha = (float)((double)(*Q.scale) / (double)Q.lm1);
+    const float alpha = __fdiv_rn(*Q.scale, (float)Q.lm1);     // = the double quotient rounded to float
     const float lm1f = (float)Q.lm1;
     for (int e = warp; e < count; e += kST / 32) {
         const uint32_t* col = Q.words + (size_t)list[e] * Q.ld;
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kST, 1) k_ud_fwd(UdArgs a)
         for (int o = 16; o; o >>= 1) N += __shfl_xor_sync(0xffffffffu, N, o);
     }
     mcols<BITS>(Q2, sm.sup, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
-    const float alpha2 = (float)((double)(*Q2.scale) / (double)Q2.lm1);
+    const float alpha2 = __fdiv_rn(*Q2.scale, (float)Q2.lm1);  // FP32: every thread computes it
     double D = 0.0;
     for (int i = tid; i < m; i += kST) {
         const float ui = alpha2 * sm.z[i];
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kST, 1) k_ud_bwd(UdArgs a, const float* __rest
     const int uc = us.code;
     // p = Phi1 hbar; rbar = [a p; b p]
     mcols<BITS>(Q1, sm.uni, sm.dlt, uc, sm.z, reinterpret_cast<float*>(sm.keys));
-    const float alpha1 = (float)((double)(*Q1.scale) / (double)Q1.lm1);
+    const float alpha1 = __fdiv_rn(*Q1.scale, (float)Q1.lm1);  // FP32: every thread computes it
     const float c3 = D > 0.0 ? (float)(-2.0 * mubar * mu / D) : 0.0f;
     float* yb = ybar + (size_t)p * 2 * m;
     float* gab = gabar + (size_t)p * m;
