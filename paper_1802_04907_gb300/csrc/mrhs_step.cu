@@ -109,13 +109,15 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
         for (int o = 16; o; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
     }
     mcols<BITS>(a.Q2, sm.sup, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
-    double zz = 0.0;
+    // sums of squares: each thread's <= 16 terms in FP32, the CTA sum of the partials in FP64
+    // (a per-element FP64 sum keeps the narrow FP64 pipe of this GPU busy for microseconds)
+    float zzf = 0.0f;
     float* zmu = a.zmu + (size_t)k * m;             // kept for the residual update
     for (int i = tid; i < m; i += kST) {
-        zz += (double)sm.z[i] * (double)sm.z[i];
+        zzf = fmaf(sm.z[i], sm.z[i], zzf);
         zmu[i] = sm.z[i];
     }
-    zz = ssum(zz, sh.d);
+    const double zz = ssum((double)zzf, sh.d);
     if (tid == 0) {
         const double den = sh.alpha2 * sh.alpha2 * zz;
         int code = 0;
@@ -146,9 +148,9 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
             for (int o = 16; o; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
         }
         mcols<BITS>(a.Q2, sm.uni, sm.dlt, uc, sm.z, reinterpret_cast<float*>(sm.keys));
-        double dz = 0.0;
-        for (int i = tid; i < m; i += kST) dz += (double)sm.z[i] * (double)sm.z[i];
-        dz = ssum(dz, sh.d);
+        float dzf = 0.0f;
+        for (int i = tid; i < m; i += kST) dzf = fmaf(sm.z[i], sm.z[i], dzf);
+        const double dz = ssum((double)dzf, sh.d);
         if (tid == 0) {
             const double dd = sh.alpha2 * sh.alpha2 * dz;
             int code = 0;                                   // 0 accept, 1 shrink, 2 give up
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
     // residual: r - alpha2 Q2 (x' - x) with the product already formed for this step (the
     // backtracking test's Q2 (x' - x) if G' != G, else mu Q2_G g_G of the step size), or
     // directly r = Q(y) - alpha2 Q2_G' x' on refresh iterations (periodically and on the last)
-    double rr = 0.0;
+    float rrf = 0.0f;
     float* rk = a.resid + (size_t)k * m;
     if (a.refresh) {
         mcols<BITS>(a.Q2, sm.sel, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
@@ -194,14 +196,14 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
             const float ri = fmaf(-sh.alpha2f, sm.z[i], __ldg(yk + i));
             sm.z[i] = ri;
             rk[i] = ri;
-            rr += (double)ri * (double)ri;
+            rrf = fmaf(ri, ri, rrf);
         }
     } else if (changed) {
         for (int i = tid; i < m; i += kST) {
             const float ri = fmaf(-sh.alpha2f, sm.z[i], rk[i]);
             sm.z[i] = ri;
             rk[i] = ri;
-            rr += (double)ri * (double)ri;
+            rrf = fmaf(ri, ri, rrf);
         }
     } else {
         const float cz = sh.alpha2f * sh.muf;
@@ -209,10 +211,10 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
             const float ri = fmaf(-cz, zmu[i], rk[i]);
             sm.z[i] = ri;
             rk[i] = ri;
-            rr += (double)ri * (double)ri;
+            rrf = fmaf(ri, ri, rrf);
         }
     }
-    rr = ssum(rr, sh.d);
+    const double rr = ssum((double)rrf, sh.d);
     if (tid == 0) {
         st->iters_run += 1;
         st->backtracks += bt;

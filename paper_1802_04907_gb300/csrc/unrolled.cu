@@ -352,14 +352,16 @@ __global__ void __launch_bounds__(kST, 1) k_ud_fwd(UdArgs a)
     }
     mcols<BITS>(Q2, sm.sup, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
     const float alpha2 = __fdiv_rn(*Q2.scale, (float)Q2.lm1);  // FP32: every thread computes it
-    double D = 0.0;
+    // D: each thread's <= 16 terms in FP32, the CTA sum of the partials in FP64 (a per-element
+    // FP64 sum keeps the narrow FP64 pipe of this GPU busy for microseconds)
+    float Df = 0.0f;
     for (int i = tid; i < m; i += kST) {
         const float ui = alpha2 * sm.z[i];
         sm.z[i] = ui;
-        const double g2 = (double)ga[i] * ga[i] + (double)gb[i] * gb[i];
-        D += g2 * (double)ui * (double)ui;
+        const float g2 = fmaf(ga[i], ga[i], gb[i] * gb[i]);
+        Df = fmaf(g2 * ui, ui, Df);
     }
-    D = ssum(D, sh.d);
+    const double D = ssum((double)Df, sh.d);
     if (tid == 0) {
         us.N = N;
         us.D = D;
