@@ -565,9 +565,10 @@ __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc
             for (int o = 16; o; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
         }
         bcols<BITS>(P.Q2, sm.sup, sm.val, s, sm);
-        double zz = 0.0;
-        for (int i = tid; i < m; i += kBT) zz += (double)sm.z[i] * (double)sm.z[i];
-        zz = bsum_n(zz, min(m, kBT), sh.d);
+        // sums of squares: each thread's terms in FP32, the CTA sum of the partials in FP64
+        float zzf = 0.0f;
+        for (int i = tid; i < m; i += kBT) zzf = fmaf(sm.z[i], sm.z[i], zzf);
+        const double zz = bsum_n((double)zzf, min(m, kBT), sh.d);
         if (tid == 0) {
             const double den = sh.alpha2 * sh.alpha2 * zz;
             int code = 0;
@@ -594,9 +595,9 @@ __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc
                 for (int o = 16; o; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
             }
             bcols<BITS>(P.Q2, sm.uni, sm.dlt, uc, sm);
-            double dz = 0.0;
-            for (int i = tid; i < m; i += kBT) dz += (double)sm.z[i] * (double)sm.z[i];
-            dz = bsum_n(dz, min(m, kBT), sh.d);
+            float dzf = 0.0f;
+            for (int i = tid; i < m; i += kBT) dzf = fmaf(sm.z[i], sm.z[i], dzf);
+            const double dz = bsum_n((double)dzf, min(m, kBT), sh.d);
             if (tid == 0) {
                 const double dd = sh.alpha2 * sh.alpha2 * dz;
                 int code = 0;                                   // 0 accept, 1 shrink, 2 give up
@@ -633,13 +634,13 @@ __device__ void solve_one(const qiht_problem& P, int iters, double kk, double cc
         __syncthreads();
         // residual r = Q(y) - alpha2 Q2_G' x'
         bcols<BITS>(P.Q2, sm.sel, sm.val, s, sm);
-        double rr = 0.0;
+        float rrf = 0.0f;
         for (int i = tid; i < m; i += kBT) {
             const float ri = fmaf(-sh.alpha2f, sm.z[i], sm.yhat[i]);
             sm.r[i] = ri;
-            rr += (double)ri * (double)ri;
+            rrf = fmaf(ri, ri, rrf);
         }
-        resid2 = bsum_n(rr, min(m, kBT), sh.d);
+        resid2 = bsum_n((double)rrf, min(m, kBT), sh.d);
         ++it;
         bt_total += bt;
         changes += changed;
