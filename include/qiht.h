@@ -371,7 +371,17 @@ size_t qiht_unrolled_workspace_size(int32_t nprob, int32_t m, int32_t n, int32_t
  * and the support of x_t after, mu_t = ||h_t on G_t||^2 / ||A2 (h_t on G_t)||^2,
  * x_{t+1} = H_s(x_t + mu_t h_t). X [device] nprob x n receives x_K. The workspace keeps the
  * state every ceil(sqrt(K)) steps for qiht_unrolled_backward. Requires m <= 16384,
- * n <= 32768, s <= 256. Asynchronous on `stream` after the descriptor copies. */
+ * n <= 32768, 1 <= s <= min(m, n, 256), K >= 0 (K = 0 gives X = 0).
+ * Definition: the iteration of Algorithm 2 with the adaptive step size (Eq. for mu) and H_s,
+ * on the stacked real form of a complex measurement (Section IV-B); the backtracking test is
+ * left out so that the map is differentiable with the supports held fixed.
+ * Ownership: the caller owns every buffer; the workspace (qiht_unrolled_workspace_size bytes,
+ * 256-byte aligned, device) holds the checkpoints and must be passed unchanged to the
+ * matching qiht_unrolled_backward. Errors: QIHT_ERR_ARG (null pointers, problems of different
+ * m, n or bits, sizes out of range), QIHT_ERR_BITS (bits not 2, 4 or 8), QIHT_ERR_WORKSPACE
+ * (too small or misaligned), QIHT_ERR_CUDA (a failed launch or copy; qiht_last_error says
+ * which). Nothing is launched when an argument check fails. Asynchronous on `stream` after
+ * the descriptor copies. */
 qiht_status qiht_unrolled_forward(const qiht_codes* Q1, const qiht_codes* Q2, int32_t nprob, const float* y,
                                   const float* gain_re, const float* gain_im, int32_t s, int32_t K, float* X,
                                   void* workspace, size_t workspace_bytes, qiht_stream_t stream);
@@ -380,7 +390,11 @@ qiht_status qiht_unrolled_forward(const qiht_codes* Q1, const qiht_codes* Q2, in
  * [device, nprob x n] it writes ybar = dL/dy (nprob x 2m), gain_re_bar = dL/da and
  * gain_im_bar = dL/db (nprob x m each). Call it after qiht_unrolled_forward with the same
  * arguments and workspace: each segment between checkpoints is recomputed, recording what
- * the reverse steps need. FP32 products, FP64 scalars. Asynchronous on `stream`. */
+ * the reverse steps need. The adjoint is that of the map defined for qiht_unrolled_forward
+ * (masks fixed): through x_{t+1} = P_{t+1}(x_t + mu_t h_t), mu_t = N_t / D_t, h_t = A1^T r_t
+ * and r_t = y - A2 x_t, with the gains entering A1 and A2 by rows. FP32 products, FP64
+ * scalars. Xbar may alias nothing that the call writes. Errors as for qiht_unrolled_forward.
+ * Asynchronous on `stream`. */
 qiht_status qiht_unrolled_backward(const qiht_codes* Q1, const qiht_codes* Q2, int32_t nprob, const float* y,
                                    const float* gain_re, const float* gain_im, int32_t s, int32_t K, const float* Xbar,
                                    float* ybar, float* gain_re_bar, float* gain_im_bar, void* workspace,
