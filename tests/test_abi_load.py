@@ -101,6 +101,53 @@ def test_argument_errors_return_before_launch(lib):
     assert lib.qiht_niht_solve_batched(arr, 1, 5, ctypes.byref(prm), None, 0, None) == q.ERR_WORKSPACE
 
 
+def test_multi_and_unrolled_argument_errors(lib):
+    # the many-right-hand-side and unrolled entry points reject bad arguments on the host,
+    # before any CUDA call (the pointers below are never dereferenced)
+    P = ctypes.c_void_p
+    c = q._Codes(16, 16, 64, 128, 8, q.ld_words(64, 8))
+    cy = q._Codes(16, 16, 64, 1, 8, q.ld_words(64, 8))
+    prm = q._Params(2.0, 0.01, 32, 0)
+    assert lib.qiht_solve_multi_workspace_size(64, 128, 4, 3) > 0
+    assert lib.qiht_solve_multi_workspace_size(16385, 128, 4, 3) == 0            # m above the limit
+    assert lib.qiht_solve_multi_workspace_size(64, 128, 257, 3) == 0             # s above the limit
+    assert lib.qiht_solve_multi_workspace_size(64, 128, 4, 0) == 0               # no right-hand side
+    ys = (q._Codes * 2)(cy, cy)
+    multi = lib.qiht_niht_solve_multi
+    assert multi(ctypes.byref(c), ctypes.byref(c), ys, 2, 0, 10, ctypes.byref(prm), P(16), P(16), P(16),
+                 P(256), 1 << 30, None) == q.ERR_ARG                              # s < 1
+    assert multi(ctypes.byref(c), ctypes.byref(c), ys, 2, 4, 10, ctypes.byref(prm), None, P(16), P(16),
+                 P(256), 1 << 30, None) == q.ERR_ARG                              # no X
+    ybad = (q._Codes * 2)(cy, q._Codes(16, 16, 63, 1, 8, q.ld_words(63, 8)))
+    assert multi(ctypes.byref(c), ctypes.byref(c), ybad, 2, 4, 10, ctypes.byref(prm), P(16), P(16), P(16),
+                 P(256), 1 << 30, None) == q.ERR_ARG                              # an observation of 63 rows
+    assert multi(ctypes.byref(c), ctypes.byref(c), ys, 2, 4, 10, ctypes.byref(prm), P(16), P(16), P(16),
+                 None, 0, None) == q.ERR_WORKSPACE
+    assert multi(ctypes.byref(c), ctypes.byref(c), ys, 2, 4, 10, ctypes.byref(prm), P(16), P(16), P(16),
+                 P(272), 1 << 30, None) == q.ERR_WORKSPACE                        # not 256-byte aligned
+
+    ws = lib.qiht_unrolled_workspace_size(2, 64, 128, 4, 5)
+    assert ws > 0 and lib.qiht_unrolled_workspace_size(2, 64, 128, 4, 0) > 0     # K = 0 is valid
+    assert lib.qiht_unrolled_workspace_size(0, 64, 128, 4, 5) == 0
+    assert lib.qiht_unrolled_workspace_size(2, 16385, 128, 4, 5) == 0
+    assert lib.qiht_unrolled_workspace_size(2, 64, 128, 65, 5) == 0              # s > m
+    assert lib.qiht_unrolled_workspace_size(2, 64, 128, 4, -1) == 0
+    Qa = (q._Codes * 2)(c, c)
+    fwd, bwd = lib.qiht_unrolled_forward, lib.qiht_unrolled_backward
+    assert fwd(Qa, Qa, 2, P(16), None, P(16), 4, 5, P(16), P(256), ws, None) == q.ERR_ARG       # no gain
+    Qm = (q._Codes * 2)(c, q._Codes(16, 16, 64, 127, 8, q.ld_words(64, 8)))
+    assert fwd(Qa, Qm, 2, P(16), P(16), P(16), 4, 5, P(16), P(256), ws, None) == q.ERR_ARG      # n differs
+    Q4 = (q._Codes * 2)(c, q._Codes(16, 16, 64, 128, 4, q.ld_words(64, 4)))
+    assert fwd(Q4, Q4, 2, P(16), P(16), P(16), 4, 5, P(16), P(256), ws, None) == q.ERR_ARG      # bits differ
+    Q3 = (q._Codes * 2)(c, q._Codes(16, 16, 64, 128, 3, 4))
+    assert fwd(Q3, Q3, 2, P(16), P(16), P(16), 4, 5, P(16), P(256), ws, None) == q.ERR_BITS
+    assert fwd(Qa, Qa, 2, P(16), P(16), P(16), 4, 5, P(16), None, 0, None) == q.ERR_WORKSPACE
+    assert fwd(Qa, Qa, 2, P(16), P(16), P(16), 4, 5, P(16), P(256), ws - 1, None) == q.ERR_WORKSPACE
+    assert fwd(Qa, Qa, 2, P(16), P(16), P(16), 4, 5, P(16), P(272), ws, None) == q.ERR_WORKSPACE
+    assert bwd(Qa, Qa, 2, P(16), P(16), P(16), 4, 5, None, P(16), P(16), P(16), P(256), ws,
+               None) == q.ERR_ARG                                                # no Xbar
+
+
 def test_grid_levels_are_checked(lib):
     P = ctypes.c_void_p
     ld = q.ld_words(64, 8)
