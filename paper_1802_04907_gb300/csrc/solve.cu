@@ -939,7 +939,9 @@ static FreshLayout fresh_layout(int m, int n, int s, int bits_phi, int bits_y)
 
 size_t qiht_solve_fresh_workspace_size(int32_t m, int32_t n, int32_t s, int32_t bits_phi, int32_t bits_y)
 {
-    if (m < 1 || n < 1 || s < 1 || s > m || s > n || !bits_ok(bits_phi) || !bits_ok(bits_y)) return 0;
+    if (m < 1 || n < 1 || s < 1 || s > m || s > n || m > kMaxRows || n > kMaxTopN || !bits_ok(bits_phi) ||
+        !bits_ok(bits_y))
+        return 0;
     return fresh_layout(m, n, s, bits_phi, bits_y).total;
 }
 

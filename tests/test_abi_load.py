@@ -148,6 +148,31 @@ def test_multi_and_unrolled_argument_errors(lib):
                None) == q.ERR_ARG                                                # no Xbar
 
 
+def test_fresh_argument_errors(lib):
+    P = ctypes.c_void_p
+    prm = q._Params(2.0, 0.01, 32, 0)
+    ws = lib.qiht_solve_fresh_workspace_size(64, 128, 4, 8, 8)
+    assert ws > 0
+    assert lib.qiht_solve_fresh_workspace_size(16385, 128, 4, 8, 8) == 0         # m above the limit
+    assert lib.qiht_solve_fresh_workspace_size(64, 128, 4, 3, 8) == 0            # bits
+    assert lib.qiht_solve_fresh_workspace_size(64, 128, 65, 8, 8) == 0           # s > m
+    fresh = lib.qiht_niht_solve_fresh
+    args = dict(phi=P(16), ld=128, y=P(16), m=64, n=128, bp=8, by=8, seed=1, flags=0, s=4, iters=10)
+
+    def call(**kw):
+        a = {**args, **kw}
+        return fresh(a["phi"], a["ld"], a["y"], a["m"], a["n"], a["bp"], a["by"], a["seed"], a["flags"], a["s"],
+                     a["iters"], ctypes.byref(prm), P(16), P(16), P(16), None, kw.get("ws", P(256)),
+                     kw.get("wsb", ws), None)
+    assert call(bp=3) == q.ERR_BITS
+    assert call(ld=100) == q.ERR_ARG                                           # row stride below n
+    assert call(y=None) == q.ERR_ARG
+    assert call(s=65) == q.ERR_ARG
+    assert call(flags=64) == q.ERR_ARG                                         # unknown flag
+    assert call(ws=None, wsb=0) == q.ERR_WORKSPACE
+    assert call(wsb=ws - 1) == q.ERR_WORKSPACE
+
+
 def test_grid_levels_are_checked(lib):
     P = ctypes.c_void_p
     ld = q.ld_words(64, 8)
