@@ -89,6 +89,32 @@ def test_forward_is_the_iteration_of_algorithm_2_without_backtracking():
     assert np.allclose(xK, ref.x, rtol=1e-12, atol=1e-14)
 
 
+def test_stacked_is_the_complex_gain():
+    # [diag(a); diag(b)] Phi x is the real and imaginary part of g * (Phi x), g = a + i b
+    rng = np.random.Generator(np.random.PCG64(11))
+    m, n = 9, 7
+    phi = rng.standard_normal((m, n))
+    a, b, x = rng.standard_normal(m), rng.standard_normal(m), rng.standard_normal(n)
+    z = (a + 1j * b) * (phi @ x)
+    assert np.allclose(unrolled.stacked(phi, a, b) @ x, np.concatenate([z.real, z.imag]), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed,bits", [(4, 4), (7, 4), (5, 8), (9, 2)])
+def test_forward_with_gains_is_algorithm_2_on_the_stacked_system(seed, bits):
+    # with the gains of the workload and the two different quantizations, one unrolled step
+    # equals the first iteration of the oracle's Algorithm 2 (C) on A_i = [diag(a); diag(b)] Q_i
+    # when that iteration did not backtrack (later iterations of these instances do, which the
+    # unrolled map leaves out)
+    P1, P2, y, a, b, x, s = _problem(seed=seed, bits=bits)
+    A1, A2 = unrolled.stacked(P1, a, b), unrolled.stacked(P2, a, b)
+    ref = oracle.niht(A1, A2, y, s, 1, trace=True)
+    assert ref.trace["bt"][1] == 0
+    xK, steps = unrolled.forward(P1, P2, y, a, b, s, 1)
+    assert np.array_equal(np.flatnonzero(xK), np.sort(ref.support))
+    assert np.allclose(xK, ref.x, rtol=1e-12, atol=1e-14)
+    assert abs(steps[0].mu - ref.trace["mu"][1]) <= 1e-12 * steps[0].mu
+
+
 def test_dropped_term_is_caught():
     # a planted mistake: the step size treated as a constant (its derivative dropped)
     def bad_backward(Phi1, Phi2, a, b, steps, xbar):
