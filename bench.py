@@ -27,6 +27,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -180,8 +181,7 @@ class Clocks:
 
     def __init__(self, uuid: str | None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/qiht_clocks_{os.getpid()}.csv"
+        self.path = os.path.join(tempfile.gettempdir(), f"qiht_clocks_{os.getpid()}.csv")
         self.uuid = uuid
 
     def start(self):
