@@ -404,6 +404,7 @@ class Unrolled:
         self.c1 = (_Codes * self.P)(*[q.c_struct() for q in Q1s])
         self.c2 = (_Codes * self.P)(*[q.c_struct() for q in Q2s])
         self.ws = _ws(lib().qiht_unrolled_workspace_size(self.P, self.m, self.n, s, K), dev)
+        self.generation = 0   # forward() calls so far: the checkpoints are those of the latest one
 
     def forward(self, y: torch.Tensor, gre: torch.Tensor, gim: torch.Tensor, stream=None) -> torch.Tensor:
         """x_K for every problem (P x n) from y (P x 2m) and the gains (P x m each)."""
@@ -411,6 +412,7 @@ class Unrolled:
         _check(lib().qiht_unrolled_forward(self.c1, self.c2, self.P, y.data_ptr(), gre.data_ptr(), gim.data_ptr(),
                                            self.s, self.K, X.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
                                            _stream(stream)), "qiht_unrolled_forward")
+        self.generation += 1
         return X
 
     def backward(self, y: torch.Tensor, gre: torch.Tensor, gim: torch.Tensor, Xbar: torch.Tensor, stream=None):
@@ -433,12 +435,16 @@ class UnrolledQIHT(torch.autograd.Function):
         y, gre, gim = y.contiguous(), gre.contiguous(), gim.contiguous()
         X = op.forward(y, gre, gim)
         ctx.op = op
+        ctx.generation = op.generation
         ctx.save_for_backward(y, gre, gim)
         return X
 
     @staticmethod
     def backward(ctx, grad_x):
         y, gre, gim = ctx.saved_tensors
+        if ctx.op.generation != ctx.generation:
+            # another forward through the same op replaced the checkpoints: recompute this one's
+            ctx.op.forward(y, gre, gim)
         yb, ab, bb = ctx.op.backward(y, gre, gim, grad_x)
         return yb, ab, bb, None
 
