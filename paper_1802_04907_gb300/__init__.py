@@ -163,6 +163,16 @@ def _ptr(t: torch.Tensor | None) -> int | None:
     return None if t is None else t.data_ptr()
 
 
+def _hold(t: torch.Tensor, stream) -> None:
+    """A temporary that work queued on `stream` uses: when that is not the current stream, tell
+    torch's caching allocator, so that the memory is not handed out again before the work ends."""
+    if stream is None:
+        return
+    s = stream if isinstance(stream, torch.cuda.Stream) else torch.cuda.ExternalStream(int(stream))
+    if s.cuda_stream != torch.cuda.current_stream(t.device).cuda_stream:
+        t.record_stream(s)
+
+
 def _ws(nbytes: int, device) -> torch.Tensor:
     # torch's caching allocator returns 512-byte aligned blocks
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
@@ -240,6 +250,8 @@ def gemv_t(Q: Codes, r: torch.Tensor, g: torch.Tensor | None = None, *, workspac
     c = Q.c_struct()
     _check(lib().qiht_gemv_t(ctypes.byref(c), r.data_ptr(), g.data_ptr(), ws.data_ptr(), ws.numel(),
                              _stream(stream)), "qiht_gemv_t")
+    if workspace is None:
+        _hold(ws, stream)
     return g
 
 
@@ -255,6 +267,8 @@ def gemv_t_multi(Q: Codes, R: torch.Tensor, G: torch.Tensor | None = None, *, st
     _check(lib().qiht_gemv_t_multi(ctypes.byref(c), R.data_ptr(), R.stride(0), nrhs, G.data_ptr(), G.stride(0),
                                    status.data_ptr() if status is not None else None, ws.data_ptr(), ws.numel(),
                                    _stream(stream)), "qiht_gemv_t_multi")
+    if workspace is None:
+        _hold(ws, stream)
     return G
 
 
@@ -276,6 +290,8 @@ def gemv_cols(Q: Codes, cols: torch.Tensor, coef: torch.Tensor, z: torch.Tensor 
     c = Q.c_struct()
     _check(lib().qiht_gemv_cols(ctypes.byref(c), cols.data_ptr(), coef.data_ptr(), count, z.data_ptr(),
                                 ws.data_ptr(), ws.numel(), _stream(stream)), "qiht_gemv_cols")
+    if workspace is None:
+        _hold(ws, stream)
     return z
 
 
