@@ -163,6 +163,16 @@ def _ptr(t: torch.Tensor | None) -> int | None:
     return None if t is None else t.data_ptr()
 
 
+def _need(t, n: int, dtype, name: str) -> None:
+    """The kernels take raw pointers: a vector of the wrong size or type would be read out of
+    bounds, so the wrappers refuse it before any launch."""
+    ok = isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() == n
+    if not ok:
+        got = (f"shape {tuple(t.shape)}, {t.dtype}, {'cuda' if t.is_cuda else 'cpu'}, contiguous={t.is_contiguous()}"
+               if isinstance(t, torch.Tensor) else type(t).__name__)
+        raise ValueError(f"{name}: needs a contiguous CUDA {dtype} tensor of {n} elements; got {got}")
+
+
 def _hold(t: torch.Tensor, stream) -> None:
     """A temporary that work queued on `stream` uses: when that is not the current stream, tell
     torch's caching allocator, so that the memory is not handed out again before the work ends."""
@@ -244,8 +254,10 @@ def quantize(v: torch.Tensor, bits: int, seed: int, stream_id: int, *, scale: to
 def gemv_t(Q: Codes, r: torch.Tensor, g: torch.Tensor | None = None, *, workspace: torch.Tensor | None = None,
            stream=None) -> torch.Tensor:
     """qiht_gemv_t: g = Q^T r."""
+    _need(r, Q.rows, torch.float32, "r")
     if g is None:
         g = torch.empty(Q.cols, dtype=torch.float32, device=r.device)
+    _need(g, Q.cols, torch.float32, "g")
     ws = workspace if workspace is not None else _ws(lib().qiht_gemv_t_workspace_size(), r.device)
     c = Q.c_struct()
     _check(lib().qiht_gemv_t(ctypes.byref(c), r.data_ptr(), g.data_ptr(), ws.data_ptr(), ws.numel(),
@@ -258,10 +270,15 @@ def gemv_t(Q: Codes, r: torch.Tensor, g: torch.Tensor | None = None, *, workspac
 def gemv_t_multi(Q: Codes, R: torch.Tensor, G: torch.Tensor | None = None, *, status: torch.Tensor | None = None,
                  workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """qiht_gemv_t_multi: G = Q^T R for the rows of R (nrhs x rows residuals) on the tensor cores."""
-    assert R.dim() == 2 and R.dtype == torch.float32 and R.stride(1) == 1
+    if not (R.dim() == 2 and R.is_cuda and R.dtype == torch.float32 and R.stride(1) == 1 and R.shape[1] == Q.rows):
+        raise ValueError(f"R: needs a CUDA float32 nrhs x {Q.rows} matrix with unit column stride; got "
+                         f"shape {tuple(R.shape)}, {R.dtype}, strides {R.stride()}")
     nrhs = R.shape[0]
     if G is None:
         G = torch.empty((nrhs, Q.cols), dtype=torch.float32, device=R.device)
+    if not (G.dim() == 2 and G.is_cuda and G.dtype == torch.float32 and G.stride(1) == 1 and
+            tuple(G.shape) == (nrhs, Q.cols)):
+        raise ValueError(f"G: needs a CUDA float32 {nrhs} x {Q.cols} matrix with unit column stride")
     ws = workspace if workspace is not None else _ws(lib().qiht_gemv_t_multi_workspace_size(Q.rows, nrhs), R.device)
     c = Q.c_struct()
     _check(lib().qiht_gemv_t_multi(ctypes.byref(c), R.data_ptr(), R.stride(0), nrhs, G.data_ptr(), G.stride(0),
@@ -274,6 +291,9 @@ def gemv_t_multi(Q: Codes, R: torch.Tensor, G: torch.Tensor | None = None, *, st
 
 def gemv_t_prescaled(Q: Codes, r: torch.Tensor, rmax: torch.Tensor, g: torch.Tensor, *, stream=None):
     """qiht_gemv_t_prescaled: g = Q^T r with max |r| given in rmax (one kernel launch)."""
+    _need(r, Q.rows, torch.float32, "r")
+    _need(rmax, 1, torch.float32, "rmax")
+    _need(g, Q.cols, torch.float32, "g")
     c = Q.c_struct()
     _check(lib().qiht_gemv_t_prescaled(ctypes.byref(c), r.data_ptr(), rmax.data_ptr(), g.data_ptr(),
                                        _stream(stream)), "qiht_gemv_t_prescaled")
@@ -284,8 +304,11 @@ def gemv_cols(Q: Codes, cols: torch.Tensor, coef: torch.Tensor, z: torch.Tensor 
               workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """qiht_gemv_cols: z = Q[:, cols] coef."""
     count = cols.numel()
+    _need(cols, count, torch.int32, "cols")
+    _need(coef, count, torch.float32, "coef")
     if z is None:
         z = torch.empty(Q.rows, dtype=torch.float32, device=coef.device)
+    _need(z, Q.rows, torch.float32, "z")
     ws = workspace if workspace is not None else _ws(lib().qiht_gemv_cols_workspace_size(Q.rows, count), coef.device)
     c = Q.c_struct()
     _check(lib().qiht_gemv_cols(ctypes.byref(c), cols.data_ptr(), coef.data_ptr(), count, z.data_ptr(),
@@ -298,6 +321,7 @@ def gemv_cols(Q: Codes, cols: torch.Tensor, coef: torch.Tensor, z: torch.Tensor 
 def top_s(a: torch.Tensor, s: int, *, with_values: bool = True, stream=None):
     """qiht_top_s: H_s of a vector; returns (indices ascending, values, kth[2])."""
     n = a.numel()
+    _need(a, n, torch.float32, "a")
     idx = torch.empty(s, dtype=torch.int32, device=a.device)
     val = torch.empty(s, dtype=torch.float32, device=a.device) if with_values else None
     kth = torch.empty(2, dtype=torch.float32, device=a.device)
@@ -424,6 +448,9 @@ class Unrolled:
 
     def forward(self, y: torch.Tensor, gre: torch.Tensor, gim: torch.Tensor, stream=None) -> torch.Tensor:
         """x_K for every problem (P x n) from y (P x 2m) and the gains (P x m each)."""
+        _need(y, self.P * 2 * self.m, torch.float32, "y")
+        _need(gre, self.P * self.m, torch.float32, "gain (real parts)")
+        _need(gim, self.P * self.m, torch.float32, "gain (imaginary parts)")
         X = torch.empty(self.P, self.n, dtype=torch.float32, device=y.device)
         _check(lib().qiht_unrolled_forward(self.c1, self.c2, self.P, y.data_ptr(), gre.data_ptr(), gim.data_ptr(),
                                            self.s, self.K, X.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
@@ -433,6 +460,11 @@ class Unrolled:
 
     def backward(self, y: torch.Tensor, gre: torch.Tensor, gim: torch.Tensor, Xbar: torch.Tensor, stream=None):
         """(dL/dy, dL/dRe g, dL/dIm g) from dL/dx_K, after forward() on the same inputs."""
+        _need(y, self.P * 2 * self.m, torch.float32, "y")
+        _need(gre, self.P * self.m, torch.float32, "gain (real parts)")
+        _need(gim, self.P * self.m, torch.float32, "gain (imaginary parts)")
+        Xbar = Xbar.contiguous()
+        _need(Xbar, self.P * self.n, torch.float32, "Xbar")
         yb = torch.empty_like(y)
         ab = torch.empty_like(gre)
         bb = torch.empty_like(gim)
