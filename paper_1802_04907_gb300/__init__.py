@@ -412,8 +412,11 @@ def niht_solve_fresh(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: 
                      max_backtrack: int = 32, stream=None) -> Solver:
     """qiht_niht_solve_fresh: Algorithm 2 with new quantizations of Phi and y in every iteration.
     Returns a Solver-like object holding x, support, report (and trace)."""
-    assert phi.is_cuda and phi.dtype == torch.float32 and phi.dim() == 2 and phi.stride(1) == 1
+    if not (isinstance(phi, torch.Tensor) and phi.is_cuda and phi.dtype == torch.float32 and phi.dim() == 2 and
+            phi.stride(1) == 1):
+        raise ValueError("phi: needs a CUDA float32 m x n matrix with unit column stride")
     m, n = phi.shape
+    _need(y, m, torch.float32, "y")
     sv = Solver(m, n, s, iters, device=phi.device, trace=trace, k=k, c=c, max_backtrack=max_backtrack)
     ws = _ws(lib().qiht_solve_fresh_workspace_size(m, n, s, bits_phi, bits_y), phi.device)
     tr = None

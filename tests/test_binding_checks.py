@@ -47,3 +47,8 @@ def test_unrolled_checks_its_operands():
     with pytest.raises(ValueError, match="y:"):
         op.backward(y, g, g, torch.zeros(2, 32))
     assert op.generation == 0                                          # nothing ran
+
+
+def test_fresh_solver_checks_its_inputs():
+    with pytest.raises(ValueError, match="phi:"):
+        q.niht_solve_fresh(torch.zeros(8, 16), torch.zeros(8), 8, 8, 1, 2, 3)
