@@ -58,3 +58,21 @@ def test_peaks_fall_back_without_the_measured_file(monkeypatch, tmp_path):
     assert bench.load_peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6794.8}')
     assert bench.load_peaks() == (6794.8, "measured")
+
+
+def test_cli_and_config_of_the_single_solve_workloads(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    for argv, want in ((["bench.py"], "large single solve"),
+                       (["bench.py", "--workload", "interferometry", "--bits", "4", "--bits-y", "8"],
+                        "interferometry-shaped"),
+                       (["bench.py", "--workload", "mri"], "MRI-shaped")):
+        monkeypatch.setattr(sys, "argv", argv)
+        args = bench.parse()
+        assert args.steps >= 1 and args.warmup >= 3
+        cfg = bench.config(args, 1)
+        assert cfg["workload"].startswith(want) and cfg["parallelism"] == "single GPU"
+        assert cfg["bits_y"] == (args.bits_y or args.bits) and "model" not in cfg
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
+    args = bench.parse()
+    assert args.impl == "reference" and args.gpus == 2
