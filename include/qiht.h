@@ -145,8 +145,9 @@ qiht_status qiht_gemv_t(const qiht_codes* Q, const float* r, float* g,
 qiht_status qiht_gemv_t_prescaled(const qiht_codes* Q, const float* r, const float* rmax, float* g,
                                   qiht_stream_t stream);
 
-/* z = Q[:, cols] coef: product with a column subset (Q2 x on the support,
- * Q2_G g_G of the step size, Q2 (x' - x) of the backtracking test).
+/* z = Q[:, cols] coef: product with a column subset, the products of Algorithm 2 with
+ * the second quantization: Q2 x on the support (the residual), Q2_G g_G of the step size
+ * (the Eq. for mu) and Q2 (x' - x) of the backtracking test (Section II-A).
  * cols [device, count int32 in [0, Q->cols)], coef [device, count floats],
  * z [device, Q->rows floats]. FP32 sums in a fixed order (deterministic).
  * Workspace: qiht_gemv_cols_workspace_size(Q->rows, count) bytes. */
