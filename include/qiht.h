@@ -150,6 +150,8 @@ qiht_status qiht_gemv_t_prescaled(const qiht_codes* Q, const float* r, const flo
  * (the Eq. for mu) and Q2 (x' - x) of the backtracking test (Section II-A).
  * cols [device, count int32 in [0, Q->cols)], coef [device, count floats],
  * z [device, Q->rows floats]. FP32 sums in a fixed order (deterministic).
+ * The indices are read on the device only: an entry outside [0, Q->cols) is never
+ * used to address the codes; it makes every entry of z NaN instead.
  * Workspace: qiht_gemv_cols_workspace_size(Q->rows, count) bytes. */
 size_t qiht_gemv_cols_workspace_size(int32_t rows, int32_t count);
 qiht_status qiht_gemv_cols(const qiht_codes* Q, const int32_t* cols, const float* coef, int32_t count,
@@ -165,10 +167,13 @@ qiht_status qiht_gemv_cols(const qiht_codes* Q, const int32_t* cols, const float
  * held on every GPU that loads the library until the process exits; the call
  * allocates nothing. Limit: qiht_gemv_cols_workspace_size(Q->rows, count) must not
  * exceed QIHT_STATIC_SCRATCH_BYTES, else QIHT_ERR_WORKSPACE is returned and nothing
- * is launched. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture. All calls share the one array: calls whose kernels overlap
- * on the GPU (other streams, other threads) race and give wrong results. */
+ * is launched. The first call in a CUDA context (the runtime's primary context of a
+ * device, or a context made current through the driver API) looks up the array's
+ * device address in that context (cudaGetSymbolAddress, with the context current);
+ * make that first call before any stream capture. All calls share the one array:
+ * calls whose kernels overlap on the GPU (other streams, other threads) race and
+ * give wrong results. Indices outside [0, Q->cols) give a NaN z, as for
+ * qiht_gemv_cols. */
 #define QIHT_STATIC_SCRATCH_BYTES (2u << 20)
 qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t* cols, const float* coef, int32_t count,
                                   float* z, qiht_stream_t stream);

@@ -151,12 +151,24 @@ def _check(status: int, where: str):
         raise QihtError(status, where)
 
 
-def _stream(stream) -> int:
+def _stream(stream, current=None) -> int:
+    """Raw handle of the stream a call launches on (None: torch's current stream).
+
+    When an explicit stream is not the current one, it is first made to wait for the
+    current stream's queued work: the buffers a wrapper (or its caller) has just taken
+    from torch's caching allocator come from the current stream's pool, and may be
+    blocks that kernels queued there still read or write. `current` stands in for
+    torch.cuda.current_stream() (tests)."""
     if stream is None:
-        return torch.cuda.current_stream().cuda_stream
-    if isinstance(stream, torch.cuda.Stream):
-        return stream.cuda_stream
-    return int(stream)
+        return (current if current is not None else torch.cuda.current_stream()).cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        s = stream
+    else:
+        s = torch.cuda.ExternalStream(int(stream))
+    cur = current if current is not None else torch.cuda.current_stream()
+    if s.cuda_stream != cur.cuda_stream:
+        s.wait_stream(cur)
+    return s.cuda_stream
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
@@ -173,13 +185,15 @@ def _need(t, n: int, dtype, name: str) -> None:
         raise ValueError(f"{name}: needs a contiguous CUDA {dtype} tensor of {n} elements; got {got}")
 
 
-def _hold(t: torch.Tensor, stream) -> None:
-    """A temporary that work queued on `stream` uses: when that is not the current stream, tell
-    torch's caching allocator, so that the memory is not handed out again before the work ends."""
+def _hold(t: torch.Tensor, stream, current=None) -> None:
+    """A buffer allocated here (a temporary or a new output) that work queued on `stream` uses:
+    when that is not the current stream, tell torch's caching allocator, so that the memory
+    is not handed out again before the work ends."""
     if stream is None:
         return
-    s = stream if isinstance(stream, torch.cuda.Stream) else torch.cuda.ExternalStream(int(stream))
-    if s.cuda_stream != torch.cuda.current_stream(t.device).cuda_stream:
+    s = stream if hasattr(stream, "cuda_stream") else torch.cuda.ExternalStream(int(stream))
+    cur = current if current is not None else torch.cuda.current_stream(t.device)
+    if s.cuda_stream != cur.cuda_stream:
         t.record_stream(s)
 
 
@@ -216,8 +230,22 @@ class Codes:
         return self.levels == odd_levels(self.bits) and self.levels != 2**self.bits
 
     def c_struct(self) -> _Codes:
-        return _Codes(self.words.data_ptr(), self.scale.data_ptr(), self.rows, self.cols, self.bits, self.ld_words,
-                      self.levels, 0)
+        """The C descriptor. The kernels read cols * ld_words words and one scale through raw
+        pointers, so a hand-made or sliced Codes of the wrong size, type or device is refused."""
+        w, sc = self.words, self.scale
+        if self.bits not in (2, 4, 8) or self.rows < 1 or self.cols < 1:
+            raise ValueError(f"Codes: bits {self.bits}, rows {self.rows}, cols {self.cols} out of range")
+        need = self.cols * self.ld_words
+        if not (isinstance(w, torch.Tensor) and w.is_cuda and w.dtype == torch.int32 and w.is_contiguous() and
+                w.numel() == need):
+            got = (f"shape {tuple(w.shape)}, {w.dtype}, {'cuda' if w.is_cuda else 'cpu'}" if isinstance(w, torch.Tensor)
+                   else type(w).__name__)
+            raise ValueError(f"Codes.words: needs a contiguous CUDA int32 tensor of cols * ld_words = {need} "
+                             f"elements; got {got}")
+        if not (isinstance(sc, torch.Tensor) and sc.is_cuda and sc.dtype == torch.float32 and sc.numel() >= 1 and
+                sc.device == w.device):
+            raise ValueError("Codes.scale: needs a CUDA float32 tensor (one element) on the device of the words")
+        return _Codes(w.data_ptr(), sc.data_ptr(), self.rows, self.cols, self.bits, self.ld_words, self.levels, 0)
 
     @property
     def nbytes(self) -> int:
@@ -248,6 +276,8 @@ def quantize(v: torch.Tensor, bits: int, seed: int, stream_id: int, *, scale: to
     st = lib().qiht_quantize(v.data_ptr(), rows, cols, ld, bits, seed & (2**64 - 1), stream_id, flags,
                              out.words.data_ptr(), ldw, out.scale.data_ptr(), _stream(stream))
     _check(st, "qiht_quantize")
+    _hold(out.words, stream)
+    _hold(out.scale, stream)
     return out
 
 
@@ -264,6 +294,7 @@ def gemv_t(Q: Codes, r: torch.Tensor, g: torch.Tensor | None = None, *, workspac
                              _stream(stream)), "qiht_gemv_t")
     if workspace is None:
         _hold(ws, stream)
+    _hold(g, stream)
     return g
 
 
@@ -286,6 +317,7 @@ def gemv_t_multi(Q: Codes, R: torch.Tensor, G: torch.Tensor | None = None, *, st
                                    _stream(stream)), "qiht_gemv_t_multi")
     if workspace is None:
         _hold(ws, stream)
+    _hold(G, stream)
     return G
 
 
@@ -315,6 +347,7 @@ def gemv_cols(Q: Codes, cols: torch.Tensor, coef: torch.Tensor, z: torch.Tensor 
                                 ws.data_ptr(), ws.numel(), _stream(stream)), "qiht_gemv_cols")
     if workspace is None:
         _hold(ws, stream)
+    _hold(z, stream)
     return z
 
 
@@ -327,6 +360,9 @@ def top_s(a: torch.Tensor, s: int, *, with_values: bool = True, stream=None):
     kth = torch.empty(2, dtype=torch.float32, device=a.device)
     _check(lib().qiht_top_s(a.data_ptr(), n, s, idx.data_ptr(), _ptr(val), kth.data_ptr(), None, 0,
                             _stream(stream)), "qiht_top_s")
+    for t in (idx, val, kth):
+        if t is not None:
+            _hold(t, stream)
     return idx, val, kth
 
 
@@ -395,7 +431,14 @@ class Solver:
                                    self.report.data_ptr(), ctypes.byref(tr) if tr is not None else None,
                                    self.workspace.data_ptr(), self.workspace.numel(), _stream(stream))
         _check(st, "qiht_niht_solve")
+        for t in self._buffers():
+            _hold(t, stream)
         return self
+
+    def _buffers(self):
+        yield from (self.x, self.support, self.report, self.workspace)
+        if self.trace is not None:
+            yield from self.trace.values()
 
     def read_report(self) -> Report:
         return report_from_bytes(bytes(self.report.cpu().numpy().tobytes()))
@@ -602,6 +645,8 @@ def quantize_pair(v: torch.Tensor, bits: int, seed: int, stream_a: int, stream_b
                                   _stream(stream))
     _check(st, "qiht_quantize_pair")
     qb.scale = qa.scale
+    for t in (qa.words, qb.words, qa.scale):
+        _hold(t, stream)
     return qa, qb
 
 

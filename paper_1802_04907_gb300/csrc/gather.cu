@@ -13,6 +13,7 @@
 #include <cfloat>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -106,16 +107,26 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     const float* coefs = (a.mode == kGatherResid) ? a.new_val : a.coef;
     __shared__ int s_col[kGatherCols];
     __shared__ float s_cf[kGatherCols];
+    __shared__ int s_bad;
 
     if (jc < nchunks) {
-        // this chunk's columns and coefficients, loaded once for the CTA
+        // this chunk's columns and coefficients, loaded once for the CTA. A column index
+        // outside [0, cols) (possible only in a caller's list) is not read: the entry is
+        // dropped and the chunk's partial sums become NaN, so every entry of z is NaN
+        if (threadIdx.x == 0) s_bad = 0;
+        __syncthreads();
         if (threadIdx.x < kGatherCols) {
             const int jj = jc * kGatherCols + threadIdx.x;
             int col = -1;
             float cf = 0.0f;
             if (jj < count) {
                 col = __ldcg(list + jj);
-                cf = (a.mode == kGatherMu) ? __ldcg(a.g + col) : __ldcg(coefs + jj);
+                if ((unsigned)col >= (unsigned)a.Q.cols) {
+                    s_bad = 1;
+                    col = -1;
+                } else {
+                    cf = (a.mode == kGatherMu) ? __ldcg(a.g + col) : __ldcg(coefs + jj);
+                }
             }
             s_col[threadIdx.x] = col;
             s_cf[threadIdx.x] = cf;
@@ -146,6 +157,10 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
                         z[k] = fmaf((float)(2 * code - lm1), cf, z[k]);
                     }
                 }
+            }
+            if (s_bad) {
+#pragma unroll
+                for (int k = 0; k < G; ++k) z[k] = __int_as_float(0x7fc00000);
             }
             float* dst = a.partial + (size_t)jc * rows_pad + (size_t)q * G;
 #pragma unroll
@@ -434,27 +449,71 @@ cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
 static __device__ __align__(256) unsigned char g_static_scratch[QIHT_STATIC_SCRATCH_BYTES];
 
 namespace {
+// Device address of g_static_scratch, per CUDA context: the array has its own address in
+// every context that loads the library (the primary context of each device, or a context
+// the caller made current through the driver API). Contexts are told apart by their
+// unique id, which is never reused within a process.
+struct StaticAddr {
+    unsigned long long ctx_id;
+    void* addr;
+};
 std::mutex g_static_mu;
-void* g_static_addr[256];   // device address of g_static_scratch, per device ordinal
-}
+std::vector<StaticAddr> g_static_addr;
 
-// Device address of the static scratch on the current device. The host-side name
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// Unique id of the current context (0 when no context is current yet).
+cudaError_t current_context_id(unsigned long long* id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1{}, q2{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f1) return cudaErrorNotSupported;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess || !f2) return cudaErrorNotSupported;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    void* ctx = nullptr;
+    *id = 0;
+    if (get_current(&ctx) != 0) return cudaErrorDeviceUninitialized;
+    if (ctx && get_id(ctx, id) != 0) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+}  // namespace
+
+// Device address of the static scratch in the current context. The host-side name
 // g_static_scratch is only a stand-in; its device address comes from
-// cudaGetSymbolAddress, taken once per device with that device current.
+// cudaGetSymbolAddress, taken once per context while that context is current.
 static cudaError_t static_scratch_address(void** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (id != 0)
+        for (const StaticAddr& sa : g_static_addr)
+            if (sa.ctx_id == id) {
+                *out = sa.addr;
+                return cudaSuccess;
+            }
+    // first call in this context (the lookup also makes the device's primary context
+    // current when the thread had none)
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    if (id == 0) {
+        e = current_context_id(&id);
         if (e != cudaSuccess) return e;
-        g_static_addr[dev] = p;
+        if (id == 0) return cudaErrorDeviceUninitialized;
     }
-    *out = g_static_addr[dev];
+    g_static_addr.push_back(StaticAddr{id, p});
+    *out = p;
     return cudaSuccess;
 }
 
@@ -464,11 +523,8 @@ extern "C" qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t*
                                              int32_t count, float* z, qiht_stream_t stream)
 {
     using namespace qiht;
-    if (!Q || !Q->words || !Q->scale) return QIHT_ERR_ARG;
-    if (Q->bits != 2 && Q->bits != 4 && Q->bits != 8) return QIHT_ERR_BITS;
-    if (Q->rows < 1 || Q->cols < 1 || Q->ld_words != qiht_ld_words(Q->rows, Q->bits)) return QIHT_ERR_ARG;
-    if (grid_levels(Q->bits, Q->levels) < 0) return QIHT_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(Q->words) & 15) != 0) return QIHT_ERR_ARG;
+    const qiht_status ce = check_codes(Q);     // the same checks as qiht_gemv_cols
+    if (ce != QIHT_OK) return ce;
     if (!cols || !coef || !z || count < 1) return QIHT_ERR_ARG;
     // same scratch layout as qiht_gemv_cols; it must fit the fixed array
     const size_t need = qiht_gemv_cols_workspace_size(Q->rows, count);
@@ -488,7 +544,7 @@ extern "C" qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t*
     const size_t off_rb = (fl * 4 + a256) & ~a256;
     const size_t off_cnt = off_rb + (((size_t)rbmax * 2 * 8 + a256) & ~a256);
     GatherArgs a{};
-    a.Q = Codes{Q->words, Q->scale, Q->rows, Q->cols, Q->bits, Q->ld_words, grid_levels(Q->bits, Q->levels) - 1};
+    a.Q = view(Q);
     a.cols = cols;
     a.coef = coef;
     a.count = count;

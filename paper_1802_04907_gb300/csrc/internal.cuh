@@ -294,8 +294,8 @@ struct InitArgs {
     qiht_trace trace;
 };
 
-// Kernel node builders (each translation unit owns its kernels). gemv_t_node needs
-// argbuf[0..2] pointing at a GemvTArgs and two ints owned by the caller.
+// Kernel node builders (each translation unit owns its kernels). argbuf[0] points at the
+// kernel's argument struct, owned by the caller.
 void gemv_t_node(const GemvTArgs& a, int num_sms, cudaKernelNodeParams* p, void** argbuf);
 void gather_node(const GatherArgs& a, cudaKernelNodeParams* p, void** argbuf);
 void top_node(const TopArgs& a, cudaKernelNodeParams* p, void** argbuf);

@@ -1809,13 +1809,11 @@ bool iter_fast(int s)
 
 int iter_grid()
 {
-    // QIHT_ITER_GRID overrides the number of CTAs (for measurement); default one per SM
+    // one CTA per SM; the partial slots hold up to kSlotCtas CTAs
     static int g = -1;
     if (g < 0) {
-        int n = num_sms();
-        const char* e = getenv("QIHT_ITER_GRID");
-        if (e && atoi(e) > 0 && atoi(e) < n) n = atoi(e);
-        g = n > kSlotCtas ? kSlotCtas : n;     // partial slots hold up to kSlotCtas CTAs
+        const int n = num_sms();
+        g = n > kSlotCtas ? kSlotCtas : n;
     }
     return g;
 }

@@ -479,7 +479,6 @@ static int body_unroll()
 struct SolveKernels {
     InitKernelArgs ia;
     GemvTArgs g0, gb;
-    int tpc0, ns0, tpcb, nsb;
     TopArgs t0, tt;
     GatherArgs gmu, gom, gre;
     void* a_tf[1];
@@ -488,8 +487,8 @@ struct SolveKernels {
     void* a_it[1];
     cudaKernelNodeParams p_it;
     void* a_init[1];
-    void* a_g0[3];
-    void* a_gb[3];
+    void* a_g0[1];
+    void* a_gb[1];
     void* a_t0[1];
     void* a_tt[1];
     void* a_mu[1];
@@ -563,7 +562,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     K.g0.g = g;
     K.g0.st = st;
     K.g0.h_outer = 0;               // the set-up product does not steer the loop
-    K.a_g0[0] = &K.g0; K.a_g0[1] = &K.tpc0; K.a_g0[2] = &K.ns0;
+    K.a_g0[0] = &K.g0;
     gemv_t_node(K.g0, nsm, &K.p_g0, K.a_g0);
     K.gb = K.g0;
     K.gb.h_outer = h_outer;         // the loop body's product decides whether to go on
@@ -578,7 +577,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
         K.gb.report = report;
         K.gb.trace_resid2 = tr.resid2;
     }
-    K.a_gb[0] = &K.gb; K.a_gb[1] = &K.tpcb; K.a_gb[2] = &K.nsb;
+    K.a_gb[0] = &K.gb;
     gemv_t_node(K.gb, nsm, &K.p_gb, K.a_gb);
 
     K.t0 = TopArgs{};
@@ -766,12 +765,12 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
         // while the previous one finishes
         GemvTArgs inner = K.gb;
         inner.h_outer = 0;                           // only the body's last product steers the loop
-        void* inner_args[3] = {&inner, &K.tpcb, &K.nsb};
+        void* inner_args[1] = {&inner};
         cudaKernelNodeParams p_inner = K.p_gb;
         p_inner.kernelParams = inner_args;
         GemvTArgs last = K.gb;
         last.guard_limit = (iters + unroll - 1) / unroll + 1;
-        void* last_args[3] = {&last, &K.tpcb, &K.nsb};
+        void* last_args[1] = {&last};
         cudaKernelNodeParams p_last = K.p_gb;
         p_last.kernelParams = last_args;
         cudaGraphEdgeData prog{};

@@ -72,6 +72,23 @@ def test_gemv_cols(bits, shape, count):
     assert np.all(np.abs(z - ref) <= bound), (np.abs(z - ref) / bound).max()
 
 
+@pytest.mark.parametrize("bad", [-1, 40, 2**31 - 1])
+def test_gemv_cols_index_out_of_range_gives_nan(bad):
+    # a caller's column index outside [0, cols) is never used to address the codes: the
+    # product is marked invalid (every entry of z NaN) instead; the next call is unaffected
+    m, n = 300, 40
+    v = synth.random_floats((m, n), seed=3)
+    Q = q.quantize(torch.from_numpy(v).cuda(), 8, 9, 1)
+    cols = torch.tensor([3, bad, 7] + list(range(10, 20)), dtype=torch.int32, device="cuda")
+    coef = torch.ones(cols.numel(), dtype=torch.float32, device="cuda")
+    z = q.gemv_cols(Q, cols, coef)
+    torch.cuda.synchronize()
+    assert torch.all(torch.isnan(z))
+    good = q.gemv_cols(Q, cols[[0, 2]].contiguous(), coef[:2].contiguous())
+    torch.cuda.synchronize()
+    assert torch.all(torch.isfinite(good))
+
+
 @pytest.mark.parametrize("n,s", [(1, 1), (5, 5), (7, 3), (1024, 16), (1000, 999), (32768, 256), (49152, 1000),
                                  (16384, 64), (40000, 1)])
 def test_top_s(n, s):

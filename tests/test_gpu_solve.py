@@ -286,6 +286,43 @@ def test_fast_and_general_iteration_kernels_agree(tmp_path):
     assert rel < 1e-5, rel
 
 
+@pytest.mark.parametrize("env", [{"QIHT_PDL": "0"}, {"QIHT_UNROLL": "1"}, {"QIHT_UNROLL": "3"},
+                                 {"QIHT_PDL": "0", "QIHT_UNROLL": "5"}])
+def test_graph_variants_match_the_default_graph(tmp_path, env):
+    # the solver graph built without programmatic edges, or with another number of iterations
+    # per loop-body execution, runs the same kernels on the same data: bitwise equal results
+    # (both switches are read once per process, hence the subprocesses)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "solve.py"
+    script.write_text(
+        "import sys, numpy as np, torch\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "import paper_1802_04907_gb300 as q, synth\n"
+        "p = synth.gaussian(900, 3000, 30, seed=21, snr_db=25.0, values='pm_u')\n"
+        "phi = torch.from_numpy(p.phi).cuda(); y = torch.from_numpy(p.y).cuda()\n"
+        "q1, q2, qy = q.quantize_problem(phi, y, 4, 8, 6)\n"
+        "sv = q.niht_solve(q1, q2, qy, p.s, 37, trace=True)\n"
+        "torch.cuda.synchronize()\n"
+        "r = sv.read_report()\n"
+        "np.savez(sys.argv[1], x=sv.x.cpu().numpy(), sup=sv.trace['support'].cpu().numpy(),\n"
+        "         mu=sv.trace['mu'].cpu().numpy(), r2=sv.trace['resid2'].cpu().numpy(),\n"
+        "         rep=np.array([r.iters_run, r.status, r.backtracks, r.support_changes]), rn=r.resid_norm2)\n")
+    outs = {}
+    for kind, extra in (("default", {}), ("variant", env)):
+        e = {k: v for k, v in os.environ.items() if k not in ("QIHT_PDL", "QIHT_UNROLL")}
+        e.update(extra)
+        out = tmp_path / f"{kind}.npz"
+        subprocess.run([sys.executable, str(script), str(out)], env=e, check=True, timeout=300)
+        outs[kind] = np.load(out)
+    a, b = outs["default"], outs["variant"]
+    assert int(a["rep"][0]) == 37 and int(a["rep"][1]) == q.OK
+    for k in ("x", "sup", "mu", "r2", "rep", "rn"):
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_exact_ties_resolve_by_index():
     # +-1 entries quantize deterministically (they sit on the two end levels), so duplicated
     # columns have identical codes and identical gradients: H_s must break the ties by the
