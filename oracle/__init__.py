@@ -2,7 +2,8 @@
 
 Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may
 import this package. It wraps the plain C implementation in qiht_oracle.c
-(FP64, single thread) with ctypes and numpy. It shares no code with the CUDA
+(FP64; the dense products and the quantizer split their outputs over OpenMP
+threads without changing any sum) with ctypes and numpy. It shares no code with the CUDA
 library of the package and never imports it.
 
 Functions mirror the paper's steps:
@@ -12,6 +13,9 @@ Functions mirror the paper's steps:
   quantize / dequantize          Q(v, b) of Section III-A, and its value c * q_code
   gemv_t, gemv_cols              plain FP64 products
   top_s                          hard threshold H_s (Eq. NIHT)
+  step_size                      the step size's numerator and denominator (Eq. step_size;
+                                 Algorithm 2's cross product of two realizations, or the
+                                 forward square)
   niht, niht_seq                 Algorithm 2 (Algorithm 1 when both matrices are Phi); niht_seq
                                  with one realization per iteration (qiht_fresh)
 """
@@ -43,7 +47,10 @@ def build(force: bool = False, mutant: int = 0, out: str | None = None) -> str:
     tmp = lib_path + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            f"-DQO_MUTANT={int(mutant)}", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP splits outputs over threads (results do not depend on the thread count); a
+    # compiler without it builds the same code single-threaded
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, lib_path)
     return lib_path
 
@@ -52,13 +59,25 @@ _lib = None
 
 
 class _Params(ctypes.Structure):
-    _fields_ = [("k", ctypes.c_double), ("c", ctypes.c_double), ("max_backtrack", ctypes.c_int32)]
+    _fields_ = [("k", ctypes.c_double), ("c", ctypes.c_double), ("max_backtrack", ctypes.c_int32),
+                ("mu_mode", ctypes.c_int32), ("tol", ctypes.c_double)]
 
 
 class _Trace(ctypes.Structure):
     _fields_ = [("support", ctypes.c_void_p), ("kth", ctypes.c_void_p), ("min_gap", ctypes.c_void_p),
                 ("mu", ctypes.c_void_p), ("bt", ctypes.c_void_p), ("min_margin", ctypes.c_void_p),
-                ("resid2", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+                ("resid2", ctypes.c_void_p), ("x", ctypes.c_void_p), ("mu_fallback", ctypes.c_void_p)]
+
+
+MU_FORWARD_SQ, MU_CROSS = 0, 1
+
+
+def _mu_mode(mode) -> int:
+    if mode in (0, "forward", "forward_sq"):
+        return MU_FORWARD_SQ
+    if mode in (1, "cross"):
+        return MU_CROSS
+    raise ValueError(f"mu_mode {mode!r}")
 
 
 class _Report(ctypes.Structure):
@@ -72,6 +91,8 @@ def lib():
     if _lib is None:
         # QIHT_ORACLE_LIB points the wrapper at another build (mutation tests only)
         path = os.environ.get("QIHT_ORACLE_LIB") or build()
+        # idle OpenMP threads sleep instead of spinning (the oracle runs beside GPU work)
+        os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
         L = ctypes.CDLL(path)
         P = ctypes.c_void_p
         L.qo_philox4x32_10.argtypes = [P, P, P]
@@ -99,6 +120,13 @@ def lib():
         L.qo_niht_seq.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.POINTER(_Params), P, P, ctypes.POINTER(_Trace), ctypes.POINTER(_Report)]
         L.qo_niht_seq.restype = ctypes.c_int
+        L.qo_step_size.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32, P, P,
+                                   P, P]
+        L.qo_step_size.restype = None
+        L.qo_set_threads.argtypes = [ctypes.c_int]
+        L.qo_set_threads.restype = None
+        L.qo_get_threads.argtypes = []
+        L.qo_get_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -186,6 +214,34 @@ def gemv_cols(A: np.ndarray, idx: np.ndarray, v: np.ndarray) -> np.ndarray:
     return z
 
 
+def set_threads(n: int) -> None:
+    """Threads of the OpenMP split of the products and the quantizer (results are the same for
+    any count)."""
+    lib().qo_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().qo_get_threads())
+
+
+def step_size(A1: np.ndarray, A2: np.ndarray, support: np.ndarray, g: np.ndarray, mu_mode=0) -> dict:
+    """The step size's parts on support G (Eq. step_size, Algorithm 2): num = ||g_G||^2 and the
+    denominator used: ||A2_G g_G||^2 (mu_mode "forward"), or the cross product
+    (A1_G g_G)^T (A2_G g_G) of the two realizations (mu_mode "cross"), which falls back to the
+    forward square when not positive."""
+    A1 = np.ascontiguousarray(A1, dtype=np.float64)
+    A2 = np.ascontiguousarray(A2, dtype=np.float64)
+    sup = np.ascontiguousarray(support, dtype=np.int32)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    m, n = A2.shape
+    out = np.zeros(4)
+    coef = np.zeros(max(sup.size, 1))
+    z1, z2 = np.zeros(m), np.zeros(m)
+    lib().qo_step_size(_ptr(A1), _ptr(A2), m, n, _ptr(sup), _ptr(g), sup.size, _mu_mode(mu_mode), _ptr(out),
+                       _ptr(coef), _ptr(z1), _ptr(z2))
+    return {"num": out[0], "den": out[1], "cross": out[2], "fallback": bool(out[3])}
+
+
 def top_s(a: np.ndarray, s: int) -> tuple[np.ndarray, np.ndarray]:
     a = np.ascontiguousarray(a, dtype=np.float64)
     sel = np.zeros(s, dtype=np.int32)
@@ -208,16 +264,20 @@ class NihtResult:
 
 
 def niht(A1: np.ndarray, A2: np.ndarray, y: np.ndarray, s: int, iters: int, *, k: float = 2.0,
-         c: float = 0.01, max_backtrack: int = 32, trace: bool | str = False) -> NihtResult:
+         c: float = 0.01, max_backtrack: int = 32, mu_mode=0, tol: float = 0.0,
+         trace: bool | str = False) -> NihtResult:
     """Algorithm 2 with matrices A1 (for g = A1^T r) and A2 (for A2 x, mu, omega), FP64.
 
+    mu_mode "cross" takes Algorithm 2's printed step-size denominator (see step_size); tol > 0
+    stops after the first iteration whose ||y - A2 x||^2 <= tol.
     trace=True records supports, gaps, step sizes and residuals per iteration;
     trace="x" also records every iterate."""
-    return niht_seq([A1], [A2], [y], s, iters, k=k, c=c, max_backtrack=max_backtrack, trace=trace)
+    return niht_seq([A1], [A2], [y], s, iters, k=k, c=c, max_backtrack=max_backtrack, mu_mode=mu_mode, tol=tol,
+                    trace=trace)
 
 
 def niht_seq(A1s: list, A2s: list, ys: list, s: int, iters: int, *, k: float = 2.0, c: float = 0.01,
-             max_backtrack: int = 32, trace: bool | str = False) -> NihtResult:
+             max_backtrack: int = 32, mu_mode=0, tol: float = 0.0, trace: bool | str = False) -> NihtResult:
     """Algorithm 2 with one realization per iteration: iteration t (1..iters) uses A1s[t], A2s[t],
     ys[t]; index 0 gives the initial support. Lists of length 1 repeat their one entry."""
     def full(lst):
@@ -229,7 +289,7 @@ def niht_seq(A1s: list, A2s: list, ys: list, s: int, iters: int, *, k: float = 2
     m, n = A1.shape
     x = np.zeros(n, dtype=np.float64)
     sup = np.zeros(s, dtype=np.int32)
-    p = _Params(k, c, max_backtrack)
+    p = _Params(k, c, max_backtrack, _mu_mode(mu_mode), float(tol))
     rep = _Report()
     tr = None
     arrays = None
@@ -238,7 +298,7 @@ def niht_seq(A1s: list, A2s: list, ys: list, s: int, iters: int, *, k: float = 2
         arrays = {"support": np.zeros((T, s), np.int32), "kth": np.zeros((T, 2)),
                   "min_gap": np.zeros(T), "mu": np.zeros(T), "bt": np.zeros(T, np.int32),
                   "min_margin": np.zeros(T), "resid2": np.zeros(T),
-                  "x": np.zeros((T, n)) if trace == "x" else None}
+                  "x": np.zeros((T, n)) if trace == "x" else None, "mu_fallback": np.zeros(T, np.int32)}
         tr = _Trace(*[_ptr(arrays[f]) if arrays[f] is not None else None for f, _ in _Trace._fields_])
     ptrs = [(ctypes.c_void_p * (iters + 1))(*[_ptr(a) for a in lst]) for lst in (A1l, A2l, yl)]
     lib().qo_niht_seq(ptrs[0], ptrs[1], ptrs[2], m, n, s, iters, ctypes.byref(p), _ptr(x), _ptr(sup),

@@ -17,6 +17,10 @@
  * taken in binary32 because the paper defines Q on single-precision inputs
  * (Section III-A) and the decision must be identical on both sides.
  * Build with -O2 -ffp-contract=off: no fused multiply-add anywhere.
+ * With -fopenmp the dense products and the quantiser split their OUTPUTS over
+ * threads (columns of A^T r, rows of A[:, list] v, elements of Q(v)); every
+ * output is still one sum in the serial order, so results do not depend on the
+ * number of threads.
  *
  * Readings of the paper (where it is silent or garbled):
  *   - 2^b equally spaced levels on [-1, 1], spacing 2/(2^b - 1)   (Section III-A)
@@ -30,8 +34,15 @@
  *     quantisation (the paper used XORShift on CPU; the generator is free)
  *   - Algorithm 2's "x^{[n]}" inside g is x^{[n-1]}; the branches that set
  *     x^{[n]} = x^{[n-1]} are read as "accept the proposal" (Section II-A text)
- *   - the mu denominator uses the second quantisation only:
- *     ||Q2[:, G] g_G||^2 (a positive number), and omega uses Q2 as well
+ *   - the mu denominator, by default, uses the second quantisation only:
+ *     ||Q2[:, G] g_G||^2 (a positive number), and omega uses Q2 as well;
+ *     mu_mode = 1 takes the denominator Algorithm 2 prints, the cross product
+ *     (Q1[:, G] g_G)^T (Q2[:, G] g_G) of the two quantisations, and falls back
+ *     to the forward square when that product is not positive
+ *   - tol > 0 stops the run after the first iteration whose residual
+ *     ||y - Q2 x||^2 is at most tol (the paper stops after a fixed number of
+ *     iterations n*, Theorem 4's n* = ceil(log2(||x^s|| / eps_s)); tol is the
+ *     same criterion stated on the residual, for when eps_s is not known)
  *   - H_s keeps exactly s indices: order by |a| descending, then index ascending
  *   - if ||g_G||^2 == 0 or ||Q2 g_G||^2 == 0 the solve stops (converged)
  *
@@ -42,6 +53,28 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the OpenMP split (1 when built without OpenMP). */
+void qo_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int qo_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define QO_OK 0
 #define QO_ERR_ARG 1
@@ -138,6 +171,7 @@ int qo_quantize(const float* v, int64_t rows, int64_t cols, int64_t ld,
 {
     if (levels < 2 || levels > 65536) return QO_ERR_BITS;
     if (!(scale >= 0.0f) || !isfinite(scale)) return QO_ERR_NONFINITE;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < rows; ++i) {
         for (int64_t j = 0; j < cols; ++j) {
             uint64_t e = (uint64_t)(col0 + j) * (uint64_t)rows_total + (uint64_t)(row0 + i);
@@ -153,6 +187,7 @@ void qo_dequantize(const uint16_t* codes, int64_t count, int levels, float scale
 {
     const double lm1 = (double)(levels - 1);
     const double alpha = (double)scale / lm1;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < count; ++i)
         out[i] = alpha * (2.0 * (double)codes[i] - ((QO_MUTANT == 9) ? lm1 + 1.0 : lm1));
 }
@@ -162,14 +197,24 @@ void qo_dequantize(const uint16_t* codes, int64_t count, int levels, float scale
 /* ascending index order; loops are arranged so A is read row by row.     */
 /* ------------------------------------------------------------------ */
 
-/* g = A^T r */
+/* g = A^T r. Each thread owns a range of columns and walks all rows, so g[j] is summed
+ * over i in ascending order whatever the number of threads. */
 void qo_gemv_t(const double* A, const double* r, int64_t m, int64_t n, double* g)
 {
-    for (int64_t j = 0; j < n; ++j) g[j] = 0.0;
-    for (int64_t i = 0; i < m; ++i) {
-        const double* row = A + i * n;
-        const double ri = r[i];
-        for (int64_t j = 0; j < n; ++j) g[j] += row[j] * ri;
+#pragma omp parallel
+    {
+        int64_t j0 = 0, j1 = n;
+#ifdef _OPENMP
+        const int64_t nt = omp_get_num_threads(), id = omp_get_thread_num();
+        j0 = n * id / nt;
+        j1 = n * (id + 1) / nt;
+#endif
+        for (int64_t j = j0; j < j1; ++j) g[j] = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            const double* row = A + i * n;
+            const double ri = r[i];
+            for (int64_t j = j0; j < j1; ++j) g[j] += row[j] * ri;
+        }
     }
 }
 
@@ -177,6 +222,7 @@ void qo_gemv_t(const double* A, const double* r, int64_t m, int64_t n, double* g
 void qo_gemv_cols(const double* A, int64_t m, int64_t n, const int32_t* idx, const double* v,
                   int64_t k, double* z)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i) {
         const double* row = A + i * n;
         double acc = 0.0;
@@ -233,7 +279,41 @@ typedef struct {
     double k;              /* shrinkage, k > 1/(1-c) (Section II-A) */
     double c;              /* small constant in (0, 1) */
     int32_t max_backtrack; /* cap on mu shrinks per iteration */
+    int32_t mu_mode;       /* 0: ||A2_G g_G||^2; 1: Algorithm 2's cross product, forward square if <= 0 */
+    double tol;            /* > 0: stop after the first iteration with ||y - A2 x||^2 <= tol */
 } qo_params;
+
+/* Step size on support G (Eq. step_size; Algorithm 2): num = ||g_G||^2 and
+ *   mu_mode 0: den = ||A2[:, G] g_G||^2
+ *   mu_mode 1: den = (A1[:, G] g_G)^T (A2[:, G] g_G), the product of the two realizations
+ *              Algorithm 2 prints; when it is not positive, den = ||A2[:, G] g_G||^2.
+ * out[0] = num, out[1] = den used, out[2] = the cross product (mode 1; else 0),
+ * out[3] = 1 when mode 1 fell back to the forward square. z1, z2: m doubles of scratch;
+ * coef: s doubles of scratch. */
+void qo_step_size(const double* A1, const double* A2, int32_t m, int32_t n, const int32_t* sup,
+                  const double* g, int32_t s, int32_t mu_mode, double* out, double* coef, double* z1, double* z2)
+{
+    double num = 0.0;
+    for (int32_t q = 0; q < s; ++q) {
+        const double gq = g[sup[q]];
+        num += (QO_MUTANT == 4) ? fabs(gq) : gq * gq;
+        coef[q] = gq;
+    }
+    qo_gemv_cols(A2, m, n, sup, coef, s, z2);
+    double fwd = 0.0;
+    for (int32_t i = 0; i < m; ++i) fwd += z2[i] * z2[i];
+    double cross = 0.0, den = fwd, fell = 0.0;
+    if (mu_mode == 1) {
+        qo_gemv_cols((QO_MUTANT == 10) ? A2 : A1, m, n, sup, coef, s, z1);
+        for (int32_t i = 0; i < m; ++i) cross += z1[i] * z2[i];
+        if (cross > 0.0) den = cross;
+        else fell = 1.0;
+    }
+    out[0] = num;
+    out[1] = den;
+    out[2] = cross;
+    out[3] = fell;
+}
 
 typedef struct {           /* all optional (NULL); arrays have iters + 1 rows */
     int32_t* support;      /* (iters+1) x s: row 0 = initial support, row t = after iteration t */
@@ -244,6 +324,7 @@ typedef struct {           /* all optional (NULL); arrays have iters + 1 rows */
     double* min_margin;    /* (iters+1): min |mu - (1-c) omega| / mu over omega tests (INFINITY if none) */
     double* resid2;        /* (iters+1): ||y - A2 x||^2 after the iteration */
     double* x;             /* (iters+1) x n: iterate after each iteration (row 0 = 0) */
+    int32_t* mu_fallback;  /* (iters+1): 1 when mu_mode 1 fell back to the forward square */
 } qo_trace;
 
 typedef struct {
@@ -299,6 +380,7 @@ int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double
     double* a = (double*)malloc(sizeof(double) * (size_t)n);
     double* r = (double*)malloc(sizeof(double) * (size_t)m);
     double* z = (double*)malloc(sizeof(double) * (size_t)m);
+    double* z1 = (double*)malloc(sizeof(double) * (size_t)m);
     double* xn = (double*)malloc(sizeof(double) * (size_t)n);
     double* coef = (double*)malloc(sizeof(double) * (size_t)(2 * s));
     int32_t* uni = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * s));
@@ -320,9 +402,11 @@ int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double
         if (tr->min_margin) tr->min_margin[0] = INFINITY;
         if (tr->resid2) { double acc = 0.0; for (int32_t i = 0; i < m; ++i) acc += y[i] * y[i]; tr->resid2[0] = acc; }
         if (tr->x) memcpy(tr->x, x, sizeof(double) * (size_t)n);
+        if (tr->mu_fallback) tr->mu_fallback[0] = 0;
     }
 
     int32_t t;
+    int tol_stop = 0;
     for (t = 1; t <= iters; ++t) {
         A1 = A1s[t];
         A2 = A2s[t];
@@ -334,19 +418,14 @@ int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double
         qo_gemv_t((QO_MUTANT == 3) ? A2 : A1, r, m, n, g);
 
         /* step size (Eq. step_size on the current support) */
-        double num = 0.0;
-        for (int32_t q = 0; q < s; ++q) {
-            double gq = g[support[q]];
-            num += (QO_MUTANT == 4) ? fabs(gq) : gq * gq;
-            coef[q] = gq;
-        }
-        qo_gemv_cols(A2, m, n, support, coef, s, z);
-        double den = 0.0;
-        for (int32_t i = 0; i < m; ++i) den += z[i] * z[i];
+        double ss[4];
+        qo_step_size(A1, A2, m, n, support, g, s, p->mu_mode, ss, coef, z1, z);
+        const double num = ss[0], den = ss[1];
         if (num == 0.0 || den == 0.0) break;               /* converged: x unchanged */
         double mu = num / den;
 
         /* proposal x' = H_s(x + mu g) */
+#pragma omp parallel for schedule(static)
         for (int32_t j = 0; j < n; ++j) a[j] = x[j] + mu * g[j];
         qo_hard_threshold(a, n, s, sel, kth, work);
         double min_gap = qo_rel_gap(kth);
@@ -406,13 +485,19 @@ int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double
             if (tr->min_margin) tr->min_margin[t] = min_margin;
             if (tr->resid2) tr->resid2[t] = qo_resid2(A2, y, m, n, support, x, s, coef, z);
             if (tr->x) memcpy(tr->x + (size_t)t * n, x, sizeof(double) * (size_t)n);
+            if (tr->mu_fallback) tr->mu_fallback[t] = (int32_t)ss[3];
+        }
+        if (p->tol > 0.0 && ((QO_MUTANT == 11) ? qo_resid2(A2, y, m, n, support, x, s, coef, z) >= p->tol
+                                               : qo_resid2(A2, y, m, n, support, x, s, coef, z) <= p->tol)) {
+            tol_stop = 1;                                  /* residual reached tol: stop */
+            break;
         }
     }
-    rep->iters_run = (t > iters) ? iters : t - 1;
+    rep->iters_run = tol_stop ? t : ((t > iters) ? iters : t - 1);
     rep->status = status;
     rep->resid_norm2 = qo_resid2(A2, y, m, n, support, x, s, coef, z);
 
-    free(g); free(a); free(r); free(z); free(xn); free(coef); free(uni); free(sel); free(work);
+    free(g); free(a); free(r); free(z); free(z1); free(xn); free(coef); free(uni); free(sel); free(work);
     return status;
 }
 
