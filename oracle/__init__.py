@@ -66,7 +66,8 @@ class _Params(ctypes.Structure):
 class _Trace(ctypes.Structure):
     _fields_ = [("support", ctypes.c_void_p), ("kth", ctypes.c_void_p), ("min_gap", ctypes.c_void_p),
                 ("mu", ctypes.c_void_p), ("bt", ctypes.c_void_p), ("min_margin", ctypes.c_void_p),
-                ("resid2", ctypes.c_void_p), ("x", ctypes.c_void_p), ("mu_fallback", ctypes.c_void_p)]
+                ("resid2", ctypes.c_void_p), ("x", ctypes.c_void_p), ("mu_fallback", ctypes.c_void_p),
+                ("num", ctypes.c_void_p), ("xnorm2", ctypes.c_void_p)]
 
 
 MU_FORWARD_SQ, MU_CROSS = 0, 1
@@ -298,7 +299,8 @@ def niht_seq(A1s: list, A2s: list, ys: list, s: int, iters: int, *, k: float = 2
         arrays = {"support": np.zeros((T, s), np.int32), "kth": np.zeros((T, 2)),
                   "min_gap": np.zeros(T), "mu": np.zeros(T), "bt": np.zeros(T, np.int32),
                   "min_margin": np.zeros(T), "resid2": np.zeros(T),
-                  "x": np.zeros((T, n)) if trace == "x" else None, "mu_fallback": np.zeros(T, np.int32)}
+                  "x": np.zeros((T, n)) if trace == "x" else None, "mu_fallback": np.zeros(T, np.int32),
+                  "num": np.zeros(T), "xnorm2": np.zeros(T)}
         tr = _Trace(*[_ptr(arrays[f]) if arrays[f] is not None else None for f, _ in _Trace._fields_])
     ptrs = [(ctypes.c_void_p * (iters + 1))(*[_ptr(a) for a in lst]) for lst in (A1l, A2l, yl)]
     lib().qo_niht_seq(ptrs[0], ptrs[1], ptrs[2], m, n, s, iters, ctypes.byref(p), _ptr(x), _ptr(sup),

@@ -325,6 +325,8 @@ typedef struct {           /* all optional (NULL); arrays have iters + 1 rows */
     double* resid2;        /* (iters+1): ||y - A2 x||^2 after the iteration */
     double* x;             /* (iters+1) x n: iterate after each iteration (row 0 = 0) */
     int32_t* mu_fallback;  /* (iters+1): 1 when mu_mode 1 fell back to the forward square */
+    double* num;           /* (iters+1): ||g_G||^2 of the iteration's step size (row 0: 0) */
+    double* xnorm2;        /* (iters+1): ||x||^2 after the iteration */
 } qo_trace;
 
 typedef struct {
@@ -403,6 +405,8 @@ int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double
         if (tr->resid2) { double acc = 0.0; for (int32_t i = 0; i < m; ++i) acc += y[i] * y[i]; tr->resid2[0] = acc; }
         if (tr->x) memcpy(tr->x, x, sizeof(double) * (size_t)n);
         if (tr->mu_fallback) tr->mu_fallback[0] = 0;
+        if (tr->num) tr->num[0] = 0.0;
+        if (tr->xnorm2) tr->xnorm2[0] = 0.0;
     }
 
     int32_t t;
@@ -486,6 +490,12 @@ int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double
             if (tr->resid2) tr->resid2[t] = qo_resid2(A2, y, m, n, support, x, s, coef, z);
             if (tr->x) memcpy(tr->x + (size_t)t * n, x, sizeof(double) * (size_t)n);
             if (tr->mu_fallback) tr->mu_fallback[t] = (int32_t)ss[3];
+            if (tr->num) tr->num[t] = num;
+            if (tr->xnorm2) {
+                double acc = 0.0;
+                for (int32_t q = 0; q < s; ++q) acc += x[support[q]] * x[support[q]];
+                tr->xnorm2[t] = acc;
+            }
         }
         if (p->tol > 0.0 && ((QO_MUTANT == 11) ? qo_resid2(A2, y, m, n, support, x, s, coef, z) >= p->tol
                                                : qo_resid2(A2, y, m, n, support, x, s, coef, z) <= p->tol)) {

@@ -29,3 +29,29 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    # the parity results of this run (tests/parity.py): how many took the strict branch,
+    # and the largest errors against the oracle
+    try:
+        import parity
+    except Exception:
+        return
+    res = parity.RESULTS
+    if not res:
+        return
+    strict = [r for r in res if r.get("branch") == "strict" and "failed" not in r]
+    fallback = [r for r in res if r.get("branch") == "fallback" and "failed" not in r]
+    failed = [r for r in res if "failed" in r]
+    xs = [r["x_rel_vs_oracle"] for r in strict if r.get("x_rel_vs_oracle") is not None]
+    r2 = [r.get("resid_norm2_rel") for r in strict if r.get("resid_norm2_rel") is not None]
+    line = (f"parity: {len(res)} solve results, {len(strict)} strict, {len(fallback)} fallback, "
+            f"{len(failed)} failed")
+    if xs:
+        line += f"; max x rel vs oracle {max(xs):.2e}"
+    if r2:
+        line += f"; max ||r||^2 rel {max(r2):.2e}"
+    terminalreporter.write_line(line)
+    for r in fallback:
+        terminalreporter.write_line(f"  fallback: {r['label']} (first ambiguous iteration {r['first_ambiguous']})")

@@ -15,6 +15,7 @@ import torch
 
 import oracle
 import paper_1802_04907_gb300 as q
+import parity
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -101,9 +102,6 @@ def test_gemv_t_multi_odd_grid():
 
 # ---- the solver for many right-hand sides (qiht_niht_solve_multi) ----
 
-GAP = 1e-5
-
-
 def _multi_run(mp, bits_phi, bits_y, iters, seed, odd=False, **kw):
     phi = torch.from_numpy(mp.phi).cuda()
     q1, q2 = q.quantize_pair(phi, bits_phi, seed, q.STREAM_Q1, q.STREAM_Q2, odd=odd)
@@ -114,29 +112,14 @@ def _multi_run(mp, bits_phi, bits_y, iters, seed, odd=False, **kw):
     return res, (q1, q2, ys)
 
 
-def _ambiguous(ref):
-    tr = ref.trace
-    return any(tr["min_gap"][t] < GAP or tr["min_margin"][t] < GAP for t in range(ref.iters_run + 1))
-
-
-def _check_rhs(res, mp, k, ref, tol=1e-4):
+def _check_rhs(res, mp, k, ref, tol=1e-4, label="multi"):
+    """parity.check for right-hand side k; True when it took the fallback branch."""
     rep = res.report(k)
-    assert rep.status == ref.status, (k, rep, ref.status)
-    x = res.x[k].cpu().numpy().astype(np.float64)
-    assert np.count_nonzero(x) <= mp.s
     sup = res.support[k].cpu().numpy()
     assert np.all(np.diff(sup) > 0)
-    if not _ambiguous(ref):
-        assert rep.iters_run == ref.iters_run, k
-        assert np.array_equal(sup, ref.support), k
-        rel = np.linalg.norm(x - ref.x) / max(np.linalg.norm(ref.x), 1e-300)
-        assert rel <= tol, (k, rel)
-        return False
-    truth = np.linalg.norm(mp.X_true[k])
-    e_gpu = np.linalg.norm(x - mp.X_true[k]) / truth
-    e_ref = np.linalg.norm(ref.x - mp.X_true[k]) / truth
-    assert e_gpu <= max(1.5 * e_ref, e_ref + 0.02), (k, e_gpu, e_ref)
-    return True
+    rec = parity.check(f"{label}[{k}]", ref, mp.X_true[k], x=res.x[k].cpu().numpy(), support=sup,
+                       status=rep.status, iters_run=rep.iters_run, resid_norm2=rep.resid_norm2, x_tol=tol)
+    return rec["branch"] == "fallback"
 
 
 @pytest.mark.parametrize("bits", [2, 4, 8])
@@ -149,8 +132,8 @@ def test_multi_against_oracle(bits):
     for k in range(mp.Y.shape[0]):
         p = mp.problem(k)
         ref, _ = oracle.qiht(p.phi, p.y, s, 40, bits_phi=bits, bits_y=bits, seed=9, trace=True)
-        amb += _check_rhs(res, mp, k, ref)
-    assert amb < mp.Y.shape[0] // 2
+        amb += _check_rhs(res, mp, k, ref, label=f"multi-{bits}bit")
+    assert amb <= mp.Y.shape[0] // 8
 
 
 def test_multi_ragged_two_tiles_mixed_widths():

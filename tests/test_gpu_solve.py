@@ -3,20 +3,9 @@
 Both sides quantize the same seeded inputs (codes are bit-exact, see
 test_gpu_quantize.py) and run the same number of iterations. The GPU computes
 g in exact integer sums of 24-bit fixed-point residuals and everything else in
-FP32 with FP64 scalars; the oracle is FP64. The rule:
-  - the support after every iteration is identical up to the first iteration
-    whose selection was ambiguous in the oracle (relative gap between the s-th
-    and (s+1)-th magnitudes below 1e-5, or a backtracking test within 1e-5 of
-    its threshold)
-  - the step size agrees to 1e-4 relative in the first three iterations and in
-    every iteration whose support changes (where mu decides the selection);
-    elsewhere g_G -> 0 as x converges and mu = ||g_G||^2 / ||Q2 g_G||^2 becomes a
-    ratio of vanishing quantities whose relative accuracy degrades like
-    (absolute error of g) / ||g_G||, so it is not compared (its effect, the
-    step mu g_G, vanishes with it and is covered by the comparison of x)
-  - when no iteration was ambiguous, the final x agrees to 1e-4 relative L2
-  - otherwise both recoveries are compared against the ground truth and the
-    first ambiguous iteration is reported.
+FP32 with FP64 scalars; the oracle is FP64. The rule is parity.check: supports,
+residuals and the step size per iteration, then x within 1e-4 relative L2 when no
+iteration of the oracle was ambiguous, else both recoveries against the ground truth.
 """
 import numpy as np
 import pytest
@@ -24,11 +13,12 @@ import torch
 
 import oracle
 import paper_1802_04907_gb300 as q
+import parity
 import synth
 
 pytestmark = pytest.mark.gpu
 
-GAP = 1e-5
+GAP = parity.GAP
 
 
 def _run_pair(p, bits_phi, bits_y, iters, seed, odd=False, **kw):
@@ -37,44 +27,28 @@ def _run_pair(p, bits_phi, bits_y, iters, seed, odd=False, **kw):
     q1, q2, qy = q.quantize_problem(phi, y, bits_phi, bits_y, seed, odd=odd)
     sv = q.niht_solve(q1, q2, qy, p.s, iters, trace=True, **kw)
     torch.cuda.synchronize()
+    okw = {k: v for k, v in kw.items() if k in ("k", "c", "max_backtrack", "mu_mode", "tol")}
     ref, _ = oracle.qiht(p.phi, p.y, p.s, iters, bits_phi=bits_phi, bits_y=bits_y, seed=seed, trace=True,
-                         odd=odd, **kw)
+                         odd=odd, **okw)
     return sv, ref
 
 
 def _first_ambiguous(ref):
-    tr = ref.trace
-    for t in range(ref.iters_run + 1):
-        if tr["min_gap"][t] < GAP or tr["min_margin"][t] < GAP:
-            return t
-    return None
+    return parity.first_ambiguous(ref)
 
 
-def _check(sv, ref, p, label="", mu_tol=1e-4):
+def _check(sv, ref, p, label="", mu_rule="decisive", require_strict=False):
+    """parity.check on a Solver's results; returns (x relative to the oracle, None) on the
+    strict branch, (None, first ambiguous iteration) on the fallback branch."""
     rep = sv.read_report()
-    assert rep.status == ref.status, (rep, ref.status)
-    amb = _first_ambiguous(ref)
-    T = ref.iters_run if amb is None else amb - 1
-    sup = sv.trace["support"].cpu().numpy()
-    mu = sv.trace["mu"].cpu().numpy()
-    rsup = ref.trace["support"]
-    for t in range(0, T + 1):
-        assert np.array_equal(sup[t], rsup[t]), f"{label}: support differs at iteration {t}"
-        if t > 0 and (t <= 3 or not np.array_equal(rsup[t], rsup[t - 1])):
-            assert abs(mu[t] - ref.trace["mu"][t]) <= mu_tol * ref.trace["mu"][t], f"{label}: mu at {t}"
-    x = sv.x.cpu().numpy().astype(np.float64)
-    assert np.count_nonzero(x) <= p.s
-    truth = np.linalg.norm(p.x_true)
-    if amb is None:
-        assert rep.iters_run == ref.iters_run
-        assert np.array_equal(np.sort(sv.support.cpu().numpy()), ref.support)
-        rel = np.linalg.norm(x - ref.x) / max(np.linalg.norm(ref.x), 1e-300)
-        assert rel <= 1e-4, f"{label}: x differs from the oracle by {rel:.3e}"
-        return rel, None
-    e_gpu = np.linalg.norm(x - p.x_true) / truth
-    e_ref = np.linalg.norm(ref.x - p.x_true) / truth
-    assert e_gpu <= max(1.5 * e_ref, e_ref + 0.02), f"{label}: gpu error {e_gpu:.3e} vs oracle {e_ref:.3e}"
-    return None, amb
+    tr = {k: v.cpu().numpy() for k, v in sv.trace.items()} if sv.trace is not None else {}
+    rec = parity.check(label, ref, p.x_true, x=sv.x.cpu().numpy(), support=sv.support.cpu().numpy(),
+                       status=rep.status, iters_run=rep.iters_run, resid_norm2=rep.resid_norm2,
+                       sup_trace=tr.get("support"), mu_trace=tr.get("mu"), resid_trace=tr.get("resid2"),
+                       mu_rule=mu_rule, require_strict=require_strict)
+    if rec["branch"] == "strict":
+        return rec["x_rel_vs_oracle"], None
+    return None, rec["first_ambiguous"]
 
 
 def test_small_noiseless_8bit():
@@ -120,11 +94,11 @@ def test_mri_small():
     # stacked real 696 x 1024, s = 48, 30 dB, 8-bit
     p = synth.mri(grid=32, s=48, seed=1)
     sv, ref = _run_pair(p, 8, 8, 100, seed=3)
-    # on this operator the iteration amplifies rounding in mu: a CPU emulation of the FP32 vectors
-    # and the 24-bit fixed-point residual drifts from the FP64 iteration by 1e-4 in mu after ~30
-    # iterations and 2.5e-4 after 96, while x stays within 1.1e-6; supports and x are checked as
-    # everywhere, mu to 1e-3
-    _check(sv, ref, p, "mri-32", mu_tol=1e-3)
+    # on this operator the iteration amplifies rounding in mu (it drifts from the FP64
+    # iteration by more than 1e-4 relative after a few tens of iterations while x stays
+    # within ~1e-6): mu is held to the displacement bound on every iteration, supports,
+    # residuals and x as everywhere
+    _check(sv, ref, p, "mri-32", mu_rule="step")
 
 
 def test_mri_full_size():
@@ -145,7 +119,7 @@ def test_backtracking_instance():
             break
     sv, ref = _run_pair(p, 8, 8, 40, seed=seed)
     _check(sv, ref, p, "backtracking")
-    amb = _first_ambiguous(ref)
+    amb = parity.first_ambiguous(ref)
     T = ref.iters_run if amb is None else amb - 1
     bt = sv.trace["bt"].cpu().numpy()
     assert np.array_equal(bt[1:T + 1], ref.trace["bt"][1:T + 1])
@@ -196,27 +170,24 @@ def test_deterministic_and_graph_reuse():
     assert sv.read_report() == r1
 
 
-def test_full_size_large_solve():
-    # 8192 x 32768, s = 256, +-U(0.5,1.5) nonzeros, 30 dB, 8-bit, 300 iterations (the benchmarked
-    # configuration): properties that hold at any size, plus recovery of the true support
+@pytest.mark.parametrize("bits,iters", [(8, 300), (4, 60)])
+def test_full_size_large_solve_against_oracle(bits, iters):
+    # the benchmarked configuration at full size: 8192 x 32768, s = 256, +-U(0.5,1.5)
+    # nonzeros, 30 dB; 8-bit with the full 300 iterations, 4-bit with 60. The oracle solves
+    # the same quantized instance in FP64 (two 2 GiB matrices); no iteration of it is
+    # ambiguous, so the strict branch is required: supports and residuals at every
+    # iteration, the step sizes, and x within 1e-4 of the oracle's
     p = synth.large_noisy(seed=0)
-    phi = torch.from_numpy(p.phi).cuda()
-    y = torch.from_numpy(p.y).cuda()
-    q1, q2, qy = q.quantize_problem(phi, y, 8, 8, 0)
-    sv = q.niht_solve(q1, q2, qy, p.s, 300, trace=True)
-    torch.cuda.synchronize()
+    sv, ref = _run_pair(p, bits, bits, iters, seed=0)
+    rel, amb = _check(sv, ref, p, f"large-{bits}bit-{iters}it", require_strict=True)
+    assert amb is None
     rep = sv.read_report()
     assert rep.status == q.OK
     x = sv.x.cpu().numpy().astype(np.float64)
-    sup = np.sort(sv.support.cpu().numpy())
-    assert np.count_nonzero(x) <= p.s
-    assert set(np.flatnonzero(x)) <= set(sup)
-    assert len(np.intersect1d(sup, p.support)) >= 0.99 * p.s
-    rel = np.linalg.norm(x - p.x_true) / np.linalg.norm(p.x_true)
-    assert rel < 0.05, rel
-    # the residual reported is the one of the returned x
-    r2 = sv.trace["resid2"].cpu().numpy()[: rep.iters_run + 1]
-    assert abs(r2[-1] - rep.resid_norm2) <= 1e-12 * rep.resid_norm2
+    assert set(np.flatnonzero(x)) <= set(sv.support.cpu().numpy())
+    if bits == 8:
+        assert len(np.intersect1d(sv.support.cpu().numpy(), p.support)) >= 0.99 * p.s
+        assert np.linalg.norm(x - p.x_true) / np.linalg.norm(p.x_true) < 0.05
 
 
 def test_eager_driver_matches_graph():
