@@ -12,8 +12,9 @@ e2e     = the same metric with Phi and y copied from pinned host memory and x,
 roofline: the gradient kernel g = Q1^T r (one pass over the codes of Q1), timed
           alone with CUDA events on its stream with the solver's launch plan;
           algorithmic bytes = m n b / 8 + 4 m + 4 n per launch.
-cpu_baseline / --impl reference: the CPU oracle (plain FP64 C, one thread) on a
-          bounded sample (the first rows of the same matrix), scaled per iteration.
+cpu_baseline / --impl reference: the CPU oracle (plain FP64 C, OpenMP over the
+          host cores) on one bounded sample (the first 2048 rows of the same matrix,
+          200 iterations), extrapolated to the full step.
 
 Under torchrun with N > 1 ranks, every rank solves its own independent instance
 (replicas; no collective in the data path) and the value is the sum over ranks.
@@ -61,6 +62,9 @@ def parse():
     ap.add_argument("--s", type=int, default=S)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-widths", action="store_true", help="skip the gradient kernel at the other code widths")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched measurements (many right-hand sides; many problems) of the default line")
     ap.add_argument("--gemv-launches", type=int, default=200)
     ap.add_argument("--workload", choices=["single", "interferometry", "mri", "batched", "multi", "fresh", "unrolled"], default="single",
                     help="single: the large single solve (default); batched: 512 independent problems in one "
@@ -117,12 +121,39 @@ def config(args, world):
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(p, bits, iters_total, rows=1024, iters=8):
-    """Oracle timing on the first `rows` rows of the workload (same n, s): the
-    quantization and the per-iteration work scale linearly with m, so the step
-    time of the full problem is estimated as (m/rows) x (quantize time +
-    iters_total x per-iteration time)."""
+SAMPLE_ROWS, SAMPLE_ITERS = 2048, 200
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (x86 'model name', or the Arm implementer/part pair)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(p, bits, iters_total, rows=SAMPLE_ROWS, iters=SAMPLE_ITERS, threads=None):
+    """The CPU oracle (FP64 C, OpenMP over the host cores) on a bounded sample of the workload:
+    the first `rows` rows (same n, s), its three quantizations and `iters` iterations. The
+    quantization and the per-iteration work scale linearly with m, so the step time of the full
+    problem is estimated as (m / rows) x (quantize time + iters_total x per-iteration time).
+    Both CPU figures of the bench (the reference arm and the cpu_baseline of our line) use this
+    one sample definition."""
     import oracle
+    nproc = os.cpu_count() or 1
+    oracle.set_threads(threads or nproc)
+    used = oracle.get_threads()
     sub_phi = np.ascontiguousarray(p.phi[:rows])
     sub_y = np.ascontiguousarray(p.y[:rows])
     t0 = time.perf_counter()
@@ -139,9 +170,11 @@ def oracle_sample(p, bits, iters_total, rows=1024, iters=8):
     t_quant = (t1 - t0) * scale
     t_iter = (t2 - t1) / iters * scale
     step = t_quant + iters_total * t_iter
-    return {"value": iters_total / step, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": iters_total / step, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"first {rows} of {p.m} rows (n={p.n}, s={p.s}): quantize Q1,Q2,Q(y) + {iters} "
-                      f"iterations, single-threaded FP64 C; step time scaled by m/{rows} = {scale:g}",
+                      f"iterations, FP64 C with OpenMP on {used} threads; the full step's time is extrapolated "
+                      f"from the sample by m/{rows} = {scale:g}",
+            "extrapolated": True, "nproc": nproc, "cpu_model": cpu_model(),
             "sample_seconds": round(t2 - t0, 3), "est_step_seconds": round(step, 3)}
 
 
@@ -165,8 +198,12 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config(args, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": last["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"], "extrapolated": True, "nproc": last["nproc"],
+                             "cpu_model": last["cpu_model"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "each step times the bounded sample (not the full problem); ms_per_step is the full "
+                    "step's time extrapolated from it",
             "wall_seconds": round(wall, 2)}
     print(json.dumps(line))
 
@@ -388,6 +425,31 @@ def run_ours(args):
                 "avg_launch_us": gemv_ms * 1e3, "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
+    # the same gradient kernel at the other code widths of the workload (b in {2, 4, 8}): the
+    # codes of the same Phi quantized to b bits, timed alone the same way
+    by_bits = {}
+    if args.workload == "single" and not args.no_widths:
+        for b in (8, 4, 2):
+            if b == bits:
+                by_bits[str(b)] = {k: roofline[k] for k in ("achieved", "frac", "avg_launch_us",
+                                                             "algorithmic_bytes_per_launch", "traffic")}
+                continue
+            qb, _ = q.quantize_pair(phi, b, 11, q.STREAM_Q1, q.STREAM_Q2)
+            for _ in range(5):
+                q.gemv_t_prescaled(qb, r, rmax, g, stream=stream)
+            barrier()
+            ev0.record(stream)
+            for _ in range(nl):
+                q.gemv_t_prescaled(qb, r, rmax, g, stream=stream)
+            ev1.record(stream)
+            barrier()
+            ms_b = ev0.elapsed_time(ev1) / nl
+            alg_b = args.m * args.n * b / 8 + 4 * args.m + 4 * args.n
+            ach_b = alg_b / (ms_b / 1e3) / 1e9
+            by_bits[str(b)] = {"achieved": ach_b, "frac": ach_b / peak, "avg_launch_us": ms_b * 1e3,
+                               "algorithmic_bytes_per_launch": alg_b, "traffic": traffic_for_kernel(b, args.m, args.n)}
+            del qb
+        roofline["by_bits"] = by_bits
     if args.m * args.n * bits / 8 < 100 * 2**20:
         roofline["note"] = ("the Q1 codes (%.0f MiB) fit in the 129 MB L2: repeated gradient launches read them "
                             "mostly from L2, so the fraction of the HBM peak can exceed 1"
@@ -452,9 +514,17 @@ def run_ours(args):
     launches_per_step = 5 + 3 + 2 * unroll * -(-iters_done // unroll)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # a bounded sample of ~10-15 s on the host: 200 iterations on the first 2048 rows
-        cpu = oracle_sample(p, bits, args.iters, rows=min(2048, p.m), iters=200)
-        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        # the bounded sample that the reference arm times too: 200 iterations on the first
+        # 2048 rows, on all host cores
+        cpu = oracle_sample(p, bits, args.iters, rows=min(SAMPLE_ROWS, p.m))
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "extrapolated", "nproc",
+                                   "cpu_model")}
+
+    # the metric's second half: batched vs plain solves/s at equal error, measured in this run
+    batched = None
+    if rank == 0 and world == 1 and args.workload == "single" and not args.no_batched:
+        del phi_h, y_h
+        batched = batched_summary(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -472,6 +542,8 @@ def run_ours(args):
                            "full_selects": rep.full_selects,
                            "iteration_phases_us": [round(v, 2) for v in rep.phase_us[:7]]},
                 "driver": "eager launches" if args.eager else "one CUDA graph per solve"}
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -480,7 +552,30 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # batched workload: many independent problems of uneven size in one launch
 # ---------------------------------------------------------------------------
-def run_batched(args):
+def batched_summary(args):
+    """Both batched workloads, one timed launch each (after one warm-up), for the default line:
+    many right-hand sides sharing the large Phi (1024 x s=256, 8-bit, 300 iterations; the
+    gradients as one tensor-core product) and many independent problems of uneven size (512,
+    4-bit, 100 iterations, one persistent launch), each against plain single solves at equal
+    error."""
+    import copy
+    a = copy.copy(args)
+    a.steps, a.warmup = 1, 1
+    a.m, a.n, a.s, a.bits, a.iters = M, N, S, 8, ITERS
+    t0 = time.perf_counter()
+    mu = run_multi(a, emit=False)
+    t1 = time.perf_counter()
+    ba = run_batched(a, emit=False)
+    t2 = time.perf_counter()
+    keep_m = ("value", "unit", "ms_per_step", "plain", "speedup_vs_plain", "equal_error", "roofline", "clocks",
+              "statuses", "config")
+    keep_b = ("value", "unit", "ms_per_step", "plain", "speedup_vs_plain", "equal_error", "roofline", "clocks",
+              "statuses", "config")
+    return {"multi_rhs": {**{k: mu[k] for k in keep_m if k in mu}, "wall_s": round(t1 - t0, 1)},
+            "many_problems": {**{k: ba[k] for k in keep_b if k in ba}, "wall_s": round(t2 - t1, 1)}}
+
+
+def run_batched(args, emit=True):
     """512 Gaussian problems, m ~ U[128, 2048], n = 4m, s ~ U[8, 128], x with N(0,1) nonzeros,
     noiseless, 4-bit Phi and y, 100 iterations each, generated on the device from seeds.
     value = solves/s of one qiht_niht_solve_batched launch; the same problems solved one by one
@@ -564,10 +659,12 @@ def run_batched(args):
                          "note": "Q1 code bytes streamed per iteration over the launch time"},
             "statuses": {str(k): sum(1 for r in reps if r.status == k) for k in sorted({r.status for r in reps})}}
     line["clocks"] = clocks
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
-def run_multi(args):
+def run_multi(args, emit=True):
     """nrhs right-hand sides sharing the large Gaussian matrix (8192 x 32768, N(0, 1/m)), each
     x_k with s = 256 N(0,1) nonzeros at a uniform support, y_k = Phi x_k + noise at 30 dB, Phi
     and y_k quantized to 8 bits, 300 iterations each; inputs generated on the device from seeds.
@@ -682,7 +779,9 @@ def run_multi(args):
             "gpu_launches": launches * args.steps,
             "clocks": clk,
             "statuses": {str(k): sum(1 for r in reps if r.status == k) for k in sorted({r.status for r in reps})}}
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
 def run_fresh(args):

@@ -76,3 +76,27 @@ def test_cli_and_config_of_the_single_solve_workloads(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
     args = bench.parse()
     assert args.impl == "reference" and args.gpus == 2
+
+
+def test_cpu_sample_is_one_definition_and_records_the_host():
+    # the reference arm and the cpu_baseline of the line time the same bounded oracle sample,
+    # on every host core, and say how many threads ran and on which CPU
+    sys.path.insert(0, ROOT)
+    import inspect
+
+    import bench
+    import oracle
+    import synth
+    sig = inspect.signature(bench.oracle_sample)
+    assert sig.parameters["rows"].default == bench.SAMPLE_ROWS
+    assert sig.parameters["iters"].default == bench.SAMPLE_ITERS
+    p = synth.gaussian(128, 512, 8, seed=1, snr_db=30.0)
+    n0 = oracle.get_threads()
+    try:
+        out = bench.oracle_sample(p, 8, 300, rows=64, iters=5)
+    finally:
+        oracle.set_threads(n0)
+    assert out["kind"] == "oracle" and out["extrapolated"] is True
+    assert out["cores"] == (os.cpu_count() or 1) and out["nproc"] == os.cpu_count()
+    assert isinstance(out["cpu_model"], str) and out["cpu_model"]
+    assert out["value"] > 0 and "first 64 of 128 rows" in out["sample"]
