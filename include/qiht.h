@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define QIHT_ABI_VERSION 2
+#define QIHT_ABI_VERSION 3
 
 /* Same type as cudaStream_t. */
 typedef struct CUstream_st* qiht_stream_t;
@@ -218,11 +218,25 @@ qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float
                                      with QIHT_ERR_TIMEOUT in the report; the CUDA context stays
                                      usable. Honoured by the kernel used for s <= 1024. */
 
+/* Denominator of the step size mu = ||g_G||^2 / den on the current support G (Eq. for mu). */
+#define QIHT_MU_FORWARD_SQ 0  /* den = ||Q2_G g_G||^2 (positive; the default) */
+#define QIHT_MU_CROSS      1  /* den = (Q1_G g_G)^T (Q2_G g_G), the product of the two quantizations that
+                                 Algorithm 2 prints (with fresh realizations: Phi-hat_{2n-1} and
+                                 Phi-hat_{2n}); when it is not positive, the forward square is used */
+
 typedef struct {
     double k;               /* shrinkage of the step size, k > 1/(1-c) (Section II-A); default 2 */
     double c;               /* small constant of the descent test, 0 < c < 1; default 0.01 */
     int32_t max_backtrack;  /* shrinks allowed per iteration before QIHT_ERR_BACKTRACK_CAP; default 32 */
     int32_t flags;          /* 0 or QIHT_SOLVE_EAGER, QIHT_SOLVE_TEST_TIMEOUT */
+    double tol;             /* 0: off. > 0: stop after the first iteration whose ||Q(y) - Q2 x||^2 (FP64) is
+                               at most tol. The paper stops after a fixed number of iterations,
+                               n* = ceil(log2(||x^s|| / eps_s)) (Section III-B, after Theorem 4); tol states
+                               the same criterion on the residual, for when eps_s is not known. Must be
+                               finite and >= 0. */
+    int32_t mu_mode;        /* QIHT_MU_FORWARD_SQ (default) or QIHT_MU_CROSS; Q1 and Q2 must then be on
+                               the same grid */
+    int32_t reserved;       /* 0 */
 } qiht_params;
 
 typedef struct {            /* written on the device after every iteration */
@@ -260,7 +274,9 @@ size_t qiht_solve_workspace_size(int32_t m, int32_t n, int32_t s);
  * ascending], report [device, one qiht_report]. trace may be NULL.
  * The whole run is one CUDA-graph launch (built on the first call with a given
  * set of arguments and cached); control never returns to the host between
- * iterations. Requires 1 <= s <= min(m, n), m <= 16384, n <= 49152. */
+ * iterations. Requires 1 <= s <= min(m, n), m <= 16384, n <= 49152.
+ * params may be NULL (the defaults). With params->tol > 0 the run stops after the
+ * first iteration whose residual is at most tol; the report's iters_run says which. */
 qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_codes* y,
                             int32_t s, int32_t iters, const qiht_params* params,
                             float* x, int32_t* support, qiht_report* report, const qiht_trace* trace,
@@ -285,7 +301,9 @@ size_t qiht_solve_fresh_workspace_size(int32_t m, int32_t n, int32_t s, int32_t 
  * `seed` and the scales max |Phi|, max |y| (so iteration 1 equals qiht_niht_solve's on the
  * quantizations with streams 0, 1, 2). phi [device] m x n row-major (row stride ld_phi
  * >= n floats), y [device] m floats; quant_flags 0 or QIHT_ODD_LEVELS. Outputs and
- * params as for qiht_niht_solve (params->flags must be 0). Every iteration re-quantizes
+ * params as for qiht_niht_solve (params->flags must be 0; with QIHT_MU_CROSS the step size
+ * takes the product of the iteration's two realizations, as Algorithm 2 prints it). Every
+ * iteration re-quantizes
  * Phi twice (one pass over the FP32 matrix) and y, then runs the iteration as separate
  * kernels; the host reads the solver state after every iteration and backtracking test,
  * so the call returns when the solve is done (the stream is synchronised). Requires
@@ -323,7 +341,8 @@ size_t qiht_solve_batched_workspace_size(int32_t nprob);
  * entirely in its shared memory (the limits above keep a problem's vectors there).
  * Results per problem are those of the same algorithm and arithmetic as
  * qiht_niht_solve (exact-integer gradient, FP32 products, FP64 step size; the order of
- * some FP32 sums differs). Errors: QIHT_ERR_ARG (a problem out of the limits, mixed bits,
+ * some FP32 sums differs). params->tol must be 0 and params->mu_mode QIHT_MU_FORWARD_SQ.
+ * Errors: QIHT_ERR_ARG (a problem out of the limits, mixed bits,
  * bad pointers), QIHT_ERR_BITS, QIHT_ERR_WORKSPACE, QIHT_ERR_CUDA; per-problem numeric
  * failures are in the problem's report. Asynchronous on `stream` after the descriptor
  * copy. */
@@ -352,7 +371,8 @@ size_t qiht_solve_multi_workspace_size(int32_t m, int32_t n, int32_t s, int32_t 
  * Arithmetic: that of qiht_niht_solve except the gradient (f16 products of the exact
  * codes with a two-part f16 split of the residual, FP32 sums; see qiht_gemv_t_multi).
  * Requires m <= QIHT_MULTI_MAX_ROWS, n <= QIHT_MULTI_MAX_COLS, 1 <= s <= min(m, n,
- * QIHT_MULTI_MAX_S); params->flags must be 0. Errors as for qiht_niht_solve; numeric
+ * QIHT_MULTI_MAX_S); params->flags and params->tol must be 0, params->mu_mode
+ * QIHT_MU_FORWARD_SQ. Errors as for qiht_niht_solve; numeric
  * failures of a right-hand side are in its report, a device-side timeout of the
  * gradient product (QIHT_ERR_TIMEOUT) in every report. Asynchronous on `stream` after
  * the descriptor copy. */

@@ -56,7 +56,20 @@ class _Problem(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_double), ("c", ctypes.c_double), ("max_backtrack", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("tol", ctypes.c_double), ("mu_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+MU_FORWARD_SQ, MU_CROSS = 0, 1
+
+
+def _mu_mode(mode) -> int:
+    """QIHT_MU_FORWARD_SQ for "forward" (the default) or QIHT_MU_CROSS for "cross"."""
+    if mode in (MU_FORWARD_SQ, "forward", "forward_sq"):
+        return MU_FORWARD_SQ
+    if mode in (MU_CROSS, "cross"):
+        return MU_CROSS
+    raise ValueError(f"mu_mode {mode!r}")
 
 
 class _Report(ctypes.Structure):
@@ -401,10 +414,11 @@ class Solver:
 
     def __init__(self, m: int, n: int, s: int, iters: int, *, device="cuda", trace: bool = False,
                  k: float = 2.0, c: float = 0.01, max_backtrack: int = 32, eager: bool = False,
-                 test_timeout: bool = False):
+                 test_timeout: bool = False, tol: float = 0.0, mu_mode="forward"):
         self.m, self.n, self.s, self.iters = m, n, s, iters
         self.params = _Params(k, c, max_backtrack,
-                              (SOLVE_EAGER if eager else 0) | (SOLVE_TEST_TIMEOUT if test_timeout else 0))
+                              (SOLVE_EAGER if eager else 0) | (SOLVE_TEST_TIMEOUT if test_timeout else 0),
+                              float(tol), _mu_mode(mu_mode), 0)
         self.x = torch.empty(n, dtype=torch.float32, device=device)
         self.support = torch.empty(s, dtype=torch.int32, device=device)
         self.report = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=device)
@@ -452,7 +466,7 @@ def niht_solve(Q1: Codes, Q2: Codes, y: Codes, s: int, iters: int, *, trace: boo
 
 def niht_solve_fresh(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: int, seed: int, s: int, iters: int,
                      *, odd: bool = False, trace: bool = False, k: float = 2.0, c: float = 0.01,
-                     max_backtrack: int = 32, stream=None) -> Solver:
+                     max_backtrack: int = 32, tol: float = 0.0, mu_mode="forward", stream=None) -> Solver:
     """qiht_niht_solve_fresh: Algorithm 2 with new quantizations of Phi and y in every iteration.
     Returns a Solver-like object holding x, support, report (and trace)."""
     if not (isinstance(phi, torch.Tensor) and phi.is_cuda and phi.dtype == torch.float32 and phi.dim() == 2 and
@@ -460,7 +474,8 @@ def niht_solve_fresh(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: 
         raise ValueError("phi: needs a CUDA float32 m x n matrix with unit column stride")
     m, n = phi.shape
     _need(y, m, torch.float32, "y")
-    sv = Solver(m, n, s, iters, device=phi.device, trace=trace, k=k, c=c, max_backtrack=max_backtrack)
+    sv = Solver(m, n, s, iters, device=phi.device, trace=trace, k=k, c=c, max_backtrack=max_backtrack, tol=tol,
+                mu_mode=mu_mode)
     ws = _ws(lib().qiht_solve_fresh_workspace_size(m, n, s, bits_phi, bits_y), phi.device)
     tr = None
     if sv.trace is not None:
@@ -578,7 +593,7 @@ def niht_solve_batched(problems: list, iters: int, *, k: float = 2.0, c: float =
         arr[i] = _Problem(q1.c_struct(), q2.c_struct(), qy.c_struct(), int(s), 0, xs[i].data_ptr(),
                           sups[i].data_ptr(), reports[i].data_ptr())
     ws = _ws(lib().qiht_solve_batched_workspace_size(nprob), dev)
-    params = _Params(k, c, max_backtrack, 0)
+    params = _Params(k, c, max_backtrack, 0, 0.0, MU_FORWARD_SQ, 0)
     st = lib().qiht_niht_solve_batched(arr, nprob, iters, ctypes.byref(params), ws.data_ptr(), ws.numel(),
                                        _stream(stream))
     _check(st, "qiht_niht_solve_batched")
@@ -618,7 +633,7 @@ def niht_solve_multi(Q1: Codes, Q2: Codes, ys: list, s: int, iters: int, *, k: f
                                                                                           nrhs), dev)
     arr = (_Codes * nrhs)(*[y.c_struct() for y in ys])
     c1, c2 = Q1.c_struct(), Q2.c_struct()
-    params = _Params(k, c, max_backtrack, 0)
+    params = _Params(k, c, max_backtrack, 0, 0.0, MU_FORWARD_SQ, 0)
     st = lib().qiht_niht_solve_multi(ctypes.byref(c1), ctypes.byref(c2), arr, nrhs, s, iters, ctypes.byref(params),
                                      X.data_ptr(), sup.data_ptr(), reports.data_ptr(), ws.data_ptr(), ws.numel(),
                                      _stream(stream))

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
                     s_bad = 1;
                     col = -1;
                 } else {
-                    cf = (a.mode == kGatherMu) ? __ldcg(a.g + col) : __ldcg(coefs + jj);
+                    cf = (a.mode == kGatherMu || a.coef_from_g) ? __ldcg(a.g + col) : __ldcg(coefs + jj);
                 }
             }
             s_col[threadIdx.x] = col;
@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     __threadfence();
 
     const float alpha = __fdiv_rn(*a.Q.scale, (float)a.Q.lm1);   // = the double quotient rounded to float
-    double acc = 0.0;
+    const bool cross = a.mode == kGatherMu && a.zx;                // QIHT_MU_CROSS: also zx . z
+    double acc = 0.0, accx = 0.0;
     unsigned mx = 0;
     if (q < ld) {
         float zz[G];
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
                     mx = max(mx, __float_as_uint(ri) & 0x7fffffffu);
                 } else {
                     acc += (double)zz[k] * (double)zz[k];
+                    if (cross) accx += (double)__ldcg(a.zx + i) * (double)zz[k];
                 }
             }
         }
@@ -231,9 +233,10 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     }
     acc = block_sum_d(acc, shd);
     mx = block_max_u(mx, shu);
+    if (cross) accx = block_sum_d(accx, shd);
     if (threadIdx.x == 0) {
         a.rb_partial[2 * rb] = acc;
-        a.rb_partial[2 * rb + 1] = (double)mx;   // exact: mx < 2^32
+        a.rb_partial[2 * rb + 1] = cross ? accx : (double)mx;   // exact: mx < 2^32
         a.counters[rb] = 0;
     }
     // arrival of this row block
@@ -251,14 +254,16 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
         double t = 0.0, mxl = 0.0, cs = 0.0;
         for (int b = threadIdx.x; b < nrb; b += 32) {
             t += __ldcg(a.rb_partial + 2 * b);
-            mxl = fmax(mxl, __ldcg(a.rb_partial + 2 * b + 1));
+            if (cross) mxl += __ldcg(a.rb_partial + 2 * b + 1);        // the sum of zx . z
+            else mxl = fmax(mxl, __ldcg(a.rb_partial + 2 * b + 1));
         }
         if (a.chunk_partial && (a.mode == kGatherMu || a.mode == kGatherOmega))
             for (int c = threadIdx.x; c < nchunks; c += 32) cs += __ldcg(a.chunk_partial + c);
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             t += __shfl_xor_sync(0xffffffffu, t, o);
-            mxl = fmax(mxl, __shfl_xor_sync(0xffffffffu, mxl, o));
+            const double om = __shfl_xor_sync(0xffffffffu, mxl, o);
+            mxl = cross ? mxl + om : fmax(mxl, om);
             cs += __shfl_xor_sync(0xffffffffu, cs, o);
         }
         if (threadIdx.x == 0) {
@@ -277,13 +282,18 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
     if (a.mode == kGatherMu) {
         if (threadIdx.x == 0) {
             const double num = coef_norm2;
-            const double den = alpha_d * alpha_d * total;
+            const double den_f = alpha_d * alpha_d * total;
+            double den = den_f;
+            if (cross) {
+                const double den_c = alpha_d * mxd;         // zx holds alpha Q1_G g_G
+                if (den_c > 0.0) den = den_c;              // else the forward square
+            }
             st->num = num;
             st->bt = 0;
-            if (!isfinite(num) || !isfinite(den)) {
+            if (!isfinite(num) || !isfinite(den_f)) {
                 st->status = QIHT_ERR_NONFINITE;
                 st->stop = 1;
-            } else if (num == 0.0 || den == 0.0) {
+            } else if (num == 0.0 || den_f == 0.0) {
                 st->stop = 1;                      // converged: x stays
             } else {
                 st->mu = num / den;
@@ -340,6 +350,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a)
             if (a.trace.bt) a.trace.bt[it] = st->bt;
             if (a.trace.resid2) a.trace.resid2[it] = total;
             if (it >= st->iters) st->stop = 1;
+            if (a.tol > 0.0 && total <= a.tol) st->stop = 1;      // the residual reached tol
             write_report(a, st);
         }
         __syncthreads();

@@ -72,8 +72,30 @@ __device__ __noinline__ void warp_prologue(const GemvTArgs& a, unsigned* s_st)
     // max |r|: from the iteration kernel's residual partials (fast path) or the state
     unsigned rmx = 0;
     if (a.rpart) rmx = (unsigned)slot_max_complete(a.rpart, kSlotRmax, a.rgrid);
+    // ||r||^2 of the iteration the iteration kernel just completed (it leaves the record to
+    // this kernel, so that none of its CTAs waits for the others at the end), and the
+    // residual tolerance: a run whose ||r||^2 reached tol stops after this iteration
+    bool tol_stop = false;
+    if (a.rpart && blockIdx.x == 0) {
+        const int st_iter = __shfl_sync(0xffffffffu, a.st->iter, 0);
+        const int logged = __shfl_sync(0xffffffffu, a.st->resid_logged, 0);
+        if (st_iter > logged) {
+            const double r2 = slot_sum_complete(a.rpart, kSlotResid, a.rgrid);
+            if (threadIdx.x == 0) {
+                a.st->resid2 = r2;
+                a.st->resid_logged = st_iter;
+                if (a.trace_resid2) a.trace_resid2[st_iter] = r2;
+                if (a.report) a.report->resid_norm2 = r2;
+            }
+            tol_stop = a.tol > 0.0 && r2 <= a.tol;
+        }
+    }
     if (threadIdx.x == 0) {
         int stop = a.st ? a.st->stop : 0;
+        if (tol_stop && !stop) {
+            stop = 1;                       // CTA 0 only; the other CTAs' products are not used
+            a.st->stop = 1;
+        }
         if (!a.rpart) rmx = *a.rmax_bits;
         if (a.rpart && !stop && rmx >= 0x7f800000u) {
             // a residual entry is not finite: the solve stops (the CTAs all see it)
@@ -91,21 +113,6 @@ __device__ __noinline__ void warp_prologue(const GemvTArgs& a, unsigned* s_st)
             const int guard = ++a.st->outer_guard;
             cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer,
                                     (!stop && guard < a.guard_limit) ? 1u : 0u);
-        }
-    }
-    // ||r||^2 of the iteration the iteration kernel just completed (it leaves the record to
-    // this kernel, so that none of its CTAs waits for the others at the end)
-    if (a.rpart && blockIdx.x == 0) {
-        const int st_iter = __shfl_sync(0xffffffffu, a.st->iter, 0);
-        const int logged = __shfl_sync(0xffffffffu, a.st->resid_logged, 0);
-        if (st_iter > logged) {
-            const double r2 = slot_sum_complete(a.rpart, kSlotResid, a.rgrid);
-            if (threadIdx.x == 0) {
-                a.st->resid2 = r2;
-                a.st->resid_logged = st_iter;
-                if (a.trace_resid2) a.trace_resid2[st_iter] = r2;
-                if (a.report) a.report->resid_norm2 = r2;
-            }
         }
     }
 }

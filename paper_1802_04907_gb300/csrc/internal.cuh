@@ -233,6 +233,10 @@ struct GatherArgs {
     unsigned long long h_outer, h_bt;   // conditional graph handles (0 when not in a graph)
     qiht_report* report;
     qiht_trace trace;
+    int coef_from_g;          // plain mode: coefficients g[cols[q]] instead of coef[q]
+    const float* zx;          // Mu: alpha Q1_G g_G (the first quantization's image; non-null: the
+                              //     cross-product step size of QIHT_MU_CROSS)
+    double tol;               // Resid: stop once ||r||^2 <= tol (0: off)
 };
 
 struct GemvTArgs {
@@ -255,6 +259,7 @@ struct GemvTArgs {
     int rgrid;                  // CTAs of the iteration kernel
     qiht_report* report;
     double* trace_resid2;       // optional
+    double tol;                 // fast path: stop once the recorded ||r||^2 <= tol (0: off)
 };
 
 struct TopArgs {
@@ -334,7 +339,7 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
                int32_t* uni, float* delta, const float* yhat, float* r, uint32_t* keys, unsigned long long* cand,
                double* part, const IterFastBufs& fb, int n, int m, int s, double k, double c, int max_bt,
                int flags, qiht_report* report, const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore,
-               void** argbuf);
+               void** argbuf, const uint32_t* q1_words = nullptr, int mu_mode = 0, double tol = 0.0);
 size_t iter_args_bytes();
 
 // Many independent problems in one persistent launch (batched.cu).

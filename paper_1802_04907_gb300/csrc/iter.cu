@@ -383,6 +383,9 @@ struct IterArgs {
     int flags;                  // QIHT_SOLVE_* (the test hook QIHT_SOLVE_TEST_TIMEOUT)
     qiht_report* report;
     qiht_trace trace;
+    const uint32_t* q1_words;   // first quantization Q1 (same layout as Q): QIHT_MU_CROSS step size
+    int mu_mode;                // QIHT_MU_FORWARD_SQ or QIHT_MU_CROSS
+    double tol;                 // general kernel: stop once ||r||^2 <= tol (0: off)
 };
 
 // Rows owned by this CTA: code words [w0, w1) of every column.
@@ -404,8 +407,9 @@ __device__ __forceinline__ RowBlock row_block(int ld)
 // z (for this CTA's rows) += sum over a list in shared memory of coef_j * code column j:
 // slice sl takes entries sl, sl + nsl, ... in order (four loads in flight per step).
 template <int BITS>
-__device__ __forceinline__ void rows_accum(const IterArgs& a, const RowBlock& rb, const int32_t* s_list,
-                                           const float* s_coef, int cn, int sl, int q, float (&z)[32 / BITS])
+__device__ __forceinline__ void rows_accum(const IterArgs& a, const uint32_t* words, const RowBlock& rb,
+                                           const int32_t* s_list, const float* s_coef, int cn, int sl, int q,
+                                           float (&z)[32 / BITS])
 {
     constexpr int G = 32 / BITS;
     constexpr int U = 8;                       // entries of a slice whose loads are in flight together
@@ -417,7 +421,7 @@ __device__ __forceinline__ void rows_accum(const IterArgs& a, const RowBlock& rb
         for (int u = 0; u < U; ++u) {
             const int e = jj + u * rb.nsl;
             const bool in = e < cn;
-            w[u] = in ? __ldg(a.Q.words + (size_t)s_list[e] * ld + q) : 0u;
+            w[u] = in ? __ldg(words + (size_t)s_list[e] * ld + q) : 0u;
             cf[u] = in ? s_coef[e] : 0.0f;         // past the end: adds exact zeros
         }
 #pragma unroll
@@ -463,8 +467,9 @@ __device__ __forceinline__ void rows_reduce(const RowBlock& rb, int sl, const fl
 template <int BITS>
 __device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_t* list, const float* coef,
                              int coef_mode, int count, int32_t* s_list, float* s_coef, float* red, float* zrow,
-                             double* coef_sq = nullptr)
+                             double* coef_sq = nullptr, const uint32_t* words = nullptr)
 {
+    if (!words) words = a.Q.words;
     constexpr int G = 32 / BITS;
     const int t = threadIdx.x;
     const int wl = t % rb.wpc, sl = t / rb.wpc;
@@ -484,7 +489,7 @@ __device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_
             if (coef_sq) *coef_sq += (double)cf * (double)cf;      // this thread's entries, in order
         }
         __syncthreads();
-        if (active) rows_accum<BITS>(a, rb, s_list, s_coef, cn, sl, q, z);
+        if (active) rows_accum<BITS>(a, words, rb, s_list, s_coef, cn, sl, q, z);
     }
     rows_reduce<BITS>(rb, sl, z, red, zrow);
 }
@@ -492,8 +497,9 @@ __device__ void rows_product(const IterArgs& a, const RowBlock& rb, const int32_
 // The same product for a list already in shared memory (no staging).
 template <int BITS>
 __device__ void rows_product_sm(const IterArgs& a, const RowBlock& rb, const int32_t* list_sm, const float* coef_sm,
-                                int count, float* red, float* zrow)
+                                int count, float* red, float* zrow, const uint32_t* words = nullptr)
 {
+    if (!words) words = a.Q.words;
     constexpr int G = 32 / BITS;
     const int t = threadIdx.x;
     const int wl = t % rb.wpc, sl = t / rb.wpc;
@@ -501,7 +507,7 @@ __device__ void rows_product_sm(const IterArgs& a, const RowBlock& rb, const int
     float z[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) z[k] = 0.0f;
-    if (sl < rb.nsl && q < rb.w1) rows_accum<BITS>(a, rb, list_sm, coef_sm, count, sl, q, z);
+    if (sl < rb.nsl && q < rb.w1) rows_accum<BITS>(a, words, rb, list_sm, coef_sm, count, sl, q, z);
     rows_reduce<BITS>(rb, sl, z, red, zrow);
 }
 
@@ -820,29 +826,49 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
     double* mypart = a.part + blockIdx.x;       // slot k of this CTA: mypart[k * kSlotCtas]
 
     // ---- Mu: z = Q2_G g_G, den = alpha^2 ||z||^2, num = ||g_G||^2 ----
+    // (QIHT_MU_CROSS: also z1 = Q1_G g_G and den = alpha^2 z1 . z when that is positive)
+    const bool cross = a.mu_mode == QIHT_MU_CROSS;
+    float z1v = 0.0f;
+    if (cross) {
+        rows_product<BITS>(a, rb, a.support, nullptr, 1, s, s_list, s_coef, red, zrow, nullptr, a.q1_words);
+        if (tid < rb.wpc * G) z1v = zrow[tid];
+    }
     double gsq = 0.0;
     rows_product<BITS>(a, rb, a.support, nullptr, 1, s, s_list, s_coef, red, zrow, &gsq);
     {
-        double acc = 0.0;
+        double acc = 0.0, cp = 0.0;
         if (tid < rb.wpc * G) {
             const int row = (rb.w0 + tid / G) * G + tid % G;
-            if (rb.w0 + tid / G < rb.w1 && row < m) acc = (double)zrow[tid] * (double)zrow[tid];
+            if (rb.w0 + tid / G < rb.w1 && row < m) {
+                acc = (double)zrow[tid] * (double)zrow[tid];
+                cp = (double)z1v * (double)zrow[tid];
+            }
         }
         acc = cta_sum(acc, shd);
         const double num = cta_sum(gsq, shd);                // ||g_G||^2 from the staged coefficients
-        if (tid == 0) { mypart[0 * kSlotCtas] = acc; mypart[1 * kSlotCtas] = num; }
+        if (cross) cp = cta_sum(cp, shd);
+        if (tid == 0) {
+            mypart[0 * kSlotCtas] = acc;
+            mypart[1 * kSlotCtas] = num;
+            if (cross) mypart[4 * kSlotCtas] = cp;
+        }
     }
     if (!grid_sync(a.gbar, target, st, a.report)) return;
     if (stamp) st->t_phase[1] = gtimer_ns();
     double mu;
     {
-        const double den = s_alpha * s_alpha * grid_partial_sum(a.part, 0, shd);
+        const double den_f = s_alpha * s_alpha * grid_partial_sum(a.part, 0, shd);
+        double den = den_f;
+        if (cross) {
+            const double den_c = s_alpha * s_alpha * grid_partial_sum(a.part, 4, shd);
+            if (den_c > 0.0) den = den_c;                      // else the forward square
+        }
         const double num = __ldcg(a.part + 1 * kSlotCtas);     // CTA 0's slot
         bool stop = false;
-        if (!isfinite(num) || !isfinite(den)) {
+        if (!isfinite(num) || !isfinite(den_f)) {
             stop = true;
             if (blockIdx.x == 0 && tid == 0) st->status = QIHT_ERR_NONFINITE;
-        } else if (num == 0.0 || den == 0.0) {
+        } else if (num == 0.0 || den_f == 0.0) {
             stop = true;                                       // converged: x stays
         }
         mu = stop ? 0.0 : num / den;
@@ -1044,6 +1070,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
         if (a.trace.bt) a.trace.bt[it] = bt;
         if (a.trace.resid2) a.trace.resid2[it] = resid2;
         if (it >= st->iters) st->stop = 1;
+        if (a.tol > 0.0 && resid2 <= a.tol) st->stop = 1;      // the residual reached tol
         if (a.report) {
             a.report->iters_run = st->iter;
             a.report->backtracks = st->backtracks_total;
@@ -1451,15 +1478,31 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
 
     // ---- Mu: z = Q2_G g_G, den = alpha^2 ||z||^2, num = ||g_G||^2 (CTA 0's warp 0) ----
     double num = 0.0;                            // CTA 0, warp 0
+    // QIHT_MU_CROSS: also z1 = Q1_G g_G; the CTA's part of z1 . z travels as its positive and
+    // negative parts (tagged slots carry non-negative values) in slots 1 and 3
+    const bool cross = a.mu_mode == QIHT_MU_CROSS;
     {
         if (cta0 && tid < 32) {
             for (int q = lane; q < s; q += 32) num += (double)sm.el_g[q] * (double)sm.el_g[q];
             num = warp_sum_d(num);
         }
+        float z1v = 0.0f;
+        if (cross) {
+            rows_product_sm<BITS>(a, rb, sm.el_idx, sm.el_g, s, sm.red, sm.zrow, a.q1_words);
+            if (row_ok) z1v = sm.zrow[tid];
+        }
         rows_product_sm<BITS>(a, rb, sm.el_idx, sm.el_g, s, sm.red, sm.zrow);
         double acc = 0.0;
         if (row_ok) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
         acc = cta_sum_n(acc, nrow_thr, shd);
+        if (cross) {
+            double cp = row_ok ? (double)z1v * (double)sm.zrow[tid] : 0.0;
+            cp = cta_sum_n(cp, nrow_thr, shd);
+            if (tid == 0) {
+                slot_put(mypart + 1 * kSlotCtas, cp > 0.0 ? cp : 0.0, tag);
+                slot_put(mypart + 3 * kSlotCtas, cp < 0.0 ? -cp : 0.0, tag);
+            }
+        }
         if (tid == 0) slot_put(mypart + 0 * kSlotCtas, acc, tag);
     }
     // CTA 0 gathers the partials and publishes mu (code 1: stop); the others wait for it
@@ -1469,15 +1512,24 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         unsigned code = 0;
         float muf = 0.0f;
         if (cta0) {
-            double densum = 0.0;
+            double densum = 0.0, cpos = 0.0, cneg = 0.0;
             if (!slot_gather(a.part, 0, -1, -1, tag, &densum, nullptr, nullptr, st, a.report, shd)) return;
+            if (cross) {
+                if (!slot_gather(a.part, 1, -1, -1, tag, &cpos, nullptr, nullptr, st, a.report, shd)) return;
+                if (!slot_gather(a.part, 3, -1, -1, tag, &cneg, nullptr, nullptr, st, a.report, shd)) return;
+            }
             if (tid == 0) {
                 tp[1] = gtimer_ns();
-                const double den = s_alpha * s_alpha * densum;
-                if (!isfinite(num) || !isfinite(den)) {
+                const double den_f = s_alpha * s_alpha * densum;
+                double den = den_f;
+                if (cross) {
+                    const double den_c = s_alpha * s_alpha * (cpos - cneg);
+                    if (den_c > 0.0) den = den_c;              // else the forward square
+                }
+                if (!isfinite(num) || !isfinite(den_f)) {
                     code = 1;
                     st->status = QIHT_ERR_NONFINITE;
-                } else if (num == 0.0 || den == 0.0) {
+                } else if (num == 0.0 || den_f == 0.0) {
                     code = 1;                                  // converged: x stays
                 } else {
                     mu = num / den;
@@ -1730,8 +1782,9 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
                int32_t* uni, float* delta, const float* yhat, float* r, uint32_t* keys, unsigned long long* cand,
                double* part, const IterFastBufs& fb, int n, int m, int s, double k, double c, int max_bt,
                int flags, qiht_report* report, const qiht_trace& trace, cudaKernelNodeParams* p, void* argstore,
-               void** argbuf)
+               void** argbuf, const uint32_t* q1_words, int mu_mode, double tol)
 {
+    static_assert(sizeof(IterArgs) <= kIterArgsMax, "iteration kernel arguments");
     IterArgs* a = reinterpret_cast<IterArgs*>(argstore);
     *a = IterArgs{};
     a->Q = Q2;
@@ -1767,6 +1820,9 @@ void iter_node(const Codes& Q2, State* st, const float* g, float* x, int32_t* su
     a->flags = flags;
     a->report = report;
     a->trace = trace;
+    a->q1_words = q1_words ? q1_words : Q2.words;
+    a->mu_mode = mu_mode;
+    a->tol = tol;
     argbuf[0] = a;
     const int G = 32 / Q2.bits;
     void* fn;

@@ -114,10 +114,11 @@ qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, co
         if ((e = check_codes(&y[k])) != QIHT_OK) return e;
         if (y[k].rows != m || y[k].cols != 1) return QIHT_ERR_ARG;
     }
-    qiht_params prm{2.0, 0.01, 32, 0};
+    qiht_params prm{2.0, 0.01, 32, 0, 0.0, QIHT_MU_FORWARD_SQ, 0};
     if (params) prm = *params;
     if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.flags != 0)
         return QIHT_ERR_ARG;
+    if (prm.tol != 0.0 || prm.mu_mode != QIHT_MU_FORWARD_SQ) return QIHT_ERR_ARG;   // the defaults only
     const MultiLayout L = multi_layout(m, n, s, nrhs);
     if (!workspace || workspace_bytes < L.total || !aligned256(workspace)) return QIHT_ERR_WORKSPACE;
     const int mk = mrhs_pad_rows(m), np = mrhs_pad_rhs(nrhs);

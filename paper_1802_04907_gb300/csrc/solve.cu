@@ -347,7 +347,7 @@ namespace {
 
 struct Plan {
     size_t off_state, off_yhat, off_r, off_g, off_sel, off_val, off_uni, off_delta, off_partial, off_rbp, off_chunk,
-        off_cand, off_keys, off_part, off_pos, off_xs, off_gsup, off_gcand, total;
+        off_cand, off_keys, off_part, off_pos, off_xs, off_gsup, off_gcand, off_z1, total;
 };
 
 Plan plan_solve(int m, int n, int s)
@@ -379,6 +379,7 @@ Plan plan_solve(int m, int n, int s)
     p.off_xs = o; o += align256((size_t)s * 4);
     p.off_gsup = o; o += align256((size_t)s * 4);
     p.off_gcand = o; o += align256((size_t)kTopCandCap * 8);
+    p.off_z1 = o; o += align256(rows_pad * 4);                   // alpha Q1_G g_G (QIHT_MU_CROSS)
     p.total = o;
     return p;
 }
@@ -480,7 +481,7 @@ struct SolveKernels {
     InitKernelArgs ia;
     GemvTArgs g0, gb;
     TopArgs t0, tt;
-    GatherArgs gmu, gom, gre;
+    GatherArgs gmu, gom, gre, gz1;
     void* a_tf[1];
     cudaKernelNodeParams p_tf;
     alignas(16) unsigned char iter_store[kIterArgsMax];
@@ -494,7 +495,9 @@ struct SolveKernels {
     void* a_mu[1];
     void* a_om[1];
     void* a_re[1];
-    cudaKernelNodeParams p_init, p_g0, p_gb, p_t0, p_tt, p_mu, p_om, p_re;
+    void* a_z1[1];
+    cudaKernelNodeParams p_init, p_g0, p_gb, p_t0, p_tt, p_mu, p_om, p_re, p_z1;
+    bool cross;                 // QIHT_MU_CROSS: p_z1 (z1 = alpha Q1_G g_G) runs before p_mu
     State* st;
 };
 
@@ -576,6 +579,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
         K.gb.rgrid = iter_grid();
         K.gb.report = report;
         K.gb.trace_resid2 = tr.resid2;
+        K.gb.tol = prm->tol;        // ... and the residual tolerance test
     }
     K.a_gb[0] = &K.gb;
     gemv_t_node(K.gb, nsm, &K.p_gb, K.a_gb);
@@ -617,7 +621,8 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     top_filter_node(K.tt, &K.p_tf, K.a_tf);
     iter_node(view(Q2), st, g, x, support, sel, val, uni, delta, yhat, r,
               reinterpret_cast<uint32_t*>(ws + pl.off_keys), cand, reinterpret_cast<double*>(ws + pl.off_part), fb, n, m, s,
-              prm->k, prm->c, prm->max_backtrack, prm->flags, report, tr, &K.p_it, K.iter_store, K.a_it);
+              prm->k, prm->c, prm->max_backtrack, prm->flags, report, tr, &K.p_it, K.iter_store, K.a_it, Q1->words,
+              prm->mu_mode, prm->tol);
 
     GatherArgs base{};
     base.Q = view(Q2);
@@ -641,9 +646,22 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     base.h_bt = h_bt;
     base.report = report;
     base.trace = tr;
+    K.cross = prm->mu_mode == QIHT_MU_CROSS;
+    float* z1 = reinterpret_cast<float*>(ws + pl.off_z1);
+    K.gz1 = base;                   // z1 = alpha Q1_G g_G (plain product with the first quantization)
+    K.gz1.Q = view(Q1);
+    K.gz1.mode = kGatherPlain;
+    K.gz1.cols = support;
+    K.gz1.coef_from_g = 1;
+    K.gz1.count = s;
+    K.gz1.z = z1;
+    K.gz1.counters = st->counters[0] + 96;
+    K.a_z1[0] = &K.gz1;
+    gather_node(K.gz1, &K.p_z1, K.a_z1);
     K.gmu = base;
     K.gmu.mode = kGatherMu;
     K.gmu.counters = st->counters[0];
+    K.gmu.zx = K.cross ? z1 : nullptr;
     K.a_mu[0] = &K.gmu;
     gather_node(K.gmu, &K.p_mu, K.a_mu);
     K.gom = base;
@@ -655,6 +673,7 @@ static void make_kernels(SolveKernels& K, const qiht_codes* Q1, const qiht_codes
     gather_node(K.gom, &K.p_om, K.a_om);
     K.gre = base;
     K.gre.mode = kGatherResid;
+    K.gre.tol = prm->tol;
     K.gre.counters = st->counters[0] + 64;
     K.a_re[0] = &K.gre;
     gather_node(K.gre, &K.p_re, K.a_re);
@@ -709,6 +728,7 @@ qiht_status run_eager(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_cod
         return QIHT_OK;
     }
     for (int t = 0; t < iters && !h.stop; ++t) {
+        if (K.cross) CK(launch_node(K.p_z1, cs));
         CK(launch_node(K.p_mu, cs));
         CK(launch_node(K.p_tf, cs));
         CK(launch_node(K.p_tt, cs));
@@ -796,8 +816,13 @@ qiht_status build_graph(const qiht_codes* Q1, const qiht_codes* Q2, const qiht_c
         return QIHT_OK;
     }
 
-    cudaGraphNode_t b_mu, b_tf, b_top, b_om, b_w, b_re, b_g;
-    TRY(add_kernel(body, &b_mu, nullptr, 0, K.p_mu));
+    cudaGraphNode_t b_mu, b_tf, b_top, b_om, b_w, b_re, b_g, b_z1;
+    if (K.cross) {
+        TRY(add_kernel(body, &b_z1, nullptr, 0, K.p_z1));
+        TRY(add_kernel(body, &b_mu, &b_z1, 1, K.p_mu));
+    } else {
+        TRY(add_kernel(body, &b_mu, nullptr, 0, K.p_mu));
+    }
     TRY(add_kernel(body, &b_tf, &b_mu, 1, K.p_tf));
     TRY(add_kernel(body, &b_top, &b_tf, 1, K.p_tt));
     TRY(add_kernel(body, &b_om, &b_top, 1, K.p_om));
@@ -836,10 +861,14 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
     if (s < 1 || s > m || s > n || iters < 0) return QIHT_ERR_ARG;
     if (m > kMaxRows || n > kMaxTopN) return QIHT_ERR_ARG;
     if (!x || !support || !report) return QIHT_ERR_ARG;
-    qiht_params prm{2.0, 0.01, 32, 0};
+    qiht_params prm{2.0, 0.01, 32, 0, 0.0, QIHT_MU_FORWARD_SQ, 0};
     if (params) prm = *params;
     if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 ||
         (prm.flags & ~(QIHT_SOLVE_EAGER | QIHT_SOLVE_TEST_TIMEOUT)) != 0)
+        return QIHT_ERR_ARG;
+    if (!(prm.tol >= 0.0 && std::isfinite(prm.tol)) || (prm.mu_mode != QIHT_MU_FORWARD_SQ && prm.mu_mode != QIHT_MU_CROSS))
+        return QIHT_ERR_ARG;
+    if (prm.mu_mode == QIHT_MU_CROSS && grid_levels(Q1->bits, Q1->levels) != grid_levels(Q2->bits, Q2->levels))
         return QIHT_ERR_ARG;
     if (!workspace || workspace_bytes < qiht_solve_workspace_size(m, n, s) || !aligned(workspace, 256))
         return QIHT_ERR_WORKSPACE;
@@ -861,6 +890,8 @@ qiht_status qiht_niht_solve(const qiht_codes* Q1, const qiht_codes* Q2, const qi
     key.v.push_back(dbits(prm.c));
     key.v.push_back((uint64_t)prm.max_backtrack);
     key.v.push_back((uint64_t)prm.flags);
+    key.v.push_back(dbits(prm.tol));
+    key.v.push_back((uint64_t)prm.mu_mode);
     key.v.push_back(reinterpret_cast<uint64_t>(x));
     key.v.push_back(reinterpret_cast<uint64_t>(support));
     key.v.push_back(reinterpret_cast<uint64_t>(report));
@@ -954,9 +985,11 @@ qiht_status qiht_niht_solve_fresh(const float* phi, int64_t ld_phi, const float*
     if (!phi || !y || !x || !support || !report || m < 1 || n < 1 || ld_phi < n) return QIHT_ERR_ARG;
     if (s < 1 || s > m || s > n || iters < 0 || m > kMaxRows || n > kMaxTopN) return QIHT_ERR_ARG;
     if (quant_flags & ~QIHT_ODD_LEVELS) return QIHT_ERR_ARG;
-    qiht_params prm{2.0, 0.01, 32, 0};
+    qiht_params prm{2.0, 0.01, 32, 0, 0.0, QIHT_MU_FORWARD_SQ, 0};
     if (params) prm = *params;
     if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.flags != 0)
+        return QIHT_ERR_ARG;
+    if (!(prm.tol >= 0.0 && std::isfinite(prm.tol)) || (prm.mu_mode != QIHT_MU_FORWARD_SQ && prm.mu_mode != QIHT_MU_CROSS))
         return QIHT_ERR_ARG;
     const FreshLayout L = fresh_layout(m, n, s, bits_phi, bits_y);
     if (!workspace || workspace_bytes < L.total || !aligned(workspace, 256)) return QIHT_ERR_WORKSPACE;
@@ -1021,6 +1054,7 @@ qiht_status qiht_niht_solve_fresh(const float* phi, int64_t ld_phi, const float*
             CK(launch_fresh_resid(view(&qy), z, yhat, r, m, &K.st->rmax_bits, cs));
             CK(launch_node(K.p_gb, cs));
         }
+        if (K.cross) CK(launch_node(K.p_z1, cs));
         CK(launch_node(K.p_mu, cs));
         CK(launch_node(K.p_tf, cs));
         CK(launch_node(K.p_tt, cs));
@@ -1100,10 +1134,11 @@ qiht_status qiht_niht_solve_batched(const qiht_problem* problems, int32_t nprob,
                                     qiht_stream_t stream)
 {
     if (!problems || nprob < 1 || iters < 0) return QIHT_ERR_ARG;
-    qiht_params prm{2.0, 0.01, 32, 0};
+    qiht_params prm{2.0, 0.01, 32, 0, 0.0, QIHT_MU_FORWARD_SQ, 0};
     if (params) prm = *params;
     if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.flags != 0)
         return QIHT_ERR_ARG;
+    if (prm.tol != 0.0 || prm.mu_mode != QIHT_MU_FORWARD_SQ) return QIHT_ERR_ARG;   // the defaults only
     const int bits = problems[0].Q1.bits;
     for (int i = 0; i < nprob; ++i) {
         const qiht_problem& P = problems[i];

@@ -93,7 +93,7 @@ def _check(rec: dict, ref, x_true, *, x, support, status, iters_run, resid_norm2
     if sup_trace is not None:
         for t in range(0, T + 1):
             assert np.array_equal(sup_trace[t], tr["support"][t]), f"{label}: support differs at iteration {t}"
-    if resid_trace is not None:
+    if resid_trace is not None and T >= 0:
         d = np.abs(resid_trace[: T + 1] - rr2[: T + 1])
         assert np.all(d <= RESID_RTOL * rr2[: T + 1] + atol), \
             f"{label}: residual differs at iteration {int(np.argmax(d / (rr2[: T + 1] + atol)))}"

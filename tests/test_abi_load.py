@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_host_only_entry_points(lib):
-    assert lib.qiht_abi_version() == 2
+    assert lib.qiht_abi_version() == 3
     assert q.status_string(q.OK) == "QIHT_OK"
     assert q.status_string(q.ERR_BACKTRACK_CAP) == "QIHT_ERR_BACKTRACK_CAP"
     # words per column: ceil(rows / (32/bits)) rounded up to a multiple of 4
@@ -77,6 +77,23 @@ def test_argument_errors_return_before_launch(lib):
                  P(16), None, None, 0, None) == q.ERR_WORKSPACE
     assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 4, 10, ctypes.byref(prm), P(16), P(16),
                  P(16), None, P(272), 1 << 30, None) == q.ERR_WORKSPACE      # not 256-byte aligned
+    # the step-size mode and the residual tolerance: unknown mode, negative or non-finite tol,
+    # the cross product across two grids
+    for bad_p in (q._Params(2.0, 0.01, 32, 0, 0.0, 2, 0), q._Params(2.0, 0.01, 32, 0, -1.0, 0, 0),
+                  q._Params(2.0, 0.01, 32, 0, float("nan"), 0, 0), q._Params(2.0, 0.01, 32, 0, float("inf"), 1, 0)):
+        assert solve(ctypes.byref(c), ctypes.byref(c), ctypes.byref(cy), 4, 10, ctypes.byref(bad_p), P(16), P(16),
+                     P(16), None, P(256), 1 << 30, None) == q.ERR_ARG
+    c_odd = q._Codes(16, 16, 64, 128, 8, q.ld_words(64, 8), q.odd_levels(8))
+    cross = q._Params(2.0, 0.01, 32, 0, 0.0, q.MU_CROSS, 0)
+    assert solve(ctypes.byref(c), ctypes.byref(c_odd), ctypes.byref(cy), 4, 10, ctypes.byref(cross), P(16), P(16),
+                 P(16), None, P(256), 1 << 30, None) == q.ERR_ARG
+    # the batched and many-right-hand-side solvers take the defaults only
+    pbt = q._Problem(c, c, cy, 4, 0, 16, 16, 16)
+    for nd in (q._Params(2.0, 0.01, 32, 0, 1e-3, 0, 0), cross):
+        assert lib.qiht_niht_solve_batched((q._Problem * 1)(pbt), 1, 5, ctypes.byref(nd), P(256), 1 << 20,
+                                           None) == q.ERR_ARG
+        assert lib.qiht_niht_solve_multi(ctypes.byref(c), ctypes.byref(c), (q._Codes * 1)(cy), 1, 4, 10,
+                                         ctypes.byref(nd), P(16), P(16), P(16), P(256), 1 << 30, None) == q.ERR_ARG
     # m above the GEMV^T limit
     big = q._Codes(16, 16, 20000, 128, 8, q.ld_words(20000, 8))
     bigy = q._Codes(16, 16, 20000, 1, 8, q.ld_words(20000, 8))
