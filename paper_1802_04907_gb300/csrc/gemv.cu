@@ -61,7 +61,9 @@ __device__ __forceinline__ int fixed_shift(unsigned rmax_bits)
 // |g| >= tau_g is appended to the candidate list (the largest |g| below tau_g is
 // kept per CTA and merged with one atomic).
 // ---------------------------------------------------------------------------
-constexpr int kWarpThreads = 512;           // 16 warps per CTA, two CTAs per SM
+constexpr int kWarpThreads = 512;           // 16 warps per CTA, two CTAs per SM (one at C = 4)
+constexpr int kColsPerWarp = 4;             // columns a warp streams together at 2 bits (measured: 30.8 vs
+                                            // 33.0 us at 8192 x 32768; at 4 bits 37.1 vs 34.9, so there C = 1)
 
 // Warp 0 of a GEMV^T CTA: stop flag, max |r| (fast path: from the iteration kernel's
 // residual partials, whose non-finite maximum stops the solve), candidate threshold, the
@@ -117,8 +119,12 @@ __device__ __noinline__ void warp_prologue(const GemvTArgs& a, unsigned* s_st)
     }
 }
 
-template <int BITS, int NPL>
-__global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
+// C = 1: a warp streams one column, NPL 16-byte pieces per lane at once (8 and 4 bits).
+// C = 4: a warp streams four adjacent columns together, one piece of each per lane, so that
+// every load of the residual's planes from shared memory serves four columns (2 bits, where
+// the per-code work, not HBM, bounds the pass).
+template <int BITS, int NPL, int C>
+__global__ void __launch_bounds__(kWarpThreads, C == 1 ? 2 : 1) k_gemv_t_warp(GemvTArgs a)
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;
@@ -138,27 +144,32 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
     // overlaps the staging.
     const int W = gridDim.x * (blockDim.x >> 5);
     const int nb = (P + 32 * NPL - 1) / (32 * NPL);     // batches per column
-    int j = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int ngc = (n + C - 1) / C;                    // groups of C adjacent columns
+    int j = blockIdx.x * (blockDim.x >> 5) + warp;      // the warp's current column group
     int pb = 0;
     // the code stream is read once per call: mark it first to leave L2, so that the small
     // working set of the rest of the iteration (support columns of Q2, g, x, r) stays there
     uint64_t stream_policy;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_policy));
-    auto load_batch = [&](uint4 (&cv)[NPL], int jj, int bb) {
-        const uint4* col = reinterpret_cast<const uint4*>(a.Q.words + (size_t)jj * ld);
+    auto load_batch = [&](uint4 (&cv)[C][NPL], int jg, int bb) {
 #pragma unroll
-        for (int u = 0; u < NPL; ++u) {
-            const int piece = bb * 32 * NPL + lane + 32 * u;
-            if (piece < P)
-                asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                             : "=r"(cv[u].x), "=r"(cv[u].y), "=r"(cv[u].z), "=r"(cv[u].w)
-                             : "l"(col + piece), "l"(stream_policy));
-            else
-                cv[u] = make_uint4(0u, 0u, 0u, 0u);
+        for (int c = 0; c < C; ++c) {
+            const int jj = jg * C + c;
+            const uint4* col = reinterpret_cast<const uint4*>(a.Q.words + (size_t)jj * ld);
+#pragma unroll
+            for (int u = 0; u < NPL; ++u) {
+                const int piece = bb * 32 * NPL + lane + 32 * u;
+                if (piece < P && jj < n)
+                    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                                 : "=r"(cv[c][u].x), "=r"(cv[c][u].y), "=r"(cv[c][u].z), "=r"(cv[c][u].w)
+                                 : "l"(col + piece), "l"(stream_policy));
+                else
+                    cv[c][u] = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
     };
-    uint4 cA[NPL], cB[NPL];
-    if (j < n) load_batch(cA, j, pb);
+    uint4 cA[C][NPL], cB[C][NPL];
+    if (j < ngc) load_batch(cA, j, pb);
 
     // everything above reads only the codes; r, max |r| and the solver state come from
     // the previous kernel. The state words are read by one thread per CTA and shared (all
@@ -240,16 +251,17 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
     const uint4* L1 = L0 + (size_t)E * P;
     const uint4* L2 = L0 + (size_t)2 * E * P;
 
-    uint32_t s0[E], s1[E];
-    int32_t s2[E];
+    uint32_t s0[C][E], s1[C][E];
+    int32_t s2[C][E];
 #pragma unroll
-    for (int k = 0; k < E; ++k) { s0[k] = 0; s1[k] = 0; s2[k] = 0; }
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int k = 0; k < E; ++k) { s0[c][k] = 0; s1[c][k] = 0; s2[c][k] = 0; }
 
-    auto use_batch = [&](const uint4 (&cv)[NPL], int bb) {
+    auto use_batch = [&](const uint4 (&cv)[C][NPL], int bb) {
 #pragma unroll
         for (int u = 0; u < NPL; ++u) {
             const int piece = min(bb * 32 * NPL + lane + 32 * u, P - 1);   // past the end: zero codes
-            const uint32_t wv[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
 #pragma unroll
             for (int q = 0; q < E; ++q) {
                 const uint4 A0 = L0[(size_t)q * P + piece];
@@ -259,29 +271,36 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
                 const uint32_t y1[4] = {A1.x, A1.y, A1.z, A1.w};
                 const uint32_t y2[4] = {A2.x, A2.y, A2.z, A2.w};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    // limb word lw = q*4 + t of the piece = word w = lw / E, position k = lw % E
-                    const int lw = q * 4 + t, w = lw / E, k = lw - w * E;
-                    const uint32_t x = wv[w] & (MASK << (BITS * k));
-                    s0[k] = dp4a_uu(x, y0[t], s0[k]);
-                    s1[k] = dp4a_uu(x, y1[t], s1[k]);
-                    s2[k] = dp4a_us(x, y2[t], s2[k]);
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t wv[4] = {cv[c][u].x, cv[c][u].y, cv[c][u].z, cv[c][u].w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        // limb word lw = q*4 + t of the piece = word w = lw / E, position k = lw % E
+                        const int lw = q * 4 + t, w = lw / E, k = lw - w * E;
+                        const uint32_t x = wv[w] & (MASK << (BITS * k));
+                        s0[c][k] = dp4a_uu(x, y0[t], s0[c][k]);
+                        s1[c][k] = dp4a_uu(x, y1[t], s1[c][k]);
+                        s2[c][k] = dp4a_us(x, y2[t], s2[c][k]);
+                    }
                 }
             }
         }
     };
-    auto finish_column = [&](int jj) {
+    auto finish_column = [&](int jg) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
         long long S = 0;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             // position k sums carry the factor 2^(b k): exact, so shift it out after the warp sum
-            const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[k]);
-            const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[k]);
-            const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[k]);
+            const long long t0 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s0[c][k]);
+            const long long t1 = (long long)(uint32_t)__reduce_add_sync(0xffffffffu, s1[c][k]);
+            const long long t2 = (long long)__reduce_add_sync(0xffffffffu, s2[c][k]);
             S += (t0 + (t1 << 8) + (t2 << 16)) >> (BITS * k);
-            s0[k] = 0; s1[k] = 0; s2[k] = 0;
+            s0[c][k] = 0; s1[c][k] = 0; s2[c][k] = 0;
         }
-        if (lane == 0) {
+        const int jj = jg * C + c;
+        if (lane == c && jj < n) {                  // lane c finishes column c of the group
             const long long T = 2 * S - R;
             const float gv = (float)((double)T * outscale_sh);
             a.g[jj] = gv;
@@ -298,34 +317,35 @@ __global__ void __launch_bounds__(kWarpThreads, 2) k_gemv_t_warp(GemvTArgs a)
                 }
             }
         }
+        }
     };
-    // support position of column jj (lane 0 only; read early, used by finish_column)
-    auto fetch_pos = [&](int jj) {
-        if (a.pos && lane == 0) pos_cur = __ldg(a.pos + jj);
+    // support position of column c of group jg (lane c; read early, used by finish_column)
+    auto fetch_pos = [&](int jg) {
+        if (a.pos && lane < C) pos_cur = jg * C + lane < n ? __ldg(a.pos + jg * C + lane) : -1;
     };
     auto advance = [&](int& jj, int& bb) {
         if (++bb == nb) { bb = 0; jj += W; }
     };
 
-    while (j < n) {
+    while (j < ngc) {
         int jB = j, pB = pb;
         advance(jB, pB);
-        if (jB < n) load_batch(cB, jB, pB);
+        if (jB < ngc) load_batch(cB, jB, pB);
         if (pb == 0) fetch_pos(j);
         use_batch(cA, pb);
         if (pb == nb - 1) finish_column(j);
         j = jB; pb = pB;
-        if (j >= n) break;
+        if (j >= ngc) break;
         int jA = j, pA = pb;
         advance(jA, pA);
-        if (jA < n) load_batch(cA, jA, pA);
+        if (jA < ngc) load_batch(cA, jA, pA);
         if (pb == 0) fetch_pos(j);
         use_batch(cB, pb);
         if (pb == nb - 1) finish_column(j);
         j = jA; pb = pA;
     }
     if (tau_g) {
-        if (lane == 0 && bmax) atomicMax(&bmax_cta, bmax);
+        if (lane < C && bmax) atomicMax(&bmax_cta, bmax);
         __syncthreads();
         if (threadIdx.x == 0 && bmax_cta) atomicMax(&a.st->bmax_g, bmax_cta);
     }
@@ -345,15 +365,16 @@ static WarpPlan plan_warp(const Codes& Q, int nsm)
     const size_t P = (size_t)Q.ld / 4;
     p.smem = 3 * (size_t)E * P * 16;
     if (p.smem > 48 * 1024 * 2) return p;          // keep at least two CTAs per SM
-    if (Q.bits == 8) p.fn = (void*)k_gemv_t_warp<8, 4>;
-    else if (Q.bits == 4) p.fn = (void*)k_gemv_t_warp<4, 2>;
-    else p.fn = (void*)k_gemv_t_warp<2, 1>;
+    if (Q.bits == 8) p.fn = (void*)k_gemv_t_warp<8, 4, 1>;
+    else if (Q.bits == 4) p.fn = (void*)k_gemv_t_warp<4, 2, 1>;
+    else p.fn = (void*)k_gemv_t_warp<2, 1, kColsPerWarp>;
     cudaFuncSetAttribute(p.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p.fn, kWarpThreads, p.smem);
     if (occ < 1) return p;
     long long grid = (long long)nsm * occ;
-    const long long want = ((long long)Q.cols + kWarpThreads / 32 - 1) / (kWarpThreads / 32);
+    const int cpw = Q.bits == 2 ? kColsPerWarp : 1;
+    const long long want = (((long long)Q.cols + cpw - 1) / cpw + kWarpThreads / 32 - 1) / (kWarpThreads / 32);
     if (grid > want) grid = want;
     p.grid = (unsigned)(grid < 1 ? 1 : grid);
     p.ok = true;
