@@ -1115,6 +1115,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a)
 // finish writes G, x_G and the scalars.
 // ---------------------------------------------------------------------------
 constexpr int kFastMaxS = 2 * 512;       // largest s of the fast path (lists held in shared memory)
+constexpr int kResidDirect = 16;         // the residual is formed directly every 16 iterations
 constexpr int kTieMax = 64;              // ties at the s-th key ranked by index in shared memory
 
 struct FastSm {
@@ -1245,6 +1246,31 @@ __device__ bool select_fast(const IterArgs& a, const FastSm& sm, int cnt, float 
     }
     if (tid == 0) tie_n = 0;
     if (__syncthreads_or(bad)) return false;                   // NaN: the full select reports it
+    {
+        // the support stays when every key of G exceeds every other key (the candidates' and
+        // outside_max, the largest key of the entries the gradient kernel rejected): then H_s
+        // keeps G whatever the order inside it, and no ranking is needed
+        unsigned inv_min = 0, cmax = 0;
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const uint32_t k = sm.key[e];
+            if (e < s) inv_min = max(inv_min, ~k);
+            else cmax = max(cmax, k);
+        }
+        const uint32_t kmin = ~cta_max(inv_min, sh_u);
+        const uint32_t rest = max(cta_max(cmax, sh_u), outside_max);
+        if (kmin > rest) {
+            for (int q = tid; q < s; q += blockDim.x) {
+                sm.u_idx[q] = sm.el_idx[q];
+                sm.u_val[q] = fmaf(muf, sm.el_g[q], sm.el_x[q]);
+            }
+            out.changed = 0;
+            out.uc = s;
+            out.kth0 = __uint_as_float(kmin);
+            out.kth1 = __uint_as_float(rest);
+            __syncthreads();
+            return true;
+        }
+    }
     int need = 0, depth = 3;
     const uint32_t P = radix_select8(sm.key, cnt, s, sm.hist, sh_i, &need, &depth);
     uint32_t T;
@@ -1417,6 +1443,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         s_state[4] = __ldcg(&st->tau_g_bits);
         s_state[5] = __ldcg(&st->gcand_count);
         s_state[6] = __ldcg(&st->bmax_g);
+        s_state[7] = (unsigned)__ldcg(&st->iters);
     }
     unsigned long long tp[5] = {0, 0, 0, 0, 0};  // CTA 0, thread 0: phase clock
     if (cta0 && tid == 0) tp[0] = gtimer_ns();
@@ -1445,6 +1472,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     }
     unsigned long long cspec = 0;
     if (tid < a.gcap) cspec = __ldcg(a.gcand + tid);
+    const float rrow = row_ok ? __ldcg(a.r + row) : 0.0f;       // this thread's row of r
     __syncthreads();
     if (s_state[0]) return;                      // uniform: read before any exchange
     const int iter0 = (int)s_state[1];
@@ -1481,6 +1509,9 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     // QIHT_MU_CROSS: also z1 = Q1_G g_G; the CTA's part of z1 . z travels as its positive and
     // negative parts (tagged slots carry non-negative values) in slots 1 and 3
     const bool cross = a.mu_mode == QIHT_MU_CROSS;
+    // this thread's row of Q2_G g_G and of the last backtracking product Q2 (x' - x): the
+    // residual update r <- r - alpha Q2 (x' - x) uses one of them
+    float zmu = 0.0f, zom = 0.0f;
     {
         if (cta0 && tid < 32) {
             for (int q = lane; q < s; q += 32) num += (double)sm.el_g[q] * (double)sm.el_g[q];
@@ -1493,7 +1524,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         }
         rows_product_sm<BITS>(a, rb, sm.el_idx, sm.el_g, s, sm.red, sm.zrow);
         double acc = 0.0;
-        if (row_ok) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
+        if (row_ok) {
+            zmu = sm.zrow[tid];
+            acc = (double)zmu * (double)zmu;
+        }
         acc = cta_sum_n(acc, nrow_thr, shd);
         if (cross) {
             double cp = row_ok ? (double)z1v * (double)sm.zrow[tid] : 0.0;
@@ -1626,7 +1660,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
             }
             rows_product_sm<BITS>(a, rb, sm.u_idx, sm.u_delta, sr.uc, sm.red, sm.zrow);
             double acc = 0.0;
-            if (row_ok) acc = (double)sm.zrow[tid] * (double)sm.zrow[tid];
+            if (row_ok) {
+                zom = sm.zrow[tid];
+                acc = (double)zom * (double)zom;
+            }
             acc = cta_sum_n(acc, nrow_thr, shd);
             if (tid == 0) slot_put(mypart + 2 * kSlotCtas, acc, otag);
         }
@@ -1727,13 +1764,19 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
         }
     }
 
-    // ---- Resid: r = Q(y) - Q2_G' x' for this CTA's rows ----
-    rows_product_sm<BITS>(a, rb, sm.u_idx, sm.u_val, s, sm.red, sm.zrow);
+    // ---- Resid for this CTA's rows: directly, r = Q(y) - alpha Q2_G' x', in the first and
+    // the last iteration, every kResidDirect-th, and when a residual tolerance is set;
+    // otherwise r <- r - alpha Q2 (x' - x) with the product this iteration already formed:
+    // mu Q2_G g_G when the support stayed, the accepted backtracking test's Q2 (x' - x) when
+    // it moved (the same vector up to FP32 rounding; the direct form resets the drift) ----
+    const bool direct = first || (it % kResidDirect) == 0 || it >= (int)s_state[7] || a.tol > 0.0;
+    if (direct) rows_product_sm<BITS>(a, rb, sm.u_idx, sm.u_val, s, sm.red, sm.zrow);
     {
         double acc = 0.0;
         unsigned mx = 0;
         if (row_ok) {
-            const float ri = fmaf(-alpha_f, sm.zrow[tid], yrow);
+            const float ri = direct ? fmaf(-alpha_f, sm.zrow[tid], yrow)
+                                    : fmaf(-alpha_f, sr.changed ? zom : s_muf * zmu, rrow);
             a.r[row] = ri;
             acc = (double)ri * (double)ri;
             mx = __float_as_uint(ri) & 0x7fffffffu;
