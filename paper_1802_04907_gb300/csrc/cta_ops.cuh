@@ -220,14 +220,20 @@ __device__ __forceinline__ float x_at(const MSm& sm, int s, int j)
 }
 
 // keys |fmaf(mu, g_j, x_j)| for all j (x is 0 off the support); returns 1 if one is not finite
-__device__ int mkeys(int n, int s, float muf, const float* g, const MSm& sm)
+// Keys |fmaf(mu, g_j, x_j)| of all n entries (x is 0 off the support G). With sh != nullptr
+// also the smallest key on G (*kmin) and the largest key off G (*rest): when kmin > rest,
+// H_s keeps G whatever the order inside it. Returns nonzero if a key is not finite.
+__device__ int mkeys(int n, int s, float muf, const float* g, const MSm& sm, int* sh = nullptr,
+                     uint32_t* kmin = nullptr, uint32_t* rest = nullptr)
 {
     const int tid = threadIdx.x;
     int bad = 0;
+    unsigned cmax = 0, inv_min = 0;
     for (int j = tid; j < n; j += kST) {
         const uint32_t k = __float_as_uint(fmaf(muf, __ldg(g + j), 0.0f)) & 0x7fffffffu;
         sm.keys[j] = k;
         bad |= k > 0x7f800000u;
+        if (sh && !((sm.gbit[j >> 5] >> (j & 31)) & 1u)) cmax = max(cmax, k);
     }
     __syncthreads();
     for (int q = tid; q < s; q += kST) {
@@ -235,6 +241,11 @@ __device__ int mkeys(int n, int s, float muf, const float* g, const MSm& sm)
         const uint32_t k = __float_as_uint(fmaf(muf, __ldg(g + j), sm.xs[q])) & 0x7fffffffu;
         sm.keys[j] = k;
         bad |= k > 0x7f800000u;
+        inv_min = max(inv_min, ~k);
+    }
+    if (sh) {
+        *rest = smax(cmax, sh);
+        *kmin = ~smax(inv_min, sh);
     }
     return __syncthreads_or(bad);
 }

@@ -371,7 +371,7 @@ struct MrhsState {
     double resid2;            // ||Q(y) - Q2 x||^2 of the current iterate
     int stop;                 // 0 running, 1 converged, 2 stopped by an error (status)
     int status;
-    int iters_run, backtracks, changes, pad;
+    int iters_run, backtracks, changes, full_selects;   // full_selects: selections that ranked all n keys
 };
 struct MrhsStepArgs {
     Codes Q2;

@@ -135,10 +135,23 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
         }
         return;
     }
-    int bt = 0, changed = 0;
+    int bt = 0, changed = 0, ranked = 0;
     for (;;) {
-        if (mkeys(n, s, sh.muf, g, sm)) { changed = -1; break; }
+        uint32_t kmin = 0, rest = 0;
+        if (mkeys(n, s, sh.muf, g, sm, sh.i, &kmin, &rest)) { changed = -1; break; }
+        if (kmin > rest) {
+            // every key of G exceeds every other key: G' = G without ranking
+            for (int q = tid; q < s; q += kST) {
+                sm.sel[q] = sm.sup[q];
+                sm.val[q] = fmaf(sh.muf, __ldg(g + sm.sup[q]), sm.xs[q]);
+            }
+            uc = s;
+            changed = 0;
+            __syncthreads();
+            break;
+        }
         changed = mselect(n, s, sh.muf, g, sm, sh, &uc, true, reinterpret_cast<int*>(sm.z), a.mk);
+        ++ranked;
         if (!changed) break;
         // backtracking test on G' u G
         double dn = 0.0;
@@ -219,6 +232,7 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
         st->iters_run += 1;
         st->backtracks += bt;
         st->changes += changed;
+        st->full_selects += ranked;
         st->mu = sh.mu;
         st->resid2 = rr;
         if (!isfinite(rr)) { st->status = QIHT_ERR_NONFINITE; st->stop = 2; }
@@ -275,6 +289,7 @@ __global__ void __launch_bounds__(kST) k_mrhs_init(MrhsStepArgs a)
         st->iters_run = 0;
         st->backtracks = 0;
         st->changes = 0;
+        st->full_selects = 1;             // the initial support
     }
     split_residual(r, m, a.mk, hi, lo, a.sc + k, sh.alpha1, sh);
 }
@@ -297,7 +312,7 @@ __global__ void __launch_bounds__(256) k_mrhs_final(MrhsStepArgs a, float* X, qi
         rp->status = *gemm_status ? *gemm_status : st->status;
         rp->resid_norm2 = st->resid2;
         rp->mu = st->mu;
-        rp->full_selects = st->iters_run + 1;
+        rp->full_selects = st->full_selects;
         rp->reserved = 0;
         for (int i = 0; i < 8; ++i) rp->phase_us[i] = 0.0f;
     }
