@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--nprob", type=int, default=512)
     ap.add_argument("--nrhs", type=int, default=1024)
     ap.add_argument("--plain-sample", type=int, default=16)
+    ap.add_argument("--fp8", action="store_true",
+                    help="multi: the FP8 (e4m3) gradient product, residual as three e4m3 terms (2- and 4-bit codes)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the solver's kernels one by one instead of one graph (for kernel profilers, "
                          "which do not see the kernels of graphs with conditional nodes)")
@@ -678,6 +680,7 @@ def run_multi(args, emit=True):
 
     dev = torch.device("cuda", torch.cuda.current_device())
     m, n, s, bits, iters, nrhs = args.m, args.n, args.s, args.bits, args.iters, args.nrhs
+    fp8 = bool(getattr(args, "fp8", False))
     gen = torch.Generator(device=dev)
     gen.manual_seed(4242)
     phi = torch.randn(m, n, generator=gen, device=dev, dtype=torch.float32) / float(np.sqrt(m))
@@ -696,7 +699,7 @@ def run_multi(args, emit=True):
     out = (torch.empty(nrhs, n, device=dev), torch.empty(nrhs, s, dtype=torch.int32, device=dev),
            torch.zeros(nrhs, q.REPORT_BYTES, dtype=torch.uint8, device=dev))
     for _ in range(max(1, args.warmup)):
-        res = q.niht_solve_multi(q1, q2, ys, s, iters, workspace=ws, out=out)
+        res = q.niht_solve_multi(q1, q2, ys, s, iters, workspace=ws, out=out, fp8=fp8)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     uuid = None
@@ -709,7 +712,7 @@ def run_multi(args, emit=True):
     time.sleep(0.3)
     ev0.record()
     for _ in range(args.steps):
-        res = q.niht_solve_multi(q1, q2, ys, s, iters, workspace=ws, out=out)
+        res = q.niht_solve_multi(q1, q2, ys, s, iters, workspace=ws, out=out, fp8=fp8)
     ev1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -740,12 +743,12 @@ def run_multi(args, emit=True):
     G = torch.empty(nrhs, n, device=dev)
     wsg = q._ws(q.lib().qiht_gemv_t_multi_workspace_size(m, nrhs), dev)
     for _ in range(3):
-        q.gemv_t_multi(q1, R, G, workspace=wsg)
+        q.gemv_t_multi(q1, R, G, workspace=wsg, fp8=fp8)
     torch.cuda.synchronize()
     reps_g = 10
     ev0.record()
     for _ in range(reps_g):
-        q.gemv_t_multi(q1, R, G, workspace=wsg)
+        q.gemv_t_multi(q1, R, G, workspace=wsg, fp8=fp8)
     ev1.record()
     torch.cuda.synchronize()
     gemm_us = ev0.elapsed_time(ev1) / reps_g * 1e3
@@ -753,11 +756,12 @@ def run_multi(args, emit=True):
     tflops = flops / (gemm_us * 1e-6) / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak = float(peaks.get("bf16_tflops", 1900.0))
-    launches = 3 + 2 * iters                          # init, GEMMs, step kernels, final
+    peak = float(peaks.get("bf16_tflops", 1900.0)) * (2.0 if fp8 else 1.0)
+    launches = 3 + 2 * iters                          # init, GEMMs, step kernels, final (the step splits the residual)
     line = {"metric": "multi-RHS solves/s", "value": nrhs / (ms / 1e3), "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": f"u{bits}", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": f"u{bits}" + ("+e4m3" if fp8 else ""),
+            "data": "synthetic",
             "config": {"workload": f"{nrhs} right-hand sides sharing Gaussian Phi {m}x{n} N(0,1/m), s={s} "
                                    f"N(0,1) nonzeros each, 30 dB, {bits}-bit Phi and y, {iters} iterations",
                        "nrhs": nrhs, "m": m, "n": n, "s": s, "bits": bits, "iters_per_step": iters,
@@ -772,13 +776,21 @@ def run_multi(args, emit=True):
                             "plain_median_rel_err_on_sample": float(np.median(err_p))},
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                          "frac": tflops / peak, "traffic": None,
-                         "kernel": "k_mrhs_gemm (G = Q1^T R, f16 tcgen05, hi + lo parts)",
+                         "kernel": ("k_mrhs_gemm (G = Q1^T R, e4m3 tcgen05 kind::f8f6f4, three residual terms)"
+                                    if fp8 else "k_mrhs_gemm (G = Q1^T R, f16 tcgen05, hi + lo parts)"),
                          "avg_launch_us": gemm_us, "algorithmic_flops_per_launch": flops,
-                         "note": "2 m n nrhs flops (R counted once; the hi and lo parts double the MMA work); "
-                                 "timed with the residual split; peak: measured dense bf16 burst (f16 rate equal)"},
+                         "note": ("2 m n nrhs flops (R counted once; the three e4m3 terms triple the MMA work); "
+                                  "timed with the residual split; peak: measured dense bf16 burst x 2 (the nominal "
+                                  "fp8/bf16 ratio)") if fp8 else
+                                 ("2 m n nrhs flops (R counted once; the hi and lo parts double the MMA work); "
+                                  "timed with the residual split; peak: measured dense bf16 burst (f16 rate equal)")},
             "gpu_launches": launches * args.steps,
             "clocks": clk,
-            "statuses": {str(k): sum(1 for r in reps if r.status == k) for k in sorted({r.status for r in reps})}}
+            "statuses": {str(k): sum(1 for r in reps if r.status == k) for k in sorted({r.status for r in reps})},
+            "per_rhs_mean": {"iterations": float(np.mean([r.iters_run for r in reps])),
+                             "backtracks": float(np.mean([r.backtracks for r in reps])),
+                             "support_changes": float(np.mean([r.support_changes for r in reps])),
+                             "ranked_selections": float(np.mean([r.full_selects for r in reps]))}}
     if emit:
         print(json.dumps(line))
     return line

@@ -194,6 +194,19 @@ qiht_status qiht_gemv_t_multi(const qiht_codes* Q, const float* R, int64_t ldr, 
                               int64_t ldg, int32_t* status, void* workspace, size_t workspace_bytes,
                               qiht_stream_t stream);
 
+/* The same product with FP8 operands, for codes of 2 or 4 bits (else QIHT_ERR_BITS): the centred
+ * codes 2c - (L-1) are exact in e4m3 (|2c - (L-1)| <= 15), the residual is scaled by a power of
+ * two (max |r| 2^-e in [2^7, 2^8)) and split into three e4m3 terms, r' ~ t1 + t2 + t3 with
+ * |r' - t1 - t2 - t3| <= 2^-12 |r'| + 2^-10, and tcgen05.mma kind::f8f6f4 sums the products in
+ * FP32 (K = 32 rows per MMA instead of 16, three terms instead of two parts: 3/4 of the MMA work
+ * of the f16 split, at about 12 significant bits instead of 22). This is the paper's observation
+ * that codes of b <= 4 bits are exact in an 8-bit floating-point format (Section III-A, the
+ * quantizer's levels), carried to the tensor cores. Arguments, workspace and errors as for
+ * qiht_gemv_t_multi. */
+qiht_status qiht_gemv_t_multi_fp8(const qiht_codes* Q, const float* R, int64_t ldr, int32_t nrhs, float* G,
+                                  int64_t ldg, int32_t* status, void* workspace, size_t workspace_bytes,
+                                  qiht_stream_t stream);
+
 /* Hard threshold H_s (Eq. NIHT): the s entries of a [device, n floats] of
  * largest magnitude, ties broken by the lower index; exactly s are kept.
  * idx [device, s int32] receives their indices in ascending order, val
@@ -217,6 +230,10 @@ qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float
                                      bounded wait on it runs out (about 0.2 s) and the solve stops
                                      with QIHT_ERR_TIMEOUT in the report; the CUDA context stays
                                      usable. Honoured by the kernel used for s <= 1024. */
+
+#define QIHT_SOLVE_FP8 4   /* qiht_niht_solve_multi only, codes of 2 or 4 bits: the gradient products run
+                              as qiht_gemv_t_multi_fp8 (e4m3 operands, about 12 significant bits of the
+                              residual) instead of the two-part f16 split (about 22 bits) */
 
 /* Denominator of the step size mu = ||g_G||^2 / den on the current support G (Eq. for mu). */
 #define QIHT_MU_FORWARD_SQ 0  /* den = ||Q2_G g_G||^2 (positive; the default) */
@@ -371,8 +388,8 @@ size_t qiht_solve_multi_workspace_size(int32_t m, int32_t n, int32_t s, int32_t 
  * Arithmetic: that of qiht_niht_solve except the gradient (f16 products of the exact
  * codes with a two-part f16 split of the residual, FP32 sums; see qiht_gemv_t_multi).
  * Requires m <= QIHT_MULTI_MAX_ROWS, n <= QIHT_MULTI_MAX_COLS, 1 <= s <= min(m, n,
- * QIHT_MULTI_MAX_S); params->flags and params->tol must be 0, params->mu_mode
- * QIHT_MU_FORWARD_SQ. Errors as for qiht_niht_solve; numeric
+ * QIHT_MULTI_MAX_S); params->flags 0 or QIHT_SOLVE_FP8 (2- and 4-bit codes: the FP8 gradient
+ * product), params->tol 0 and params->mu_mode QIHT_MU_FORWARD_SQ. Errors as for qiht_niht_solve; numeric
  * failures of a right-hand side are in its report, a device-side timeout of the
  * gradient product (QIHT_ERR_TIMEOUT) in every report. Asynchronous on `stream` after
  * the descriptor copy. */

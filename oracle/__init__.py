@@ -60,7 +60,8 @@ _lib = None
 
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_double), ("c", ctypes.c_double), ("max_backtrack", ctypes.c_int32),
-                ("mu_mode", ctypes.c_int32), ("tol", ctypes.c_double)]
+                ("mu_mode", ctypes.c_int32), ("tol", ctypes.c_double), ("grad_e4m3", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class _Trace(ctypes.Structure):
@@ -124,6 +125,10 @@ def lib():
         L.qo_step_size.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32, P, P,
                                    P, P]
         L.qo_step_size.restype = None
+        L.qo_e4m3.argtypes = [ctypes.c_double]
+        L.qo_e4m3.restype = ctypes.c_double
+        L.qo_e4m3_terms.argtypes = [P, ctypes.c_int64, ctypes.c_int, P]
+        L.qo_e4m3_terms.restype = None
         L.qo_set_threads.argtypes = [ctypes.c_int]
         L.qo_set_threads.restype = None
         L.qo_get_threads.argtypes = []
@@ -243,6 +248,22 @@ def step_size(A1: np.ndarray, A2: np.ndarray, support: np.ndarray, g: np.ndarray
     return {"num": out[0], "den": out[1], "cross": out[2], "fallback": bool(out[3])}
 
 
+def e4m3(v) -> np.ndarray:
+    """Nearest E4M3 values (OCP 8-bit floating point: bias 7, 3 fraction bits, subnormals,
+    largest finite 448), ties to even, saturating at 448; elementwise."""
+    v = np.asarray(v, dtype=np.float64)
+    return np.vectorize(lambda t: lib().qo_e4m3(float(t)), otypes=[np.float64])(v) if v.size else v.copy()
+
+
+def e4m3_terms(r: np.ndarray, terms: int = 3) -> np.ndarray:
+    """r held as 2^e (t_1 + ... + t_terms): max |r| 2^-e in [2^7, 2^8), t_k the E4M3 value
+    nearest to what t_1 .. t_{k-1} leave of r 2^-e."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    out = np.zeros_like(r)
+    lib().qo_e4m3_terms(_ptr(r), r.size, int(terms), _ptr(out))
+    return out
+
+
 def top_s(a: np.ndarray, s: int) -> tuple[np.ndarray, np.ndarray]:
     a = np.ascontiguousarray(a, dtype=np.float64)
     sel = np.zeros(s, dtype=np.int32)
@@ -265,20 +286,22 @@ class NihtResult:
 
 
 def niht(A1: np.ndarray, A2: np.ndarray, y: np.ndarray, s: int, iters: int, *, k: float = 2.0,
-         c: float = 0.01, max_backtrack: int = 32, mu_mode=0, tol: float = 0.0,
+         c: float = 0.01, max_backtrack: int = 32, mu_mode=0, tol: float = 0.0, grad_e4m3: bool = False,
          trace: bool | str = False) -> NihtResult:
     """Algorithm 2 with matrices A1 (for g = A1^T r) and A2 (for A2 x, mu, omega), FP64.
 
     mu_mode "cross" takes Algorithm 2's printed step-size denominator (see step_size); tol > 0
-    stops after the first iteration whose ||y - A2 x||^2 <= tol.
+    stops after the first iteration whose ||y - A2 x||^2 <= tol; grad_e4m3 forms every gradient
+    from the residual (and y) held as three e4m3 terms (see e4m3_terms).
     trace=True records supports, gaps, step sizes and residuals per iteration;
     trace="x" also records every iterate."""
     return niht_seq([A1], [A2], [y], s, iters, k=k, c=c, max_backtrack=max_backtrack, mu_mode=mu_mode, tol=tol,
-                    trace=trace)
+                    grad_e4m3=grad_e4m3, trace=trace)
 
 
 def niht_seq(A1s: list, A2s: list, ys: list, s: int, iters: int, *, k: float = 2.0, c: float = 0.01,
-             max_backtrack: int = 32, mu_mode=0, tol: float = 0.0, trace: bool | str = False) -> NihtResult:
+             max_backtrack: int = 32, mu_mode=0, tol: float = 0.0, grad_e4m3: bool = False,
+             trace: bool | str = False) -> NihtResult:
     """Algorithm 2 with one realization per iteration: iteration t (1..iters) uses A1s[t], A2s[t],
     ys[t]; index 0 gives the initial support. Lists of length 1 repeat their one entry."""
     def full(lst):
@@ -290,7 +313,7 @@ def niht_seq(A1s: list, A2s: list, ys: list, s: int, iters: int, *, k: float = 2
     m, n = A1.shape
     x = np.zeros(n, dtype=np.float64)
     sup = np.zeros(s, dtype=np.int32)
-    p = _Params(k, c, max_backtrack, _mu_mode(mu_mode), float(tol))
+    p = _Params(k, c, max_backtrack, _mu_mode(mu_mode), float(tol), int(bool(grad_e4m3)), 0)
     rep = _Report()
     tr = None
     arrays = None

@@ -45,6 +45,12 @@
  *     same criterion stated on the residual, for when eps_s is not known)
  *   - H_s keeps exactly s indices: order by |a| descending, then index ascending
  *   - if ||g_G||^2 == 0 or ||Q2 g_G||^2 == 0 the solve stops (converged)
+ *   - grad_e4m3 = 1 forms the gradient from the residual held as three e4m3 terms
+ *     (the 8-bit floating-point gradient for codes of at most 4 bits, which e4m3
+ *     holds exactly, Section III-A): r -> 2^e (t1 + t2 + t3), e such that max |r| 2^-e
+ *     lies in [2^7, 2^8), each term the e4m3 value nearest to what the earlier terms
+ *     leave; A1^T is applied to that vector in FP64. The same holds for y in the
+ *     initial gradient A1^T y.
  *
  * QO_MUTANT (default 0) plants one deliberate mistake; it is set only by the
  * mutation tests, which build such variants to show that the pins catch them.
@@ -281,7 +287,51 @@ typedef struct {
     int32_t max_backtrack; /* cap on mu shrinks per iteration */
     int32_t mu_mode;       /* 0: ||A2_G g_G||^2; 1: Algorithm 2's cross product, forward square if <= 0 */
     double tol;            /* > 0: stop after the first iteration with ||y - A2 x||^2 <= tol */
+    int32_t grad_e4m3;     /* 1: the gradient's residual as three e4m3 terms (qo_e4m3_terms) */
+    int32_t reserved;
 } qo_params;
+
+/* Nearest value of the 8-bit floating-point format E4M3 (OCP 8-bit floating point
+ * specification: sign, 4 exponent bits with bias 7, 3 fraction bits, subnormals with
+ * spacing 2^-9, largest finite value 448), ties to the even fraction, magnitudes past 448
+ * saturated to 448. The quantum of a value with leading bit 2^E (E >= -6) is 2^(E-3). */
+double qo_e4m3(double v)
+{
+    if (v == 0.0 || v != v) return v;
+    const double a = fabs(v);
+    int e;
+    frexp(a, &e);                    /* a = f 2^e, f in [0.5, 1): leading bit 2^(e-1) */
+    int E = e - 1;
+    if (E < -6) E = -6;              /* subnormal range: one quantum 2^-9 */
+    const double q = ldexp(1.0, E - 3);
+    double rnd = nearbyint(a / q) * q; /* a / q is exact; nearbyint rounds ties to even */
+    if (rnd > 448.0) rnd = 448.0;
+    return copysign(rnd, v);
+}
+
+/* r (m values) -> out = 2^e (t_1 + ... + t_terms): e puts max |r| 2^-e in [2^7, 2^8)
+ * (0 when r is all zero or not finite), t_k = qo_e4m3 of r 2^-e - (t_1 + ... + t_{k-1}). */
+void qo_e4m3_terms(const double* r, int64_t m, int terms, double* out)
+{
+    double mx = 0.0;
+    for (int64_t i = 0; i < m; ++i) if (fabs(r[i]) > mx) mx = fabs(r[i]);
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) {
+        int ex;
+        frexp(mx, &ex);
+        e = ex - ((QO_MUTANT == 13) ? 7 : 8);
+    }
+    const int nt = (QO_MUTANT == 12) ? terms - 1 : terms;
+    for (int64_t i = 0; i < m; ++i) {
+        double v = ldexp(r[i], -e), acc = 0.0;
+        for (int k = 0; k < nt; ++k) {
+            const double t = qo_e4m3(v);
+            acc += t;
+            v -= t;
+        }
+        out[i] = ldexp(acc, e);
+    }
+}
 
 /* Step size on support G (Eq. step_size; Algorithm 2): num = ||g_G||^2 and
  *   mu_mode 0: den = ||A2[:, G] g_G||^2
@@ -392,7 +442,12 @@ int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double
 
     /* Initialisation (Algorithm 2): x = 0, support of H_s(A1^T y). */
     for (int32_t j = 0; j < n; ++j) x[j] = 0.0;
-    qo_gemv_t(A1, y, m, n, g);
+    if (p->grad_e4m3) {
+        qo_e4m3_terms(y, m, 3, r);
+        qo_gemv_t(A1, r, m, n, g);
+    } else {
+        qo_gemv_t(A1, y, m, n, g);
+    }
     double kth[2];
     qo_hard_threshold(g, n, s, support, kth, work);
     if (tr) {
@@ -419,6 +474,10 @@ int qo_niht_seq(const double* const* A1s, const double* const* A2s, const double
         for (int32_t q = 0; q < s; ++q) coef[q] = x[support[q]];
         qo_gemv_cols(A2, m, n, support, coef, s, z);
         for (int32_t i = 0; i < m; ++i) r[i] = (QO_MUTANT == 8) ? z[i] - y[i] : y[i] - z[i];
+        if (p->grad_e4m3) {
+            qo_e4m3_terms(r, m, 3, z1);
+            memcpy(r, z1, sizeof(double) * (size_t)m);
+        }
         qo_gemv_t((QO_MUTANT == 3) ? A2 : A1, r, m, n, g);
 
         /* step size (Eq. step_size on the current support) */

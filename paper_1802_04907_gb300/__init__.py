@@ -26,6 +26,7 @@ CHECK_FINITE = 2
 ODD_LEVELS = 4
 SOLVE_EAGER = 1
 SOLVE_TEST_TIMEOUT = 2
+SOLVE_FP8 = 4
 
 # stream ids of the random numbers, by convention of the solver
 STREAM_Q1, STREAM_Q2, STREAM_Y = 0, 1, 2
@@ -93,7 +94,8 @@ EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld
            "qiht_gemv_cols_workspace_size", "qiht_gemv_cols", "qiht_gemv_cols_static",
            "qiht_top_s_workspace_size", "qiht_top_s", "qiht_solve_workspace_size", "qiht_niht_solve",
            "qiht_clear_graph_cache", "qiht_solve_batched_workspace_size", "qiht_niht_solve_batched",
-           "qiht_gemv_t_multi_workspace_size", "qiht_gemv_t_multi", "qiht_solve_multi_workspace_size",
+           "qiht_gemv_t_multi_workspace_size", "qiht_gemv_t_multi", "qiht_gemv_t_multi_fp8",
+           "qiht_solve_multi_workspace_size",
            "qiht_niht_solve_multi", "qiht_solve_fresh_workspace_size", "qiht_niht_solve_fresh",
            "qiht_unrolled_workspace_size", "qiht_unrolled_forward", "qiht_unrolled_backward"]
 
@@ -132,6 +134,7 @@ def lib():
             "qiht_niht_solve_batched": ([ctypes.POINTER(_Problem), I32, I32, ctypes.POINTER(_Params), P, SZ, P], I32),
             "qiht_gemv_t_multi_workspace_size": ([I32, I32], SZ),
             "qiht_gemv_t_multi": ([ctypes.POINTER(_Codes), P, I64, I32, P, I64, P, P, SZ, P], I32),
+            "qiht_gemv_t_multi_fp8": ([ctypes.POINTER(_Codes), P, I64, I32, P, I64, P, P, SZ, P], I32),
             "qiht_solve_multi_workspace_size": ([I32, I32, I32, I32], SZ),
             "qiht_solve_fresh_workspace_size": ([I32, I32, I32, I32, I32], SZ),
             "qiht_unrolled_workspace_size": ([I32, I32, I32, I32, I32], SZ),
@@ -312,8 +315,9 @@ def gemv_t(Q: Codes, r: torch.Tensor, g: torch.Tensor | None = None, *, workspac
 
 
 def gemv_t_multi(Q: Codes, R: torch.Tensor, G: torch.Tensor | None = None, *, status: torch.Tensor | None = None,
-                 workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """qiht_gemv_t_multi: G = Q^T R for the rows of R (nrhs x rows residuals) on the tensor cores."""
+                 workspace: torch.Tensor | None = None, fp8: bool = False, stream=None) -> torch.Tensor:
+    """qiht_gemv_t_multi (fp8: qiht_gemv_t_multi_fp8): G = Q^T R for the rows of R (nrhs x rows
+    residuals) on the tensor cores."""
     if not (R.dim() == 2 and R.is_cuda and R.dtype == torch.float32 and R.stride(1) == 1 and R.shape[1] == Q.rows):
         raise ValueError(f"R: needs a CUDA float32 nrhs x {Q.rows} matrix with unit column stride; got "
                          f"shape {tuple(R.shape)}, {R.dtype}, strides {R.stride()}")
@@ -325,9 +329,10 @@ def gemv_t_multi(Q: Codes, R: torch.Tensor, G: torch.Tensor | None = None, *, st
         raise ValueError(f"G: needs a CUDA float32 {nrhs} x {Q.cols} matrix with unit column stride")
     ws = workspace if workspace is not None else _ws(lib().qiht_gemv_t_multi_workspace_size(Q.rows, nrhs), R.device)
     c = Q.c_struct()
-    _check(lib().qiht_gemv_t_multi(ctypes.byref(c), R.data_ptr(), R.stride(0), nrhs, G.data_ptr(), G.stride(0),
-                                   status.data_ptr() if status is not None else None, ws.data_ptr(), ws.numel(),
-                                   _stream(stream)), "qiht_gemv_t_multi")
+    fn = lib().qiht_gemv_t_multi_fp8 if fp8 else lib().qiht_gemv_t_multi
+    _check(fn(ctypes.byref(c), R.data_ptr(), R.stride(0), nrhs, G.data_ptr(), G.stride(0),
+              status.data_ptr() if status is not None else None, ws.data_ptr(), ws.numel(), _stream(stream)),
+           "qiht_gemv_t_multi_fp8" if fp8 else "qiht_gemv_t_multi")
     if workspace is None:
         _hold(ws, stream)
     _hold(G, stream)
@@ -619,7 +624,7 @@ class MultiResult:
 
 def niht_solve_multi(Q1: Codes, Q2: Codes, ys: list, s: int, iters: int, *, k: float = 2.0, c: float = 0.01,
                      max_backtrack: int = 32, workspace: torch.Tensor | None = None, out: tuple | None = None,
-                     stream=None) -> MultiResult:
+                     fp8: bool = False, stream=None) -> MultiResult:
     """qiht_niht_solve_multi: Algorithm 2 for every observation in ys (Codes vectors) sharing Q1, Q2."""
     nrhs = len(ys)
     dev = Q1.words.device
@@ -633,7 +638,7 @@ def niht_solve_multi(Q1: Codes, Q2: Codes, ys: list, s: int, iters: int, *, k: f
                                                                                           nrhs), dev)
     arr = (_Codes * nrhs)(*[y.c_struct() for y in ys])
     c1, c2 = Q1.c_struct(), Q2.c_struct()
-    params = _Params(k, c, max_backtrack, 0, 0.0, MU_FORWARD_SQ, 0)
+    params = _Params(k, c, max_backtrack, SOLVE_FP8 if fp8 else 0, 0.0, MU_FORWARD_SQ, 0)
     st = lib().qiht_niht_solve_multi(ctypes.byref(c1), ctypes.byref(c2), arr, nrhs, s, iters, ctypes.byref(params),
                                      X.data_ptr(), sup.data_ptr(), reports.data_ptr(), ws.data_ptr(), ws.numel(),
                                      _stream(stream))

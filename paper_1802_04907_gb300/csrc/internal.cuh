@@ -363,7 +363,31 @@ cudaError_t mrhs_make_map(void* map, const void* R16, int mk, int rows);
 cudaError_t launch_mrhs_split(const float* R, long long ldr, int m, int nrhs, void* R16, float* sc,
                               const float* scale, int lm1, cudaStream_t s);
 cudaError_t launch_mrhs_gemm(const Codes& Q, const void* map, const float* sc, float* G, long long ldg, int nrhs,
-                             int* status, cudaStream_t s);
+                             int* status, cudaStream_t s, bool fp8 = false);
+// FP8 variant (codes of at most 4 bits): the residual as three e4m3 terms, rows padded to 64
+size_t mrhs_gemm_smem8();
+int mrhs_pad_rows8(int m);
+cudaError_t mrhs_make_map8(void* map, const void* R8, int mk, int rows);
+cudaError_t launch_mrhs_split8(const float* R, long long ldr, int m, int nrhs, void* R8, float* sc,
+                               const float* scale, int lm1, cudaStream_t s);
+constexpr int kMrhsTerms8 = 3;
+
+// float -> e4m3 byte (round to nearest, saturating) and back; the converted pair holds the
+// value twice, so the byte taken does not depend on the pair's packing order
+__device__ __forceinline__ uint32_t f_to_e4m3(float v)
+{
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %1;" : "=h"(r) : "f"(v));
+    return (uint32_t)r & 0xffu;
+}
+
+__device__ __forceinline__ float e4m3_to_f(uint32_t b)
+{
+    const uint16_t pair = (uint16_t)(b * 0x0101u);
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(pair));
+    return __half2float(__ushort_as_half((unsigned short)(h2 & 0xffffu)));
+}
 
 // Per-right-hand-side iterations after the gradient product (mrhs_step.cu).
 struct MrhsState {
@@ -394,6 +418,9 @@ struct MrhsStepArgs {
     int mode;                 // 0: initial support, 1: an iteration
     int last;                 // 1: no gradient product follows (skip the split)
     int refresh;              // 1: form the residual directly (else update it)
+    int fp8;                  // 1: the next gradient product takes e4m3 terms (R16's bytes reused:
+                              //    term t of right-hand side k at row t * rhi + k, mk8 bytes each)
+    int mk8;
 };
 size_t mrhs_step_smem(int n, int mk, int s);
 cudaError_t launch_mrhs_init(const MrhsStepArgs& a, cudaStream_t s);

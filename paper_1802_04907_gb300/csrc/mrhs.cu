@@ -24,39 +24,69 @@ bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) =
 
 extern "C" {
 
+// bytes of the residual operand: two f16 parts (mk halves per row), or three e4m3 terms
+// (mk8 bytes per row) of the FP8 variant, which reuses the same memory
+static size_t operand_bytes(int rows, int nrhs)
+{
+    const size_t np = (size_t)mrhs_pad_rhs(nrhs), mk = (size_t)mrhs_pad_rows(rows), mk8 = (size_t)mrhs_pad_rows8(rows);
+    const size_t f16 = 2 * np * mk * 2, f8 = (size_t)kMrhsTerms8 * np * mk8;
+    return f16 > f8 ? f16 : f8;
+}
+
 size_t qiht_gemv_t_multi_workspace_size(int32_t rows, int32_t nrhs)
 {
     if (rows < 1 || nrhs < 1) return 0;
-    const size_t np = (size_t)mrhs_pad_rhs(nrhs), mk = (size_t)mrhs_pad_rows(rows);
-    return align256(2 * np * mk * 2) + align256(np * 4) + 256;
+    const size_t np = (size_t)mrhs_pad_rhs(nrhs);
+    return align256(operand_bytes(rows, nrhs)) + align256(np * 4) + 256;
+}
+
+static qiht_status gemv_t_multi_impl(const qiht_codes* Q, const float* R, int64_t ldr, int32_t nrhs, float* G,
+                                     int64_t ldg, int32_t* status, void* workspace, size_t workspace_bytes,
+                                     qiht_stream_t stream, bool fp8)
+{
+    qiht_status e = check_codes(Q);
+    if (e != QIHT_OK) return e;
+    if (fp8 && Q->bits == 8) return QIHT_ERR_BITS;           // 8-bit centred codes are not exact in e4m3
+    if (!R || !G || nrhs < 1 || ldr < Q->rows || ldg < Q->cols) return QIHT_ERR_ARG;
+    if (Q->rows > kMaxRows) return QIHT_ERR_ARG;
+    if (!workspace || workspace_bytes < qiht_gemv_t_multi_workspace_size(Q->rows, nrhs) || !aligned256(workspace))
+        return QIHT_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int np = mrhs_pad_rhs(nrhs), mk = mrhs_pad_rows(Q->rows), mk8 = mrhs_pad_rows8(Q->rows);
+    char* w = reinterpret_cast<char*>(workspace);
+    void* rop = w;
+    const size_t ob = align256(operand_bytes(Q->rows, nrhs));
+    float* sc = reinterpret_cast<float*>(w + ob);
+    int* st = reinterpret_cast<int*>(w + ob + align256((size_t)np * 4));
+    if (!status) {
+        CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+        status = st;
+    }
+    const Codes c = view(Q);
+    alignas(64) unsigned char map[kMrhsMapBytes];
+    if (fp8) {
+        CK(launch_mrhs_split8(R, ldr, Q->rows, nrhs, rop, sc, Q->scale, c.lm1, s));
+        CK(mrhs_make_map8(map, rop, mk8, kMrhsTerms8 * np));
+    } else {
+        CK(launch_mrhs_split(R, ldr, Q->rows, nrhs, rop, sc, Q->scale, c.lm1, s));
+        CK(mrhs_make_map(map, rop, mk, 2 * np));
+    }
+    CK(launch_mrhs_gemm(c, map, sc, G, ldg, nrhs, status, s, fp8));
+    return QIHT_OK;
 }
 
 qiht_status qiht_gemv_t_multi(const qiht_codes* Q, const float* R, int64_t ldr, int32_t nrhs, float* G,
                               int64_t ldg, int32_t* status, void* workspace, size_t workspace_bytes,
                               qiht_stream_t stream)
 {
-    qiht_status e = check_codes(Q);
-    if (e != QIHT_OK) return e;
-    if (!R || !G || nrhs < 1 || ldr < Q->rows || ldg < Q->cols) return QIHT_ERR_ARG;
-    if (Q->rows > kMaxRows) return QIHT_ERR_ARG;
-    if (!workspace || workspace_bytes < qiht_gemv_t_multi_workspace_size(Q->rows, nrhs) || !aligned256(workspace))
-        return QIHT_ERR_WORKSPACE;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int np = mrhs_pad_rhs(nrhs), mk = mrhs_pad_rows(Q->rows);
-    char* w = reinterpret_cast<char*>(workspace);
-    void* r16 = w;
-    float* sc = reinterpret_cast<float*>(w + align256((size_t)2 * np * mk * 2));
-    int* st = reinterpret_cast<int*>(w + align256((size_t)2 * np * mk * 2) + align256((size_t)np * 4));
-    if (!status) {
-        CK(cudaMemsetAsync(st, 0, sizeof(int), s));
-        status = st;
-    }
-    const Codes c = view(Q);
-    CK(launch_mrhs_split(R, ldr, Q->rows, nrhs, r16, sc, Q->scale, c.lm1, s));
-    alignas(64) unsigned char map[kMrhsMapBytes];
-    CK(mrhs_make_map(map, r16, mk, 2 * np));
-    CK(launch_mrhs_gemm(c, map, sc, G, ldg, nrhs, status, s));
-    return QIHT_OK;
+    return gemv_t_multi_impl(Q, R, ldr, nrhs, G, ldg, status, workspace, workspace_bytes, stream, false);
+}
+
+qiht_status qiht_gemv_t_multi_fp8(const qiht_codes* Q, const float* R, int64_t ldr, int32_t nrhs, float* G,
+                                  int64_t ldg, int32_t* status, void* workspace, size_t workspace_bytes,
+                                  qiht_stream_t stream)
+{
+    return gemv_t_multi_impl(Q, R, ldr, nrhs, G, ldg, status, workspace, workspace_bytes, stream, true);
 }
 
 // the residual is formed directly every kMultiRefresh iterations (and on the last), else
@@ -69,14 +99,14 @@ struct MultiLayout {
 
 static MultiLayout multi_layout(int m, int n, int s, int nrhs)
 {
-    const size_t np = (size_t)mrhs_pad_rhs(nrhs), mk = (size_t)mrhs_pad_rows(m);
+    const size_t np = (size_t)mrhs_pad_rhs(nrhs);
     MultiLayout L;
     size_t o = 0;
     L.ydesc = o; o += align256((size_t)nrhs * sizeof(qiht_codes));
     L.yhat = o; o += align256((size_t)nrhs * m * 4);
     L.resid = o; o += align256((size_t)nrhs * m * 4);
     L.zmu = o; o += align256((size_t)nrhs * m * 4);
-    L.r16 = o; o += align256(2 * np * mk * 2);
+    L.r16 = o; o += align256(operand_bytes(m, nrhs));
     L.sc = o; o += align256(np * 4);
     L.g = o; o += align256((size_t)nrhs * n * 4);
     L.xs = o; o += align256((size_t)nrhs * s * 4);
@@ -116,9 +146,12 @@ qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, co
     }
     qiht_params prm{2.0, 0.01, 32, 0, 0.0, QIHT_MU_FORWARD_SQ, 0};
     if (params) prm = *params;
-    if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 || prm.flags != 0)
+    if (!(prm.c > 0.0 && prm.c < 1.0) || !(prm.k * (1.0 - prm.c) > 1.0) || prm.max_backtrack < 0 ||
+        (prm.flags & ~QIHT_SOLVE_FP8) != 0)
         return QIHT_ERR_ARG;
     if (prm.tol != 0.0 || prm.mu_mode != QIHT_MU_FORWARD_SQ) return QIHT_ERR_ARG;   // the defaults only
+    const bool fp8 = (prm.flags & QIHT_SOLVE_FP8) != 0;
+    if (fp8 && Q1->bits == 8) return QIHT_ERR_BITS;
     const MultiLayout L = multi_layout(m, n, s, nrhs);
     if (!workspace || workspace_bytes < L.total || !aligned256(workspace)) return QIHT_ERR_WORKSPACE;
     const int mk = mrhs_pad_rows(m), np = mrhs_pad_rhs(nrhs);
@@ -153,13 +186,16 @@ qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, co
     a.kk = prm.k;
     a.cc = prm.c;
     a.max_bt = prm.max_backtrack;
+    a.fp8 = fp8 ? 1 : 0;
+    a.mk8 = mrhs_pad_rows8(m);
     alignas(64) unsigned char map[kMrhsMapBytes];
-    CK(mrhs_make_map(map, a.R16, mk, 2 * np));
+    if (fp8) CK(mrhs_make_map8(map, a.R16, a.mk8, kMrhsTerms8 * np));
+    else CK(mrhs_make_map(map, a.R16, mk, 2 * np));
     const Codes c1 = view(Q1);
     float* G = reinterpret_cast<float*>(w + L.g);
 
     CK(launch_mrhs_init(a, cs));
-    CK(launch_mrhs_gemm(c1, map, a.sc, G, n, nrhs, gstatus, cs));
+    CK(launch_mrhs_gemm(c1, map, a.sc, G, n, nrhs, gstatus, cs, fp8));
     a.mode = 0;
     a.last = iters == 0;
     CK(launch_mrhs_step(a, Q1->bits, cs));
@@ -168,7 +204,7 @@ qiht_status qiht_niht_solve_multi(const qiht_codes* Q1, const qiht_codes* Q2, co
         a.last = it == iters;
         a.refresh = a.last || it % kMultiRefresh == 0;
         CK(launch_mrhs_step(a, Q1->bits, cs));
-        if (!a.last) CK(launch_mrhs_gemm(c1, map, a.sc, G, n, nrhs, gstatus, cs));
+        if (!a.last) CK(launch_mrhs_gemm(c1, map, a.sc, G, n, nrhs, gstatus, cs, fp8));
     }
     CK(launch_mrhs_final(a, X, reports, gstatus, cs));
     return QIHT_OK;

@@ -45,6 +45,25 @@ constexpr uint32_t kStageBytes = kMT * kABytes + 2 * kBBytes;
 constexpr uint32_t kTmemCols = kMT * kTN;      // FP32 accumulators: 128 lanes x 512 columns
 constexpr unsigned long long kGemmWaitNs = 250ull * 1000 * 1000;
 
+// FP8 variant (codes of at most 4 bits): the centred codes are exact in e4m3, and the residual
+// is split into three e4m3 terms (about 12 significant bits). A stage holds 64 rows of Q, still
+// 64 bytes per operand row, so the layouts and descriptors are those of the f16 kernel;
+// tcgen05.mma kind::f8f6f4 takes K = 32 per instruction, so 64 rows take 2 x 2 x 3 MMAs
+// (12, against 16 for 64 rows of the f16 split).
+constexpr int kTK8 = 64;                       // rows of Q per stage: 64 bytes of e4m3
+constexpr int kTerms8 = 3;                     // e4m3 terms of the residual
+constexpr int kStages8 = 3;
+constexpr uint32_t kBBytes8 = kTN * kTK8;      // 16 KB per term
+constexpr uint32_t kStageBytes8 = kMT * kABytes + kTerms8 * kBBytes8;
+
+template <bool F8> struct GemmShape {
+    static constexpr int tk = F8 ? kTK8 : kTK;
+    static constexpr int stages = F8 ? kStages8 : kStages;
+    static constexpr int terms = F8 ? kTerms8 : 2;
+    static constexpr uint32_t bbytes = F8 ? kBBytes8 : kBBytes;
+    static constexpr uint32_t stage_bytes = F8 ? kStageBytes8 : kStageBytes;
+};
+
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B f16, both K-major,
 // N = 256, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
@@ -138,6 +157,32 @@ __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t
         : "memory");
 }
 
+// the same with e4m3 operands (the descriptor's format fields: 0 = e4m3 for A and B)
+__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// one f16 value (the low 16 bits of h) -> its e4m3 byte; the pair converted holds the value
+// twice, so the result does not depend on which half goes to which byte
+__device__ __forceinline__ uint32_t h_to_e4m3(uint32_t h)
+{
+    const uint32_t hh = (h & 0xffffu) * 0x00010001u;
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(r) : "r"(hh));
+    return (uint32_t)r & 0xffu;
+}
+
+// two f16 values that are exact in e4m3 -> two e4m3 bytes in the same order (low 16 bits)
+__device__ __forceinline__ uint32_t h2_to_e4m3x2(uint32_t h2)
+{
+    return h_to_e4m3(h2) | (h_to_e4m3(h2 >> 16) << 8);
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_u32(bar))
@@ -184,10 +229,11 @@ struct GemmArgs {
     int* status;
 };
 
-template <int BITS>
+template <int BITS, bool F8>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_constant__ CUtensorMap rmap, GemmArgs a)
 {
-    constexpr int WPS = BITS;                  // code words per column per stage (32 codes)
+    using Sh = GemmShape<F8>;
+    constexpr int WPS = Sh::tk * BITS / 32;    // code words per column per stage (32 or 64 codes)
     constexpr uint32_t MASK8 = 0x01010101u * ((1u << BITS) - 1);
     constexpr int PD = 3;                      // stages of codes a converter has in flight
     constexpr int PL = 8 / BITS;               // 4-code planes per word
@@ -203,7 +249,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
     const int nk = a.nk;
 
     if (tid == 0) {
-        for (int i = 0; i < kStages; ++i) {
+        for (int i = 0; i < Sh::stages; ++i) {
             bar_init(&full_a[i], kConvWarps);
             bar_init(&full_b[i], 1);
             bar_init(&empty[i], 1);
@@ -222,47 +268,52 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    auto stage_a = [&](int s) { return smem + (size_t)s * kStageBytes; };
-    auto stage_bh = [&](int s) { return smem + (size_t)s * kStageBytes + kMT * kABytes; };
-    auto stage_bl = [&](int s) { return smem + (size_t)s * kStageBytes + kMT * kABytes + kBBytes; };
+    auto stage_a = [&](int s) { return smem + (size_t)s * Sh::stage_bytes; };
+    auto stage_b = [&](int s, int t) { return smem + (size_t)s * Sh::stage_bytes + kMT * kABytes + (size_t)t * Sh::bbytes; };
 
     if (warp == 0) {
         // ---- TMA producer of the R tiles (hi and lo parts) ----
         if (lane == 0) {
             int issued = 0;
             for (int it = 0; it < nk; ++it) {
-                const int s = it % kStages;
-                const unsigned u = (unsigned)(it / kStages);
-                if (it >= kStages && !bar_wait(&empty[s], (u & 1u) ^ 1u, &s_abort, a.status)) break;
-                bar_expect(&full_b[s], 2 * kBBytes);
-                tma_load_2d(s_u32(stage_bh(s)), &rmap, it * kTK, n0, &full_b[s]);
-                tma_load_2d(s_u32(stage_bl(s)), &rmap, it * kTK, a.rhi + n0, &full_b[s]);
+                const int s = it % Sh::stages;
+                const unsigned u = (unsigned)(it / Sh::stages);
+                if (it >= Sh::stages && !bar_wait(&empty[s], (u & 1u) ^ 1u, &s_abort, a.status)) break;
+                bar_expect(&full_b[s], Sh::terms * Sh::bbytes);
+#pragma unroll
+                for (int t = 0; t < Sh::terms; ++t)
+                    tma_load_2d(s_u32(stage_b(s, t)), &rmap, it * Sh::tk, t * a.rhi + n0, &full_b[s]);
                 ++issued;
             }
             // no copy may still be in flight when the CTA leaves
-            for (int s = 0; s < kStages && s < issued; ++s) {
-                const int last = s + ((issued - 1 - s) / kStages) * kStages;
-                bar_drain(&full_b[s], (unsigned)(last / kStages) & 1u);
+            for (int s = 0; s < Sh::stages && s < issued; ++s) {
+                const int last = s + ((issued - 1 - s) / Sh::stages) * Sh::stages;
+                bar_drain(&full_b[s], (unsigned)(last / Sh::stages) & 1u);
             }
         }
     } else if (warp == 1) {
         // ---- MMA issuer ----
         if (lane == 0) {
             for (int it = 0; it < nk; ++it) {
-                const int s = it % kStages;
-                const unsigned par = (unsigned)(it / kStages) & 1u;
+                const int s = it % Sh::stages;
+                const unsigned par = (unsigned)(it / Sh::stages) & 1u;
                 if (!bar_wait(&full_a[s], par, &s_abort, a.status)) break;
                 if (!bar_wait(&full_b[s], par, &s_abort, a.status)) break;
                 tc_fence_after();
-                const uint32_t ab = s_u32(stage_a(s)), bh = s_u32(stage_bh(s)), bl = s_u32(stage_bl(s));
+                const uint32_t ab = s_u32(stage_a(s));
+                // 32 bytes of every operand row per MMA: K = 16 f16 or K = 32 e4m3
 #pragma unroll
-                for (int kk = 0; kk < kTK / 16; ++kk) {
-                    const uint64_t bhd = sw64_desc(bh + 32 * kk), bld = sw64_desc(bl + 32 * kk);
+                for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
                     for (int t = 0; t < kMT; ++t) {
                         const uint64_t ad = sw64_desc(ab + t * kABytes + 32 * kk);
-                        mma_f16(tmem + (uint32_t)(t * kTN), ad, bhd, (it | kk) != 0);
-                        mma_f16(tmem + (uint32_t)(t * kTN), ad, bld, 1u);
+#pragma unroll
+                        for (int u = 0; u < Sh::terms; ++u) {
+                            const uint64_t bd = sw64_desc(s_u32(stage_b(s, u)) + 32 * kk);
+                            const uint32_t acc = (it | kk | u) != 0;
+                            if (F8) mma_f8(tmem + (uint32_t)(t * kTN), ad, bd, acc);
+                            else mma_f16(tmem + (uint32_t)(t * kTN), ad, bd, acc);
+                        }
                     }
                 }
                 mma_commit(&empty[s]);
@@ -300,8 +351,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
 #pragma unroll
         for (int p = 0; p < PD; ++p) fetch(p, ring[p]);
         for (int it = 0; it < nk; ++it) {
-            const int s = it % kStages;
-            const unsigned u = (unsigned)(it / kStages);
+            const int s = it % Sh::stages;
+            const unsigned u = (unsigned)(it / Sh::stages);
             uint32_t cur[WPS];
 #pragma unroll
             for (int q = 0; q < WPS; ++q) {
@@ -311,10 +362,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
             }
             fetch(it + PD, ring[PD - 1]);
             // the whole warp leaves together (the arrive and the epilogue's loads are warp-wide)
-            if (it >= kStages && !__all_sync(0xffffffffu, bar_wait(&empty[s], (u & 1u) ^ 1u, &s_abort, a.status)))
+            if (it >= Sh::stages && !__all_sync(0xffffffffu, bar_wait(&empty[s], (u & 1u) ^ 1u, &s_abort, a.status)))
                 break;
-            // 32 codes of column j in K order -> 32 f16 values in four 16-byte chunks
-            uint32_t h[16];
+            // the stage's codes of column j in K order -> f16 values (then e4m3), 64 bytes per row
+            uint32_t h[Sh::tk / 2];
 #pragma unroll
             for (int q = 0; q < WPS; ++q) {
 #pragma unroll
@@ -327,6 +378,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
             }
             unsigned char* A = stage_a(s) + (ct / kTM) * kABytes;
             const int row = ct % kTM, sw = (row >> 1) & 3;
+            if (F8) {
+#pragma unroll
+                for (int i = 0; i < Sh::tk / 4; ++i) h[i] = h2_to_e4m3x2(h[2 * i]) | (h2_to_e4m3x2(h[2 * i + 1]) << 16);
+            }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 *reinterpret_cast<uint4*>(A + row * 64 + ((c ^ sw) << 4)) =
@@ -398,28 +453,99 @@ __global__ void __launch_bounds__(256) k_mrhs_split(const float* __restrict__ R,
     if (threadIdx.x == 0) sc[k] = (float)ldexp((double)*scale / (double)lm1, e);
 }
 
+// Residuals -> three scaled e4m3 terms (FP8 variant): e_k puts max |r_k| 2^-e_k in [2^7, 2^8)
+// (e4m3 reaches 448); term 1 = e4m3(r'), term 2 = e4m3(r' - term 1), term 3 = e4m3 of what is
+// left, each a row of bytes (term t of right-hand side k at row t * rhi + k).
+__global__ void __launch_bounds__(256) k_mrhs_split8(const float* __restrict__ R, long long ldr, int m, int nrhs,
+                                                     int mk, int rhi, unsigned char* __restrict__ R8,
+                                                     float* __restrict__ sc, const float* __restrict__ scale, int lm1)
+{
+    const int k = blockIdx.x;
+    __shared__ unsigned s_max[8];
+    unsigned mx = 0;
+    const float* r = R + (size_t)k * ldr;
+    if (k < nrhs)
+        for (int i = threadIdx.x; i < m; i += 256) mx = max(mx, __float_as_uint(r[i]) & 0x7fffffffu);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    unsigned M = 0;
+    for (int w = 0; w < 8; ++w) M = max(M, s_max[w]);
+    int e = 0;
+    const float Mf = __uint_as_float(M);
+    if (Mf > 0.0f && isfinite(Mf)) {
+        int ex;
+        frexpf(Mf, &ex);
+        e = ex - 8;
+    }
+    for (int i = threadIdx.x; i < mk; i += 256) {
+        float v = (k < nrhs && i < m) ? ldexpf(r[i], -e) : 0.0f;
+#pragma unroll
+        for (int t = 0; t < kTerms8; ++t) {
+            const uint32_t b = f_to_e4m3(v);
+            R8[(size_t)(t * rhi + k) * mk + i] = (unsigned char)b;
+            v -= e4m3_to_f(b);                     // exact: v and the term are close
+        }
+    }
+    if (threadIdx.x == 0) sc[k] = (float)ldexp((double)*scale / (double)lm1, e);
+}
+
 }  // namespace
 
 size_t mrhs_gemm_smem() { return (size_t)kStages * kStageBytes + 1024; }
+size_t mrhs_gemm_smem8() { return (size_t)kStages8 * kStageBytes8 + 1024; }
 
 int mrhs_pad_rhs(int nrhs) { return (nrhs + kTN - 1) / kTN * kTN; }
 int mrhs_pad_rows(int m) { return (m + kTK - 1) / kTK * kTK; }
+int mrhs_pad_rows8(int m) { return (m + kTK8 - 1) / kTK8 * kTK8; }
 
-// Tensor map of the f16 residual parts: rows of mk halves (K), 2 * nrhs_pad rows (hi, then lo).
-cudaError_t mrhs_make_map(void* map, const void* R16, int mk, int rows)
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+static EncodeFn tensor_map_encoder()
 {
-    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     static EncodeFn encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess) return e;
-        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return nullptr;
         encode = reinterpret_cast<EncodeFn>(fn);
     }
+    return encode;
+}
+
+// Tensor map of the e4m3 residual terms: rows of mk bytes (K), 3 * nrhs_pad rows.
+cudaError_t mrhs_make_map8(void* map, const void* R8, int mk, int rows)
+{
+    EncodeFn encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)mk, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)mk};
+    const cuuint32_t box[2] = {(cuuint32_t)kTK8, (cuuint32_t)kTN};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                              const_cast<void*>(R8), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mrhs_split8(const float* R, long long ldr, int m, int nrhs, void* R8, float* sc,
+                               const float* scale, int lm1, cudaStream_t s)
+{
+    const int np = mrhs_pad_rhs(nrhs), mk = mrhs_pad_rows8(m);
+    k_mrhs_split8<<<np, 256, 0, s>>>(R, ldr, m, nrhs, mk, np, reinterpret_cast<unsigned char*>(R8), sc, scale, lm1);
+    return cudaGetLastError();
+}
+
+// Tensor map of the f16 residual parts: rows of mk halves (K), 2 * nrhs_pad rows (hi, then lo).
+cudaError_t mrhs_make_map(void* map, const void* R16, int mk, int rows)
+{
+    EncodeFn encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {(cuuint64_t)mk, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)mk * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTN};
@@ -440,7 +566,7 @@ cudaError_t launch_mrhs_split(const float* R, long long ldr, int m, int nrhs, vo
 }
 
 cudaError_t launch_mrhs_gemm(const Codes& Q, const void* map, const float* sc, float* G, long long ldg, int nrhs,
-                             int* status, cudaStream_t s)
+                             int* status, cudaStream_t s, bool fp8)
 {
     GemmArgs a;
     a.Q = Q;
@@ -453,8 +579,12 @@ cudaError_t launch_mrhs_gemm(const Codes& Q, const void* map, const float* sc, f
     a.rhi = mrhs_pad_rhs(nrhs);
     a.status = status;
     const int ntm = (Q.cols + kTM * kMT - 1) / (kTM * kMT);
-    const size_t smem = mrhs_gemm_smem();
-    void* fn = Q.bits == 8 ? (void*)k_mrhs_gemm<8> : Q.bits == 4 ? (void*)k_mrhs_gemm<4> : (void*)k_mrhs_gemm<2>;
+    const size_t smem = fp8 ? mrhs_gemm_smem8() : mrhs_gemm_smem();
+    if (fp8) a.nk = mrhs_pad_rows8(Q.rows) / kTK8;
+    if (fp8 && Q.bits == 8) return cudaErrorInvalidValue;     // 8-bit codes are not exact in e4m3
+    void* fn = fp8 ? (Q.bits == 4 ? (void*)k_mrhs_gemm<4, true> : (void*)k_mrhs_gemm<2, true>)
+                   : (Q.bits == 8 ? (void*)k_mrhs_gemm<8, false>
+                                  : Q.bits == 4 ? (void*)k_mrhs_gemm<4, false> : (void*)k_mrhs_gemm<2, false>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     CUtensorMap m;

@@ -56,6 +56,33 @@ __device__ void split_residual(const float* r, int m, int mk, __half* hi, __half
     if (threadIdx.x == 0) *sc_k = (float)ldexp(alpha1, e);
 }
 
+// r (in z[0..m)) -> the three scaled e4m3 terms of the FP8 gradient product (max |r| 2^-e in
+// [2^7, 2^8)): term t of right-hand side k at row t * rhi + k of the byte tensor, mk8 bytes each
+__device__ void split_residual8(const float* r, int m, int mk8, int rhi, int k, unsigned char* R8, float* sc_k,
+                                double alpha1, SSh& sh)
+{
+    unsigned mx = 0;
+    for (int i = threadIdx.x; i < m; i += kST) mx = max(mx, __float_as_uint(r[i]) & 0x7fffffffu);
+    mx = smax(mx, sh.i);
+    int e = 0;
+    const float M = __uint_as_float(mx);
+    if (M > 0.0f && isfinite(M)) {
+        int ex;
+        frexpf(M, &ex);
+        e = ex - 8;
+    }
+    for (int i = threadIdx.x; i < mk8; i += kST) {
+        float v = i < m ? ldexpf(r[i], -e) : 0.0f;
+#pragma unroll
+        for (int t = 0; t < kMrhsTerms8; ++t) {
+            const uint32_t b = f_to_e4m3(v);
+            R8[(size_t)(t * rhi + k) * mk8 + i] = (unsigned char)b;
+            v -= e4m3_to_f(b);                 // exact: the term is within a factor 2 of v (or v is tiny)
+        }
+    }
+    if (threadIdx.x == 0) *sc_k = (float)ldexp(alpha1, e);
+}
+
 template <int BITS>
 __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
 {
@@ -237,9 +264,13 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
         st->resid2 = rr;
         if (!isfinite(rr)) { st->status = QIHT_ERR_NONFINITE; st->stop = 2; }
     }
-    if (!a.last && isfinite(rr))
-        split_residual(sm.z, m, a.mk, a.R16 + (size_t)k * a.mk, a.R16 + (size_t)(a.rhi + k) * a.mk, a.sc + k,
-                       sh.alpha1, sh);
+    if (!a.last && isfinite(rr)) {
+        if (a.fp8)
+            split_residual8(sm.z, m, a.mk8, a.rhi, k, reinterpret_cast<unsigned char*>(a.R16), a.sc + k, sh.alpha1, sh);
+        else
+            split_residual(sm.z, m, a.mk, a.R16 + (size_t)k * a.mk, a.R16 + (size_t)(a.rhi + k) * a.mk, a.sc + k,
+                           sh.alpha1, sh);
+    }
 }
 
 // Q(y_k) -> r = Q(y_k), its f16 parts, ||Q(y_k)||^2; the state of every right-hand side reset.
@@ -252,8 +283,14 @@ __global__ void __launch_bounds__(kST) k_mrhs_init(MrhsStepArgs a)
     const int k = blockIdx.x, tid = threadIdx.x, m = a.m;
     __half* hi = a.R16 + (size_t)k * a.mk;
     __half* lo = a.R16 + (size_t)(a.rhi + k) * a.mk;
+    unsigned char* R8 = reinterpret_cast<unsigned char*>(a.R16);
     if (k >= a.nrhs) {
-        for (int i = tid; i < a.mk; i += kST) { hi[i] = __float2half_rn(0.0f); lo[i] = __float2half_rn(0.0f); }
+        if (a.fp8) {
+            for (int t = 0; t < kMrhsTerms8; ++t)
+                for (int i = tid; i < a.mk8; i += kST) R8[(size_t)(t * a.rhi + k) * a.mk8 + i] = 0;
+        } else {
+            for (int i = tid; i < a.mk; i += kST) { hi[i] = __float2half_rn(0.0f); lo[i] = __float2half_rn(0.0f); }
+        }
         if (tid == 0) a.sc[k] = 0.0f;
         return;
     }
@@ -291,7 +328,10 @@ __global__ void __launch_bounds__(kST) k_mrhs_init(MrhsStepArgs a)
         st->changes = 0;
         st->full_selects = 1;             // the initial support
     }
-    split_residual(r, m, a.mk, hi, lo, a.sc + k, sh.alpha1, sh);
+    if (a.fp8)
+        split_residual8(r, m, a.mk8, a.rhi, k, R8, a.sc + k, sh.alpha1, sh);
+    else
+        split_residual(r, m, a.mk, hi, lo, a.sc + k, sh.alpha1, sh);
 }
 
 // dense x, the support and the report of every right-hand side

@@ -125,6 +125,12 @@ def test_multi_and_unrolled_argument_errors(lib):
     c = q._Codes(16, 16, 64, 128, 8, q.ld_words(64, 8))
     cy = q._Codes(16, 16, 64, 1, 8, q.ld_words(64, 8))
     prm = q._Params(2.0, 0.01, 32, 0)
+    # the FP8 product and solve take codes of 2 or 4 bits only (8-bit centred codes are not exact in e4m3)
+    assert lib.qiht_gemv_t_multi_fp8(ctypes.byref(c), P(256), 64, 4, P(256), 128, None, P(256), 1 << 30,
+                                     None) == q.ERR_BITS
+    fp8 = q._Params(2.0, 0.01, 32, q.SOLVE_FP8)
+    assert lib.qiht_niht_solve_multi(ctypes.byref(c), ctypes.byref(c), (q._Codes * 1)(cy), 1, 4, 10,
+                                     ctypes.byref(fp8), P(16), P(16), P(16), P(256), 1 << 30, None) == q.ERR_BITS
     assert lib.qiht_solve_multi_workspace_size(64, 128, 4, 3) > 0
     assert lib.qiht_solve_multi_workspace_size(16385, 128, 4, 3) == 0            # m above the limit
     assert lib.qiht_solve_multi_workspace_size(64, 128, 257, 3) == 0             # s above the limit

@@ -25,6 +25,8 @@ MUTANTS = {
     9: ("dequantised level off by one", "test_codes_on_grid or test_unbiased"),
     10: ("cross step size formed with the second quantization twice", "test_cross_is_unbiased"),
     11: ("residual tolerance test reversed", "test_tol_stops_exact_recovery_early"),
+    12: ("e4m3 residual with its third term dropped", "test_e4m3_terms_error_bound"),
+    13: ("e4m3 residual scaled one binade too high (saturates)", "test_e4m3_terms_error_bound"),
 }
 
 
@@ -39,7 +41,8 @@ def test_pins_catch_mutant(mutant, tmp_path):
            os.path.join(ROOT, "tests", "test_oracle_rng.py"),
            os.path.join(ROOT, "tests", "test_oracle_quantizer.py"),
            os.path.join(ROOT, "tests", "test_oracle_niht.py"),
-           os.path.join(ROOT, "tests", "test_oracle_step_modes.py"), "-k", sel]
+           os.path.join(ROOT, "tests", "test_oracle_step_modes.py"),
+           os.path.join(ROOT, "tests", "test_oracle_e4m3.py"), "-k", sel]
     out = subprocess.run(cmd, env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert "passed" in out.stdout or "failed" in out.stdout, out.stdout[-500:] + out.stderr[-500:]
     assert out.returncode != 0, f"mutant {mutant} ({what}) passed every selected pin:\n{out.stdout[-800:]}"
@@ -53,6 +56,7 @@ def test_unmutated_oracle_passes_the_same_selection(tmp_path):
            os.path.join(ROOT, "tests", "test_oracle_rng.py"),
            os.path.join(ROOT, "tests", "test_oracle_quantizer.py"),
            os.path.join(ROOT, "tests", "test_oracle_niht.py"),
-           os.path.join(ROOT, "tests", "test_oracle_step_modes.py"), "-k", sel]
+           os.path.join(ROOT, "tests", "test_oracle_step_modes.py"),
+           os.path.join(ROOT, "tests", "test_oracle_e4m3.py"), "-k", sel]
     out = subprocess.run(cmd, env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-1500:]
