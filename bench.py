@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched measurements (many right-hand sides; many problems) of the default line")
     ap.add_argument("--gemv-launches", type=int, default=200)
-    ap.add_argument("--workload", choices=["single", "interferometry", "mri", "batched", "multi", "fresh", "unrolled"], default="single",
+    ap.add_argument("--workload", choices=["single", "interferometry", "mri", "batched", "multi", "fresh", "unrolled", "fly"],
+                    default="single",
                     help="single: the large single solve (default); batched: 512 independent problems in one "
                          "launch; multi: 1024 right-hand sides sharing the large matrix (tensor-core gradient)")
     ap.add_argument("--nprob", type=int, default=512)
@@ -855,6 +856,97 @@ def run_fresh(args):
     print(json.dumps(line))
 
 
+def run_fly(args):
+    """Phi computed on the fly (Section IV-C) for the gridded interferometry matrix: 48 antennas
+    (2256 baselines, 4512 stacked rows), 128 x 128 sky (16384 columns), 50 sources, s = 64, 20 dB,
+    --bits for Phi and y, --iters iterations (default here 60). value = iterations/s of Algorithm 2
+    with both realizations of Q(Phi) drawn from the operator in every iteration
+    (qiht_niht_solve_fresh_fly: no copy of Phi, FP32 or codes of all realizations, is held). Beside
+    it: the same solve from the stored FP32 matrix, and the fused generate + quantize + GEMV^T
+    against the GEMV^T of stored codes at 8, 4 and 2 bits. The roofline is the fused product's
+    instruction issue (bound "alu")."""
+    import torch
+
+    import paper_1802_04907_gb300 as q
+    import synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bits = args.bits
+    iters = args.iters if args.iters != ITERS else 60
+    p = synth.interferometry_gridded(48, 128, n_src=50, s=64, snr_db=20.0, seed=0)
+    m, n, s = p.m, p.n, p.s
+    op = q.FlyOp(torch.from_numpy(np.ascontiguousarray(p.meta["uv"], dtype=np.int32)).to(dev),
+                 torch.from_numpy(p.meta["table"]).to(dev), p.meta["grid"])
+    y = torch.from_numpy(p.y).to(dev)
+    xt = torch.from_numpy(p.x_true).to(dev, torch.float32)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            out = fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps, out
+
+    clk = start_clocks(dev)
+    torch.cuda.synchronize()
+    ms, sv = timed(lambda: q.niht_solve_fresh_fly(op, y, bits, bits, 5, s, iters), args.steps)
+    clocks = clk.stop()
+    rep = sv.read_report()
+    err = float(torch.linalg.norm(sv.x - xt) / torch.linalg.norm(xt))
+    phi = torch.from_numpy(p.phi).to(dev)
+    ms_st, st = timed(lambda: q.niht_solve_fresh(phi, y, bits, bits, 5, s, iters), max(1, args.steps // 2))
+    same = bool(torch.equal(st.x, sv.x) and torch.equal(st.support, sv.support))
+    # the gradient product alone: fused on the fly against stored codes (max |r| given to both)
+    r = torch.from_numpy(synth.random_floats(m, seed=3, scale=0.3)).to(dev)
+    g = torch.empty(n, device=dev)
+    sc = torch.empty(1, device=dev)
+    rmax = torch.abs(r).max().reshape(1)
+    prod = {}
+    for b in (8, 4, 2):
+        us_fly = timed(lambda: q.gemv_t_fly(op, b, 1, 0, r, g, scale=sc), 100)[0] * 1e3
+        Q = q.fly_quantize(op, b, 1, 0)
+        us_st = timed(lambda: q.gemv_t_prescaled(Q, r, rmax, g), 100)[0] * 1e3
+        us_qp = timed(lambda: q.fly_quantize(op, b, 1, 0, 1), 20)[0] * 1e3
+        prod[f"bits{b}"] = {"fused_on_the_fly_us": us_fly, "stored_codes_us": us_st,
+                            "two_realizations_from_operator_us": us_qp}
+    us_qp_fp32 = timed(lambda: q.quantize_pair(phi, bits, 1, 0, 1), 20)[0] * 1e3
+    # roofline of the fused product: algorithmic operations per entry (Philox4x32-10: 10 rounds of
+    # two wide multiplies and two three-input XORs per four entries = 10; phase index 1.5; table
+    # read 1; code 3; multiply-accumulate 1) against the issue rate of 152 SMs x 4 schedulers x
+    # 32 lanes at the maximum SM clock
+    ops = 16.5 * m * n
+    us_f = prod[f"bits{bits}"]["fused_on_the_fly_us"]
+    peak = 152 * 4 * 32 * 2.07e9 / 1e12
+    achieved = ops / (us_f * 1e-6) / 1e12
+    line = {"metric": "NIHT iterations/s (fresh realizations, Phi on the fly)", "value": rep.iters_run / (ms / 1e3),
+            "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"u{bits}",
+            "data": "synthetic",
+            "config": {"workload": f"gridded interferometry {m}x{n} (48 antennas, 128x128 sky), 50 sources, s={s}, "
+                                   f"20 dB, {bits}-bit Phi and y, {iters} iterations, fresh Q(Phi) x2 and Q(y) per "
+                                   "iteration drawn from the operator",
+                       "m": m, "n": n, "s": s, "bits": bits, "iters_per_step": iters,
+                       "l2": "no matrix is read: the operator is 9 KB of baselines and a 1 KB table"},
+            "ms_per_iteration": ms / max(1, rep.iters_run), "rel_err": err, "status": rep.status,
+            "stored_fp32_phi": {"iterations_per_s": iters / (ms_st / 1e3), "identical_results": same,
+                                "quantize_two_realizations_us": us_qp_fp32},
+            "gradient_product": prod,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"k_fly_gemv_t (generate + quantize + Q^T r, {bits}-bit codes)",
+                         "avg_launch_us": us_f, "algorithmic_ops_per_launch": ops,
+                         "note": "16.5 lane operations per entry (Philox 10, phase index 1.5, table read 1, code 3, "
+                                 "multiply-accumulate 1); peak = 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz "
+                                 "(the maximum SM clock), the issue limit"},
+            "gpu_launches": None, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def run_unrolled(args):
     """Differentiation workload: 64 problems, Gaussian Phi 2048 x 8192 N(0, 1/m), s = 64 N(0,1)
     nonzeros, per-row complex gain |g| ~ U(0.9, 1.1), arg g ~ U(-0.1, 0.1), y = [Re g; Im g] Phi x
@@ -948,6 +1040,8 @@ def main():
         run_batched(args)
     elif args.workload == "multi":
         run_multi(args)
+    elif args.workload == "fly":
+        run_fly(args)
     elif args.workload == "fresh":
         run_fresh(args)
     elif args.workload == "unrolled":

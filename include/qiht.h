@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define QIHT_ABI_VERSION 3
+#define QIHT_ABI_VERSION 4
 
 /* Same type as cudaStream_t. */
 typedef struct CUstream_st* qiht_stream_t;
@@ -442,6 +442,66 @@ qiht_status qiht_unrolled_backward(const qiht_codes* Q1, const qiht_codes* Q2, i
                                    const float* gain_re, const float* gain_im, int32_t s, int32_t K, const float* Xbar,
                                    float* ybar, float* gain_re_bar, float* gain_im_bar, void* workspace,
                                    size_t workspace_bytes, qiht_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Phi computed on the fly (Section IV-C: the entries of Phi generated      */
+/* inside the device instead of read from memory), for the gridded         */
+/* radio-interferometry matrix of Section IV-B                              */
+/* ---------------------------------------------------------------------- */
+
+#define QIHT_FLY_MAX_GRID 256
+
+/* The interferometry measurement matrix (Section IV-B: Phi_kp = exp(-2 pi i (u_k l_p + v_k m_p)),
+ * stacked real) with gridded visibilities: baseline k lies on the uv grid of a g x g sky image at
+ * integer coordinates (u_k, v_k), and pixel p = ix * g + iy (direction cosines proportional to
+ * ix - g/2 and iy - g/2, spacing the inverse of the grid's extent). The phase of entry (k, p) is
+ * then 2 pi t_kp / g with the integer index
+ *   t_kp = (u_k (ix - g/2) + v_k (iy - g/2)) mod g,
+ * and the stacked real matrix (m = 2K rows, n = g^2 columns) is
+ *   Phi[k][p]     = table[t_kp]        (k < K, the real part)
+ *   Phi[K + k][p] = table[g + t_kp]    (the imaginary part)
+ * where table [device, 2g floats] holds cos(2 pi t / g) for t < g, then -sin(2 pi t / g)
+ * (the values are the caller's; any 2g floats define a matrix the same way). An entry costs one
+ * integer index and one table read; nothing of size m x n is stored. The scale of this
+ * operator's quantizations is c = max |table|, which is max |Phi| whenever the table's largest
+ * magnitude is reached (table[0] = cos 0 = 1 is, by the centre pixel, for every baseline). */
+typedef struct {
+    const int32_t* uv;      /* [device] 2K ints: u_0, v_0, u_1, v_1, ... (any integers; taken mod g) */
+    const float* table;     /* [device] 2g floats */
+    int32_t baselines;      /* K: a multiple of 4, 4 <= K <= 8192 (m = 2K <= 16384 rows) */
+    int32_t grid;           /* g: a power of two, 2 <= g <= QIHT_FLY_MAX_GRID */
+} qiht_fly_op;
+
+/* Codes of the operator's Phi in the column-packed layout: bit-identical to qiht_quantize (and,
+ * with words_b, qiht_quantize_pair) of the materialized m x n matrix with the same bits, seed,
+ * streams, flags (0 or QIHT_ODD_LEVELS) and scale. *scale [device] receives max |table|.
+ * words_a, words_b [device, n * ld_words words each; words_b NULL for one quantization],
+ * ld_words = qiht_ld_words(2K, bits). One kernel launch (after one for the scale);
+ * asynchronous on `stream`. Errors: QIHT_ERR_BITS, QIHT_ERR_ARG (operator out of its limits,
+ * bad pointers or ld_words). */
+qiht_status qiht_fly_quantize(const qiht_fly_op* op, int32_t bits, uint64_t seed, uint32_t stream_a,
+                              uint32_t stream_b, int32_t flags, uint32_t* words_a, uint32_t* words_b,
+                              int32_t ld_words, float* scale, qiht_stream_t stream);
+
+/* g = Q^T r where Q is the quantization (bits, seed, stream_id, flags) of the operator's Phi,
+ * generated, quantized and multiplied inside one kernel and never stored. The result is
+ * bit-identical to qiht_gemv_t on the codes qiht_fly_quantize makes (the same exact integer sums
+ * and final scaling). r [device, 2K floats], g [device, g^2 floats], scale [device, one float,
+ * receives max |table|]. Asynchronous on `stream`. Errors as for qiht_fly_quantize. */
+qiht_status qiht_gemv_t_fly(const qiht_fly_op* op, int32_t bits, uint64_t seed, uint32_t stream_id, int32_t flags,
+                            const float* r, float* g, float* scale, qiht_stream_t stream);
+
+/* qiht_niht_solve_fresh with Phi given by the operator: each iteration's two realizations of
+ * Q(Phi) are drawn from the operator (as qiht_fly_quantize does) instead of from a stored FP32
+ * matrix, so the solve holds no copy of Phi; results are identical to qiht_niht_solve_fresh on
+ * the materialized matrix. y [device, 2K floats]; the workspace is
+ * qiht_solve_fresh_workspace_size(2K, g^2, s, bits_phi, bits_y) bytes; g^2 <= 49152. Other
+ * arguments, errors and synchronisation as for qiht_niht_solve_fresh. */
+qiht_status qiht_niht_solve_fresh_fly(const qiht_fly_op* op, const float* y, int32_t bits_phi, int32_t bits_y,
+                                      uint64_t seed, int32_t quant_flags, int32_t s, int32_t iters,
+                                      const qiht_params* params, float* x, int32_t* support, qiht_report* report,
+                                      const qiht_trace* trace, void* workspace, size_t workspace_bytes,
+                                      qiht_stream_t stream);
 
 #ifdef __cplusplus
 }

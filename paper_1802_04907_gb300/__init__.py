@@ -88,6 +88,14 @@ class _Trace(ctypes.Structure):
 
 REPORT_BYTES = ctypes.sizeof(_Report)
 
+
+class _FlyOp(ctypes.Structure):
+    _fields_ = [("uv", ctypes.c_void_p), ("table", ctypes.c_void_p), ("baselines", ctypes.c_int32),
+                ("grid", ctypes.c_int32)]
+
+
+FLY_MAX_GRID = 256
+
 EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld_words", "qiht_quantize",
            "qiht_quantize_pair",
            "qiht_gemv_t_workspace_size", "qiht_gemv_t", "qiht_gemv_t_prescaled",
@@ -97,7 +105,8 @@ EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld
            "qiht_gemv_t_multi_workspace_size", "qiht_gemv_t_multi", "qiht_gemv_t_multi_fp8",
            "qiht_solve_multi_workspace_size",
            "qiht_niht_solve_multi", "qiht_solve_fresh_workspace_size", "qiht_niht_solve_fresh",
-           "qiht_unrolled_workspace_size", "qiht_unrolled_forward", "qiht_unrolled_backward"]
+           "qiht_unrolled_workspace_size", "qiht_unrolled_forward", "qiht_unrolled_backward",
+           "qiht_fly_quantize", "qiht_gemv_t_fly", "qiht_niht_solve_fresh_fly"]
 
 _lib = None
 
@@ -146,6 +155,10 @@ def lib():
                                        P, P, P, ctypes.POINTER(_Trace), P, SZ, P], I32),
             "qiht_niht_solve_multi": ([ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), ctypes.POINTER(_Codes), I32,
                                        I32, I32, ctypes.POINTER(_Params), P, P, P, P, SZ, P], I32),
+            "qiht_fly_quantize": ([ctypes.POINTER(_FlyOp), I32, U64, U32, U32, I32, P, P, I32, P, P], I32),
+            "qiht_gemv_t_fly": ([ctypes.POINTER(_FlyOp), I32, U64, U32, I32, P, P, P, P], I32),
+            "qiht_niht_solve_fresh_fly": ([ctypes.POINTER(_FlyOp), P, I32, I32, U64, I32, I32, I32,
+                                           ctypes.POINTER(_Params), P, P, P, ctypes.POINTER(_Trace), P, SZ, P], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -493,6 +506,84 @@ def niht_solve_fresh(phi: torch.Tensor, y: torch.Tensor, bits_phi: int, bits_y: 
                                      ctypes.byref(tr) if tr is not None else None, ws.data_ptr(), ws.numel(),
                                      _stream(stream))
     _check(st, "qiht_niht_solve_fresh")
+    sv.workspace = ws
+    return sv
+
+
+class FlyOp:
+    """The gridded interferometry operator of qiht_fly_op: Phi[k][p] = table[t_kp] and
+    Phi[K + k][p] = table[g + t_kp], t_kp = (u_k (ix - g/2) + v_k (iy - g/2)) mod g, p = ix g + iy.
+    uv: CUDA int32 (K, 2); table: CUDA float32 (2g,). Holds both tensors for the calls that use it."""
+
+    def __init__(self, uv: torch.Tensor, table: torch.Tensor, grid: int):
+        if not (uv.is_cuda and uv.dtype == torch.int32 and uv.dim() == 2 and uv.shape[1] == 2 and uv.is_contiguous()):
+            raise ValueError("uv: needs a contiguous CUDA int32 (K, 2) tensor")
+        _need(table, 2 * grid, torch.float32, "table")
+        self.uv, self.table, self.grid = uv, table, int(grid)
+        self.baselines = int(uv.shape[0])
+        self.rows, self.cols = 2 * self.baselines, self.grid * self.grid
+
+    def c_struct(self) -> _FlyOp:
+        return _FlyOp(self.uv.data_ptr(), self.table.data_ptr(), self.baselines, self.grid)
+
+
+def fly_quantize(op: FlyOp, bits: int, seed: int, stream_id: int, stream_b: int | None = None, *,
+                 odd: bool = False, stream=None):
+    """qiht_fly_quantize: the codes of the operator's Phi (one quantization, or two with stream_b)."""
+    dev = op.uv.device
+    ldw = ld_words(op.rows, bits)
+    levels = odd_levels(bits) if odd else 2**bits
+    scale = torch.empty(1, dtype=torch.float32, device=dev)
+    wa = torch.empty((op.cols, ldw), dtype=torch.int32, device=dev)
+    wb = torch.empty((op.cols, ldw), dtype=torch.int32, device=dev) if stream_b is not None else None
+    c = op.c_struct()
+    _check(lib().qiht_fly_quantize(ctypes.byref(c), bits, seed & (2**64 - 1), stream_id,
+                                   stream_b if stream_b is not None else 0, ODD_LEVELS if odd else 0, wa.data_ptr(),
+                                   wb.data_ptr() if wb is not None else None, ldw, scale.data_ptr(), _stream(stream)),
+           "qiht_fly_quantize")
+    qa = Codes(wa, scale, op.rows, op.cols, bits, levels)
+    if wb is None:
+        return qa
+    return qa, Codes(wb, scale, op.rows, op.cols, bits, levels)
+
+
+def gemv_t_fly(op: FlyOp, bits: int, seed: int, stream_id: int, r: torch.Tensor, g: torch.Tensor | None = None, *,
+               odd: bool = False, scale: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """qiht_gemv_t_fly: g = Q^T r with Q generated and quantized inside the product."""
+    _need(r, op.rows, torch.float32, "r")
+    if g is None:
+        g = torch.empty(op.cols, dtype=torch.float32, device=r.device)
+    _need(g, op.cols, torch.float32, "g")
+    if scale is None:
+        scale = torch.empty(1, dtype=torch.float32, device=r.device)
+    c = op.c_struct()
+    _check(lib().qiht_gemv_t_fly(ctypes.byref(c), bits, seed & (2**64 - 1), stream_id, ODD_LEVELS if odd else 0,
+                                 r.data_ptr(), g.data_ptr(), scale.data_ptr(), _stream(stream)), "qiht_gemv_t_fly")
+    _hold(g, stream)
+    return g
+
+
+def niht_solve_fresh_fly(op: FlyOp, y: torch.Tensor, bits_phi: int, bits_y: int, seed: int, s: int, iters: int, *,
+                         odd: bool = False, trace: bool = False, k: float = 2.0, c: float = 0.01,
+                         max_backtrack: int = 32, tol: float = 0.0, mu_mode="forward", stream=None) -> Solver:
+    """qiht_niht_solve_fresh_fly: Algorithm 2 with new realizations every iteration, Phi from the operator."""
+    m, n = op.rows, op.cols
+    _need(y, m, torch.float32, "y")
+    sv = Solver(m, n, s, iters, device=y.device, trace=trace, k=k, c=c, max_backtrack=max_backtrack, tol=tol,
+                mu_mode=mu_mode)
+    ws = _ws(lib().qiht_solve_fresh_workspace_size(m, n, s, bits_phi, bits_y), y.device)
+    tr = None
+    if sv.trace is not None:
+        t = sv.trace
+        tr = _Trace(t["support"].data_ptr(), t["kth"].data_ptr(), t["mu"].data_ptr(), t["bt"].data_ptr(),
+                    t["resid2"].data_ptr())
+    cs = op.c_struct()
+    st = lib().qiht_niht_solve_fresh_fly(ctypes.byref(cs), y.data_ptr(), bits_phi, bits_y, seed & (2**64 - 1),
+                                         ODD_LEVELS if odd else 0, s, iters, ctypes.byref(sv.params), sv.x.data_ptr(),
+                                         sv.support.data_ptr(), sv.report.data_ptr(),
+                                         ctypes.byref(tr) if tr is not None else None, ws.data_ptr(), ws.numel(),
+                                         _stream(stream))
+    _check(st, "qiht_niht_solve_fresh_fly")
     sv.workspace = ws
     return sv
 

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 
 SOURCES = ["quantize.cu", "gemv.cu", "gather.cu", "topk.cu", "iter.cu", "solve.cu", "batched.cu", "mrhs_gemm.cu",
            "mrhs_step.cu", "unrolled.cu",
-           "mrhs.cu"]
+           "mrhs.cu", "fly.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
                      "-I", os.path.join(ROOT, "include")]
@@ -40,7 +40,7 @@ def _stale(obj: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "cta_ops.cuh"), os.path.join(ROOT, "include", "qiht.h"),
+    headers = [os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "cta_ops.cuh"), os.path.join(CSRC, "quant_rng.cuh"), os.path.join(ROOT, "include", "qiht.h"),
                __file__]
     jobs = []
     for src in SOURCES:

@@ -475,4 +475,12 @@ size_t gather_partial_floats(int rows, int bits, int count);
 size_t top_smem_bytes(int n);
 int num_sms();
 
+// Phi computed on the fly (fly.cu): the operator's limits, codes of one or two quantizations,
+// and the fused generate + quantize + GEMV^T (scale = max |table| written by both).
+bool fly_op_ok(const qiht_fly_op* op);
+cudaError_t launch_fly_quantize(const qiht_fly_op* op, int bits, int levels, uint64_t seed, uint32_t s0, uint32_t s1,
+                                uint32_t* w0, uint32_t* w1, int ldw, float* scale, cudaStream_t s);
+cudaError_t launch_fly_gemv_t(const qiht_fly_op* op, int bits, int levels, uint64_t seed, uint32_t stream_id,
+                              const float* r, float* g, float* scale, cudaStream_t s);
+
 }  // namespace qiht

@@ -1,26 +1,9 @@
 // Stochastic quantizer Q(v, b) (Section III-A) with max-abs scaling c_v
 // (Appendix, quantization-error lemma), emitting the column-packed code layout.
 #include "internal.cuh"
+#include "quant_rng.cuh"
 
 namespace qiht {
-
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As Easy
-// as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplications with the
-// published multipliers, the key bumped by the published Weyl constants.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        if (round) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    }
-    return c;
-}
 
 __device__ __forceinline__ uint32_t abs_bits(float v)
 {
@@ -61,29 +44,6 @@ __global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ in, in
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = max(b, wmax[w]);
         atomicMax(out, b);
     }
-}
-
-// One rounding decision in binary32, every operation correctly rounded, on a grid of
-// `levels` points (lm1 = levels - 1 intervals): t = (v / c + 1) * lm1/2, clamped to
-// [0, lm1]; fi = floor(t), f = t - fi. The code is fi + (u < f) (at most lm1); the
-// decision does not depend on u, so several quantizations of the same value share it.
-struct Decision {
-    float fi, f;
-};
-
-__device__ __forceinline__ Decision quant_decide(float v, float c, float half, int lm1)
-{
-    const float vt = (c > 0.0f) ? __fdiv_rn(v, c) : 0.0f;
-    float t = __fmul_rn(__fadd_rn(vt, 1.0f), half);
-    t = fminf(fmaxf(t, 0.0f), (float)lm1);
-    const float fi = floorf(t);
-    return Decision{fi, __fsub_rn(t, fi)};
-}
-
-__device__ __forceinline__ uint32_t quant_code(const Decision& d, int lm1, float u)
-{
-    const int code = (int)d.fi + (u < d.f ? 1 : 0);
-    return (uint32_t)min(code, lm1);
 }
 
 constexpr int kQTileRows = 128;

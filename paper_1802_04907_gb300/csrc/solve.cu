@@ -975,14 +975,22 @@ size_t qiht_solve_fresh_workspace_size(int32_t m, int32_t n, int32_t s, int32_t 
     return fresh_layout(m, n, s, bits_phi, bits_y).total;
 }
 
-qiht_status qiht_niht_solve_fresh(const float* phi, int64_t ld_phi, const float* y, int32_t m, int32_t n,
-                                  int32_t bits_phi, int32_t bits_y, uint64_t seed, int32_t quant_flags, int32_t s,
-                                  int32_t iters, const qiht_params* params, float* x, int32_t* support,
-                                  qiht_report* report, const qiht_trace* trace, void* workspace,
-                                  size_t workspace_bytes, qiht_stream_t stream)
+// Where the fresh solve's realizations of Q(Phi) come from: a stored FP32 matrix (quantized
+// every iteration), or the on-the-fly operator (its codes generated every iteration).
+struct FreshSource {
+    const float* phi;
+    int64_t ld_phi;
+    const qiht_fly_op* op;
+};
+
+static qiht_status fresh_solve(const FreshSource& src, const float* y, int32_t m, int32_t n, int32_t bits_phi,
+                               int32_t bits_y, uint64_t seed, int32_t quant_flags, int32_t s, int32_t iters,
+                               const qiht_params* params, float* x, int32_t* support, qiht_report* report,
+                               const qiht_trace* trace, void* workspace, size_t workspace_bytes, qiht_stream_t stream)
 {
     if (!bits_ok(bits_phi) || !bits_ok(bits_y)) return QIHT_ERR_BITS;
-    if (!phi || !y || !x || !support || !report || m < 1 || n < 1 || ld_phi < n) return QIHT_ERR_ARG;
+    if (!y || !x || !support || !report || m < 1 || n < 1) return QIHT_ERR_ARG;
+    if (src.op ? !fly_op_ok(src.op) : (!src.phi || src.ld_phi < n)) return QIHT_ERR_ARG;
     if (s < 1 || s > m || s > n || iters < 0 || m > kMaxRows || n > kMaxTopN) return QIHT_ERR_ARG;
     if (quant_flags & ~QIHT_ODD_LEVELS) return QIHT_ERR_ARG;
     qiht_params prm{2.0, 0.01, 32, 0, 0.0, QIHT_MU_FORWARD_SQ, 0};
@@ -1008,13 +1016,16 @@ qiht_status qiht_niht_solve_fresh(const float* phi, int64_t ld_phi, const float*
     const qiht_codes q2{w2, sc, m, n, bits_phi, ldp, lev_phi, 0};
     const qiht_codes qy{wy, sc + 1, m, 1, bits_y, ldy, lev_y, 0};
     auto quantize_iteration = [&](int t) -> cudaError_t {
-        cudaError_t e = launch_quantize(phi, m, n, ld_phi, bits_phi, seed, (uint32_t)phi_stream(2 * t - 1), w1, ldp,
-                                        sc, cs, (uint32_t)phi_stream(2 * t), w2, lev_phi);
+        cudaError_t e = src.op ? launch_fly_quantize(src.op, bits_phi, lev_phi, seed, (uint32_t)phi_stream(2 * t - 1),
+                                                     (uint32_t)phi_stream(2 * t), w1, w2, ldp, sc, cs)
+                               : launch_quantize(src.phi, m, n, src.ld_phi, bits_phi, seed,
+                                                 (uint32_t)phi_stream(2 * t - 1), w1, ldp, sc, cs,
+                                                 (uint32_t)phi_stream(2 * t), w2, lev_phi);
         if (e != cudaSuccess) return e;
         return launch_quantize(y, m, 1, 1, bits_y, seed, (uint32_t)y_stream(t), wy, ldy, sc + 1, cs, 0, nullptr,
                                lev_y);
     };
-    CK(launch_absmax(phi, m, n, ld_phi, sc, cs));
+    if (!src.op) CK(launch_absmax(src.phi, m, n, src.ld_phi, sc, cs));   // the operator's kernels write max |table|
     CK(launch_absmax(y, m, 1, 1, sc + 1, cs));
     CK(quantize_iteration(1));
 
@@ -1070,6 +1081,29 @@ qiht_status qiht_niht_solve_fresh(const float* phi, int64_t ld_phi, const float*
         if (!read_state()) return QIHT_ERR_CUDA;
     }
     return QIHT_OK;
+}
+
+qiht_status qiht_niht_solve_fresh(const float* phi, int64_t ld_phi, const float* y, int32_t m, int32_t n,
+                                  int32_t bits_phi, int32_t bits_y, uint64_t seed, int32_t quant_flags, int32_t s,
+                                  int32_t iters, const qiht_params* params, float* x, int32_t* support,
+                                  qiht_report* report, const qiht_trace* trace, void* workspace,
+                                  size_t workspace_bytes, qiht_stream_t stream)
+{
+    if (!phi) return bits_ok(bits_phi) && bits_ok(bits_y) ? QIHT_ERR_ARG : QIHT_ERR_BITS;
+    return fresh_solve(FreshSource{phi, ld_phi, nullptr}, y, m, n, bits_phi, bits_y, seed, quant_flags, s, iters,
+                       params, x, support, report, trace, workspace, workspace_bytes, stream);
+}
+
+qiht_status qiht_niht_solve_fresh_fly(const qiht_fly_op* op, const float* y, int32_t bits_phi, int32_t bits_y,
+                                      uint64_t seed, int32_t quant_flags, int32_t s, int32_t iters,
+                                      const qiht_params* params, float* x, int32_t* support, qiht_report* report,
+                                      const qiht_trace* trace, void* workspace, size_t workspace_bytes,
+                                      qiht_stream_t stream)
+{
+    if (!fly_op_ok(op)) return bits_ok(bits_phi) && bits_ok(bits_y) ? QIHT_ERR_ARG : QIHT_ERR_BITS;
+    return fresh_solve(FreshSource{nullptr, 0, op}, y, 2 * op->baselines, op->grid * op->grid, bits_phi, bits_y,
+                       seed, quant_flags, s, iters, params, x, support, report, trace, workspace, workspace_bytes,
+                       stream);
 }
 
 size_t qiht_solve_batched_workspace_size(int32_t nprob)

@@ -27,7 +27,7 @@ import numpy as np
 class Problem:
     """One sparse recovery instance y = Phi x + e (Section I-A, Eq. 1)."""
 
-    phi: np.ndarray          # float32, m x n, C order (row-major)
+    phi: np.ndarray | None   # float32, m x n, C order (row-major); None for an operator-only instance
     y: np.ndarray            # float32, m
     x_true: np.ndarray       # float64, n (s nonzeros)
     support: np.ndarray      # int64, sorted indices of the nonzeros of x_true
@@ -37,11 +37,11 @@ class Problem:
 
     @property
     def m(self) -> int:
-        return int(self.phi.shape[0])
+        return int(self.phi.shape[0]) if self.phi is not None else int(self.meta["rows"])
 
     @property
     def n(self) -> int:
-        return int(self.phi.shape[1])
+        return int(self.phi.shape[1]) if self.phi is not None else int(self.meta["cols"])
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -129,6 +129,61 @@ def interferometry(n_ant: int = 48, grid: int = 128, n_src: int = 50, s: int = 6
                    name=name or f"interferometry_{2 * k}x{n}_s{s}",
                    meta={"snr_db": snr_db, "n_ant": n_ant, "grid": grid, "n_src": n_src,
                          "seed": seed, "wavelength_m": wavelength_m})
+
+
+def interferometry_gridded(n_ant: int = 48, grid: int = 128, n_src: int = 50, s: int = 64,
+                           snr_db: float = 20.0, seed: int = 0, *, wavelength_m: float = 5.0,
+                           array_diameter_m: float = 1000.0, materialize: bool = True,
+                           name: str | None = None) -> Problem:
+    """The interferometry instance of `interferometry` with gridded visibilities: every
+    baseline's (u, v) is moved to the nearest point of the uv grid dual to the g x g sky grid
+    (spacing 1 / (g dl) wavelengths), the usual gridding step of synthesis imaging. The phase of
+    entry (k, p), p = ix g + iy, is then 2 pi t / g with the integer
+      t = (u_k (ix - g/2) + v_k (iy - g/2)) mod g,
+    so Phi is generated from the integer baselines and a table of 2g values:
+      Phi[k][p] = table[t] = cos(2 pi t / g),  Phi[K + k][p] = table[g + t] = -sin(2 pi t / g).
+    meta holds "uv" (int32, K x 2), "table" (float32, 2g) and "grid". K = n_ant (n_ant - 1)
+    ordered pairs, cut to a multiple of four. materialize=False leaves phi as None (only the
+    operator) for sizes whose dense matrix is not wanted; y is then formed from the sources'
+    columns alone."""
+    rng = _rng(seed)
+    radius = 0.5 * array_diameter_m
+    r = radius * np.sqrt(rng.random(n_ant))
+    th = 2.0 * np.pi * rng.random(n_ant)
+    pos = np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
+    a, b = np.meshgrid(np.arange(n_ant), np.arange(n_ant), indexing="ij")
+    keep = a != b
+    uv = (pos[a[keep]] - pos[b[keep]]) / wavelength_m             # (K, 2) in wavelengths
+    uv = uv[: uv.shape[0] - uv.shape[0] % 4]
+    dl = wavelength_m / (3.0 * array_diameter_m)
+    uvi = np.rint(uv * (grid * dl)).astype(np.int32)               # grid units
+    K = uvi.shape[0]
+    n = grid * grid
+    tt = np.arange(grid, dtype=np.float64)
+    table = np.concatenate([np.cos(2.0 * np.pi * tt / grid), -np.sin(2.0 * np.pi * tt / grid)]).astype(np.float32)
+    off = np.arange(grid, dtype=np.int64) - grid // 2
+
+    def columns(idx):
+        ix, iy = idx // grid, idx % grid
+        t = (uvi[:, :1].astype(np.int64) * off[ix][None, :] + uvi[:, 1:].astype(np.int64) * off[iy][None, :]) % grid
+        return np.concatenate([table[t], table[grid + t]], axis=0)   # (2K, len(idx)) float32
+
+    src = np.sort(rng.choice(n, size=n_src, replace=False)).astype(np.int64)
+    x = np.zeros(n, dtype=np.float64)
+    x[src] = rng.lognormal(0.0, 1.0, size=n_src)
+    phi = None
+    if materialize:
+        phi = np.empty((2 * K, n), dtype=np.float32)
+        for c0 in range(0, n, 4096):
+            idx = np.arange(c0, min(n, c0 + 4096))
+            phi[:, c0:c0 + idx.size] = columns(idx)
+    clean = columns(src).astype(np.float64) @ x[src]
+    sigma = _noise_sigma(clean, snr_db)
+    y = clean + sigma * rng.standard_normal(2 * K)
+    return Problem(phi=phi, y=y.astype(np.float32), x_true=x, support=src, s=s,
+                   name=name or f"interferometry_gridded_{2 * K}x{n}_s{s}",
+                   meta={"snr_db": snr_db, "n_ant": n_ant, "grid": grid, "n_src": n_src, "seed": seed,
+                         "uv": uvi, "table": table, "rows": 2 * K, "cols": n})
 
 
 def haar_synthesis(N: int) -> np.ndarray:

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_host_only_entry_points(lib):
-    assert lib.qiht_abi_version() == 3
+    assert lib.qiht_abi_version() == 4
     assert q.status_string(q.OK) == "QIHT_OK"
     assert q.status_string(q.ERR_BACKTRACK_CAP) == "QIHT_ERR_BACKTRACK_CAP"
     # words per column: ceil(rows / (32/bits)) rounded up to a multiple of 4
@@ -196,6 +196,39 @@ def test_fresh_argument_errors(lib):
     assert call(wsb=ws - 1) == q.ERR_WORKSPACE
 
 
+def test_fly_argument_errors(lib):
+    # the on-the-fly operator's limits are checked on the host, before any CUDA call (the
+    # pointers below are never dereferenced)
+    P = ctypes.c_void_p
+    ok = q._FlyOp(16, 16, 8, 16)                     # K = 8 baselines, 16 x 16 grid
+    ldw = q.ld_words(16, 8)
+    fq, fg = lib.qiht_fly_quantize, lib.qiht_gemv_t_fly
+    assert fq(ctypes.byref(ok), 3, 0, 0, 0, 0, P(256), None, ldw, P(16), None) == q.ERR_BITS
+    assert fg(ctypes.byref(ok), 5, 0, 0, 0, P(16), P(16), P(16), None) == q.ERR_BITS
+    for bad in (q._FlyOp(16, 16, 6, 16),            # K not a multiple of 4
+                q._FlyOp(16, 16, 0, 16),            # no baselines
+                q._FlyOp(16, 16, 8200, 16),         # 2K above the row limit
+                q._FlyOp(16, 16, 8, 24),            # g not a power of two
+                q._FlyOp(16, 16, 8, 512),           # g above the limit
+                q._FlyOp(None, 16, 8, 16), q._FlyOp(16, None, 8, 16)):
+        assert fq(ctypes.byref(bad), 8, 0, 0, 0, 0, P(256), None, ldw, P(16), None) == q.ERR_ARG
+        assert fg(ctypes.byref(bad), 8, 0, 0, 0, P(16), P(16), P(16), None) == q.ERR_ARG
+    assert fq(ctypes.byref(ok), 8, 0, 0, 0, 0, P(256), None, ldw + 4, P(16), None) == q.ERR_ARG   # ld_words
+    assert fq(ctypes.byref(ok), 8, 0, 0, 0, 0, P(260), None, ldw, P(16), None) == q.ERR_ARG       # unaligned
+    assert fq(ctypes.byref(ok), 8, 0, 0, 1, 0, P(256), P(256), ldw, P(16), None) == q.ERR_ARG     # same buffer
+    assert fq(ctypes.byref(ok), 8, 0, 0, 0, 64, P(256), None, ldw, P(16), None) == q.ERR_ARG      # unknown flag
+    assert fg(ctypes.byref(ok), 8, 0, 0, 0, None, P(16), P(16), None) == q.ERR_ARG
+    prm = q._Params(2.0, 0.01, 32, 0)
+    sf = lib.qiht_niht_solve_fresh_fly
+    big = q._FlyOp(16, 16, 8, 256)                  # n = 65536 columns: above the solve's limit
+    assert sf(ctypes.byref(big), P(16), 8, 8, 1, 0, 4, 10, ctypes.byref(prm), P(16), P(16), P(16), None, P(256),
+              1 << 30, None) == q.ERR_ARG
+    assert sf(ctypes.byref(q._FlyOp(16, 16, 6, 16)), P(16), 8, 8, 1, 0, 4, 10, ctypes.byref(prm), P(16), P(16),
+              P(16), None, P(256), 1 << 30, None) == q.ERR_ARG
+    assert sf(ctypes.byref(ok), P(16), 3, 8, 1, 0, 4, 10, ctypes.byref(prm), P(16), P(16), P(16), None, P(256),
+              1 << 30, None) == q.ERR_BITS
+
+
 def test_grid_levels_are_checked(lib):
     P = ctypes.c_void_p
     ld = q.ld_words(64, 8)
@@ -225,13 +258,14 @@ def test_struct_layout_matches_header(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "qiht.h"\n'
         'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(qiht_codes), offsetof(qiht_codes, levels),'
         ' sizeof(qiht_problem), offsetof(qiht_problem, s), offsetof(qiht_problem, x), sizeof(qiht_report),'
-        ' sizeof(qiht_params)); return 0; }\n')
+        ' sizeof(qiht_params)); printf("%zu %zu\\n", sizeof(qiht_fly_op), offsetof(qiht_fly_op, grid)); return 0; }\n')
     exe = tmp_path / "layout"
     import subprocess
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(q._Codes), q._Codes.levels.offset, ctypes.sizeof(q._Problem), q._Problem.s.offset,
-            q._Problem.x.offset, ctypes.sizeof(q._Report), ctypes.sizeof(q._Params)]
+            q._Problem.x.offset, ctypes.sizeof(q._Report), ctypes.sizeof(q._Params), ctypes.sizeof(q._FlyOp),
+            q._FlyOp.grid.offset]
     assert got == want
 
 
