@@ -66,13 +66,15 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched measurements (many right-hand sides; many problems) of the default line")
     ap.add_argument("--gemv-launches", type=int, default=200)
-    ap.add_argument("--workload", choices=["single", "interferometry", "mri", "batched", "multi", "fresh", "unrolled", "fly"],
+    ap.add_argument("--workload", choices=["single", "interferometry", "mri", "batched", "multi", "fresh", "unrolled", "fly",
+                                           "mri_op"],
                     default="single",
                     help="single: the large single solve (default); batched: 512 independent problems in one "
                          "launch; multi: 1024 right-hand sides sharing the large matrix (tensor-core gradient)")
     ap.add_argument("--nprob", type=int, default=512)
     ap.add_argument("--nrhs", type=int, default=1024)
     ap.add_argument("--plain-sample", type=int, default=16)
+    ap.add_argument("--bits-factor", type=int, default=12, help="mri_op: bits of the quantized transform factor")
     ap.add_argument("--fp8", action="store_true",
                     help="multi: the FP8 (e4m3) gradient product, residual as three e4m3 terms (2- and 4-bit codes)")
     ap.add_argument("--eager", action="store_true",
@@ -947,6 +949,98 @@ def run_fly(args):
     print(json.dumps(line))
 
 
+def run_mri_op(args):
+    """The MRI operator form (Section IV-B): Phi = S (A (x) A) on the 128 x 128 head-like phantom
+    (a third of k-space on radial lines, 11364 stacked rows, 16384 Haar coefficients), s = 512,
+    30 dB, the 1D transform A = F_1 H^T quantized to --bits-factor bits (default 12, the paper's
+    transform width), k-space to --bits-y (default 8), --iters iterations (default here 100).
+    value = iterations/s of qiht_niht_solve_separable (dense transforms of the image, never an
+    m x n matrix). Beside it: the dense materialized composite at 8 bits (the fixed-codes
+    solver), whose recovery is limited by that quantization."""
+    import torch
+
+    import paper_1802_04907_gb300 as q
+    import synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    iters = args.iters if args.iters != ITERS else 100
+    bf = args.bits_factor
+    by = args.bits_y or 8
+    p = synth.mri(128, s=512, snr_db=30.0, seed=0)
+    N, s = p.meta["grid"], p.s
+    op = q.SepOp(torch.from_numpy(p.meta["factor"]).to(dev), torch.from_numpy(p.meta["mask"]).to(dev))
+    y = torch.from_numpy(p.y).to(dev)
+    xt = torch.from_numpy(p.x_true).to(dev, torch.float32)
+    for _ in range(max(1, args.warmup)):
+        sv = q.niht_solve_separable(op, y, bf, by, 5, s, iters)
+    torch.cuda.synchronize()
+    clk = start_clocks(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        sv = q.niht_solve_separable(op, y, bf, by, 5, s, iters)
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    rep = sv.read_report()
+    err = float(torch.linalg.norm(sv.x - xt) / torch.linalg.norm(xt))
+    # the materialized composite at 8 bits through the fixed-codes solver, for the recovery
+    phi = torch.from_numpy(p.phi).to(dev)
+    q1, q2, qy = q.quantize_problem(phi, y, 8, by, 5)
+    fx = q.Solver(p.m, p.n, s, iters, device=dev)
+    fx(q1, q2, qy)
+    torch.cuda.synchronize()
+    ev0.record()
+    fx(q1, q2, qy)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_fx = ev0.elapsed_time(ev1)
+    err_fx = float(torch.linalg.norm(fx.x - xt) / torch.linalg.norm(xt))
+    # one operator application: 6 N^3 multiply-adds (two GEMMs) and the gather or scatter
+    _, fh, _ = q.sep_quantize_factor(op, bf, 5, 0)
+    xv = torch.randn(op.cols, device=dev)
+    rv = torch.randn(op.rows, device=dev)
+    for _ in range(5):
+        q.sep_apply(op, fh, xv)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(200):
+        q.sep_apply(op, fh, xv)
+    ev1.record()
+    torch.cuda.synchronize()
+    us_f = ev0.elapsed_time(ev1) / 200 * 1e3
+    ev0.record()
+    for _ in range(200):
+        q.sep_apply(op, fh, rv, adjoint=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    us_a = ev0.elapsed_time(ev1) / 200 * 1e3
+    flops = 12.0 * N**3
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12                  # FP32 FMA: 128 lanes per SM per clock
+    line = {"metric": "NIHT iterations/s (MRI operator form)", "value": rep.iters_run / (ms / 1e3),
+            "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"f32 products, u{bf} factor",
+            "data": "synthetic",
+            "config": {"workload": f"MRI operator form: 128x128 head phantom, radial third of k-space ({p.m} stacked "
+                                   f"rows), {p.n} Haar coefficients, s={s}, 30 dB, {bf}-bit transform factor, "
+                                   f"{by}-bit k-space, {iters} iterations",
+                       "N": N, "m": p.m, "n": p.n, "s": s, "bits_factor": bf, "bits_y": by, "iters_per_step": iters,
+                       "l2": "operator state (two 256x128 factors, 2N x 2N products) fits L2"},
+            "ms_per_iteration": ms / max(1, rep.iters_run), "rel_err": err, "status": rep.status,
+            "backtracks": rep.backtracks,
+            "dense_8bit_composite": {"iterations_per_s": iters / (ms_fx / 1e3), "rel_err": err_fx},
+            "operator_application_us": {"forward": us_f, "adjoint": us_a},
+            "roofline": {"bound": "alu", "achieved": flops / (us_f * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (us_f * 1e-6) / 1e12 / peak, "traffic": None,
+                         "kernel": "k_sgemm (forward application: two FP32 GEMMs and the gather)",
+                         "avg_launch_us": us_f, "algorithmic_flops_per_launch": flops,
+                         "note": "12 N^3 flops per application; peak = FP32 FMA of 152 SMs x 128 lanes x 2.07 GHz; "
+                                 "at N = 128 an application is a few microseconds of launches (latency-bound)"},
+            "gpu_launches": None, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def run_unrolled(args):
     """Differentiation workload: 64 problems, Gaussian Phi 2048 x 8192 N(0, 1/m), s = 64 N(0,1)
     nonzeros, per-row complex gain |g| ~ U(0.9, 1.1), arg g ~ U(-0.1, 0.1), y = [Re g; Im g] Phi x
@@ -1042,6 +1136,8 @@ def main():
         run_multi(args)
     elif args.workload == "fly":
         run_fly(args)
+    elif args.workload == "mri_op":
+        run_mri_op(args)
     elif args.workload == "fresh":
         run_fresh(args)
     elif args.workload == "unrolled":

@@ -503,6 +503,62 @@ qiht_status qiht_niht_solve_fresh_fly(const qiht_fly_op* op, const float* y, int
                                       const qiht_trace* trace, void* workspace, size_t workspace_bytes,
                                       qiht_stream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* Separable operator with quantized transform factors (Section IV-B, MRI: */
+/* Phi formed by the Fourier and inverse wavelet transforms and the        */
+/* sampling operator, the transformation matrices themselves quantized)    */
+/* ---------------------------------------------------------------------- */
+
+#define QIHT_SEP_MAX_N 128     /* n = N^2 columns must fit the one-CTA threshold (<= 49152) */
+
+/* Phi = S (A (x) A), stacked real: A is the N x N complex 1D transform of the separable 2D
+ * transform (for MRI, the orthonormal DFT times the Haar synthesis, A = F_1 H^T), x the N x N
+ * coefficient image in row-major order (index j1 N + j2), S the M sampled positions
+ * (k1 N + k2). Row k of the complex operator is kron(A[k1], A[k2]); the stacked real matrix has
+ * m = 2M rows (real parts, then imaginary parts) and n = N^2 columns. The factor is given as its
+ * real and imaginary parts stacked into one 2N x N row-major float matrix [Re A; Im A], which
+ * is what is quantized: one scale c = max |[Re A; Im A]|, element (i, j) of the stacked matrix
+ * numbered j * 2N + i for the quantizer's random numbers. */
+typedef struct {
+    const float* factor;    /* [device] 2N x N floats: Re A (rows 0..N-1), then Im A */
+    const int32_t* mask;    /* [device] M ints: sampled positions k1 * N + k2, distinct (one off the grid samples 0) */
+    int32_t N;              /* 2 <= N <= QIHT_SEP_MAX_N */
+    int32_t M;              /* 1 <= M <= N^2 */
+} qiht_sep_op;
+
+/* Workspace bytes for qiht_niht_solve_separable (0 if out of range). */
+size_t qiht_solve_separable_workspace_size(int32_t N, int32_t M, int32_t s);
+
+/* Algorithm 2 on the separable operator with its factor quantized: Q1 and Q2 are two
+ * quantizations of the stacked factor to bits_factor bits (2..16; 2^bits levels, or
+ * 2^(bits-1) + 1 with QIHT_ODD_LEVELS in quant_flags), random-number streams 0 and 1 with
+ * `seed`; Phi-hat_k = S (A-hat_k (x) A-hat_k). y [device, 2M floats: real parts, then imaginary]
+ * is quantized to bits_y bits (2..16) with stream 2. Then, as qiht_niht_solve:
+ * g = Phi-hat_1^T (y-hat - Phi-hat_2 x), mu = ||g_G||^2 / ||Phi-hat_2 g_G||^2,
+ * x' = H_s(x + mu g), shrink mu by k(1 - c) while mu > (1 - c) ||x'-x||^2 / ||Phi-hat_2 (x'-x)||^2.
+ * The operator is applied as dense transforms of the N x N image (FP32 products of the
+ * dequantized factors, the sampling as a gather and its adjoint as a scatter), never as an
+ * m x n matrix. The host drives the iteration and reads scalars after every product, so the
+ * call returns when the solve is done. params: as for qiht_niht_solve (flags must be 0;
+ * mu_mode QIHT_MU_FORWARD_SQ only). s <= M, s <= N^2. Outputs and trace as for qiht_niht_solve. */
+qiht_status qiht_niht_solve_separable(const qiht_sep_op* op, const float* y, int32_t bits_factor, int32_t bits_y,
+                                      uint64_t seed, int32_t quant_flags, int32_t s, int32_t iters,
+                                      const qiht_params* params, float* x, int32_t* support, qiht_report* report,
+                                      const qiht_trace* trace, void* workspace, size_t workspace_bytes,
+                                      qiht_stream_t stream);
+
+/* The building blocks, for tests: the quantized factor (codes [device, 2N x N uint16, may be
+ * NULL] and dequantized values [device, 2N x N floats]: scale/(L-1) (2c - (L-1)), rounded once)
+ * of one realization, and the products of its operator: forward out = Phi-hat x
+ * (x [device, N^2 floats] -> out [device, 2M floats]) and adjoint out = Phi-hat^T r
+ * (r [device, 2M] -> out [device, N^2]). Workspace: qiht_solve_separable_workspace_size(N, M, 1).
+ * Asynchronous on `stream`. */
+qiht_status qiht_sep_quantize_factor(const qiht_sep_op* op, int32_t bits, uint64_t seed, uint32_t stream_id,
+                                     int32_t quant_flags, uint16_t* codes, float* factor_hat, float* scale,
+                                     qiht_stream_t stream);
+qiht_status qiht_sep_apply(const qiht_sep_op* op, const float* factor_hat, int32_t adjoint, const float* in,
+                           float* out, void* workspace, size_t workspace_bytes, qiht_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,13 @@ class _FlyOp(ctypes.Structure):
 
 FLY_MAX_GRID = 256
 
+
+class _SepOp(ctypes.Structure):
+    _fields_ = [("factor", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("N", ctypes.c_int32), ("M", ctypes.c_int32)]
+
+
+SEP_MAX_N = 128
+
 EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld_words", "qiht_quantize",
            "qiht_quantize_pair",
            "qiht_gemv_t_workspace_size", "qiht_gemv_t", "qiht_gemv_t_prescaled",
@@ -106,7 +113,9 @@ EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld
            "qiht_solve_multi_workspace_size",
            "qiht_niht_solve_multi", "qiht_solve_fresh_workspace_size", "qiht_niht_solve_fresh",
            "qiht_unrolled_workspace_size", "qiht_unrolled_forward", "qiht_unrolled_backward",
-           "qiht_fly_quantize", "qiht_gemv_t_fly", "qiht_niht_solve_fresh_fly"]
+           "qiht_fly_quantize", "qiht_gemv_t_fly", "qiht_niht_solve_fresh_fly",
+           "qiht_solve_separable_workspace_size", "qiht_niht_solve_separable", "qiht_sep_quantize_factor",
+           "qiht_sep_apply"]
 
 _lib = None
 
@@ -159,6 +168,11 @@ def lib():
             "qiht_gemv_t_fly": ([ctypes.POINTER(_FlyOp), I32, U64, U32, I32, P, P, P, P], I32),
             "qiht_niht_solve_fresh_fly": ([ctypes.POINTER(_FlyOp), P, I32, I32, U64, I32, I32, I32,
                                            ctypes.POINTER(_Params), P, P, P, ctypes.POINTER(_Trace), P, SZ, P], I32),
+            "qiht_solve_separable_workspace_size": ([I32, I32, I32], SZ),
+            "qiht_niht_solve_separable": ([ctypes.POINTER(_SepOp), P, I32, I32, U64, I32, I32, I32,
+                                           ctypes.POINTER(_Params), P, P, P, ctypes.POINTER(_Trace), P, SZ, P], I32),
+            "qiht_sep_quantize_factor": ([ctypes.POINTER(_SepOp), I32, U64, U32, I32, P, P, P, P], I32),
+            "qiht_sep_apply": ([ctypes.POINTER(_SepOp), P, I32, P, P, P, SZ, P], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -584,6 +598,75 @@ def niht_solve_fresh_fly(op: FlyOp, y: torch.Tensor, bits_phi: int, bits_y: int,
                                          ctypes.byref(tr) if tr is not None else None, ws.data_ptr(), ws.numel(),
                                          _stream(stream))
     _check(st, "qiht_niht_solve_fresh_fly")
+    sv.workspace = ws
+    return sv
+
+
+class SepOp:
+    """The separable operator of qiht_sep_op: Phi = S (A (x) A) stacked real, with the factor
+    given as the stacked real matrix [Re A; Im A] (CUDA float32, 2N x N) and the sampled
+    positions k1 * N + k2 (CUDA int32, M)."""
+
+    def __init__(self, factor: torch.Tensor, mask: torch.Tensor):
+        if not (factor.is_cuda and factor.dtype == torch.float32 and factor.dim() == 2 and factor.is_contiguous()
+                and factor.shape[0] == 2 * factor.shape[1]):
+            raise ValueError("factor: needs a contiguous CUDA float32 2N x N tensor")
+        if not (mask.is_cuda and mask.dtype == torch.int32 and mask.dim() == 1 and mask.is_contiguous()):
+            raise ValueError("mask: needs a contiguous CUDA int32 vector")
+        self.factor, self.mask = factor, mask
+        self.N, self.M = int(factor.shape[1]), int(mask.shape[0])
+        self.rows, self.cols = 2 * self.M, self.N * self.N
+
+    def c_struct(self) -> _SepOp:
+        return _SepOp(self.factor.data_ptr(), self.mask.data_ptr(), self.N, self.M)
+
+
+def sep_quantize_factor(op: SepOp, bits: int, seed: int, stream_id: int, *, odd: bool = False, stream=None):
+    """qiht_sep_quantize_factor: (codes uint16 as int16 tensor, dequantized factor, scale) of one
+    quantization of the stacked factor."""
+    dev = op.factor.device
+    codes = torch.empty((2 * op.N, op.N), dtype=torch.int16, device=dev)
+    fh = torch.empty((2 * op.N, op.N), dtype=torch.float32, device=dev)
+    scale = torch.empty(1, dtype=torch.float32, device=dev)
+    c = op.c_struct()
+    _check(lib().qiht_sep_quantize_factor(ctypes.byref(c), bits, seed & (2**64 - 1), stream_id, ODD_LEVELS if odd else 0,
+                                          codes.data_ptr(), fh.data_ptr(), scale.data_ptr(), _stream(stream)),
+           "qiht_sep_quantize_factor")
+    return codes, fh, scale
+
+
+def sep_apply(op: SepOp, factor_hat: torch.Tensor, v: torch.Tensor, *, adjoint: bool = False, stream=None):
+    """qiht_sep_apply: Phi-hat v (v of N^2 floats -> 2M) or, adjoint, Phi-hat^T v (2M -> N^2)."""
+    _need(v, op.rows if adjoint else op.cols, torch.float32, "v")
+    out = torch.empty(op.cols if adjoint else op.rows, dtype=torch.float32, device=v.device)
+    ws = _ws(lib().qiht_solve_separable_workspace_size(op.N, op.M, 1), v.device)
+    c = op.c_struct()
+    _check(lib().qiht_sep_apply(ctypes.byref(c), factor_hat.data_ptr(), 1 if adjoint else 0, v.data_ptr(),
+                                out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "qiht_sep_apply")
+    _hold(ws, stream)
+    return out
+
+
+def niht_solve_separable(op: SepOp, y: torch.Tensor, bits_factor: int, bits_y: int, seed: int, s: int, iters: int, *,
+                         odd: bool = False, trace: bool = False, k: float = 2.0, c: float = 0.01,
+                         max_backtrack: int = 32, tol: float = 0.0, stream=None) -> Solver:
+    """qiht_niht_solve_separable: Algorithm 2 on the separable operator with quantized factors."""
+    m, n = op.rows, op.cols
+    _need(y, m, torch.float32, "y")
+    sv = Solver(m, n, s, iters, device=y.device, trace=trace, k=k, c=c, max_backtrack=max_backtrack, tol=tol)
+    ws = _ws(lib().qiht_solve_separable_workspace_size(op.N, op.M, s), y.device)
+    tr = None
+    if sv.trace is not None:
+        t = sv.trace
+        tr = _Trace(t["support"].data_ptr(), t["kth"].data_ptr(), t["mu"].data_ptr(), t["bt"].data_ptr(),
+                    t["resid2"].data_ptr())
+    cs = op.c_struct()
+    st = lib().qiht_niht_solve_separable(ctypes.byref(cs), y.data_ptr(), bits_factor, bits_y, seed & (2**64 - 1),
+                                         ODD_LEVELS if odd else 0, s, iters, ctypes.byref(sv.params), sv.x.data_ptr(),
+                                         sv.support.data_ptr(), sv.report.data_ptr(),
+                                         ctypes.byref(tr) if tr is not None else None, ws.data_ptr(), ws.numel(),
+                                         _stream(stream))
+    _check(st, "qiht_niht_solve_separable")
     sv.workspace = ws
     return sv
 

@@ -252,7 +252,9 @@ def mri(grid: int = 128, s: int = 512, snr_db: float = 30.0, seed: int = 0, *,
     is kron(A[k1], A[k2]) over the coefficient index j1 N + j2. The real and imaginary parts are
     stacked: [Re Phi; Im Phi] x = [Re y; Im y]. x is the s largest Haar coefficients of
     head_phantom (exactly s-sparse); y = Phi x + complex Gaussian noise at the given SNR. The
-    paper's brain image and SparseMRI are not available, so the image is synthetic.
+    paper's brain image and SparseMRI are not available, so the image is synthetic. meta holds
+    the operator form too: "factor" = [Re A; Im A] (float32, 2N x N) and "mask" = k1 N + k2 of
+    every row (int32, in row order).
     """
     N = grid
     H = haar_synthesis(N)
@@ -277,7 +279,9 @@ def mri(grid: int = 128, s: int = 512, snr_db: float = 30.0, seed: int = 0, *,
     y = clean + _noise_sigma(clean, snr_db) * rng.standard_normal(2 * k)
     return Problem(phi=phi, y=y.astype(np.float32), x_true=x, support=support, s=s,
                    name=name or f"mri_{2 * k}x{n}_s{s}",
-                   meta={"snr_db": snr_db, "grid": N, "fraction": fraction, "samples": k, "seed": seed})
+                   meta={"snr_db": snr_db, "grid": N, "fraction": fraction, "samples": k, "seed": seed,
+                         "factor": np.concatenate([A.real, A.imag]).astype(np.float32),
+                         "mask": (ks[:, 0] * N + ks[:, 1]).astype(np.int32)})
 
 
 # Named workloads (sizes from the configurations this library is measured on).

@@ -229,6 +229,34 @@ def test_fly_argument_errors(lib):
               1 << 30, None) == q.ERR_BITS
 
 
+def test_sep_argument_errors(lib):
+    # the separable operator's limits are checked on the host before any CUDA call
+    P = ctypes.c_void_p
+    prm = q._Params(2.0, 0.01, 32, 0)
+    ws = lib.qiht_solve_separable_workspace_size(32, 300, 16)
+    assert ws > 0
+    assert lib.qiht_solve_separable_workspace_size(256, 300, 16) == 0            # N above the limit
+    assert lib.qiht_solve_separable_workspace_size(32, 2000, 16) == 0            # M > N^2
+    ok = q._SepOp(16, 16, 32, 300)
+    sv = lib.qiht_niht_solve_separable
+
+    def call(op=ok, bf=12, by=8, flags=0, s=16, iters=5, params=prm, wsb=ws, y=P(16)):
+        return sv(ctypes.byref(op), y, bf, by, 1, flags, s, iters, ctypes.byref(params), P(16), P(16), P(16), None,
+                  P(256), wsb, None)
+    assert call(bf=1) == q.ERR_BITS and call(by=17) == q.ERR_BITS
+    assert call(op=q._SepOp(16, 16, 129, 300)) == q.ERR_ARG
+    assert call(op=q._SepOp(None, 16, 32, 300)) == q.ERR_ARG
+    assert call(op=q._SepOp(16, 16, 32, 0)) == q.ERR_ARG
+    assert call(s=601) == q.ERR_ARG                                              # s > m = 2M
+    assert call(flags=64) == q.ERR_ARG
+    assert call(y=None) == q.ERR_ARG
+    assert call(params=q._Params(2.0, 0.01, 32, 0, 0.0, q.MU_CROSS, 0)) == q.ERR_ARG   # forward square only
+    assert call(wsb=ws - 1) == q.ERR_WORKSPACE
+    assert lib.qiht_sep_quantize_factor(ctypes.byref(ok), 20, 0, 0, 0, None, P(16), P(16), None) == q.ERR_BITS
+    assert lib.qiht_sep_quantize_factor(ctypes.byref(ok), 12, 0, 0, 0, None, None, P(16), None) == q.ERR_ARG
+    assert lib.qiht_sep_apply(ctypes.byref(ok), P(16), 0, P(16), P(16), P(256), 16, None) == q.ERR_WORKSPACE
+
+
 def test_grid_levels_are_checked(lib):
     P = ctypes.c_void_p
     ld = q.ld_words(64, 8)
@@ -258,14 +286,14 @@ def test_struct_layout_matches_header(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "qiht.h"\n'
         'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(qiht_codes), offsetof(qiht_codes, levels),'
         ' sizeof(qiht_problem), offsetof(qiht_problem, s), offsetof(qiht_problem, x), sizeof(qiht_report),'
-        ' sizeof(qiht_params)); printf("%zu %zu\\n", sizeof(qiht_fly_op), offsetof(qiht_fly_op, grid)); return 0; }\n')
+        ' sizeof(qiht_params)); printf("%zu %zu %zu\\n", sizeof(qiht_fly_op), offsetof(qiht_fly_op, grid), sizeof(qiht_sep_op)); return 0; }\n')
     exe = tmp_path / "layout"
     import subprocess
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(q._Codes), q._Codes.levels.offset, ctypes.sizeof(q._Problem), q._Problem.s.offset,
             q._Problem.x.offset, ctypes.sizeof(q._Report), ctypes.sizeof(q._Params), ctypes.sizeof(q._FlyOp),
-            q._FlyOp.grid.offset]
+            q._FlyOp.grid.offset, ctypes.sizeof(q._SepOp)]
     assert got == want
 
 
