@@ -63,7 +63,9 @@ __device__ __forceinline__ int fixed_shift(unsigned rmax_bits)
 // ---------------------------------------------------------------------------
 constexpr int kWarpThreads = 512;           // 16 warps per CTA, two CTAs per SM (one at C = 4)
 constexpr int kColsPerWarp = 4;             // columns a warp streams together at 2 bits (measured: 30.8 vs
-                                            // 33.0 us at 8192 x 32768; at 4 bits 37.1 vs 34.9, so there C = 1)
+                                            // 33.0 us at 8192 x 32768 with one column)
+constexpr int kColsPerWarp4 = 2;            // at 4 bits, one piece per lane (measured: 33.0 us, against
+                                            // 34.9 with one column and two pieces, 37.1 with four columns)
 
 // Warp 0 of a GEMV^T CTA: stop flag, max |r| (fast path: from the iteration kernel's
 // residual partials, whose non-finite maximum stops the solve), candidate threshold, the
@@ -119,12 +121,12 @@ __device__ __noinline__ void warp_prologue(const GemvTArgs& a, unsigned* s_st)
     }
 }
 
-// C = 1: a warp streams one column, NPL 16-byte pieces per lane at once (8 and 4 bits).
-// C = 4: a warp streams four adjacent columns together, one piece of each per lane, so that
-// every load of the residual's planes from shared memory serves four columns (2 bits, where
-// the per-code work, not HBM, bounds the pass).
+// C = 1: a warp streams one column, NPL 16-byte pieces per lane at once (8 bits).
+// C = 2, 4: a warp streams C adjacent columns together, one piece of each per lane, so that
+// every load of the residual's planes from shared memory serves C columns (4 and 2 bits,
+// where the per-code work and the planes' shared-memory reads, not HBM, bound the pass).
 template <int BITS, int NPL, int C>
-__global__ void __launch_bounds__(kWarpThreads, C == 1 ? 2 : 1) k_gemv_t_warp(GemvTArgs a)
+__global__ void __launch_bounds__(kWarpThreads, C <= 2 ? 2 : 1) k_gemv_t_warp(GemvTArgs a)
 {
     constexpr int G = 32 / BITS;
     constexpr int E = G / 4;
@@ -366,14 +368,14 @@ static WarpPlan plan_warp(const Codes& Q, int nsm)
     p.smem = 3 * (size_t)E * P * 16;
     if (p.smem > 48 * 1024 * 2) return p;          // keep at least two CTAs per SM
     if (Q.bits == 8) p.fn = (void*)k_gemv_t_warp<8, 4, 1>;
-    else if (Q.bits == 4) p.fn = (void*)k_gemv_t_warp<4, 2, 1>;
+    else if (Q.bits == 4) p.fn = (void*)k_gemv_t_warp<4, 1, kColsPerWarp4>;
     else p.fn = (void*)k_gemv_t_warp<2, 1, kColsPerWarp>;
     cudaFuncSetAttribute(p.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p.fn, kWarpThreads, p.smem);
     if (occ < 1) return p;
     long long grid = (long long)nsm * occ;
-    const int cpw = Q.bits == 2 ? kColsPerWarp : 1;
+    const int cpw = Q.bits == 2 ? kColsPerWarp : Q.bits == 4 ? kColsPerWarp4 : 1;
     const long long want = (((long long)Q.cols + cpw - 1) / cpw + kWarpThreads / 32 - 1) / (kWarpThreads / 32);
     if (grid > want) grid = want;
     p.grid = (unsigned)(grid < 1 ? 1 : grid);

@@ -9,8 +9,9 @@
 // omega = ||x' - x||^2 / ||Q2 (x' - x)||^2, and the residual r = Q(y) - Q2_G' x', updated
 // from the product the step already formed (Q2 (x' - x) of the backtracking test, or
 // mu Q2_G g_G when the support is unchanged), and directly as Q(y) - Q2_G' x' every few
-// iterations and on the last. The CTA then splits r into the scaled f16 parts the next
-// GEMM reads.
+// iterations and on the last. The backtracking test's product reads only the columns that
+// enter or leave the support and adds mu Q2_G g_G for the rest. The CTA then splits r into
+// the scaled f16 parts the next GEMM reads.
 // The iterate of a right-hand side is kept sparse (its support and the values on it).
 #include <cuda_fp16.h>
 
@@ -82,6 +83,8 @@ __device__ void split_residual8(const float* r, int m, int mk8, int rhi, int k, 
     }
     if (threadIdx.x == 0) *sc_k = (float)ldexp(alpha1, e);
 }
+
+static_assert(2 * QIHT_MULTI_MAX_S <= kST, "the backtracking test gives each union entry its own thread");
 
 template <int BITS>
 __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
@@ -187,9 +190,37 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
 #pragma unroll
             for (int o = 16; o; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
         }
-        mcols<BITS>(a.Q2, sm.uni, sm.dlt, uc, sm.z, reinterpret_cast<float*>(sm.keys));
+        // Q2 (x' - x) = mu Q2_G g_G + Q2 over the columns that enter or leave the support: on
+        // G n G' the step is mu g, which the step size's own product covers; on G' \ G it is x';
+        // on G \ G' it is -x, from which mu g is taken back out. So only those columns are read
+        // (a few, against s for the whole union). s <= 256 leaves one union entry per thread.
+        int keep = 0, jk = 0;
+        float ck = 0.0f;
+        if (tid < uc) {
+            jk = sm.uni[tid];
+            if (tid >= s) {
+                keep = 1;
+                ck = sm.dlt[tid] - sh.muf * __ldg(g + jk);
+            } else if (!((sm.gbit[jk >> 5] >> (jk & 31)) & 1u)) {
+                keep = 1;
+                ck = sm.dlt[tid];
+            }
+        }
+        int nsym;
+        const int pos = sscan(keep, sh.i, &nsym);
+        __syncthreads();                     // every entry (and the sum above) read before the list is rewritten
+        if (keep) {
+            sm.uni[pos] = jk;
+            sm.dlt[pos] = ck;
+        }
+        __syncthreads();
+        mcols<BITS>(a.Q2, sm.uni, sm.dlt, nsym, sm.z, reinterpret_cast<float*>(sm.keys));
         float dzf = 0.0f;
-        for (int i = tid; i < m; i += kST) dzf = fmaf(sm.z[i], sm.z[i], dzf);
+        for (int i = tid; i < m; i += kST) {
+            const float v = fmaf(sh.muf, __ldcg(zmu + i), sm.z[i]);
+            sm.z[i] = v;
+            dzf = fmaf(v, v, dzf);
+        }
         const double dz = ssum((double)dzf, sh.d);
         if (tid == 0) {
             const double dd = sh.alpha2 * sh.alpha2 * dz;
