@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-widths", action="store_true", help="skip the gradient kernel at the other code widths")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched measurements (many right-hand sides; many problems) of the default line")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the brief runs of the other workloads (interferometry, MRI operator form, Phi on the "
+                         "fly, fresh realizations, unrolled) in the default line")
     ap.add_argument("--gemv-launches", type=int, default=200)
     ap.add_argument("--workload", choices=["single", "interferometry", "mri", "batched", "multi", "fresh", "unrolled", "fly",
                                            "mri_op"],
@@ -530,6 +533,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and args.workload == "single" and not args.no_batched:
         del phi_h, y_h
         batched = batched_summary(args)
+    others = None
+    if rank == 0 and world == 1 and args.workload == "single" and not args.no_others:
+        others = others_summary(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -549,6 +555,8 @@ def run_ours(args):
                 "driver": "eager launches" if args.eager else "one CUDA graph per solve"}
         if batched is not None:
             line["batched"] = batched
+        if others is not None:
+            line["other_workloads"] = others
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -578,6 +586,91 @@ def batched_summary(args):
               "statuses", "config")
     return {"multi_rhs": {**{k: mu[k] for k in keep_m if k in mu}, "wall_s": round(t1 - t0, 1)},
             "many_problems": {**{k: ba[k] for k in keep_b if k in ba}, "wall_s": round(t2 - t1, 1)}}
+
+
+def quick_solves(p, bits_phi, bits_y, iters, steps, dev):
+    """it/s of qiht_niht_solve (cached graph) on problem p, CUDA events over `steps` solves after a
+    warm-up one, with the relative error of x against the truth and the product timed alone."""
+    import torch
+
+    import paper_1802_04907_gb300 as q
+
+    phi = torch.from_numpy(p.phi).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    q1, q2, qy = q.quantize_problem(phi, y, bits_phi, bits_y, 5)
+    sv = q.Solver(p.m, p.n, p.s, iters, device=dev)
+    sv(q1, q2, qy)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        sv(q1, q2, qy)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    rep = sv.read_report()
+    xt = torch.from_numpy(p.x_true).to(dev, torch.float32)
+    err = float(torch.linalg.norm(sv.x - xt) / torch.linalg.norm(xt))
+    r = torch.randn(p.m, device=dev)
+    rmax = r.abs().max().reshape(1)
+    g = torch.empty(p.n, device=dev)
+    for _ in range(5):
+        q.gemv_t_prescaled(q1, r, rmax, g)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(100):
+        q.gemv_t_prescaled(q1, r, rmax, g)
+    ev1.record()
+    torch.cuda.synchronize()
+    us = ev0.elapsed_time(ev1) / 100 * 1e3
+    del phi, y, q1, q2, qy
+    return {"iterations_per_s": rep.iters_run / (ms / 1e3), "ms_per_solve": ms, "rel_err": err,
+            "backtracks": rep.backtracks, "gemv_t_us": us}
+
+
+def others_summary(args):
+    """The other workloads, briefly, for the default line (so that a run of the default bench
+    records them): the interferometry-shaped solve at 8/8 and 2/8 bits, the MRI operator form
+    (with the dense 8-bit composite beside it), Phi on the fly, fresh realizations of the large
+    matrix, and the unrolled forward + adjoint."""
+    import copy
+
+    import torch
+
+    import synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    t0 = time.perf_counter()
+    p = synth.interferometry(seed=0)
+    intf = {}
+    for bp, by in ((8, 8), (2, 8)):
+        r = quick_solves(p, bp, by, ITERS, 3, dev)
+        by_ = p.m * p.n * bp / 8 + 4 * p.m + 4 * p.n
+        r["gemv_t_hbm_frac"] = by_ / (r["gemv_t_us"] * 1e-6) / 1e9 / hbm
+        intf[f"{bp}/{by}"] = r
+    out["interferometry_4512x16384_s64_300it"] = {**intf, "wall_s": round(time.perf_counter() - t0, 1)}
+    del p
+    keep = ("value", "unit", "ms_per_step", "ms_per_iteration", "rel_err", "status", "config")
+    for name, fn, extra in (("mri_operator_form", run_mri_op, ("dense_8bit_composite", "operator_application_us")),
+                            ("phi_on_the_fly", run_fly, ("stored_fp32_phi", "gradient_product")),
+                            ("fresh_realizations", run_fresh, ("fixed_quantizations",)),
+                            ("unrolled_forward_adjoint", run_unrolled, ())):
+        a = copy.copy(args)
+        a.steps, a.warmup, a.iters = 3, 3, ITERS
+        a.bits, a.bits_y = 8, None
+        a.m, a.n, a.s = M, N, S
+        t0 = time.perf_counter()
+        ln = fn(a, emit=False)
+        torch.cuda.empty_cache()
+        rf = ln.get("roofline") or {}
+        out[name] = {**{k: ln[k] for k in keep + extra if k in ln},
+                     "roofline": {k: rf[k] for k in ("bound", "frac", "avg_launch_us", "kernel") if k in rf},
+                     "wall_s": round(time.perf_counter() - t0, 1)}
+    return out
 
 
 def run_batched(args, emit=True):
@@ -799,7 +892,7 @@ def run_multi(args, emit=True):
     return line
 
 
-def run_fresh(args):
+def run_fresh(args, emit=True):
     """The large single solve with fresh realizations of Q(Phi) and Q(y) in every iteration
     (Algorithm 2 as written): 8192 x 32768, s = 256, 30 dB, 8-bit, --iters iterations (default
     here 60). value = iterations/s of qiht_niht_solve_fresh (Phi resident in HBM; every iteration
@@ -855,10 +948,12 @@ def run_fresh(args):
             "fixed_quantizations": {"iterations_per_s": iters / (ms_fx / 1e3), "rel_err": err_fx},
             "rel_err": err, "status": rep.status, "gpu_launches": None}
     line["clocks"] = clocks
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
-def run_fly(args):
+def run_fly(args, emit=True):
     """Phi computed on the fly (Section IV-C) for the gridded interferometry matrix: 48 antennas
     (2256 baselines, 4512 stacked rows), 128 x 128 sky (16384 columns), 50 sources, s = 64, 20 dB,
     --bits for Phi and y, --iters iterations (default here 60). value = iterations/s of Algorithm 2
@@ -946,10 +1041,12 @@ def run_fly(args):
                                  "multiply-accumulate 1); peak = 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz "
                                  "(the maximum SM clock), the issue limit"},
             "gpu_launches": None, "clocks": clocks}
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
-def run_mri_op(args):
+def run_mri_op(args, emit=True):
     """The MRI operator form (Section IV-B): Phi = S (A (x) A) on the 128 x 128 head-like phantom
     (a third of k-space on radial lines, 11364 stacked rows, 16384 Haar coefficients), s = 512,
     30 dB, the 1D transform A = F_1 H^T quantized to --bits-factor bits (default 12, the paper's
@@ -1038,10 +1135,12 @@ def run_mri_op(args):
                          "note": "12 N^3 flops per application; peak = FP32 FMA of 152 SMs x 128 lanes x 2.07 GHz; "
                                  "at N = 128 an application is a few microseconds of launches (latency-bound)"},
             "gpu_launches": None, "clocks": clocks}
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
-def run_unrolled(args):
+def run_unrolled(args, emit=True):
     """Differentiation workload: 64 problems, Gaussian Phi 2048 x 8192 N(0, 1/m), s = 64 N(0,1)
     nonzeros, per-row complex gain |g| ~ U(0.9, 1.1), arg g ~ U(-0.1, 0.1), y = [Re g; Im g] Phi x
     + noise at 30 dB (not quantized), 4-bit codes of Phi, K = 50 unrolled iterations, loss
@@ -1123,7 +1222,9 @@ def run_unrolled(args):
                          "note": "3K dense code passes (forward, recomputation, adjoint) over the step time; "
                                  "the per-problem step kernels are not counted"},
             "clocks": clocks, "gpu_launches": ud_launches}
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
 def main():
