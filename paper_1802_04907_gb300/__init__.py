@@ -555,6 +555,9 @@ def fly_quantize(op: FlyOp, bits: int, seed: int, stream_id: int, stream_b: int 
                                    stream_b if stream_b is not None else 0, ODD_LEVELS if odd else 0, wa.data_ptr(),
                                    wb.data_ptr() if wb is not None else None, ldw, scale.data_ptr(), _stream(stream)),
            "qiht_fly_quantize")
+    for t in (wa, wb, scale):
+        if t is not None:
+            _hold(t, stream)
     qa = Codes(wa, scale, op.rows, op.cols, bits, levels)
     if wb is None:
         return qa
@@ -574,6 +577,7 @@ def gemv_t_fly(op: FlyOp, bits: int, seed: int, stream_id: int, r: torch.Tensor,
     _check(lib().qiht_gemv_t_fly(ctypes.byref(c), bits, seed & (2**64 - 1), stream_id, ODD_LEVELS if odd else 0,
                                  r.data_ptr(), g.data_ptr(), scale.data_ptr(), _stream(stream)), "qiht_gemv_t_fly")
     _hold(g, stream)
+    _hold(scale, stream)
     return g
 
 
@@ -632,6 +636,8 @@ def sep_quantize_factor(op: SepOp, bits: int, seed: int, stream_id: int, *, odd:
     _check(lib().qiht_sep_quantize_factor(ctypes.byref(c), bits, seed & (2**64 - 1), stream_id, ODD_LEVELS if odd else 0,
                                           codes.data_ptr(), fh.data_ptr(), scale.data_ptr(), _stream(stream)),
            "qiht_sep_quantize_factor")
+    for t in (codes, fh, scale):
+        _hold(t, stream)
     return codes, fh, scale
 
 
@@ -644,6 +650,7 @@ def sep_apply(op: SepOp, factor_hat: torch.Tensor, v: torch.Tensor, *, adjoint: 
     _check(lib().qiht_sep_apply(ctypes.byref(c), factor_hat.data_ptr(), 1 if adjoint else 0, v.data_ptr(),
                                 out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "qiht_sep_apply")
     _hold(ws, stream)
+    _hold(out, stream)
     return out
 
 
