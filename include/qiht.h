@@ -212,7 +212,9 @@ qiht_status qiht_gemv_t_multi_fp8(const qiht_codes* Q, const float* R, int64_t l
  * idx [device, s int32] receives their indices in ascending order, val
  * [device, s floats, may be NULL] their values, kth [device, 2 floats, may be
  * NULL] the s-th and (s+1)-th largest magnitudes (0 if s == n).
- * Requires 1 <= s <= n <= 49152. Workspace: qiht_top_s_workspace_size(n). */
+ * Requires 1 <= s <= n <= 2^24. Up to 49152 entries one CTA selects (no workspace); above,
+ * a multi-CTA radix select with the same result needs qiht_top_s_workspace_size(n) bytes
+ * of workspace (256-byte aligned, else QIHT_ERR_WORKSPACE). */
 size_t qiht_top_s_workspace_size(int32_t n);
 qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float* val, float* kth,
                        void* workspace, size_t workspace_bytes, qiht_stream_t stream);
@@ -509,7 +511,7 @@ qiht_status qiht_niht_solve_fresh_fly(const qiht_fly_op* op, const float* y, int
 /* sampling operator, the transformation matrices themselves quantized)    */
 /* ---------------------------------------------------------------------- */
 
-#define QIHT_SEP_MAX_N 128     /* n = N^2 columns must fit the one-CTA threshold (<= 49152) */
+#define QIHT_SEP_MAX_N 512     /* n = N^2 <= 262144 (above 49152 the threshold is the multi-CTA select) */
 
 /* Phi = S (A (x) A), stacked real: A is the N x N complex 1D transform of the separable 2D
  * transform (for MRI, the orthonormal DFT times the Haar synthesis, A = F_1 H^T), x the N x N

@@ -101,7 +101,7 @@ class _SepOp(ctypes.Structure):
     _fields_ = [("factor", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("N", ctypes.c_int32), ("M", ctypes.c_int32)]
 
 
-SEP_MAX_N = 128
+SEP_MAX_N = 512
 
 EXPORTS = ["qiht_status_string", "qiht_abi_version", "qiht_last_error", "qiht_ld_words", "qiht_quantize",
            "qiht_quantize_pair",
@@ -403,9 +403,11 @@ def top_s(a: torch.Tensor, s: int, *, with_values: bool = True, stream=None):
     idx = torch.empty(s, dtype=torch.int32, device=a.device)
     val = torch.empty(s, dtype=torch.float32, device=a.device) if with_values else None
     kth = torch.empty(2, dtype=torch.float32, device=a.device)
-    _check(lib().qiht_top_s(a.data_ptr(), n, s, idx.data_ptr(), _ptr(val), kth.data_ptr(), None, 0,
-                            _stream(stream)), "qiht_top_s")
-    for t in (idx, val, kth):
+    wsb = int(lib().qiht_top_s_workspace_size(n))
+    ws = _ws(wsb, a.device) if wsb else None
+    _check(lib().qiht_top_s(a.data_ptr(), n, s, idx.data_ptr(), _ptr(val), kth.data_ptr(), _ptr(ws),
+                            ws.numel() if ws is not None else 0, _stream(stream)), "qiht_top_s")
+    for t in (idx, val, kth, ws):
         if t is not None:
             _hold(t, stream)
     return idx, val, kth

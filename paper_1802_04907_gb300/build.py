@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 
 SOURCES = ["quantize.cu", "gemv.cu", "gather.cu", "topk.cu", "iter.cu", "solve.cu", "batched.cu", "mrhs_gemm.cu",
            "mrhs_step.cu", "unrolled.cu",
-           "mrhs.cu", "fly.cu", "sep.cu"]
+           "mrhs.cu", "fly.cu", "sep.cu", "bigsel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
                      "-I", os.path.join(ROOT, "include")]

@@ -475,6 +475,13 @@ size_t gather_partial_floats(int rows, int bits, int count);
 size_t top_smem_bytes(int n);
 int num_sms();
 
+// H_s over more keys than one CTA holds (bigsel.cu): keys |fmaf(mu, g, x)| (|g| when x is null),
+// exactly s kept, ties to the lower index, indices ascending; workspace big_top_workspace(n).
+constexpr int kMaxBigTopN = 1 << 24;
+size_t big_top_workspace(int n);
+cudaError_t launch_big_top(const float* g, const float* x, const double* mu, int n, int s, int32_t* sel, float* val,
+                           float* kth, void* ws, cudaStream_t st);
+
 // Phi computed on the fly (fly.cu): the operator's limits, codes of one or two quantizations,
 // and the fused generate + quantize + GEMV^T (scale = max |table| written by both).
 bool fly_op_ok(const qiht_fly_op* op);

@@ -267,7 +267,7 @@ __global__ void k_sep_place(const int32_t* __restrict__ sel, const float* __rest
 
 // ---- workspace ----
 struct SepPlan {
-    size_t f1, f2, m2, fn, t1, t2, z, pq, yhat, x, xn, g, d, r, zv, sel, val, kth, scal, sc, total;
+    size_t f1, f2, m2, fn, t1, t2, z, pq, yhat, x, xn, g, d, r, zv, sel, val, kth, scal, sc, big, total;
 };
 
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -297,6 +297,7 @@ SepPlan sep_plan(int N, int M, int s)
     p.kth = o; o += al(8);
     p.scal = o; o += al(8 * 8);
     p.sc = o; o += al(16);
+    p.big = o; o += (int)n > kMaxTopN ? al(big_top_workspace((int)n)) : 0;
     p.total = o;
     return p;
 }
@@ -469,6 +470,8 @@ qiht_status qiht_niht_solve_separable(const qiht_sep_op* op, const float* y, int
         return cudaStreamSynchronize(cs) == cudaSuccess;
     };
     auto top = [&](const double* mu_dev) -> cudaError_t {
+        if (n > kMaxTopN)
+            return launch_big_top(g, mu_dev ? xd : nullptr, mu_dev, n, s, sel, val, kth, w + P.big, cs);
         TopArgs t{};
         t.g = g;
         t.x = mu_dev ? xd : nullptr;

@@ -318,12 +318,23 @@ qiht_status qiht_gemv_cols(const qiht_codes* Q, const int32_t* cols, const float
     return QIHT_OK;
 }
 
-size_t qiht_top_s_workspace_size(int32_t) { return 0; }
-
-qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float* val, float* kth, void*, size_t,
-                       qiht_stream_t stream)
+size_t qiht_top_s_workspace_size(int32_t n)
 {
-    if (!a || !idx || n < 1 || s < 1 || s > n || n > kMaxTopN) return QIHT_ERR_ARG;
+    return (n > kMaxTopN && n <= kMaxBigTopN) ? big_top_workspace(n) : 0;
+}
+
+qiht_status qiht_top_s(const float* a, int32_t n, int32_t s, int32_t* idx, float* val, float* kth, void* workspace,
+                       size_t workspace_bytes, qiht_stream_t stream)
+{
+    if (!a || !idx || n < 1 || s < 1 || s > n || n > kMaxBigTopN) return QIHT_ERR_ARG;
+    if (n > kMaxTopN) {
+        // more keys than one CTA holds: the multi-CTA select (same result)
+        if (!workspace || workspace_bytes < big_top_workspace(n) || !aligned(workspace, 256)) return QIHT_ERR_WORKSPACE;
+        if (launch_big_top(a, nullptr, nullptr, n, s, idx, val, kth, workspace, reinterpret_cast<cudaStream_t>(stream)) !=
+            cudaSuccess)
+            return QIHT_ERR_CUDA;
+        return QIHT_OK;
+    }
     TopArgs t{};
     t.g = a;
     t.x = nullptr;

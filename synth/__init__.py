@@ -242,7 +242,7 @@ def head_phantom(N: int) -> np.ndarray:
 
 
 def mri(grid: int = 128, s: int = 512, snr_db: float = 30.0, seed: int = 0, *,
-        fraction: float = 1.0 / 3.0, name: str | None = None) -> Problem:
+        fraction: float = 1.0 / 3.0, materialize: bool = True, name: str | None = None) -> Problem:
     """MRI-shaped instance (Section IV-B, magnetic resonance imaging), stacked to a real system.
 
     Phi = S F W^-1: W^-1 the 2D orthonormal Haar synthesis (tensor product of the 1D basis of
@@ -254,7 +254,8 @@ def mri(grid: int = 128, s: int = 512, snr_db: float = 30.0, seed: int = 0, *,
     head_phantom (exactly s-sparse); y = Phi x + complex Gaussian noise at the given SNR. The
     paper's brain image and SparseMRI are not available, so the image is synthetic. meta holds
     the operator form too: "factor" = [Re A; Im A] (float32, 2N x N) and "mask" = k1 N + k2 of
-    every row (int32, in row order).
+    every row (int32, in row order). materialize=False leaves phi as None (the paper's 512 x 512
+    size would need ~180 GB) and forms y through the transforms.
     """
     N = grid
     H = haar_synthesis(N)
@@ -263,23 +264,32 @@ def mri(grid: int = 128, s: int = 512, snr_db: float = 30.0, seed: int = 0, *,
     ks = radial_mask(N, fraction)
     k = ks.shape[0]
     n = N * N
-    phi = np.empty((2 * k, n), dtype=np.float32)
-    for b0 in range(0, k, 512):
-        b1 = min(k, b0 + 512)
-        rows = (A[ks[b0:b1, 0]][:, :, None] * A[ks[b0:b1, 1]][:, None, :]).reshape(b1 - b0, n)
-        phi[b0:b1] = rows.real
-        phi[k + b0:k + b1] = rows.imag
+    phi = None
+    if materialize:
+        phi = np.empty((2 * k, n), dtype=np.float32)
+        for b0 in range(0, k, 512):
+            b1 = min(k, b0 + 512)
+            rows = (A[ks[b0:b1, 0]][:, :, None] * A[ks[b0:b1, 1]][:, None, :]).reshape(b1 - b0, n)
+            phi[b0:b1] = rows.real
+            phi[k + b0:k + b1] = rows.imag
     coef = H.T @ head_phantom(N) @ H                     # analysis: C = H_a X H_a^T, H_a = H^T
     flat = coef.ravel()
     support = np.sort(np.argsort(-np.abs(flat), kind="stable")[:s]).astype(np.int64)
     x = np.zeros(n)
     x[support] = flat[support]
-    clean = phi[:, support].astype(np.float64) @ x[support]
+    if materialize:
+        clean = phi[:, support].astype(np.float64) @ x[support]
+    else:
+        # the same samples through the transforms: B = A X A^T read at the mask
+        B = A @ x.reshape(N, N) @ A.T
+        b = B[ks[:, 0], ks[:, 1]]
+        clean = np.concatenate([b.real, b.imag])
     rng = _rng(seed)
     y = clean + _noise_sigma(clean, snr_db) * rng.standard_normal(2 * k)
     return Problem(phi=phi, y=y.astype(np.float32), x_true=x, support=support, s=s,
                    name=name or f"mri_{2 * k}x{n}_s{s}",
                    meta={"snr_db": snr_db, "grid": N, "fraction": fraction, "samples": k, "seed": seed,
+                         "rows": 2 * k, "cols": n,
                          "factor": np.concatenate([A.real, A.imag]).astype(np.float32),
                          "mask": (ks[:, 0] * N + ks[:, 1]).astype(np.int32)})
 

@@ -101,6 +101,10 @@ def test_argument_errors_return_before_launch(lib):
                  P(16), P(16), None, P(256), 1 << 40, None) == q.ERR_ARG
     # top_s: s > n
     assert lib.qiht_top_s(P(16), 10, 11, P(16), None, None, None, 0, None) == q.ERR_ARG
+    # past one CTA's keys the select needs its workspace
+    assert lib.qiht_top_s_workspace_size(49152) == 0 and lib.qiht_top_s_workspace_size(49153) > 4 * 49153
+    assert lib.qiht_top_s(P(16), 49153, 10, P(16), None, None, None, 0, None) == q.ERR_WORKSPACE
+    assert lib.qiht_top_s(P(16), (1 << 24) + 1, 10, P(16), None, None, P(256), 1 << 30, None) == q.ERR_ARG
     # batched: empty batch, a problem above the limits, mixed widths, null outputs, no workspace
     assert lib.qiht_solve_batched_workspace_size(0) == 0 and lib.qiht_solve_batched_workspace_size(3) > 0
     pb = q._Problem(c, c, cy, 4, 0, 16, 16, 16)
@@ -235,7 +239,7 @@ def test_sep_argument_errors(lib):
     prm = q._Params(2.0, 0.01, 32, 0)
     ws = lib.qiht_solve_separable_workspace_size(32, 300, 16)
     assert ws > 0
-    assert lib.qiht_solve_separable_workspace_size(256, 300, 16) == 0            # N above the limit
+    assert lib.qiht_solve_separable_workspace_size(513, 300, 16) == 0            # N above the limit
     assert lib.qiht_solve_separable_workspace_size(32, 2000, 16) == 0            # M > N^2
     ok = q._SepOp(16, 16, 32, 300)
     sv = lib.qiht_niht_solve_separable
@@ -244,7 +248,7 @@ def test_sep_argument_errors(lib):
         return sv(ctypes.byref(op), y, bf, by, 1, flags, s, iters, ctypes.byref(params), P(16), P(16), P(16), None,
                   P(256), wsb, None)
     assert call(bf=1) == q.ERR_BITS and call(by=17) == q.ERR_BITS
-    assert call(op=q._SepOp(16, 16, 129, 300)) == q.ERR_ARG
+    assert call(op=q._SepOp(16, 16, 513, 300)) == q.ERR_ARG
     assert call(op=q._SepOp(None, 16, 32, 300)) == q.ERR_ARG
     assert call(op=q._SepOp(16, 16, 32, 0)) == q.ERR_ARG
     assert call(s=601) == q.ERR_ARG                                              # s > m = 2M

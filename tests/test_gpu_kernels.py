@@ -90,7 +90,10 @@ def test_gemv_cols_index_out_of_range_gives_nan(bad):
 
 
 @pytest.mark.parametrize("n,s", [(1, 1), (5, 5), (7, 3), (1024, 16), (1000, 999), (32768, 256), (49152, 1000),
-                                 (16384, 64), (40000, 1)])
+                                 (16384, 64), (40000, 1),
+                                 # past one CTA's 49152 keys: the multi-CTA radix select
+                                 (49153, 100), (262144, 512), (262144, 1), (100000, 99999), (300000, 300000),
+                                 (1 << 20, 4096)])
 def test_top_s(n, s):
     rng = np.random.Generator(np.random.PCG64(n + s))
     a = rng.standard_normal(n).astype(np.float32)
@@ -103,10 +106,26 @@ def test_top_s(n, s):
 
 
 def test_top_s_all_equal_and_zeros():
-    for a in (np.zeros(1000, np.float32), np.full(777, -2.5, np.float32)):
+    for a in (np.zeros(1000, np.float32), np.full(777, -2.5, np.float32), np.zeros(70000, np.float32),
+              np.full(123457, 3.0, np.float32)):
         idx, _, kth = q.top_s(torch.from_numpy(a).cuda(), 10)
         assert np.array_equal(idx.cpu().numpy(), np.arange(10))
         assert kth[0].item() == abs(a[0]) and kth[1].item() == abs(a[0])
+
+
+def test_top_s_multi_cta_magnitude_ties_across_chunks():
+    # equal magnitudes of both signs spread over many chunks: the lowest indices win
+    n, s = 200000, 5000
+    a = np.zeros(n, np.float32)
+    rng = np.random.Generator(np.random.PCG64(11))
+    hot = np.sort(rng.choice(n, 9000, replace=False))
+    a[hot] = np.where(rng.random(9000) < 0.5, -1.25, 1.25).astype(np.float32)
+    a[hot[:100]] = 2.0                                    # above the tie level
+    idx, val, kth = q.top_s(torch.from_numpy(a).cuda(), s)
+    ref, rkth = oracle.top_s(a.astype(np.float64), s)
+    assert np.array_equal(idx.cpu().numpy(), ref)
+    assert np.array_equal(val.cpu().numpy(), a[ref])
+    assert np.array_equal(kth.cpu().numpy().astype(np.float64), rkth)
 
 
 @pytest.mark.parametrize("bits", [2, 4, 8])

@@ -149,3 +149,42 @@ def test_sep_solve_full_size():
     # 20 iterations, against the oracle on the materialized quantized operator
     p, sv, ref = _solve_pair(128, 512, 20, 12, 8, seed=0)
     _check(p, sv, ref, "sep-128-12/8")
+
+
+def test_sep_solve_512_first_iteration():
+    # the paper's MRI size, 512 x 512 (176028 stacked rows, 262144 coefficients, s = 4096), where the
+    # threshold is the multi-CTA select and no m x n matrix can be formed: the first iteration
+    # against FP64 products of the oracle's quantized factors (the initial support H_s(Phi-hat_1^T
+    # y-hat), the step size on it and the residual after it)
+    p = synth.mri(512, s=4096, seed=0, materialize=False)
+    N, s = 512, 4096
+    sv = q.niht_solve_separable(_op(p), torch.from_numpy(p.y).cuda(), 12, 8, 9, s, 1, trace=True)
+    torch.cuda.synchronize()
+    tr = {k: v.cpu().numpy() for k, v in sv.trace.items()}
+    _, F1 = _factor_hat(p, 12, 9, 0)
+    _, F2 = _factor_hat(p, 12, 9, 1)
+    cy, sy = oracle.quantize(p.y, 8, 9, 2)
+    yq = oracle.dequantize(cy, 8, sy)
+    mask = p.meta["mask"]
+    M = mask.size
+    k1, k2 = mask // N, mask % N
+    A1 = F1[:N] + 1j * F1[N:]
+    A2 = F2[:N] + 1j * F2[N:]
+    Z = np.zeros((N, N), complex)
+    Z[k1, k2] = yq[:M] + 1j * yq[M:]
+    g0 = (A1.T @ np.conj(Z) @ A1).real.reshape(-1)           # Phi-hat_1^T y-hat
+    sup0, kth = oracle.top_s(g0, s)
+    assert (kth[0] - kth[1]) / kth[0] > 1e-4                 # an unambiguous initial selection
+    assert np.array_equal(tr["support"][0], sup0)
+    # mu = ||g_G||^2 / ||Phi-hat_2 g_G||^2, then x1 = mu g on G and ||y-hat - Phi-hat_2 x1||^2
+    X = np.zeros(N * N)
+    X[sup0] = g0[sup0]
+    B = A2 @ X.reshape(N, N) @ A2.T
+    z = np.concatenate([B[k1, k2].real, B[k1, k2].imag])
+    mu = float(g0[sup0] @ g0[sup0]) / float(z @ z)
+    assert abs(tr["mu"][1] - mu) <= 1e-4 * mu, (tr["mu"][1], mu)
+    assert np.array_equal(tr["support"][1], sup0)
+    r1 = yq - mu * z
+    assert abs(tr["resid2"][1] - float(r1 @ r1)) <= 1e-4 * float(r1 @ r1)
+    rep = sv.read_report()
+    assert rep.status == q.OK and rep.iters_run == 1
