@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
                                                float alpha, float beta)
 {
     constexpr int R = T / 16;                          // outputs per thread along each dimension
-    __shared__ float As[kGK][T + 4];
-    __shared__ float Bs[kGK][T + 4];
+    __shared__ __align__(16) float As[kGK][T + 4];
+    __shared__ __align__(16) float Bs[kGK][T + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * T, n0 = blockIdx.x * T;
     const int kh = K >> 1;
@@ -61,11 +61,19 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kGK; ++kk) {
+            // a thread's R consecutive rows and R consecutive columns: vector loads, and the
+            // lanes of a warp read one contiguous run of B (no bank conflicts) and broadcast A
             float a[R], b[R];
-#pragma unroll
-            for (int u = 0; u < R; ++u) {
-                a[u] = As[kk][ty + 16 * u];
-                b[u] = Bs[kk][tx + 16 * u];
+            if (R == 4) {
+                const float4 va = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+                const float4 vb = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+                a[0] = va.x; a[R > 1 ? 1 : 0] = va.y; a[R > 2 ? 2 : 0] = va.z; a[R > 3 ? 3 : 0] = va.w;
+                b[0] = vb.x; b[R > 1 ? 1 : 0] = vb.y; b[R > 2 ? 2 : 0] = vb.z; b[R > 3 ? 3 : 0] = vb.w;
+            } else {
+                const float2 va = *reinterpret_cast<const float2*>(&As[kk][ty * 2]);
+                const float2 vb = *reinterpret_cast<const float2*>(&Bs[kk][tx * 2]);
+                a[0] = va.x; a[R > 1 ? 1 : 0] = va.y;
+                b[0] = vb.x; b[R > 1 ? 1 : 0] = vb.y;
             }
 #pragma unroll
             for (int u = 0; u < R; ++u)
@@ -78,7 +86,7 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
     for (int u = 0; u < R; ++u)
 #pragma unroll
         for (int v = 0; v < R; ++v) {
-            const int i = m0 + ty + 16 * u, j = n0 + tx + 16 * v;
+            const int i = m0 + ty * R + u, j = n0 + tx * R + v;
             if (i < M && j < N) {
                 float* c = C + (size_t)i * ldc + j;
                 *c = beta != 0.0f ? fmaf(alpha, acc[u][v], beta * *c) : alpha * acc[u][v];
