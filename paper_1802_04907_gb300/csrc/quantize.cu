@@ -57,7 +57,7 @@ constexpr int kQTileCols = 32;
 // decision of an element is computed once and shared by the streams.
 template <int BITS, int NS>
 __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, int rows, int cols,
-                                                  long long ld, uint64_t seed, uint32_t stream0, uint32_t stream1,
+                                                  long long ld, PhiloxKeys keys, uint32_t stream0, uint32_t stream1,
                                                   uint32_t* __restrict__ words0, uint32_t* __restrict__ words1,
                                                   int ldw, const float* __restrict__ scale_p, int lm1)
 {
@@ -69,7 +69,6 @@ __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, 
 
     const float c = *scale_p;
     const float half = (float)lm1 * 0.5f;
-    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
     const int row_tiles = (ldw * G + kQTileRows - 1) / kQTileRows;
     const int col_tiles = (cols + kQTileCols - 1) / kQTileCols;
     const long long ntiles = (long long)row_tiles * col_tiles;
@@ -135,9 +134,9 @@ __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, 
                         if (qq != cur) {
 #pragma unroll
                             for (int st = 0; st < NS; ++st)
-                                rnd[st] = philox4x32_10(
+                                rnd[st] = philox4x32_10_keys(
                                     make_uint4((uint32_t)qq, (uint32_t)(qq >> 32), st == 0 ? stream0 : stream1, 0u),
-                                    key0, key1);
+                                    keys);
                             cur = qq;
                         }
                         const uint32_t sel = e & 3;
@@ -175,6 +174,7 @@ cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int
                             uint32_t stream_id, uint32_t* words, int ld_words, const float* scale,
                             cudaStream_t s, uint32_t stream_id2, uint32_t* words2, int levels)
 {
+    const PhiloxKeys keys = philox_keys(seed);   // the ten round keys, as launch constants
     if (levels <= 0) levels = 1 << bits;
     const int lm1 = levels - 1;
     const int G = 32 / bits;
@@ -187,16 +187,16 @@ cudaError_t launch_quantize(const float* in, int rows, int cols, int64_t ld, int
     const bool two = words2 != nullptr;
     switch (bits) {
     case 2:
-        if (two) k_quantize<2, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
-        else k_quantize<2, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale, lm1);
+        if (two) k_quantize<2, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, keys, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
+        else k_quantize<2, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, keys, stream_id, stream_id, words, words, ld_words, scale, lm1);
         break;
     case 4:
-        if (two) k_quantize<4, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
-        else k_quantize<4, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale, lm1);
+        if (two) k_quantize<4, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, keys, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
+        else k_quantize<4, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, keys, stream_id, stream_id, words, words, ld_words, scale, lm1);
         break;
     case 8:
-        if (two) k_quantize<8, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
-        else k_quantize<8, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, seed, stream_id, stream_id, words, words, ld_words, scale, lm1);
+        if (two) k_quantize<8, 2><<<nb, 256, 0, s>>>(in, rows, cols, ld, keys, stream_id, stream_id2, words, words2, ld_words, scale, lm1);
+        else k_quantize<8, 1><<<nb, 256, 0, s>>>(in, rows, cols, ld, keys, stream_id, stream_id, words, words, ld_words, scale, lm1);
         break;
     default: return cudaErrorInvalidValue;
     }
