@@ -81,7 +81,7 @@ def _gemv_bound(codes, bits, c, r, ref, L=None):
 
 
 @pytest.mark.parametrize("bits", [2, 4, 8])
-@pytest.mark.parametrize("ant_grid", SMALL + [(48, 128)])
+@pytest.mark.parametrize("ant_grid", SMALL + [(48, 128), (66, 16)])   # 66 antennas: 4288 baselines
 def test_fly_gemv_t(bits, ant_grid):
     p = synth.interferometry_gridded(ant_grid[0], ant_grid[1], n_src=4, s=4, seed=bits)
     op = _op(p)
