@@ -22,10 +22,12 @@
 namespace qiht {
 
 constexpr int kIterThreads = 512;
-// bytes of the next gradient pass's codes a thread brings into L2 (about 30 MB over the grid;
-// measured per iteration at 8192 x 32768, 8 bits: none 55.1 us, 256 B 53.7, 384 B 53.6,
-// 768 B 54.0, 1024 B 55.3, where the prefetch starts delaying the next pass's own reads)
-constexpr int kIterPrefetch = 384;
+// bytes of the next gradient pass's codes each CTA brings into L2, in one bulk request from one
+// thread (about 97 MB over the grid). Measured per iteration at 8192 x 32768, 8 bits: no prefetch
+// 55.1 us; 192 KB 52.6; 384 KB 52.2; 640 KB 52.1; 768 KB 52.1. The same bytes as 384-byte
+// requests from every thread cost ~1.2 us to issue (53.6 us). At 4 bits 50.6 -> 50.4 us, at 2 bits
+// 72.6 -> 72.0 us.
+constexpr unsigned kIterPrefetchCta = 640u * 1024u;
 constexpr int kListChunk = 1024;                          // list entries staged in shared memory at once
 constexpr unsigned long long kBarrierBudgetNs = 200ull * 1000 * 1000;
 
@@ -1442,11 +1444,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter_fast(IterArgs a)
     // meanwhile (issued earlier, it slows the step size's own reads). A hint only; nothing
     // waits on it.
     auto prefetch_next = [&]() {
-        if (BITS != 8) return;                      // below 8 bits the gradient pass is not HBM-bound
+        if (tid != 0) return;
         const size_t total = (size_t)a.n * (size_t)a.Q.ld * 4;
-        const size_t off = ((size_t)blockIdx.x * blockDim.x + tid) * kIterPrefetch;
+        const size_t off = (size_t)blockIdx.x * kIterPrefetchCta;
         if (off < total) {
-            const unsigned len = (unsigned)min((size_t)kIterPrefetch, total - off);   // a multiple of 16
+            const unsigned len = (unsigned)min((size_t)kIterPrefetchCta, total - off);   // a multiple of 16
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const char*>(a.q1_words) + off),
                          "r"(len)
                          : "memory");
