@@ -206,6 +206,123 @@ __device__ void mcols(const Codes& Q, const int* list, const float* coef, int co
     __syncthreads();
 }
 
+// ---- exact-integer column-subset products (8- and 4-bit codes) ----
+__device__ __forceinline__ uint32_t cdp4a_uu(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ int32_t cdp4a_us(uint32_t a, uint32_t b, int32_t c)
+{
+    int32_t d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// 4 x 4 byte transpose: out[p] byte u = byte p of in[u]
+__device__ __forceinline__ void transpose4(const uint32_t (&in)[4], uint32_t (&out)[4])
+{
+    const uint32_t t0 = __byte_perm(in[0], in[1], 0x5140), t1 = __byte_perm(in[0], in[1], 0x7362);
+    const uint32_t t2 = __byte_perm(in[2], in[3], 0x5140), t3 = __byte_perm(in[2], in[3], 0x7362);
+    out[0] = __byte_perm(t0, t2, 0x5410);
+    out[1] = __byte_perm(t0, t2, 0x7632);
+    out[2] = __byte_perm(t1, t3, 0x5410);
+    out[3] = __byte_perm(t1, t3, 0x7632);
+}
+
+// z[0..m) = sum over the list of coef_e (2 c_{i, list_e} - (L-1)), as exact integer sums: the
+// coefficients in 24-bit block fixed point, kappa_e = rn(coef_e 2^sh) with |kappa_e| <= 2^22 and
+// sh from max |coef|; four list entries' codes of a row (a byte transpose of their code words)
+// times the three byte planes of their kappa by dp4a; z_i = 2^-sh (2 sum_e kappa_e c_ie - (L-1)
+// sum_e kappa_e), rounded once to FP32. planes: scratch of 3 ceil(count / 4) words. A coefficient
+// that is not finite makes every z_i NaN.
+template <int BITS>
+__device__ void mcols_fx(const Codes& Q, const int* list, const float* coef, int count, float* z, uint32_t* planes,
+                         SSh& sh)
+{
+    static_assert(BITS == 8 || BITS == 4, "8- and 4-bit codes");
+    constexpr int WPT = BITS == 8 ? 2 : 1;      // code words of a column per thread
+    constexpr int R = 4 * WPT * (BITS == 4 ? 2 : 1);   // rows per thread
+    const int tid = threadIdx.x;
+    const int ld = Q.ld, m = Q.rows;
+    const int ng = (count + 3) / 4;
+    unsigned mx = 0;
+    for (int e = tid; e < count; e += kST) mx = max(mx, __float_as_uint(coef[e]) & 0x7fffffffu);
+    mx = smax(mx, sh.i);
+    const bool finite = mx < 0x7f800000u;
+    int fsh = 0;
+    if (finite && mx) {
+        int ex;
+        frexpf(__uint_as_float(mx), &ex);       // max |coef| < 2^ex
+        fsh = 22 - ex;
+    }
+    double ksum = 0.0;
+    for (int gq = tid; gq < ng; gq += kST) {
+        uint32_t p0 = 0, p1 = 0, p2 = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = 4 * gq + u;
+            const int kv = (e < count && finite) ? __float2int_rn(ldexpf(coef[e], fsh)) : 0;
+            ksum += (double)kv;
+            p0 |= (uint32_t)(kv & 255) << (8 * u);
+            p1 |= (uint32_t)((kv >> 8) & 255) << (8 * u);
+            p2 |= (uint32_t)((kv >> 16) & 255) << (8 * u);
+        }
+        planes[3 * gq] = p0;
+        planes[3 * gq + 1] = p1;
+        planes[3 * gq + 2] = p2;
+    }
+    const long long K = (long long)ssum(ksum, sh.d);   // exact (|K| < 2^31); its barriers publish the planes
+    const long long lk = (long long)Q.lm1 * K;
+    for (int rw = tid * WPT; rw < ld; rw += kST * WPT) {
+        uint32_t a0[R], a1[R];
+        int32_t a2[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { a0[r] = 0u; a1[r] = 0u; a2[r] = 0; }
+#pragma unroll 2
+        for (int gq = 0; gq < ng; ++gq) {
+            uint32_t w[WPT][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * gq + u;
+                const uint32_t* src = Q.words + (size_t)(e < count ? list[e] : 0) * ld + rw;
+                if (WPT == 2) {
+                    const uint2 v = e < count ? __ldg(reinterpret_cast<const uint2*>(src)) : make_uint2(0u, 0u);
+                    w[0][u] = v.x;
+                    w[WPT - 1][u] = v.y;
+                } else {
+                    w[0][u] = e < count ? __ldg(src) : 0u;
+                }
+            }
+            const uint32_t P0 = planes[3 * gq], P1 = planes[3 * gq + 1], P2 = planes[3 * gq + 2];
+#pragma unroll
+            for (int h = 0; h < WPT * (BITS == 4 ? 2 : 1); ++h) {
+                uint32_t in[4], T[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    in[u] = BITS == 8 ? w[h][u] : (h == 0 ? (w[0][u] & 0x0F0F0F0Fu) : ((w[0][u] >> 4) & 0x0F0F0F0Fu));
+                transpose4(in, T);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    a0[4 * h + p] = cdp4a_uu(T[p], P0, a0[4 * h + p]);
+                    a1[4 * h + p] = cdp4a_uu(T[p], P1, a1[4 * h + p]);
+                    a2[4 * h + p] = cdp4a_us(T[p], P2, a2[4 * h + p]);
+                }
+            }
+        }
+        // rows: 8 bits: 4 rw + r; 4 bits: 8 rw + r (low nibbles rows 0-3, high 4-7)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = (BITS == 8 ? 4 : 8) * rw + r;
+            if (i < m) {
+                const long long S = (long long)a0[r] + ((long long)a1[r] << 8) + ((long long)a2[r] << 16);
+                z[i] = finite ? ldexpf(__ll2float_rn(2 * S - lk), -fsh) : __int_as_float(0x7fc00000);
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // x_j of the current iterate (0 off the support): binary search of the ascending support
 __device__ __forceinline__ float x_at(const MSm& sm, int s, int j)
 {
@@ -250,6 +367,53 @@ __device__ int mkeys(int n, int s, float muf, const float* g, const MSm& sm, int
     return __syncthreads_or(bad);
 }
 
+// mkeys for a step from the support G, which also lists the candidates of H_s: the s-th
+// largest key is at least the smallest key on G (*kmin; the smallest of any s keys bounds it),
+// so H_s over all n keys is H_s over G and the entries off G whose key reaches *kmin. The list
+// gets G's s indices, then those entries (list[0 .. s + *ncand)), at most cap in all; *ncand is
+// -1 when they do not fit. *rest = the largest key off G. Returns nonzero if a key is not finite.
+__device__ int mkeys_cand(int n, int s, float muf, const float* g, const MSm& sm, int* sh, uint32_t* kmin,
+                          uint32_t* rest, int* list, int cap, int* ncand)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    int bad = 0;
+    unsigned inv_min = 0, cmax = 0;
+    for (int q = tid; q < s; q += kST) {
+        const int j = sm.sup[q];
+        const uint32_t k = __float_as_uint(fmaf(muf, __ldg(g + j), sm.xs[q])) & 0x7fffffffu;
+        sm.keys[j] = k;
+        list[q] = j;
+        bad |= k > 0x7f800000u;
+        inv_min = max(inv_min, ~k);
+    }
+    const uint32_t km = ~smax(inv_min, sh);
+    if (tid == 0) sh[35] = 0;                   // candidate count
+    __syncthreads();
+    for (int j = tid; j - lane < n; j += kST) { // warp-uniform trip count (the ballot below)
+        bool cand = false;
+        if (j < n && !((sm.gbit[j >> 5] >> (j & 31)) & 1u)) {
+            const uint32_t k = __float_as_uint(fmaf(muf, __ldg(g + j), 0.0f)) & 0x7fffffffu;
+            sm.keys[j] = k;
+            bad |= k > 0x7f800000u;
+            cmax = max(cmax, k);
+            cand = k >= km;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (bal) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&sh[35], __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int pos = s + base + __popc(bal & ((1u << lane) - 1u));
+            if (cand && pos < cap) list[pos] = j;
+        }
+    }
+    *rest = smax(cmax, sh);                     // its barriers make the count final
+    *kmin = km;
+    const int c = sh[35];
+    *ncand = s + c <= cap ? c : -1;
+    return __syncthreads_or(bad);
+}
+
 // H_s over the keys: the s largest, ties to the lower index. G' ascending in sel / val
 // (val = x'), the list x' - x over G' u G in uni / dlt (G \ G' after G', in support
 // order; only with with_old). Returns 1 if G' != G, else 0; *uc = entries of the list.
@@ -287,11 +451,19 @@ __device__ void radix_pick(const MSm& sm, SSh& sh, int need)
 // (val = x'), the list x' - x over G' u G in uni / dlt (G \ G' after G', in support
 // order; only with with_old). Returns 1 if G' != G, else 0; *uc = entries of the list.
 // list (capacity listcap ints, free shared memory) holds the candidates of the top digit's
-// bucket: the three later radix passes run over them only.
+// bucket: the three later radix passes run over them only. With given >= 0 the list already
+// holds every entry H_s can take (given of them, from mkeys_cand): all four passes run over it.
 __device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, SSh& sh, int* uc, bool with_old,
-                       int* list, int listcap)
+                       int* list, int listcap, int given = -1)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t prefix = 0;
+    int need = s, cnt = 0, pass0 = 1;
+    bool compact = true;
+    if (given >= 0) {
+        cnt = given;
+        pass0 = 0;
+    } else {
     // first digit (top 8 bits) over all keys
     if (tid < 256) sm.hist[tid] = 0;
     __syncthreads();
@@ -306,11 +478,10 @@ __device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, S
     }
     __syncthreads();
     radix_pick(sm, sh, s);
-    uint32_t prefix = (uint32_t)sh.i[0] << 24;
-    int need = s - sh.i[1];
+    prefix = (uint32_t)sh.i[0] << 24;
+    need = s - sh.i[1];
     const int c0 = sh.i[2];
-    const bool compact = c0 <= listcap;
-    int cnt = 0;
+    compact = c0 <= listcap;
     __syncthreads();
     if (compact) {
         // the bucket's keys into the list (order does not matter for the histograms)
@@ -331,14 +502,16 @@ __device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, S
         cnt = sh.i[3];
         __syncthreads();
     }
-    for (int pass = 1; pass < 4; ++pass) {
+    }
+    for (int pass = pass0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         if (tid < 256) sm.hist[tid] = 0;
         __syncthreads();
         if (compact) {
             for (int e = tid; e < cnt; e += kST) {
                 const uint32_t k = sm.keys[list[e]];
-                if ((k >> (shift + 8)) == (prefix >> (shift + 8))) atomicAdd(&sm.hist[(k >> shift) & 255u], 1u);
+                if (pass == 0 || (k >> (shift + 8)) == (prefix >> (shift + 8)))
+                    atomicAdd(&sm.hist[(k >> shift) & 255u], 1u);
             }
         } else {
             for (int b = warp * 32; b < n; b += kST) {
@@ -364,7 +537,16 @@ __device__ int mselect(int n, int s, float muf, const float* g, const MSm& sm, S
     // `need` keys): the selection is every key >= T, marked in one pass
     const bool all_ties = sh.i[2] == need;
     __syncthreads();
-    if (all_ties) {
+    if (all_ties && given >= 0) {
+        // the keys >= T are all in the list (the others are below *kmin <= T)
+        for (int w = tid; w < nbw; w += kST) sm.bitmap[w] = 0u;
+        __syncthreads();
+        for (int e = tid; e < cnt; e += kST) {
+            const int j = list[e];
+            if (sm.keys[j] >= T) atomicOr(&sm.bitmap[j >> 5], 1u << (j & 31));
+        }
+        __syncthreads();
+    } else if (all_ties) {
         for (int b = warp * 32; b < n; b += kST) {
             const int j = b + lane;
             const unsigned bal = __ballot_sync(0xffffffffu, j < n && sm.keys[j] >= T);

@@ -2,10 +2,13 @@
 // iteration except the gradient product, one CTA per right-hand side.
 //
 // The gradients of all right-hand sides come from one tensor-core GEMM (mrhs_gemm.cu);
-// the rest of an iteration is per right-hand side and runs here with the single-solve
-// arithmetic: the step size mu = ||g_G||^2 / ||Q2_G g_G||^2 (FP64 sums of FP32 products
-// with column subsets of Q2, summed in list order), H_s as a radix select over the
-// binary32 keys |fmaf(mu, g, x)| with ties to the lower index, the backtracking test
+// the rest of an iteration is per right-hand side and runs here: the step size
+// mu = ||g_G||^2 / ||Q2_G g_G||^2 (FP64 sums of squares; the product Q2_G g_G as exact
+// integer sums of the codes with the coefficients in 24-bit fixed point, rounded once to
+// FP32, at 8 and 4 bits, and FP32 products summed in list order at 2 bits), H_s over the
+// binary32 keys |fmaf(mu, g, x)| with ties to the lower index (a radix select over the
+// support and the entries off it whose key reaches the smallest key on it, which hold the
+// s largest; over all n when those do not fit), the backtracking test
 // omega = ||x' - x||^2 / ||Q2 (x' - x)||^2, and the residual r = Q(y) - Q2_G' x', updated
 // from the product the step already formed (Q2 (x' - x) of the backtracking test, or
 // mu Q2_G g_G when the support is unchanged), and directly as Q(y) - Q2_G' x' every few
@@ -86,6 +89,16 @@ __device__ void split_residual8(const float* r, int m, int mk8, int rhi, int k, 
 
 static_assert(2 * QIHT_MULTI_MAX_S <= kST, "the backtracking test gives each union entry its own thread");
 
+// the products over s columns (the step size's and the refresh's): exact integer sums at 8 and
+// 4 bits, FP32 at 2 bits
+template <int BITS>
+__device__ __forceinline__ void mcols_s(const Codes& Q, const int* list, const float* coef, int count, float* z,
+                                        uint32_t* scratch, SSh& sh)
+{
+    if constexpr (BITS == 2) mcols<BITS>(Q, list, coef, count, z, reinterpret_cast<float*>(scratch));
+    else mcols_fx<BITS>(Q, list, coef, count, z, scratch, sh);
+}
+
 template <int BITS>
 __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
 {
@@ -138,7 +151,7 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
 #pragma unroll
         for (int o = 16; o; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
     }
-    mcols<BITS>(a.Q2, sm.sup, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
+    mcols_s<BITS>(a.Q2, sm.sup, sm.val, s, sm.z, sm.keys, sh);
     // sums of squares: each thread's <= 16 terms in FP32, the CTA sum of the partials in FP64
     // (a per-element FP64 sum keeps the narrow FP64 pipe of this GPU busy for microseconds)
     float zzf = 0.0f;
@@ -168,7 +181,9 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
     int bt = 0, changed = 0, ranked = 0;
     for (;;) {
         uint32_t kmin = 0, rest = 0;
-        if (mkeys(n, s, sh.muf, g, sm, sh.i, &kmin, &rest)) { changed = -1; break; }
+        int ncand = -1;
+        int* clist = reinterpret_cast<int*>(sm.z);      // free here: the step size's product is in zmu
+        if (mkeys_cand(n, s, sh.muf, g, sm, sh.i, &kmin, &rest, clist, a.mk, &ncand)) { changed = -1; break; }
         if (kmin > rest) {
             // every key of G exceeds every other key: G' = G without ranking
             for (int q = tid; q < s; q += kST) {
@@ -180,7 +195,7 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
             __syncthreads();
             break;
         }
-        changed = mselect(n, s, sh.muf, g, sm, sh, &uc, true, reinterpret_cast<int*>(sm.z), a.mk);
+        changed = mselect(n, s, sh.muf, g, sm, sh, &uc, true, clist, a.mk, ncand >= 0 ? s + ncand : -1);
         ++ranked;
         if (!changed) break;
         // backtracking test on G' u G
@@ -261,7 +276,7 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
     float rrf = 0.0f;
     float* rk = a.resid + (size_t)k * m;
     if (a.refresh) {
-        mcols<BITS>(a.Q2, sm.sel, sm.val, s, sm.z, reinterpret_cast<float*>(sm.keys));
+        mcols_s<BITS>(a.Q2, sm.sel, sm.val, s, sm.z, sm.keys, sh);
         const float* yk = a.yhat + (size_t)k * m;
         for (int i = tid; i < m; i += kST) {
             const float ri = fmaf(-sh.alpha2f, sm.z[i], __ldg(yk + i));
