@@ -378,6 +378,18 @@ static WarpPlan plan_warp(const Codes& Q, int nsm)
     const int cpw = Q.bits == 2 ? kColsPerWarp : Q.bits == 4 ? kColsPerWarp4 : 1;
     const long long want = (((long long)Q.cols + cpw - 1) / cpw + kWarpThreads / 32 - 1) / (kWarpThreads / 32);
     if (grid > want) grid = want;
+    if (Q.bits == 8) {
+        // HBM-bound: no fewer CTAs than needed for the busiest warp's rounds of columns, so that
+        // every warp runs that many (32768 columns: 293 CTAs, ~7 columns per warp, in place of
+        // 304 CTAs with 6 or 7; measured 45.27 -> 44.7 us). At 4 and 2 bits the pass is bound by
+        // per-code work and wants every SM full (4 bits: 33.0 -> 38.8 us with the same rule).
+        const long long ngc = ((long long)Q.cols + cpw - 1) / cpw;
+        const long long w0 = grid * (kWarpThreads / 32);
+        const long long rounds = (ngc + w0 - 1) / w0;
+        const long long wneed = (ngc + rounds - 1) / rounds;
+        const long long gb = (wneed + kWarpThreads / 32 - 1) / (kWarpThreads / 32);
+        if (gb < grid) grid = gb;
+    }
     p.grid = (unsigned)(grid < 1 ? 1 : grid);
     p.ok = true;
     return p;
