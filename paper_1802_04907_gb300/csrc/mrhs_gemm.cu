@@ -227,6 +227,10 @@ struct GemmArgs {
     int ntn;                  // N tiles
     int rhi;                  // row of the first lo part in the R tensor (= nrhs_pad)
     int* status;
+    // tiles [0, nfull) take one CTA each over all nk stages; every later tile takes two, one per
+    // half of the stages ([0, khalf) and [khalf, nk)), whose products add into G (zeroed first)
+    int nfull;
+    int khalf;
 };
 
 template <int BITS, bool F8>
@@ -244,9 +248,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
 
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tm = blockIdx.x / a.ntn, tn = blockIdx.x % a.ntn;
+    int tile = blockIdx.x, kb = 0, ke = a.nk;
+    const bool part = (int)blockIdx.x >= a.nfull;
+    if (part) {
+        const int u = (int)blockIdx.x - a.nfull;
+        tile = a.nfull + (u >> 1);
+        if (u & 1) kb = a.khalf;
+        else ke = a.khalf;
+    }
+    const int tm = tile / a.ntn, tn = tile % a.ntn;
     const int m0 = tm * kTM * kMT, n0 = tn * kTN;
-    const int nk = a.nk;
 
     if (tid == 0) {
         for (int i = 0; i < Sh::stages; ++i) {
@@ -275,10 +286,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
         // ---- TMA producer of the R tiles (hi and lo parts) ----
         if (lane == 0) {
             int issued = 0;
-            for (int it = 0; it < nk; ++it) {
-                const int s = it % Sh::stages;
-                const unsigned u = (unsigned)(it / Sh::stages);
-                if (it >= Sh::stages && !bar_wait(&empty[s], (u & 1u) ^ 1u, &s_abort, a.status)) break;
+            for (int it = kb; it < ke; ++it) {
+                const int rr = it - kb;             // stages are counted from this CTA's first
+                const int s = rr % Sh::stages;
+                const unsigned u = (unsigned)(rr / Sh::stages);
+                if (rr >= Sh::stages && !bar_wait(&empty[s], (u & 1u) ^ 1u, &s_abort, a.status)) break;
                 bar_expect(&full_b[s], Sh::terms * Sh::bbytes);
 #pragma unroll
                 for (int t = 0; t < Sh::terms; ++t)
@@ -294,9 +306,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
     } else if (warp == 1) {
         // ---- MMA issuer ----
         if (lane == 0) {
-            for (int it = 0; it < nk; ++it) {
-                const int s = it % Sh::stages;
-                const unsigned par = (unsigned)(it / Sh::stages) & 1u;
+            for (int it = kb; it < ke; ++it) {
+                const int s = (it - kb) % Sh::stages;
+                const unsigned par = (unsigned)((it - kb) / Sh::stages) & 1u;
                 if (!bar_wait(&full_a[s], par, &s_abort, a.status)) break;
                 if (!bar_wait(&full_b[s], par, &s_abort, a.status)) break;
                 tc_fence_after();
@@ -310,7 +322,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
 #pragma unroll
                         for (int u = 0; u < Sh::terms; ++u) {
                             const uint64_t bd = sw64_desc(s_u32(stage_b(s, u)) + 32 * kk);
-                            const uint32_t acc = (it | kk | u) != 0;
+                            const uint32_t acc = ((it - kb) | kk | u) != 0;
                             if (F8) mma_f8(tmem + (uint32_t)(t * kTN), ad, bd, acc);
                             else mma_f16(tmem + (uint32_t)(t * kTN), ad, bd, acc);
                         }
@@ -337,22 +349,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
                 const int wo = it * WPS + q;
                 if (WPS >= 4) {
                     uint4 v = make_uint4(0, 0, 0, 0);
-                    if (colok && it < nk && wo + 4 <= ldw)
+                    if (colok && it < ke && wo + 4 <= ldw)
                         v = __ldg(reinterpret_cast<const uint4*>(col + wo));
                     w[q] = v.x; w[q + 1] = v.y; w[q + 2] = v.z; w[q + 3] = v.w;
                 } else {
                     uint2 v = make_uint2(0, 0);
-                    if (colok && it < nk && wo + 2 <= ldw)
+                    if (colok && it < ke && wo + 2 <= ldw)
                         v = __ldg(reinterpret_cast<const uint2*>(col + wo));
                     w[q] = v.x; w[q + 1] = v.y;
                 }
             }
         };
 #pragma unroll
-        for (int p = 0; p < PD; ++p) fetch(p, ring[p]);
-        for (int it = 0; it < nk; ++it) {
-            const int s = it % Sh::stages;
-            const unsigned u = (unsigned)(it / Sh::stages);
+        for (int p = 0; p < PD; ++p) fetch(kb + p, ring[p]);
+        for (int it = kb; it < ke; ++it) {
+            const int s = (it - kb) % Sh::stages;
+            const unsigned u = (unsigned)((it - kb) / Sh::stages);
             uint32_t cur[WPS];
 #pragma unroll
             for (int q = 0; q < WPS; ++q) {
@@ -362,7 +374,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
             }
             fetch(it + PD, ring[PD - 1]);
             // the whole warp leaves together (the arrive and the epilogue's loads are warp-wide)
-            if (it >= Sh::stages && !__all_sync(0xffffffffu, bar_wait(&empty[s], (u & 1u) ^ 1u, &s_abort, a.status)))
+            if (it - kb >= Sh::stages && !__all_sync(0xffffffffu, bar_wait(&empty[s], (u & 1u) ^ 1u, &s_abort, a.status)))
                 break;
             // the stage's codes of column j in K order -> f16 values (then e4m3), 64 bytes per row
             uint32_t h[Sh::tk / 2];
@@ -403,7 +415,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_mrhs_gemm(const __grid_cons
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int k = n0 + c0 + i;
-                    if (jj < a.Q.cols && k < a.nrhs) a.G[(size_t)k * a.ldg + jj] = __uint_as_float(v[i]) * a.sc[k];
+                    if (jj < a.Q.cols && k < a.nrhs) {
+                        const float gv = __uint_as_float(v[i]) * a.sc[k];
+                        if (part) atomicAdd(a.G + (size_t)k * a.ldg + jj, gv);   // two terms onto zero: order-free
+                        else a.G[(size_t)k * a.ldg + jj] = gv;
+                    }
                 }
             }
         } else if (!fin) {
@@ -490,6 +506,16 @@ __global__ void __launch_bounds__(256) k_mrhs_split8(const float* __restrict__ R
     if (threadIdx.x == 0) sc[k] = (float)ldexp((double)*scale / (double)lm1, e);
 }
 
+// G = 0 on the tiles [t0, t0 + gridDim.x / kTN) that two CTAs add into: one block per (tile,
+// right-hand side), one thread per column
+__global__ void __launch_bounds__(kTM * kMT) k_mrhs_zero_tiles(float* __restrict__ G, long long ldg, int n, int nrhs,
+                                                               int ntn, int t0)
+{
+    const int tile = t0 + (int)blockIdx.x / kTN, kk = (int)blockIdx.x % kTN;
+    const int tm = tile / ntn, tn = tile % ntn;
+    const int k = tn * kTN + kk, jj = tm * kTM * kMT + (int)threadIdx.x;
+    if (k < nrhs && jj < n) G[(size_t)k * ldg + jj] = 0.0f;
+}
 }  // namespace
 
 size_t mrhs_gemm_smem() { return (size_t)kStages * kStageBytes + 1024; }
@@ -587,10 +613,23 @@ cudaError_t launch_mrhs_gemm(const Codes& Q, const void* map, const float* sc, f
                                   : Q.bits == 4 ? (void*)k_mrhs_gemm<4, false> : (void*)k_mrhs_gemm<2, false>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // One CTA per SM: a last wave of few tiles would keep most SMs idle for a whole tile's time.
+    // When it holds at most half the SMs, each of its tiles is split into two halves of the
+    // stages (two CTAs adding into G), so the wave takes about half as long.
+    const int ntiles = ntm * a.ntn, nsm = num_sms();
+    const int tail = ntiles % nsm;
+    const bool split = ntiles > nsm && tail > 0 && 2 * tail <= nsm && a.nk >= 2;
+    a.nfull = split ? ntiles - tail : ntiles;
+    a.khalf = a.nk / 2;
+    if (split) {
+        k_mrhs_zero_tiles<<<(unsigned)(tail * kTN), kTM * kMT, 0, s>>>(G, ldg, Q.cols, nrhs, a.ntn, a.nfull);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     CUtensorMap m;
     memcpy(&m, map, sizeof(m));
     void* args[] = {(void*)&m, (void*)&a};
-    return cudaLaunchKernel(fn, dim3((unsigned)(ntm * a.ntn)), dim3(kGemmThreads), args, smem, s);
+    return cudaLaunchKernel(fn, dim3((unsigned)(split ? a.nfull + 2 * tail : ntiles)), dim3(kGemmThreads), args, smem, s);
 }
 
 }  // namespace qiht
