@@ -31,7 +31,7 @@ struct FlyCtx {
 
 __device__ __forceinline__ FlyDec fly_decision(float v, float c, float half, int lm1)
 {
-    const Decision d = quant_decide(v, c, half, lm1);
+    const Decision d = quant_decide(v, qscale(c), half, lm1);
     return FlyDec{(int)d.fi, (uint32_t)ceilf(d.f * 16777216.0f)};
 }
 

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, 
     __shared__ float tile[kQTileCols][kQTileRows + 1];
 
     const float c = *scale_p;
+    const QScale qs = qscale(c);
     const float half = (float)lm1 * 0.5f;
     const int row_tiles = (ldw * G + kQTileRows - 1) / kQTileRows;
     const int col_tiles = (cols + kQTileCols - 1) / kQTileCols;
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(256) k_quantize(const float* __restrict__ in, 
                             cur = qq;
                         }
                         const uint32_t sel = e & 3;
-                        const Decision d = quant_decide(tile[cc][q * G + kk], c, half, lm1);
+                        const Decision d = quant_decide(tile[cc][q * G + kk], qs, half, lm1);
 #pragma unroll
                         for (int st = 0; st < NS; ++st) {
                             const uint32_t rw = sel == 0 ? rnd[st].x : sel == 1 ? rnd[st].y : sel == 2 ? rnd[st].z : rnd[st].w;

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(256) k_sep_quantize(const float* __restrict__ 
                                                       float* __restrict__ out)
 {
     const float c = *scale;
+    const QScale qs = qscale(c);
     const float half = (float)lm1 * 0.5f;
     const double alpha = (double)c / (double)lm1;
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(256) k_sep_quantize(const float* __restrict__ 
         const uint4 rnd = philox4x32_10(make_uint4((uint32_t)qq, (uint32_t)(qq >> 32), stream_id, 0u), key0, key1);
         const uint32_t sel = (uint32_t)(e & 3);
         const uint32_t rw = sel == 0 ? rnd.x : sel == 1 ? rnd.y : sel == 2 ? rnd.z : rnd.w;
-        const Decision d = quant_decide(v[t], c, half, lm1);
+        const Decision d = quant_decide(v[t], qs, half, lm1);
         const uint32_t code = quant_code(d, lm1, (float)(rw >> 8) * 0x1p-24f);
         if (codes) codes[t] = (uint16_t)code;
         out[t] = (float)(alpha * (double)(2 * (int)code - lm1));
