@@ -19,8 +19,8 @@ Rule (Algorithm 2 run on both sides from bit-identical codes):
     accuracy degrades like (error of g) / ||g_G||, but its effect on x vanishes with g_G,
     and that effect is what the x tolerance bounds.
 Each check appends one JSON record (label, branch, first ambiguous iteration, errors) to
-the file named by QIHT_PARITY_LOG (default: gpurun_out/parity_results.jsonl at the
-repository root); conftest.py prints a summary at the end of the run.
+the file named by QIHT_PARITY_LOG (default: .pytest_cache/parity_results.jsonl at the
+repository root, a folder git ignores); conftest.py prints a summary at the end of the run.
 """
 from __future__ import annotations
 
@@ -35,7 +35,7 @@ MU_RTOL = 1e-4
 STEP_RTOL = 1e-4
 
 _ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-LOG = os.environ.get("QIHT_PARITY_LOG", os.path.join(_ROOT, "gpurun_out", "parity_results.jsonl"))
+LOG = os.environ.get("QIHT_PARITY_LOG", os.path.join(_ROOT, ".pytest_cache", "parity_results.jsonl"))
 RESULTS: list[dict] = []
 
 
