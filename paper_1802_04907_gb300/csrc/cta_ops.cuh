@@ -389,22 +389,35 @@ __device__ int mkeys_cand(int n, int s, float muf, const float* g, const MSm& sm
     const uint32_t km = ~smax(inv_min, sh);
     if (tid == 0) sh[35] = 0;                   // candidate count
     __syncthreads();
-    for (int j = tid; j - lane < n; j += kST) { // warp-uniform trip count (the ballot below)
-        bool cand = false;
-        if (j < n && !((sm.gbit[j >> 5] >> (j & 31)) & 1u)) {
-            const uint32_t k = __float_as_uint(fmaf(muf, __ldg(g + j), 0.0f)) & 0x7fffffffu;
-            sm.keys[j] = k;
-            bad |= k > 0x7f800000u;
-            cmax = max(cmax, k);
-            cand = k >= km;
+    // the entries of a thread in groups of KU, their loads of g issued together (one after the
+    // other, the pass is a chain of global-load latencies)
+    constexpr int KU = 8;
+    for (int j0 = tid; j0 - lane < n; j0 += KU * kST) {   // warp-uniform trip count (the ballots below)
+        float gv[KU];
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            const int j = j0 + u * kST;
+            gv[u] = j < n ? __ldg(g + j) : 0.0f;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, cand);
-        if (bal) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&sh[35], __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const int pos = s + base + __popc(bal & ((1u << lane) - 1u));
-            if (cand && pos < cap) list[pos] = j;
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            const int j = j0 + u * kST;
+            bool cand = false;
+            if (j < n && !((sm.gbit[j >> 5] >> (j & 31)) & 1u)) {
+                const uint32_t k = __float_as_uint(fmaf(muf, gv[u], 0.0f)) & 0x7fffffffu;
+                sm.keys[j] = k;
+                bad |= k > 0x7f800000u;
+                cmax = max(cmax, k);
+                cand = k >= km;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, cand);
+            if (bal) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&sh[35], __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const int pos = s + base + __popc(bal & ((1u << lane) - 1u));
+                if (cand && pos < cap) list[pos] = j;
+            }
         }
     }
     *rest = smax(cmax, sh);                     // its barriers make the count final

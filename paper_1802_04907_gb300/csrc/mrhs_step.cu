@@ -275,30 +275,40 @@ __global__ void __launch_bounds__(kST, 1) k_mrhs_step(MrhsStepArgs a)
     // directly r = Q(y) - alpha2 Q2_G' x' on refresh iterations (periodically and on the last)
     float rrf = 0.0f;
     float* rk = a.resid + (size_t)k * m;
+    // r_i = base_i - c prod_i for this thread's rows i = tid + kST u, in groups of RU whose loads
+    // are issued before any of their stores (a store to rk may alias a later load, so the
+    // compiler would otherwise wait on each load in turn); the sum of squares keeps row order
+    constexpr int RU = 8;
+    auto resid_rows = [&](const float* base, const float* prod, bool prod_shared, float c) {
+        for (int i0 = tid; i0 < m; i0 += RU * kST) {
+            float bv[RU], pv[RU];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int i = i0 + u * kST;
+                if (i < m) {
+                    bv[u] = __ldcg(base + i);
+                    pv[u] = prod_shared ? sm.z[i] : __ldcg(prod + i);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int i = i0 + u * kST;
+                if (i < m) {
+                    const float ri = fmaf(-c, pv[u], bv[u]);
+                    sm.z[i] = ri;
+                    rk[i] = ri;
+                    rrf = fmaf(ri, ri, rrf);
+                }
+            }
+        }
+    };
     if (a.refresh) {
         mcols_s<BITS>(a.Q2, sm.sel, sm.val, s, sm.z, sm.keys, sh);
-        const float* yk = a.yhat + (size_t)k * m;
-        for (int i = tid; i < m; i += kST) {
-            const float ri = fmaf(-sh.alpha2f, sm.z[i], __ldg(yk + i));
-            sm.z[i] = ri;
-            rk[i] = ri;
-            rrf = fmaf(ri, ri, rrf);
-        }
+        resid_rows(a.yhat + (size_t)k * m, nullptr, true, sh.alpha2f);
     } else if (changed) {
-        for (int i = tid; i < m; i += kST) {
-            const float ri = fmaf(-sh.alpha2f, sm.z[i], rk[i]);
-            sm.z[i] = ri;
-            rk[i] = ri;
-            rrf = fmaf(ri, ri, rrf);
-        }
+        resid_rows(rk, nullptr, true, sh.alpha2f);
     } else {
-        const float cz = sh.alpha2f * sh.muf;
-        for (int i = tid; i < m; i += kST) {
-            const float ri = fmaf(-cz, zmu[i], rk[i]);
-            sm.z[i] = ri;
-            rk[i] = ri;
-            rrf = fmaf(ri, ri, rrf);
-        }
+        resid_rows(rk, zmu, false, sh.alpha2f * sh.muf);
     }
     const double rr = ssum((double)rrf, sh.d);
     if (tid == 0) {
