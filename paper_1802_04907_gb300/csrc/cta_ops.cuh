@@ -346,11 +346,24 @@ __device__ int mkeys(int n, int s, float muf, const float* g, const MSm& sm, int
     const int tid = threadIdx.x;
     int bad = 0;
     unsigned cmax = 0, inv_min = 0;
-    for (int j = tid; j < n; j += kST) {
-        const uint32_t k = __float_as_uint(fmaf(muf, __ldg(g + j), 0.0f)) & 0x7fffffffu;
-        sm.keys[j] = k;
-        bad |= k > 0x7f800000u;
-        if (sh && !((sm.gbit[j >> 5] >> (j & 31)) & 1u)) cmax = max(cmax, k);
+    constexpr int KU = 8;                       // a thread's loads of g issued KU at a time
+    for (int j0 = tid; j0 < n; j0 += KU * kST) {
+        float gv[KU];
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            const int j = j0 + u * kST;
+            gv[u] = j < n ? __ldg(g + j) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            const int j = j0 + u * kST;
+            if (j < n) {
+                const uint32_t k = __float_as_uint(fmaf(muf, gv[u], 0.0f)) & 0x7fffffffu;
+                sm.keys[j] = k;
+                bad |= k > 0x7f800000u;
+                if (sh && !((sm.gbit[j >> 5] >> (j & 31)) & 1u)) cmax = max(cmax, k);
+            }
+        }
     }
     __syncthreads();
     for (int q = tid; q < s; q += kST) {
