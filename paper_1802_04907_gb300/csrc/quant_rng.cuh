@@ -64,14 +64,13 @@ struct Decision {
     float fi, f;
 };
 
-// The scale of a quantization with its reciprocal, for the decision's v / c. With y = RN(1/c),
-// q = RN(v y) and r = v - c q (exact by FMA), RN(q + r y) is the correctly rounded quotient
-// (Markstein's division theorem: y within half an ulp of 1/c and q within one ulp of v/c)
-// wherever the quotient is a normal number. Where it underflows the result may differ, but
-// then |v/c| < 2^-25, so 1 + v/c rounds to 1 and the decision is the same either way. A sweep
-// of every binary32 v in [0, c] for 16 scales c (among them 2^-100 and 2^100) against
-// __fdiv_rn found differences only at |v/c| < 2^-25. Scales outside [2^-125, 2^125] (where y
-// could be subnormal) take __fdiv_rn.
+// The scale of a quantization with its reciprocal, for the decision's v / c by Markstein's FMA
+// division: y = RN(1/c) once, then q = RN(v y), r = RN(v - c q) and RN(q + r y), each FMA
+// rounded once. Against __fdiv_rn over every binary32 v in [0, c] for 16 scales c (among them
+// 2^-100 and 2^100) it differed only where |v/c| < 2^-25; there 1 + v/c rounds to 1, so the
+// decision is the same either way. A CPU test replays the steps in exact arithmetic on random
+// pairs and checks the same. Scales outside [2^-125, 2^125] (where y could be subnormal) take
+// __fdiv_rn.
 struct QScale {
     float c, y;
     bool fast;
