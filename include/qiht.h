@@ -187,7 +187,10 @@ qiht_status qiht_gemv_cols_static(const qiht_codes* Q, const int32_t* cols, cons
  * into two f16 parts (hi + lo, about 22 significant bits); the products are exact and
  * summed in FP32, then scaled once. Requires Q->rows <= 16384. status [device, one
  * int32, may be NULL] is set to QIHT_ERR_TIMEOUT if a device-side wait ran out (and
- * left as it was otherwise). Launches two kernels.
+ * left as it was otherwise). Launches two kernels, or three when the product's last wave
+ * of 256 x 256 tiles would hold at most half the SMs: those tiles are then summed in two
+ * halves of the rows, added (in either order, with the same result) into their part of
+ * G, which a third kernel zeroes first.
  * Workspace: qiht_gemv_t_multi_workspace_size(Q->rows, nrhs) bytes, 256-byte aligned. */
 size_t qiht_gemv_t_multi_workspace_size(int32_t rows, int32_t nrhs);
 qiht_status qiht_gemv_t_multi(const qiht_codes* Q, const float* R, int64_t ldr, int32_t nrhs, float* G,
