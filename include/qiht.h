@@ -37,7 +37,9 @@
  * (i, j); element e uses output word e & 3 and u = (word >> 8) * 2^-24.
  * The rounding decision is taken in binary32: t = (v / c + 1) * (L - 1) / 2,
  * clamped to [0, L - 1], code = floor(t) + (u < t - floor(t)) (at most L - 1),
- * each operation correctly rounded.
+ * each operation correctly rounded. (The kernels divide by c with a reciprocal and
+ * two FMAs; where |v / c| < 2^-25 their quotient may differ in its last bits, but
+ * 1 + v / c rounds to 1 either way, so t and the code are the same.)
  */
 #ifndef QIHT_H
 #define QIHT_H
